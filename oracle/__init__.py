@@ -1,0 +1,256 @@
+"""FP64 CPU oracle for the recursive Hermite-regularized LBM (arXiv:1710.02065).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  The
+product library never calls it, and nothing here imports the product package.
+
+The arithmetic lives in ``rrlbm_oracle.c`` (plain loops, FP64); this module
+compiles it with the host C compiler and wraps it with ctypes/numpy.
+
+Each function cites the part of the paper it follows:
+  * ``feqH``      -- Eq. eqH with Eq. recursive1 (Sec. II.A)
+  * ``fneqH``     -- Eq. neqH with Eq. recursive2 at n = 3 (Sec. II.A)
+  * ``collide``   -- Eq. optimizedLB, and Eq. spongeLB / Eq. dampingLBM (Sec. II.C)
+  * ``Problem.step`` -- pull streaming (left side of Eq. optimizedLB) plus the
+    boundary rules of Sec. III (velocity inflow, zero-gradient outflow,
+    bounce-back walls) and the sponge layers of Sec. II.C.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rrlbm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+D2Q9, D3Q19 = 0, 1
+PERIODIC, VELOCITY, OUTFLOW = 0, 1, 2
+CS2 = 1.0 / 3.0
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (host C compiler)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cc = os.environ.get("CC", "gcc")
+        subprocess.check_call([cc, "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("lattice", C.c_int),
+        ("n", C.c_int * 3),
+        ("tau", C.c_double),
+        ("face_kind", C.c_int * 6),
+        ("u_face", (C.c_double * 3) * 6),
+        ("u_profile", C.POINTER(C.c_double) * 6),
+        ("noise_seed", C.c_uint64),
+        ("noise_amp", C.c_double),
+        ("sponge_width", C.c_int * 6),
+        ("sponge_chi", C.c_double * 6),
+        ("rho_ref", C.c_double),
+        ("u_ref", C.c_double * 3),
+        ("solid", C.POINTER(C.c_uint8)),
+        ("g", C.c_double * 3),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            dp = C.POINTER(C.c_double)
+            P = C.POINTER(_Problem)
+            _lib.orc_lattice.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(C.c_int), dp, C.POINTER(C.c_int)]
+            _lib.orc_feqH.argtypes = [C.c_int, C.c_double, dp, dp]
+            _lib.orc_fneqH.argtypes = [C.c_int, dp, dp, dp]
+            _lib.orc_collide.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double, dp, dp, dp]
+            _lib.orc_step.argtypes = [P, dp, dp, C.c_int64]
+            _lib.orc_run.argtypes = [P, dp, dp, C.c_int64, C.c_int64]
+            _lib.orc_update_cell.argtypes = [P, dp, C.c_int64, C.c_int64, dp]
+            _lib.orc_field_moments.argtypes = [P, dp, dp, dp, dp]
+            _lib.orc_init_equilibrium.argtypes = [P, dp, dp, dp]
+            _lib.orc_chi_at.argtypes = [P, C.c_int, C.c_int, C.c_int]
+            _lib.orc_chi_at.restype = C.c_double
+            _lib.orc_sigma.argtypes = [C.c_double, C.c_double]
+            _lib.orc_sigma.restype = C.c_double
+            _lib.orc_splitmix64.argtypes = [C.c_uint64]
+            _lib.orc_splitmix64.restype = C.c_uint64
+            _lib.orc_u01.argtypes = [C.c_uint64]
+            _lib.orc_u01.restype = C.c_double
+        return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def lattice(which: int):
+    """(d, q, xi[q,3] int, w[q], opp[q]) of D2Q9 (0) or D3Q19 (1)."""
+    d, q = C.c_int(), C.c_int()
+    xi = np.zeros(19 * 3, dtype=np.int32)
+    w = np.zeros(19)
+    opp = np.zeros(19, dtype=np.int32)
+    rc = lib().orc_lattice(which, C.byref(d), C.byref(q), xi.ctypes.data_as(C.POINTER(C.c_int)),
+                           _dp(w), opp.ctypes.data_as(C.POINTER(C.c_int)))
+    assert rc == 0
+    q = q.value
+    return d.value, q, xi.reshape(19, 3)[:q].copy(), w[:q].copy(), opp[:q].copy()
+
+
+def feqH(which: int, rho: float, u) -> np.ndarray:
+    """Hermite-regularized equilibrium, Eq. eqH (order 3, lattice-supported terms)."""
+    q = 9 if which == D2Q9 else 19
+    out = np.zeros(q)
+    lib().orc_feqH(which, float(rho), _dp(np.ascontiguousarray(u, dtype=np.float64)), _dp(out))
+    return out
+
+
+def fneqH(which: int, u, pi_neq) -> np.ndarray:
+    """Hermite-regularized off-equilibrium part, Eq. neqH with Eq. recursive2."""
+    q = 9 if which == D2Q9 else 19
+    out = np.zeros(q)
+    pn = np.ascontiguousarray(np.asarray(pi_neq, dtype=np.float64).reshape(9))
+    lib().orc_fneqH(which, _dp(np.ascontiguousarray(u, dtype=np.float64)), _dp(pn), _dp(out))
+    return out
+
+
+def collide(which: int, f, tau: float, chi: float = 0.0, rho_ref: float = 1.0,
+            u_ref=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """One cell's rrBGK collision, Eq. optimizedLB (Eq. spongeLB when chi > 0)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros_like(f)
+    lib().orc_collide(which, _dp(f), float(tau), float(chi), float(rho_ref),
+                      _dp(np.ascontiguousarray(u_ref, dtype=np.float64)),
+                      _dp(np.ascontiguousarray(g, dtype=np.float64)), _dp(out))
+    return out
+
+
+def sigma(d: float, width: float) -> float:
+    """Sponge profile of Sec. II.C, 3125 (W-d) d^4 / (256 W^5), d from the inner edge."""
+    return lib().orc_sigma(float(d), float(width))
+
+
+def splitmix64(x: int) -> int:
+    return int(lib().orc_splitmix64(C.c_uint64(x & (2**64 - 1))))
+
+
+def u01(counter: int) -> float:
+    return float(lib().orc_u01(C.c_uint64(counter & (2**64 - 1))))
+
+
+class Problem:
+    """A single-level lattice with its boundary rules, mirroring the C struct."""
+
+    def __init__(self, lattice: int, extents, tau: float):
+        self.lattice = lattice
+        n = list(extents) + [1] * (3 - len(extents))
+        if lattice == D2Q9:
+            n[2] = 1
+        self.n = tuple(int(v) for v in n)
+        self.q = 9 if lattice == D2Q9 else 19
+        self.tau = float(tau)
+        self.face_kind = [PERIODIC] * 6
+        self.u_face = [[0.0, 0.0, 0.0] for _ in range(6)]
+        self.u_profile = [None] * 6
+        self.noise_seed = 0
+        self.noise_amp = 0.0
+        self.sponge_width = [0] * 6
+        self.sponge_chi = [0.0] * 6
+        self.rho_ref = 1.0
+        self.u_ref = [0.0, 0.0, 0.0]
+        self.solid = None
+        self.g = [0.0, 0.0, 0.0]
+
+    @property
+    def ncell(self) -> int:
+        return self.n[0] * self.n[1] * self.n[2]
+
+    def set_boundary(self, face: int, kind: int, u=(0.0, 0.0, 0.0), profile=None):
+        self.face_kind[face] = kind
+        self.u_face[face] = [float(v) for v in u]
+        self.u_profile[face] = None if profile is None else np.ascontiguousarray(profile, dtype=np.float64)
+
+    def set_sponge(self, face: int, width: int, chi_max: float, rho_ref=1.0, u_ref=(0.0, 0.0, 0.0)):
+        self.sponge_width[face] = int(width)
+        self.sponge_chi[face] = float(chi_max)
+        self.rho_ref = float(rho_ref)
+        self.u_ref = [float(v) for v in u_ref]
+
+    def _struct(self) -> _Problem:
+        s = _Problem()
+        s.lattice = self.lattice
+        for a in range(3):
+            s.n[a] = self.n[a]
+            s.u_ref[a] = self.u_ref[a]
+            s.g[a] = self.g[a]
+        s.tau = self.tau
+        for f in range(6):
+            s.face_kind[f] = self.face_kind[f]
+            for a in range(3):
+                s.u_face[f][a] = self.u_face[f][a]
+            s.u_profile[f] = _dp(self.u_profile[f]) if self.u_profile[f] is not None else None
+            s.sponge_width[f] = self.sponge_width[f]
+            s.sponge_chi[f] = self.sponge_chi[f]
+        s.noise_seed = int(self.noise_seed)
+        s.noise_amp = float(self.noise_amp)
+        s.rho_ref = self.rho_ref
+        if self.solid is not None:
+            self._solid_keep = np.ascontiguousarray(self.solid.reshape(-1), dtype=np.uint8)
+            s.solid = self._solid_keep.ctypes.data_as(C.POINTER(C.c_uint8))
+        else:
+            s.solid = None
+        return s
+
+    def equilibrium(self, rho: np.ndarray, u: np.ndarray) -> np.ndarray:
+        """Field f = feqH(rho, u); rho shape (ncell,), u shape (ncell, 3)."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1, 3)
+        f = np.zeros(self.q * self.ncell)
+        s = self._struct()
+        lib().orc_init_equilibrium(C.byref(s), _dp(rho), _dp(u), _dp(f))
+        return f.reshape(self.q, self.ncell)
+
+    def run(self, f: np.ndarray, nsteps: int, step0: int = 0) -> np.ndarray:
+        """Advance a (q, ncell) field nsteps steps; returns the new field."""
+        f = np.array(f, dtype=np.float64, order="C").reshape(self.q, self.ncell)
+        work = np.empty_like(f)
+        s = self._struct()
+        lib().orc_run(C.byref(s), _dp(f), _dp(work), int(step0), int(nsteps))
+        return f
+
+    def update_cell(self, f: np.ndarray, cell: int, step: int = 0) -> np.ndarray:
+        """Post-collision populations of one cell from the full field f."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        out = np.zeros(self.q)
+        s = self._struct()
+        lib().orc_update_cell(C.byref(s), _dp(f), int(cell), int(step), _dp(out))
+        return out
+
+    def moments(self, f: np.ndarray):
+        """(rho[ncell], u[ncell,3], pi_neq[ncell,6]) of a stored field."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        rho = np.zeros(self.ncell)
+        u = np.zeros(3 * self.ncell)
+        pn = np.zeros(6 * self.ncell)
+        s = self._struct()
+        lib().orc_field_moments(C.byref(s), _dp(f), _dp(rho), _dp(u), _dp(pn))
+        return rho, u.reshape(-1, 3), pn.reshape(-1, 6)
+
+    def chi(self, x: int, y: int, z: int = 0) -> float:
+        s = self._struct()
+        return lib().orc_chi_at(C.byref(s), x, y, z)

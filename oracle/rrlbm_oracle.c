@@ -1,0 +1,529 @@
+/*
+ * FP64 CPU oracle for the recursive Hermite-regularized lattice Boltzmann
+ * update (rrBGK) of Brogi, Malaspinas, Chopard and Bonadonna, arXiv:1710.02065.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct
+ * restatement of the method that the CUDA library is checked against.  It is
+ * compiled and called only by tests/, by __graft_entry__.smoke() and by the
+ * CPU-baseline / reference legs of bench.py.  The product path never links,
+ * loads or calls it, and it shares no code, header or table with the CUDA
+ * sources: the lattice, the Hermite tensors and every boundary rule are
+ * written out again here from the paper.
+ *
+ * Conventions
+ *   - Populations are plain f_i (not shifted), one double per direction.
+ *     A field is stored direction-major: f[i * ncell + cell], with
+ *     cell = x + nx * (y + ny * z).
+ *   - The stored state is the post-collision field f*(t).  One step pulls
+ *     f_i(x) = f*_i(x - xi_i) (streaming, the left side of Eq. optimizedLB
+ *     evaluated at x), applies the boundary rules, and collides.
+ *   - Lattice units: dx = dt = 1, c_s^2 = 1/3.
+ *
+ * Readings of the paper taken here (it is silent or garbled on these):
+ *   R1  a^2 = Pi - rho c_s^2 I, a^2_eq = rho u u, a^2_neq = Pi^neq
+ *       (the printed a^2 = P - rho(uu - delta) is a garbled form), Sec. II.A.
+ *   R2  Eq. eqH is read with xi_i . u (the print drops the ". u"), and Eq. neqH
+ *       without the spurious rho prefactor and index i on a^2_neq.
+ *   R3  Third order on D3Q19: Sec. II.A defers to Malaspinas (2015).  The six
+ *       a_aab components are kept as the sum/difference pairs (xxy,yzz),
+ *       (xzz,xyy), (yyz,xxz), each projected with its own lattice norm, so that
+ *       the regularized populations reproduce a_p + a_q and a_p - a_q exactly.
+ *   R4  Sponge (Eq. spongeLB, Eq. dampingLBM): the modified moments use
+ *       n = m = 1/2 and rho* u* = j + m sum_i F_i xi_i, which close to
+ *       rho* = (rho + chi rho_ref / 2) / (1 + chi / 2) and
+ *       rho* u* = (j + chi rho_ref u_ref / 2) / (1 + chi / 2).
+ *       Pi^neq in a sponge cell is taken about rho*, u*.
+ *   R5  Sponge strength chi(x) = chi_max * sigma(d) with the polynomial
+ *       profile of Sec. II.C, sigma(d) = 3125 (W - d) d^4 / (256 W^5), where d
+ *       is the distance of the cell from the inner edge of a layer of W cells
+ *       (x0 = inner edge, L = x0 + W); overlapping layers take the maximum.
+ *   R6  Velocity inflow (Dirichlet, scheme not given in Sec. III): the node
+ *       takes rho and Pi^neq from its inward neighbour after streaming and
+ *       rebuilds f = feqH(rho, u_in) + fneqH(u_in, Pi^neq) before colliding.
+ *   R7  Outflow (zero gradient for all components, Sec. III): the node copies
+ *       the streamed populations of its inward neighbour and collides them.
+ *   R8  Walls: halfway bounce-back; a population that would stream out of a
+ *       solid cell is replaced by the node's own post-collision population in
+ *       the opposite direction.
+ *   R9  Inlet noise: counter-based uniform numbers from splitmix64 (Steele,
+ *       Lea and Flood 2014) keyed by (seed, step, face cell, component).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define CS2 (1.0 / 3.0)
+
+/* ------------------------------------------------------------------------ */
+/* Lattices (velocities and weights are the textbook Gauss-Hermite sets; the */
+/* paper only says they are specific to the lattice, Eq. truncatedEq).       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int d, q;
+    int xi[19][3];
+    double w[19];
+    int opp[19];
+} lattice_t;
+
+static void build_lattice(int which, lattice_t *L)
+{
+    /* Directions 1..Q/2 are listed; Q/2+1..Q-1 are their negatives in the
+     * same order, so that opp(i) = i +- Q/2.  Weight depends on |xi|^2. */
+    static const int d2q9_half[4][3] = {
+        {1, 0, 0}, {0, 1, 0}, {1, 1, 0}, {-1, 1, 0}};
+    static const int d3q19_half[9][3] = {
+        {1, 0, 0}, {0, 1, 0}, {0, 0, 1},
+        {1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
+    const int (*half)[3];
+    int h;
+    double w0, w1, w2;
+    if (which == 0) {
+        L->d = 2; L->q = 9; half = d2q9_half; h = 4;
+        w0 = 4.0 / 9.0; w1 = 1.0 / 9.0; w2 = 1.0 / 36.0;
+    } else {
+        L->d = 3; L->q = 19; half = d3q19_half; h = 9;
+        w0 = 1.0 / 3.0; w1 = 1.0 / 18.0; w2 = 1.0 / 36.0;
+    }
+    memset(L->xi, 0, sizeof L->xi);
+    for (int i = 0; i < h; ++i)
+        for (int a = 0; a < 3; ++a) {
+            L->xi[1 + i][a] = half[i][a];
+            L->xi[1 + h + i][a] = -half[i][a];
+        }
+    for (int i = 0; i < L->q; ++i) {
+        int n2 = L->xi[i][0] * L->xi[i][0] + L->xi[i][1] * L->xi[i][1] +
+                 L->xi[i][2] * L->xi[i][2];
+        L->w[i] = n2 == 0 ? w0 : (n2 == 1 ? w1 : w2);
+        for (int k = 0; k < L->q; ++k)
+            if (L->xi[k][0] == -L->xi[i][0] && L->xi[k][1] == -L->xi[i][1] &&
+                L->xi[k][2] == -L->xi[i][2])
+                L->opp[i] = k;
+    }
+}
+
+static const lattice_t *lattice(int which)
+{
+    static lattice_t lat[2];
+    static int ready[2];
+    if (!ready[which]) {
+        build_lattice(which, &lat[which]);
+        ready[which] = 1;
+    }
+    return &lat[which];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hermite polynomials on the lattice (Sec. II.A, Eq. HE and Eq. HEeqAndNeq) */
+/* ------------------------------------------------------------------------ */
+
+static double delta(int a, int b) { return a == b ? 1.0 : 0.0; }
+
+/* H^(2)_{i,ab} = xi_a xi_b - c_s^2 delta_ab */
+static double H2(const lattice_t *L, int i, int a, int b)
+{
+    return (double)L->xi[i][a] * L->xi[i][b] - CS2 * delta(a, b);
+}
+
+/* H^(3)_{i,abc} = xi_a xi_b xi_c - c_s^2 (xi_a d_bc + xi_b d_ac + xi_c d_ab) */
+static double H3(const lattice_t *L, int i, int a, int b, int c)
+{
+    double xa = L->xi[i][a], xb = L->xi[i][b], xc = L->xi[i][c];
+    return xa * xb * xc - CS2 * (xa * delta(b, c) + xb * delta(a, c) + xc * delta(a, b));
+}
+
+/* Third-order contribution T3_i(a) for a symmetric third-order tensor a,
+ * given as a full 3x3x3 array.  Only components the lattice supports are
+ * kept (reading R3 for D3Q19; on D2Q9 H_xxx = H_yyy = 0 and the surviving
+ * terms xxy, xyy carry the full-contraction multiplicity 3/3! = 1/2). */
+static double T3(const lattice_t *L, int i, double a[3][3][3])
+{
+    const double cs6 = CS2 * CS2 * CS2;
+    enum { X = 0, Y = 1, Z = 2 };
+    if (L->d == 2) {
+        return (H3(L, i, X, X, Y) * a[X][X][Y] + H3(L, i, X, Y, Y) * a[X][Y][Y]) /
+               (2.0 * cs6);
+    }
+    /* pairs (p, q): (xxy, yzz), (xzz, xyy), (yyz, xxz) */
+    static const int P[3][2][3] = {
+        {{X, X, Y}, {Y, Z, Z}},
+        {{X, Z, Z}, {X, Y, Y}},
+        {{Y, Y, Z}, {X, X, Z}}};
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const int *p = P[k][0], *q = P[k][1];
+        double hp = H3(L, i, p[0], p[1], p[2]);
+        double hq = H3(L, i, q[0], q[1], q[2]);
+        double ap = a[p[0]][p[1]][p[2]];
+        double aq = a[q[0]][q[1]][q[2]];
+        s += (hp + hq) * (ap + aq) / (2.0 * cs6) + (hp - hq) * (ap - aq) / (6.0 * cs6);
+    }
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Moments, equilibrium and non-equilibrium parts                             */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. moments plus the second moment Pi = sum_i f_i xi_i xi_i (Sec. II.A). */
+static void moments(const lattice_t *L, const double *f, double *rho, double j[3],
+                    double Pi[3][3])
+{
+    *rho = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        j[a] = 0.0;
+        for (int b = 0; b < 3; ++b) Pi[a][b] = 0.0;
+    }
+    for (int i = 0; i < L->q; ++i) {
+        *rho += f[i];
+        for (int a = 0; a < 3; ++a) {
+            j[a] += f[i] * L->xi[i][a];
+            for (int b = 0; b < 3; ++b) Pi[a][b] += f[i] * L->xi[i][a] * L->xi[i][b];
+        }
+    }
+}
+
+/* Eq. eqH with a^0 = rho, a^1 = rho u and, from Eq. recursive1,
+ * a^2_eq = rho u u, a^3_eq = rho u u u. */
+static void feqH(const lattice_t *L, double rho, const double u[3], double *out)
+{
+    const double cs4 = CS2 * CS2;
+    double a3[3][3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 3; ++c) a3[a][b][c] = rho * u[a] * u[b] * u[c];
+    for (int i = 0; i < L->q; ++i) {
+        double xu = 0.0, h2 = 0.0;
+        for (int a = 0; a < L->d; ++a) {
+            xu += L->xi[i][a] * rho * u[a];
+            for (int b = 0; b < L->d; ++b) h2 += H2(L, i, a, b) * rho * u[a] * u[b];
+        }
+        out[i] = L->w[i] * (rho + xu / CS2 + h2 / (2.0 * cs4) + T3(L, i, a3));
+    }
+}
+
+/* Eq. neqH with a^2_neq = Pi^neq and a^3_neq from Eq. recursive2 at n = 3:
+ * a^3_neq,abc = u_a Pi^neq_bc + u_b Pi^neq_ac + u_c Pi^neq_ab. */
+static void fneqH(const lattice_t *L, const double u[3], double Pn[3][3], double *out)
+{
+    const double cs4 = CS2 * CS2;
+    double a3[3][3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 3; ++c)
+                a3[a][b][c] = u[a] * Pn[b][c] + u[b] * Pn[a][c] + u[c] * Pn[a][b];
+    for (int i = 0; i < L->q; ++i) {
+        double h2 = 0.0;
+        for (int a = 0; a < L->d; ++a)
+            for (int b = 0; b < L->d; ++b) h2 += H2(L, i, a, b) * Pn[a][b];
+        out[i] = L->w[i] * (h2 / (2.0 * cs4) + T3(L, i, a3));
+    }
+}
+
+/* Pi^neq = Pi - rho c_s^2 I - rho u u (reading R1); components outside the
+ * lattice's d dimensions are zero. */
+static void pi_neq(int d, double rho, const double u[3], double Pi[3][3], double Pn[3][3])
+{
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            Pn[a][b] = (a < d && b < d) ? Pi[a][b] - rho * CS2 * delta(a, b) - rho * u[a] * u[b] : 0.0;
+}
+
+/* One cell's collision: Eq. optimizedLB, or Eq. spongeLB with
+ * Eq. dampingLBM when chi > 0 (reading R4).  g is a body force used only by
+ * the oracle's own Poiseuille check (momentum source w_i rho xi_i.g / c_s^2). */
+static void collide(const lattice_t *L, const double *f, double tau, double chi,
+                    double rho_ref, const double u_ref[3], const double g[3], double *out)
+{
+    double rho, j[3], Pi[3][3], u[3], Pn[3][3];
+    double feq[19], fneq[19];
+    moments(L, f, &rho, j, Pi);
+    if (chi > 0.0) {
+        double rs = (rho + 0.5 * chi * rho_ref) / (1.0 + 0.5 * chi);
+        double fref[19];
+        for (int a = 0; a < 3; ++a)
+            u[a] = (j[a] + 0.5 * chi * rho_ref * u_ref[a]) / (1.0 + 0.5 * chi) / rs;
+        pi_neq(L->d, rs, u, Pi, Pn);
+        feqH(L, rs, u, feq);
+        fneqH(L, u, Pn, fneq);
+        feqH(L, rho_ref, u_ref, fref);
+        for (int i = 0; i < L->q; ++i)
+            out[i] = feq[i] + (1.0 - 1.0 / tau) * fneq[i] + chi * (fref[i] - feq[i]);
+    } else {
+        for (int a = 0; a < 3; ++a) u[a] = j[a] / rho;
+        pi_neq(L->d, rho, u, Pi, Pn);
+        feqH(L, rho, u, feq);
+        fneqH(L, u, Pn, fneq);
+        for (int i = 0; i < L->q; ++i) out[i] = feq[i] + (1.0 - 1.0 / tau) * fneq[i];
+    }
+    if (g && (g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0))
+        for (int i = 0; i < L->q; ++i) {
+            double xg = 0.0;
+            for (int a = 0; a < 3; ++a) xg += L->xi[i][a] * g[a];
+            out[i] += L->w[i] * rho * xg / CS2;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Counter-based uniform numbers (reading R9)                                 */
+/* ------------------------------------------------------------------------ */
+
+uint64_t orc_splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+double orc_u01(uint64_t counter)
+{
+    return (double)(orc_splitmix64(counter) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Problem description                                                       */
+/* ------------------------------------------------------------------------ */
+
+enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_OUTFLOW = 2 };
+
+typedef struct {
+    int lattice;             /* 0 = D2Q9, 1 = D3Q19 */
+    int n[3];                /* extents; n[2] = 1 for D2Q9 */
+    double tau;
+    int face_kind[6];        /* -x, +x, -y, +y, -z, +z */
+    double u_face[6][3];     /* uniform velocity of a velocity face */
+    const double *u_profile[6]; /* optional per-face-cell velocity, 3 per cell */
+    uint64_t noise_seed;
+    double noise_amp;        /* relative amplitude of inlet noise (0 = none) */
+    int sponge_width[6];
+    double sponge_chi[6];
+    double rho_ref;
+    double u_ref[3];
+    const uint8_t *solid;    /* optional, 1 = solid, per cell */
+    double g[3];             /* oracle-only body force */
+} orc_problem;
+
+static int64_t ncell(const orc_problem *P) { return (int64_t)P->n[0] * P->n[1] * P->n[2]; }
+
+/* Tangential index of a cell on a face (fastest tangential axis first). */
+static int64_t face_index(const orc_problem *P, int face, const int c[3])
+{
+    int a = face / 2;
+    int t0 = a == 0 ? 1 : 0, t1 = a == 2 ? 1 : 2;
+    return (int64_t)c[t0] + (int64_t)P->n[t0] * c[t1];
+}
+
+static int64_t face_cells(const orc_problem *P, int face)
+{
+    int a = face / 2;
+    int t0 = a == 0 ? 1 : 0, t1 = a == 2 ? 1 : 2;
+    return (int64_t)P->n[t0] * P->n[t1];
+}
+
+/* Sponge profile of Sec. II.C for a layer of width W, d from the inner edge. */
+double orc_sigma(double d, double W)
+{
+    if (d < 0.0 || d > W) return 0.0;
+    return 3125.0 * (W - d) * d * d * d * d / (256.0 * W * W * W * W * W);
+}
+
+static double sponge_chi(const orc_problem *P, const int c[3])
+{
+    double chi = 0.0;
+    for (int face = 0; face < 6; ++face) {
+        int W = P->sponge_width[face];
+        if (W <= 0) continue;
+        int a = face / 2;
+        double d = (face % 2) ? (double)(c[a] - (P->n[a] - W)) : (double)(W - 1 - c[a]);
+        double s = P->sponge_chi[face] * orc_sigma(d, (double)W);
+        if (s > chi) chi = s;
+    }
+    return chi;
+}
+
+/* Post-collision populations of one cell at step `step` (the step that turns
+ * f*(step) into f*(step+1)), read from the full field fin. */
+void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int64_t step,
+                     double *out)
+{
+    const lattice_t *L = lattice(P->lattice);
+    const int64_t N = ncell(P);
+    int c[3], s[3];
+    c[0] = (int)(cell % P->n[0]);
+    c[1] = (int)((cell / P->n[0]) % P->n[1]);
+    c[2] = (int)(cell / ((int64_t)P->n[0] * P->n[1]));
+
+    if (P->solid && P->solid[cell]) {
+        for (int i = 0; i < L->q; ++i) out[i] = fin[(int64_t)i * N + cell];
+        return;
+    }
+
+    /* Boundary role and the node whose streamed populations are used (R6, R7). */
+    int inlet = -1;
+    for (int a = 0; a < 3; ++a) {
+        s[a] = c[a];
+        int lo = 2 * a, hi = 2 * a + 1;
+        if (P->face_kind[lo] != BC_PERIODIC && c[a] == 0) {
+            s[a] = 1;
+            if (P->face_kind[lo] == BC_VELOCITY && inlet < 0) inlet = lo;
+        }
+        if (P->face_kind[hi] != BC_PERIODIC && c[a] == P->n[a] - 1) {
+            s[a] = P->n[a] - 2;
+            if (P->face_kind[hi] == BC_VELOCITY && inlet < 0) inlet = hi;
+        }
+    }
+    int64_t scell = s[0] + (int64_t)P->n[0] * (s[1] + (int64_t)P->n[1] * s[2]);
+
+    /* Streaming: pull f_i(s) = f*_i(s - xi_i), periodic wrap, bounce-back (R8). */
+    double f[19];
+    for (int i = 0; i < L->q; ++i) {
+        int src[3];
+        for (int a = 0; a < 3; ++a) {
+            src[a] = s[a] - L->xi[i][a];
+            if (P->face_kind[2 * a] == BC_PERIODIC) src[a] = ((src[a] % P->n[a]) + P->n[a]) % P->n[a];
+        }
+        int64_t scl = src[0] + (int64_t)P->n[0] * (src[1] + (int64_t)P->n[1] * src[2]);
+        if (P->solid && P->solid[scl])
+            f[i] = fin[(int64_t)L->opp[i] * N + scell];
+        else
+            f[i] = fin[(int64_t)i * N + scl];
+    }
+
+    if (inlet >= 0) {
+        /* Velocity node (R6). */
+        double rho, j[3], Pi[3][3], us[3], ub[3], Pn[3][3], feq[19], fneq[19];
+        moments(L, f, &rho, j, Pi);
+        for (int a = 0; a < 3; ++a) us[a] = j[a] / rho;
+        pi_neq(L->d, rho, us, Pi, Pn);
+        int64_t k = face_index(P, inlet, c);
+        for (int a = 0; a < 3; ++a)
+            ub[a] = P->u_profile[inlet] ? P->u_profile[inlet][3 * k + a] : P->u_face[inlet][a];
+        if (P->noise_amp > 0.0) {
+            double mag = sqrt(ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+            if (mag > 0.0) {
+                uint64_t base = (P->noise_seed << 32) +
+                                ((uint64_t)step * (uint64_t)face_cells(P, inlet) + (uint64_t)k) * 3u;
+                for (int a = 0; a < L->d; ++a)
+                    ub[a] += P->noise_amp * mag * (2.0 * orc_u01(base + (uint64_t)a) - 1.0);
+            }
+        }
+        feqH(L, rho, ub, feq);
+        fneqH(L, ub, Pn, fneq);
+        for (int i = 0; i < L->q; ++i) out[i] = feq[i] + (1.0 - 1.0 / P->tau) * fneq[i];
+        return;
+    }
+
+    collide(L, f, P->tau, sponge_chi(P, c), P->rho_ref, P->u_ref, P->g, out);
+}
+
+/* One full step: fout = update(fin).  Returns 0. */
+int orc_step(const orc_problem *P, const double *fin, double *fout, int64_t step)
+{
+    const lattice_t *L = lattice(P->lattice);
+    const int64_t N = ncell(P);
+    double out[19];
+    for (int64_t cell = 0; cell < N; ++cell) {
+        orc_update_cell(P, fin, cell, step, out);
+        for (int i = 0; i < L->q; ++i) fout[(int64_t)i * N + cell] = out[i];
+    }
+    return 0;
+}
+
+/* nsteps steps starting at step index step0, ping-ponging between f and work;
+ * the result is left in f. */
+int orc_run(const orc_problem *P, double *f, double *work, int64_t step0, int64_t nsteps)
+{
+    const lattice_t *L = lattice(P->lattice);
+    const int64_t N = ncell(P);
+    double *a = f, *b = work;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        orc_step(P, a, b, step0 + t);
+        double *tmp = a; a = b; b = tmp;
+    }
+    if (a != f) memcpy(f, a, sizeof(double) * (size_t)N * (size_t)L->q);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exported single-cell pieces (for the oracle's own checks)                  */
+/* ------------------------------------------------------------------------ */
+
+int orc_lattice(int which, int *d, int *q, int *xi /* q*3 */, double *w, int *opp)
+{
+    if (which != 0 && which != 1) return -1;
+    const lattice_t *L = lattice(which);
+    *d = L->d;
+    *q = L->q;
+    for (int i = 0; i < L->q; ++i) {
+        for (int a = 0; a < 3; ++a) xi[3 * i + a] = L->xi[i][a];
+        w[i] = L->w[i];
+        opp[i] = L->opp[i];
+    }
+    return 0;
+}
+
+void orc_feqH(int which, double rho, const double *u, double *out)
+{
+    feqH(lattice(which), rho, u, out);
+}
+
+void orc_fneqH(int which, const double *u, const double *Pn9, double *out)
+{
+    double Pn[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Pn[a][b] = Pn9[3 * a + b];
+    fneqH(lattice(which), u, Pn, out);
+}
+
+void orc_collide(int which, const double *f, double tau, double chi, double rho_ref,
+                 const double *u_ref, const double *g, double *out)
+{
+    collide(lattice(which), f, tau, chi, rho_ref, u_ref, g, out);
+}
+
+/* Moments of a stored field: rho (N), u (3N, per cell xyz), Pi^neq (6N, per
+ * cell xx,xy,xz,yy,yz,zz; in 2D only xx,xy,yy are meaningful). */
+void orc_field_moments(const orc_problem *P, const double *fin, double *rho, double *u,
+                       double *pn6)
+{
+    const lattice_t *L = lattice(P->lattice);
+    const int64_t N = ncell(P);
+    for (int64_t cell = 0; cell < N; ++cell) {
+        double f[19], r, j[3], Pi[3][3], v[3], Pn[3][3];
+        for (int i = 0; i < L->q; ++i) f[i] = fin[(int64_t)i * N + cell];
+        moments(L, f, &r, j, Pi);
+        for (int a = 0; a < 3; ++a) v[a] = j[a] / r;
+        pi_neq(L->d, r, v, Pi, Pn);
+        if (rho) rho[cell] = r;
+        if (u)
+            for (int a = 0; a < 3; ++a) u[3 * cell + a] = v[a];
+        if (pn6) {
+            pn6[6 * cell + 0] = Pn[0][0];
+            pn6[6 * cell + 1] = Pn[0][1];
+            pn6[6 * cell + 2] = Pn[0][2];
+            pn6[6 * cell + 3] = Pn[1][1];
+            pn6[6 * cell + 4] = Pn[1][2];
+            pn6[6 * cell + 5] = Pn[2][2];
+        }
+    }
+}
+
+/* Initial state f = feqH(rho, u) per cell (rho: N, u: 3N). */
+void orc_init_equilibrium(const orc_problem *P, const double *rho, const double *u, double *f)
+{
+    const lattice_t *L = lattice(P->lattice);
+    const int64_t N = ncell(P);
+    for (int64_t cell = 0; cell < N; ++cell) {
+        double out[19];
+        feqH(L, rho[cell], u + 3 * cell, out);
+        for (int i = 0; i < L->q; ++i) f[(int64_t)i * N + cell] = out[i];
+    }
+}
+
+double orc_chi_at(const orc_problem *P, int x, int y, int z)
+{
+    int c[3] = {x, y, z};
+    return sponge_chi(P, c);
+}

@@ -1,0 +1,195 @@
+"""Whole-scheme pins of the oracle against what the physics fixes.
+
+  * Taylor-Green decay at nu = c_s^2 (tau - 1/2) (Sec. II.A, below Eq. truncatedEq)
+  * Poiseuille profile between halfway bounce-back walls (viscosity + walls)
+  * plane acoustic pulse moving at u0 +- c_s, c_s = 1/sqrt(3) (Sec. II.A, p = c_s^2 rho)
+  * exact global conservation on a periodic lattice (Eq. optimizedLB conserves
+    rho and rho u cell by cell; streaming only permutes populations)
+  * mass conservation in a closed bounce-back box
+  * a uniform stream is a fixed point of the inflow / outflow / sponge rules
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import D2Q9, D3Q19, CS2, VELOCITY, OUTFLOW
+from paper_1710_02065_gb300 import inputs
+
+
+def _fit_rate(ts, amps):
+    return -np.polyfit(ts, np.log(amps), 1)[0]
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8])
+def test_taylor_green_2d_viscosity(tau):
+    n = 64
+    P = oracle.Problem(D2Q9, (n, n), tau)
+    rho, u = inputs.taylor_green_2d(n, 0.01)
+    f = P.equilibrium(rho, u)
+    k = 2 * math.pi / n
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    basis = (np.sin(k * x) * np.cos(k * y)).reshape(-1)
+    ts, amps = [], []
+    for t in range(0, 401, 50):
+        if t:
+            f = P.run(f, 50, step0=t - 50)
+        _, uu, _ = P.moments(f)
+        ts.append(t)
+        amps.append((uu[:, 0] * basis).sum() / (basis * basis).sum())
+    nu_fit = _fit_rate(np.array(ts[1:]), np.array(amps[1:])) / (2 * k * k)
+    nu = CS2 * (tau - 0.5)
+    assert abs(nu_fit / nu - 1) < 0.01, (nu_fit, nu)
+
+
+def test_taylor_green_3d_viscosity():
+    n, tau = 24, 0.7
+    P = oracle.Problem(D3Q19, (n, n, n), tau)
+    rho, u = inputs.taylor_green_3d(n, 0.005)
+    f = P.equilibrium(rho, u)
+    k = 2 * math.pi / n
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    basis = (np.sin(k * x) * np.cos(k * y) * np.cos(k * z)).reshape(-1)
+    ts, amps = [], []
+    for t in range(0, 121, 30):
+        if t:
+            f = P.run(f, 30, step0=t - 30)
+        _, uu, _ = P.moments(f)
+        ts.append(t)
+        amps.append((uu[:, 0] * basis).sum() / (basis * basis).sum())
+    rate = _fit_rate(np.array(ts[1:]), np.array(amps[1:]))
+    nu_fit = rate / (3 * k * k)
+    nu = CS2 * (tau - 0.5)
+    assert abs(nu_fit / nu - 1) < 0.02, (nu_fit, nu)
+
+
+def test_poiseuille_between_bounce_back_walls():
+    """Body-force channel: u(y) = g/(2 nu) (y - 1/2)(H + 1/2 - y), walls halfway."""
+    H, tau, g = 24, 0.8, 2e-6
+    nx, ny = 2, H + 2
+    P = oracle.Problem(D2Q9, (nx, ny), tau)
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = 1
+    solid[-1, :] = 1
+    P.solid = solid.reshape(-1)
+    P.g = [g, 0.0, 0.0]
+    rho = np.ones(nx * ny)
+    u = np.zeros((nx * ny, 3))
+    f = P.equilibrium(rho, u)
+    f = P.run(f, 12000)
+    _, uu, _ = P.moments(f)
+    ux = uu[:, 0].reshape(ny, nx)[1:-1, 0]
+    nu = CS2 * (tau - 0.5)
+    yy = np.arange(1, H + 1)
+    exact = g / (2 * nu) * (yy - 0.5) * (H + 0.5 - yy)
+    err = np.linalg.norm(ux - exact) / np.linalg.norm(exact)
+    assert err < 0.01, err
+
+
+def test_plane_acoustic_pulse_speed():
+    """A planar pulse splits into waves at u0 + c_s and u0 - c_s."""
+    nx, ny, u0, tau = 400, 2, 0.05, 0.6
+    P = oracle.Problem(D2Q9, (nx, ny), tau)
+    rho, u = inputs.plane_pulse_2d(nx, ny, 1e-3, 6.0, u0)
+    f = P.equilibrium(rho, u)
+    ts, right, left = [], [], []
+
+    def peak(prof, lo, hi):
+        i = lo + int(np.argmax(prof[lo:hi]))
+        a, b, c = prof[i - 1], prof[i], prof[i + 1]
+        return i + 0.5 * (a - c) / (a - 2 * b + c)
+
+    for t in range(0, 121, 20):
+        if t:
+            f = P.run(f, 20, step0=t - 20)
+        r, _, _ = P.moments(f)
+        prof = r.reshape(ny, nx)[0] - 1.0
+        if t >= 40:
+            ts.append(t)
+            right.append(peak(prof, nx // 2 + 5, nx - 2))
+            left.append(peak(prof, 2, nx // 2 - 5))
+    cr = np.polyfit(ts, right, 1)[0]
+    cl = np.polyfit(ts, left, 1)[0]
+    cs = 1 / math.sqrt(3)
+    assert abs(cr - (u0 + cs)) / cs < 0.01, cr
+    assert abs(cl - (u0 - cs)) / cs < 0.01, cl
+
+
+def test_acoustic_pulse_2d_global_conservation():
+    """The D2Q9 128^2 periodic Gaussian pulse (tau = 0.6, u0 = (0.05, 0)):
+    total mass and momentum are invariant to round-off over 200 steps."""
+    n = 128
+    P = oracle.Problem(D2Q9, (n, n), 0.6)
+    rho, u = inputs.gaussian_pulse_2d(n, 1e-3, 6.0, (0.05, 0.0))
+    f = P.equilibrium(rho, u)
+    _, _, xi, _, _ = oracle.lattice(D2Q9)
+    m0 = f.sum()
+    j0 = (f * xi[:, 0:1]).sum()
+    f = P.run(f, 200)
+    assert abs(f.sum() - m0) / m0 < 1e-13
+    assert abs((f * xi[:, 0:1]).sum() - j0) / abs(j0) < 1e-12
+    assert abs((f * xi[:, 1:2]).sum()) < 1e-12 * m0
+
+
+@pytest.mark.parametrize("which", [D2Q9, D3Q19])
+def test_closed_bounce_back_box_conserves_mass(which):
+    n = (12, 10, 8) if which == D3Q19 else (16, 12)
+    P = oracle.Problem(which, n, 0.7)
+    shape = tuple(reversed(P.n))
+    solid = np.zeros(shape, np.uint8)
+    solid[:, 0, :] = solid[:, -1, :] = 1
+    solid[:, :, 0] = solid[:, :, -1] = 1
+    if which == D3Q19:
+        solid[0] = solid[-1] = 1
+    solid[shape[0] // 2, shape[1] // 2, shape[2] // 2] = 1  # an obstacle inside
+    P.solid = solid.reshape(-1)
+    _, _, _, w, _ = oracle.lattice(which)
+    f = inputs.random_populations(w, P.ncell, seed=3, spread=0.05)
+    fluid = solid.reshape(-1) == 0
+    m0 = f[:, fluid].sum()
+    f = P.run(f, 50)
+    assert abs(f[:, fluid].sum() - m0) / m0 < 1e-13
+
+
+@pytest.mark.parametrize("which", [D2Q9, D3Q19])
+def test_uniform_stream_is_fixed_point_of_open_boundaries(which):
+    """Velocity inlet on -x, zero-gradient outflow on +x, sponge layers with the
+    stream as reference: a uniform stream stays uniform to round-off."""
+    U = 0.08
+    if which == D2Q9:
+        P = oracle.Problem(D2Q9, (40, 12), 0.6)
+    else:
+        P = oracle.Problem(D3Q19, (20, 8, 6), 0.6)
+    P.set_boundary(0, VELOCITY, (U, 0, 0))
+    P.set_boundary(1, OUTFLOW)
+    for face in ([1, 2, 3] if which == D2Q9 else [1, 2, 3, 4, 5]):
+        P.set_sponge(face, 5, 0.5, 1.0, (U, 0, 0))
+    if which == D3Q19:
+        for face in (2, 3, 4, 5):
+            P.set_boundary(face, OUTFLOW)
+    rho = np.ones(P.ncell)
+    u = np.zeros((P.ncell, 3))
+    u[:, 0] = U
+    f0 = P.equilibrium(rho, u)
+    f = P.run(f0, 30)
+    assert np.abs(f - f0).max() < 1e-15
+
+
+def test_inlet_noise_statistics():
+    """Seeded inlet noise is within +-amp*|u_in| per component and averages out."""
+    U, amp = 0.1, 0.01
+    P = oracle.Problem(D2Q9, (8, 400), 0.6)
+    P.set_boundary(0, VELOCITY, (U, 0, 0))
+    P.set_boundary(1, OUTFLOW)
+    P.noise_seed, P.noise_amp = 3, amp
+    rho = np.ones(P.ncell)
+    u = np.zeros((P.ncell, 3)); u[:, 0] = U
+    f = P.equilibrium(rho, u)
+    f = P.run(f, 1)
+    _, uu, _ = P.moments(f)
+    inlet = uu.reshape(400, 8, 3)[:, 0, :]
+    dv = inlet[:, :2] - np.array([U, 0])
+    assert np.abs(dv).max() <= amp * U * (1 + 1e-12)
+    assert abs(dv.mean()) < 0.2 * amp * U
+    assert dv.std() > 0.4 * amp * U  # uniform on [-a, a] has std a/sqrt(3)
