@@ -1,0 +1,402 @@
+"""Benchmark of the fused rrBGK stream+collide update on GB300.
+
+Default workload: the D3Q19 round jet, 384 x 256 x 256 cells, FP32 population
+storage (top-hat velocity inflow of diameter 24 at Ma 0.3 with 1% seeded
+noise, ambient at rest, 32-cell sponges and zero-gradient outflow on the five
+open faces, tau for Re_D = 1e4).  One "step" is one time step of the whole
+lattice: one launch of the fused kernel.
+
+Prints one JSON line (rank 0).  `value` is whole-job MLUPS (cells x steps /
+s) with the populations resident in HBM; `e2e` is the same metric through
+the public C ABI with host buffers (initial rho, u uploaded and final rho, u
+read back inside the timed region).  `roofline` reports the fused kernel's
+algorithmic HBM bandwidth (2 Q s bytes per cell update) against the measured
+copy bandwidth.  `cpu_baseline` times the FP64 CPU oracle on a bounded sample.
+
+--impl reference times the FP64 CPU oracle itself on that sample.
+--gpus N under torchrun runs N independent replicas (one solve per GPU; a
+single solve is not sharded), weak scaling, max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % of HBM roofline, D3Q19 regularized LBM; FP16-store speedup; p99 latency"
+CS = 1.0 / math.sqrt(3.0)
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def jet_spec(nx=384, ny=256, nz=256, diameter=24.0, sponge=32, Ma=0.3, Re=1e4, chi=0.5, seed=3,
+             noise=0.01):
+    U = Ma * CS
+    tau = 3 * U * diameter / Re + 0.5
+    return dict(n=(nx, ny, nz), diameter=diameter, sponge=sponge, U=U, tau=tau, chi=chi, seed=seed,
+                noise=noise)
+
+
+def configure_gpu(lbm, spec, precision, stream):
+    from paper_1710_02065_gb300 import inputs
+    nx, ny, nz = spec["n"]
+    s = lbm.Solver(lbm.LBM_D3Q19, spec["n"], spec["tau"], precision, Ma_ref=0.3, stream=stream)
+    prof = inputs.top_hat_profile(ny, nz, ny / 2, nz / 2, spec["diameter"] / 2, spec["U"])
+    lbm.lbm_set_boundary(s.h, lbm.LBM_FACE_XM, lbm.LBM_BC_VELOCITY, None, prof)
+    for f in range(1, 6):
+        lbm.lbm_set_boundary(s.h, f, lbm.LBM_BC_OUTFLOW)
+        lbm.lbm_set_sponge(s.h, f, spec["sponge"], spec["chi"], 1.0, (0.0, 0.0, 0.0))
+    lbm.lbm_set_inlet_noise(s.h, spec["seed"], spec["noise"])
+    return s
+
+
+def configure_oracle(spec):
+    import oracle
+    from paper_1710_02065_gb300 import inputs
+    nx, ny, nz = spec["n"]
+    P = oracle.Problem(oracle.D3Q19, spec["n"], spec["tau"])
+    prof = inputs.top_hat_profile(ny, nz, ny / 2, nz / 2, spec["diameter"] / 2, spec["U"])
+    P.set_boundary(0, oracle.VELOCITY, (0, 0, 0), prof)
+    for f in range(1, 6):
+        P.set_boundary(f, oracle.OUTFLOW)
+        P.set_sponge(f, spec["sponge"], spec["chi"], 1.0, (0, 0, 0))
+    P.noise_seed, P.noise_amp = spec["seed"], spec["noise"]
+    n = P.ncell
+    f = P.equilibrium(np.ones(n), np.zeros((n, 3)))
+    return P, f
+
+
+SAMPLE_SPEC = dict(nx=96, ny=64, nz=64, diameter=6.0, sponge=8)  # the jet scaled by 1/4
+REF_SAMPLE_SPEC = dict(nx=64, ny=48, nz=48, diameter=4.5, sponge=6)  # about 0.3 s per oracle step
+
+
+def time_oracle(max_seconds=15.0, max_steps=40, min_steps=2):
+    """MLUPS of the FP64 CPU oracle (one thread) on the jet scaled to 96 x 64 x 64."""
+    spec = jet_spec(**SAMPLE_SPEC)
+    P, f = configure_oracle(spec)
+    f = P.run(f, 1)  # warm-up (builds the oracle)
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps and (steps < min_steps or time.perf_counter() - t0 < max_seconds):
+        f = P.run(f, 1, step0=1 + steps)
+        steps += 1
+    dt = time.perf_counter() - t0
+    mlups = P.ncell * steps / dt / 1e6
+    return mlups, steps, dt, P.ncell
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("rr.cuh", "step.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1710_02065_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel_key and parts[1] == src:
+            return float(parts[2])
+    return None
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(v: float, pg, world: int) -> float:
+    if pg is None or world == 1:
+        return v
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+# ---------------------------------------------------------------------------
+# timing of one precision
+# ---------------------------------------------------------------------------
+def time_precision(lbm, torch, spec, precision, steps, warmup, pg, stream):
+    s = configure_gpu(lbm, spec, precision, stream.cuda_stream)
+    n = s.ncell
+    s.set_state(np.ones(n), np.zeros((n, 3)))
+    lbm.lbm_step(s.h, warmup)
+    s.sync()
+    info0 = s.info()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    barrier(pg)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(steps):
+            lbm.lbm_step(s.h, 1)
+            ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    total_ms = ev[0].elapsed_time(ev[steps])
+    info1 = s.info()
+    m, j, rc = s.reduce()
+    s.close()
+    return dict(total_ms=total_ms, per_ms=per, launches=info1["launches"] - info0["launches"],
+                bytes_per_cell=info1["bytes_per_cell"], ncell=n, stable=(rc == 0))
+
+
+def e2e_run(lbm, torch, spec, precision, steps, stream):
+    """Through the public API with host buffers: upload rho, u from pinned
+    memory, advance `steps`, read rho, u back."""
+    s = configure_gpu(lbm, spec, precision, stream.cuda_stream)
+    n = s.ncell
+    rho_t = torch.ones(n, dtype=torch.float64).pin_memory()
+    u_t = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+    rho_o = torch.empty(n, dtype=torch.float64).pin_memory()
+    u_o = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    rho, u, ro, uo = rho_t.numpy(), u_t.numpy(), rho_o.numpy(), u_o.numpy()
+    # one untimed pass to page everything in
+    s.set_state(rho, u)
+    lbm.lbm_step(s.h, 2)
+    lbm.lbm_moments(s.h, ro, uo, None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_state(rho, u)
+    lbm.lbm_step(s.h, steps)
+    lbm.lbm_moments(s.h, ro, uo, None)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    return dict(seconds=dt, h2d=(rho.nbytes + u.nbytes) / steps, d2h=(ro.nbytes + uo.nbytes) / steps)
+
+
+# ---------------------------------------------------------------------------
+# main
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    """The FP64 CPU oracle, timed on the host cores on the jet scaled to 96x64x64."""
+    if rank != 0:
+        return
+    spec = jet_spec(**REF_SAMPLE_SPEC)
+    P, f = configure_oracle(spec)
+    for k in range(args.warmup):
+        f = P.run(f, 1, step0=k)
+    t0 = time.perf_counter()
+    f = P.run(f, args.steps, step0=args.warmup)
+    dt = time.perf_counter() - t0
+    mlups = P.ncell * args.steps / dt / 1e6
+    sample = f"D3Q19 round jet scaled to 64x48x48 (D=4.5, sponge 6), FP64 oracle, {args.steps} timed steps"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "D3Q19 round jet 384x256x256 (bounded sample 64x48x48 on host cores)",
+                   "parallelism": "none (host, 1 thread)"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the other storage precisions")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world, rank, local, pg = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1710_02065_gb300 import build
+    if rank == 0:
+        build.build()
+    barrier(pg)
+    from paper_1710_02065_gb300 import lbm
+
+    spec = jet_spec()
+    prec = lbm.PRECISIONS[args.precision]
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    main_run = time_precision(lbm, torch, spec, prec, args.steps, args.warmup, pg, stream)
+    clk = clocks.stop()
+    total_s = max_over_ranks(main_run["total_ms"] / 1e3, pg, world)
+    ncell = main_run["ncell"]
+    value = world * ncell * args.steps / total_s / 1e6
+    per = np.array(main_run["per_ms"])
+    kernel_ms = float(per.mean())
+    bpc = main_run["bytes_per_cell"]
+    achieved = bpc * ncell / (kernel_ms / 1e3) / 1e9
+    peaks = measured_peaks()
+    if peaks and "hbm_gbs" in peaks:
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    key = f"k_stream_collide_d3q19_{args.precision}_jet384"
+    traffic = recorded_traffic(key)
+
+    extra = {}
+    if not args.no_extra:
+        for name in ("fp16", "bf16", "fp64"):
+            if name == args.precision:
+                continue
+            r = time_precision(lbm, torch, spec, lbm.PRECISIONS[name], max(20, args.steps // 4),
+                               args.warmup, pg, stream)
+            k_ms = float(np.mean(r["per_ms"]))
+            extra[name] = {"mlups": r["ncell"] / (k_ms / 1e3) / 1e6,
+                           "gbs": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9,
+                           "frac_of_measured_hbm": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9 / peak}
+        if "fp16" in extra:
+            extra["fp16_store_speedup"] = extra["fp16"]["mlups"] / (ncell / (kernel_ms / 1e3) / 1e6)
+        if "bf16" in extra:
+            extra["bf16_store_speedup"] = extra["bf16"]["mlups"] / (ncell / (kernel_ms / 1e3) / 1e6)
+
+    e2e = e2e_run(lbm, torch, spec, prec, args.steps, stream)
+    e2e_s = max_over_ranks(e2e["seconds"], pg, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        mlups_cpu, st, dt, nc = time_oracle()
+        cpu = {"value": mlups_cpu, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"D3Q19 round jet scaled to 96x64x64 ({nc} cells), {st} FP64 steps in {dt:.1f} s, 1 thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": f"D3Q19 round jet 384x256x256, {args.precision} population storage, "
+                                   "two-lattice pull, fused inflow/outflow/sponge",
+                       "cells": ncell, "tau": spec["tau"], "storage": args.precision,
+                       "l2": "inputs larger than L2 (populations %.2f GB per lattice)" % (bpc / 2 * ncell / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                         "kernel": "k_stream_collide<D3Q19>", "bytes_per_cell": bpc,
+                         "kernel_ms": kernel_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * ncell * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+            "gpu_launches": main_run["launches"],
+            "clocks": clk,
+            "stable": main_run["stable"],
+            "extra": extra,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

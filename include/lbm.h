@@ -1,0 +1,251 @@
+/*
+ * lbm.h -- C ABI of liblbm, a GB300 (sm_103a) implementation of the fused
+ * stream-and-collide update of the recursive Hermite-regularized lattice
+ * Boltzmann method (rrBGK) of Brogi, Malaspinas, Chopard and Bonadonna,
+ * "Hermite regularization of the lattice Boltzmann method for open source
+ * computational aeroacoustics", arXiv:1710.02065.
+ *
+ * The problem the library solves is the one of Sec. II: given a lattice
+ * (D2Q9 or D3Q19), a box of cells, a relaxation time tau (or a viscosity
+ * nu = c_s^2 (tau - 1/2), Sec. II.A) and the boundary treatment of Sec. III
+ * (bounce-back walls, velocity inflow, zero-gradient outflow, absorbing
+ * sponge layers of Sec. II.C), advance the populations f_i in time with
+ *     f_i(x + xi_i, t + 1) = feqH_i(x, t) + (1 - 1/tau) fneqH_i(x, t)
+ * (Eq. optimizedLB; Eq. spongeLB inside sponge layers).
+ *
+ * Conventions shared by every entry point
+ *   - Lattice units: dx = dt = 1, c_s^2 = 1/3.
+ *   - Cells are numbered x fastest: cell = x + nx * (y + ny * z); a 2D
+ *     lattice has nz = 1.
+ *   - Directions follow the order reported by lbm_lattice_table(): 0 is the
+ *     rest velocity; directions 1..Q/2 and Q/2+1..Q-1 are opposite pairs
+ *     (opp(i) = i + Q/2 for 1 <= i <= Q/2).
+ *   - Population arrays exchanged with the caller are plain (unshifted) f_i
+ *     in FP64, direction-major: f[i * ncell + cell].
+ *   - The state held by a handle is the post-collision field after the last
+ *     step (after lbm_set_state / lbm_set_populations: the field given).
+ *     One step pulls f_i(x) = f*_i(x - xi_i), applies the boundary rules and
+ *     collides.  Moments reported by lbm_moments / lbm_reduce / lbm_probe are
+ *     those of this stored field.
+ *   - Host buffers passed in are only read during the call; the caller keeps
+ *     ownership.  Output buffers are caller-allocated.  Device memory is
+ *     owned by the handle and released by lbm_destroy.
+ *   - All work is enqueued on the CUDA stream given to lbm_create.  Calls that
+ *     return data to the host synchronise that stream; lbm_step does not
+ *     (launch errors are returned at once, execution errors at the next
+ *     synchronising call).
+ *   - Every function returns LBM_OK (0) or a negative LBM_E* code; the
+ *     message of the last failure is available from lbm_last_error().
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx *lbm_handle;
+
+/* Return codes */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)    /* invalid argument or unsupported combination      */
+#define LBM_ENOMEM (-2)    /* device or host allocation failed                  */
+#define LBM_ECUDA (-3)     /* a CUDA call failed (message has the CUDA error)   */
+#define LBM_EUNSTABLE (-4) /* non-finite populations found by lbm_reduce        */
+#define LBM_EIO (-5)       /* file error in lbm_save / lbm_load                 */
+
+/* Lattices (Sec. II.A: D2Q9 in 2D, D3Q19 in 3D) */
+#define LBM_D2Q9 0
+#define LBM_D3Q19 1
+
+/* Storage precision of the populations.  FP64 computes in FP64; the others
+ * compute in FP32.  The *_SHIFTED formats store f_i - w_i (rho_0 = 1). */
+#define LBM_FP64 0
+#define LBM_FP32 1
+#define LBM_FP16_SHIFTED 2
+#define LBM_BF16_SHIFTED 3
+
+/* Faces of the box */
+#define LBM_FACE_XM 0
+#define LBM_FACE_XP 1
+#define LBM_FACE_YM 2
+#define LBM_FACE_YP 3
+#define LBM_FACE_ZM 4
+#define LBM_FACE_ZP 5
+
+/* Boundary kinds of a face (Sec. III) */
+#define LBM_BC_PERIODIC 0 /* wrap-around; both faces of an axis must be periodic */
+#define LBM_BC_VELOCITY 1 /* Dirichlet velocity inflow                          */
+#define LBM_BC_OUTFLOW 2  /* zero-gradient outflow for all populations           */
+
+/* Cell types for lbm_set_geometry */
+#define LBM_CELL_FLUID 0
+#define LBM_CELL_SOLID 1 /* halfway bounce-back wall */
+
+/*
+ * lbm_lattice_table -- velocities and weights of a lattice (host only, no GPU
+ * needed).  Sec. II.A, Eq. truncatedEq ("w_i ... specific to the lattice").
+ *   q, d : out, number of directions and dimensions (may be NULL)
+ *   xi   : out, q*3 ints, xi[3*i + a] (may be NULL)
+ *   w    : out, q doubles (may be NULL)
+ * Returns LBM_EINVAL for an unknown lattice.
+ */
+int lbm_lattice_table(int lattice, int *q, int *d, int *xi, double *w);
+
+/*
+ * lbm_create -- allocate a lattice of extents[0] x extents[1] x extents[2]
+ * cells on the current CUDA device, fully periodic, every cell fluid and at
+ * rest (rho = 1, u = 0).
+ *   lattice     : LBM_D2Q9 (extents[2] must be 1) or LBM_D3Q19
+ *   tau_or_nu   : relaxation time tau (> 1/2) or, if value_is_nu != 0, the
+ *                 kinematic viscosity nu > 0, tau = nu / c_s^2 + 1/2
+ *                 (Sec. II.A, below Eq. truncatedEq)
+ *   Ma_ref      : reference Mach number, 0 <= Ma_ref <= 0.6 (the paper reports
+ *                 stable runs up to Ma 0.6, Sec. V); informational, it sets
+ *                 U_ref = Ma_ref c_s reported by lbm_info
+ *   precision   : LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED or LBM_BF16_SHIFTED
+ *   cuda_stream : cudaStream_t to enqueue work on, or NULL for the legacy
+ *                 default stream
+ * Errors: LBM_EINVAL (extents < 1, or < 3 along a later non-periodic axis;
+ * tau <= 1/2; bad lattice/precision; Ma_ref outside [0, 0.6]),
+ * LBM_ENOMEM, LBM_ECUDA.  On error *out is NULL.
+ */
+int lbm_create(lbm_handle *out, int lattice, const int extents[3], double tau_or_nu,
+               int value_is_nu, double Ma_ref, int precision, void *cuda_stream);
+
+/* lbm_destroy -- free the handle and its device memory (NULL is ignored). */
+void lbm_destroy(lbm_handle h);
+
+/* lbm_last_error -- message of the last failed call on h (h may be NULL for
+ * failures of lbm_create).  The string lives until the next call on h. */
+const char *lbm_last_error(lbm_handle h);
+
+/*
+ * lbm_set_geometry -- cell types, ncell bytes (LBM_CELL_FLUID / LBM_CELL_SOLID),
+ * host memory; NULL removes all solids.  Solid cells are walls with halfway
+ * bounce-back (Sec. III: the paper's cylinder and pipe walls): a population
+ * that would stream out of a solid cell is replaced by the receiving cell's
+ * own post-collision population in the opposite direction.  Solid cells keep
+ * their stored populations unchanged.
+ */
+int lbm_set_geometry(lbm_handle h, const uint8_t *cell_type);
+
+/*
+ * lbm_set_boundary -- boundary rule of one face (Sec. III).
+ *   face      : LBM_FACE_*
+ *   kind      : LBM_BC_PERIODIC, LBM_BC_VELOCITY or LBM_BC_OUTFLOW.  Both faces
+ *               of an axis are periodic or neither is; a non-periodic axis
+ *               needs at least 3 cells.
+ *   u_in      : velocity of a LBM_BC_VELOCITY face (3 doubles; may be NULL if
+ *               u_profile is given)
+ *   u_profile : optional per-face-cell velocity, 3 doubles per face cell,
+ *               face cells numbered by the two tangential coordinates, the
+ *               lower axis fastest (x faces: y + ny z; y faces: x + nx z;
+ *               z faces: x + nx y).  Replaces u_in when given.
+ * Velocity node: rho and Pi^neq are taken from the streamed populations of
+ * the inward neighbour and the node is rebuilt as feqH(rho, u_in) +
+ * fneqH(u_in, Pi^neq) before the collision.  Outflow node: takes all
+ * streamed populations of the inward neighbour (zero gradient), then collides.
+ */
+int lbm_set_boundary(lbm_handle h, int face, int kind, const double u_in[3],
+                     const double *u_profile);
+
+/*
+ * lbm_set_inlet_noise -- seeded random perturbation of velocity-face nodes.
+ * At step t, face cell k, component a < d, a node with prescribed velocity
+ * u (|u| > 0) gets u_a + amplitude |u| (2 U - 1) with
+ * U = (splitmix64(seed * 2^32 + (t * n_face_cells + k) * 3 + a) >> 11) * 2^-53
+ * (splitmix64 of Steele, Lea and Flood 2014).  amplitude = 0 disables it.
+ */
+int lbm_set_inlet_noise(lbm_handle h, uint64_t seed, double amplitude);
+
+/*
+ * lbm_set_sponge -- absorbing layer of width cells along a face (Sec. II.C,
+ * Eq. spongeLB with the damping term Eq. dampingLBM).  In the layer,
+ * chi(x) = chi_max sigma(d), sigma(d) = 3125 (W - d) d^4 / (256 W^5), d the
+ * distance of the cell from the layer's inner edge (W = width); overlapping
+ * layers take the larger chi.  The damped moments are rho* = (rho + chi
+ * rho_ref / 2) / (1 + chi / 2), rho* u* = (j + chi rho_ref u_ref / 2) /
+ * (1 + chi / 2).  Stability needs chi_max < 4 tau (Sec. II.C); larger values
+ * are rejected.  The reference state (rho_ref, u_ref) is shared by all
+ * layers: a call with a reference different from an earlier layer's is
+ * rejected.  width = 0 removes the layer.
+ */
+int lbm_set_sponge(lbm_handle h, int face, int width, double chi_max, double rho_ref,
+                   const double u_ref[3]);
+
+/*
+ * lbm_set_state -- initialise every cell to feqH(rho, u) (Eq. eqH).
+ *   rho : ncell doubles; u : 3*ncell doubles, per cell (ux, uy, uz) (host).
+ * Resets the step counter to 0.
+ */
+int lbm_set_state(lbm_handle h, const double *rho, const double *u);
+
+/* lbm_set_populations / lbm_get_populations -- the full stored field as plain
+ * FP64 f_i, direction-major, q*ncell doubles (host).  set resets the step
+ * counter to 0; get synchronises the stream. */
+int lbm_set_populations(lbm_handle h, const double *f);
+int lbm_get_populations(lbm_handle h, double *f);
+
+/*
+ * lbm_step -- advance n >= 0 time steps: stream (pull), apply the boundary
+ * rules, collide with Eq. optimizedLB / Eq. spongeLB.  Asynchronous.
+ */
+int lbm_step(lbm_handle h, int64_t n);
+
+/*
+ * lbm_moments -- moments of the stored field (host outputs, any may be NULL):
+ *   rho    : ncell doubles, sum_i f_i                       (Eq. moments)
+ *   u      : 3*ncell doubles, (sum_i f_i xi_i) / rho        (Eq. moments)
+ *   pi_neq : 6*ncell doubles, Pi - rho c_s^2 I - rho u u, Pi = sum_i f_i xi_i xi_i,
+ *            per cell (xx, xy, xz, yy, yz, zz); z components are 0 in 2D.
+ * Computed in FP64 on the device from the stored populations.
+ */
+int lbm_moments(lbm_handle h, double *rho, double *u, double *pi_neq);
+
+/*
+ * lbm_reduce -- FP64 totals over fluid cells: *mass = sum rho,
+ * momentum[0..2] = sum rho u.  Returns LBM_EUNSTABLE if any population is
+ * non-finite (the totals are still written).
+ */
+int lbm_reduce(lbm_handle h, double *mass, double momentum[3]);
+
+/*
+ * lbm_probe -- acoustic pressure fluctuation p' = c_s^2 (rho - rho_ref)
+ * (Sec. II.A: p = c_s^2 rho) at n cells (host list of cell indices);
+ * rho_ref is the sponge reference density (1 if no sponge).
+ */
+int lbm_probe(lbm_handle h, int n, const int64_t *cells, double *p_prime);
+
+/* lbm_sync -- wait for all work of h; returns any pending execution error. */
+int lbm_sync(lbm_handle h);
+
+/*
+ * lbm_info -- read-only facts about a handle (any pointer may be NULL):
+ *   step           : steps taken since the last set_state / set_populations / load
+ *   launches       : number of kernels this handle has launched so far
+ *   bytes_per_cell : algorithmic bytes one cell update moves (2 Q s, + 1 with
+ *                    a geometry mask)
+ *   tau            : relaxation time in use
+ */
+int lbm_info(lbm_handle h, int64_t *step, int64_t *launches, double *bytes_per_cell,
+             double *tau);
+
+/*
+ * lbm_save / lbm_load -- write / read the stored field and step counter to a
+ * host file (raw storage format with a header).  lbm_load requires a handle
+ * created with the same lattice, extents and precision (else LBM_EINVAL).
+ * Boundary rules, geometry and sponges are not part of the file.
+ */
+int lbm_save(lbm_handle h, const char *path);
+int lbm_load(lbm_handle h, const char *path);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

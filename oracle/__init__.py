@@ -81,6 +81,7 @@ def lib():
             _lib.orc_step.argtypes = [P, dp, dp, C.c_int64]
             _lib.orc_run.argtypes = [P, dp, dp, C.c_int64, C.c_int64]
             _lib.orc_update_cell.argtypes = [P, dp, C.c_int64, C.c_int64, dp]
+            _lib.orc_update_cells.argtypes = [P, dp, C.c_int64, C.POINTER(C.c_int64), C.c_int64, dp]
             _lib.orc_field_moments.argtypes = [P, dp, dp, dp, dp]
             _lib.orc_init_equilibrium.argtypes = [P, dp, dp, dp]
             _lib.orc_chi_at.argtypes = [P, C.c_int, C.c_int, C.c_int]
@@ -239,6 +240,16 @@ class Problem:
         out = np.zeros(self.q)
         s = self._struct()
         lib().orc_update_cell(C.byref(s), _dp(f), int(cell), int(step), _dp(out))
+        return out
+
+    def update_cells(self, f: np.ndarray, cells, step: int = 0) -> np.ndarray:
+        """Post-collision populations (len(cells), q) of listed cells from the full field f."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros((len(cells), self.q))
+        s = self._struct()
+        lib().orc_update_cells(C.byref(s), _dp(f), len(cells), cells.ctypes.data_as(C.POINTER(C.c_int64)),
+                               int(step), _dp(out))
         return out
 
     def moments(self, f: np.ndarray):

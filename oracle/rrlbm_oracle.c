@@ -418,6 +418,14 @@ void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int6
     collide(L, f, P->tau, sponge_chi(P, c), P->rho_ref, P->u_ref, P->g, out);
 }
 
+/* Post-collision populations of a list of cells (out: n x q, cell-major). */
+void orc_update_cells(const orc_problem *P, const double *fin, int64_t n, const int64_t *cells,
+                      int64_t step, double *out)
+{
+    const lattice_t *L = lattice(P->lattice);
+    for (int64_t k = 0; k < n; ++k) orc_update_cell(P, fin, cells[k], step, out + k * L->q);
+}
+
 /* One full step: fout = update(fin).  Returns 0. */
 int orc_step(const orc_problem *P, const double *fin, double *fout, int64_t step)
 {

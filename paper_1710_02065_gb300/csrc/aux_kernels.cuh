@@ -1,0 +1,169 @@
+// aux_kernels.cuh -- initialisation, conversion and diagnostic kernels.
+//
+//   k_init_eq     : f = feqH(rho, u)  (Eq. eqH) into both lattices
+//   k_set_dir     : one direction of a caller field, f_i - w_i, into both lattices
+//   k_get_dir     : one direction of the stored field as plain FP64 f_i
+//   k_moments     : rho, u, Pi^neq per cell in FP64 (Eq. moments, Sec. II.A)
+//   k_reduce      : FP64 per-block totals of rho - 1, rho u, fluid count and
+//                   non-finite count (warp shuffles, then a fixed-order pass)
+//   k_probe       : rho at listed cells
+#pragma once
+
+#include "rr.cuh"
+
+namespace rr {
+
+template <class L>
+__device__ __forceinline__ double weight_rt(int i)
+{
+    double w = 0.0;
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k)
+        if (k == i) w = weight<L>(k);
+    return w;
+}
+
+template <class L, class S>
+__global__ void k_init_eq(int64_t N, const double *__restrict__ rho, const double *__restrict__ u,
+                          S *__restrict__ f0, S *__restrict__ f1)
+{
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= N) return;
+    Coef<double> k{};
+    add_eq<double>(k, 1.0, rho[cell], u[3 * cell], u[3 * cell + 1], L::D == 3 ? u[3 * cell + 2] : 0.0);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const S v = Store<S>::from(rebuild<L, double>(k, i));
+        f0[(int64_t)i * N + cell] = v;
+        f1[(int64_t)i * N + cell] = v;
+    }
+}
+
+template <class L, class S>
+__global__ void k_set_dir(int64_t N, int i, const double *__restrict__ src, S *__restrict__ f0,
+                          S *__restrict__ f1)
+{
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= N) return;
+    const S v = Store<S>::from(src[cell] - weight_rt<L>(i));
+    f0[(int64_t)i * N + cell] = v;
+    f1[(int64_t)i * N + cell] = v;
+}
+
+template <class L, class S>
+__global__ void k_get_dir(int64_t N, int i, const S *__restrict__ f, double *__restrict__ dst)
+{
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= N) return;
+    dst[cell] = (double)Store<S>::ld(f + (int64_t)i * N + cell) + weight_rt<L>(i);
+}
+
+template <class L, class S>
+__device__ __forceinline__ void load_cell_fp64(const S *__restrict__ f, int64_t N, int64_t cell,
+                                               double (&g)[L::Q])
+{
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) g[i] = (double)Store<S>::ld(f + (int64_t)i * N + cell);
+}
+
+template <class L, class S>
+__global__ void k_moments(int64_t N, const S *__restrict__ f, double *__restrict__ rho,
+                          double *__restrict__ u, double *__restrict__ pn)
+{
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= N) return;
+    double g[L::Q];
+    load_cell_fp64<L, S>(f, N, cell, g);
+    const Mom<double> m = moments<L, double>(g);
+    const double r = 1.0 + m.dr;
+    const double ux = m.jx / r, uy = m.jy / r, uz = L::D == 3 ? m.jz / r : 0.0;
+    if (rho) rho[cell] = r;
+    if (u) {
+        u[3 * cell] = ux;
+        u[3 * cell + 1] = uy;
+        u[3 * cell + 2] = uz;
+    }
+    if (pn) {
+        const Sym2<double> p = pi_neq<double>(m, r, ux, uy, uz, L::D);
+        pn[6 * cell + 0] = p.xx;
+        pn[6 * cell + 1] = p.xy;
+        pn[6 * cell + 2] = p.xz;
+        pn[6 * cell + 3] = p.yy;
+        pn[6 * cell + 4] = p.yz;
+        pn[6 * cell + 5] = p.zz;
+    }
+}
+
+// Per-block partial sums: [sum dr, sum jx, sum jy, sum jz, fluid cells, non-finite cells]
+constexpr int RED_FIELDS = 6;
+constexpr int RED_BLOCK = 256;
+
+template <class L, class S>
+__global__ void __launch_bounds__(RED_BLOCK) k_reduce(int64_t N, const S *__restrict__ f,
+                                                      const uint8_t *__restrict__ solid,
+                                                      double *__restrict__ partial)
+{
+    double acc[RED_FIELDS] = {0, 0, 0, 0, 0, 0};
+    for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < N;
+         cell += (int64_t)gridDim.x * blockDim.x) {
+        if (solid && solid[cell]) continue;
+        double g[L::Q];
+        load_cell_fp64<L, S>(f, N, cell, g);
+        bool finite = true;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) finite = finite && isfinite(g[i]);
+        const Mom<double> m = moments<L, double>(g);
+        if (finite) {
+            acc[0] += m.dr;
+            acc[1] += m.jx;
+            acc[2] += m.jy;
+            acc[3] += m.jz;
+        } else {
+            acc[5] += 1.0;
+        }
+        acc[4] += 1.0;
+    }
+    // warp, then block, in a fixed order
+    __shared__ double sh[RED_BLOCK / 32][RED_FIELDS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < RED_FIELDS; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < RED_FIELDS) {
+        double v = 0.0;
+        for (int w = 0; w < RED_BLOCK / 32; ++w) v += sh[w][threadIdx.x];
+        partial[(int64_t)blockIdx.x * RED_FIELDS + threadIdx.x] = v;
+    }
+}
+
+// Final pass: one warp per field, strided then shuffled: fixed order, deterministic.
+__global__ void k_reduce_final(int nblocks, const double *__restrict__ partial,
+                               double *__restrict__ out)
+{
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k >= RED_FIELDS) return;
+    double v = 0.0;
+    for (int b = lane; b < nblocks; b += 32) v += partial[(int64_t)b * RED_FIELDS + k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) out[k] = v;
+}
+
+template <class L, class S>
+__global__ void k_probe(int n, const int64_t *__restrict__ cells, int64_t N, const S *__restrict__ f,
+                        double *__restrict__ rho)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double g[L::Q];
+    load_cell_fp64<L, S>(f, N, cells[t], g);
+    double dr = 0.0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) dr += g[i];
+    rho[t] = 1.0 + dr;
+}
+
+}  // namespace rr

@@ -1,0 +1,289 @@
+// rr.cuh -- lattice descriptors and the Hermite-regularized reconstruction
+// shared by every kernel of liblbm (device code, sm_103a).
+//
+// Method: Brogi et al., arXiv:1710.02065, Sec. II.A.  A cell's populations
+// are rebuilt from a small set of Hermite coefficients,
+//     f_i = w_i [ a0 + xi_i . a1 / c_s^2 + H2_i : A2 / (2 c_s^4) + T3_i(A3) ]
+// (Eq. HEeqAndNeq truncated to order 3, Eq. eqH + Eq. neqH), where
+//   a0 = rho, a1 = rho u, A2 = rho u u (+ (1 - 1/tau) Pi^neq after collision),
+//   A3 = rho u u u (Eq. recursive1) (+ (1 - 1/tau) a3_neq, Eq. recursive2).
+// Populations are handled shifted, g_i = f_i - w_i (rho_0 = 1), so that
+// a0 is replaced by rho - 1; sums of small numbers keep FP32 round-off low.
+//
+// Third order: on D2Q9 the supported components are xxy and xyy (H_xxx and
+// H_yyy vanish on the lattice).  On D3Q19 the six a_aab components enter as
+// the sum/difference pairs (xxy,yzz), (xzz,xyy), (yyz,xxz), each with the
+// inverse of its lattice norm (2 c_s^6 for sums, 6 c_s^6 for differences), so
+// the rebuilt populations carry exactly a_p + a_q and a_p - a_q.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rr {
+
+// ---------------------------------------------------------------------------
+// Lattices.  Direction 0 is the rest velocity; i and i + Q/2 (1 <= i <= Q/2)
+// are opposite.  Weights: D2Q9 4/9, 1/9, 1/36; D3Q19 1/3, 1/18, 1/36 by |xi|^2.
+// ---------------------------------------------------------------------------
+struct D2Q9 {
+    static constexpr int Q = 9, D = 2, HALF = 4;
+    __host__ __device__ static constexpr int cx(int i)
+    {
+        constexpr int v[9] = {0, 1, 0, 1, -1, -1, 0, -1, 1};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int cy(int i)
+    {
+        constexpr int v[9] = {0, 0, 1, 1, 1, 0, -1, -1, -1};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+};
+
+struct D3Q19 {
+    static constexpr int Q = 19, D = 3, HALF = 9;
+    __host__ __device__ static constexpr int cx(int i)
+    {
+        constexpr int v[19] = {0, 1, 0, 0, 1, 1, 1, 1, 0, 0, -1, 0, 0, -1, -1, -1, -1, 0, 0};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int cy(int i)
+    {
+        constexpr int v[19] = {0, 0, 1, 0, 1, -1, 0, 0, 1, 1, 0, -1, 0, -1, 1, 0, 0, -1, -1};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int cz(int i)
+    {
+        constexpr int v[19] = {0, 0, 0, 1, 0, 0, 1, -1, 1, -1, 0, 0, -1, 0, 0, -1, 1, -1, 1};
+        return v[i];
+    }
+};
+
+template <class L>
+__host__ __device__ constexpr int opp(int i)
+{
+    return i == 0 ? 0 : (i <= L::HALF ? i + L::HALF : i - L::HALF);
+}
+
+template <class L>
+__host__ __device__ constexpr double weight(int i)
+{
+    // |xi|^2 decides the weight class
+    return (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i)) == 0
+               ? (L::D == 2 ? 4.0 / 9.0 : 1.0 / 3.0)
+               : ((L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i)) == 1
+                      ? (L::D == 2 ? 1.0 / 9.0 : 1.0 / 18.0)
+                      : 1.0 / 36.0);
+}
+
+// ---------------------------------------------------------------------------
+// Storage formats
+// ---------------------------------------------------------------------------
+template <class S>
+struct Store;
+template <>
+struct Store<double> {
+    __device__ static double ld(const double *p) { return __ldg(p); }
+    __device__ static void st(double *p, double v) { *p = v; }
+    template <class C>
+    __device__ static C to(double v) { return (C)v; }
+    __device__ static double from(double v) { return v; }
+    __device__ static double from(float v) { return (double)v; }
+};
+template <>
+struct Store<float> {
+    __device__ static float ld(const float *p) { return __ldg(p); }
+    __device__ static void st(float *p, float v) { *p = v; }
+    __device__ static float from(float v) { return v; }
+    __device__ static float from(double v) { return (float)v; }
+};
+template <>
+struct Store<__half> {
+    __device__ static float ld(const __half *p) { return __half2float(__ldg(p)); }
+    __device__ static void st(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ static __half from(float v) { return __float2half_rn(v); }
+    __device__ static __half from(double v) { return __double2half(v); }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    __device__ static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    __device__ static void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
+    __device__ static __nv_bfloat16 from(double v) { return __double2bfloat16(v); }
+};
+
+// ---------------------------------------------------------------------------
+// Moments of shifted populations g_i = f_i - w_i:
+//   dr = rho - 1, j = rho u, s_ab = Pi_ab - c_s^2 delta_ab   (Eq. moments)
+// ---------------------------------------------------------------------------
+template <class C>
+struct Mom {
+    C dr, jx, jy, jz, sxx, syy, szz, sxy, sxz, syz;
+};
+
+template <class L, class C>
+__device__ __forceinline__ Mom<C> moments(const C (&g)[L::Q])
+{
+    Mom<C> m{};
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
+        m.dr += g[i];
+        if (x) m.jx += x > 0 ? g[i] : -g[i];
+        if (y) m.jy += y > 0 ? g[i] : -g[i];
+        if (z) m.jz += z > 0 ? g[i] : -g[i];
+        if (x) m.sxx += g[i];
+        if (y) m.syy += g[i];
+        if (z) m.szz += g[i];
+        if (x && y) m.sxy += x * y > 0 ? g[i] : -g[i];
+        if (x && z) m.sxz += x * z > 0 ? g[i] : -g[i];
+        if (y && z) m.syz += y * z > 0 ? g[i] : -g[i];
+    }
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// Hermite coefficients of a rebuilt cell (shifted form)
+//   a0 = rho - 1, a1 = (jx, jy, jz), A2 (xx, yy, zz, xy, xz, yz),
+//   A3 (xxy, xyy, xxz, xzz, yyz, yzz); the z ones are unused on D2Q9.
+// ---------------------------------------------------------------------------
+template <class C>
+struct Coef {
+    C a0, a1x, a1y, a1z;
+    C xx, yy, zz, xy, xz, yz;
+    C xxy, xyy, xxz, xzz, yyz, yzz;
+};
+
+// Second-order symmetric tensor (xx, yy, zz, xy, xz, yz)
+template <class C>
+struct Sym2 {
+    C xx, yy, zz, xy, xz, yz;
+};
+
+// Equilibrium coefficients of (rho, u), scaled by s: A2 += s rho u u, A3 += s rho u u u
+template <class C>
+__device__ __forceinline__ void add_eq(Coef<C> &k, C s, C rho, C ux, C uy, C uz)
+{
+    const C r = s * rho;
+    k.a0 += s * (rho - C(1));
+    k.a1x += r * ux;
+    k.a1y += r * uy;
+    k.a1z += r * uz;
+    k.xx += r * ux * ux;
+    k.yy += r * uy * uy;
+    k.zz += r * uz * uz;
+    k.xy += r * ux * uy;
+    k.xz += r * ux * uz;
+    k.yz += r * uy * uz;
+    k.xxy += r * ux * ux * uy;
+    k.xyy += r * ux * uy * uy;
+    k.xxz += r * ux * ux * uz;
+    k.xzz += r * ux * uz * uz;
+    k.yyz += r * uy * uy * uz;
+    k.yzz += r * uy * uz * uz;
+}
+
+// Off-equilibrium coefficients scaled by s: A2 += s Pi^neq and
+// A3 += s a3_neq, a3_neq,abc = u_a P_bc + u_b P_ac + u_c P_ab (Eq. recursive2, n = 3)
+template <class C>
+__device__ __forceinline__ void add_neq(Coef<C> &k, C s, C ux, C uy, C uz, const Sym2<C> &p)
+{
+    k.xx += s * p.xx;
+    k.yy += s * p.yy;
+    k.zz += s * p.zz;
+    k.xy += s * p.xy;
+    k.xz += s * p.xz;
+    k.yz += s * p.yz;
+    k.xxy += s * (C(2) * ux * p.xy + uy * p.xx);
+    k.xyy += s * (C(2) * uy * p.xy + ux * p.yy);
+    k.xxz += s * (C(2) * ux * p.xz + uz * p.xx);
+    k.xzz += s * (C(2) * uz * p.xz + ux * p.zz);
+    k.yyz += s * (C(2) * uy * p.yz + uz * p.yy);
+    k.yzz += s * (C(2) * uz * p.yz + uy * p.zz);
+}
+
+// g_i = w_i [ a0 + 3 xi.a1 + 4.5 H2_i:A2 + T3_i(A3) ]   (c_s^2 = 1/3)
+template <class L, class C>
+__device__ __forceinline__ C rebuild(const Coef<C> &k, int i)
+{
+    constexpr double cs2 = 1.0 / 3.0;
+    const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
+    C r = k.a0;
+    // first order: xi . a1 / c_s^2
+    C f1 = C(0);
+    if (x) f1 += x > 0 ? k.a1x : -k.a1x;
+    if (y) f1 += y > 0 ? k.a1y : -k.a1y;
+    if (z) f1 += z > 0 ? k.a1z : -k.a1z;
+    r += C(3) * f1;
+    // second order: H2 : A2 / (2 c_s^4), H2_ab = xi_a xi_b - c_s^2 delta_ab
+    C f2 = C(x * x - cs2) * k.xx + C(y * y - cs2) * k.yy;
+    if (L::D == 3) f2 += C(z * z - cs2) * k.zz;
+    if (x * y) f2 += C(2 * x * y) * k.xy;
+    if (L::D == 3 && x * z) f2 += C(2 * x * z) * k.xz;
+    if (L::D == 3 && y * z) f2 += C(2 * y * z) * k.yz;
+    r += C(4.5) * f2;
+    // third order, H_aab = xi_a^2 xi_b - c_s^2 xi_b
+    const double hxxy = (x * x - cs2) * y, hxyy = (y * y - cs2) * x;
+    if (L::D == 2) {
+        // 1 / (2 c_s^6) = 13.5
+        if (hxxy != 0.0) r += C(13.5 * hxxy) * k.xxy;
+        if (hxyy != 0.0) r += C(13.5 * hxyy) * k.xyy;
+    } else {
+        const double hyzz = (z * z - cs2) * y, hxzz = (z * z - cs2) * x;
+        const double hyyz = (y * y - cs2) * z, hxxz = (x * x - cs2) * z;
+        // pairs (xxy, yzz), (xzz, xyy), (yyz, xxz); 1/(2 c_s^6) = 13.5, 1/(6 c_s^6) = 4.5
+        const double p1 = hxxy + hyzz, m1 = hxxy - hyzz;
+        const double p2 = hxzz + hxyy, m2 = hxzz - hxyy;
+        const double p3 = hyyz + hxxz, m3 = hyyz - hxxz;
+        if (p1 != 0.0) r += C(13.5 * p1) * (k.xxy + k.yzz);
+        if (m1 != 0.0) r += C(4.5 * m1) * (k.xxy - k.yzz);
+        if (p2 != 0.0) r += C(13.5 * p2) * (k.xzz + k.xyy);
+        if (m2 != 0.0) r += C(4.5 * m2) * (k.xzz - k.xyy);
+        if (p3 != 0.0) r += C(13.5 * p3) * (k.yyz + k.xxz);
+        if (m3 != 0.0) r += C(4.5 * m3) * (k.yyz - k.xxz);
+    }
+    return C(weight<L>(i)) * r;
+}
+
+// Pi^neq about (rho, u) from shifted moments: s_ab - (rho - 1) c_s^2 delta_ab - rho u_a u_b
+template <class C>
+__device__ __forceinline__ Sym2<C> pi_neq(const Mom<C> &m, C rho, C ux, C uy, C uz, int D)
+{
+    const C c = (rho - C(1)) * C(1.0 / 3.0);
+    Sym2<C> p;
+    p.xx = m.sxx - c - rho * ux * ux;
+    p.yy = m.syy - c - rho * uy * uy;
+    p.xy = m.sxy - rho * ux * uy;
+    if (D == 3) {
+        p.zz = m.szz - c - rho * uz * uz;
+        p.xz = m.sxz - rho * ux * uz;
+        p.yz = m.syz - rho * uy * uz;
+    } else {
+        p.zz = p.xz = p.yz = C(0);
+    }
+    return p;
+}
+
+// splitmix64 (Steele, Lea and Flood 2014): counter-based uniform in [0, 1)
+__device__ __forceinline__ double u01(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Sponge profile (Sec. II.C): sigma(d) = 3125 (W - d) d^4 / (256 W^5), 0 <= d <= W
+template <class C>
+__device__ __forceinline__ C sigma(C d, C W)
+{
+    if (d < C(0) || d > W) return C(0);
+    const C d2 = d * d, W2 = W * W;
+    return C(3125) * (W - d) * d2 * d2 / (C(256) * W2 * W2 * W);
+}
+
+}  // namespace rr

@@ -1,0 +1,271 @@
+"""Thin ctypes binding of liblbm (``include/lbm.h``).
+
+Functions keep the C names and argument order; they only marshal numpy
+arrays and raise ``LBMError`` on a negative return code.  Every step of the
+computation runs in liblbm's CUDA kernels.  Importing this module loads
+``_build/liblbm.so`` and fails loudly if it has not been built: there is no
+fallback implementation.
+
+``Solver`` wraps a handle with numpy-friendly helpers for tests and benchmarks.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_EIO = 0, -1, -2, -3, -4, -5
+LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED, LBM_BF16_SHIFTED = 0, 1, 2, 3
+LBM_FACE_XM, LBM_FACE_XP, LBM_FACE_YM, LBM_FACE_YP, LBM_FACE_ZM, LBM_FACE_ZP = range(6)
+LBM_BC_PERIODIC, LBM_BC_VELOCITY, LBM_BC_OUTFLOW = 0, 1, 2
+LBM_CELL_FLUID, LBM_CELL_SOLID = 0, 1
+
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16_SHIFTED, "bf16": LBM_BF16_SHIFTED}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"liblbm.so is not built ({LIB_PATH}); run `python -m paper_1710_02065_gb300.build` "
+        "(the CUDA library is the only implementation)")
+
+_lib = C.CDLL(LIB_PATH)
+_h = C.c_void_p
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_i64p = C.POINTER(C.c_int64)
+
+
+def _sig(name, args, res=C.c_int):
+    fn = getattr(_lib, name)
+    fn.argtypes = args
+    fn.restype = res
+    return fn
+
+
+_sig("lbm_lattice_table", [C.c_int, _ip, _ip, _ip, _dp])
+_sig("lbm_create", [C.POINTER(_h), C.c_int, _ip, C.c_double, C.c_int, C.c_double, C.c_int, C.c_void_p])
+_sig("lbm_destroy", [_h], None)
+_sig("lbm_last_error", [_h], C.c_char_p)
+_sig("lbm_set_geometry", [_h, C.POINTER(C.c_uint8)])
+_sig("lbm_set_boundary", [_h, C.c_int, C.c_int, _dp, _dp])
+_sig("lbm_set_inlet_noise", [_h, C.c_uint64, C.c_double])
+_sig("lbm_set_sponge", [_h, C.c_int, C.c_int, C.c_double, C.c_double, _dp])
+_sig("lbm_set_state", [_h, _dp, _dp])
+_sig("lbm_set_populations", [_h, _dp])
+_sig("lbm_get_populations", [_h, _dp])
+_sig("lbm_step", [_h, C.c_int64])
+_sig("lbm_moments", [_h, _dp, _dp, _dp])
+_sig("lbm_reduce", [_h, _dp, _dp])
+_sig("lbm_probe", [_h, C.c_int, _i64p, _dp])
+_sig("lbm_sync", [_h])
+_sig("lbm_info", [_h, _i64p, _i64p, _dp, _dp])
+_sig("lbm_save", [_h, C.c_char_p])
+_sig("lbm_load", [_h, C.c_char_p])
+
+EXPORTED = [
+    "lbm_lattice_table", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_geometry",
+    "lbm_set_boundary", "lbm_set_inlet_noise", "lbm_set_sponge", "lbm_set_state",
+    "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_moments", "lbm_reduce",
+    "lbm_probe", "lbm_sync", "lbm_info", "lbm_save", "lbm_load",
+]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"liblbm error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc: int, h=None):
+    if rc != LBM_OK:
+        msg = _lib.lbm_last_error(h)
+        raise LBMError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _d(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous, "float64 C-contiguous array required"
+    return a.ctypes.data_as(_dp)
+
+
+def _c64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Same-name wrappers of the C ABI
+# ---------------------------------------------------------------------------
+def lbm_lattice_table(lattice: int):
+    q, d = C.c_int(), C.c_int()
+    xi = np.zeros(19 * 3, dtype=np.int32)
+    w = np.zeros(19)
+    _check(_lib.lbm_lattice_table(lattice, C.byref(q), C.byref(d), xi.ctypes.data_as(_ip), _d(w)))
+    return q.value, d.value, xi[: 3 * q.value].reshape(q.value, 3).copy(), w[: q.value].copy()
+
+
+def lbm_create(lattice: int, extents, tau_or_nu: float, value_is_nu: bool = False,
+               Ma_ref: float = 0.0, precision: int = LBM_FP32, cuda_stream: int | None = None):
+    h = _h()
+    ext = (C.c_int * 3)(*[int(v) for v in (list(extents) + [1] * (3 - len(extents)))])
+    rc = _lib.lbm_create(C.byref(h), lattice, ext, float(tau_or_nu), int(bool(value_is_nu)),
+                         float(Ma_ref), precision, C.c_void_p(cuda_stream or 0))
+    _check(rc, None)
+    return h
+
+
+def lbm_destroy(h):
+    _lib.lbm_destroy(h)
+
+
+def lbm_last_error(h) -> str:
+    m = _lib.lbm_last_error(h)
+    return m.decode() if m else ""
+
+
+def lbm_set_geometry(h, cell_type):
+    if cell_type is None:
+        return _check(_lib.lbm_set_geometry(h, None), h)
+    a = np.ascontiguousarray(cell_type, dtype=np.uint8).reshape(-1)
+    return _check(_lib.lbm_set_geometry(h, a.ctypes.data_as(C.POINTER(C.c_uint8))), h)
+
+
+def lbm_set_boundary(h, face: int, kind: int, u_in=None, u_profile=None):
+    u = _c64(u_in)
+    p = _c64(u_profile)
+    return _check(_lib.lbm_set_boundary(h, face, kind, _d(u), _d(p)), h)
+
+
+def lbm_set_inlet_noise(h, seed: int, amplitude: float):
+    return _check(_lib.lbm_set_inlet_noise(h, C.c_uint64(int(seed)), float(amplitude)), h)
+
+
+def lbm_set_sponge(h, face: int, width: int, chi_max: float, rho_ref: float = 1.0, u_ref=(0.0, 0.0, 0.0)):
+    u = _c64(u_ref)
+    return _check(_lib.lbm_set_sponge(h, face, int(width), float(chi_max), float(rho_ref), _d(u)), h)
+
+
+def lbm_set_state(h, rho, u):
+    r = _c64(rho).reshape(-1)
+    v = _c64(u).reshape(-1)
+    return _check(_lib.lbm_set_state(h, _d(r), _d(v)), h)
+
+
+def lbm_set_populations(h, f):
+    a = _c64(f)
+    return _check(_lib.lbm_set_populations(h, _d(a)), h)
+
+
+def lbm_get_populations(h, out: np.ndarray):
+    return _check(_lib.lbm_get_populations(h, _d(out)), h)
+
+
+def lbm_step(h, n: int):
+    return _check(_lib.lbm_step(h, C.c_int64(int(n))), h)
+
+
+def lbm_moments(h, rho=None, u=None, pi_neq=None):
+    return _check(_lib.lbm_moments(h, _d(rho), _d(u), _d(pi_neq)), h)
+
+
+def lbm_reduce(h):
+    m = C.c_double()
+    j = np.zeros(3)
+    rc = _lib.lbm_reduce(h, C.byref(m), _d(j))
+    if rc not in (LBM_OK, LBM_EUNSTABLE):
+        _check(rc, h)
+    return m.value, j, rc
+
+
+def lbm_probe(h, cells) -> np.ndarray:
+    c = np.ascontiguousarray(cells, dtype=np.int64)
+    out = np.zeros(len(c))
+    _check(_lib.lbm_probe(h, len(c), c.ctypes.data_as(_i64p), _d(out)), h)
+    return out
+
+
+def lbm_sync(h):
+    return _check(_lib.lbm_sync(h), h)
+
+
+def lbm_info(h):
+    s, l = C.c_int64(), C.c_int64()
+    b, t = C.c_double(), C.c_double()
+    _check(_lib.lbm_info(h, C.byref(s), C.byref(l), C.byref(b), C.byref(t)), h)
+    return {"step": s.value, "launches": l.value, "bytes_per_cell": b.value, "tau": t.value}
+
+
+def lbm_save(h, path: str):
+    return _check(_lib.lbm_save(h, path.encode()), h)
+
+
+def lbm_load(h, path: str):
+    return _check(_lib.lbm_load(h, path.encode()), h)
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+class Solver:
+    """Owns one liblbm handle; numpy in, numpy out."""
+
+    def __init__(self, lattice: int, extents, tau: float, precision: int = LBM_FP32,
+                 Ma_ref: float = 0.0, stream: int | None = None, value_is_nu: bool = False):
+        self.lattice = lattice
+        ext = list(extents) + [1] * (3 - len(extents))
+        self.n = tuple(int(v) for v in ext)
+        self.ncell = self.n[0] * self.n[1] * self.n[2]
+        self.q = 9 if lattice == LBM_D2Q9 else 19
+        self.h = lbm_create(lattice, self.n, tau, value_is_nu, Ma_ref, precision, stream)
+
+    def close(self):
+        if self.h:
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, rho, u):
+        lbm_set_state(self.h, rho, u)
+
+    def set_populations(self, f):
+        lbm_set_populations(self.h, np.asarray(f, dtype=np.float64).reshape(self.q, self.ncell))
+
+    def populations(self) -> np.ndarray:
+        out = np.zeros((self.q, self.ncell))
+        lbm_get_populations(self.h, out)
+        return out
+
+    def step(self, n: int = 1):
+        lbm_step(self.h, n)
+
+    def sync(self):
+        lbm_sync(self.h)
+
+    def moments(self):
+        rho = np.zeros(self.ncell)
+        u = np.zeros((self.ncell, 3))
+        pn = np.zeros((self.ncell, 6))
+        lbm_moments(self.h, rho, u, pn)
+        return rho, u, pn
+
+    def reduce(self):
+        return lbm_reduce(self.h)
+
+    def info(self):
+        return lbm_info(self.h)

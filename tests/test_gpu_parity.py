@@ -1,0 +1,303 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances
+  * FP64 storage/compute: 1e-12 normwise relative in rho and u, and
+    populations within 1e-13 absolute after a few steps (round-off only).
+  * FP32: 1e-5 normwise relative in rho and u; populations within 1e-5 of
+    max |f| (FP32 round-off of sums of O(Q) terms of size <= 1).
+  * FP16 / BF16 shifted storage: each stored value g = f - w is rounded to a
+    10-bit / 7-bit mantissa, so one step may err by 2^-11 / 2^-8 of max |g|;
+    the bound used is (steps + 1) * 2^-10 (FP16) or 2^-7 (BF16) of max |g|.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from cases import (Case, D2Q9, D3Q19, OUTFLOW, PERIODIC, VELOCITY, acoustic_pulse, cylinder,
+                   round_jet, taylor_green_3d, to_gpu, to_oracle, with_random_state)
+from paper_1710_02065_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+PRECS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_02065_gb300 import build
+    build.build()
+
+
+def _pop_tol(prec, f_ref, w, steps):
+    g = np.abs(f_ref - w[:, None]).max()
+    if prec == "fp64":
+        return 1e-13
+    if prec == "fp32":
+        return 1e-5 * np.abs(f_ref).max()
+    bits = 10 if prec == "fp16" else 7
+    return (steps + 1) * 2.0 ** -bits * g + 1e-7
+
+
+def _normwise(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _boxed_case(lattice, seed=5):
+    """Small ragged box exercising every boundary rule at once: velocity
+    inflow with a profile and noise, zero-gradient outflow, sponges, a solid
+    obstacle, periodic axes, random off-equilibrium populations."""
+    if lattice == D2Q9:
+        n = (37, 23, 1)
+    else:
+        n = (19, 13, 11)
+    ncell = int(np.prod(n))
+    c = Case("boxed", lattice, n, 0.58)
+    U = 0.06
+    nf = n[1] * n[2]
+    prof = np.zeros((nf, 3))
+    prof[:, 0] = U * (0.5 + np.random.default_rng(seed).random(nf))
+    if lattice == D3Q19:
+        prof[:, 2] = 0.01
+    c.faces = {0: (VELOCITY, (0, 0, 0), prof), 1: (OUTFLOW, (0, 0, 0), None)}
+    if lattice == D3Q19:
+        c.faces[4] = (OUTFLOW, (0, 0, 0), None)
+        c.faces[5] = (OUTFLOW, (0, 0, 0), None)
+        c.sponges = {1: (6, 0.6), 5: (4, 0.9), 3: (3, 0.3)}
+    else:
+        c.sponges = {1: (8, 0.7), 3: (5, 0.4)}
+    c.rho_ref, c.u_ref = 1.01, (0.02, -0.01, 0.0)
+    c.noise = (7, 0.05)
+    solid = np.zeros(n[::-1], np.uint8)
+    if lattice == D2Q9:
+        solid[0, 9:12, 14:18] = 1
+    else:
+        solid[4:7, 5:8, 8:11] = 1
+    c.solid = solid.reshape(-1)
+    return with_random_state(c, seed=seed, spread=0.08)
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
+def test_equilibrium_initialisation(lattice, prec):
+    n = (13, 7, 1) if lattice == D2Q9 else (9, 7, 5)
+    ncell = int(np.prod(n))
+    rng = np.random.default_rng(1)
+    rho = 1 + 0.01 * rng.normal(size=ncell)
+    u = 0.1 * rng.normal(size=(ncell, 3))
+    if lattice == D2Q9:
+        u[:, 2] = 0
+    c = Case("eq", lattice, n, 0.7, rho0=rho, u0=u)
+    P, f_ref = to_oracle(c)
+    s = to_gpu(c, PRECS[prec])
+    f = s.populations()
+    _, _, _, w, _ = oracle.lattice(lattice)
+    assert np.abs(f - f_ref).max() <= _pop_tol(prec, f_ref, w, 0)
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
+def test_all_boundary_rules_few_steps(lattice, prec):
+    c = _boxed_case(lattice)
+    P, f = to_oracle(c)
+    s = to_gpu(c, PRECS[prec])
+    _, _, _, w, _ = oracle.lattice(lattice)
+    f_gpu0 = s.populations()
+    assert np.abs(f_gpu0 - f).max() <= _pop_tol(prec, f, w, 0)
+    t = 0
+    for steps in (1, 2):
+        f = P.run(f, steps, step0=t)
+        s.step(steps)
+        t += steps
+        got = s.populations()
+        err = np.abs(got - f).max()
+        assert err <= _pop_tol(prec, f, w, t), (t, err)
+    assert s.info()["step"] == t
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_acoustic_pulse_128_parity_200_steps(prec, tol):
+    """D2Q9 128^2 periodic Gaussian pulse, tau 0.6, 200 steps."""
+    c = acoustic_pulse(128)
+    P, f = to_oracle(c)
+    f = P.run(f, 200)
+    r_ref, u_ref, _ = P.moments(f)
+    s = to_gpu(c, PRECS[prec])
+    s.step(200)
+    r, u, _ = s.moments()
+    assert _normwise(r, r_ref) <= tol
+    assert _normwise(u, u_ref) <= tol
+    # GPU FP64 totals: mass and momentum conserved over 200 steps
+    m, j, rc = s.reduce()
+    assert rc == 0
+    if prec == "fp64":
+        r0 = c.rho0.sum()
+        assert abs(m - r0) / r0 < 1e-13
+        assert abs(j[0] - (c.rho0 * 0.05).sum()) / abs(j[0]) < 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_taylor_green_3d_parity(prec, tol):
+    c = taylor_green_3d(24, 0.7, 0.02)
+    P, f = to_oracle(c)
+    f = P.run(f, 40)
+    r_ref, u_ref, pn_ref = P.moments(f)
+    s = to_gpu(c, PRECS[prec])
+    s.step(40)
+    r, u, pn = s.moments()
+    assert _normwise(r, r_ref) <= tol
+    assert _normwise(u, u_ref) <= tol
+    assert np.abs(pn - pn_ref).max() <= tol * np.abs(pn_ref).max() * 10
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_cylinder_scaled_parity(prec, tol):
+    """The cylinder workload scaled to 200 x 100 (D = 10), 300 steps."""
+    c = cylinder(200, 100, diameter=10.0, sponge=25)
+    P, f = to_oracle(c)
+    f = P.run(f, 300)
+    r_ref, u_ref, _ = P.moments(f)
+    s = to_gpu(c, PRECS[prec])
+    s.step(300)
+    r, u, _ = s.moments()
+    fluid = c.solid == 0
+    assert _normwise(r[fluid], r_ref[fluid]) <= tol
+    assert _normwise(u[fluid], u_ref[fluid]) <= tol
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_round_jet_scaled_parity(prec, tol):
+    """The round jet scaled to 48 x 32 x 32 (D = 6, sponges 8), 60 steps, seeded inlet noise."""
+    c = round_jet(48, 32, 32, diameter=6.0, sponge=8, Re=2500.0)
+    P, f = to_oracle(c)
+    f = P.run(f, 60)
+    r_ref, u_ref, _ = P.moments(f)
+    s = to_gpu(c, PRECS[prec])
+    s.step(60)
+    r, u, _ = s.moments()
+    assert _normwise(r, r_ref) <= tol
+    assert _normwise(u, u_ref) <= tol
+
+
+def test_edge_sizes_and_zero_steps():
+    """Tiny and ragged boxes: 1x1 periodic, 3x3 with open faces, 129 wide (one
+    cell past a block), n = 0 steps."""
+    for n, faces in [((1, 1, 1), {}), ((3, 3, 1), {0: (VELOCITY, (0.05, 0, 0), None), 1: (OUTFLOW, (0, 0, 0), None),
+                                                   2: (OUTFLOW, (0, 0, 0), None), 3: (OUTFLOW, (0, 0, 0), None)}),
+                     ((129, 2, 1), {})]:
+        c = with_random_state(Case("edge", D2Q9, n, 0.8), seed=2)
+        c.faces = faces
+        P, f = to_oracle(c)
+        s = to_gpu(c, PRECS["fp64"])
+        s.step(0)
+        assert np.abs(s.populations() - f).max() < 1e-15
+        f = P.run(f, 3)
+        s.step(3)
+        assert np.abs(s.populations() - f).max() < 1e-13
+    c = with_random_state(Case("edge3", D3Q19, (3, 3, 3), 0.8), seed=2)
+    c.faces = {k: (OUTFLOW, (0, 0, 0), None) for k in range(6)}
+    P, f = to_oracle(c)
+    s = to_gpu(c, PRECS["fp64"])
+    f = P.run(f, 2)
+    s.step(2)
+    assert np.abs(s.populations() - f).max() < 1e-13
+
+
+def test_moments_probe_and_reduce_match_oracle():
+    c = _boxed_case(D3Q19, seed=9)
+    P, f = to_oracle(c)
+    f = P.run(f, 2)
+    s = to_gpu(c, PRECS["fp64"])
+    s.step(2)
+    r, u, pn = s.moments()
+    r0, u0, pn0 = P.moments(f)
+    assert np.abs(r - r0).max() < 1e-14
+    assert np.abs(u - u0).max() < 1e-13
+    assert np.abs(pn - pn0).max() < 1e-14
+    from paper_1710_02065_gb300 import lbm
+    cells = [0, 17, 400, c.ncell - 1]
+    p = lbm.lbm_probe(s.h, cells)
+    assert np.abs(p - (r0[cells] - c.rho_ref) / 3.0).max() < 1e-15
+    m, j, rc = s.reduce()
+    fluid = c.solid == 0
+    assert rc == 0
+    assert abs(m - r0[fluid].sum()) < 1e-11
+    assert np.abs(j - (r0[fluid, None] * u0[fluid]).sum(0)).max() < 1e-11
+
+
+def test_non_finite_state_is_reported():
+    from paper_1710_02065_gb300 import lbm
+    c = with_random_state(Case("nan", D2Q9, (16, 8, 1), 0.8), seed=2)
+    c.f0[3, 5] = np.nan
+    s = to_gpu(c, PRECS["fp32"])
+    _, _, rc = s.reduce()
+    assert rc == lbm.LBM_EUNSTABLE
+
+
+def test_checkpoint_resume_is_bit_identical(tmp_path):
+    c = _boxed_case(D2Q9, seed=4)
+    a = to_gpu(c, PRECS["fp32"])
+    a.step(5)
+    from paper_1710_02065_gb300 import lbm
+    path = str(tmp_path / "ck.bin")
+    lbm.lbm_save(a.h, path)
+    a.step(7)
+    b = to_gpu(c, PRECS["fp32"])
+    lbm.lbm_load(b.h, path)
+    assert b.info()["step"] == 5
+    b.step(7)
+    assert np.array_equal(a.populations(), b.populations())
+
+
+def test_full_size_cylinder_one_step():
+    """1600 x 800 cylinder workload at full size, FP32, one step from a random
+    off-equilibrium state, every cell compared with the oracle."""
+    c = with_random_state(cylinder(), seed=21, spread=0.05)
+    P, f = to_oracle(c)
+    s = to_gpu(c, PRECS["fp32"])
+    s.step(1)
+    got = s.populations()
+    ref = P.run(f, 1)
+    _, _, _, w, _ = oracle.lattice(D2Q9)
+    assert np.abs(got - ref).max() <= _pop_tol("fp32", ref, w, 1)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_full_size_round_jet_sampled_cells(prec):
+    """384 x 256 x 256 round jet at full size in the benchmark's launch
+    configuration: one step from a random state; 6000 sampled cells (random,
+    plus every face, edge, sponge and inlet class) checked cell by cell."""
+    c = round_jet()
+    _, _, _, w, _ = oracle.lattice(D3Q19)
+    c.f0 = inputs.random_populations(w, c.ncell, seed=31, spread=0.05)
+    s = to_gpu(c, PRECS[prec])
+    f0 = s.populations()  # the stored (possibly rounded) state is the oracle's input
+    s.step(1)
+    got = s.populations()
+    P = oracle.Problem(D3Q19, c.n, c.tau)
+    for face, (kind, u, prof) in c.faces.items():
+        P.set_boundary(face, kind, u, prof)
+    for face, (wd, chi) in c.sponges.items():
+        P.set_sponge(face, wd, chi, c.rho_ref, c.u_ref)
+    P.noise_seed, P.noise_amp = c.noise
+    nx, ny, nz = c.n
+    rng = np.random.default_rng(5)
+    cells = list(rng.integers(0, c.ncell, 4000))
+    for x in (0, 1, nx - 1, nx - 2, nx - 20):
+        for y in (0, ny // 2, ny - 1, 3):
+            for z in (0, nz // 2, nz - 1, 250):
+                cells.append(x + nx * (y + ny * z))
+    # inlet disc cells
+    for dy in range(-12, 13, 3):
+        for dz in range(-12, 13, 3):
+            cells.append(0 + nx * ((ny // 2 + dy) + ny * (nz // 2 + dz)))
+    cells = np.unique(np.array(cells, dtype=np.int64))
+    ref = P.update_cells(f0, cells, step=0)
+    err = np.abs(got[:, cells].T - ref).max()
+    g = np.abs(ref - w[None, :]).max()
+    tol = 1e-5 * np.abs(ref).max() if prec == "fp32" else 2 * 2.0 ** -10 * g + 1e-7
+    assert err <= tol, (err, tol)
