@@ -116,7 +116,8 @@ class ClockSampler:
             self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=self.out, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # nvidia-smi needs a moment before its first sample
         except Exception:
             self.proc = None
 
@@ -298,12 +299,15 @@ def run_reference(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16", "fp64"])
     ap.add_argument("--no-extra", action="store_true", help="skip the other storage precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
+    ap.add_argument("--grid", default="384x256x256",
+                    help="jet extents NXxNYxNZ; inlet diameter and sponges scale with NX/384")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -322,7 +326,9 @@ def main():
     barrier(pg)
     from paper_1710_02065_gb300 import lbm
 
-    spec = jet_spec()
+    nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
+    scale = nx / 384.0
+    spec = jet_spec(nx, ny, nz, diameter=24.0 * scale, sponge=max(2, int(round(32 * scale))))
     prec = lbm.PRECISIONS[args.precision]
     stream = torch.cuda.Stream()
     clocks = ClockSampler(torch.cuda.current_device())
@@ -341,7 +347,7 @@ def main():
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     else:
         peak, peak_src = 6800.0, "fallback"
-    key = f"k_stream_collide_d3q19_{args.precision}_jet384"
+    key = f"k_stream_collide_d3q19_{args.precision}_jet{nx}x{ny}x{nz}"
     traffic = recorded_traffic(key)
 
     extra = {}
@@ -360,8 +366,8 @@ def main():
         if "bf16" in extra:
             extra["bf16_store_speedup"] = extra["bf16"]["mlups"] / (ncell / (kernel_ms / 1e3) / 1e6)
 
-    e2e = e2e_run(lbm, torch, spec, prec, args.steps, stream)
-    e2e_s = max_over_ranks(e2e["seconds"], pg, world)
+    e2e = None if args.no_e2e else e2e_run(lbm, torch, spec, prec, args.steps, stream)
+    e2e_s = max_over_ranks(e2e["seconds"], pg, world) if e2e else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -376,7 +382,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic",
-            "config": {"workload": f"D3Q19 round jet 384x256x256, {args.precision} population storage, "
+            "config": {"workload": f"D3Q19 round jet {nx}x{ny}x{nz}, {args.precision} population storage, "
                                    "two-lattice pull, fused inflow/outflow/sponge",
                        "cells": ncell, "tau": spec["tau"], "storage": args.precision,
                        "l2": "inputs larger than L2 (populations %.2f GB per lattice)" % (bpc / 2 * ncell / 1e9),
@@ -386,8 +392,8 @@ def main():
                          "kernel": "k_stream_collide<D3Q19>", "bytes_per_cell": bpc,
                          "kernel_ms": kernel_ms},
             "cpu_baseline": cpu,
-            "e2e": {"value": world * ncell * args.steps / e2e_s / 1e6, "unit": "MLUPS",
-                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+            "e2e": ({"value": world * ncell * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]} if e2e else None),
             "gpu_launches": main_run["launches"],
             "clocks": clk,
             "stable": main_run["stable"],

@@ -85,6 +85,8 @@ typedef struct lbm_ctx *lbm_handle;
 /* Cell types for lbm_set_geometry */
 #define LBM_CELL_FLUID 0
 #define LBM_CELL_SOLID 1 /* halfway bounce-back wall */
+#define LBM_CELL_FIXED 2 /* populations held fixed (set by the caller or by a
+                            coupling step); streamed from like a fluid cell */
 
 /*
  * lbm_lattice_table -- velocities and weights of a lattice (host only, no GPU
@@ -125,12 +127,14 @@ void lbm_destroy(lbm_handle h);
 const char *lbm_last_error(lbm_handle h);
 
 /*
- * lbm_set_geometry -- cell types, ncell bytes (LBM_CELL_FLUID / LBM_CELL_SOLID),
- * host memory; NULL removes all solids.  Solid cells are walls with halfway
- * bounce-back (Sec. III: the paper's cylinder and pipe walls): a population
- * that would stream out of a solid cell is replaced by the receiving cell's
- * own post-collision population in the opposite direction.  Solid cells keep
- * their stored populations unchanged.
+ * lbm_set_geometry -- cell types, ncell bytes (LBM_CELL_FLUID / LBM_CELL_SOLID /
+ * LBM_CELL_FIXED), host memory; NULL removes all solids.  Solid cells are
+ * walls with halfway bounce-back (Sec. III: the paper's cylinder and pipe
+ * walls): a population that would stream out of a solid cell is replaced by
+ * the receiving cell's own post-collision population in the opposite
+ * direction.  Solid and fixed cells keep their stored populations unchanged;
+ * fixed cells are streamed from like fluid cells.  lbm_reduce skips solid
+ * cells only.
  */
 int lbm_set_geometry(lbm_handle h, const uint8_t *cell_type);
 
@@ -220,6 +224,22 @@ int lbm_reduce(lbm_handle h, double *mass, double momentum[3]);
  * rho_ref is the sponge reference density (1 if no sponge).
  */
 int lbm_probe(lbm_handle h, int n, const int64_t *cells, double *p_prime);
+
+/*
+ * lbm_set_launch -- launch shape of the update kernel (a tuning knob; the
+ * result does not depend on it beyond FP round-off order).
+ *   block            : threads per block, a multiple of 32 in [32, 256], or 0
+ *                      for the default (128)
+ *   cells_per_thread : 1 = one cell per thread (the general kernel); 2 or 4 =
+ *                      vectorised kernel with that many consecutive x cells per
+ *                      thread (FP64: 2; FP32: 2 or 4; FP16/BF16: 4); 0 = default
+ *                      (4, FP64 2).  The vectorised kernel is used only when
+ *                      there is no cell-type mask and nx is a multiple of it;
+ *                      otherwise the general kernel runs.
+ * lbm_get_launch reports the shape lbm_step will use now.
+ */
+int lbm_set_launch(lbm_handle h, int block, int cells_per_thread);
+int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread);
 
 /* lbm_sync -- wait for all work of h; returns any pending execution error. */
 int lbm_sync(lbm_handle h);

@@ -66,6 +66,10 @@ class _Problem(C.Structure):
     ]
 
 
+class _Patch(C.Structure):
+    _fields_ = [("X0", C.c_int), ("Y0", C.c_int), ("Wc", C.c_int), ("Hc", C.c_int)]
+
+
 def lib():
     global _lib
     with _lock:
@@ -92,6 +96,9 @@ def lib():
             _lib.orc_splitmix64.restype = C.c_uint64
             _lib.orc_u01.argtypes = [C.c_uint64]
             _lib.orc_u01.restype = C.c_double
+            G = C.POINTER(_Patch)
+            _lib.orc_refined_init_moments.argtypes = [P, G, dp, dp]
+            _lib.orc_refined_step.argtypes = [P, P, G, dp, dp, dp, dp, dp, dp, C.c_int64]
         return _lib
 
 
@@ -265,3 +272,56 @@ class Problem:
     def chi(self, x: int, y: int, z: int = 0) -> float:
         s = self._struct()
         return lib().orc_chi_at(C.byref(s), x, y, z)
+
+
+FLUID, SOLID, FIXED = 0, 1, 2
+
+
+class TwoLevel:
+    """Two-level 2:1 D2Q9 grid (Sec. II.B): a coarse Problem plus a fine patch
+    over coarse nodes X0..X0+Wc, Y0..Y0+Hc, with tau_f = 2 tau_c - 1/2.
+
+    The coarse problem carries its own boundaries; the fine one is periodic
+    with its boundary ring fixed (rebuilt from coarse data every half step).
+    The patch must keep 2 coarse nodes from every coarse face.
+    """
+
+    def __init__(self, coarse: Problem, X0: int, Y0: int, Wc: int, Hc: int):
+        assert coarse.lattice == D2Q9
+        nxc, nyc = coarse.n[0], coarse.n[1]
+        assert X0 >= 2 and Y0 >= 2 and X0 + Wc <= nxc - 3 and Y0 + Hc <= nyc - 3 and Wc >= 4 and Hc >= 4
+        self.Pc = coarse
+        self.patch = (X0, Y0, Wc, Hc)
+        self.Pf = Problem(D2Q9, (2 * Wc + 1, 2 * Hc + 1), 2 * coarse.tau - 0.5)
+        cmask = np.zeros((nyc, nxc), np.uint8) if coarse.solid is None else coarse.solid.reshape(nyc, nxc).copy()
+        cmask[Y0 + 1:Y0 + Hc, X0 + 1:X0 + Wc] = FIXED
+        self.Pc.solid = cmask.reshape(-1)
+        fmask = np.zeros((2 * Hc + 1, 2 * Wc + 1), np.uint8)
+        fmask[0, :] = fmask[-1, :] = FIXED
+        fmask[:, 0] = fmask[:, -1] = FIXED
+        self.Pf.solid = fmask.reshape(-1)
+        self.step_index = 0
+
+    def set_fine_solid(self, solid_fine: np.ndarray):
+        m = self.Pf.solid.reshape(self.Pf.n[1], self.Pf.n[0]).copy()
+        s = np.asarray(solid_fine, np.uint8).reshape(m.shape)
+        m[(s == SOLID) & (m != FIXED)] = SOLID
+        self.Pf.solid = m.reshape(-1)
+
+    def init(self, rho_c, u_c, rho_f, u_f):
+        self.fc = self.Pc.equilibrium(rho_c, u_c)
+        self.ff = self.Pf.equilibrium(rho_f, u_f)
+        self.M0 = np.zeros(6 * self.Pc.ncell)
+        self.M1 = np.zeros(6 * self.Pc.ncell)
+        sc, g = self.Pc._struct(), _Patch(*self.patch)
+        lib().orc_refined_init_moments(C.byref(sc), C.byref(g), _dp(self.fc), _dp(self.M0))
+        self.step_index = 0
+
+    def run(self, nsteps: int):
+        sc, sf, g = self.Pc._struct(), self.Pf._struct(), _Patch(*self.patch)
+        wc = np.empty_like(self.fc)
+        wf = np.empty_like(self.ff)
+        for _ in range(int(nsteps)):
+            lib().orc_refined_step(C.byref(sc), C.byref(sf), C.byref(g), _dp(self.fc), _dp(wc),
+                                   _dp(self.ff), _dp(wf), _dp(self.M0), _dp(self.M1), self.step_index)
+            self.step_index += 1

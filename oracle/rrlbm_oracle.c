@@ -44,7 +44,8 @@
  *       the streamed populations of its inward neighbour and collides them.
  *   R8  Walls: halfway bounce-back; a population that would stream out of a
  *       solid cell is replaced by the node's own post-collision population in
- *       the opposite direction.
+ *       the opposite direction.  Solid cells, and "fixed" cells whose
+ *       populations are imposed from outside (grid coupling), are not updated.
  *   R9  Inlet noise: counter-based uniform numbers from splitmix64 (Steele,
  *       Lea and Flood 2014) keyed by (seed, step, face cell, component).
  */
@@ -301,7 +302,7 @@ typedef struct {
     double sponge_chi[6];
     double rho_ref;
     double u_ref[3];
-    const uint8_t *solid;    /* optional, 1 = solid, per cell */
+    const uint8_t *solid;    /* optional per cell: 1 = solid wall, 2 = fixed */
     double g[3];             /* oracle-only body force */
 } orc_problem;
 
@@ -385,7 +386,7 @@ void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int6
             if (P->face_kind[2 * a] == BC_PERIODIC) src[a] = ((src[a] % P->n[a]) + P->n[a]) % P->n[a];
         }
         int64_t scl = src[0] + (int64_t)P->n[0] * (src[1] + (int64_t)P->n[1] * src[2]);
-        if (P->solid && P->solid[scl])
+        if (P->solid && P->solid[scl] == 1)
             f[i] = fin[(int64_t)L->opp[i] * N + scell];
         else
             f[i] = fin[(int64_t)i * N + scl];
@@ -534,4 +535,211 @@ double orc_chi_at(const orc_problem *P, int x, int y, int z)
 {
     int c[3] = {x, y, z};
     return sponge_chi(P, c);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Two-level 2:1 grid refinement (Sec. II.B), 2D                             */
+/* ------------------------------------------------------------------------ */
+/*
+ * Layout (reading R10; Fig. 1 of the paper is not available):
+ *   - The fine patch covers the coarse nodes X0..X0+Wc, Y0..Y0+Hc (vertex
+ *     based, dx_f = dx_c / 2): fine node (i, j), 0 <= i <= 2 Wc,
+ *     0 <= j <= 2 Hc, sits at coarse coordinates (X0 + i/2, Y0 + j/2); even
+ *     (i, j) coincide with coarse nodes.
+ *   - The fine boundary ring (i or j on the patch edge) is not updated by the
+ *     fine step; it is rebuilt from coarse data (Eq. couplingFC).
+ *   - Coarse nodes strictly inside the patch are not updated by the coarse
+ *     step; the first ring of them is rebuilt from fine data
+ *     (Eq. couplingCF); deeper ones are never read.
+ *   - Exchanged data are the pre-collision rho, u and Pi^neq of the sending
+ *     grid; the receiving node is rebuilt as feqH(rho, u) + (1 - 1/tau)
+ *     fneqH(u, alpha Pi^neq) in its own post-collision form, the regularized
+ *     f^neq being a function of u and Pi^neq only (Eq. neqH, Eq. recursive2).
+ *   - Scaling (reading R11): tau_f = 2 tau_c - 1/2 (Sec. II.B); alpha =
+ *     tau_f / (2 tau_c) coarse -> fine and 2 tau_c / tau_f fine -> coarse,
+ *     from the leading-order Chapman-Enskog f^neq ~ tau dt grad(u) with
+ *     dt_f = dt_c / 2 (the printed alpha = 2 tau_f / tau_c is read as a misprint).
+ *   - Coarse -> fine in space: copy at coincident nodes, 4-point centred cubic
+ *     (-1, 9, 9, -1)/16 along the interface line at mid nodes; in time: the
+ *     average of the coarse values at t and t + 1 for the fine half step
+ *     (linear in time, Sec. II.B).
+ *   - Fine -> coarse: rho and u of the coincident fine node, Pi^neq low-pass
+ *     filtered with the 3 x 3 full-weighting kernel (1,2,1) x (1,2,1) / 16
+ *     (reading R12: the filter is not specified).
+ */
+typedef struct {
+    int X0, Y0, Wc, Hc;
+} orc_patch;
+
+/* Pre-collision moments at an interior node (pull with wrap and walls):
+ * m = (rho, ux, uy, Pxx, Pxy, Pyy). */
+static void streamed_moments(const orc_problem *P, const double *fin, int x, int y, double m[6])
+{
+    const lattice_t *L = lattice(P->lattice);
+    const int64_t N = ncell(P);
+    const int64_t cell = x + (int64_t)P->n[0] * y;
+    double f[19], rho, j[3], Pi[3][3], u[3], Pn[3][3];
+    for (int i = 0; i < L->q; ++i) {
+        int sx = x - L->xi[i][0], sy = y - L->xi[i][1];
+        sx = ((sx % P->n[0]) + P->n[0]) % P->n[0];
+        sy = ((sy % P->n[1]) + P->n[1]) % P->n[1];
+        int64_t scl = sx + (int64_t)P->n[0] * sy;
+        if (P->solid && P->solid[scl] == 1)
+            f[i] = fin[(int64_t)L->opp[i] * N + cell];
+        else
+            f[i] = fin[(int64_t)i * N + scl];
+    }
+    moments(L, f, &rho, j, Pi);
+    for (int a = 0; a < 3; ++a) u[a] = j[a] / rho;
+    pi_neq(L->d, rho, u, Pi, Pn);
+    m[0] = rho; m[1] = u[0]; m[2] = u[1];
+    m[3] = Pn[0][0]; m[4] = Pn[0][1]; m[5] = Pn[1][1];
+}
+
+/* Post-collision populations rebuilt from (rho, u, alpha Pi^neq). */
+static void rebuild_post(const lattice_t *L, const double m[6], double alpha, double tau, double *out)
+{
+    double u[3] = {m[1], m[2], 0.0};
+    double Pn[3][3] = {{alpha * m[3], alpha * m[4], 0}, {alpha * m[4], alpha * m[5], 0}, {0, 0, 0}};
+    double feq[19], fneq[19];
+    feqH(L, m[0], u, feq);
+    fneqH(L, u, Pn, fneq);
+    for (int i = 0; i < L->q; ++i) out[i] = feq[i] + (1.0 - 1.0 / tau) * fneq[i];
+}
+
+/* Coarse moments on the interface lines, extended by one node past each end:
+ * stored per coarse cell (6 doubles), only line entries are written. */
+static void coarse_line_moments(const orc_problem *Pc, const orc_patch *G, const double *fc, double *M)
+{
+    for (int x = G->X0 - 1; x <= G->X0 + G->Wc + 1; ++x) {
+        streamed_moments(Pc, fc, x, G->Y0, M + 6 * (x + (int64_t)Pc->n[0] * G->Y0));
+        streamed_moments(Pc, fc, x, G->Y0 + G->Hc, M + 6 * (x + (int64_t)Pc->n[0] * (G->Y0 + G->Hc)));
+    }
+    for (int y = G->Y0 - 1; y <= G->Y0 + G->Hc + 1; ++y) {
+        streamed_moments(Pc, fc, G->X0, y, M + 6 * (G->X0 + (int64_t)Pc->n[0] * y));
+        streamed_moments(Pc, fc, G->X0 + G->Wc, y, M + 6 * (G->X0 + G->Wc + (int64_t)Pc->n[0] * y));
+    }
+}
+
+/* Time-weighted coarse moment at coarse node (x, y): (1 - a) M0 + a M1. */
+static void mix(const double *M0, const double *M1, double a, int nxc, int x, int y, double out[6])
+{
+    const double *p = M0 + 6 * (x + (int64_t)nxc * y), *q = M1 + 6 * (x + (int64_t)nxc * y);
+    for (int k = 0; k < 6; ++k) out[k] = (1.0 - a) * p[k] + a * q[k];
+}
+
+/* Rebuild the fine boundary ring from coarse line moments at time weight a. */
+static void fill_fine_ring(const orc_problem *Pc, const orc_problem *Pf, const orc_patch *G,
+                           const double *M0, const double *M1, double a, double *ff)
+{
+    const lattice_t *L = lattice(Pf->lattice);
+    const int64_t Nf = ncell(Pf);
+    const int nxc = Pc->n[0];
+    const double tau_c = Pc->tau, tau_f = Pf->tau;
+    const double alpha = tau_f / (2.0 * tau_c);
+    const int nfx = 2 * G->Wc + 1, nfy = 2 * G->Hc + 1;
+    for (int j = 0; j < nfy; ++j)
+        for (int i = 0; i < nfx; ++i) {
+            int on_h = (j == 0 || j == nfy - 1), on_v = (i == 0 || i == nfx - 1);
+            if (!on_h && !on_v) continue;
+            double m[6], t0[6], t1[6], t2[6], t3[6];
+            if (i % 2 == 0 && j % 2 == 0) {
+                mix(M0, M1, a, nxc, G->X0 + i / 2, G->Y0 + j / 2, m);
+            } else if (on_h && i % 2 == 1) {
+                int xa = G->X0 + (i - 1) / 2, yc = G->Y0 + j / 2;
+                mix(M0, M1, a, nxc, xa - 1, yc, t0);
+                mix(M0, M1, a, nxc, xa, yc, t1);
+                mix(M0, M1, a, nxc, xa + 1, yc, t2);
+                mix(M0, M1, a, nxc, xa + 2, yc, t3);
+                for (int k = 0; k < 6; ++k) m[k] = (-t0[k] + 9.0 * t1[k] + 9.0 * t2[k] - t3[k]) / 16.0;
+            } else {
+                int xc = G->X0 + i / 2, ya = G->Y0 + (j - 1) / 2;
+                mix(M0, M1, a, nxc, xc, ya - 1, t0);
+                mix(M0, M1, a, nxc, xc, ya, t1);
+                mix(M0, M1, a, nxc, xc, ya + 1, t2);
+                mix(M0, M1, a, nxc, xc, ya + 2, t3);
+                for (int k = 0; k < 6; ++k) m[k] = (-t0[k] + 9.0 * t1[k] + 9.0 * t2[k] - t3[k]) / 16.0;
+            }
+            double out[19];
+            rebuild_post(L, m, alpha, tau_f, out);
+            int64_t cell = i + (int64_t)nfx * j;
+            for (int q = 0; q < L->q; ++q) ff[(int64_t)q * Nf + cell] = out[q];
+        }
+}
+
+/* Rebuild the first ring of covered coarse nodes from the fine grid
+ * (Eq. couplingCF): rho, u at the coincident fine node, filtered Pi^neq. */
+static void restrict_to_coarse(const orc_problem *Pc, const orc_problem *Pf, const orc_patch *G,
+                               const double *ff_prev, double *fc)
+{
+    const lattice_t *L = lattice(Pc->lattice);
+    const int64_t Nc = ncell(Pc);
+    const double alpha = 2.0 * Pc->tau / Pf->tau;
+    static const double w3[3] = {1.0, 2.0, 1.0};
+    for (int y = G->Y0 + 1; y <= G->Y0 + G->Hc - 1; ++y)
+        for (int x = G->X0 + 1; x <= G->X0 + G->Wc - 1; ++x) {
+            int ring = (x == G->X0 + 1 || x == G->X0 + G->Wc - 1 || y == G->Y0 + 1 || y == G->Y0 + G->Hc - 1);
+            if (!ring) continue;
+            int i = 2 * (x - G->X0), j = 2 * (y - G->Y0);
+            double m[6], mc[6] = {0, 0, 0, 0, 0, 0};
+            for (int l = -1; l <= 1; ++l)
+                for (int k = -1; k <= 1; ++k) {
+                    streamed_moments(Pf, ff_prev, i + k, j + l, m);
+                    double wgt = w3[k + 1] * w3[l + 1] / 16.0;
+                    for (int c = 3; c < 6; ++c) mc[c] += wgt * m[c];
+                    if (k == 0 && l == 0) { mc[0] = m[0]; mc[1] = m[1]; mc[2] = m[2]; }
+                }
+            double out[19];
+            rebuild_post(L, mc, alpha, Pc->tau, out);
+            int64_t cell = x + (int64_t)Pc->n[0] * y;
+            for (int q = 0; q < L->q; ++q) fc[(int64_t)q * Nc + cell] = out[q];
+        }
+}
+
+/* Moments stored at t = 0 on the interface lines: local moments of the
+ * stored populations (the initial state has no earlier step). */
+void orc_refined_init_moments(const orc_problem *Pc, const orc_patch *G, const double *fc, double *M)
+{
+    const lattice_t *L = lattice(Pc->lattice);
+    const int64_t N = ncell(Pc);
+    for (int y = G->Y0 - 1; y <= G->Y0 + G->Hc + 1; ++y)
+        for (int x = G->X0 - 1; x <= G->X0 + G->Wc + 1; ++x) {
+            int64_t cell = x + (int64_t)Pc->n[0] * y;
+            double f[19], rho, j[3], Pi[3][3], u[3], Pn[3][3];
+            for (int i = 0; i < L->q; ++i) f[i] = fc[(int64_t)i * N + cell];
+            moments(L, f, &rho, j, Pi);
+            for (int a = 0; a < 3; ++a) u[a] = j[a] / rho;
+            pi_neq(L->d, rho, u, Pi, Pn);
+            double *m = M + 6 * cell;
+            m[0] = rho; m[1] = u[0]; m[2] = u[1];
+            m[3] = Pn[0][0]; m[4] = Pn[0][1]; m[5] = Pn[1][1];
+        }
+}
+
+/* One coarse step t -> t + 1 of the two-level grid:
+ *   1. coarse step; coarse line moments at t + 1 from the pre-step field
+ *   2. fine step t -> t + 1/2 (the ring holds t)
+ *   3. fine ring <- coarse moments averaged between t and t + 1
+ *   4. fine step t + 1/2 -> t + 1
+ *   5. fine ring <- coarse moments at t + 1
+ *   6. first covered coarse ring <- fine moments at t + 1
+ * M0 holds the line moments at t on entry and at t + 1 on return. */
+int orc_refined_step(const orc_problem *Pc, const orc_problem *Pf, const orc_patch *G,
+                     double *fc, double *fc_work, double *ff, double *ff_work, double *M0,
+                     double *M1, int64_t step)
+{
+    const lattice_t *L = lattice(Pc->lattice);
+    const int64_t Nc = ncell(Pc), Nf = ncell(Pf);
+    const size_t Mbytes = sizeof(double) * 6 * (size_t)Nc;
+    coarse_line_moments(Pc, G, fc, M1);
+    orc_step(Pc, fc, fc_work, step);
+    orc_step(Pf, ff, ff_work, 2 * step);
+    fill_fine_ring(Pc, Pf, G, M0, M1, 0.5, ff_work);
+    orc_step(Pf, ff_work, ff, 2 * step + 1);
+    fill_fine_ring(Pc, Pf, G, M0, M1, 1.0, ff);
+    restrict_to_coarse(Pc, Pf, G, ff_work, fc_work);
+    memcpy(fc, fc_work, sizeof(double) * (size_t)Nc * (size_t)L->q);
+    memcpy(M0, M1, Mbytes);
+    (void)Nf;
+    return 0;
 }

@@ -30,7 +30,8 @@ __global__ void k_init_eq(int64_t N, const double *__restrict__ rho, const doubl
     const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (cell >= N) return;
     Coef<double> k{};
-    add_eq<double>(k, 1.0, rho[cell], u[3 * cell], u[3 * cell + 1], L::D == 3 ? u[3 * cell + 2] : 0.0);
+    add_eq<double>(k, 1.0, rho[cell] - 1.0, rho[cell], u[3 * cell], u[3 * cell + 1],
+                   L::D == 3 ? u[3 * cell + 2] : 0.0);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const S v = Store<S>::from(rebuild<L, double>(k, i));
@@ -84,7 +85,7 @@ __global__ void k_moments(int64_t N, const S *__restrict__ f, double *__restrict
         u[3 * cell + 2] = uz;
     }
     if (pn) {
-        const Sym2<double> p = pi_neq<double>(m, r, ux, uy, uz, L::D);
+        const Sym2<double> p = pi_neq<double>(m, m.dr, r, ux, uy, uz, L::D);
         pn[6 * cell + 0] = p.xx;
         pn[6 * cell + 1] = p.xy;
         pn[6 * cell + 2] = p.xz;
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(int64_t N, const S *__rest
     double acc[RED_FIELDS] = {0, 0, 0, 0, 0, 0};
     for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < N;
          cell += (int64_t)gridDim.x * blockDim.x) {
-        if (solid && solid[cell]) continue;
+        if (solid && solid[cell] == 1) continue;
         double g[L::Q];
         load_cell_fp64<L, S>(f, N, cell, g);
         bool finite = true;

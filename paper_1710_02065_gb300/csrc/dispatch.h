@@ -14,3 +14,27 @@ cudaError_t step_d3q19(int precision, const StepParams &p, const void *fin, void
                        cudaStream_t st);
 
 }  // namespace rr
+
+namespace rr {
+
+// Vectorised kernel (no cell-type mask, nx % vec == 0).  Supported (precision,
+// vec): FP64 2; FP32 2, 4; FP16 4; BF16 4.
+cudaError_t stepvec_d2q9(int precision, int vec, const StepParams &p, const void *fin, void *fout,
+                         int block, cudaStream_t st);
+cudaError_t stepvec_d3q19(int precision, int vec, const StepParams &p, const void *fin, void *fout,
+                          int block, cudaStream_t st);
+
+// Cells per thread the vectorised kernel supports for a precision (0: none)
+inline bool vec_supported(int precision, int vec)
+{
+    switch (precision) {
+    case PREC_FP64: return vec == 2;
+    case PREC_FP32: return vec == 2 || vec == 4;
+    case PREC_FP16:
+    case PREC_BF16: return vec == 4;
+    }
+    return false;
+}
+inline int vec_default(int precision) { return precision == PREC_FP64 ? 2 : 4; }
+
+}  // namespace rr

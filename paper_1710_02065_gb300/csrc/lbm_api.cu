@@ -35,7 +35,8 @@ struct lbm_ctx {
     uint64_t noise_seed = 0;
     double noise_amp = 0.0;
     int64_t step = 0, launches = 0;
-    int block = 128;
+    int block = 0;  // 0: automatic
+    int vec = 0;    // cells per thread; 0: automatic, 1: scalar kernel
     double *red_d = nullptr;  // reduction partials + result
     int red_blocks = 0;
     std::string err;
@@ -291,7 +292,7 @@ extern "C" int lbm_set_geometry(lbm_handle h, const uint8_t *cell_type)
         return LBM_OK;
     }
     for (int64_t c = 0; c < h->ncell; ++c)
-        if (cell_type[c] > LBM_CELL_SOLID)
+        if (cell_type[c] > LBM_CELL_FIXED)
             return fail(h, LBM_EINVAL, "cell_type[%lld] = %d is not a cell type", (long long)c, cell_type[c]);
     if (!h->solid_d) CUDA_TRY(h, cudaMalloc(&h->solid_d, (size_t)h->ncell));
     CUDA_TRY(h, cudaMemcpyAsync(h->solid_d, cell_type, (size_t)h->ncell, cudaMemcpyHostToDevice, h->stream));
@@ -475,6 +476,7 @@ static int build_params(lbm_ctx *h, StepParams &p)
         p.u_profile[f] = h->prof_d[f];
     }
     p.rho_ref = h->rho_ref;
+    p.rho_ref_m1 = h->rho_ref - 1.0;
     for (int a = 0; a < 3; ++a) p.u_ref[a] = h->u_ref[a];
     p.noise_seed = h->noise_seed;
     p.noise_amp = h->noise_amp;
@@ -491,16 +493,46 @@ extern "C" int lbm_step(lbm_handle h, int64_t n)
     StepParams p;
     int rc = build_params(h, p);
     if (rc != LBM_OK) return rc;
+    int vec = h->vec == 0 ? vec_default(h->prec) : h->vec;
+    if (h->solid_d || vec == 1 || !vec_supported(h->prec, vec) || h->n[0] % vec != 0) vec = 1;
+    const int block = h->block > 0 ? h->block : (vec == 1 ? 128 : 128);
     for (int64_t t = 0; t < n; ++t) {
         p.step = h->step;
-        cudaError_t e = h->lattice == LBM_D2Q9
-                            ? step_d2q9(h->prec, p, h->f[h->cur], h->f[1 - h->cur], h->block, h->stream)
-                            : step_d3q19(h->prec, p, h->f[h->cur], h->f[1 - h->cur], h->block, h->stream);
+        cudaError_t e;
+        if (vec == 1)
+            e = h->lattice == LBM_D2Q9 ? step_d2q9(h->prec, p, h->f[h->cur], h->f[1 - h->cur], block, h->stream)
+                                       : step_d3q19(h->prec, p, h->f[h->cur], h->f[1 - h->cur], block, h->stream);
+        else
+            e = h->lattice == LBM_D2Q9
+                    ? stepvec_d2q9(h->prec, vec, p, h->f[h->cur], h->f[1 - h->cur], block, h->stream)
+                    : stepvec_d3q19(h->prec, vec, p, h->f[h->cur], h->f[1 - h->cur], block, h->stream);
         if (e != cudaSuccess) return fail(h, LBM_ECUDA, "stream-collide launch: %s", cudaGetErrorString(e));
         h->cur = 1 - h->cur;
         h->step += 1;
         h->launches += 1;
     }
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_launch(lbm_handle h, int block, int cells_per_thread)
+{
+    CHECK_HANDLE(h);
+    if (block != 0 && (block < 32 || block > 256 || block % 32 != 0))
+        return fail(h, LBM_EINVAL, "block = %d must be 0 or a multiple of 32 in [32, 256]", block);
+    if (cells_per_thread != 0 && cells_per_thread != 1 && !vec_supported(h->prec, cells_per_thread))
+        return fail(h, LBM_EINVAL, "cells_per_thread = %d is not supported for this precision", cells_per_thread);
+    h->block = block;
+    h->vec = cells_per_thread;
+    return LBM_OK;
+}
+
+extern "C" int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread)
+{
+    CHECK_HANDLE(h);
+    int vec = h->vec == 0 ? vec_default(h->prec) : h->vec;
+    if (h->solid_d || vec == 1 || !vec_supported(h->prec, vec) || h->n[0] % vec != 0) vec = 1;
+    if (block) *block = h->block > 0 ? h->block : 128;
+    if (cells_per_thread) *cells_per_thread = vec;
     return LBM_OK;
 }
 

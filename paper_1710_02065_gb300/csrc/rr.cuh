@@ -100,17 +100,33 @@ struct Store<float> {
     __device__ static float from(float v) { return v; }
     __device__ static float from(double v) { return (float)v; }
 };
+// 16-bit formats are moved as raw 16-bit words through the plain read-only
+// load path and converted in registers (bf16 -> f32 is a 16-bit shift).
 template <>
 struct Store<__half> {
-    __device__ static float ld(const __half *p) { return __half2float(__ldg(p)); }
-    __device__ static void st(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ static float ld(const __half *p)
+    {
+        const unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p));
+        return __half2float(__ushort_as_half(b));
+    }
+    __device__ static void st(__half *p, float v)
+    {
+        *reinterpret_cast<unsigned short *>(p) = __half_as_ushort(__float2half_rn(v));
+    }
     __device__ static __half from(float v) { return __float2half_rn(v); }
     __device__ static __half from(double v) { return __double2half(v); }
 };
 template <>
 struct Store<__nv_bfloat16> {
-    __device__ static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-    __device__ static void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static float ld(const __nv_bfloat16 *p)
+    {
+        const unsigned short b = __ldg(reinterpret_cast<const unsigned short *>(p));
+        return __uint_as_float((unsigned)b << 16);
+    }
+    __device__ static void st(__nv_bfloat16 *p, float v)
+    {
+        *reinterpret_cast<unsigned short *>(p) = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    }
     __device__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
     __device__ static __nv_bfloat16 from(double v) { return __double2bfloat16(v); }
 };
@@ -163,12 +179,14 @@ struct Sym2 {
     C xx, yy, zz, xy, xz, yz;
 };
 
-// Equilibrium coefficients of (rho, u), scaled by s: A2 += s rho u u, A3 += s rho u u u
+// Equilibrium coefficients of (rho, u), scaled by s: a0 += s (rho - 1),
+// a1 += s rho u, A2 += s rho u u, A3 += s rho u u u.  dr = rho - 1 is passed
+// separately so that it keeps its own precision.
 template <class C>
-__device__ __forceinline__ void add_eq(Coef<C> &k, C s, C rho, C ux, C uy, C uz)
+__device__ __forceinline__ void add_eq(Coef<C> &k, C s, C dr, C rho, C ux, C uy, C uz)
 {
     const C r = s * rho;
-    k.a0 += s * (rho - C(1));
+    k.a0 += s * dr;
     k.a1x += r * ux;
     k.a1y += r * uy;
     k.a1z += r * uz;
@@ -248,11 +266,12 @@ __device__ __forceinline__ C rebuild(const Coef<C> &k, int i)
     return C(weight<L>(i)) * r;
 }
 
-// Pi^neq about (rho, u) from shifted moments: s_ab - (rho - 1) c_s^2 delta_ab - rho u_a u_b
+// Pi^neq about (rho, u) from shifted moments, dr = rho - 1:
+//   s_ab - dr c_s^2 delta_ab - rho u_a u_b
 template <class C>
-__device__ __forceinline__ Sym2<C> pi_neq(const Mom<C> &m, C rho, C ux, C uy, C uz, int D)
+__device__ __forceinline__ Sym2<C> pi_neq(const Mom<C> &m, C dr, C rho, C ux, C uy, C uz, int D)
 {
-    const C c = (rho - C(1)) * C(1.0 / 3.0);
+    const C c = dr * C(1.0 / 3.0);
     Sym2<C> p;
     p.xx = m.sxx - c - rho * ux * ux;
     p.yy = m.syy - c - rho * uy * uy;

@@ -36,7 +36,7 @@ struct StepParams {
     double u_face[6][3];
     const double *u_profile[6];  // device, 3 doubles per face cell, or null
     double sponge_chi[6];
-    double rho_ref, u_ref[3];
+    double rho_ref, rho_ref_m1, u_ref[3];  // rho_ref_m1 = rho_ref - 1
     uint64_t noise_seed;
     double noise_amp;
     double omega;  // 1 - 1/tau
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ 
     const int64_t nxy = (int64_t)nx * ny;
     const int64_t cell = x + (int64_t)nx * y + nxy * z;
     const uint8_t *__restrict__ solid = p.solid;
-    if (solid && solid[cell]) return;
+    if (solid && solid[cell]) return;  // solid (1) and fixed (2) cells keep their populations
 
     // ---- boundary role and the node whose streamed populations are used
     int c[3] = {x, y, z};
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ 
         const int Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : s[1]);
         const int Z = L::D == 2 ? 0 : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : s[2]));
         const int64_t src = X + (int64_t)nx * Y + nxy * Z;
-        if (solid && i != 0 && solid[src])
+        if (solid && i != 0 && solid[src] == 1)
             g[i] = Store<S>::ld(fin + (int64_t)opp<L>(i) * N + scell);
         else
             g[i] = Store<S>::ld(fin + (int64_t)i * N + src);
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ 
         const C rho = C(1) + m.dr;
         const C inv = C(1) / rho;
         const C vx = m.jx * inv, vy = m.jy * inv, vz = m.jz * inv;
-        const Sym2<C> pn = pi_neq<C>(m, rho, vx, vy, vz, L::D);
+        const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, vx, vy, vz, L::D);
         const int a = inlet / 2;
         const int t0 = a == 0 ? 1 : 0, t1 = a == 2 ? 1 : 2;
         const int64_t kf = c[t0] + (int64_t)p.n[t0] * c[t1];
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ 
             }
         }
         const C ux = C(ub[0]), uy = C(ub[1]), uz = L::D == 3 ? C(ub[2]) : C(0);
-        add_eq<C>(k, C(1), rho, ux, uy, uz);
+        add_eq<C>(k, C(1), m.dr, rho, ux, uy, uz);
         add_neq<C>(k, om, ux, uy, uz, pn);
     } else {
         C chi = C(0);
@@ -145,22 +145,23 @@ __global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ 
             // sponge: damped moments rho*, rho* u* (n = m = 1/2)
             const C h = C(1) / (C(1) + C(0.5) * chi);
             const C rr = C(p.rho_ref);
-            const C rs = (C(1) + m.dr + C(0.5) * chi * rr) * h;
+            const C drs = (m.dr + C(0.5) * chi * C(p.rho_ref_m1)) * h;  // rho* - 1
+            const C rs = C(1) + drs;
             const C jsx = (m.jx + C(0.5) * chi * rr * C(p.u_ref[0])) * h;
             const C jsy = (m.jy + C(0.5) * chi * rr * C(p.u_ref[1])) * h;
             const C jsz = (m.jz + C(0.5) * chi * rr * C(p.u_ref[2])) * h;
             const C inv = C(1) / rs;
             const C ux = jsx * inv, uy = jsy * inv, uz = L::D == 3 ? jsz * inv : C(0);
-            const Sym2<C> pn = pi_neq<C>(m, rs, ux, uy, uz, L::D);
-            add_eq<C>(k, C(1) - chi, rs, ux, uy, uz);
-            add_eq<C>(k, chi, rr, C(p.u_ref[0]), C(p.u_ref[1]), L::D == 3 ? C(p.u_ref[2]) : C(0));
+            const Sym2<C> pn = pi_neq<C>(m, drs, rs, ux, uy, uz, L::D);
+            add_eq<C>(k, C(1) - chi, drs, rs, ux, uy, uz);
+            add_eq<C>(k, chi, C(p.rho_ref_m1), rr, C(p.u_ref[0]), C(p.u_ref[1]), L::D == 3 ? C(p.u_ref[2]) : C(0));
             add_neq<C>(k, om, ux, uy, uz, pn);
         } else {
             const C rho = C(1) + m.dr;
             const C inv = C(1) / rho;
             const C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
-            const Sym2<C> pn = pi_neq<C>(m, rho, ux, uy, uz, L::D);
-            add_eq<C>(k, C(1), rho, ux, uy, uz);
+            const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
+            add_eq<C>(k, C(1), m.dr, rho, ux, uy, uz);
             add_neq<C>(k, om, ux, uy, uz, pn);
         }
     }

@@ -62,6 +62,8 @@ _sig("lbm_moments", [_h, _dp, _dp, _dp])
 _sig("lbm_reduce", [_h, _dp, _dp])
 _sig("lbm_probe", [_h, C.c_int, _i64p, _dp])
 _sig("lbm_sync", [_h])
+_sig("lbm_set_launch", [_h, C.c_int, C.c_int])
+_sig("lbm_get_launch", [_h, _ip, _ip])
 _sig("lbm_info", [_h, _i64p, _i64p, _dp, _dp])
 _sig("lbm_save", [_h, C.c_char_p])
 _sig("lbm_load", [_h, C.c_char_p])
@@ -70,7 +72,7 @@ EXPORTED = [
     "lbm_lattice_table", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_geometry",
     "lbm_set_boundary", "lbm_set_inlet_noise", "lbm_set_sponge", "lbm_set_state",
     "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_moments", "lbm_reduce",
-    "lbm_probe", "lbm_sync", "lbm_info", "lbm_save", "lbm_load",
+    "lbm_probe", "lbm_sync", "lbm_info", "lbm_save", "lbm_load", "lbm_set_launch", "lbm_get_launch",
 ]
 
 
@@ -187,6 +189,16 @@ def lbm_probe(h, cells) -> np.ndarray:
     out = np.zeros(len(c))
     _check(_lib.lbm_probe(h, len(c), c.ctypes.data_as(_i64p), _d(out)), h)
     return out
+
+
+def lbm_set_launch(h, block: int = 0, cells_per_thread: int = 0):
+    return _check(_lib.lbm_set_launch(h, int(block), int(cells_per_thread)), h)
+
+
+def lbm_get_launch(h):
+    b, v = C.c_int(), C.c_int()
+    _check(_lib.lbm_get_launch(h, C.byref(b), C.byref(v)), h)
+    return b.value, v.value
 
 
 def lbm_sync(h):

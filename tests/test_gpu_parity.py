@@ -301,3 +301,59 @@ def test_full_size_round_jet_sampled_cells(prec):
     g = np.abs(ref - w[None, :]).max()
     tol = 1e-5 * np.abs(ref).max() if prec == "fp32" else 2 * 2.0 ** -10 * g + 1e-7
     assert err <= tol, (err, tol)
+
+
+def _open_box(lattice, n, seed):
+    """Box without a mask: velocity inflow (profile + noise) on -x, outflow on
+    +x, open or periodic y/z, sponges; random off-equilibrium state."""
+    c = Case("open", lattice, n, 0.56)
+    nf = n[1] * n[2]
+    prof = np.zeros((nf, 3))
+    prof[:, 0] = 0.05 * (0.5 + np.random.default_rng(seed).random(nf))
+    c.faces = {0: (VELOCITY, (0, 0, 0), prof), 1: (OUTFLOW, (0, 0, 0), None)}
+    c.sponges = {1: (5, 0.8)}
+    if lattice == D3Q19:
+        c.faces[2] = (OUTFLOW, (0, 0, 0), None)
+        c.faces[3] = (VELOCITY, (0.01, -0.02, 0.0), None)
+        c.sponges[4] = (3, 0.5)
+    else:
+        c.faces[2] = (VELOCITY, (0.0, 0.01, 0.0), None)
+        c.faces[3] = (OUTFLOW, (0, 0, 0), None)
+    c.noise = (9, 0.05)
+    c.rho_ref, c.u_ref = 1.0, (0.01, 0.0, 0.0)
+    return with_random_state(c, seed=seed, spread=0.08)
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
+def test_launch_shapes_match_oracle(lattice, prec):
+    """Scalar and vectorised kernels, several block sizes, partial warps
+    (nx/V not a multiple of 32), periodic and open x: all equal the oracle."""
+    from paper_1710_02065_gb300 import lbm
+    _, _, _, w, _ = oracle.lattice(lattice)
+    vecs = {"fp64": [1, 2], "fp32": [1, 2, 4], "fp16": [1, 4], "bf16": [1, 4]}[prec]
+    sizes = [(40, 12, 1), (136, 7, 1)] if lattice == D2Q9 else [(24, 10, 6), (136, 5, 4)]
+    for n in sizes:
+        c = _open_box(lattice, n, seed=n[0])
+        P, f = to_oracle(c)
+        ref = P.run(f, 3)
+        tol = _pop_tol(prec, ref, w, 3)
+        for vec in vecs:
+            for block in (32, 128, 256):
+                s = to_gpu(c, PRECS[prec])
+                lbm.lbm_set_launch(s.h, block, vec)
+                assert lbm.lbm_get_launch(s.h) == (block, vec)
+                s.step(3)
+                err = np.abs(s.populations() - ref).max()
+                assert err <= tol, (n, vec, block, err)
+                s.close()
+        # periodic x (vectorised kernel wraps through lane 0 / lane 31 loads)
+        cp = with_random_state(Case("periodic", lattice, n, 0.7), seed=3)
+        P, f = to_oracle(cp)
+        ref = P.run(f, 2)
+        for vec in vecs:
+            s = to_gpu(cp, PRECS[prec])
+            lbm.lbm_set_launch(s.h, 64, vec)
+            s.step(2)
+            assert np.abs(s.populations() - ref).max() <= _pop_tol(prec, ref, w, 2)
+            s.close()
