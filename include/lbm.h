@@ -133,7 +133,7 @@ const char *lbm_last_error(lbm_handle h);
  * walls): a population that would stream out of a solid cell is replaced by
  * the receiving cell's own post-collision population in the opposite
  * direction.  Solid and fixed cells keep their stored populations unchanged;
- * fixed cells are streamed from like fluid cells.  lbm_reduce skips solid
+ * fixed cells are streamed from like fluid cells.  lbm_reduce counts fluid
  * cells only.
  */
 int lbm_set_geometry(lbm_handle h, const uint8_t *cell_type);
@@ -212,7 +212,7 @@ int lbm_step(lbm_handle h, int64_t n);
 int lbm_moments(lbm_handle h, double *rho, double *u, double *pi_neq);
 
 /*
- * lbm_reduce -- FP64 totals over fluid cells: *mass = sum rho,
+ * lbm_reduce -- FP64 totals over fluid cells of level 0: *mass = sum rho,
  * momentum[0..2] = sum rho u.  Returns LBM_EUNSTABLE if any population is
  * non-finite (the totals are still written).
  */
@@ -232,7 +232,7 @@ int lbm_probe(lbm_handle h, int n, const int64_t *cells, double *p_prime);
  *                      for the default (128)
  *   cells_per_thread : 1 = one cell per thread (the general kernel); 2 or 4 =
  *                      vectorised kernel with that many consecutive x cells per
- *                      thread (FP64: 2; FP32: 2 or 4; FP16/BF16: 4); 0 = default
+ *                      thread (FP64: 2; FP32, FP16, BF16: 2 or 4); 0 = default
  *                      (4, FP64 2).  The vectorised kernel is used only when
  *                      there is no cell-type mask and nx is a multiple of it;
  *                      otherwise the general kernel runs.
@@ -254,6 +254,39 @@ int lbm_sync(lbm_handle h);
  */
 int lbm_info(lbm_handle h, int64_t *step, int64_t *launches, double *bytes_per_cell,
              double *tau);
+
+/*
+ * Two-level grid (Sec. II.B, multi-domain 2:1 refinement; D2Q9).
+ *
+ * lbm_add_refinement_patch -- add a fine level over the coarse nodes
+ * origin[0]..origin[0]+extent[0], origin[1]..origin[1]+extent[1] (extent >= 4,
+ * at least 2 coarse cells from every face).  The fine level has
+ * (2 extent[0] + 1) x (2 extent[1] + 1) nodes, dx_f = dx_c / 2, two fine
+ * steps per coarse step (Eq. convective), tau_f = 2 tau_c - 1/2 (same
+ * physical viscosity), starts at rest.  Coupling per coarse step: the fine
+ * boundary ring is rebuilt from coarse rho, u, Pi^neq interpolated in space
+ * (copy at coincident nodes, 4-point cubic at mid nodes) and linearly in time
+ * (t + 1/2, t + 1), Eq. couplingFC; the first ring of covered coarse nodes is
+ * rebuilt from the coincident fine node's rho, u and its 3 x 3 full-weighted
+ * (1,2,1)x(1,2,1)/16 Pi^neq, Eq. couplingCF.  f^neq is rescaled by
+ * tau_f / (2 tau_c) coarse -> fine and 2 tau_c / tau_f fine -> coarse (the
+ * leading-order Chapman-Enskog scaling of Sec. II.B).  Deeper covered coarse
+ * cells are frozen.  Solids of level 1 must stay 2 fine cells inside the ring.
+ * At most one patch per handle.
+ *
+ * Level-indexed variants (level 0 = coarse, the plain functions; level 1 =
+ * fine): extents and tau of a level; geometry (fine cell types, the ring is
+ * managed by the library); initial state and populations (set_*_level does
+ * not touch the other level; setting level 0 also refreshes the interface
+ * moments); populations and moments of the stored field.
+ */
+int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const int extent[3]);
+int lbm_level_info(lbm_handle h, int level, int extents[3], double *tau);
+int lbm_set_geometry_level(lbm_handle h, int level, const uint8_t *cell_type);
+int lbm_set_state_level(lbm_handle h, int level, const double *rho, const double *u);
+int lbm_set_populations_level(lbm_handle h, int level, const double *f);
+int lbm_get_populations_level(lbm_handle h, int level, double *f);
+int lbm_moments_level(lbm_handle h, int level, double *rho, double *u, double *pi_neq);
 
 /*
  * lbm_save / lbm_load -- write / read the stored field and step counter to a

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(int64_t N, const S *__rest
     double acc[RED_FIELDS] = {0, 0, 0, 0, 0, 0};
     for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < N;
          cell += (int64_t)gridDim.x * blockDim.x) {
-        if (solid && solid[cell] == 1) continue;
+        if (solid && solid[cell]) continue;  // fluid cells only
         double g[L::Q];
         load_cell_fp64<L, S>(f, N, cell, g);
         bool finite = true;

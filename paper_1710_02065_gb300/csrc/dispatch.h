@@ -18,7 +18,7 @@ cudaError_t step_d3q19(int precision, const StepParams &p, const void *fin, void
 namespace rr {
 
 // Vectorised kernel (no cell-type mask, nx % vec == 0).  Supported (precision,
-// vec): FP64 2; FP32 2, 4; FP16 4; BF16 4.
+// vec): FP64 2; FP32 2, 4; FP16 2, 4; BF16 2, 4.
 cudaError_t stepvec_d2q9(int precision, int vec, const StepParams &p, const void *fin, void *fout,
                          int block, cudaStream_t st);
 cudaError_t stepvec_d3q19(int precision, int vec, const StepParams &p, const void *fin, void *fout,
@@ -31,7 +31,7 @@ inline bool vec_supported(int precision, int vec)
     case PREC_FP64: return vec == 2;
     case PREC_FP32: return vec == 2 || vec == 4;
     case PREC_FP16:
-    case PREC_BF16: return vec == 4;
+    case PREC_BF16: return vec == 2 || vec == 4;
     }
     return false;
 }

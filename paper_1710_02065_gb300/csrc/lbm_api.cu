@@ -11,9 +11,24 @@
 #include "lbm.h"
 #include "aux_kernels.cuh"
 #include "dispatch.h"
+#include "refine.cuh"
 #include "step.cuh"
 
 using namespace rr;
+
+// The fine level of a two-level grid (Sec. II.B)
+struct FineLevel {
+    int n[3] = {1, 1, 1};
+    int64_t ncell = 0;
+    double tau = 0.0;
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint8_t *mask_d = nullptr;           // ring fixed + user solids
+    std::vector<uint8_t> user_mask;      // user solids (host copy)
+    RefineGeom geom{};
+    double *M[2] = {nullptr, nullptr};   // coarse line moments at t and t + 1
+    int mcur = 0;
+};
 
 struct lbm_ctx {
     int lattice = 0, q = 0, d = 0, prec = 0;
@@ -39,8 +54,29 @@ struct lbm_ctx {
     int vec = 0;    // cells per thread; 0: automatic, 1: scalar kernel
     double *red_d = nullptr;  // reduction partials + result
     int red_blocks = 0;
+    std::vector<uint8_t> user_mask;  // caller's cell types (host copy); empty: none
+    FineLevel *fine = nullptr;       // two-level grid, or null
     std::string err;
 };
+
+// View of one level's storage, so state and diagnostics work on either level
+struct GridRef {
+    int n[3];
+    int64_t ncell;
+    void **f;
+    int *cur;
+    const uint8_t *mask;
+};
+
+static GridRef coarse_ref(lbm_ctx *h)
+{
+    return GridRef{{h->n[0], h->n[1], h->n[2]}, h->ncell, h->f, &h->cur, h->solid_d};
+}
+static GridRef fine_ref(lbm_ctx *h)
+{
+    FineLevel *F = h->fine;
+    return GridRef{{F->n[0], F->n[1], F->n[2]}, F->ncell, F->f, &F->cur, F->mask_d};
+}
 
 static thread_local std::string g_create_err;
 
@@ -203,6 +239,14 @@ static void release(lbm_ctx *h)
     for (int k = 0; k < 6; ++k)
         if (h->prof_d[k]) cudaFree(h->prof_d[k]);
     if (h->red_d) cudaFree(h->red_d);
+    if (h->fine) {
+        for (int k = 0; k < 2; ++k) {
+            if (h->fine->f[k]) cudaFree(h->fine->f[k]);
+            if (h->fine->M[k]) cudaFree(h->fine->M[k]);
+        }
+        if (h->fine->mask_d) cudaFree(h->fine->mask_d);
+        delete h->fine;
+    }
     delete h;
 }
 
@@ -283,21 +327,63 @@ extern "C" const char *lbm_last_error(lbm_handle h)
 // ---------------------------------------------------------------------------
 // Configuration
 // ---------------------------------------------------------------------------
-extern "C" int lbm_set_geometry(lbm_handle h, const uint8_t *cell_type)
+// Upload the coarse mask: the caller's cell types, plus the covered patch
+// interior as fixed cells when a fine level exists.
+static int upload_coarse_mask(lbm_ctx *h)
 {
-    CHECK_HANDLE(h);
-    if (!cell_type) {
+    const bool patch = h->fine != nullptr;
+    if (h->user_mask.empty() && !patch) {
         if (h->solid_d) cudaFree(h->solid_d);
         h->solid_d = nullptr;
         return LBM_OK;
     }
-    for (int64_t c = 0; c < h->ncell; ++c)
-        if (cell_type[c] > LBM_CELL_FIXED)
-            return fail(h, LBM_EINVAL, "cell_type[%lld] = %d is not a cell type", (long long)c, cell_type[c]);
+    std::vector<uint8_t> m(h->user_mask);
+    if (m.empty()) m.assign((size_t)h->ncell, (uint8_t)LBM_CELL_FLUID);
+    if (patch) {
+        const RefineGeom &g = h->fine->geom;
+        for (int y = g.Y0 + 1; y < g.Y0 + g.Hc; ++y)
+            for (int x = g.X0 + 1; x < g.X0 + g.Wc; ++x) m[(size_t)x + (size_t)h->n[0] * y] = LBM_CELL_FIXED;
+    }
     if (!h->solid_d) CUDA_TRY(h, cudaMalloc(&h->solid_d, (size_t)h->ncell));
-    CUDA_TRY(h, cudaMemcpyAsync(h->solid_d, cell_type, (size_t)h->ncell, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->solid_d, m.data(), (size_t)h->ncell, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
+}
+
+static int upload_fine_mask(lbm_ctx *h)
+{
+    FineLevel *F = h->fine;
+    std::vector<uint8_t> m(F->user_mask);
+    if (m.empty()) m.assign((size_t)F->ncell, (uint8_t)LBM_CELL_FLUID);
+    for (int j = 0; j < F->n[1]; ++j)
+        for (int i = 0; i < F->n[0]; ++i)
+            if (i == 0 || j == 0 || i == F->n[0] - 1 || j == F->n[1] - 1)
+                m[(size_t)i + (size_t)F->n[0] * j] = LBM_CELL_FIXED;
+    if (!F->mask_d) CUDA_TRY(h, cudaMalloc(&F->mask_d, (size_t)F->ncell));
+    CUDA_TRY(h, cudaMemcpyAsync(F->mask_d, m.data(), (size_t)F->ncell, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+static int check_cell_types(lbm_ctx *h, const uint8_t *t, int64_t n)
+{
+    for (int64_t c = 0; c < n; ++c)
+        if (t[c] > LBM_CELL_FIXED)
+            return fail(h, LBM_EINVAL, "cell_type[%lld] = %d is not a cell type", (long long)c, t[c]);
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_geometry(lbm_handle h, const uint8_t *cell_type)
+{
+    CHECK_HANDLE(h);
+    if (cell_type) {
+        int rc = check_cell_types(h, cell_type, h->ncell);
+        if (rc != LBM_OK) return rc;
+        h->user_mask.assign(cell_type, cell_type + h->ncell);
+    } else {
+        h->user_mask.clear();
+    }
+    return upload_coarse_mask(h);
 }
 
 static int64_t face_cells(const lbm_ctx *h, int face)
@@ -385,11 +471,10 @@ extern "C" int lbm_set_sponge(lbm_handle h, int face, int width, double chi_max,
 // ---------------------------------------------------------------------------
 // State
 // ---------------------------------------------------------------------------
-extern "C" int lbm_set_state(lbm_handle h, const double *rho, const double *u)
+static int set_state_grid(lbm_ctx *h, const GridRef &g, const double *rho, const double *u)
 {
-    CHECK_HANDLE(h);
     if (!rho || !u) return fail(h, LBM_EINVAL, "rho and u are required");
-    const int64_t N = h->ncell;
+    const int64_t N = g.ncell;
     for (int64_t c = 0; c < N; ++c) {
         if (!(rho[c] > 0.0) || !std::isfinite(rho[c]))
             return fail(h, LBM_EINVAL, "rho[%lld] = %g must be finite and > 0", (long long)c, rho[c]);
@@ -400,55 +485,78 @@ extern "C" int lbm_set_state(lbm_handle h, const double *rho, const double *u)
     cudaError_t e = cudaMemcpyAsync(buf, rho, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(buf + N, u, sizeof(double) * 3 * (size_t)N, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = dispatch<InitEq>(h->lattice, h->prec, h->stream, N, buf, buf + N, h->f[0], h->f[1]);
+    if (e == cudaSuccess) e = dispatch<InitEq>(h->lattice, h->prec, h->stream, N, buf, buf + N, g.f[0], g.f[1]);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(buf);
-    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "lbm_set_state: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "set state: %s", cudaGetErrorString(e));
     h->launches += 1;
-    h->cur = 0;
-    h->step = 0;
+    *g.cur = 0;
     return LBM_OK;
 }
 
-extern "C" int lbm_set_populations(lbm_handle h, const double *f)
+static int set_pops_grid(lbm_ctx *h, const GridRef &g, const double *f)
 {
-    CHECK_HANDLE(h);
     if (!f) return fail(h, LBM_EINVAL, "f is null");
-    const int64_t N = h->ncell;
+    const int64_t N = g.ncell;
     double *buf = nullptr;
     CUDA_TRY(h, cudaMalloc(&buf, sizeof(double) * (size_t)N));
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < h->q && e == cudaSuccess; ++i) {
         e = cudaMemcpyAsync(buf, f + (size_t)i * N, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = dispatch<SetDir>(h->lattice, h->prec, h->stream, N, i, (const double *)buf, h->f[0], h->f[1]);
+        if (e == cudaSuccess) e = dispatch<SetDir>(h->lattice, h->prec, h->stream, N, i, (const double *)buf, g.f[0], g.f[1]);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         h->launches += 1;
     }
     cudaFree(buf);
-    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "lbm_set_populations: %s", cudaGetErrorString(e));
-    h->cur = 0;
-    h->step = 0;
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "set populations: %s", cudaGetErrorString(e));
+    *g.cur = 0;
     return LBM_OK;
 }
 
-extern "C" int lbm_get_populations(lbm_handle h, double *f)
+static int get_pops_grid(lbm_ctx *h, const GridRef &g, double *f)
 {
-    CHECK_HANDLE(h);
     if (!f) return fail(h, LBM_EINVAL, "f is null");
-    const int64_t N = h->ncell;
+    const int64_t N = g.ncell;
     double *buf = nullptr;
     CUDA_TRY(h, cudaMalloc(&buf, sizeof(double) * (size_t)N));
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < h->q && e == cudaSuccess; ++i) {
-        e = dispatch<GetDir>(h->lattice, h->prec, h->stream, N, i, (const void *)h->f[h->cur], buf);
+        e = dispatch<GetDir>(h->lattice, h->prec, h->stream, N, i, (const void *)g.f[*g.cur], buf);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(f + (size_t)i * N, buf, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         h->launches += 1;
     }
     cudaFree(buf);
-    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "lbm_get_populations: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "get populations: %s", cudaGetErrorString(e));
     return LBM_OK;
+}
+
+static int init_line_moments(lbm_ctx *h);
+static int moments_grid(lbm_ctx *h, const GridRef &g, double *rho, double *u, double *pi_neq);
+
+extern "C" int lbm_set_state(lbm_handle h, const double *rho, const double *u)
+{
+    CHECK_HANDLE(h);
+    int rc = set_state_grid(h, coarse_ref(h), rho, u);
+    if (rc != LBM_OK) return rc;
+    h->step = 0;
+    return h->fine ? init_line_moments(h) : LBM_OK;
+}
+
+extern "C" int lbm_set_populations(lbm_handle h, const double *f)
+{
+    CHECK_HANDLE(h);
+    int rc = set_pops_grid(h, coarse_ref(h), f);
+    if (rc != LBM_OK) return rc;
+    h->step = 0;
+    return h->fine ? init_line_moments(h) : LBM_OK;
+}
+
+extern "C" int lbm_get_populations(lbm_handle h, double *f)
+{
+    CHECK_HANDLE(h);
+    return get_pops_grid(h, coarse_ref(h), f);
 }
 
 // ---------------------------------------------------------------------------
@@ -485,6 +593,90 @@ static int build_params(lbm_ctx *h, StepParams &p)
     return LBM_OK;
 }
 
+// Launch one update of a grid: vectorised kernel when there is no mask and
+// the row length allows it, the general kernel otherwise.
+static cudaError_t launch_update(lbm_ctx *h, const StepParams &p, const void *fin, void *fout)
+{
+    int vec = h->vec == 0 ? vec_default(h->prec) : h->vec;
+    if (p.solid || vec == 1 || !vec_supported(h->prec, vec) || p.n[0] % vec != 0) vec = 1;
+    const int block = h->block > 0 ? h->block : 128;
+    h->launches += 1;
+    if (vec == 1)
+        return h->lattice == LBM_D2Q9 ? step_d2q9(h->prec, p, fin, fout, block, h->stream)
+                                      : step_d3q19(h->prec, p, fin, fout, block, h->stream);
+    return h->lattice == LBM_D2Q9 ? stepvec_d2q9(h->prec, vec, p, fin, fout, block, h->stream)
+                                  : stepvec_d3q19(h->prec, vec, p, fin, fout, block, h->stream);
+}
+
+// Step parameters of the fine level: periodic box, ring fixed, no sponge/inflow
+static void fine_params(lbm_ctx *h, StepParams &p)
+{
+    FineLevel *F = h->fine;
+    std::memset(&p, 0, sizeof p);
+    for (int a = 0; a < 3; ++a) {
+        p.n[a] = F->n[a];
+        p.periodic[a] = 1;
+    }
+    p.ncell = F->ncell;
+    for (int f = 0; f < 6; ++f) p.face_cells[f] = 1;
+    p.rho_ref = 1.0;
+    p.omega = 1.0 - 1.0 / F->tau;
+    p.solid = F->mask_d;
+}
+
+template <class S>
+static cudaError_t refine_kernels(lbm_ctx *h, int stage, int a_half)
+{
+    FineLevel *F = h->fine;
+    const RefineGeom &g = F->geom;
+    cudaStream_t st = h->stream;
+    switch (stage) {
+    case 0: {  // coarse line moments at t + 1 from the pre-step coarse field
+        const int n = line_count(g);
+        k_line_moments<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)h->f[h->cur], h->solid_d, 1, F->M[1 - F->mcur]);
+        break;
+    }
+    case 1: {  // fine ring at t + 1/2 (a_half = 1) or t + 1 (a_half = 0)
+        const int n = 2 * g.nfx + 2 * (g.nfy - 2);
+        k_fill_ring<S><<<grid1(n, 128), 128, 0, st>>>(g, F->M[F->mcur], F->M[1 - F->mcur], a_half ? 0.5 : 1.0,
+                                                       F->tau / (2.0 * h->tau), F->tau, (S *)F->f[F->cur]);
+        break;
+    }
+    case 2: {  // covered coarse ring from the fine field; pre-collision fine moments pulled from f(t + 1/2)
+        const int n = 2 * (g.Wc - 1) + 2 * (g.Hc - 3);
+        k_restrict<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)F->f[1 - F->cur], F->mask_d, 2.0 * h->tau / F->tau,
+                                                     h->tau, (S *)h->f[h->cur]);
+        break;
+    }
+    case 3: {  // line moments at t = 0: local moments of the stored coarse field
+        const int n = line_count(g);
+        k_line_moments<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)h->f[h->cur], h->solid_d, 0, F->M[F->mcur]);
+        break;
+    }
+    }
+    h->launches += 1;
+    return cudaGetLastError();
+}
+
+static cudaError_t refine_stage(lbm_ctx *h, int stage, int a_half = 0)
+{
+    switch (h->prec) {
+    case LBM_FP64: return refine_kernels<double>(h, stage, a_half);
+    case LBM_FP32: return refine_kernels<float>(h, stage, a_half);
+    case LBM_FP16_SHIFTED: return refine_kernels<__half>(h, stage, a_half);
+    case LBM_BF16_SHIFTED: return refine_kernels<__nv_bfloat16>(h, stage, a_half);
+    }
+    return cudaErrorInvalidValue;
+}
+
+static int init_line_moments(lbm_ctx *h)
+{
+    cudaError_t e = refine_stage(h, 3);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "interface moments: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
 extern "C" int lbm_step(lbm_handle h, int64_t n)
 {
     CHECK_HANDLE(h);
@@ -493,25 +685,171 @@ extern "C" int lbm_step(lbm_handle h, int64_t n)
     StepParams p;
     int rc = build_params(h, p);
     if (rc != LBM_OK) return rc;
-    int vec = h->vec == 0 ? vec_default(h->prec) : h->vec;
-    if (h->solid_d || vec == 1 || !vec_supported(h->prec, vec) || h->n[0] % vec != 0) vec = 1;
-    const int block = h->block > 0 ? h->block : (vec == 1 ? 128 : 128);
+    StepParams pf;
+    if (h->fine) fine_params(h, pf);
     for (int64_t t = 0; t < n; ++t) {
         p.step = h->step;
-        cudaError_t e;
-        if (vec == 1)
-            e = h->lattice == LBM_D2Q9 ? step_d2q9(h->prec, p, h->f[h->cur], h->f[1 - h->cur], block, h->stream)
-                                       : step_d3q19(h->prec, p, h->f[h->cur], h->f[1 - h->cur], block, h->stream);
-        else
-            e = h->lattice == LBM_D2Q9
-                    ? stepvec_d2q9(h->prec, vec, p, h->f[h->cur], h->f[1 - h->cur], block, h->stream)
-                    : stepvec_d3q19(h->prec, vec, p, h->f[h->cur], h->f[1 - h->cur], block, h->stream);
-        if (e != cudaSuccess) return fail(h, LBM_ECUDA, "stream-collide launch: %s", cudaGetErrorString(e));
-        h->cur = 1 - h->cur;
+        cudaError_t e = cudaSuccess;
+        if (h->fine) {
+            // one coarse step of the two-level grid (Sec. II.B):
+            // coarse line moments, coarse step, fine step, ring at t + 1/2,
+            // fine step, ring at t + 1, covered coarse ring from the fine grid
+            FineLevel *F = h->fine;
+            e = refine_stage(h, 0);
+            if (e == cudaSuccess) e = launch_update(h, p, h->f[h->cur], h->f[1 - h->cur]);
+            if (e == cudaSuccess) {
+                h->cur = 1 - h->cur;
+                pf.step = 2 * h->step;
+                e = launch_update(h, pf, F->f[F->cur], F->f[1 - F->cur]);
+            }
+            if (e == cudaSuccess) {
+                F->cur = 1 - F->cur;
+                e = refine_stage(h, 1, 1);
+            }
+            if (e == cudaSuccess) {
+                pf.step = 2 * h->step + 1;
+                e = launch_update(h, pf, F->f[F->cur], F->f[1 - F->cur]);
+            }
+            if (e == cudaSuccess) {
+                F->cur = 1 - F->cur;
+                e = refine_stage(h, 1, 0);
+            }
+            if (e == cudaSuccess) e = refine_stage(h, 2);
+            F->mcur = 1 - F->mcur;
+        } else {
+            e = launch_update(h, p, h->f[h->cur], h->f[1 - h->cur]);
+            h->cur = 1 - h->cur;
+        }
+        if (e != cudaSuccess) return fail(h, LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
         h->step += 1;
-        h->launches += 1;
     }
     return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Two-level grid
+// ---------------------------------------------------------------------------
+extern "C" int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const int extent[3])
+{
+    CHECK_HANDLE(h);
+    if (h->fine) return fail(h, LBM_EINVAL, "the handle already has a refinement patch");
+    if (h->lattice != LBM_D2Q9) return fail(h, LBM_EINVAL, "refinement patches are implemented for D2Q9");
+    if (!origin || !extent) return fail(h, LBM_EINVAL, "origin and extent are required");
+    const int X0 = origin[0], Y0 = origin[1], Wc = extent[0], Hc = extent[1];
+    if (Wc < 4 || Hc < 4) return fail(h, LBM_EINVAL, "patch extent must be >= 4 coarse cells per axis");
+    if (X0 < 2 || Y0 < 2 || X0 + Wc > h->n[0] - 3 || Y0 + Hc > h->n[1] - 3)
+        return fail(h, LBM_EINVAL, "patch must keep 2 coarse cells from every face");
+    FineLevel *F = new FineLevel();
+    F->n[0] = 2 * Wc + 1;
+    F->n[1] = 2 * Hc + 1;
+    F->n[2] = 1;
+    F->ncell = (int64_t)F->n[0] * F->n[1];
+    F->tau = 2.0 * h->tau - 0.5;
+    F->geom = RefineGeom{X0, Y0, Wc, Hc, h->n[0], h->n[1], F->n[0], F->n[1]};
+    const size_t bytes = (size_t)h->q * (size_t)F->ncell * h->elem;
+    const size_t mbytes = sizeof(double) * 6 * (size_t)line_count(F->geom);
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k)
+        ok = cudaMalloc(&F->f[k], bytes) == cudaSuccess && cudaMalloc(&F->M[k], mbytes) == cudaSuccess &&
+             cudaMemsetAsync(F->f[k], 0, bytes, h->stream) == cudaSuccess;
+    h->fine = F;
+    if (!ok) {
+        cudaGetLastError();
+        for (int k = 0; k < 2; ++k) {
+            if (F->f[k]) cudaFree(F->f[k]);
+            if (F->M[k]) cudaFree(F->M[k]);
+        }
+        delete F;
+        h->fine = nullptr;
+        return fail(h, LBM_ENOMEM, "allocating the fine level failed");
+    }
+    int rc = upload_fine_mask(h);
+    if (rc == LBM_OK) rc = upload_coarse_mask(h);
+    if (rc == LBM_OK) rc = init_line_moments(h);
+    return rc;
+}
+
+static int level_ref(lbm_ctx *h, int level, GridRef &g)
+{
+    if (level == 0) {
+        g = coarse_ref(h);
+        return LBM_OK;
+    }
+    if (level == 1 && h->fine) {
+        g = fine_ref(h);
+        return LBM_OK;
+    }
+    return fail(h, LBM_EINVAL, "no level %d", level);
+}
+
+extern "C" int lbm_level_info(lbm_handle h, int level, int extents[3], double *tau)
+{
+    CHECK_HANDLE(h);
+    GridRef g;
+    int rc = level_ref(h, level, g);
+    if (rc != LBM_OK) return rc;
+    if (extents)
+        for (int a = 0; a < 3; ++a) extents[a] = g.n[a];
+    if (tau) *tau = level == 0 ? h->tau : h->fine->tau;
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_geometry_level(lbm_handle h, int level, const uint8_t *cell_type)
+{
+    CHECK_HANDLE(h);
+    if (level == 0) return lbm_set_geometry(h, cell_type);
+    GridRef g;
+    int rc = level_ref(h, level, g);
+    if (rc != LBM_OK) return rc;
+    FineLevel *F = h->fine;
+    if (cell_type) {
+        rc = check_cell_types(h, cell_type, F->ncell);
+        if (rc != LBM_OK) return rc;
+        F->user_mask.assign(cell_type, cell_type + F->ncell);
+    } else {
+        F->user_mask.clear();
+    }
+    return upload_fine_mask(h);
+}
+
+extern "C" int lbm_set_state_level(lbm_handle h, int level, const double *rho, const double *u)
+{
+    CHECK_HANDLE(h);
+    if (level == 0) return lbm_set_state(h, rho, u);
+    GridRef g;
+    int rc = level_ref(h, level, g);
+    if (rc != LBM_OK) return rc;
+    h->step = 0;
+    return set_state_grid(h, g, rho, u);
+}
+
+extern "C" int lbm_set_populations_level(lbm_handle h, int level, const double *f)
+{
+    CHECK_HANDLE(h);
+    if (level == 0) return lbm_set_populations(h, f);
+    GridRef g;
+    int rc = level_ref(h, level, g);
+    if (rc != LBM_OK) return rc;
+    h->step = 0;
+    return set_pops_grid(h, g, f);
+}
+
+extern "C" int lbm_get_populations_level(lbm_handle h, int level, double *f)
+{
+    CHECK_HANDLE(h);
+    GridRef g;
+    int rc = level_ref(h, level, g);
+    if (rc != LBM_OK) return rc;
+    return get_pops_grid(h, g, f);
+}
+
+extern "C" int lbm_moments_level(lbm_handle h, int level, double *rho, double *u, double *pi_neq)
+{
+    CHECK_HANDLE(h);
+    GridRef g;
+    int rc = level_ref(h, level, g);
+    if (rc != LBM_OK) return rc;
+    return moments_grid(h, g, rho, u, pi_neq);
 }
 
 extern "C" int lbm_set_launch(lbm_handle h, int block, int cells_per_thread)
@@ -531,7 +869,7 @@ extern "C" int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread)
     CHECK_HANDLE(h);
     int vec = h->vec == 0 ? vec_default(h->prec) : h->vec;
     if (h->solid_d || vec == 1 || !vec_supported(h->prec, vec) || h->n[0] % vec != 0) vec = 1;
-    if (block) *block = h->block > 0 ? h->block : 128;
+    if (block) *block = h->block > 0 ? h->block : 128;  // level 0
     if (cells_per_thread) *cells_per_thread = vec;
     return LBM_OK;
 }
@@ -547,15 +885,14 @@ extern "C" int lbm_sync(lbm_handle h)
 // ---------------------------------------------------------------------------
 // Diagnostics
 // ---------------------------------------------------------------------------
-extern "C" int lbm_moments(lbm_handle h, double *rho, double *u, double *pi_neq)
+static int moments_grid(lbm_ctx *h, const GridRef &g, double *rho, double *u, double *pi_neq)
 {
-    CHECK_HANDLE(h);
     if (!rho && !u && !pi_neq) return LBM_OK;
-    const int64_t N = h->ncell;
+    const int64_t N = g.ncell;
     double *buf = nullptr;
     CUDA_TRY(h, cudaMalloc(&buf, sizeof(double) * 10 * (size_t)N));
     double *rd = buf, *ud = buf + N, *pd = buf + 4 * N;
-    cudaError_t e = dispatch<Moments>(h->lattice, h->prec, h->stream, N, (const void *)h->f[h->cur],
+    cudaError_t e = dispatch<Moments>(h->lattice, h->prec, h->stream, N, (const void *)g.f[*g.cur],
                                       rho ? rd : nullptr, u ? ud : nullptr, pi_neq ? pd : nullptr);
     if (e == cudaSuccess && rho)
         e = cudaMemcpyAsync(rho, rd, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, h->stream);
@@ -566,8 +903,14 @@ extern "C" int lbm_moments(lbm_handle h, double *rho, double *u, double *pi_neq)
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(buf);
     h->launches += 1;
-    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "lbm_moments: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "moments: %s", cudaGetErrorString(e));
     return LBM_OK;
+}
+
+extern "C" int lbm_moments(lbm_handle h, double *rho, double *u, double *pi_neq)
+{
+    CHECK_HANDLE(h);
+    return moments_grid(h, coarse_ref(h), rho, u, pi_neq);
 }
 
 extern "C" int lbm_reduce(lbm_handle h, double *mass, double momentum[3])

@@ -131,6 +131,16 @@ struct Store<__nv_bfloat16> {
     __device__ static __nv_bfloat16 from(double v) { return __double2bfloat16(v); }
 };
 
+// compute type a storage format is written from
+template <class S>
+struct StoreC {
+    using C = float;
+};
+template <>
+struct StoreC<double> {
+    using C = double;
+};
+
 // ---------------------------------------------------------------------------
 // Moments of shifted populations g_i = f_i - w_i:
 //   dr = rho - 1, j = rho u, s_ab = Pi_ab - c_s^2 delta_ab   (Eq. moments)
@@ -284,6 +294,78 @@ __device__ __forceinline__ Sym2<C> pi_neq(const Mom<C> &m, C dr, C rho, C ux, C 
         p.zz = p.xz = p.yz = C(0);
     }
     return p;
+}
+
+// ---------------------------------------------------------------------------
+// Moments from direction pairs: s = g_i + g_opp (even), d = g_i - g_opp (odd)
+// ---------------------------------------------------------------------------
+template <class L, class C>
+__device__ __forceinline__ Mom<C> moments_pairs(const C *g)
+{
+    Mom<C> m{};
+    m.dr = g[0];
+#pragma unroll
+    for (int i = 1; i <= L::HALF; ++i) {
+        const C s = g[i] + g[i + L::HALF], d = g[i] - g[i + L::HALF];
+        const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
+        m.dr += s;
+        if (x) m.jx += x > 0 ? d : -d;
+        if (y) m.jy += y > 0 ? d : -d;
+        if (z) m.jz += z > 0 ? d : -d;
+        if (x) m.sxx += s;
+        if (y) m.syy += s;
+        if (z) m.szz += s;
+        if (x && y) m.sxy += x * y > 0 ? s : -s;
+        if (x && z) m.sxz += x * z > 0 ? s : -s;
+        if (y && z) m.syz += y * z > 0 ? s : -s;
+    }
+    return m;
+}
+
+// Even (E) and odd (O) parts of the rebuilt population of direction i (1 <= i <= HALF)
+template <class L, class C>
+__device__ __forceinline__ void rebuild_pair(const Coef<C> &k, int i, C &even, C &odd)
+{
+    constexpr double cs2 = 1.0 / 3.0;
+    const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
+    C f2 = C(x * x - cs2) * k.xx + C(y * y - cs2) * k.yy;
+    if (L::D == 3) f2 += C(z * z - cs2) * k.zz;
+    if (x * y) f2 += C(2 * x * y) * k.xy;
+    if (L::D == 3 && x * z) f2 += C(2 * x * z) * k.xz;
+    if (L::D == 3 && y * z) f2 += C(2 * y * z) * k.yz;
+    even = k.a0 + C(4.5) * f2;
+    C f1 = C(0);
+    if (x) f1 += x > 0 ? k.a1x : -k.a1x;
+    if (y) f1 += y > 0 ? k.a1y : -k.a1y;
+    if (z) f1 += z > 0 ? k.a1z : -k.a1z;
+    C o = C(3) * f1;
+    const double hxxy = (x * x - cs2) * y, hxyy = (y * y - cs2) * x;
+    if (L::D == 2) {
+        if (hxxy != 0.0) o += C(13.5 * hxxy) * k.xxy;
+        if (hxyy != 0.0) o += C(13.5 * hxyy) * k.xyy;
+    } else {
+        const double hyzz = (z * z - cs2) * y, hxzz = (z * z - cs2) * x;
+        const double hyyz = (y * y - cs2) * z, hxxz = (x * x - cs2) * z;
+        const double p1 = hxxy + hyzz, m1 = hxxy - hyzz;
+        const double p2 = hxzz + hxyy, m2 = hxzz - hxyy;
+        const double p3 = hyyz + hxxz, m3 = hyyz - hxxz;
+        if (p1 != 0.0) o += C(13.5 * p1) * (k.xxy + k.yzz);
+        if (m1 != 0.0) o += C(4.5 * m1) * (k.xxy - k.yzz);
+        if (p2 != 0.0) o += C(13.5 * p2) * (k.xzz + k.xyy);
+        if (m2 != 0.0) o += C(4.5 * m2) * (k.xzz - k.xyy);
+        if (p3 != 0.0) o += C(13.5 * p3) * (k.yyz + k.xxz);
+        if (m3 != 0.0) o += C(4.5 * m3) * (k.yyz - k.xxz);
+    }
+    odd = o;
+}
+
+// Rest population: w_0 (a0 - c_s^2 trace(A2) / (2 c_s^4))
+template <class L, class C>
+__device__ __forceinline__ C rebuild_rest(const Coef<C> &k)
+{
+    C tr = k.xx + k.yy;
+    if (L::D == 3) tr += k.zz;
+    return C(weight<L>(0)) * (k.a0 - C(1.5) * tr);
 }
 
 // splitmix64 (Steele, Lea and Flood 2014): counter-based uniform in [0, 1)

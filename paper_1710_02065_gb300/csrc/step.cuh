@@ -17,6 +17,10 @@
 //     f* = (1 - chi) feqH(rho*, u*) + chi feqH(rho_ref, u_ref)
 //          + (1 - 1/tau) fneqH(u*, Pi^neq about rho*, u*)
 //   * bulk: f* = feqH(rho, u) + (1 - 1/tau) fneqH(u, Pi^neq)
+//
+// Populations are rebuilt by opposite pairs: the even Hermite part E = a0 +
+// H2:A2 / (2 c_s^4) is shared and the odd part O = xi.a1 / c_s^2 + T3(A3)
+// changes sign, f_i = w (E + O), f_opp = w (E - O).
 #pragma once
 
 #include "rr.cuh"
@@ -44,6 +48,114 @@ struct StepParams {
     int64_t step;
 };
 
+// ---------------------------------------------------------------------------
+// Sponge strength chi = chi_max sigma(d), maximum over the layers (Sec. II.C).
+// The y/z layers are uniform along a row; only the x layers vary along it.
+// ---------------------------------------------------------------------------
+template <class L, class C>
+__device__ __forceinline__ C chi_face(const StepParams &p, int f, int coord)
+{
+    const int W = p.sponge_w[f];
+    if (W <= 0) return C(0);
+    const int a = f >> 1;
+    const int d = (f & 1) ? coord - (p.n[a] - W) : W - 1 - coord;
+    if (d < 0) return C(0);
+    return C(p.sponge_chi[f]) * sigma<C>(C(d), C(W));
+}
+
+template <class L, class C>
+__device__ __forceinline__ C chi_row(const StepParams &p, int y, int z)
+{
+    C chi = C(0);
+    if (!p.any_sponge) return chi;
+    C v = chi_face<L, C>(p, 2, y);
+    chi = v > chi ? v : chi;
+    v = chi_face<L, C>(p, 3, y);
+    chi = v > chi ? v : chi;
+    if (L::D == 3) {
+        v = chi_face<L, C>(p, 4, z);
+        chi = v > chi ? v : chi;
+        v = chi_face<L, C>(p, 5, z);
+        chi = v > chi ? v : chi;
+    }
+    return chi;
+}
+
+template <class L, class C>
+__device__ __forceinline__ C chi_cell(const StepParams &p, C row, int x)
+{
+    if (!p.any_sponge) return row;
+    C v = chi_face<L, C>(p, 0, x);
+    row = v > row ? v : row;
+    v = chi_face<L, C>(p, 1, x);
+    return v > row ? v : row;
+}
+
+// ---------------------------------------------------------------------------
+// Collision coefficients of one cell: velocity node, sponge cell or bulk.
+// ---------------------------------------------------------------------------
+template <class L, class C>
+__device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const Mom<C> &m, C chi, int cx,
+                                                     int cy, int cz, int inlet)
+{
+    const C om = C(p.omega);
+    Coef<C> k{};
+    if (inlet >= 0) {
+        // velocity node: rho, Pi^neq from the streamed neighbour, prescribed u (+ noise)
+        const C rho = C(1) + m.dr;
+        const C inv = C(1) / rho;
+        const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, m.jx * inv, m.jy * inv, m.jz * inv, L::D);
+        const int a = inlet >> 1;
+        const int t0c = a == 0 ? cy : cx, t1c = a == 2 ? cy : cz;
+        const int n0 = a == 0 ? p.n[1] : p.n[0];
+        const int64_t kf = t0c + (int64_t)n0 * t1c;
+        double ub[3];
+        const double *prof = p.u_profile[inlet];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) ub[b] = prof ? prof[3 * kf + b] : p.u_face[inlet][b];
+        if (p.noise_amp > 0.0) {
+            const double mag = sqrt(ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+            if (mag > 0.0) {
+                const uint64_t base =
+                    (p.noise_seed << 32) + ((uint64_t)p.step * (uint64_t)p.face_cells[inlet] + (uint64_t)kf) * 3u;
+#pragma unroll
+                for (int b = 0; b < L::D; ++b) ub[b] += p.noise_amp * mag * (2.0 * u01(base + b) - 1.0);
+            }
+        }
+        const C ux = C(ub[0]), uy = C(ub[1]), uz = L::D == 3 ? C(ub[2]) : C(0);
+        add_eq<C>(k, C(1), m.dr, rho, ux, uy, uz);
+        add_neq<C>(k, om, ux, uy, uz, pn);
+        return k;
+    }
+    if (chi > C(0)) {
+        // sponge: damped moments rho*, rho* u* (n = m = 1/2), then
+        // f* = (1 - chi) feqH(rho*, u*) + chi feqH(rho_ref, u_ref) + (1 - 1/tau) fneqH
+        const C h = C(1) / (C(1) + C(0.5) * chi);
+        const C rr = C(p.rho_ref);
+        const C drs = (m.dr + C(0.5) * chi * C(p.rho_ref_m1)) * h;  // rho* - 1
+        const C rs = C(1) + drs;
+        const C inv = C(1) / rs;
+        const C ux = (m.jx + C(0.5) * chi * rr * C(p.u_ref[0])) * h * inv;
+        const C uy = (m.jy + C(0.5) * chi * rr * C(p.u_ref[1])) * h * inv;
+        const C uz = L::D == 3 ? (m.jz + C(0.5) * chi * rr * C(p.u_ref[2])) * h * inv : C(0);
+        const Sym2<C> pn = pi_neq<C>(m, drs, rs, ux, uy, uz, L::D);
+        add_eq<C>(k, C(1) - chi, drs, rs, ux, uy, uz);
+        add_eq<C>(k, chi, C(p.rho_ref_m1), rr, C(p.u_ref[0]), C(p.u_ref[1]), L::D == 3 ? C(p.u_ref[2]) : C(0));
+        add_neq<C>(k, om, ux, uy, uz, pn);
+        return k;
+    }
+    const C rho = C(1) + m.dr;
+    const C inv = C(1) / rho;
+    const C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
+    const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
+    add_eq<C>(k, C(1), m.dr, rho, ux, uy, uz);
+    add_neq<C>(k, om, ux, uy, uz, pn);
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// General kernel: one thread per cell, optional cell-type mask.
+// ---------------------------------------------------------------------------
 template <class L, class S, class C>
 __global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ StepParams p,
                                                          const S *__restrict__ fin,
@@ -60,35 +172,32 @@ __global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ 
     if (solid && solid[cell]) return;  // solid (1) and fixed (2) cells keep their populations
 
     // ---- boundary role and the node whose streamed populations are used
-    int c[3] = {x, y, z};
-    int s[3] = {x, y, z};
-    int inlet = -1;
-#pragma unroll
-    for (int a = 0; a < L::D; ++a) {
-        if (!p.periodic[a]) {
-            if (c[a] == 0) {
-                s[a] = 1;
-                if (p.kind[2 * a] == BC_VELOCITY && inlet < 0) inlet = 2 * a;
-            }
-            if (c[a] == p.n[a] - 1) {
-                s[a] = p.n[a] - 2;
-                if (p.kind[2 * a + 1] == BC_VELOCITY && inlet < 0) inlet = 2 * a + 1;
-            }
-        }
+    int sx = x, sy = y, sz = z, inlet = -1;
+    if (!p.periodic[0]) {
+        if (x == 0) { sx = 1; if (p.kind[0] == BC_VELOCITY) inlet = 0; }
+        if (x == nx - 1) { sx = nx - 2; if (p.kind[1] == BC_VELOCITY && inlet < 0) inlet = 1; }
+    }
+    if (!p.periodic[1]) {
+        if (y == 0) { sy = 1; if (p.kind[2] == BC_VELOCITY && inlet < 0) inlet = 2; }
+        if (y == ny - 1) { sy = ny - 2; if (p.kind[3] == BC_VELOCITY && inlet < 0) inlet = 3; }
+    }
+    if (L::D == 3 && !p.periodic[2]) {
+        if (z == 0) { sz = 1; if (p.kind[4] == BC_VELOCITY && inlet < 0) inlet = 4; }
+        if (z == nz - 1) { sz = nz - 2; if (p.kind[5] == BC_VELOCITY && inlet < 0) inlet = 5; }
     }
     // neighbour coordinates of s with wrap-around on periodic axes
-    const int xm = s[0] == 0 ? nx - 1 : s[0] - 1, xp = s[0] == nx - 1 ? 0 : s[0] + 1;
-    const int ym = s[1] == 0 ? ny - 1 : s[1] - 1, yp = s[1] == ny - 1 ? 0 : s[1] + 1;
-    const int zm = s[2] == 0 ? nz - 1 : s[2] - 1, zp = s[2] == nz - 1 ? 0 : s[2] + 1;
-    const int64_t scell = s[0] + (int64_t)nx * s[1] + nxy * s[2];
+    const int xm = sx == 0 ? nx - 1 : sx - 1, xp = sx == nx - 1 ? 0 : sx + 1;
+    const int ym = sy == 0 ? ny - 1 : sy - 1, yp = sy == ny - 1 ? 0 : sy + 1;
+    const int zm = sz == 0 ? nz - 1 : sz - 1, zp = sz == nz - 1 ? 0 : sz + 1;
+    const int64_t scell = sx + (int64_t)nx * sy + nxy * sz;
 
     // ---- streaming (pull) with halfway bounce-back
     C g[L::Q];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        const int X = L::cx(i) > 0 ? xm : (L::cx(i) < 0 ? xp : s[0]);
-        const int Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : s[1]);
-        const int Z = L::D == 2 ? 0 : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : s[2]));
+        const int X = L::cx(i) > 0 ? xm : (L::cx(i) < 0 ? xp : sx);
+        const int Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
+        const int Z = L::D == 2 ? 0 : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
         const int64_t src = X + (int64_t)nx * Y + nxy * Z;
         if (solid && i != 0 && solid[src] == 1)
             g[i] = Store<S>::ld(fin + (int64_t)opp<L>(i) * N + scell);
@@ -96,79 +205,19 @@ __global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ 
             g[i] = Store<S>::ld(fin + (int64_t)i * N + src);
     }
 
-    const Mom<C> m = moments<L, C>(g);
-    const C om = C(p.omega);
-    Coef<C> k{};
+    const Mom<C> m = moments_pairs<L, C>(g);
+    const C chi = inlet >= 0 ? C(0) : chi_cell<L, C>(p, chi_row<L, C>(p, y, z), x);
+    const Coef<C> k = cell_coefficients<L, C>(p, m, chi, x, y, z, inlet);
 
-    if (inlet >= 0) {
-        // velocity node: rho, Pi^neq from the streamed neighbour, prescribed u
-        const C rho = C(1) + m.dr;
-        const C inv = C(1) / rho;
-        const C vx = m.jx * inv, vy = m.jy * inv, vz = m.jz * inv;
-        const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, vx, vy, vz, L::D);
-        const int a = inlet / 2;
-        const int t0 = a == 0 ? 1 : 0, t1 = a == 2 ? 1 : 2;
-        const int64_t kf = c[t0] + (int64_t)p.n[t0] * c[t1];
-        double ub[3];
-        const double *prof = p.u_profile[inlet];
+    // ---- rebuild, relax and store (even/odd parts of each opposite pair)
+    Store<S>::st(fout + cell, rebuild_rest<L, C>(k));
 #pragma unroll
-        for (int b = 0; b < 3; ++b) ub[b] = prof ? prof[3 * kf + b] : p.u_face[inlet][b];
-        if (p.noise_amp > 0.0) {
-            const double mag = sqrt(ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
-            if (mag > 0.0) {
-                const uint64_t base = (p.noise_seed << 32) +
-                                      ((uint64_t)p.step * (uint64_t)p.face_cells[inlet] + (uint64_t)kf) * 3u;
-#pragma unroll
-                for (int b = 0; b < L::D; ++b) ub[b] += p.noise_amp * mag * (2.0 * u01(base + b) - 1.0);
-            }
-        }
-        const C ux = C(ub[0]), uy = C(ub[1]), uz = L::D == 3 ? C(ub[2]) : C(0);
-        add_eq<C>(k, C(1), m.dr, rho, ux, uy, uz);
-        add_neq<C>(k, om, ux, uy, uz, pn);
-    } else {
-        C chi = C(0);
-        if (p.any_sponge) {
-#pragma unroll
-            for (int f = 0; f < 2 * L::D; ++f) {
-                const int W = p.sponge_w[f];
-                if (W > 0) {
-                    const int a = f >> 1;
-                    const int d = (f & 1) ? c[a] - (p.n[a] - W) : W - 1 - c[a];
-                    if (d >= 0) {
-                        const C v = C(p.sponge_chi[f]) * sigma<C>(C(d), C(W));
-                        chi = v > chi ? v : chi;
-                    }
-                }
-            }
-        }
-        if (chi > C(0)) {
-            // sponge: damped moments rho*, rho* u* (n = m = 1/2)
-            const C h = C(1) / (C(1) + C(0.5) * chi);
-            const C rr = C(p.rho_ref);
-            const C drs = (m.dr + C(0.5) * chi * C(p.rho_ref_m1)) * h;  // rho* - 1
-            const C rs = C(1) + drs;
-            const C jsx = (m.jx + C(0.5) * chi * rr * C(p.u_ref[0])) * h;
-            const C jsy = (m.jy + C(0.5) * chi * rr * C(p.u_ref[1])) * h;
-            const C jsz = (m.jz + C(0.5) * chi * rr * C(p.u_ref[2])) * h;
-            const C inv = C(1) / rs;
-            const C ux = jsx * inv, uy = jsy * inv, uz = L::D == 3 ? jsz * inv : C(0);
-            const Sym2<C> pn = pi_neq<C>(m, drs, rs, ux, uy, uz, L::D);
-            add_eq<C>(k, C(1) - chi, drs, rs, ux, uy, uz);
-            add_eq<C>(k, chi, C(p.rho_ref_m1), rr, C(p.u_ref[0]), C(p.u_ref[1]), L::D == 3 ? C(p.u_ref[2]) : C(0));
-            add_neq<C>(k, om, ux, uy, uz, pn);
-        } else {
-            const C rho = C(1) + m.dr;
-            const C inv = C(1) / rho;
-            const C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
-            const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
-            add_eq<C>(k, C(1), m.dr, rho, ux, uy, uz);
-            add_neq<C>(k, om, ux, uy, uz, pn);
-        }
+    for (int i = 1; i <= L::HALF; ++i) {
+        C e, o;
+        rebuild_pair<L, C>(k, i, e, o);
+        Store<S>::st(fout + (int64_t)i * N + cell, C(weight<L>(i)) * (e + o));
+        Store<S>::st(fout + (int64_t)(i + L::HALF) * N + cell, C(weight<L>(i)) * (e - o));
     }
-
-    // ---- rebuild, relax and store
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) Store<S>::st(fout + (int64_t)i * N + cell, rebuild<L, C>(k, i));
 }
 
 // Launch wrapper: one thread per cell, blocks along x.

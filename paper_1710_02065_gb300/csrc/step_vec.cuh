@@ -90,6 +90,30 @@ struct VecIO<__half, 4> {
     }
 };
 template <>
+struct VecIO<__half, 2> {
+    __device__ static void ld(const __half *p, float (&o)[2])
+    {
+        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
+        o[0] = h2f(v & 0xffffu); o[1] = h2f(v >> 16);
+    }
+    __device__ static void st(__half *p, const float (&o)[2])
+    {
+        *reinterpret_cast<unsigned *>(p) = (unsigned)f2h(o[0]) | ((unsigned)f2h(o[1]) << 16);
+    }
+};
+template <>
+struct VecIO<__nv_bfloat16, 2> {
+    __device__ static void ld(const __nv_bfloat16 *p, float (&o)[2])
+    {
+        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
+        o[0] = __uint_as_float(v << 16); o[1] = __uint_as_float(v & 0xffff0000u);
+    }
+    __device__ static void st(__nv_bfloat16 *p, const float (&o)[2])
+    {
+        *reinterpret_cast<unsigned *>(p) = (unsigned)f2b(o[0]) | ((unsigned)f2b(o[1]) << 16);
+    }
+};
+template <>
 struct VecIO<__nv_bfloat16, 4> {
     __device__ static void ld(const __nv_bfloat16 *p, float (&o)[4])
     {
@@ -105,142 +129,6 @@ struct VecIO<__nv_bfloat16, 4> {
         *reinterpret_cast<uint2 *>(p) = v;
     }
 };
-
-// ---------------------------------------------------------------------------
-// Moments from direction pairs: s = g_i + g_opp (even), d = g_i - g_opp (odd)
-// ---------------------------------------------------------------------------
-template <class L, class C>
-__device__ __forceinline__ Mom<C> moments_pairs(const C *g)
-{
-    Mom<C> m{};
-    m.dr = g[0];
-#pragma unroll
-    for (int i = 1; i <= L::HALF; ++i) {
-        const C s = g[i] + g[i + L::HALF], d = g[i] - g[i + L::HALF];
-        const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
-        m.dr += s;
-        if (x) m.jx += x > 0 ? d : -d;
-        if (y) m.jy += y > 0 ? d : -d;
-        if (z) m.jz += z > 0 ? d : -d;
-        if (x) m.sxx += s;
-        if (y) m.syy += s;
-        if (z) m.szz += s;
-        if (x && y) m.sxy += x * y > 0 ? s : -s;
-        if (x && z) m.sxz += x * z > 0 ? s : -s;
-        if (y && z) m.syz += y * z > 0 ? s : -s;
-    }
-    return m;
-}
-
-// Even (E) and odd (O) parts of the rebuilt population of direction i (1 <= i <= HALF)
-template <class L, class C>
-__device__ __forceinline__ void rebuild_pair(const Coef<C> &k, int i, C &even, C &odd)
-{
-    constexpr double cs2 = 1.0 / 3.0;
-    const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
-    C f2 = C(x * x - cs2) * k.xx + C(y * y - cs2) * k.yy;
-    if (L::D == 3) f2 += C(z * z - cs2) * k.zz;
-    if (x * y) f2 += C(2 * x * y) * k.xy;
-    if (L::D == 3 && x * z) f2 += C(2 * x * z) * k.xz;
-    if (L::D == 3 && y * z) f2 += C(2 * y * z) * k.yz;
-    even = k.a0 + C(4.5) * f2;
-    C f1 = C(0);
-    if (x) f1 += x > 0 ? k.a1x : -k.a1x;
-    if (y) f1 += y > 0 ? k.a1y : -k.a1y;
-    if (z) f1 += z > 0 ? k.a1z : -k.a1z;
-    C o = C(3) * f1;
-    const double hxxy = (x * x - cs2) * y, hxyy = (y * y - cs2) * x;
-    if (L::D == 2) {
-        if (hxxy != 0.0) o += C(13.5 * hxxy) * k.xxy;
-        if (hxyy != 0.0) o += C(13.5 * hxyy) * k.xyy;
-    } else {
-        const double hyzz = (z * z - cs2) * y, hxzz = (z * z - cs2) * x;
-        const double hyyz = (y * y - cs2) * z, hxxz = (x * x - cs2) * z;
-        const double p1 = hxxy + hyzz, m1 = hxxy - hyzz;
-        const double p2 = hxzz + hxyy, m2 = hxzz - hxyy;
-        const double p3 = hyyz + hxxz, m3 = hyyz - hxxz;
-        if (p1 != 0.0) o += C(13.5 * p1) * (k.xxy + k.yzz);
-        if (m1 != 0.0) o += C(4.5 * m1) * (k.xxy - k.yzz);
-        if (p2 != 0.0) o += C(13.5 * p2) * (k.xzz + k.xyy);
-        if (m2 != 0.0) o += C(4.5 * m2) * (k.xzz - k.xyy);
-        if (p3 != 0.0) o += C(13.5 * p3) * (k.yyz + k.xxz);
-        if (m3 != 0.0) o += C(4.5 * m3) * (k.yyz - k.xxz);
-    }
-    odd = o;
-}
-
-// Collision coefficients of one cell (bulk, sponge or velocity node)
-template <class L, class C>
-__device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const Mom<C> &m, int cx,
-                                                     int cy, int cz, int inlet)
-{
-    const C om = C(p.omega);
-    Coef<C> k{};
-    if (inlet >= 0) {
-        const C rho = C(1) + m.dr;
-        const C inv = C(1) / rho;
-        const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, m.jx * inv, m.jy * inv, m.jz * inv, L::D);
-        const int a = inlet >> 1;
-        const int c[3] = {cx, cy, cz};
-        const int t0 = a == 0 ? 1 : 0, t1 = a == 2 ? 1 : 2;
-        const int64_t kf = c[t0] + (int64_t)p.n[t0] * c[t1];
-        double ub[3];
-        const double *prof = p.u_profile[inlet];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) ub[b] = prof ? prof[3 * kf + b] : p.u_face[inlet][b];
-        if (p.noise_amp > 0.0) {
-            const double mag = sqrt(ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
-            if (mag > 0.0) {
-                const uint64_t base =
-                    (p.noise_seed << 32) + ((uint64_t)p.step * (uint64_t)p.face_cells[inlet] + (uint64_t)kf) * 3u;
-#pragma unroll
-                for (int b = 0; b < L::D; ++b) ub[b] += p.noise_amp * mag * (2.0 * u01(base + b) - 1.0);
-            }
-        }
-        const C ux = C(ub[0]), uy = C(ub[1]), uz = L::D == 3 ? C(ub[2]) : C(0);
-        add_eq<C>(k, C(1), m.dr, rho, ux, uy, uz);
-        add_neq<C>(k, om, ux, uy, uz, pn);
-        return k;
-    }
-    C chi = C(0);
-    if (p.any_sponge) {
-        const int c[3] = {cx, cy, cz};
-#pragma unroll
-        for (int f = 0; f < 2 * L::D; ++f) {
-            const int W = p.sponge_w[f];
-            if (W > 0) {
-                const int a = f >> 1;
-                const int d = (f & 1) ? c[a] - (p.n[a] - W) : W - 1 - c[a];
-                if (d >= 0) {
-                    const C v = C(p.sponge_chi[f]) * sigma<C>(C(d), C(W));
-                    chi = v > chi ? v : chi;
-                }
-            }
-        }
-    }
-    if (chi > C(0)) {
-        const C h = C(1) / (C(1) + C(0.5) * chi);
-        const C rr = C(p.rho_ref);
-        const C drs = (m.dr + C(0.5) * chi * C(p.rho_ref_m1)) * h;
-        const C rs = C(1) + drs;
-        const C inv = C(1) / rs;
-        const C ux = (m.jx + C(0.5) * chi * rr * C(p.u_ref[0])) * h * inv;
-        const C uy = (m.jy + C(0.5) * chi * rr * C(p.u_ref[1])) * h * inv;
-        const C uz = L::D == 3 ? (m.jz + C(0.5) * chi * rr * C(p.u_ref[2])) * h * inv : C(0);
-        const Sym2<C> pn = pi_neq<C>(m, drs, rs, ux, uy, uz, L::D);
-        add_eq<C>(k, C(1) - chi, drs, rs, ux, uy, uz);
-        add_eq<C>(k, chi, C(p.rho_ref_m1), rr, C(p.u_ref[0]), C(p.u_ref[1]), L::D == 3 ? C(p.u_ref[2]) : C(0));
-        add_neq<C>(k, om, ux, uy, uz, pn);
-        return k;
-    }
-    const C rho = C(1) + m.dr;
-    const C inv = C(1) / rho;
-    const C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
-    const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
-    add_eq<C>(k, C(1), m.dr, rho, ux, uy, uz);
-    add_neq<C>(k, om, ux, uy, uz, pn);
-    return k;
-}
 
 // ---------------------------------------------------------------------------
 // The kernel.  Block = one warp-multiple of threads along one x row.
@@ -316,6 +204,7 @@ __global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constan
     }
 
     // ---- collision coefficients of the V cells
+    const C chirow = chi_row<L, C>(p, y, z);
     Coef<C> cf[V];
 #pragma unroll
     for (int k = 0; k < V; ++k) {
@@ -327,20 +216,16 @@ __global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constan
         if (k == 0 && xlo && p.kind[0] == BC_VELOCITY) inlet = 0;
         else if (k == V - 1 && xhi && p.kind[1] == BC_VELOCITY) inlet = 1;
         if (inlet < 0) inlet = inlet_row;
-        cf[k] = cell_coefficients<L, C>(p, m, x0 + k, y, z, inlet);
+        const C chi = inlet >= 0 ? C(0) : chi_cell<L, C>(p, chirow, x0 + k);
+        cf[k] = cell_coefficients<L, C>(p, m, chi, x0 + k, y, z, inlet);
     }
 
     // ---- rebuild and store, one direction pair at a time
     const int64_t base = (int64_t)nx * y + nxy * z + x0;
     {
-        constexpr double cs2 = 1.0 / 3.0;
         C o[V];
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
-            C f2 = C(-cs2) * (cf[k].xx + cf[k].yy);
-            if (L::D == 3) f2 += C(-cs2) * cf[k].zz;
-            o[k] = C(weight<L>(0)) * (cf[k].a0 + C(4.5) * f2);
-        }
+        for (int k = 0; k < V; ++k) o[k] = rebuild_rest<L, C>(cf[k]);
         VecIO<S, V>::st(fout + base, o);
     }
 #pragma unroll

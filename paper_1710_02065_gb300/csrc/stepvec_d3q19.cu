@@ -17,9 +17,11 @@ cudaError_t stepvec_d3q19(int precision, int vec, const StepParams &p, const voi
         break;
     case PREC_FP16:
         if (vec == 4) return launch_stream_collide_vec<D3Q19, __half, float, 4>(p, fin, fout, block, st);
+        if (vec == 2) return launch_stream_collide_vec<D3Q19, __half, float, 2>(p, fin, fout, block, st);
         break;
     case PREC_BF16:
         if (vec == 4) return launch_stream_collide_vec<D3Q19, __nv_bfloat16, float, 4>(p, fin, fout, block, st);
+        if (vec == 2) return launch_stream_collide_vec<D3Q19, __nv_bfloat16, float, 2>(p, fin, fout, block, st);
         break;
     }
     return cudaErrorInvalidValue;

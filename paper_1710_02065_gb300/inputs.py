@@ -105,12 +105,21 @@ def uniform_flow_perturbed(nx: int, ny: int, U: float, seed: int, rel: float = 0
     return rho, u
 
 
-def top_hat_profile(ny: int, nz: int, yc: float, zc: float, radius: float, U: float):
-    """Per-face-cell inlet velocity (ny*nz, 3) for the x faces: (U,0,0) where r < radius."""
+def top_hat_profile(ny: int, nz: int, yc: float, zc: float, radius: float, U: float,
+                    theta: float = 0.0):
+    """Per-face-cell inlet velocity (ny*nz, 3) for the x faces.
+
+    theta = 0: sharp top hat, (U, 0, 0) where r < radius.  theta > 0: the
+    usual smoothed top hat U/2 (1 - tanh((r - radius) / (2 theta))) with
+    shear-layer momentum thickness theta (cells).
+    """
     z, y = np.meshgrid(np.arange(nz), np.arange(ny), indexing="ij")
-    inside = ((y - yc) ** 2 + (z - zc) ** 2) < radius ** 2
+    r = np.sqrt((y - yc) ** 2 + (z - zc) ** 2).reshape(-1)
     prof = np.zeros((ny * nz, 3))
-    prof[:, 0] = np.where(inside.reshape(-1), U, 0.0)
+    if theta > 0:
+        prof[:, 0] = 0.5 * U * (1.0 - np.tanh((r - radius) / (2.0 * theta)))
+    else:
+        prof[:, 0] = np.where(r < radius, U, 0.0)
     return prof
 
 

@@ -65,6 +65,13 @@ _sig("lbm_sync", [_h])
 _sig("lbm_set_launch", [_h, C.c_int, C.c_int])
 _sig("lbm_get_launch", [_h, _ip, _ip])
 _sig("lbm_info", [_h, _i64p, _i64p, _dp, _dp])
+_sig("lbm_add_refinement_patch", [_h, _ip, _ip])
+_sig("lbm_level_info", [_h, C.c_int, _ip, _dp])
+_sig("lbm_set_geometry_level", [_h, C.c_int, C.POINTER(C.c_uint8)])
+_sig("lbm_set_state_level", [_h, C.c_int, _dp, _dp])
+_sig("lbm_set_populations_level", [_h, C.c_int, _dp])
+_sig("lbm_get_populations_level", [_h, C.c_int, _dp])
+_sig("lbm_moments_level", [_h, C.c_int, _dp, _dp, _dp])
 _sig("lbm_save", [_h, C.c_char_p])
 _sig("lbm_load", [_h, C.c_char_p])
 
@@ -73,6 +80,8 @@ EXPORTED = [
     "lbm_set_boundary", "lbm_set_inlet_noise", "lbm_set_sponge", "lbm_set_state",
     "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_moments", "lbm_reduce",
     "lbm_probe", "lbm_sync", "lbm_info", "lbm_save", "lbm_load", "lbm_set_launch", "lbm_get_launch",
+    "lbm_add_refinement_patch", "lbm_level_info", "lbm_set_geometry_level", "lbm_set_state_level",
+    "lbm_set_populations_level", "lbm_get_populations_level", "lbm_moments_level",
 ]
 
 
@@ -218,6 +227,45 @@ def lbm_save(h, path: str):
 
 def lbm_load(h, path: str):
     return _check(_lib.lbm_load(h, path.encode()), h)
+
+
+def lbm_add_refinement_patch(h, origin, extent):
+    o = (C.c_int * 3)(*[int(v) for v in (list(origin) + [0] * (3 - len(origin)))])
+    e = (C.c_int * 3)(*[int(v) for v in (list(extent) + [1] * (3 - len(extent)))])
+    return _check(_lib.lbm_add_refinement_patch(h, o, e), h)
+
+
+def lbm_level_info(h, level: int):
+    e = (C.c_int * 3)()
+    t = C.c_double()
+    _check(_lib.lbm_level_info(h, level, e, C.byref(t)), h)
+    return tuple(e), t.value
+
+
+def lbm_set_geometry_level(h, level: int, cell_type):
+    if cell_type is None:
+        return _check(_lib.lbm_set_geometry_level(h, level, None), h)
+    a = np.ascontiguousarray(cell_type, dtype=np.uint8).reshape(-1)
+    return _check(_lib.lbm_set_geometry_level(h, level, a.ctypes.data_as(C.POINTER(C.c_uint8))), h)
+
+
+def lbm_set_state_level(h, level: int, rho, u):
+    r = _c64(rho).reshape(-1)
+    v = _c64(u).reshape(-1)
+    return _check(_lib.lbm_set_state_level(h, level, _d(r), _d(v)), h)
+
+
+def lbm_set_populations_level(h, level: int, f):
+    a = _c64(f)
+    return _check(_lib.lbm_set_populations_level(h, level, _d(a)), h)
+
+
+def lbm_get_populations_level(h, level: int, out: np.ndarray):
+    return _check(_lib.lbm_get_populations_level(h, level, _d(out)), h)
+
+
+def lbm_moments_level(h, level: int, rho=None, u=None, pi_neq=None):
+    return _check(_lib.lbm_moments_level(h, level, _d(rho), _d(u), _d(pi_neq)), h)
 
 
 # ---------------------------------------------------------------------------

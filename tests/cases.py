@@ -136,3 +136,28 @@ def with_random_state(c: Case, seed=11, spread=0.05):
     _, _, _, w, _ = oracle.lattice(c.lattice)
     c.f0 = inputs.random_populations(w, c.ncell, seed, spread)
     return c
+
+
+def cylinder_two_level(nxc=200, nyc=100, patch=(40, 30, 80, 40), diameter_c=10.0, xc=None, yc=None,
+                       Ma=0.2, Re=150.0, sponge=25, chi=0.5, seed=2):
+    """The cylinder workload on a 2:1 two-level grid: coarse box with inflow,
+    sponge and outflow; a fine patch over coarse nodes X0..X0+Wc, Y0..Y0+Hc
+    holding the cylinder (diameter 2 diameter_c fine cells).  tau from Re on
+    the fine level (the cylinder's resolution), tau_c = (tau_f + 1/2) / 2.
+    Returns (coarse Case, patch, fine rho, fine u, fine solid)."""
+    X0, Y0, Wc, Hc = patch
+    U = Ma * CS
+    D_f = 2 * diameter_c
+    tau_f = 3 * U * D_f / Re + 0.5
+    tau_c = (tau_f + 0.5) / 2
+    rho, u = inputs.uniform_flow_perturbed(nxc, nyc, U, seed)
+    c = Case("cylinder2", D2Q9, (nxc, nyc, 1), tau_c, rho0=rho, u0=u, rho_ref=1.0, u_ref=(U, 0.0, 0.0))
+    c.faces = {0: (VELOCITY, (U, 0.0, 0.0), None), 1: (OUTFLOW, (0, 0, 0), None)}
+    c.sponges = {1: (sponge, chi)}
+    nfx, nfy = 2 * Wc + 1, 2 * Hc + 1
+    xc = (Wc // 2) if xc is None else xc
+    yc = (Hc // 2) if yc is None else yc
+    solid_f = inputs.cylinder_mask(nfx, nfy, 2 * xc, 2 * yc, D_f)
+    rho_f, u_f = inputs.uniform_flow_perturbed(nfx, nfy, U, seed + 1)
+    u_f[solid_f == 1] = 0.0
+    return c, patch, rho_f, u_f, solid_f

@@ -331,7 +331,7 @@ def test_launch_shapes_match_oracle(lattice, prec):
     (nx/V not a multiple of 32), periodic and open x: all equal the oracle."""
     from paper_1710_02065_gb300 import lbm
     _, _, _, w, _ = oracle.lattice(lattice)
-    vecs = {"fp64": [1, 2], "fp32": [1, 2, 4], "fp16": [1, 4], "bf16": [1, 4]}[prec]
+    vecs = {"fp64": [1, 2], "fp32": [1, 2, 4], "fp16": [1, 2, 4], "bf16": [1, 2, 4]}[prec]
     sizes = [(40, 12, 1), (136, 7, 1)] if lattice == D2Q9 else [(24, 10, 6), (136, 5, 4)]
     for n in sizes:
         c = _open_box(lattice, n, seed=n[0])
