@@ -43,17 +43,19 @@ CS = 1.0 / math.sqrt(3.0)
 # ---------------------------------------------------------------------------
 def jet_spec(nx=384, ny=256, nz=256, diameter=24.0, sponge=32, Ma=0.3, Re=1e4, chi=0.5, seed=3,
              noise=0.01):
+    """The round jet: top-hat inflow (tanh shear layer of momentum thickness
+    R/20), Ma 0.3, Re_D, 1% seeded inlet noise, sponges chi_max 0.5."""
     U = Ma * CS
     tau = 3 * U * diameter / Re + 0.5
     return dict(n=(nx, ny, nz), diameter=diameter, sponge=sponge, U=U, tau=tau, chi=chi, seed=seed,
-                noise=noise)
+                noise=noise, theta=diameter / 40.0)
 
 
 def configure_gpu(lbm, spec, precision, stream):
     from paper_1710_02065_gb300 import inputs
     nx, ny, nz = spec["n"]
     s = lbm.Solver(lbm.LBM_D3Q19, spec["n"], spec["tau"], precision, Ma_ref=0.3, stream=stream)
-    prof = inputs.top_hat_profile(ny, nz, ny / 2, nz / 2, spec["diameter"] / 2, spec["U"])
+    prof = inputs.top_hat_profile(ny, nz, ny / 2, nz / 2, spec["diameter"] / 2, spec["U"], spec["theta"])
     lbm.lbm_set_boundary(s.h, lbm.LBM_FACE_XM, lbm.LBM_BC_VELOCITY, None, prof)
     for f in range(1, 6):
         lbm.lbm_set_boundary(s.h, f, lbm.LBM_BC_OUTFLOW)
@@ -67,7 +69,7 @@ def configure_oracle(spec):
     from paper_1710_02065_gb300 import inputs
     nx, ny, nz = spec["n"]
     P = oracle.Problem(oracle.D3Q19, spec["n"], spec["tau"])
-    prof = inputs.top_hat_profile(ny, nz, ny / 2, nz / 2, spec["diameter"] / 2, spec["U"])
+    prof = inputs.top_hat_profile(ny, nz, ny / 2, nz / 2, spec["diameter"] / 2, spec["U"], spec["theta"])
     P.set_boundary(0, oracle.VELOCITY, (0, 0, 0), prof)
     for f in range(1, 6):
         P.set_boundary(f, oracle.OUTFLOW)
@@ -216,10 +218,13 @@ def barrier(pg):
 # ---------------------------------------------------------------------------
 # timing of one precision
 # ---------------------------------------------------------------------------
-def time_precision(lbm, torch, spec, precision, steps, warmup, pg, stream):
+def time_precision(lbm, torch, spec, precision, steps, warmup, pg, stream, tune=True):
+    from paper_1710_02065_gb300 import autotune
     s = configure_gpu(lbm, spec, precision, stream.cuda_stream)
     n = s.ncell
     s.set_state(np.ones(n), np.zeros((n, 3)))
+    tuned = autotune.autotune(s.h, precision, stream, steps=5, torch=torch)[1] if tune else {}
+    launch = lbm.lbm_get_launch(s.h)
     lbm.lbm_step(s.h, warmup)
     s.sync()
     info0 = s.info()
@@ -239,7 +244,9 @@ def time_precision(lbm, torch, spec, precision, steps, warmup, pg, stream):
     m, j, rc = s.reduce()
     s.close()
     return dict(total_ms=total_ms, per_ms=per, launches=info1["launches"] - info0["launches"],
-                bytes_per_cell=info1["bytes_per_cell"], ncell=n, stable=(rc == 0))
+                bytes_per_cell=info1["bytes_per_cell"], ncell=n, stable=(rc == 0),
+                launch={"block": launch[0], "cells_per_thread": launch[1]},
+                tuning={f"{b}x{v}": round(ms, 4) for (b, v), ms in tuned.items()})
 
 
 def e2e_run(lbm, torch, spec, precision, steps, stream):
@@ -265,6 +272,39 @@ def e2e_run(lbm, torch, spec, precision, steps, stream):
     dt = time.perf_counter() - t0
     s.close()
     return dict(seconds=dt, h2d=(rho.nbytes + u.nbytes) / steps, d2h=(ro.nbytes + uo.nbytes) / steps)
+
+
+def pprime_errors(lbm, torch, stream, checkpoints=(100, 500, 1000, 5000)):
+    """p' = c_s^2 (rho - 1) of each storage precision against the FP64 path on
+    the jet scaled to 96x64x64 (D = 6, sponges 8, same Ma and Re_D)."""
+    spec = jet_spec(**SAMPLE_SPEC)
+    runs = {}
+    for name in ("fp64", "fp32", "fp16", "bf16"):
+        s = configure_gpu(lbm, spec, lbm.PRECISIONS[name], stream.cuda_stream)
+        n = s.ncell
+        s.set_state(np.ones(n), np.zeros((n, 3)))
+        t, fields = 0, {}
+        for c in checkpoints:
+            lbm.lbm_step(s.h, c - t)
+            t = c
+            rho = np.zeros(n)
+            lbm.lbm_moments(s.h, rho, None, None)
+            fields[c] = (rho - 1.0) / 3.0
+        runs[name] = fields
+        s.close()
+    out = {}
+    for name in ("fp32", "fp16", "bf16"):
+        out[name] = {}
+        for c in checkpoints:
+            ref = runs["fp64"][c]
+            d = runs[name][c] - ref
+            scale = np.abs(ref).max()
+            out[name][str(c)] = {"max_rel": float(np.abs(d).max() / scale),
+                                 "rms_rel": float(np.sqrt(np.mean(d * d)) / scale),
+                                 "finite": bool(np.isfinite(runs[name][c]).all())}
+    out["reference"] = "GPU FP64 path (parity with the FP64 oracle 1e-12); max |p'_64| per step in max_p64"
+    out["max_p64"] = {str(c): float(np.abs(runs["fp64"][c]).max()) for c in checkpoints}
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -306,6 +346,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the other storage precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
+    ap.add_argument("--no-tune", action="store_true", help="use the default launch shape (no autotuning)")
     ap.add_argument("--grid", default="384x256x256",
                     help="jet extents NXxNYxNZ; inlet diameter and sponges scale with NX/384")
     args = ap.parse_args()
@@ -333,7 +374,7 @@ def main():
     stream = torch.cuda.Stream()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    main_run = time_precision(lbm, torch, spec, prec, args.steps, args.warmup, pg, stream)
+    main_run = time_precision(lbm, torch, spec, prec, args.steps, args.warmup, pg, stream, tune=not args.no_tune)
     clk = clocks.stop()
     total_s = max_over_ranks(main_run["total_ms"] / 1e3, pg, world)
     ncell = main_run["ncell"]
@@ -356,15 +397,18 @@ def main():
             if name == args.precision:
                 continue
             r = time_precision(lbm, torch, spec, lbm.PRECISIONS[name], max(20, args.steps // 4),
-                               args.warmup, pg, stream)
+                               args.warmup, pg, stream, tune=not args.no_tune)
             k_ms = float(np.mean(r["per_ms"]))
-            extra[name] = {"mlups": r["ncell"] / (k_ms / 1e3) / 1e6,
+            extra[name] = {"launch": r["launch"], "mlups": r["ncell"] / (k_ms / 1e3) / 1e6,
                            "gbs": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9,
                            "frac_of_measured_hbm": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9 / peak}
         if "fp16" in extra:
             extra["fp16_store_speedup"] = extra["fp16"]["mlups"] / (ncell / (kernel_ms / 1e3) / 1e6)
         if "bf16" in extra:
             extra["bf16_store_speedup"] = extra["bf16"]["mlups"] / (ncell / (kernel_ms / 1e3) / 1e6)
+
+    if not args.no_extra:
+        extra["pprime_error_vs_fp64_96x64x64"] = pprime_errors(lbm, torch, stream)
 
     e2e = None if args.no_e2e else e2e_run(lbm, torch, spec, prec, args.steps, stream)
     e2e_s = max_over_ranks(e2e["seconds"], pg, world) if e2e else None
@@ -385,6 +429,8 @@ def main():
             "config": {"workload": f"D3Q19 round jet {nx}x{ny}x{nz}, {args.precision} population storage, "
                                    "two-lattice pull, fused inflow/outflow/sponge",
                        "cells": ncell, "tau": spec["tau"], "storage": args.precision,
+                       "inlet": "top hat, tanh shear layer theta = D/40, Ma 0.3, 1% seeded noise",
+                       "launch": main_run["launch"], "autotune_ms_per_step": main_run["tuning"],
                        "l2": "inputs larger than L2 (populations %.2f GB per lattice)" % (bpc / 2 * ncell / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

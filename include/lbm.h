@@ -229,11 +229,11 @@ int lbm_probe(lbm_handle h, int n, const int64_t *cells, double *p_prime);
  * lbm_set_launch -- launch shape of the update kernel (a tuning knob; the
  * result does not depend on it beyond FP round-off order).
  *   block            : threads per block, a multiple of 32 in [32, 256], or 0
- *                      for the default (128)
+ *                      for the default (128 one cell per thread, else 64)
  *   cells_per_thread : 1 = one cell per thread (the general kernel); 2 or 4 =
  *                      vectorised kernel with that many consecutive x cells per
  *                      thread (FP64: 2; FP32, FP16, BF16: 2 or 4); 0 = default
- *                      (4, FP64 2).  The vectorised kernel is used only when
+ *                      (FP32 1; FP16, BF16, FP64 2).  The vectorised kernel is used only when
  *                      there is no cell-type mask and nx is a multiple of it;
  *                      otherwise the general kernel runs.
  * lbm_get_launch reports the shape lbm_step will use now.

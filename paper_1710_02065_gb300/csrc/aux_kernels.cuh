@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(int64_t N, const S *__rest
 }
 
 // Final pass: one warp per field, strided then shuffled: fixed order, deterministic.
-__global__ void k_reduce_final(int nblocks, const double *__restrict__ partial,
+static __global__ void k_reduce_final(int nblocks, const double *__restrict__ partial,
                                double *__restrict__ out)
 {
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;

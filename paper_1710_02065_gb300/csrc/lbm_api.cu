@@ -80,6 +80,8 @@ static GridRef fine_ref(lbm_ctx *h)
 
 static thread_local std::string g_create_err;
 
+void rr::rr_set_global_error(const char *msg) { g_create_err = msg; }
+
 static int fail(lbm_ctx *h, int code, const char *fmt, ...)
 {
     char buf[512];
@@ -599,7 +601,7 @@ static cudaError_t launch_update(lbm_ctx *h, const StepParams &p, const void *fi
 {
     int vec = h->vec == 0 ? vec_default(h->prec) : h->vec;
     if (p.solid || vec == 1 || !vec_supported(h->prec, vec) || p.n[0] % vec != 0) vec = 1;
-    const int block = h->block > 0 ? h->block : 128;
+    const int block = h->block > 0 ? h->block : block_default(vec);
     h->launches += 1;
     if (vec == 1)
         return h->lattice == LBM_D2Q9 ? step_d2q9(h->prec, p, fin, fout, block, h->stream)
@@ -869,7 +871,7 @@ extern "C" int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread)
     CHECK_HANDLE(h);
     int vec = h->vec == 0 ? vec_default(h->prec) : h->vec;
     if (h->solid_d || vec == 1 || !vec_supported(h->prec, vec) || h->n[0] % vec != 0) vec = 1;
-    if (block) *block = h->block > 0 ? h->block : 128;  // level 0
+    if (block) *block = h->block > 0 ? h->block : block_default(vec);  // level 0
     if (cells_per_thread) *cells_per_thread = vec;
     return LBM_OK;
 }

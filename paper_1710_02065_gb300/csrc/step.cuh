@@ -154,17 +154,15 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
 }
 
 // ---------------------------------------------------------------------------
-// General kernel: one thread per cell, optional cell-type mask.
+// One cell's update (general form): pull with wrap and bounce-back, boundary
+// role from coordinates, collision, store.  Shared by the single-lattice
+// kernel below and the batched multi-domain kernel.
 // ---------------------------------------------------------------------------
 template <class L, class S, class C>
-__global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ StepParams p,
-                                                         const S *__restrict__ fin,
-                                                         S *__restrict__ fout)
+__device__ __forceinline__ void update_cell(const StepParams &p, const S *__restrict__ fin, S *__restrict__ fout,
+                                            int x, int y, int z)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
-    if (x >= nx) return;
     const int64_t N = p.ncell;
     const int64_t nxy = (int64_t)nx * ny;
     const int64_t cell = x + (int64_t)nx * y + nxy * z;
@@ -218,6 +216,17 @@ __global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ 
         Store<S>::st(fout + (int64_t)i * N + cell, C(weight<L>(i)) * (e + o));
         Store<S>::st(fout + (int64_t)(i + L::HALF) * N + cell, C(weight<L>(i)) * (e - o));
     }
+}
+
+// General kernel: one thread per cell, optional cell-type mask.
+template <class L, class S, class C>
+__global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ StepParams p,
+                                                         const S *__restrict__ fin,
+                                                         S *__restrict__ fout)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.n[0]) return;
+    update_cell<L, S, C>(p, fin, fout, x, blockIdx.y, blockIdx.z);
 }
 
 // Launch wrapper: one thread per cell, blocks along x.

@@ -133,3 +133,4 @@ def random_populations(weights: np.ndarray, ncell: int, seed: int, spread: float
     rng = np.random.default_rng(seed)
     r = rng.random((len(weights), ncell))
     return np.asarray(weights)[:, None] * (1.0 + spread * (2.0 * r - 1.0))
+

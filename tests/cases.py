@@ -115,12 +115,13 @@ def cylinder(nx=1600, ny=800, diameter=40.0, xc=None, yc=None, Ma=0.2, Re=150.0,
 
 def round_jet(nx=384, ny=256, nz=256, diameter=24.0, Ma=0.3, Re=1e4, sponge=32, chi=0.5, seed=3,
               noise=0.01):
-    """D3Q19 round jet: top-hat inflow of the given diameter on -x at U = Ma c_s,
-    ambient at rest, sponges and zero-gradient outflow on the five other faces."""
+    """D3Q19 round jet: top-hat inflow of the given diameter on -x at U = Ma c_s
+    (tanh shear layer, momentum thickness D/40), ambient at rest, sponges and
+    zero-gradient outflow on the five other faces."""
     U = Ma * CS
     nu = U * diameter / Re
     tau = 3 * nu + 0.5
-    prof = inputs.top_hat_profile(ny, nz, ny / 2, nz / 2, diameter / 2, U)
+    prof = inputs.top_hat_profile(ny, nz, ny / 2, nz / 2, diameter / 2, U, diameter / 40.0)
     n = nx * ny * nz
     c = Case("round_jet", D3Q19, (nx, ny, nz), tau, rho0=np.ones(n), u0=np.zeros((n, 3)),
              rho_ref=1.0, u_ref=(0.0, 0.0, 0.0), noise=(seed, noise))
