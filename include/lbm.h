@@ -297,6 +297,43 @@ int lbm_moments_level(lbm_handle h, int level, double *rho, double *u, double *p
 int lbm_save(lbm_handle h, const char *path);
 int lbm_load(lbm_handle h, const char *path);
 
+/*
+ * lbm_reduce_noalloc -- the totals of lbm_reduce for a population field the
+ * caller owns, computed without allocating any memory.  (The paper has no
+ * counterpart: this is an integration entry point.)
+ *
+ * For callers that cannot allocate device memory where they need the totals:
+ * code being recorded into a CUDA graph by stream capture (allocation is not
+ * capturable), loops that must never enter an allocator, or hosts that keep
+ * a fixed device-memory budget and lend the library only their own buffers.
+ * The per-block partial sums live in a static device array inside the
+ * library, sized for at most LBM_NOALLOC_MAX_CELLS cells, which every GPU
+ * that loads the library keeps until the process exits.  The call itself
+ * allocates nothing and does not use a handle.
+ *   lattice, precision : as for lbm_create
+ *   f         : device pointer to the field in the library's storage layout:
+ *               q * ncell values of the precision's type, direction-major
+ *               (f[i * ncell + cell]), each holding f_i - w_i
+ *   ncell     : number of cells, 1 <= ncell <= LBM_NOALLOC_MAX_CELLS (larger
+ *               fields are rejected with LBM_EINVAL)
+ *   cell_type : device pointer to ncell cell types, or NULL (all fluid); only
+ *               fluid cells are counted
+ *   out       : device pointer to 6 doubles, written in stream order:
+ *               [sum rho, sum rho ux, sum rho uy, sum rho uz, fluid cells,
+ *               non-finite cells]
+ *   cuda_stream : stream to enqueue on (NULL: legacy default stream)
+ * Asynchronous: synchronise the stream before reading out.  The first call on
+ * a device looks up the scratch array's device address (once per device,
+ * with that device current); make that first call before any stream capture
+ * begins.  Every call reuses the same scratch, so calls that overlap on the
+ * GPU (other streams, other host threads) race; each call overwrites all the
+ * scratch it reads, so nothing needs clearing between calls.  Errors are
+ * reported by lbm_last_error(NULL).
+ */
+#define LBM_NOALLOC_MAX_CELLS 67108864LL
+int lbm_reduce_noalloc(int lattice, int precision, const void *f, int64_t ncell,
+                       const uint8_t *cell_type, double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,7 @@ _sig("lbm_set_state_level", [_h, C.c_int, _dp, _dp])
 _sig("lbm_set_populations_level", [_h, C.c_int, _dp])
 _sig("lbm_get_populations_level", [_h, C.c_int, _dp])
 _sig("lbm_moments_level", [_h, C.c_int, _dp, _dp, _dp])
+_sig("lbm_reduce_noalloc", [C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p])
 _sig("lbm_save", [_h, C.c_char_p])
 _sig("lbm_load", [_h, C.c_char_p])
 
@@ -82,6 +83,7 @@ EXPORTED = [
     "lbm_probe", "lbm_sync", "lbm_info", "lbm_save", "lbm_load", "lbm_set_launch", "lbm_get_launch",
     "lbm_add_refinement_patch", "lbm_level_info", "lbm_set_geometry_level", "lbm_set_state_level",
     "lbm_set_populations_level", "lbm_get_populations_level", "lbm_moments_level",
+    "lbm_reduce_noalloc",
 ]
 
 
@@ -266,6 +268,14 @@ def lbm_get_populations_level(h, level: int, out: np.ndarray):
 
 def lbm_moments_level(h, level: int, rho=None, u=None, pi_neq=None):
     return _check(_lib.lbm_moments_level(h, level, _d(rho), _d(u), _d(pi_neq)), h)
+
+
+def lbm_reduce_noalloc(lattice: int, precision: int, f_dev: int, ncell: int, cell_type_dev: int | None,
+                       out_dev: int, cuda_stream: int | None = None):
+    """Device pointers in, device pointer out (6 doubles); no allocation."""
+    return _check(_lib.lbm_reduce_noalloc(lattice, precision, C.c_void_p(f_dev), C.c_int64(int(ncell)),
+                                          C.c_void_p(cell_type_dev or 0), C.c_void_p(out_dev),
+                                          C.c_void_p(cuda_stream or 0)), None)
 
 
 # ---------------------------------------------------------------------------
