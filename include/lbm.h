@@ -112,8 +112,9 @@ int lbm_lattice_table(int lattice, int *q, int *d, int *xi, double *w);
  *   precision   : LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED or LBM_BF16_SHIFTED
  *   cuda_stream : cudaStream_t to enqueue work on, or NULL for the legacy
  *                 default stream
- * Errors: LBM_EINVAL (extents < 1, or < 3 along a later non-periodic axis;
- * tau <= 1/2; bad lattice/precision; Ma_ref outside [0, 0.6]),
+ * Errors: LBM_EINVAL (extents < 1, extents[1] or extents[2] > 65535, more
+ * than 2^31 - 1 cells; tau <= 1/2; bad lattice/precision; Ma_ref outside
+ * [0, 0.6]; a non-periodic axis needs >= 3 cells, checked at lbm_step),
  * LBM_ENOMEM, LBM_ECUDA.  On error *out is NULL.
  */
 int lbm_create(lbm_handle *out, int lattice, const int extents[3], double tau_or_nu,
@@ -241,6 +242,17 @@ int lbm_probe(lbm_handle h, int n, const int64_t *cells, double *p_prime);
 int lbm_set_launch(lbm_handle h, int block, int cells_per_thread);
 int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread);
 
+/*
+ * lbm_force -- force on the solid cells of a level (0 coarse / single level, 1
+ * fine), FP64 on the device: momentum exchange over the halfway bounce-back
+ * links, F = sum over fluid cells x and directions i with x + xi_i solid of
+ * 2 xi_i f*_i(x), f* the stored post-collision field (momentum per step in
+ * that level's lattice units).  The paper reports lift and drag coefficients
+ * of its cylinder (Sec. III) without stating how they are computed; this is
+ * the standard estimate for the bounce-back wall.  Zero without solids.
+ */
+int lbm_force(lbm_handle h, int level, double F[3]);
+
 /* lbm_sync -- wait for all work of h; returns any pending execution error. */
 int lbm_sync(lbm_handle h);
 
@@ -296,6 +308,61 @@ int lbm_moments_level(lbm_handle h, int level, double *rho, double *u, double *p
  */
 int lbm_save(lbm_handle h, const char *path);
 int lbm_load(lbm_handle h, const char *path);
+
+/*
+ * Solve server: continuous batching of independent solves (serving).
+ *
+ * A request is a fully periodic lattice with its own lattice type, extents,
+ * tau, number of steps, storage precision and initial rho, u (Eq. eqH
+ * populations).  lbm_server_submit queues it (the initial fields are copied).
+ * Each lbm_server_run call is one round: queued requests are admitted in
+ * arrival order, first fit, while their two population lattices fit in the
+ * HBM budget and a slot is free; then every active request advances by up to
+ * `steps` steps in one CUDA-graph replay of batched updates (one persistent
+ * launch per (lattice, precision) group, plus a per-request step counter), a
+ * request stopping exactly at its own step count; finished requests are
+ * retired at the end of the round (rho and u of the final post-collision
+ * field kept on the host, device memory returned to the budget).  A request's
+ * arithmetic is the single-lattice update's and does not depend on what it
+ * is batched with.
+ *   lbm_server_create : budget in bytes, max_slots concurrent requests, stream
+ *                       (NULL: the server creates its own)
+ *   lbm_server_run    : *completed (may be NULL) = requests finished this round
+ *   lbm_server_poll   : state LBM_REQ_* and steps done so far
+ *   lbm_server_result : copies rho (ncell) and u (3 ncell) of a finished request
+ *                       to host buffers (either may be NULL) and forgets it;
+ *                       LBM_EUNSTABLE if the result is not finite
+ *   lbm_server_stats  : queue length, running requests, budget in use, total
+ *                       cell updates advanced
+ * Errors: LBM_EINVAL (bad request, a request larger than the whole budget,
+ * unknown id, result of an unfinished request), LBM_ECUDA.
+ */
+typedef struct lbm_server *lbm_server_handle;
+
+#define LBM_REQ_QUEUED 0
+#define LBM_REQ_RUNNING 1
+#define LBM_REQ_DONE 2
+#define LBM_REQ_FAILED 3
+
+typedef struct {
+    int lattice;        /* LBM_D2Q9 or LBM_D3Q19 */
+    int precision;      /* LBM_FP64 .. LBM_BF16_SHIFTED */
+    int extents[3];     /* extents[2] = 1 for D2Q9 */
+    double tau;         /* > 1/2 */
+    int64_t steps;      /* >= 0 */
+    const double *rho;  /* ncell, host, or NULL for 1 */
+    const double *u;    /* 3 ncell, host, or NULL for 0 */
+} lbm_request;
+
+int lbm_server_create(lbm_server_handle *out, size_t hbm_budget_bytes, int max_slots, void *cuda_stream);
+void lbm_server_destroy(lbm_server_handle s);
+const char *lbm_server_last_error(lbm_server_handle s);
+int lbm_server_submit(lbm_server_handle s, const lbm_request *req, int64_t *id);
+int lbm_server_run(lbm_server_handle s, int64_t steps, int *completed);
+int lbm_server_poll(lbm_server_handle s, int64_t id, int *state, int64_t *steps_done);
+int lbm_server_result(lbm_server_handle s, int64_t id, double *rho, double *u);
+int lbm_server_stats(lbm_server_handle s, int *queued, int *running, size_t *bytes_in_use,
+                     int64_t *cell_updates);
 
 /*
  * lbm_reduce_noalloc -- the totals of lbm_reduce for a population field the

@@ -88,6 +88,7 @@ def lib():
             _lib.orc_update_cells.argtypes = [P, dp, C.c_int64, C.POINTER(C.c_int64), C.c_int64, dp]
             _lib.orc_field_moments.argtypes = [P, dp, dp, dp, dp]
             _lib.orc_init_equilibrium.argtypes = [P, dp, dp, dp]
+            _lib.orc_wall_force.argtypes = [P, dp, dp]
             _lib.orc_chi_at.argtypes = [P, C.c_int, C.c_int, C.c_int]
             _lib.orc_chi_at.restype = C.c_double
             _lib.orc_sigma.argtypes = [C.c_double, C.c_double]
@@ -268,6 +269,14 @@ class Problem:
         s = self._struct()
         lib().orc_field_moments(C.byref(s), _dp(f), _dp(rho), _dp(u), _dp(pn))
         return rho, u.reshape(-1, 3), pn.reshape(-1, 6)
+
+    def wall_force(self, f: np.ndarray) -> np.ndarray:
+        """Momentum-exchange force on the solid cells from the stored field f."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        F = np.zeros(3)
+        s = self._struct()
+        lib().orc_wall_force(C.byref(s), _dp(f), _dp(F))
+        return F
 
     def chi(self, x: int, y: int, z: int = 0) -> float:
         s = self._struct()

@@ -48,6 +48,8 @@
  *       populations are imposed from outside (grid coupling), are not updated.
  *   R9  Inlet noise: counter-based uniform numbers from splitmix64 (Steele,
  *       Lea and Flood 2014) keyed by (seed, step, face cell, component).
+ *   R15 Forces on walls (lift, drag; not printed as a formula in the paper):
+ *       momentum exchange over the bounce-back links.
  */
 #include <math.h>
 #include <stdint.h>
@@ -528,6 +530,39 @@ void orc_init_equilibrium(const orc_problem *P, const double *rho, const double 
         double out[19];
         feqH(L, rho[cell], u + 3 * cell, out);
         for (int i = 0; i < L->q; ++i) f[(int64_t)i * N + cell] = out[i];
+    }
+}
+
+/* Force on the solid cells by momentum exchange over halfway bounce-back
+ * links (reading R15): every fluid cell x and direction i with x + xi_i solid
+ * hands the wall 2 xi_i f*_i(x) per step, f* the stored post-collision
+ * field (the population leaves x towards the wall and comes back reversed). */
+void orc_wall_force(const orc_problem *P, const double *fin, double F[3])
+{
+    const lattice_t *L = lattice(P->lattice);
+    const int64_t N = ncell(P);
+    F[0] = F[1] = F[2] = 0.0;
+    if (!P->solid) return;
+    for (int64_t cell = 0; cell < N; ++cell) {
+        if (P->solid[cell]) continue;
+        int c[3];
+        c[0] = (int)(cell % P->n[0]);
+        c[1] = (int)((cell / P->n[0]) % P->n[1]);
+        c[2] = (int)(cell / ((int64_t)P->n[0] * P->n[1]));
+        for (int i = 1; i < L->q; ++i) {
+            int d[3];
+            int inside = 1;
+            for (int a = 0; a < 3; ++a) {
+                d[a] = c[a] + L->xi[i][a];
+                if (P->face_kind[2 * a] == BC_PERIODIC) d[a] = ((d[a] % P->n[a]) + P->n[a]) % P->n[a];
+                else if (d[a] < 0 || d[a] >= P->n[a]) inside = 0;
+            }
+            if (!inside) continue;
+            int64_t nb = d[0] + (int64_t)P->n[0] * (d[1] + (int64_t)P->n[1] * d[2]);
+            if (P->solid[nb] != 1) continue;
+            double fi = fin[(int64_t)i * N + cell];
+            for (int a = 0; a < 3; ++a) F[a] += 2.0 * L->xi[i][a] * fi;
+        }
     }
 }
 

@@ -153,6 +153,51 @@ static __global__ void k_reduce_final(int nblocks, const double *__restrict__ pa
     if (lane == 0) out[k] = v;
 }
 
+// Momentum-exchange force on solid cells: every fluid cell x and direction i
+// with x + xi_i solid adds 2 xi_i f*_i(x) (halfway bounce-back link).
+// Per-block partials in the reduction layout: [Fx, Fy, Fz, 0, 0, 0].
+template <class L, class S>
+__global__ void __launch_bounds__(RED_BLOCK) k_force(int nx, int ny, int nz, int px, int py, int pz,
+                                                     const S *__restrict__ f, const uint8_t *__restrict__ mask,
+                                                     double *__restrict__ partial)
+{
+    const int64_t N = (int64_t)nx * ny * nz;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < N;
+         cell += (int64_t)gridDim.x * blockDim.x) {
+        if (mask[cell]) continue;
+        const int x = (int)(cell % nx), y = (int)((cell / nx) % ny), z = (int)(cell / ((int64_t)nx * ny));
+#pragma unroll
+        for (int i = 1; i < L::Q; ++i) {
+            int X = x + L::cx(i), Y = y + L::cy(i), Z = z + L::cz(i);
+            if (px) X = X < 0 ? X + nx : (X >= nx ? X - nx : X);
+            if (py) Y = Y < 0 ? Y + ny : (Y >= ny ? Y - ny : Y);
+            if (pz) Z = Z < 0 ? Z + nz : (Z >= nz ? Z - nz : Z);
+            if (X < 0 || X >= nx || Y < 0 || Y >= ny || Z < 0 || Z >= nz) continue;
+            if (mask[X + (int64_t)nx * (Y + (int64_t)ny * Z)] != 1) continue;
+            const double fi = (double)Store<S>::ld(f + (int64_t)i * N + cell) + weight<L>(i);
+            acc[0] += 2.0 * L::cx(i) * fi;
+            acc[1] += 2.0 * L::cy(i) * fi;
+            acc[2] += 2.0 * L::cz(i) * fi;
+        }
+    }
+    __shared__ double sh[RED_BLOCK / 32][3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < RED_FIELDS) {
+        double v = 0.0;
+        if (threadIdx.x < 3)
+            for (int w = 0; w < RED_BLOCK / 32; ++w) v += sh[w][threadIdx.x];
+        partial[(int64_t)blockIdx.x * RED_FIELDS + threadIdx.x] = v;
+    }
+}
+
 template <class L, class S>
 __global__ void k_probe(int n, const int64_t *__restrict__ cells, int64_t N, const S *__restrict__ f,
                         double *__restrict__ rho)

@@ -180,6 +180,19 @@ struct Reduce {
     }
 };
 template <class L, class S>
+struct Force {
+    static cudaError_t run(cudaStream_t st, const int *n, const int *per, const void *f, const uint8_t *mask,
+                           double *partial, int nblocks)
+    {
+        k_force<L, S><<<nblocks, RED_BLOCK, 0, st>>>(n[0], n[1], n[2], per[0], per[1], per[2], (const S *)f, mask,
+                                                      partial);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_reduce_final<<<1, 32 * RED_FIELDS, 0, st>>>(nblocks, partial, partial + (int64_t)nblocks * RED_FIELDS);
+        return cudaGetLastError();
+    }
+};
+template <class L, class S>
 struct Probe {
     static cudaError_t run(cudaStream_t st, int n, const int64_t *cells, int64_t N, const void *f,
                            double *rho)
@@ -267,6 +280,8 @@ extern "C" int lbm_create(lbm_handle *out, int lattice, const int extents[3], do
         return fail(nullptr, LBM_EINVAL, "D2Q9 needs extents[2] == 1");
     if (extents[1] > 65535 || extents[2] > 65535)
         return fail(nullptr, LBM_EINVAL, "extents[1] and extents[2] must be <= 65535");
+    if ((int64_t)extents[0] * extents[1] * extents[2] > 2147483647LL)
+        return fail(nullptr, LBM_EINVAL, "a lattice holds at most 2^31 - 1 cells");
     double tau = value_is_nu ? tau_or_nu * 3.0 + 0.5 : tau_or_nu;
     if (!(tau > 0.5) || !std::isfinite(tau))
         return fail(nullptr, LBM_EINVAL, "tau = %g must be > 1/2 (nu > 0)", tau);
@@ -535,6 +550,7 @@ static int get_pops_grid(lbm_ctx *h, const GridRef &g, double *f)
 }
 
 static int init_line_moments(lbm_ctx *h);
+static int level_ref(lbm_ctx *h, int level, GridRef &g);
 static int moments_grid(lbm_ctx *h, const GridRef &g, double *rho, double *u, double *pi_neq);
 
 extern "C" int lbm_set_state(lbm_handle h, const double *rho, const double *u)
@@ -782,6 +798,31 @@ static int level_ref(lbm_ctx *h, int level, GridRef &g)
         return LBM_OK;
     }
     return fail(h, LBM_EINVAL, "no level %d", level);
+}
+
+extern "C" int lbm_force(lbm_handle h, int level, double F[3])
+{
+    CHECK_HANDLE(h);
+    if (!F) return fail(h, LBM_EINVAL, "F is null");
+    GridRef g;
+    int rc = level_ref(h, level, g);
+    if (rc != LBM_OK) return rc;
+    F[0] = F[1] = F[2] = 0.0;
+    if (!g.mask) return LBM_OK;
+    int per[3] = {1, 1, 1};
+    if (level == 0)
+        for (int a = 0; a < 3; ++a) per[a] = h->kind[2 * a] == LBM_BC_PERIODIC ? 1 : 0;
+    double out[RED_FIELDS];
+    cudaError_t e = dispatch<Force>(h->lattice, h->prec, h->stream, (const int *)g.n, (const int *)per,
+                                    (const void *)g.f[*g.cur], g.mask, h->red_d, h->red_blocks);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, h->red_d + (size_t)h->red_blocks * RED_FIELDS, sizeof out, cudaMemcpyDeviceToHost,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->launches += 2;
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "lbm_force: %s", cudaGetErrorString(e));
+    for (int a = 0; a < 3; ++a) F[a] = out[a];
+    return LBM_OK;
 }
 
 extern "C" int lbm_level_info(lbm_handle h, int level, int extents[3], double *tau)

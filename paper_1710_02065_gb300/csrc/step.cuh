@@ -46,7 +46,21 @@ struct StepParams {
     double omega;  // 1 - 1/tau
     const uint8_t *solid;  // device, or null
     int64_t step;
+    // per-direction base addresses of the lattice read (in) and written (out):
+    // in[i] = f_in + i * ncell elements; filled by the launchers
+    const char *in[19];
+    char *out[19];
 };
+
+// Fill the per-direction base addresses for one launch (host)
+template <class L, class S>
+inline void set_bases(StepParams &p, const void *fin, void *fout)
+{
+    for (int i = 0; i < L::Q; ++i) {
+        p.in[i] = (const char *)fin + (size_t)i * (size_t)p.ncell * sizeof(S);
+        p.out[i] = (char *)fout + (size_t)i * (size_t)p.ncell * sizeof(S);
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Sponge strength chi = chi_max sigma(d), maximum over the layers (Sec. II.C).
@@ -159,48 +173,49 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
 // kernel below and the batched multi-domain kernel.
 // ---------------------------------------------------------------------------
 template <class L, class S, class C>
-__device__ __forceinline__ void update_cell(const StepParams &p, const S *__restrict__ fin, S *__restrict__ fout,
+__device__ __forceinline__ void update_cell(const StepParams &p, const char *const *in, char *const *out,
                                             int x, int y, int z)
 {
-    const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
-    const int64_t N = p.ncell;
-    const int64_t nxy = (int64_t)nx * ny;
-    const int64_t cell = x + (int64_t)nx * y + nxy * z;
+    // 32-bit cell offsets: a lattice holds fewer than 2^31 cells
+    const unsigned nx = p.n[0], ny = p.n[1], nz = p.n[2];
+    const unsigned nxy = nx * ny;
+    const unsigned cell = x + nx * y + nxy * z;
     const uint8_t *__restrict__ solid = p.solid;
     if (solid && solid[cell]) return;  // solid (1) and fixed (2) cells keep their populations
 
     // ---- boundary role and the node whose streamed populations are used
-    int sx = x, sy = y, sz = z, inlet = -1;
+    unsigned sx = x, sy = y, sz = z;
+    int inlet = -1;
     if (!p.periodic[0]) {
         if (x == 0) { sx = 1; if (p.kind[0] == BC_VELOCITY) inlet = 0; }
-        if (x == nx - 1) { sx = nx - 2; if (p.kind[1] == BC_VELOCITY && inlet < 0) inlet = 1; }
+        if (x == (int)nx - 1) { sx = nx - 2; if (p.kind[1] == BC_VELOCITY && inlet < 0) inlet = 1; }
     }
     if (!p.periodic[1]) {
         if (y == 0) { sy = 1; if (p.kind[2] == BC_VELOCITY && inlet < 0) inlet = 2; }
-        if (y == ny - 1) { sy = ny - 2; if (p.kind[3] == BC_VELOCITY && inlet < 0) inlet = 3; }
+        if (y == (int)ny - 1) { sy = ny - 2; if (p.kind[3] == BC_VELOCITY && inlet < 0) inlet = 3; }
     }
     if (L::D == 3 && !p.periodic[2]) {
         if (z == 0) { sz = 1; if (p.kind[4] == BC_VELOCITY && inlet < 0) inlet = 4; }
-        if (z == nz - 1) { sz = nz - 2; if (p.kind[5] == BC_VELOCITY && inlet < 0) inlet = 5; }
+        if (z == (int)nz - 1) { sz = nz - 2; if (p.kind[5] == BC_VELOCITY && inlet < 0) inlet = 5; }
     }
     // neighbour coordinates of s with wrap-around on periodic axes
-    const int xm = sx == 0 ? nx - 1 : sx - 1, xp = sx == nx - 1 ? 0 : sx + 1;
-    const int ym = sy == 0 ? ny - 1 : sy - 1, yp = sy == ny - 1 ? 0 : sy + 1;
-    const int zm = sz == 0 ? nz - 1 : sz - 1, zp = sz == nz - 1 ? 0 : sz + 1;
-    const int64_t scell = sx + (int64_t)nx * sy + nxy * sz;
+    const unsigned xm = sx == 0 ? nx - 1 : sx - 1, xp = sx == nx - 1 ? 0 : sx + 1;
+    const unsigned ym = sy == 0 ? ny - 1 : sy - 1, yp = sy == ny - 1 ? 0 : sy + 1;
+    const unsigned zm = sz == 0 ? nz - 1 : sz - 1, zp = sz == nz - 1 ? 0 : sz + 1;
+    const unsigned scell = sx + nx * sy + nxy * sz;
 
     // ---- streaming (pull) with halfway bounce-back
     C g[L::Q];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        const int X = L::cx(i) > 0 ? xm : (L::cx(i) < 0 ? xp : sx);
-        const int Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
-        const int Z = L::D == 2 ? 0 : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
-        const int64_t src = X + (int64_t)nx * Y + nxy * Z;
+        const unsigned X = L::cx(i) > 0 ? xm : (L::cx(i) < 0 ? xp : sx);
+        const unsigned Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
+        const unsigned Z = L::D == 2 ? 0u : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
+        const unsigned src = X + nx * Y + nxy * Z;
         if (solid && i != 0 && solid[src] == 1)
-            g[i] = Store<S>::ld(fin + (int64_t)opp<L>(i) * N + scell);
+            g[i] = Store<S>::ld((const S *)in[opp<L>(i)] + scell);
         else
-            g[i] = Store<S>::ld(fin + (int64_t)i * N + src);
+            g[i] = Store<S>::ld((const S *)in[i] + src);
     }
 
     const Mom<C> m = moments_pairs<L, C>(g);
@@ -208,25 +223,23 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const S *__rest
     const Coef<C> k = cell_coefficients<L, C>(p, m, chi, x, y, z, inlet);
 
     // ---- rebuild, relax and store (even/odd parts of each opposite pair)
-    Store<S>::st(fout + cell, rebuild_rest<L, C>(k));
+    Store<S>::st((S *)out[0] + cell, rebuild_rest<L, C>(k));
 #pragma unroll
     for (int i = 1; i <= L::HALF; ++i) {
         C e, o;
         rebuild_pair<L, C>(k, i, e, o);
-        Store<S>::st(fout + (int64_t)i * N + cell, C(weight<L>(i)) * (e + o));
-        Store<S>::st(fout + (int64_t)(i + L::HALF) * N + cell, C(weight<L>(i)) * (e - o));
+        Store<S>::st((S *)out[i] + cell, C(weight<L>(i)) * (e + o));
+        Store<S>::st((S *)out[i + L::HALF] + cell, C(weight<L>(i)) * (e - o));
     }
 }
 
 // General kernel: one thread per cell, optional cell-type mask.
 template <class L, class S, class C>
-__global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ StepParams p,
-                                                         const S *__restrict__ fin,
-                                                         S *__restrict__ fout)
+__global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ StepParams p)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.n[0]) return;
-    update_cell<L, S, C>(p, fin, fout, x, blockIdx.y, blockIdx.z);
+    update_cell<L, S, C>(p, p.in, p.out, x, blockIdx.y, blockIdx.z);
 }
 
 // Launch wrapper: one thread per cell, blocks along x.
@@ -234,9 +247,11 @@ template <class L, class S, class C>
 cudaError_t launch_stream_collide(const StepParams &p, const void *fin, void *fout, int block,
                                   cudaStream_t st)
 {
+    StepParams q = p;
+    set_bases<L, S>(q, fin, fout);
     dim3 b(block, 1, 1);
     dim3 g((p.n[0] + block - 1) / block, p.n[1], p.n[2]);
-    k_stream_collide<L, S, C><<<g, b, 0, st>>>(p, (const S *)fin, (S *)fout);
+    k_stream_collide<L, S, C><<<g, b, 0, st>>>(q);
     return cudaGetLastError();
 }
 

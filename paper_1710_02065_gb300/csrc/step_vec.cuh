@@ -135,9 +135,7 @@ struct VecIO<__nv_bfloat16, 4> {
 // Requires: no cell-type mask, nx % V == 0.
 // ---------------------------------------------------------------------------
 template <class L, class S, class C, int V>
-__global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constant__ StepParams p,
-                                                             const S *__restrict__ fin,
-                                                             S *__restrict__ fout)
+__global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constant__ StepParams p)
 {
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
     const int lane = threadIdx.x & 31;
@@ -145,8 +143,7 @@ __global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constan
     const bool active = x0raw < nx;
     const int x0 = x0raw % nx;  // idle lanes load a wrapped, valid vector
     const int y = blockIdx.y, z = blockIdx.z;
-    const int64_t N = p.ncell;
-    const int64_t nxy = (int64_t)nx * ny;
+    const unsigned nxy = (unsigned)nx * ny;
 
     // rows streamed from (uniform per thread): inward neighbour on non-periodic y/z faces
     int sy = y, sz = z, inlet_row = -1;
@@ -169,7 +166,7 @@ __global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constan
     for (int i = 0; i < L::Q; ++i) {
         const int Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
         const int Z = L::D == 2 ? 0 : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
-        const S *row = fin + (int64_t)i * N + (int64_t)nx * Y + nxy * Z;
+        const S *row = (const S *)p.in[i] + ((unsigned)nx * Y + nxy * Z);
         C v[V];
         VecIO<S, V>::ld(row + x0, v);
         if (L::cx(i) == 0) {
@@ -221,12 +218,12 @@ __global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constan
     }
 
     // ---- rebuild and store, one direction pair at a time
-    const int64_t base = (int64_t)nx * y + nxy * z + x0;
+    const unsigned base = (unsigned)nx * y + nxy * z + x0;
     {
         C o[V];
 #pragma unroll
         for (int k = 0; k < V; ++k) o[k] = rebuild_rest<L, C>(cf[k]);
-        VecIO<S, V>::st(fout + base, o);
+        VecIO<S, V>::st((S *)p.out[0] + base, o);
     }
 #pragma unroll
     for (int i = 1; i <= L::HALF; ++i) {
@@ -238,8 +235,8 @@ __global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constan
             op[k] = C(weight<L>(i)) * (e + o);
             om[k] = C(weight<L>(i)) * (e - o);
         }
-        VecIO<S, V>::st(fout + (int64_t)i * N + base, op);
-        VecIO<S, V>::st(fout + (int64_t)(i + L::HALF) * N + base, om);
+        VecIO<S, V>::st((S *)p.out[i] + base, op);
+        VecIO<S, V>::st((S *)p.out[i + L::HALF] + base, om);
     }
 }
 
@@ -251,7 +248,9 @@ cudaError_t launch_stream_collide_vec(const StepParams &p, const void *fin, void
     const int b = block < threads_per_row ? block : threads_per_row;
     dim3 bd(b, 1, 1);
     dim3 g((p.n[0] / V + b - 1) / b, p.n[1], p.n[2]);
-    k_stream_collide_vec<L, S, C, V><<<g, bd, 0, st>>>(p, (const S *)fin, (S *)fout);
+    StepParams q = p;
+    set_bases<L, S>(q, fin, fout);
+    k_stream_collide_vec<L, S, C, V><<<g, bd, 0, st>>>(q);
     return cudaGetLastError();
 }
 

@@ -134,3 +134,39 @@ def random_populations(weights: np.ndarray, ncell: int, seed: int, spread: float
     r = rng.random((len(weights), ncell))
     return np.asarray(weights)[:, None] * (1.0 + spread * (2.0 * r - 1.0))
 
+
+def serving_requests(n: int = 512, seed: int = 5, rate_per_s: float = 8.0, steps_scale: float = 1.0,
+                     sizes_2d=(64, 128, 256, 512, 1024), sizes_3d=(32, 48, 64, 96, 128, 192)):
+    """Seeded stream of independent solve requests.
+
+    Arrivals are a Poisson process of the given rate; half of the requests are
+    D2Q9 periodic acoustic pulses of N^2 cells, half D3Q19 Taylor-Green
+    vortices of N^3 cells (N uniform over the given sets), tau ~ U[0.52, 0.9],
+    steps ~ U{500..5000} (times steps_scale), storage FP32 or FP16 50/50.
+    Returns a list of dicts sorted by arrival time.
+    """
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+    out = []
+    for k in range(n):
+        is2d = rng.random() < 0.5
+        N = int(rng.choice(sizes_2d if is2d else sizes_3d))
+        steps = int(rng.integers(500, 5001))
+        out.append({
+            "arrival": float(t[k]),
+            "lattice": 0 if is2d else 1,
+            "extents": (N, N, 1) if is2d else (N, N, N),
+            "tau": float(rng.uniform(0.52, 0.9)),
+            "steps": max(1, int(round(steps * steps_scale))),
+            "precision": 1 if rng.random() < 0.5 else 2,
+        })
+    return out
+
+
+def request_initial_state(req: dict):
+    """(rho, u) of a request: a Gaussian pulse (amplitude 1e-3, half-width N/20)
+    on a fluid at rest in 2D, a Taylor-Green vortex (U0 = 0.02) in 3D."""
+    N = req["extents"][0]
+    if req["lattice"] == 0:
+        return gaussian_pulse_2d(N, 1e-3, max(2.0, N / 20.0), (0.0, 0.0))
+    return taylor_green_3d(N, 0.02)

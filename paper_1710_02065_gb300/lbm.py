@@ -66,12 +66,26 @@ _sig("lbm_set_launch", [_h, C.c_int, C.c_int])
 _sig("lbm_get_launch", [_h, _ip, _ip])
 _sig("lbm_info", [_h, _i64p, _i64p, _dp, _dp])
 _sig("lbm_add_refinement_patch", [_h, _ip, _ip])
+_sig("lbm_force", [_h, C.c_int, _dp])
 _sig("lbm_level_info", [_h, C.c_int, _ip, _dp])
 _sig("lbm_set_geometry_level", [_h, C.c_int, C.POINTER(C.c_uint8)])
 _sig("lbm_set_state_level", [_h, C.c_int, _dp, _dp])
 _sig("lbm_set_populations_level", [_h, C.c_int, _dp])
 _sig("lbm_get_populations_level", [_h, C.c_int, _dp])
 _sig("lbm_moments_level", [_h, C.c_int, _dp, _dp, _dp])
+class lbm_request(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("precision", C.c_int), ("extents", C.c_int * 3), ("tau", C.c_double),
+                ("steps", C.c_int64), ("rho", _dp), ("u", _dp)]
+
+
+_sig("lbm_server_create", [C.POINTER(C.c_void_p), C.c_size_t, C.c_int, C.c_void_p])
+_sig("lbm_server_destroy", [C.c_void_p], None)
+_sig("lbm_server_last_error", [C.c_void_p], C.c_char_p)
+_sig("lbm_server_submit", [C.c_void_p, C.POINTER(lbm_request), _i64p])
+_sig("lbm_server_run", [C.c_void_p, C.c_int64, _ip])
+_sig("lbm_server_poll", [C.c_void_p, C.c_int64, _ip, _i64p])
+_sig("lbm_server_result", [C.c_void_p, C.c_int64, _dp, _dp])
+_sig("lbm_server_stats", [C.c_void_p, _ip, _ip, C.POINTER(C.c_size_t), _i64p])
 _sig("lbm_reduce_noalloc", [C.c_int, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p])
 _sig("lbm_save", [_h, C.c_char_p])
 _sig("lbm_load", [_h, C.c_char_p])
@@ -81,10 +95,12 @@ EXPORTED = [
     "lbm_set_boundary", "lbm_set_inlet_noise", "lbm_set_sponge", "lbm_set_state",
     "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_moments", "lbm_reduce",
     "lbm_probe", "lbm_sync", "lbm_info", "lbm_save", "lbm_load", "lbm_set_launch", "lbm_get_launch",
-    "lbm_add_refinement_patch", "lbm_level_info", "lbm_set_geometry_level", "lbm_set_state_level",
+    "lbm_add_refinement_patch", "lbm_level_info", "lbm_force", "lbm_set_geometry_level", "lbm_set_state_level",
     "lbm_set_populations_level", "lbm_get_populations_level", "lbm_moments_level",
-    "lbm_reduce_noalloc",
+    "lbm_reduce_noalloc", "lbm_server_create", "lbm_server_destroy", "lbm_server_last_error",
+    "lbm_server_submit", "lbm_server_run", "lbm_server_poll", "lbm_server_result", "lbm_server_stats",
 ]
+LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_DONE, LBM_REQ_FAILED = 0, 1, 2, 3
 
 
 class LBMError(RuntimeError):
@@ -237,6 +253,12 @@ def lbm_add_refinement_patch(h, origin, extent):
     return _check(_lib.lbm_add_refinement_patch(h, o, e), h)
 
 
+def lbm_force(h, level: int = 0) -> np.ndarray:
+    F = np.zeros(3)
+    _check(_lib.lbm_force(h, level, _d(F)), h)
+    return F
+
+
 def lbm_level_info(h, level: int):
     e = (C.c_int * 3)()
     t = C.c_double()
@@ -276,6 +298,68 @@ def lbm_reduce_noalloc(lattice: int, precision: int, f_dev: int, ncell: int, cel
     return _check(_lib.lbm_reduce_noalloc(lattice, precision, C.c_void_p(f_dev), C.c_int64(int(ncell)),
                                           C.c_void_p(cell_type_dev or 0), C.c_void_p(out_dev),
                                           C.c_void_p(cuda_stream or 0)), None)
+
+
+def _scheck(rc: int, s):
+    if rc != LBM_OK:
+        msg = _lib.lbm_server_last_error(s)
+        raise LBMError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def lbm_server_create(hbm_budget_bytes: int, max_slots: int, cuda_stream: int | None = None):
+    s = C.c_void_p()
+    rc = _lib.lbm_server_create(C.byref(s), C.c_size_t(int(hbm_budget_bytes)), int(max_slots),
+                                C.c_void_p(cuda_stream or 0))
+    _check(rc, None)
+    return s
+
+
+def lbm_server_destroy(s):
+    _lib.lbm_server_destroy(s)
+
+
+def lbm_server_last_error(s) -> str:
+    m = _lib.lbm_server_last_error(s)
+    return m.decode() if m else ""
+
+
+def lbm_server_submit(s, lattice: int, precision: int, extents, tau: float, steps: int, rho=None, u=None) -> int:
+    ext = list(extents) + [1] * (3 - len(extents))
+    r = _c64(rho)
+    v = _c64(u)
+    req = lbm_request(lattice, precision, (C.c_int * 3)(*[int(e) for e in ext]), float(tau), int(steps),
+                      _d(r.reshape(-1)) if r is not None else None, _d(v.reshape(-1)) if v is not None else None)
+    rid = C.c_int64()
+    _scheck(_lib.lbm_server_submit(s, C.byref(req), C.byref(rid)), s)
+    return rid.value
+
+
+def lbm_server_run(s, steps: int) -> int:
+    done = C.c_int()
+    _scheck(_lib.lbm_server_run(s, C.c_int64(int(steps)), C.byref(done)), s)
+    return done.value
+
+
+def lbm_server_poll(s, rid: int):
+    st, d = C.c_int(), C.c_int64()
+    _scheck(_lib.lbm_server_poll(s, C.c_int64(rid), C.byref(st), C.byref(d)), s)
+    return st.value, d.value
+
+
+def lbm_server_result(s, rid: int, rho=None, u=None):
+    rc = _lib.lbm_server_result(s, C.c_int64(rid), _d(rho), _d(u))
+    if rc not in (LBM_OK, LBM_EUNSTABLE):
+        _scheck(rc, s)
+    return rc
+
+
+def lbm_server_stats(s):
+    q, r = C.c_int(), C.c_int()
+    b = C.c_size_t()
+    cu = C.c_int64()
+    _scheck(_lib.lbm_server_stats(s, C.byref(q), C.byref(r), C.byref(b), C.byref(cu)), s)
+    return {"queued": q.value, "running": r.value, "bytes_in_use": b.value, "cell_updates": cu.value}
 
 
 # ---------------------------------------------------------------------------

@@ -167,6 +167,11 @@ def test_cylinder_scaled_parity(prec, tol):
     fluid = c.solid == 0
     assert _normwise(r[fluid], r_ref[fluid]) <= tol
     assert _normwise(u[fluid], u_ref[fluid]) <= tol
+    # momentum-exchange force on the cylinder
+    from paper_1710_02065_gb300 import lbm
+    F = lbm.lbm_force(s.h, 0)
+    F_ref = P.wall_force(f)
+    assert np.abs(F - F_ref).max() <= tol * np.abs(F_ref).max() * 10
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])

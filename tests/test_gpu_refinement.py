@@ -73,6 +73,9 @@ def test_two_level_cylinder_parity(prec, tol):
     assert _normwise(guc[live], uc[live]) <= tol
     assert _normwise(grf[fluid_f], rf[fluid_f]) <= tol
     assert _normwise(guf[fluid_f], uf[fluid_f]) <= tol
+    F = lbm.lbm_force(s.h, 1)
+    F_ref = T.Pf.wall_force(T.ff)
+    assert np.abs(F - F_ref).max() <= tol * np.abs(F_ref).max() * 10
 
 
 def test_two_level_uniform_stream_exact():

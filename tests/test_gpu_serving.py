@@ -1,0 +1,125 @@
+"""The solve server: continuous batching of independent solves.
+
+  * a request's result is bitwise the same alone and batched with others
+    (its arithmetic does not depend on the mix)
+  * results equal the oracle within the parity tolerances (FP64 1e-12,
+    FP32 1e-5 normwise in rho and u); for a pulse at rest |u| is ~1e-5, so
+    u also passes when its absolute error is below the round-off of O(1)
+    populations in that precision (FP64 1e-13, FP32 1e-8)
+  * admission respects the HBM budget: a request that does not fit waits
+    and runs once memory is returned
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_02065_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def serving():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_02065_gb300 import build
+    build.build()
+    from paper_1710_02065_gb300 import serving as mod
+    return mod
+
+
+def _req(lattice, N, tau, steps, prec):
+    ext = (N, N, 1) if lattice == 0 else (N, N, N)
+    return {"arrival": 0.0, "lattice": lattice, "extents": ext, "tau": tau, "steps": steps, "precision": prec}
+
+
+def _run(serving, reqs, budget=1 << 30, rounds_steps=7):
+    srv = serving.Server(budget, 64)
+    ids = []
+    for r in reqs:
+        rho, u = inputs.request_initial_state(r)
+        ids.append(srv.submit(r, rho, u))
+    out = {}
+    for _ in range(10000):
+        srv.run(rounds_steps)
+        for k, rid in enumerate(ids):
+            if k in out:
+                continue
+            st, done = srv.poll(rid)
+            if st in (2, 3):
+                out[k] = srv.result(rid, int(np.prod(reqs[k]["extents"])))
+        if len(out) == len(ids):
+            break
+    srv.close()
+    return out
+
+
+def test_result_is_the_same_alone_and_in_a_mix(serving):
+    a = _req(0, 64, 0.61, 150, 1)
+    alone = _run(serving, [a])[0]
+    mix = [_req(1, 24, 0.7, 90, 2), a, _req(0, 40, 0.55, 33, 0), _req(1, 16, 0.9, 200, 1),
+           _req(0, 128, 0.8, 10, 2)]
+    batched = _run(serving, mix)
+    for k in range(len(mix)):
+        assert batched[k][2] == 0
+    assert np.array_equal(alone[0], batched[1][0])
+    assert np.array_equal(alone[1], batched[1][1])
+
+
+@pytest.mark.parametrize("lattice,N,prec,tol,floor", [(0, 32, 0, 1e-12, 1e-13), (0, 48, 1, 1e-5, 1e-8),
+                                                      (1, 12, 0, 1e-12, 1e-13), (1, 16, 1, 1e-5, 1e-8)])
+def test_served_results_match_oracle(serving, lattice, N, prec, tol, floor):
+    r = _req(lattice, N, 0.66, 40, prec)
+    rho_g, u_g, rc = _run(serving, [r])[0]
+    assert rc == 0
+    rho0, u0 = inputs.request_initial_state(r)
+    P = oracle.Problem(lattice, r["extents"], r["tau"])
+    f = P.run(P.equilibrium(rho0, u0), r["steps"])
+    rho, u, _ = P.moments(f)
+    assert np.linalg.norm(rho_g - rho) / np.linalg.norm(rho) <= tol
+    du = u_g - u
+    assert np.linalg.norm(du) / np.linalg.norm(u) <= tol or np.abs(du).max() <= floor
+
+
+def test_admission_waits_for_budget(serving):
+    big = _req(1, 32, 0.7, 60, 1)            # 2 * 19 * 32^3 * 4 B = 4.98 MB
+    budget = int(2 * 19 * 32 ** 3 * 4 * 1.5)  # room for one at a time
+    srv = serving.Server(budget, 8)
+    ids = []
+    for _ in range(3):
+        rho, u = inputs.request_initial_state(big)
+        ids.append(srv.submit(big, rho, u))
+    srv.run(10)
+    states = [srv.poll(i)[0] for i in ids]
+    assert states.count(1) == 1 and states.count(0) == 2
+    assert srv.stats()["bytes_in_use"] <= budget
+    finished = set()
+    for _ in range(100):
+        srv.run(10)
+        for i in ids:
+            if i not in finished and srv.poll(i)[0] == 2:
+                finished.add(i)
+                srv.result(i, 32 ** 3)
+        if len(finished) == 3:
+            break
+    assert len(finished) == 3
+    srv.close()
+
+
+def test_zero_step_request_returns_initial_state(serving):
+    r = _req(0, 16, 0.7, 0, 0)
+    rho, u, rc = _run(serving, [r])[0]
+    rho0, u0 = inputs.request_initial_state(r)
+    assert rc == 0
+    assert np.abs(rho - rho0).max() < 1e-15
+
+
+def test_serving_stream_small(serving):
+    """A short stream with overlapping arrivals completes with sane statistics."""
+    reqs = inputs.serving_requests(12, seed=1, rate_per_s=200.0, steps_scale=0.02, sizes_2d=(64, 128),
+                                   sizes_3d=(16, 24))
+    out = serving.serve(reqs, hbm_budget_bytes=64 << 20, max_slots=8, steps_per_round=10)
+    assert out["requests"] == 12 and out["failed"] == 0
+    assert out["tts_p99_s"] >= out["tts_p50_s"] > 0
+    assert out["aggregate_mlups"] > 0

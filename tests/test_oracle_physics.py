@@ -193,3 +193,31 @@ def test_inlet_noise_statistics():
     assert np.abs(dv).max() <= amp * U * (1 + 1e-12)
     assert abs(dv.mean()) < 0.2 * amp * U
     assert dv.std() > 0.4 * amp * U  # uniform on [-a, a] has std a/sqrt(3)
+
+
+def test_wall_force_balances_body_force_in_poiseuille():
+    """Steady channel flow: the walls take exactly the momentum the body force
+    puts in, F_wall = g * (fluid mass), by momentum exchange on the links."""
+    H, tau, g = 16, 0.8, 2e-6
+    nx, ny = 3, H + 2
+    P = oracle.Problem(D2Q9, (nx, ny), tau)
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0, :] = 1
+    solid[-1, :] = 1
+    P.solid = solid.reshape(-1)
+    P.g = [g, 0.0, 0.0]
+    f = P.equilibrium(np.ones(nx * ny), np.zeros((nx * ny, 3)))
+    f = P.run(f, 6000)
+    F = P.wall_force(f)
+    fluid = solid.reshape(-1) == 0
+    mass = f[:, fluid].sum()
+    assert abs(F[0] - g * mass) / (g * mass) < 1e-6
+    assert abs(F[1]) < 1e-12 * g * mass * 1e6
+
+
+def test_wall_force_zero_at_rest_and_symmetric_for_uniform_obstacle():
+    P = oracle.Problem(D2Q9, (30, 20), 0.7)
+    P.solid = inputs.cylinder_mask(30, 20, 15, 10, 6)
+    f = P.equilibrium(np.ones(P.ncell), np.zeros((P.ncell, 3)))
+    F = P.wall_force(f)
+    assert np.abs(F).max() < 1e-14
