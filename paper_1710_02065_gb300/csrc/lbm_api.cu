@@ -608,6 +608,7 @@ static int build_params(lbm_ctx *h, StepParams &p)
     p.noise_amp = h->noise_amp;
     p.omega = 1.0 - 1.0 / h->tau;
     p.solid = h->solid_d;
+    set_bulk_box(p);
     return LBM_OK;
 }
 
@@ -640,6 +641,7 @@ static void fine_params(lbm_ctx *h, StepParams &p)
     p.rho_ref = 1.0;
     p.omega = 1.0 - 1.0 / F->tau;
     p.solid = F->mask_d;
+    set_bulk_box(p);
 }
 
 template <class S>

@@ -285,6 +285,7 @@ static int admit(lbm_server *s)
         for (int f = 0; f < 6; ++f) d.p.face_cells[f] = 1;
         d.p.rho_ref = 1.0;
         d.p.omega = 1.0 - 1.0 / r->tau;
+        set_bulk_box(d.p);
         d.f[0] = r->f[0];
         d.f[1] = r->f[1];
         for (int b = 0; b < 2; ++b)

@@ -368,6 +368,11 @@ __device__ __forceinline__ C rebuild_rest(const Coef<C> &k)
     return C(weight<L>(0)) * (k.a0 - C(1.5) * tr);
 }
 
+// Reciprocal used for 1 / rho: the fast single-precision division intrinsic
+// in FP32 (a few ulp; the FP32 path's tolerance is 1e-5), IEEE in FP64.
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 // splitmix64 (Steele, Lea and Flood 2014): counter-based uniform in [0, 1)
 __device__ __forceinline__ double u01(uint64_t x)
 {

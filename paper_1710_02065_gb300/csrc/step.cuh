@@ -46,11 +46,30 @@ struct StepParams {
     double omega;  // 1 - 1/tau
     const uint8_t *solid;  // device, or null
     int64_t step;
+    // bulk box: cells with blo[a] <= c[a] < bhi[a] on every axis have no
+    // boundary role and no sponge (filled by the host from faces and layers)
+    int blo[3], bhi[3];
     // per-direction base addresses of the lattice read (in) and written (out):
     // in[i] = f_in + i * ncell elements; filled by the launchers
     const char *in[19];
     char *out[19];
 };
+
+// Bulk box of a lattice (host): on each axis the coordinates that are neither
+// on a non-periodic face nor inside a sponge layer of that axis.
+inline void set_bulk_box(StepParams &p)
+{
+    for (int a = 0; a < 3; ++a) {
+        int lo = p.periodic[a] ? 0 : 1, hi = p.periodic[a] ? p.n[a] : p.n[a] - 1;
+        if (p.any_sponge) {
+            if (p.sponge_w[2 * a] > 0 && p.sponge_chi[2 * a] > 0.0 && p.sponge_w[2 * a] > lo) lo = p.sponge_w[2 * a];
+            if (p.sponge_w[2 * a + 1] > 0 && p.sponge_chi[2 * a + 1] > 0.0 && p.n[a] - p.sponge_w[2 * a + 1] < hi)
+                hi = p.n[a] - p.sponge_w[2 * a + 1];
+        }
+        p.blo[a] = lo;
+        p.bhi[a] = hi > lo ? hi : lo;
+    }
+}
 
 // Fill the per-direction base addresses for one launch (host)
 template <class L, class S>
@@ -117,7 +136,7 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
     if (inlet >= 0) {
         // velocity node: rho, Pi^neq from the streamed neighbour, prescribed u (+ noise)
         const C rho = C(1) + m.dr;
-        const C inv = C(1) / rho;
+        const C inv = recip(rho);
         const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, m.jx * inv, m.jy * inv, m.jz * inv, L::D);
         const int a = inlet >> 1;
         const int t0c = a == 0 ? cy : cx, t1c = a == 2 ? cy : cz;
@@ -148,7 +167,7 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
         const C rr = C(p.rho_ref);
         const C drs = (m.dr + C(0.5) * chi * C(p.rho_ref_m1)) * h;  // rho* - 1
         const C rs = C(1) + drs;
-        const C inv = C(1) / rs;
+        const C inv = recip(rs);
         const C ux = (m.jx + C(0.5) * chi * rr * C(p.u_ref[0])) * h * inv;
         const C uy = (m.jy + C(0.5) * chi * rr * C(p.u_ref[1])) * h * inv;
         const C uz = L::D == 3 ? (m.jz + C(0.5) * chi * rr * C(p.u_ref[2])) * h * inv : C(0);
@@ -159,7 +178,7 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
         return k;
     }
     const C rho = C(1) + m.dr;
-    const C inv = C(1) / rho;
+    const C inv = recip(rho);
     const C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
     const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
     add_eq<C>(k, C(1), m.dr, rho, ux, uy, uz);
@@ -186,6 +205,9 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     // ---- boundary role and the node whose streamed populations are used
     unsigned sx = x, sy = y, sz = z;
     int inlet = -1;
+    const bool bulk = x >= p.blo[0] && x < p.bhi[0] && y >= p.blo[1] && y < p.bhi[1] && z >= p.blo[2] &&
+                      z < p.bhi[2];
+    if (!bulk) {
     if (!p.periodic[0]) {
         if (x == 0) { sx = 1; if (p.kind[0] == BC_VELOCITY) inlet = 0; }
         if (x == (int)nx - 1) { sx = nx - 2; if (p.kind[1] == BC_VELOCITY && inlet < 0) inlet = 1; }
@@ -197,6 +219,7 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     if (L::D == 3 && !p.periodic[2]) {
         if (z == 0) { sz = 1; if (p.kind[4] == BC_VELOCITY && inlet < 0) inlet = 4; }
         if (z == (int)nz - 1) { sz = nz - 2; if (p.kind[5] == BC_VELOCITY && inlet < 0) inlet = 5; }
+    }
     }
     // neighbour coordinates of s with wrap-around on periodic axes
     const unsigned xm = sx == 0 ? nx - 1 : sx - 1, xp = sx == nx - 1 ? 0 : sx + 1;
@@ -219,7 +242,7 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     }
 
     const Mom<C> m = moments_pairs<L, C>(g);
-    const C chi = inlet >= 0 ? C(0) : chi_cell<L, C>(p, chi_row<L, C>(p, y, z), x);
+    const C chi = (bulk || inlet >= 0) ? C(0) : chi_cell<L, C>(p, chi_row<L, C>(p, y, z), x);
     const Coef<C> k = cell_coefficients<L, C>(p, m, chi, x, y, z, inlet);
 
     // ---- rebuild, relax and store (even/odd parts of each opposite pair)

@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constan
     }
 
     // ---- collision coefficients of the V cells
-    const C chirow = chi_row<L, C>(p, y, z);
+    const bool bulk_row = y >= p.blo[1] && y < p.bhi[1] && z >= p.blo[2] && z < p.bhi[2];
+    const C chirow = bulk_row ? C(0) : chi_row<L, C>(p, y, z);
     Coef<C> cf[V];
 #pragma unroll
     for (int k = 0; k < V; ++k) {
@@ -213,7 +214,8 @@ __global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constan
         if (k == 0 && xlo && p.kind[0] == BC_VELOCITY) inlet = 0;
         else if (k == V - 1 && xhi && p.kind[1] == BC_VELOCITY) inlet = 1;
         if (inlet < 0) inlet = inlet_row;
-        const C chi = inlet >= 0 ? C(0) : chi_cell<L, C>(p, chirow, x0 + k);
+        const bool bulk = bulk_row && x0 + k >= p.blo[0] && x0 + k < p.bhi[0];
+        const C chi = (bulk || inlet >= 0) ? C(0) : chi_cell<L, C>(p, chirow, x0 + k);
         cf[k] = cell_coefficients<L, C>(p, m, chi, x0 + k, y, z, inlet);
     }
 
