@@ -56,6 +56,13 @@ struct lbm_ctx {
     int red_blocks = 0;
     std::vector<uint8_t> user_mask;  // caller's cell types (host copy); empty: none
     FineLevel *fine = nullptr;       // two-level grid, or null
+    // graph of two steps (the parity period) replayed by lbm_step; valid for
+    // one configuration version and parity
+    int64_t cfg_version = 0;
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_version = -1;
+    int graph_cur = -1, graph_mcur = -1;
+    int64_t graph_launches = 0;
     std::string err;
 };
 
@@ -254,6 +261,7 @@ static void release(lbm_ctx *h)
     for (int k = 0; k < 6; ++k)
         if (h->prof_d[k]) cudaFree(h->prof_d[k]);
     if (h->red_d) cudaFree(h->red_d);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->fine) {
         for (int k = 0; k < 2; ++k) {
             if (h->fine->f[k]) cudaFree(h->fine->f[k]);
@@ -393,6 +401,7 @@ static int check_cell_types(lbm_ctx *h, const uint8_t *t, int64_t n)
 extern "C" int lbm_set_geometry(lbm_handle h, const uint8_t *cell_type)
 {
     CHECK_HANDLE(h);
+    h->cfg_version++;
     if (cell_type) {
         int rc = check_cell_types(h, cell_type, h->ncell);
         if (rc != LBM_OK) return rc;
@@ -414,6 +423,7 @@ extern "C" int lbm_set_boundary(lbm_handle h, int face, int kind, const double u
                                 const double *u_profile)
 {
     CHECK_HANDLE(h);
+    h->cfg_version++;
     if (face < 0 || face > 5) return fail(h, LBM_EINVAL, "face %d out of range", face);
     if (kind < LBM_BC_PERIODIC || kind > LBM_BC_OUTFLOW) return fail(h, LBM_EINVAL, "unknown boundary kind %d", kind);
     if (h->d == 2 && face >= 4 && kind != LBM_BC_PERIODIC)
@@ -443,6 +453,7 @@ extern "C" int lbm_set_boundary(lbm_handle h, int face, int kind, const double u
 extern "C" int lbm_set_inlet_noise(lbm_handle h, uint64_t seed, double amplitude)
 {
     CHECK_HANDLE(h);
+    h->cfg_version++;
     if (!(amplitude >= 0.0) || !std::isfinite(amplitude))
         return fail(h, LBM_EINVAL, "noise amplitude %g must be finite and >= 0", amplitude);
     if (seed >= (1ull << 32)) return fail(h, LBM_EINVAL, "noise seed must be < 2^32");
@@ -455,6 +466,7 @@ extern "C" int lbm_set_sponge(lbm_handle h, int face, int width, double chi_max,
                               const double u_ref[3])
 {
     CHECK_HANDLE(h);
+    h->cfg_version++;
     if (face < 0 || face > 5) return fail(h, LBM_EINVAL, "face %d out of range", face);
     if (h->d == 2 && face >= 4 && width != 0) return fail(h, LBM_EINVAL, "2D lattice: no z sponge");
     if (width < 0 || width > h->n[face / 2])
@@ -697,16 +709,9 @@ static int init_line_moments(lbm_ctx *h)
     return LBM_OK;
 }
 
-extern "C" int lbm_step(lbm_handle h, int64_t n)
+// Enqueue n steps (single level, or coarse steps of the two-level grid).
+static int enqueue_steps(lbm_ctx *h, StepParams &p, StepParams &pf, int64_t n)
 {
-    CHECK_HANDLE(h);
-    if (n < 0) return fail(h, LBM_EINVAL, "n = %lld < 0", (long long)n);
-    if (n == 0) return LBM_OK;
-    StepParams p;
-    int rc = build_params(h, p);
-    if (rc != LBM_OK) return rc;
-    StepParams pf;
-    if (h->fine) fine_params(h, pf);
     for (int64_t t = 0; t < n; ++t) {
         p.step = h->step;
         cudaError_t e = cudaSuccess;
@@ -746,12 +751,81 @@ extern "C" int lbm_step(lbm_handle h, int64_t n)
     return LBM_OK;
 }
 
+// Capture two steps into a graph for the current configuration and parity.
+// The host-side counters advanced by the capture are restored: the captured
+// work runs only when the graph is launched.
+static int capture_pair(lbm_ctx *h, StepParams &p, StepParams &pf)
+{
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    const int cur = h->cur, fcur = h->fine ? h->fine->cur : 0, mcur = h->fine ? h->fine->mcur : 0;
+    const int64_t step = h->step, launches = h->launches;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_steps(h, p, pf, 2);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    const int64_t per_pair = h->launches - launches;
+    h->cur = cur;
+    h->step = step;
+    h->launches = launches;
+    if (h->fine) {
+        h->fine->cur = fcur;
+        h->fine->mcur = mcur;
+    }
+    if (rc != LBM_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc != LBM_OK ? rc : fail(h, LBM_ECUDA, "capturing steps: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "instantiating steps: %s", cudaGetErrorString(e));
+    h->graph_version = h->cfg_version;
+    h->graph_cur = cur;
+    h->graph_mcur = mcur;
+    h->graph_launches = per_pair;
+    return LBM_OK;
+}
+
+extern "C" int lbm_step(lbm_handle h, int64_t n)
+{
+    CHECK_HANDLE(h);
+    if (n < 0) return fail(h, LBM_EINVAL, "n = %lld < 0", (long long)n);
+    if (n == 0) return LBM_OK;
+    StepParams p;
+    int rc = build_params(h, p);
+    if (rc != LBM_OK) return rc;
+    StepParams pf;
+    if (h->fine) fine_params(h, pf);
+    // Without inlet noise every step of a pair has the same parameters, so
+    // pairs of steps are replayed from a captured graph (needs a stream other
+    // than the legacy default one).
+    if (h->stream && h->noise_amp == 0.0 && n >= 2) {
+        const int mcur = h->fine ? h->fine->mcur : 0;
+        if (!h->graph || h->graph_version != h->cfg_version || h->graph_cur != h->cur || h->graph_mcur != mcur) {
+            rc = capture_pair(h, p, pf);
+            if (rc != LBM_OK) return rc;
+        }
+        for (int64_t k = 0; k < n / 2; ++k) {
+            cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+            if (e != cudaSuccess) return fail(h, LBM_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+        }
+        h->step += 2 * (n / 2);
+        h->launches += h->graph_launches * (n / 2);
+        n -= 2 * (n / 2);
+    }
+    return enqueue_steps(h, p, pf, n);
+}
+
 // ---------------------------------------------------------------------------
 // Two-level grid
 // ---------------------------------------------------------------------------
 extern "C" int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const int extent[3])
 {
     CHECK_HANDLE(h);
+    h->cfg_version++;
     if (h->fine) return fail(h, LBM_EINVAL, "the handle already has a refinement patch");
     if (h->lattice != LBM_D2Q9) return fail(h, LBM_EINVAL, "refinement patches are implemented for D2Q9");
     if (!origin || !extent) return fail(h, LBM_EINVAL, "origin and extent are required");
@@ -842,6 +916,7 @@ extern "C" int lbm_level_info(lbm_handle h, int level, int extents[3], double *t
 extern "C" int lbm_set_geometry_level(lbm_handle h, int level, const uint8_t *cell_type)
 {
     CHECK_HANDLE(h);
+    h->cfg_version++;
     if (level == 0) return lbm_set_geometry(h, cell_type);
     GridRef g;
     int rc = level_ref(h, level, g);
@@ -900,6 +975,7 @@ extern "C" int lbm_moments_level(lbm_handle h, int level, double *rho, double *u
 extern "C" int lbm_set_launch(lbm_handle h, int block, int cells_per_thread)
 {
     CHECK_HANDLE(h);
+    h->cfg_version++;
     if (block != 0 && (block < 32 || block > 256 || block % 32 != 0))
         return fail(h, LBM_EINVAL, "block = %d must be 0 or a multiple of 32 in [32, 256]", block);
     if (cells_per_thread != 0 && cells_per_thread != 1 && !vec_supported(h->prec, cells_per_thread))

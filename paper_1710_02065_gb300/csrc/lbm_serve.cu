@@ -42,30 +42,40 @@ struct Request {
     void *f[2] = {nullptr, nullptr};
 };
 
-constexpr int NGROUPS = 8;  // lattice (2) x precision (4)
-inline int group_of(int lattice, int prec) { return lattice * 4 + prec; }
+// groups: lattice (2) x precision (4) x cells per lane (1, 2)
+constexpr int NGROUPS = 16;
+inline int lanes_v(int prec, int nx) { return (prec != LBM_FP32 && nx % 2 == 0) ? 2 : 1; }
+inline int group_of(int lattice, int prec, int v) { return (lattice * 4 + prec) * 2 + (v == 2 ? 1 : 0); }
 
 size_t elem_bytes(int prec) { return prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2); }
 
-template <class L, class S>
+template <class L, class S, int V>
 cudaError_t launch_batched(const BatchDomain *doms, const BatchTile *tiles, int ntiles, int grid, cudaStream_t st)
 {
     using C = typename StoreC<S>::C;
-    k_batched<L, S, C><<<grid, 128, 0, st>>>(doms, tiles, ntiles);
+    k_batched<L, S, C, V><<<grid, 128, 0, st>>>(doms, tiles, ntiles);
     return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t launch_v(int v, const BatchDomain *doms, const BatchTile *tiles, int ntiles, int grid, cudaStream_t st)
+{
+    return v == 2 ? launch_batched<L, S, 2>(doms, tiles, ntiles, grid, st)
+                  : launch_batched<L, S, 1>(doms, tiles, ntiles, grid, st);
 }
 
 cudaError_t launch_group(int g, const BatchDomain *doms, const BatchTile *tiles, int ntiles, int grid, cudaStream_t st)
 {
-    switch (g) {
-    case 0: return launch_batched<D2Q9, double>(doms, tiles, ntiles, grid, st);
-    case 1: return launch_batched<D2Q9, float>(doms, tiles, ntiles, grid, st);
-    case 2: return launch_batched<D2Q9, __half>(doms, tiles, ntiles, grid, st);
-    case 3: return launch_batched<D2Q9, __nv_bfloat16>(doms, tiles, ntiles, grid, st);
-    case 4: return launch_batched<D3Q19, double>(doms, tiles, ntiles, grid, st);
-    case 5: return launch_batched<D3Q19, float>(doms, tiles, ntiles, grid, st);
-    case 6: return launch_batched<D3Q19, __half>(doms, tiles, ntiles, grid, st);
-    case 7: return launch_batched<D3Q19, __nv_bfloat16>(doms, tiles, ntiles, grid, st);
+    const int v = (g & 1) ? 2 : 1;
+    switch (g >> 1) {
+    case 0: return launch_v<D2Q9, double>(v, doms, tiles, ntiles, grid, st);
+    case 1: return launch_v<D2Q9, float>(v, doms, tiles, ntiles, grid, st);
+    case 2: return launch_v<D2Q9, __half>(v, doms, tiles, ntiles, grid, st);
+    case 3: return launch_v<D2Q9, __nv_bfloat16>(v, doms, tiles, ntiles, grid, st);
+    case 4: return launch_v<D3Q19, double>(v, doms, tiles, ntiles, grid, st);
+    case 5: return launch_v<D3Q19, float>(v, doms, tiles, ntiles, grid, st);
+    case 6: return launch_v<D3Q19, __half>(v, doms, tiles, ntiles, grid, st);
+    case 7: return launch_v<D3Q19, __nv_bfloat16>(v, doms, tiles, ntiles, grid, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -309,8 +319,7 @@ static int admit(lbm_server *s)
     return LBM_OK;
 }
 
-// Tile lists per (lattice, precision) group: enough consecutive rows per tile
-// for about 512 cells.
+// Warp tile lists per group: 32 x V consecutive cells of a row each.
 static int build_tiles(lbm_server *s)
 {
     for (int g = 0; g < NGROUPS; ++g) s->tiles_h[g].clear();
@@ -318,11 +327,12 @@ static int build_tiles(lbm_server *s)
         if (!s->slot_req[k]) continue;
         Request *r = s->reqs[s->slot_req[k]];
         if (r->state != LBM_REQ_RUNNING) continue;
+        const int v = lanes_v(r->prec, r->n[0]);
         const int rows = r->n[1] * r->n[2];
-        int per = 512 / r->n[0];
-        if (per < 1) per = 1;
-        for (int r0 = 0; r0 < rows; r0 += per)
-            s->tiles_h[group_of(r->lattice, r->prec)].push_back(BatchTile{k, r0, r0 + per <= rows ? per : rows - r0, 0});
+        const int segs = (r->n[0] + 32 * v - 1) / (32 * v);
+        std::vector<BatchTile> &list = s->tiles_h[group_of(r->lattice, r->prec, v)];
+        for (int row = 0; row < rows; ++row)
+            for (int xs = 0; xs < segs; ++xs) list.push_back(BatchTile{k, row, xs, 0});
     }
     for (int g = 0; g < NGROUPS; ++g) {
         const size_t n = s->tiles_h[g].size();
@@ -346,7 +356,8 @@ static cudaError_t enqueue_steps(lbm_server *s, int64_t steps)
         for (int g = 0; g < NGROUPS; ++g) {
             const int n = (int)s->tiles_h[g].size();
             if (n == 0) continue;
-            cudaError_t e = launch_group(g, s->doms_d, s->tiles_d[g], n, n < s->grid ? n : s->grid, s->stream);
+            const int blocks = (n + 3) / 4;  // 4 warps per block
+            cudaError_t e = launch_group(g, s->doms_d, s->tiles_d[g], n, blocks < s->grid ? blocks : s->grid, s->stream);
             if (e != cudaSuccess) return e;
         }
         k_batch_advance<<<(s->max_slots + 127) / 128, 128, 0, s->stream>>>(s->doms_d, s->max_slots);

@@ -1,16 +1,17 @@
 // serve.cuh -- batched multi-domain update for the serving engine.
 //
 // Many independent lattices advance in one launch: a tile list enumerates
-// (domain, first row, rows) work items; a persistent grid strides over the
-// tiles and every thread updates cells with the same update_cell() as the
-// single-lattice kernel, so a domain's arithmetic does not depend on what it
-// is batched with.  Each domain carries its own step parameters, buffer pair,
+// warp work items (domain, row, x segment); a persistent grid strides over
+// them and every lane updates its cells with the same device functions as
+// the single-lattice kernels (update_cell one cell per lane, update_vec V
+// cells per lane), so a domain's arithmetic does not depend on what it is
+// batched with.  Each domain carries its own step parameters, buffer pair,
 // parity and remaining-step counter; k_batch_advance flips the parity and
 // counts down after every step, and a domain whose counter reaches zero is
 // skipped by later steps of the same captured round.
 #pragma once
 
-#include "step.cuh"
+#include "step_vec.cuh"
 
 namespace rr {
 
@@ -23,28 +24,30 @@ struct BatchDomain {
     int64_t remaining;
 };
 
+// Work item of one warp: 32 * V consecutive cells of one row of one domain.
 struct BatchTile {
     int domain;
-    int row0;   // first row (y + ny z)
-    int rows;   // number of consecutive rows
+    int row;   // y + ny z
+    int xseg;  // cells [xseg * 32 V, (xseg + 1) * 32 V) of the row
     int pad;
 };
 
-template <class L, class S, class C>
+template <class L, class S, class C, int V>
 __global__ void __launch_bounds__(128) k_batched(const BatchDomain *__restrict__ doms,
                                                   const BatchTile *__restrict__ tiles, int ntiles)
 {
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = blockIdx.x * wpb + warp; t < ntiles; t += gridDim.x * wpb) {
         const BatchTile tl = tiles[t];
         const BatchDomain &d = doms[tl.domain];
-        if (!d.active) continue;
-        const int nx = d.p.n[0], ny = d.p.n[1];
-        const char *const *in = d.base[d.cur];
-        char *const *out = d.base[1 - d.cur];
-        const int cells = tl.rows * nx;
-        for (int i = threadIdx.x; i < cells; i += blockDim.x) {
-            const int r = tl.row0 + i / nx;
-            update_cell<L, S, C>(d.p, in, out, i % nx, r % ny, r / ny);
+        if (!d.active) continue;  // uniform across the warp
+        const int ny = d.p.n[1];
+        const int y = tl.row % ny, z = tl.row / ny;
+        const int x0 = (tl.xseg * 32 + lane) * V;
+        if constexpr (V == 1) {
+            if (x0 < d.p.n[0]) update_cell<L, S, C>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);
+        } else {
+            update_vec<L, S, C, V>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);
         }
     }
 }

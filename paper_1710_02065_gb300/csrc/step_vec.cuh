@@ -134,15 +134,18 @@ struct VecIO<__nv_bfloat16, 4> {
 // The kernel.  Block = one warp-multiple of threads along one x row.
 // Requires: no cell-type mask, nx % V == 0.
 // ---------------------------------------------------------------------------
+// One thread's V cells of a row (x0raw = first cell, a multiple of V); the
+// 32 lanes of a warp hold consecutive V-cell groups of the same row.  Lanes
+// past the row end load wrapped data for their neighbours' shuffles and
+// store nothing.
 template <class L, class S, class C, int V>
-__global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constant__ StepParams p)
+__device__ __forceinline__ void update_vec(const StepParams &p, const char *const *in, char *const *out, int x0raw,
+                                           int y, int z)
 {
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
     const int lane = threadIdx.x & 31;
-    const int x0raw = (blockIdx.x * blockDim.x + threadIdx.x) * V;
     const bool active = x0raw < nx;
     const int x0 = x0raw % nx;  // idle lanes load a wrapped, valid vector
-    const int y = blockIdx.y, z = blockIdx.z;
     const unsigned nxy = (unsigned)nx * ny;
 
     // rows streamed from (uniform per thread): inward neighbour on non-periodic y/z faces
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constan
     for (int i = 0; i < L::Q; ++i) {
         const int Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
         const int Z = L::D == 2 ? 0 : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
-        const S *row = (const S *)p.in[i] + ((unsigned)nx * Y + nxy * Z);
+        const S *row = (const S *)in[i] + ((unsigned)nx * Y + nxy * Z);
         C v[V];
         VecIO<S, V>::ld(row + x0, v);
         if (L::cx(i) == 0) {
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constan
         C o[V];
 #pragma unroll
         for (int k = 0; k < V; ++k) o[k] = rebuild_rest<L, C>(cf[k]);
-        VecIO<S, V>::st((S *)p.out[0] + base, o);
+        VecIO<S, V>::st((S *)out[0] + base, o);
     }
 #pragma unroll
     for (int i = 1; i <= L::HALF; ++i) {
@@ -237,9 +240,15 @@ __global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constan
             op[k] = C(weight<L>(i)) * (e + o);
             om[k] = C(weight<L>(i)) * (e - o);
         }
-        VecIO<S, V>::st((S *)p.out[i] + base, op);
-        VecIO<S, V>::st((S *)p.out[i + L::HALF] + base, om);
+        VecIO<S, V>::st((S *)out[i] + base, op);
+        VecIO<S, V>::st((S *)out[i + L::HALF] + base, om);
     }
+}
+
+template <class L, class S, class C, int V>
+__global__ void __launch_bounds__(256) k_stream_collide_vec(const __grid_constant__ StepParams p)
+{
+    update_vec<L, S, C, V>(p, p.in, p.out, (blockIdx.x * blockDim.x + threadIdx.x) * V, blockIdx.y, blockIdx.z);
 }
 
 template <class L, class S, class C, int V>

@@ -362,3 +362,68 @@ def test_launch_shapes_match_oracle(lattice, prec):
             s.step(2)
             assert np.abs(s.populations() - ref).max() <= _pop_tol(prec, ref, w, 2)
             s.close()
+
+
+def test_graph_replay_matches_direct_launches():
+    """lbm_step on a non-default stream replays captured step pairs; the result
+    is bitwise that of launching every step (single level with walls, open
+    jet, and the two-level grid), and a configuration change recaptures."""
+    import torch
+    from paper_1710_02065_gb300 import lbm
+    from cases import cylinder_two_level
+    stream = torch.cuda.Stream()
+
+    def pair(c, setup=None):
+        a = to_gpu(c, PRECS["fp32"])                     # legacy stream: direct launches
+        b = lbm.Solver(c.lattice, c.n, c.tau, PRECS["fp32"], stream=stream.cuda_stream)
+        for face, (kind, u, prof) in c.faces.items():
+            lbm.lbm_set_boundary(b.h, face, kind, u, prof)
+        for face, (w, chi) in c.sponges.items():
+            lbm.lbm_set_sponge(b.h, face, w, chi, c.rho_ref, c.u_ref)
+        if c.solid is not None:
+            lbm.lbm_set_geometry(b.h, c.solid)
+        b.set_state(c.rho0, c.u0) if c.f0 is None else b.set_populations(c.f0)
+        if setup:
+            setup(a)
+            setup(b)
+        return a, b
+
+    c = cylinder(120, 60, diameter=8.0, sponge=20)
+    a, b = pair(c)
+    a.step(11)
+    b.step(7)
+    b.step(4)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.populations(), b.populations())
+    assert a.info()["step"] == b.info()["step"] == 11
+    # configuration change between calls: recaptured graph
+    lbm.lbm_set_sponge(a.h, 1, 10, 0.9, c.rho_ref, c.u_ref)
+    lbm.lbm_set_sponge(b.h, 1, 10, 0.9, c.rho_ref, c.u_ref)
+    a.step(6)
+    b.step(6)
+    assert np.array_equal(a.populations(), b.populations())
+
+    cj = round_jet(32, 24, 24, diameter=6.0, sponge=6, Re=1000.0, noise=0.0)
+    a, b = pair(cj)
+    a.step(9)
+    b.step(9)
+    assert np.array_equal(a.populations(), b.populations())
+
+    c2, patch, rho_f, u_f, solid_f = cylinder_two_level(100, 60, (20, 16, 40, 24), diameter_c=5.0, sponge=10)
+
+    def refine(s):
+        lbm.lbm_add_refinement_patch(s.h, (patch[0], patch[1], 0), (patch[2], patch[3], 1))
+        lbm.lbm_set_geometry_level(s.h, 1, solid_f)
+        lbm.lbm_set_state_level(s.h, 1, rho_f, u_f)
+        lbm.lbm_set_state(s.h, c2.rho0, c2.u0)
+
+    a, b = pair(c2, refine)
+    a.step(10)
+    b.step(5)
+    b.step(5)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.populations(), b.populations())
+    fa = np.zeros((9, 81 * 49)); fb = np.zeros((9, 81 * 49))
+    lbm.lbm_get_populations_level(a.h, 1, fa)
+    lbm.lbm_get_populations_level(b.h, 1, fb)
+    assert np.array_equal(fa, fb)

@@ -95,3 +95,24 @@ def test_two_level_uniform_stream_exact():
     lbm.lbm_get_populations_level(s.h, 1, f1f)
     assert np.abs(s.populations() - f0c).max() < 1e-15
     assert np.abs(f1f - f0f).max() < 1e-15
+
+
+def test_two_level_full_size_few_steps():
+    """The two-level cylinder at full size (coarse 800x400, fine 641x321),
+    FP32, 3 coarse steps: both levels equal the oracle within 1e-5."""
+    from paper_1710_02065_gb300 import lbm
+    c, patch, rho_f, u_f, solid_f = cylinder_two_level(800, 400, (160, 120, 320, 160), diameter_c=20.0,
+                                                       xc=40, yc=80, sponge=50)
+    T = _oracle_two_level(c, patch, rho_f, u_f, solid_f)
+    s = _gpu_two_level(c, patch, rho_f, u_f, solid_f, 1)
+    T.run(3)
+    s.step(3)
+    rc, uc, _ = T.Pc.moments(T.fc)
+    rf, uf, _ = T.Pf.moments(T.ff)
+    grc = np.zeros(T.Pc.ncell); guc = np.zeros((T.Pc.ncell, 3))
+    grf = np.zeros(T.Pf.ncell); guf = np.zeros((T.Pf.ncell, 3))
+    lbm.lbm_moments_level(s.h, 0, grc, guc, None)
+    lbm.lbm_moments_level(s.h, 1, grf, guf, None)
+    fluid_f = solid_f == 0
+    assert _normwise(grc, rc) <= 1e-5 and _normwise(guc, uc) <= 1e-5
+    assert _normwise(grf[fluid_f], rf[fluid_f]) <= 1e-5 and _normwise(guf[fluid_f], uf[fluid_f]) <= 1e-5

@@ -123,3 +123,20 @@ def test_serving_stream_small(serving):
     assert out["requests"] == 12 and out["failed"] == 0
     assert out["tts_p99_s"] >= out["tts_p50_s"] > 0
     assert out["aggregate_mlups"] > 0
+
+
+def test_largest_2d_request_matches_oracle(serving):
+    """The largest D2Q9 request size of the serving stream (1024^2), FP32, 3
+    steps, next to a small D3Q19 request: equal to the oracle within 1e-5."""
+    big = _req(0, 1024, 0.53, 3, 1)
+    small = _req(1, 32, 0.8, 5, 2)
+    out = _run(serving, [big, small], budget=2 << 30, rounds_steps=2)
+    rho_g, u_g, rc = out[0]
+    assert rc == 0
+    rho0, u0 = inputs.request_initial_state(big)
+    P = oracle.Problem(0, big["extents"], big["tau"])
+    f = P.run(P.equilibrium(rho0, u0), big["steps"])
+    rho, u, _ = P.moments(f)
+    assert np.linalg.norm(rho_g - rho) / np.linalg.norm(rho) <= 1e-5
+    du = u_g - u
+    assert np.linalg.norm(du) / np.linalg.norm(u) <= 1e-5 or np.abs(du).max() <= 1e-8
