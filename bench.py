@@ -165,7 +165,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("rr.cuh", "step.cuh"):
+    for name in ("rr.cuh", "step.cuh", "step_vec.cuh", "step_rows.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1710_02065_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -224,7 +224,7 @@ def time_precision(lbm, torch, spec, precision, steps, warmup, pg, stream, tune=
     n = s.ncell
     s.set_state(np.ones(n), np.zeros((n, 3)))
     tuned = autotune.autotune(s.h, precision, stream, steps=5, torch=torch)[1] if tune else {}
-    launch = lbm.lbm_get_launch(s.h)
+    launch = autotune.describe(s.h)
     lbm.lbm_step(s.h, warmup)
     s.sync()
     info0 = s.info()
@@ -245,8 +245,7 @@ def time_precision(lbm, torch, spec, precision, steps, warmup, pg, stream, tune=
     s.close()
     return dict(total_ms=total_ms, per_ms=per, launches=info1["launches"] - info0["launches"],
                 bytes_per_cell=info1["bytes_per_cell"], ncell=n, stable=(rc == 0),
-                launch={"block": launch[0], "cells_per_thread": launch[1]},
-                tuning={f"{b}x{v}": round(ms, 4) for (b, v), ms in tuned.items()})
+                launch=launch, tuning={k: round(ms, 4) for k, ms in tuned.items()})
 
 
 def e2e_run(lbm, torch, spec, precision, steps, stream):
@@ -554,7 +553,9 @@ def main():
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     else:
         peak, peak_src = 6800.0, "fallback"
-    key = f"k_stream_collide_d3q19_{args.precision}_jet{nx}x{ny}x{nz}"
+    kind = main_run["launch"]["kernel"]
+    kname = {"rows": "k_stream_collide_rows", "cell": "k_stream_collide"}.get(kind, "k_stream_collide_vec")
+    key = f"{kname}_d3q19_{args.precision}_jet{nx}x{ny}x{nz}"
     traffic = recorded_traffic(key)
 
     extra = {}
@@ -607,7 +608,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                         "kernel": "k_stream_collide<D3Q19>", "bytes_per_cell": bpc,
+                         "kernel": f"{kname}<D3Q19>", "bytes_per_cell": bpc,
                          "kernel_ms": kernel_ms},
             "cpu_baseline": cpu,
             "e2e": ({"value": world * ncell * args.steps / e2e_s / 1e6, "unit": "MLUPS",

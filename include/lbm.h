@@ -81,6 +81,8 @@ typedef struct lbm_ctx *lbm_handle;
 #define LBM_BC_PERIODIC 0 /* wrap-around; both faces of an axis must be periodic */
 #define LBM_BC_VELOCITY 1 /* Dirichlet velocity inflow                          */
 #define LBM_BC_OUTFLOW 2  /* zero-gradient outflow for all populations           */
+#define LBM_BC_FREESLIP 3 /* free-slip wall (no normal flow, no shear)          */
+#define LBM_BC_PRESSURE 4 /* constant pressure (density), see lbm_set_pressure */
 
 /* Cell types for lbm_set_geometry */
 #define LBM_CELL_FLUID 0
@@ -155,9 +157,22 @@ int lbm_set_geometry(lbm_handle h, const uint8_t *cell_type);
  * the inward neighbour and the node is rebuilt as feqH(rho, u_in) +
  * fneqH(u_in, Pi^neq) before the collision.  Outflow node: takes all
  * streamed populations of the inward neighbour (zero gradient), then collides.
+ * Free-slip node (Sec. III: lateral boundaries, zero gradient of the
+ * tangential velocity): rho, u and Pi^neq of the inward neighbour with the
+ * normal velocity and the normal-tangential Pi^neq set to zero, rebuilt the
+ * same way.  A node on several faces takes the first non-outflow face in the
+ * order -x, +x, -y, +y, -z, +z.
  */
 int lbm_set_boundary(lbm_handle h, int face, int kind, const double u_in[3],
                      const double *u_profile);
+
+/*
+ * lbm_set_pressure -- constant-pressure face (Sec. IV: the jet's right
+ * boundary): p = c_s^2 rho_out imposed; the node takes u and Pi^neq of its
+ * inward neighbour (zero gradient) and is rebuilt as feqH(rho_out, u) +
+ * fneqH(u, Pi^neq) before the collision.  rho_out > 0.
+ */
+int lbm_set_pressure(lbm_handle h, int face, double rho_out);
 
 /*
  * lbm_set_inlet_noise -- seeded random perturbation of velocity-face nodes.
@@ -182,6 +197,19 @@ int lbm_set_inlet_noise(lbm_handle h, uint64_t seed, double amplitude);
  */
 int lbm_set_sponge(lbm_handle h, int face, int width, double chi_max, double rho_ref,
                    const double u_ref[3]);
+
+/*
+ * lbm_set_radial_sponge -- circular (D2Q9) or spherical (D3Q19) absorbing
+ * layer (Sec. III: the cylinder's sponge is circular and covers the corners
+ * of the domain): with r the distance of a cell from center and d = r - r0,
+ * chi = chi_max sigma(d) (the profile of lbm_set_sponge, width W = width) for
+ * 0 <= d < 0.8 W, and chi = chi_max (the profile's maximum) for d >= 0.8 W, so
+ * the corners beyond the circle are damped at full strength.  Combined with
+ * planar layers by taking the larger chi; shares their reference state.
+ * width = 0 removes it.  Errors as lbm_set_sponge.
+ */
+int lbm_set_radial_sponge(lbm_handle h, const double center[3], double r0, double width,
+                          double chi_max, double rho_ref, const double u_ref[3]);
 
 /*
  * lbm_set_state -- initialise every cell to feqH(rho, u) (Eq. eqH).
@@ -236,11 +264,38 @@ int lbm_probe(lbm_handle h, int n, const int64_t *cells, double *p_prime);
  *                      thread (FP64: 2; FP32, FP16, BF16: 2 or 4); 0 = default
  *                      (FP32 1; FP16, BF16, FP64 2).  The vectorised kernel is used only when
  *                      there is no cell-type mask and nx is a multiple of it;
- *                      otherwise the general kernel runs.
+ *                      otherwise the general kernel runs.  These kernels
+ *                      run when the row-staged kernel (lbm_set_staging) is off
+ *                      or not eligible.
  * lbm_get_launch reports the shape lbm_step will use now.
  */
 int lbm_set_launch(lbm_handle h, int block, int cells_per_thread);
 int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread);
+
+/*
+ * lbm_set_staging -- the row-staged update kernel (a tuning knob; same update
+ * as the other kernels, results equal up to FP round-off order).  A
+ * persistent grid of CTAs walks over tiles of whole x rows; bulk asynchronous
+ * copies bring, for every direction, the rows the tile's cells pull from into
+ * shared memory (`stages` tiles in flight per CTA) while the CTA updates the
+ * previous tile.  It exists for FP32, FP16 and BF16 storage and runs only on a
+ * level without a cell-type mask whose rows are a multiple of 16 bytes (nx a
+ * multiple of 4 for FP32, of 8 for FP16 / BF16); elsewhere lbm_step falls
+ * back to the kernels of lbm_set_launch.
+ *   mode   : -1 default (= off: on GB300 the register kernels of
+ *            lbm_set_launch are faster for the D3Q19 jet), 0 off, 1 on
+ *            where eligible
+ *   stages : shared-memory stages per CTA, 0 (= 2) or 2..8
+ *   block  : threads per CTA, 0 (one per cell of a tile, at most 384) or a
+ *            multiple of 32 in [32, 384]
+ * The kernel bounds each wait for a copy at 2 s; a copy that does not arrive
+ * makes the next lbm_sync return LBM_ECUDA (and clears the condition).
+ * lbm_get_staging reports whether lbm_step uses it now (*active) and its
+ * plan: stages, threads per CTA, rows per tile and CTAs; zeros when inactive.
+ * Any output pointer may be NULL.
+ */
+int lbm_set_staging(lbm_handle h, int mode, int stages, int block);
+int lbm_get_staging(lbm_handle h, int *active, int *stages, int *block, int *rows_per_tile, int *grid);
 
 /*
  * lbm_force -- force on the solid cells of a level (0 coarse / single level, 1
@@ -253,7 +308,8 @@ int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread);
  */
 int lbm_force(lbm_handle h, int level, double F[3]);
 
-/* lbm_sync -- wait for all work of h; returns any pending execution error. */
+/* lbm_sync -- wait for all work of h; returns any pending execution error,
+ * including a bulk copy of the row-staged kernel that timed out. */
 int lbm_sync(lbm_handle h);
 
 /*

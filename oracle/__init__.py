@@ -32,7 +32,7 @@ _lock = threading.Lock()
 _lib = None
 
 D2Q9, D3Q19 = 0, 1
-PERIODIC, VELOCITY, OUTFLOW = 0, 1, 2
+PERIODIC, VELOCITY, OUTFLOW, FREESLIP, PRESSURE = 0, 1, 2, 3, 4
 CS2 = 1.0 / 3.0
 
 
@@ -54,6 +54,7 @@ class _Problem(C.Structure):
         ("tau", C.c_double),
         ("face_kind", C.c_int * 6),
         ("u_face", (C.c_double * 3) * 6),
+        ("rho_face", C.c_double * 6),
         ("u_profile", C.POINTER(C.c_double) * 6),
         ("noise_seed", C.c_uint64),
         ("noise_amp", C.c_double),
@@ -61,6 +62,7 @@ class _Problem(C.Structure):
         ("sponge_chi", C.c_double * 6),
         ("rho_ref", C.c_double),
         ("u_ref", C.c_double * 3),
+        ("radial", C.c_double * 6),
         ("solid", C.POINTER(C.c_uint8)),
         ("g", C.c_double * 3),
     ]
@@ -175,6 +177,7 @@ class Problem:
         self.tau = float(tau)
         self.face_kind = [PERIODIC] * 6
         self.u_face = [[0.0, 0.0, 0.0] for _ in range(6)]
+        self.rho_face = [1.0] * 6
         self.u_profile = [None] * 6
         self.noise_seed = 0
         self.noise_amp = 0.0
@@ -184,15 +187,25 @@ class Problem:
         self.u_ref = [0.0, 0.0, 0.0]
         self.solid = None
         self.g = [0.0, 0.0, 0.0]
+        self.radial = [0.0] * 6
 
     @property
     def ncell(self) -> int:
         return self.n[0] * self.n[1] * self.n[2]
 
-    def set_boundary(self, face: int, kind: int, u=(0.0, 0.0, 0.0), profile=None):
+    def set_boundary(self, face: int, kind: int, u=(0.0, 0.0, 0.0), profile=None, rho=1.0):
+        """kind PERIODIC, VELOCITY (u or profile), OUTFLOW, FREESLIP or PRESSURE (rho)."""
         self.face_kind[face] = kind
-        self.u_face[face] = [float(v) for v in u]
+        self.rho_face[face] = float(rho)
+        self.u_face[face] = [float(v) for v in (u if u is not None else (0.0, 0.0, 0.0))]
         self.u_profile[face] = None if profile is None else np.ascontiguousarray(profile, dtype=np.float64)
+
+    def set_radial_sponge(self, center, r0: float, width: float, chi_max: float, rho_ref=1.0,
+                          u_ref=(0.0, 0.0, 0.0)):
+        c = list(center) + [0.0] * (3 - len(center))
+        self.radial = [float(c[0]), float(c[1]), float(c[2]), float(r0), float(width), float(chi_max)]
+        self.rho_ref = float(rho_ref)
+        self.u_ref = [float(v) for v in u_ref]
 
     def set_sponge(self, face: int, width: int, chi_max: float, rho_ref=1.0, u_ref=(0.0, 0.0, 0.0)):
         self.sponge_width[face] = int(width)
@@ -210,11 +223,14 @@ class Problem:
         s.tau = self.tau
         for f in range(6):
             s.face_kind[f] = self.face_kind[f]
+            s.rho_face[f] = self.rho_face[f]
             for a in range(3):
                 s.u_face[f][a] = self.u_face[f][a]
             s.u_profile[f] = _dp(self.u_profile[f]) if self.u_profile[f] is not None else None
             s.sponge_width[f] = self.sponge_width[f]
             s.sponge_chi[f] = self.sponge_chi[f]
+        for k in range(6):
+            s.radial[k] = self.radial[k]
         s.noise_seed = int(self.noise_seed)
         s.noise_amp = float(self.noise_amp)
         s.rho_ref = self.rho_ref

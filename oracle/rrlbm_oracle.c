@@ -48,6 +48,16 @@
  *       populations are imposed from outside (grid coupling), are not updated.
  *   R9  Inlet noise: counter-based uniform numbers from splitmix64 (Steele,
  *       Lea and Flood 2014) keyed by (seed, step, face cell, component).
+ *   R16 Free-slip wall (Sec. III, lateral boundaries: "zero-gradient for
+ *       tangential velocity components"): the node takes rho, u and Pi^neq of
+ *       its inward neighbour, sets the normal velocity and the normal-
+ *       tangential Pi^neq components to zero (no flux, no shear), and is
+ *       rebuilt as feqH(rho, u) + fneqH(u, Pi^neq) before colliding.
+ *   R17 Constant-pressure outlet (Sec. IV, right boundary of the jet): the
+ *       node takes u and Pi^neq of its inward neighbour (zero gradient) and
+ *       the imposed density, p = c_s^2 rho_out, and is rebuilt likewise.
+ *   R18 Circular sponge (Sec. III: circular layer, corners covered): chi =
+ *       chi_max sigma(r - r0) for r - r0 < 0.8 W, chi_max beyond.
  *   R15 Forces on walls (lift, drag; not printed as a formula in the paper):
  *       momentum exchange over the bounce-back links.
  */
@@ -289,7 +299,7 @@ double orc_u01(uint64_t counter)
 /* Problem description                                                       */
 /* ------------------------------------------------------------------------ */
 
-enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_OUTFLOW = 2 };
+enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_OUTFLOW = 2, BC_FREESLIP = 3, BC_PRESSURE = 4 };
 
 typedef struct {
     int lattice;             /* 0 = D2Q9, 1 = D3Q19 */
@@ -297,6 +307,7 @@ typedef struct {
     double tau;
     int face_kind[6];        /* -x, +x, -y, +y, -z, +z */
     double u_face[6][3];     /* uniform velocity of a velocity face */
+    double rho_face[6];      /* density of a constant-pressure face */
     const double *u_profile[6]; /* optional per-face-cell velocity, 3 per cell */
     uint64_t noise_seed;
     double noise_amp;        /* relative amplitude of inlet noise (0 = none) */
@@ -304,6 +315,7 @@ typedef struct {
     double sponge_chi[6];
     double rho_ref;
     double u_ref[3];
+    double radial[6];        /* circular (spherical) layer: cx, cy, cz, r0, W, chi_max; W = 0: none */
     const uint8_t *solid;    /* optional per cell: 1 = solid wall, 2 = fixed */
     double g[3];             /* oracle-only body force */
 } orc_problem;
@@ -335,6 +347,15 @@ double orc_sigma(double d, double W)
 static double sponge_chi(const orc_problem *P, const int c[3])
 {
     double chi = 0.0;
+    if (P->radial[4] > 0.0) {
+        /* circular layer (R18): d = r - r0; the polynomial profile up to its
+         * maximum at d = 0.8 W, held at that maximum beyond (corners covered) */
+        const lattice_t *L = lattice(P->lattice);
+        double r2 = 0.0;
+        for (int a = 0; a < L->d; ++a) r2 += (c[a] - P->radial[a]) * (c[a] - P->radial[a]);
+        double d = sqrt(r2) - P->radial[3], W = P->radial[4];
+        if (d >= 0.0) chi = P->radial[5] * (d >= 0.8 * W ? 1.0 : orc_sigma(d, W));
+    }
     for (int face = 0; face < 6; ++face) {
         int W = P->sponge_width[face];
         if (W <= 0) continue;
@@ -363,18 +384,20 @@ void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int6
         return;
     }
 
-    /* Boundary role and the node whose streamed populations are used (R6, R7). */
+    /* Boundary role and the node whose streamed populations are used (R6, R7,
+     * R16, R17): the first velocity, free-slip or pressure face the node lies
+     * on decides how it is rebuilt. */
     int inlet = -1;
     for (int a = 0; a < 3; ++a) {
         s[a] = c[a];
         int lo = 2 * a, hi = 2 * a + 1;
         if (P->face_kind[lo] != BC_PERIODIC && c[a] == 0) {
             s[a] = 1;
-            if (P->face_kind[lo] == BC_VELOCITY && inlet < 0) inlet = lo;
+            if (P->face_kind[lo] != BC_OUTFLOW && inlet < 0) inlet = lo;
         }
         if (P->face_kind[hi] != BC_PERIODIC && c[a] == P->n[a] - 1) {
             s[a] = P->n[a] - 2;
-            if (P->face_kind[hi] == BC_VELOCITY && inlet < 0) inlet = hi;
+            if (P->face_kind[hi] != BC_OUTFLOW && inlet < 0) inlet = hi;
         }
     }
     int64_t scell = s[0] + (int64_t)P->n[0] * (s[1] + (int64_t)P->n[1] * s[2]);
@@ -392,6 +415,26 @@ void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int6
             f[i] = fin[(int64_t)L->opp[i] * N + scell];
         else
             f[i] = fin[(int64_t)i * N + scl];
+    }
+
+    if (inlet >= 0 && P->face_kind[inlet] != BC_VELOCITY) {
+        /* Free-slip (R16) or constant-pressure (R17) node. */
+        double rho, j[3], Pi[3][3], us[3], Pn[3][3], feq[19], fneq[19];
+        moments(L, f, &rho, j, Pi);
+        for (int a = 0; a < 3; ++a) us[a] = j[a] / rho;
+        pi_neq(L->d, rho, us, Pi, Pn);
+        if (P->face_kind[inlet] == BC_FREESLIP) {
+            int an = inlet / 2;
+            us[an] = 0.0;
+            for (int b = 0; b < 3; ++b)
+                if (b != an) Pn[an][b] = Pn[b][an] = 0.0;
+        } else {
+            rho = P->rho_face[inlet];
+        }
+        feqH(L, rho, us, feq);
+        fneqH(L, us, Pn, fneq);
+        for (int i = 0; i < L->q; ++i) out[i] = feq[i] + (1.0 - 1.0 / P->tau) * fneq[i];
+        return;
     }
 
     if (inlet >= 0) {

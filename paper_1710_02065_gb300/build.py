@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lbm_api.cu", "step_d2q9.cu", "step_d3q19.cu", "stepvec_d2q9.cu", "stepvec_d3q19.cu",
-           "lbm_noalloc.cu", "lbm_serve.cu"]
+           "rows_d2q9.cu", "rows_d3q19.cu", "lbm_noalloc.cu", "lbm_serve.cu"]
 
 
 def _nvcc() -> str:

@@ -27,14 +27,15 @@ template <class L, class S>
 __global__ void k_init_eq(int64_t N, const double *__restrict__ rho, const double *__restrict__ u,
                           S *__restrict__ f0, S *__restrict__ f1)
 {
+    using C = typename StoreC<S>::C;  // FP32 arithmetic for FP32/FP16/BF16 storage
     const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (cell >= N) return;
-    Coef<double> k{};
-    add_eq<double>(k, 1.0, rho[cell] - 1.0, rho[cell], u[3 * cell], u[3 * cell + 1],
-                   L::D == 3 ? u[3 * cell + 2] : 0.0);
+    Coef<C> k{};
+    add_eq<C, L::D>(k, C(1), C(rho[cell] - 1.0), C(rho[cell]), C(u[3 * cell]), C(u[3 * cell + 1]),
+              L::D == 3 ? C(u[3 * cell + 2]) : C(0));
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        const S v = Store<S>::from(rebuild<L, double>(k, i));
+        const S v = Store<S>::from(rebuild<L, C>(k, i));
         f0[(int64_t)i * N + cell] = v;
         f1[(int64_t)i * N + cell] = v;
     }

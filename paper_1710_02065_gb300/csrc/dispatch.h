@@ -43,4 +43,25 @@ inline bool vec_supported(int precision, int vec)
 inline int vec_default(int precision) { return precision == PREC_FP32 ? 1 : 2; }
 inline int block_default(int vec) { return vec == 1 ? 128 : 64; }
 
+// Row-staged kernel (bulk copies of whole rows into shared memory; FP32,
+// FP16, BF16; no cell-type mask; nx * element size a multiple of 16 bytes).
+struct RowsPlan {
+    int R;        // rows per tile
+    int RS;       // elements per direction and stage (R nx)
+    int stages;   // shared-memory stages
+    int block;    // threads per CTA
+    int grid;     // CTAs (resident: SMs x CTAs per SM, at most the tile count)
+    int per_sm;   // CTAs resident per SM
+    size_t smem;  // dynamic shared memory per CTA, bytes
+};
+// cudaErrorNotSupported (nothing launched, no CUDA error state): not eligible
+cudaError_t rows_d2q9(int precision, const StepParams &p, const void *fin, void *fout, int block, int stages,
+                      unsigned *err, cudaStream_t st);
+cudaError_t rows_d3q19(int precision, const StepParams &p, const void *fin, void *fout, int block, int stages,
+                       unsigned *err, cudaStream_t st);
+cudaError_t rows_plan_d2q9(int precision, const StepParams &p, const void *fin, const void *fout, int block,
+                           int stages, RowsPlan &pl);
+cudaError_t rows_plan_d3q19(int precision, const StepParams &p, const void *fin, const void *fout, int block,
+                            int stages, RowsPlan &pl);
+
 }  // namespace rr

@@ -43,8 +43,10 @@ struct lbm_ctx {
     double *prof_d[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int kind[6] = {0, 0, 0, 0, 0, 0};
     double u_face[6][3] = {};
+    double rho_face[6] = {1, 1, 1, 1, 1, 1};
     int sponge_w[6] = {0, 0, 0, 0, 0, 0};
     double sponge_chi[6] = {0, 0, 0, 0, 0, 0};
+    double radial[6] = {0, 0, 0, 0, 0, 0};
     bool ref_set = false;
     double rho_ref = 1.0, u_ref[3] = {0, 0, 0};
     uint64_t noise_seed = 0;
@@ -52,6 +54,10 @@ struct lbm_ctx {
     int64_t step = 0, launches = 0;
     int block = 0;  // 0: automatic
     int vec = 0;    // cells per thread; 0: automatic, 1: scalar kernel
+    int staging = -1;     // row-staged kernel: -1 default (off), 0 off, 1 on where eligible
+    int stages = 0;       // its shared-memory stages (0: 2)
+    int rows_block = 0;   // its threads per CTA (0: automatic)
+    unsigned *err_d = nullptr;  // device error word of the row-staged kernel (bounded waits)
     double *red_d = nullptr;  // reduction partials + result
     int red_blocks = 0;
     std::vector<uint8_t> user_mask;  // caller's cell types (host copy); empty: none
@@ -261,6 +267,7 @@ static void release(lbm_ctx *h)
     for (int k = 0; k < 6; ++k)
         if (h->prof_d[k]) cudaFree(h->prof_d[k]);
     if (h->red_d) cudaFree(h->red_d);
+    if (h->err_d) cudaFree(h->err_d);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->fine) {
         for (int k = 0; k < 2; ++k) {
@@ -324,6 +331,12 @@ extern "C" int lbm_create(lbm_handle *out, int lattice, const int extents[3], do
         cudaGetLastError();
         release(h);
         return fail(nullptr, LBM_ENOMEM, "cudaMalloc of reduction scratch failed");
+    }
+    if (cudaMalloc(&h->err_d, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemsetAsync(h->err_d, 0, sizeof(unsigned), h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        release(h);
+        return fail(nullptr, LBM_ENOMEM, "cudaMalloc of the error word failed");
     }
     // rest state: rho = 1, u = 0 is g = f - w = 0 in every storage format
     for (int k = 0; k < 2; ++k)
@@ -425,7 +438,7 @@ extern "C" int lbm_set_boundary(lbm_handle h, int face, int kind, const double u
     CHECK_HANDLE(h);
     h->cfg_version++;
     if (face < 0 || face > 5) return fail(h, LBM_EINVAL, "face %d out of range", face);
-    if (kind < LBM_BC_PERIODIC || kind > LBM_BC_OUTFLOW) return fail(h, LBM_EINVAL, "unknown boundary kind %d", kind);
+    if (kind < LBM_BC_PERIODIC || kind > LBM_BC_PRESSURE) return fail(h, LBM_EINVAL, "unknown boundary kind %d", kind);
     if (h->d == 2 && face >= 4 && kind != LBM_BC_PERIODIC)
         return fail(h, LBM_EINVAL, "2D lattice: z faces are periodic");
     if (kind == LBM_BC_VELOCITY && !u_in && !u_profile)
@@ -447,6 +460,18 @@ extern "C" int lbm_set_boundary(lbm_handle h, int face, int kind, const double u
                                     cudaMemcpyHostToDevice, h->stream));
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     }
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_pressure(lbm_handle h, int face, double rho_out)
+{
+    CHECK_HANDLE(h);
+    h->cfg_version++;
+    if (!(rho_out > 0.0) || !std::isfinite(rho_out))
+        return fail(h, LBM_EINVAL, "rho_out = %g must be finite and > 0", rho_out);
+    int rc = lbm_set_boundary(h, face, LBM_BC_PRESSURE, nullptr, nullptr);
+    if (rc != LBM_OK) return rc;
+    h->rho_face[face] = rho_out;
     return LBM_OK;
 }
 
@@ -483,7 +508,7 @@ extern "C" int lbm_set_sponge(lbm_handle h, int face, int width, double chi_max,
         for (int a = 0; a < 3; ++a) ur[a] = u_ref[a];
     if (h->d == 2 && ur[2] != 0.0) return fail(h, LBM_EINVAL, "2D lattice: u_ref z must be 0");
     if (!(rho_ref > 0.0)) return fail(h, LBM_EINVAL, "rho_ref = %g must be > 0", rho_ref);
-    bool other = false;
+    bool other = h->radial[4] > 0.0;
     for (int f = 0; f < 6; ++f)
         if (f != face && h->sponge_w[f] > 0) other = true;
     if (other && h->ref_set &&
@@ -491,6 +516,40 @@ extern "C" int lbm_set_sponge(lbm_handle h, int face, int width, double chi_max,
         return fail(h, LBM_EINVAL, "all sponge layers share one reference state");
     h->sponge_w[face] = width;
     h->sponge_chi[face] = chi_max;
+    h->rho_ref = rho_ref;
+    for (int a = 0; a < 3; ++a) h->u_ref[a] = ur[a];
+    h->ref_set = true;
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_radial_sponge(lbm_handle h, const double center[3], double r0, double width,
+                                     double chi_max, double rho_ref, const double u_ref[3])
+{
+    CHECK_HANDLE(h);
+    h->cfg_version++;
+    if (width == 0.0) {
+        for (int k = 0; k < 6; ++k) h->radial[k] = 0.0;
+        return LBM_OK;
+    }
+    if (!center) return fail(h, LBM_EINVAL, "center is null");
+    if (!(r0 >= 0.0) || !(width > 0.0) || !std::isfinite(r0) || !std::isfinite(width))
+        return fail(h, LBM_EINVAL, "r0 must be >= 0 and width > 0");
+    if (!(chi_max >= 0.0) || !(chi_max < 4.0 * h->tau))
+        return fail(h, LBM_EINVAL, "chi_max = %g must be in [0, 4 tau = %g) for stability", chi_max, 4.0 * h->tau);
+    double ur[3] = {0, 0, 0};
+    if (u_ref)
+        for (int a = 0; a < 3; ++a) ur[a] = u_ref[a];
+    if (h->d == 2 && ur[2] != 0.0) return fail(h, LBM_EINVAL, "2D lattice: u_ref z must be 0");
+    if (!(rho_ref > 0.0)) return fail(h, LBM_EINVAL, "rho_ref = %g must be > 0", rho_ref);
+    bool other = false;
+    for (int f = 0; f < 6; ++f) other = other || h->sponge_w[f] > 0;
+    if (other && h->ref_set &&
+        (rho_ref != h->rho_ref || ur[0] != h->u_ref[0] || ur[1] != h->u_ref[1] || ur[2] != h->u_ref[2]))
+        return fail(h, LBM_EINVAL, "all sponge layers share one reference state");
+    for (int a = 0; a < 3; ++a) h->radial[a] = (a < h->d) ? center[a] : 0.0;
+    h->radial[3] = r0;
+    h->radial[4] = width;
+    h->radial[5] = chi_max;
     h->rho_ref = rho_ref;
     for (int a = 0; a < 3; ++a) h->u_ref[a] = ur[a];
     h->ref_set = true;
@@ -609,10 +668,14 @@ static int build_params(lbm_ctx *h, StepParams &p)
         p.sponge_w[f] = h->sponge_w[f];
         p.sponge_chi[f] = h->sponge_chi[f];
         if (h->sponge_w[f] > 0 && h->sponge_chi[f] > 0.0) p.any_sponge = 1;
+        p.radial[f] = h->radial[f];
         p.face_cells[f] = face_cells(h, f);
+        p.rho_face[f] = h->rho_face[f];
+        p.rho_face_m1[f] = h->rho_face[f] - 1.0;
         for (int a = 0; a < 3; ++a) p.u_face[f][a] = h->u_face[f][a];
         p.u_profile[f] = h->prof_d[f];
     }
+    if (h->radial[4] > 0.0 && h->radial[5] > 0.0) p.any_sponge = 1;
     p.rho_ref = h->rho_ref;
     p.rho_ref_m1 = h->rho_ref - 1.0;
     for (int a = 0; a < 3; ++a) p.u_ref[a] = h->u_ref[a];
@@ -624,10 +687,29 @@ static int build_params(lbm_ctx *h, StepParams &p)
     return LBM_OK;
 }
 
-// Launch one update of a grid: vectorised kernel when there is no mask and
-// the row length allows it, the general kernel otherwise.
+// Whether the row-staged kernel is asked for (it still runs only where eligible)
+static bool staging_wanted(const lbm_ctx *h)
+{
+    if (h->staging == 0) return false;
+    // default: off -- measured on GB300 for the D3Q19 jet (384 x 256 x 256) the
+    // register kernels are faster (FP32 43.3 vs 25.9 GLUPS, FP16 48.9 vs 34.9)
+    return h->staging == 1;
+}
+
+// Launch one update of a grid: the row-staged kernel where it is wanted and
+// eligible; else the vectorised kernel when there is no mask and the row
+// length allows it; else the general kernel.
 static cudaError_t launch_update(lbm_ctx *h, const StepParams &p, const void *fin, void *fout)
 {
+    if (staging_wanted(h)) {
+        const cudaError_t e = h->lattice == LBM_D2Q9
+                                  ? rows_d2q9(h->prec, p, fin, fout, h->rows_block, h->stages, h->err_d, h->stream)
+                                  : rows_d3q19(h->prec, p, fin, fout, h->rows_block, h->stages, h->err_d, h->stream);
+        if (e != cudaErrorNotSupported) {
+            h->launches += 1;
+            return e;
+        }
+    }
     int vec = h->vec == 0 ? vec_default(h->prec) : h->vec;
     if (p.solid || vec == 1 || !vec_supported(h->prec, vec) || p.n[0] % vec != 0) vec = 1;
     const int block = h->block > 0 ? h->block : block_default(vec);
@@ -995,11 +1077,60 @@ extern "C" int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread)
     return LBM_OK;
 }
 
+extern "C" int lbm_set_staging(lbm_handle h, int mode, int stages, int block)
+{
+    CHECK_HANDLE(h);
+    h->cfg_version++;
+    if (mode < -1 || mode > 1) return fail(h, LBM_EINVAL, "mode = %d must be -1, 0 or 1", mode);
+    if (stages != 0 && (stages < 2 || stages > 8)) return fail(h, LBM_EINVAL, "stages = %d must be 0 or in [2, 8]", stages);
+    if (block != 0 && (block < 32 || block > 384 || block % 32 != 0))
+        return fail(h, LBM_EINVAL, "block = %d must be 0 or a multiple of 32 in [32, 384]", block);
+    h->staging = mode;
+    h->stages = stages;
+    h->rows_block = block;
+    return LBM_OK;
+}
+
+extern "C" int lbm_get_staging(lbm_handle h, int *active, int *stages, int *block, int *rows_per_tile,
+                               int *grid)
+{
+    CHECK_HANDLE(h);
+    RowsPlan pl{};
+    bool on = false;
+    if (staging_wanted(h)) {
+        StepParams p;
+        int rc = build_params(h, p);
+        if (rc != LBM_OK) return rc;
+        const void *fin = h->f[h->cur];
+        const void *fout = h->f[1 - h->cur];
+        const cudaError_t e = h->lattice == LBM_D2Q9
+                                  ? rows_plan_d2q9(h->prec, p, fin, fout, h->rows_block, h->stages, pl)
+                                  : rows_plan_d3q19(h->prec, p, fin, fout, h->rows_block, h->stages, pl);
+        if (e != cudaSuccess && e != cudaErrorNotSupported) {
+            cudaGetLastError();
+            return fail(h, LBM_ECUDA, "row-staged kernel plan: %s", cudaGetErrorString(e));
+        }
+        on = e == cudaSuccess;
+    }
+    if (active) *active = on ? 1 : 0;
+    if (stages) *stages = on ? pl.stages : 0;
+    if (block) *block = on ? pl.block : 0;
+    if (rows_per_tile) *rows_per_tile = on ? pl.R : 0;
+    if (grid) *grid = on ? pl.grid : 0;
+    return LBM_OK;
+}
+
 extern "C" int lbm_sync(lbm_handle h)
 {
     CHECK_HANDLE(h);
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     CUDA_TRY(h, cudaGetLastError());
+    unsigned err = 0;
+    CUDA_TRY(h, cudaMemcpy(&err, h->err_d, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) {
+        CUDA_TRY(h, cudaMemset(h->err_d, 0, sizeof err));
+        return fail(h, LBM_ECUDA, "row-staged kernel: a bulk copy did not arrive within 2 s (error word %u)", err);
+    }
     return LBM_OK;
 }
 

@@ -131,6 +131,13 @@ struct Store<__nv_bfloat16> {
     __device__ static __nv_bfloat16 from(double v) { return __double2bfloat16(v); }
 };
 
+// ---------------------------------------------------------------------------
+// Fused multiply-add a * b + c with one rounding, written out so that every
+// kernel performs the same operations in the same order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fmac(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmac(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // compute type a storage format is written from
 template <class S>
 struct StoreC {
@@ -192,45 +199,55 @@ struct Sym2 {
 // Equilibrium coefficients of (rho, u), scaled by s: a0 += s (rho - 1),
 // a1 += s rho u, A2 += s rho u u, A3 += s rho u u u.  dr = rho - 1 is passed
 // separately so that it keeps its own precision.
-template <class C>
+template <class C, int D = 3>
 __device__ __forceinline__ void add_eq(Coef<C> &k, C s, C dr, C rho, C ux, C uy, C uz)
 {
     const C r = s * rho;
-    k.a0 += s * dr;
-    k.a1x += r * ux;
-    k.a1y += r * uy;
-    k.a1z += r * uz;
-    k.xx += r * ux * ux;
-    k.yy += r * uy * uy;
-    k.zz += r * uz * uz;
-    k.xy += r * ux * uy;
-    k.xz += r * ux * uz;
-    k.yz += r * uy * uz;
-    k.xxy += r * ux * ux * uy;
-    k.xyy += r * ux * uy * uy;
-    k.xxz += r * ux * ux * uz;
-    k.xzz += r * ux * uz * uz;
-    k.yyz += r * uy * uy * uz;
-    k.yzz += r * uy * uz * uz;
+    k.a0 = fmac(s, dr, k.a0);
+    const C rx = r * ux, ry = r * uy;
+    k.a1x += rx;
+    k.a1y += ry;
+    k.xx = fmac(rx, ux, k.xx);
+    k.yy = fmac(ry, uy, k.yy);
+    k.xy = fmac(rx, uy, k.xy);
+    const C rxx = rx * ux, ryy = ry * uy;
+    k.xxy = fmac(rxx, uy, k.xxy);
+    k.xyy = fmac(ryy, ux, k.xyy);
+    if (D == 3) {
+        const C rz = r * uz;
+        k.a1z += rz;
+        k.zz = fmac(rz, uz, k.zz);
+        k.xz = fmac(rx, uz, k.xz);
+        k.yz = fmac(ry, uz, k.yz);
+        const C rzz = rz * uz;
+        k.xxz = fmac(rxx, uz, k.xxz);
+        k.xzz = fmac(rzz, ux, k.xzz);
+        k.yyz = fmac(ryy, uz, k.yyz);
+        k.yzz = fmac(rzz, uy, k.yzz);
+    }
 }
 
 // Off-equilibrium coefficients scaled by s: A2 += s Pi^neq and
 // A3 += s a3_neq, a3_neq,abc = u_a P_bc + u_b P_ac + u_c P_ab (Eq. recursive2, n = 3)
-template <class C>
+template <class C, int D = 3>
 __device__ __forceinline__ void add_neq(Coef<C> &k, C s, C ux, C uy, C uz, const Sym2<C> &p)
 {
-    k.xx += s * p.xx;
-    k.yy += s * p.yy;
-    k.zz += s * p.zz;
-    k.xy += s * p.xy;
-    k.xz += s * p.xz;
-    k.yz += s * p.yz;
-    k.xxy += s * (C(2) * ux * p.xy + uy * p.xx);
-    k.xyy += s * (C(2) * uy * p.xy + ux * p.yy);
-    k.xxz += s * (C(2) * ux * p.xz + uz * p.xx);
-    k.xzz += s * (C(2) * uz * p.xz + ux * p.zz);
-    k.yyz += s * (C(2) * uy * p.yz + uz * p.yy);
-    k.yzz += s * (C(2) * uz * p.yz + uy * p.zz);
+    k.xx = fmac(s, p.xx, k.xx);
+    k.yy = fmac(s, p.yy, k.yy);
+    k.xy = fmac(s, p.xy, k.xy);
+    const C ux2 = ux + ux, uy2 = uy + uy;
+    k.xxy = fmac(s, fmac(ux2, p.xy, uy * p.xx), k.xxy);
+    k.xyy = fmac(s, fmac(uy2, p.xy, ux * p.yy), k.xyy);
+    if (D == 3) {
+        const C uz2 = uz + uz;
+        k.zz = fmac(s, p.zz, k.zz);
+        k.xz = fmac(s, p.xz, k.xz);
+        k.yz = fmac(s, p.yz, k.yz);
+        k.xxz = fmac(s, fmac(ux2, p.xz, uz * p.xx), k.xxz);
+        k.xzz = fmac(s, fmac(uz2, p.xz, ux * p.zz), k.xzz);
+        k.yyz = fmac(s, fmac(uy2, p.yz, uz * p.yy), k.yyz);
+        k.yzz = fmac(s, fmac(uz2, p.yz, uy * p.zz), k.yzz);
+    }
 }
 
 // g_i = w_i [ a0 + 3 xi.a1 + 4.5 H2_i:A2 + T3_i(A3) ]   (c_s^2 = 1/3)
@@ -282,14 +299,16 @@ template <class C>
 __device__ __forceinline__ Sym2<C> pi_neq(const Mom<C> &m, C dr, C rho, C ux, C uy, C uz, int D)
 {
     const C c = dr * C(1.0 / 3.0);
+    const C rx = -(rho * ux), ry = -(rho * uy);
     Sym2<C> p;
-    p.xx = m.sxx - c - rho * ux * ux;
-    p.yy = m.syy - c - rho * uy * uy;
-    p.xy = m.sxy - rho * ux * uy;
+    p.xx = fmac(rx, ux, m.sxx - c);
+    p.yy = fmac(ry, uy, m.syy - c);
+    p.xy = fmac(rx, uy, m.sxy);
     if (D == 3) {
-        p.zz = m.szz - c - rho * uz * uz;
-        p.xz = m.sxz - rho * ux * uz;
-        p.yz = m.syz - rho * uy * uz;
+        const C rz = -(rho * uz);
+        p.zz = fmac(rz, uz, m.szz - c);
+        p.xz = fmac(rx, uz, m.sxz);
+        p.yz = fmac(ry, uz, m.syz);
     } else {
         p.zz = p.xz = p.yz = C(0);
     }
@@ -309,15 +328,15 @@ __device__ __forceinline__ Mom<C> moments_pairs(const C *g)
         const C s = g[i] + g[i + L::HALF], d = g[i] - g[i + L::HALF];
         const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
         m.dr += s;
-        if (x) m.jx += x > 0 ? d : -d;
-        if (y) m.jy += y > 0 ? d : -d;
-        if (z) m.jz += z > 0 ? d : -d;
+        if (x) m.jx = x > 0 ? m.jx + d : m.jx - d;
+        if (y) m.jy = y > 0 ? m.jy + d : m.jy - d;
+        if (z) m.jz = z > 0 ? m.jz + d : m.jz - d;
         if (x) m.sxx += s;
         if (y) m.syy += s;
         if (z) m.szz += s;
-        if (x && y) m.sxy += x * y > 0 ? s : -s;
-        if (x && z) m.sxz += x * z > 0 ? s : -s;
-        if (y && z) m.syz += y * z > 0 ? s : -s;
+        if (x && y) m.sxy = x * y > 0 ? m.sxy + s : m.sxy - s;
+        if (x && z) m.sxz = x * z > 0 ? m.sxz + s : m.sxz - s;
+        if (y && z) m.syz = y * z > 0 ? m.syz + s : m.syz - s;
     }
     return m;
 }
@@ -328,33 +347,35 @@ __device__ __forceinline__ void rebuild_pair(const Coef<C> &k, int i, C &even, C
 {
     constexpr double cs2 = 1.0 / 3.0;
     const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
-    C f2 = C(x * x - cs2) * k.xx + C(y * y - cs2) * k.yy;
-    if (L::D == 3) f2 += C(z * z - cs2) * k.zz;
-    if (x * y) f2 += C(2 * x * y) * k.xy;
-    if (L::D == 3 && x * z) f2 += C(2 * x * z) * k.xz;
-    if (L::D == 3 && y * z) f2 += C(2 * y * z) * k.yz;
-    even = k.a0 + C(4.5) * f2;
-    C f1 = C(0);
-    if (x) f1 += x > 0 ? k.a1x : -k.a1x;
-    if (y) f1 += y > 0 ? k.a1y : -k.a1y;
-    if (z) f1 += z > 0 ? k.a1z : -k.a1z;
+    C f2 = C(y * y - cs2) * k.yy;
+    f2 = fmac(C(x * x - cs2), k.xx, f2);
+    if (L::D == 3) f2 = fmac(C(z * z - cs2), k.zz, f2);
+    if (x * y) f2 = fmac(C(2 * x * y), k.xy, f2);
+    if (L::D == 3 && x * z) f2 = fmac(C(2 * x * z), k.xz, f2);
+    if (L::D == 3 && y * z) f2 = fmac(C(2 * y * z), k.yz, f2);
+    even = fmac(C(4.5), f2, k.a0);
+    // xi . a1 over the non-zero components only
+    C f1;
+    if (x) f1 = x > 0 ? k.a1x : -k.a1x;
+    if (y) f1 = x ? (y > 0 ? f1 + k.a1y : f1 - k.a1y) : (y > 0 ? k.a1y : -k.a1y);
+    if (z) f1 = (x || y) ? (z > 0 ? f1 + k.a1z : f1 - k.a1z) : (z > 0 ? k.a1z : -k.a1z);
     C o = C(3) * f1;
     const double hxxy = (x * x - cs2) * y, hxyy = (y * y - cs2) * x;
     if (L::D == 2) {
-        if (hxxy != 0.0) o += C(13.5 * hxxy) * k.xxy;
-        if (hxyy != 0.0) o += C(13.5 * hxyy) * k.xyy;
+        if (hxxy != 0.0) o = fmac(C(13.5 * hxxy), k.xxy, o);
+        if (hxyy != 0.0) o = fmac(C(13.5 * hxyy), k.xyy, o);
     } else {
         const double hyzz = (z * z - cs2) * y, hxzz = (z * z - cs2) * x;
         const double hyyz = (y * y - cs2) * z, hxxz = (x * x - cs2) * z;
         const double p1 = hxxy + hyzz, m1 = hxxy - hyzz;
         const double p2 = hxzz + hxyy, m2 = hxzz - hxyy;
         const double p3 = hyyz + hxxz, m3 = hyyz - hxxz;
-        if (p1 != 0.0) o += C(13.5 * p1) * (k.xxy + k.yzz);
-        if (m1 != 0.0) o += C(4.5 * m1) * (k.xxy - k.yzz);
-        if (p2 != 0.0) o += C(13.5 * p2) * (k.xzz + k.xyy);
-        if (m2 != 0.0) o += C(4.5 * m2) * (k.xzz - k.xyy);
-        if (p3 != 0.0) o += C(13.5 * p3) * (k.yyz + k.xxz);
-        if (m3 != 0.0) o += C(4.5 * m3) * (k.yyz - k.xxz);
+        if (p1 != 0.0) o = fmac(C(13.5 * p1), k.xxy + k.yzz, o);
+        if (m1 != 0.0) o = fmac(C(4.5 * m1), k.xxy - k.yzz, o);
+        if (p2 != 0.0) o = fmac(C(13.5 * p2), k.xzz + k.xyy, o);
+        if (m2 != 0.0) o = fmac(C(4.5 * m2), k.xzz - k.xyy, o);
+        if (p3 != 0.0) o = fmac(C(13.5 * p3), k.yyz + k.xxz, o);
+        if (m3 != 0.0) o = fmac(C(4.5 * m3), k.yyz - k.xxz, o);
     }
     odd = o;
 }
@@ -365,7 +386,7 @@ __device__ __forceinline__ C rebuild_rest(const Coef<C> &k)
 {
     C tr = k.xx + k.yy;
     if (L::D == 3) tr += k.zz;
-    return C(weight<L>(0)) * (k.a0 - C(1.5) * tr);
+    return C(weight<L>(0)) * fmac(C(-1.5), tr, k.a0);
 }
 
 // Reciprocal used for 1 / rho: the fast single-precision division intrinsic

@@ -11,6 +11,10 @@
 //   * velocity node (Sec. III, Dirichlet inflow): rho and Pi^neq of the
 //     inward neighbour, prescribed u (+ seeded noise), f* = feqH(rho, u) +
 //     (1 - 1/tau) fneqH(u, Pi^neq)
+//   * free-slip node (Sec. III lateral walls): rho, u, Pi^neq of the inward
+//     neighbour with zero normal velocity and zero normal-tangential Pi^neq
+//   * constant-pressure node (Sec. IV outlet): u, Pi^neq of the inward
+//     neighbour, imposed rho
 //   * outflow node (zero gradient): collides the inward neighbour's streamed
 //     populations
 //   * sponge cell (Sec. II.C, Eq. spongeLB + Eq. dampingLBM, n = m = 1/2):
@@ -23,11 +27,13 @@
 // changes sign, f_i = w (E + O), f_opp = w (E - O).
 #pragma once
 
+#include <cmath>
+
 #include "rr.cuh"
 
 namespace rr {
 
-enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_OUTFLOW = 2 };
+enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_OUTFLOW = 2, BC_FREESLIP = 3, BC_PRESSURE = 4 };
 
 struct StepParams {
     int n[3];
@@ -38,8 +44,10 @@ struct StepParams {
     int64_t ncell;
     int64_t face_cells[6];
     double u_face[6][3];
+    double rho_face[6], rho_face_m1[6];  // density of a constant-pressure face (and minus 1)
     const double *u_profile[6];  // device, 3 doubles per face cell, or null
     double sponge_chi[6];
+    double radial[6];  // circular / spherical layer: centre (3), r0, width W, chi_max; W = 0: none
     double rho_ref, rho_ref_m1, u_ref[3];  // rho_ref_m1 = rho_ref - 1
     uint64_t noise_seed;
     double noise_amp;
@@ -65,6 +73,13 @@ inline void set_bulk_box(StepParams &p)
             if (p.sponge_w[2 * a] > 0 && p.sponge_chi[2 * a] > 0.0 && p.sponge_w[2 * a] > lo) lo = p.sponge_w[2 * a];
             if (p.sponge_w[2 * a + 1] > 0 && p.sponge_chi[2 * a + 1] > 0.0 && p.n[a] - p.sponge_w[2 * a + 1] < hi)
                 hi = p.n[a] - p.sponge_w[2 * a + 1];
+        }
+        if (p.any_sponge && p.radial[4] > 0.0 && a < (p.n[2] > 1 ? 3 : 2)) {
+            // inside the cube inscribed in the circle (sphere) of radius r0
+            const double half = p.radial[3] / std::sqrt(p.n[2] > 1 ? 3.0 : 2.0);
+            const int rlo = (int)std::ceil(p.radial[a] - half), rhi = (int)std::floor(p.radial[a] + half) + 1;
+            if (rlo > lo) lo = rlo;
+            if (rhi < hi) hi = rhi;
         }
         p.blo[a] = lo;
         p.bhi[a] = hi > lo ? hi : lo;
@@ -115,13 +130,28 @@ __device__ __forceinline__ C chi_row(const StepParams &p, int y, int z)
 }
 
 template <class L, class C>
-__device__ __forceinline__ C chi_cell(const StepParams &p, C row, int x)
+__device__ __forceinline__ C chi_cell(const StepParams &p, C row, int x, int y, int z)
 {
     if (!p.any_sponge) return row;
     C v = chi_face<L, C>(p, 0, x);
     row = v > row ? v : row;
     v = chi_face<L, C>(p, 1, x);
-    return v > row ? v : row;
+    row = v > row ? v : row;
+    if (p.radial[4] > 0.0) {
+        // circular layer: the profile up to its maximum at r0 + 0.8 W, chi_max beyond
+        const C dx = C(x) - C(p.radial[0]), dy = C(y) - C(p.radial[1]);
+        C r2 = dx * dx + dy * dy;
+        if (L::D == 3) {
+            const C dz = C(z) - C(p.radial[2]);
+            r2 += dz * dz;
+        }
+        const C d = sqrt(r2) - C(p.radial[3]), W = C(p.radial[4]);
+        if (d >= C(0)) {
+            v = C(p.radial[5]) * (d >= C(0.8) * W ? C(1) : sigma<C>(d, W));
+            row = v > row ? v : row;
+        }
+    }
+    return row;
 }
 
 // ---------------------------------------------------------------------------
@@ -133,6 +163,24 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
 {
     const C om = C(p.omega);
     Coef<C> k{};
+    if (inlet >= 0 && p.kind[inlet] != BC_VELOCITY) {
+        // free-slip or constant-pressure node: moments of the streamed neighbour
+        const C rho = C(1) + m.dr;
+        const C inv = recip(rho);
+        C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
+        Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
+        if (p.kind[inlet] == BC_PRESSURE) {
+            add_eq<C, L::D>(k, C(1), C(p.rho_face_m1[inlet]), C(p.rho_face[inlet]), ux, uy, uz);
+        } else {
+            const int a = inlet >> 1;
+            if (a == 0) { ux = C(0); pn.xy = C(0); pn.xz = C(0); }
+            if (a == 1) { uy = C(0); pn.xy = C(0); pn.yz = C(0); }
+            if (a == 2) { uz = C(0); pn.xz = C(0); pn.yz = C(0); }
+            add_eq<C, L::D>(k, C(1), m.dr, rho, ux, uy, uz);
+        }
+        add_neq<C, L::D>(k, om, ux, uy, uz, pn);
+        return k;
+    }
     if (inlet >= 0) {
         // velocity node: rho, Pi^neq from the streamed neighbour, prescribed u (+ noise)
         const C rho = C(1) + m.dr;
@@ -156,8 +204,8 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
             }
         }
         const C ux = C(ub[0]), uy = C(ub[1]), uz = L::D == 3 ? C(ub[2]) : C(0);
-        add_eq<C>(k, C(1), m.dr, rho, ux, uy, uz);
-        add_neq<C>(k, om, ux, uy, uz, pn);
+        add_eq<C, L::D>(k, C(1), m.dr, rho, ux, uy, uz);
+        add_neq<C, L::D>(k, om, ux, uy, uz, pn);
         return k;
     }
     if (chi > C(0)) {
@@ -172,17 +220,17 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
         const C uy = (m.jy + C(0.5) * chi * rr * C(p.u_ref[1])) * h * inv;
         const C uz = L::D == 3 ? (m.jz + C(0.5) * chi * rr * C(p.u_ref[2])) * h * inv : C(0);
         const Sym2<C> pn = pi_neq<C>(m, drs, rs, ux, uy, uz, L::D);
-        add_eq<C>(k, C(1) - chi, drs, rs, ux, uy, uz);
-        add_eq<C>(k, chi, C(p.rho_ref_m1), rr, C(p.u_ref[0]), C(p.u_ref[1]), L::D == 3 ? C(p.u_ref[2]) : C(0));
-        add_neq<C>(k, om, ux, uy, uz, pn);
+        add_eq<C, L::D>(k, C(1) - chi, drs, rs, ux, uy, uz);
+        add_eq<C, L::D>(k, chi, C(p.rho_ref_m1), rr, C(p.u_ref[0]), C(p.u_ref[1]), L::D == 3 ? C(p.u_ref[2]) : C(0));
+        add_neq<C, L::D>(k, om, ux, uy, uz, pn);
         return k;
     }
     const C rho = C(1) + m.dr;
     const C inv = recip(rho);
     const C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
     const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
-    add_eq<C>(k, C(1), m.dr, rho, ux, uy, uz);
-    add_neq<C>(k, om, ux, uy, uz, pn);
+    add_eq<C, L::D>(k, C(1), m.dr, rho, ux, uy, uz);
+    add_neq<C, L::D>(k, om, ux, uy, uz, pn);
     return k;
 }
 
@@ -209,16 +257,16 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
                       z < p.bhi[2];
     if (!bulk) {
     if (!p.periodic[0]) {
-        if (x == 0) { sx = 1; if (p.kind[0] == BC_VELOCITY) inlet = 0; }
-        if (x == (int)nx - 1) { sx = nx - 2; if (p.kind[1] == BC_VELOCITY && inlet < 0) inlet = 1; }
+        if (x == 0) { sx = 1; if (p.kind[0] != BC_OUTFLOW) inlet = 0; }
+        if (x == (int)nx - 1) { sx = nx - 2; if (p.kind[1] != BC_OUTFLOW && inlet < 0) inlet = 1; }
     }
     if (!p.periodic[1]) {
-        if (y == 0) { sy = 1; if (p.kind[2] == BC_VELOCITY && inlet < 0) inlet = 2; }
-        if (y == (int)ny - 1) { sy = ny - 2; if (p.kind[3] == BC_VELOCITY && inlet < 0) inlet = 3; }
+        if (y == 0) { sy = 1; if (p.kind[2] != BC_OUTFLOW && inlet < 0) inlet = 2; }
+        if (y == (int)ny - 1) { sy = ny - 2; if (p.kind[3] != BC_OUTFLOW && inlet < 0) inlet = 3; }
     }
     if (L::D == 3 && !p.periodic[2]) {
-        if (z == 0) { sz = 1; if (p.kind[4] == BC_VELOCITY && inlet < 0) inlet = 4; }
-        if (z == (int)nz - 1) { sz = nz - 2; if (p.kind[5] == BC_VELOCITY && inlet < 0) inlet = 5; }
+        if (z == 0) { sz = 1; if (p.kind[4] != BC_OUTFLOW && inlet < 0) inlet = 4; }
+        if (z == (int)nz - 1) { sz = nz - 2; if (p.kind[5] != BC_OUTFLOW && inlet < 0) inlet = 5; }
     }
     }
     // neighbour coordinates of s with wrap-around on periodic axes
@@ -242,7 +290,7 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     }
 
     const Mom<C> m = moments_pairs<L, C>(g);
-    const C chi = (bulk || inlet >= 0) ? C(0) : chi_cell<L, C>(p, chi_row<L, C>(p, y, z), x);
+    const C chi = (bulk || inlet >= 0) ? C(0) : chi_cell<L, C>(p, chi_row<L, C>(p, y, z), x, y, z);
     const Coef<C> k = cell_coefficients<L, C>(p, m, chi, x, y, z, inlet);
 
     // ---- rebuild, relax and store (even/odd parts of each opposite pair)

@@ -151,12 +151,12 @@ __device__ __forceinline__ void update_vec(const StepParams &p, const char *cons
     // rows streamed from (uniform per thread): inward neighbour on non-periodic y/z faces
     int sy = y, sz = z, inlet_row = -1;
     if (!p.periodic[1]) {
-        if (y == 0) { sy = 1; if (p.kind[2] == BC_VELOCITY) inlet_row = 2; }
-        if (y == ny - 1) { sy = ny - 2; if (p.kind[3] == BC_VELOCITY && inlet_row < 0) inlet_row = 3; }
+        if (y == 0) { sy = 1; if (p.kind[2] != BC_OUTFLOW) inlet_row = 2; }
+        if (y == ny - 1) { sy = ny - 2; if (p.kind[3] != BC_OUTFLOW && inlet_row < 0) inlet_row = 3; }
     }
     if (L::D == 3 && !p.periodic[2]) {
-        if (z == 0) { sz = 1; if (p.kind[4] == BC_VELOCITY && inlet_row < 0) inlet_row = 4; }
-        if (z == nz - 1) { sz = nz - 2; if (p.kind[5] == BC_VELOCITY && inlet_row < 0) inlet_row = 5; }
+        if (z == 0) { sz = 1; if (p.kind[4] != BC_OUTFLOW && inlet_row < 0) inlet_row = 4; }
+        if (z == nz - 1) { sz = nz - 2; if (p.kind[5] != BC_OUTFLOW && inlet_row < 0) inlet_row = 5; }
     }
     const int ym = sy == 0 ? ny - 1 : sy - 1, yp = sy == ny - 1 ? 0 : sy + 1;
     const int zm = sz == 0 ? nz - 1 : sz - 1, zp = sz == nz - 1 ? 0 : sz + 1;
@@ -214,11 +214,11 @@ __device__ __forceinline__ void update_vec(const StepParams &p, const char *cons
         for (int i = 0; i < L::Q; ++i) gk[i] = g[i][k];
         const Mom<C> m = moments_pairs<L, C>(gk);
         int inlet = -1;
-        if (k == 0 && xlo && p.kind[0] == BC_VELOCITY) inlet = 0;
-        else if (k == V - 1 && xhi && p.kind[1] == BC_VELOCITY) inlet = 1;
+        if (k == 0 && xlo && p.kind[0] != BC_OUTFLOW) inlet = 0;
+        else if (k == V - 1 && xhi && p.kind[1] != BC_OUTFLOW) inlet = 1;
         if (inlet < 0) inlet = inlet_row;
         const bool bulk = bulk_row && x0 + k >= p.blo[0] && x0 + k < p.bhi[0];
-        const C chi = (bulk || inlet >= 0) ? C(0) : chi_cell<L, C>(p, chirow, x0 + k);
+        const C chi = (bulk || inlet >= 0) ? C(0) : chi_cell<L, C>(p, chirow, x0 + k, y, z);
         cf[k] = cell_coefficients<L, C>(p, m, chi, x0 + k, y, z, inlet);
     }
 

@@ -22,7 +22,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_EIO = 0, -1, -2, -
 LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED, LBM_BF16_SHIFTED = 0, 1, 2, 3
 LBM_FACE_XM, LBM_FACE_XP, LBM_FACE_YM, LBM_FACE_YP, LBM_FACE_ZM, LBM_FACE_ZP = range(6)
-LBM_BC_PERIODIC, LBM_BC_VELOCITY, LBM_BC_OUTFLOW = 0, 1, 2
+LBM_BC_PERIODIC, LBM_BC_VELOCITY, LBM_BC_OUTFLOW, LBM_BC_FREESLIP, LBM_BC_PRESSURE = 0, 1, 2, 3, 4
 LBM_CELL_FLUID, LBM_CELL_SOLID = 0, 1
 
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16_SHIFTED, "bf16": LBM_BF16_SHIFTED}
@@ -53,7 +53,9 @@ _sig("lbm_last_error", [_h], C.c_char_p)
 _sig("lbm_set_geometry", [_h, C.POINTER(C.c_uint8)])
 _sig("lbm_set_boundary", [_h, C.c_int, C.c_int, _dp, _dp])
 _sig("lbm_set_inlet_noise", [_h, C.c_uint64, C.c_double])
+_sig("lbm_set_pressure", [_h, C.c_int, C.c_double])
 _sig("lbm_set_sponge", [_h, C.c_int, C.c_int, C.c_double, C.c_double, _dp])
+_sig("lbm_set_radial_sponge", [_h, _dp, C.c_double, C.c_double, C.c_double, C.c_double, _dp])
 _sig("lbm_set_state", [_h, _dp, _dp])
 _sig("lbm_set_populations", [_h, _dp])
 _sig("lbm_get_populations", [_h, _dp])
@@ -64,6 +66,8 @@ _sig("lbm_probe", [_h, C.c_int, _i64p, _dp])
 _sig("lbm_sync", [_h])
 _sig("lbm_set_launch", [_h, C.c_int, C.c_int])
 _sig("lbm_get_launch", [_h, _ip, _ip])
+_sig("lbm_set_staging", [_h, C.c_int, C.c_int, C.c_int])
+_sig("lbm_get_staging", [_h, _ip, _ip, _ip, _ip, _ip])
 _sig("lbm_info", [_h, _i64p, _i64p, _dp, _dp])
 _sig("lbm_add_refinement_patch", [_h, _ip, _ip])
 _sig("lbm_force", [_h, C.c_int, _dp])
@@ -92,9 +96,10 @@ _sig("lbm_load", [_h, C.c_char_p])
 
 EXPORTED = [
     "lbm_lattice_table", "lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_geometry",
-    "lbm_set_boundary", "lbm_set_inlet_noise", "lbm_set_sponge", "lbm_set_state",
+    "lbm_set_boundary", "lbm_set_pressure", "lbm_set_inlet_noise", "lbm_set_sponge", "lbm_set_radial_sponge", "lbm_set_state",
     "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_moments", "lbm_reduce",
     "lbm_probe", "lbm_sync", "lbm_info", "lbm_save", "lbm_load", "lbm_set_launch", "lbm_get_launch",
+    "lbm_set_staging", "lbm_get_staging",
     "lbm_add_refinement_patch", "lbm_level_info", "lbm_force", "lbm_set_geometry_level", "lbm_set_state_level",
     "lbm_set_populations_level", "lbm_get_populations_level", "lbm_moments_level",
     "lbm_reduce_noalloc", "lbm_server_create", "lbm_server_destroy", "lbm_server_last_error",
@@ -170,6 +175,10 @@ def lbm_set_boundary(h, face: int, kind: int, u_in=None, u_profile=None):
     return _check(_lib.lbm_set_boundary(h, face, kind, _d(u), _d(p)), h)
 
 
+def lbm_set_pressure(h, face: int, rho_out: float):
+    return _check(_lib.lbm_set_pressure(h, face, float(rho_out)), h)
+
+
 def lbm_set_inlet_noise(h, seed: int, amplitude: float):
     return _check(_lib.lbm_set_inlet_noise(h, C.c_uint64(int(seed)), float(amplitude)), h)
 
@@ -177,6 +186,13 @@ def lbm_set_inlet_noise(h, seed: int, amplitude: float):
 def lbm_set_sponge(h, face: int, width: int, chi_max: float, rho_ref: float = 1.0, u_ref=(0.0, 0.0, 0.0)):
     u = _c64(u_ref)
     return _check(_lib.lbm_set_sponge(h, face, int(width), float(chi_max), float(rho_ref), _d(u)), h)
+
+
+def lbm_set_radial_sponge(h, center, r0: float, width: float, chi_max: float, rho_ref: float = 1.0,
+                          u_ref=(0.0, 0.0, 0.0)):
+    c = _c64(list(center) + [0.0] * (3 - len(center)))
+    return _check(_lib.lbm_set_radial_sponge(h, _d(c), float(r0), float(width), float(chi_max), float(rho_ref),
+                                             _d(_c64(u_ref))), h)
 
 
 def lbm_set_state(h, rho, u):
@@ -226,6 +242,17 @@ def lbm_get_launch(h):
     b, v = C.c_int(), C.c_int()
     _check(_lib.lbm_get_launch(h, C.byref(b), C.byref(v)), h)
     return b.value, v.value
+
+
+def lbm_set_staging(h, mode: int = -1, stages: int = 0, block: int = 0):
+    return _check(_lib.lbm_set_staging(h, int(mode), int(stages), int(block)), h)
+
+
+def lbm_get_staging(h):
+    """(active, stages, block, rows_per_tile, grid) of the row-staged kernel."""
+    v = [C.c_int() for _ in range(5)]
+    _check(_lib.lbm_get_staging(h, *[C.byref(x) for x in v]), h)
+    return tuple(x.value for x in v)
 
 
 def lbm_sync(h):

@@ -16,7 +16,7 @@ import oracle
 from paper_1710_02065_gb300 import inputs
 
 D2Q9, D3Q19 = 0, 1
-PERIODIC, VELOCITY, OUTFLOW = 0, 1, 2
+PERIODIC, VELOCITY, OUTFLOW, FREESLIP, PRESSURE = 0, 1, 2, 3, 4
 CS = 1.0 / math.sqrt(3.0)
 
 
@@ -26,7 +26,7 @@ class Case:
     lattice: int
     n: tuple
     tau: float
-    faces: dict = dataclasses.field(default_factory=dict)       # face -> (kind, u, profile)
+    faces: dict = dataclasses.field(default_factory=dict)       # face -> (kind, u, profile[, rho])
     sponges: dict = dataclasses.field(default_factory=dict)     # face -> (width, chi)
     rho_ref: float = 1.0
     u_ref: tuple = (0.0, 0.0, 0.0)
@@ -35,6 +35,7 @@ class Case:
     rho0: np.ndarray | None = None
     u0: np.ndarray | None = None
     f0: np.ndarray | None = None                               # explicit populations (q, ncell)
+    radial: tuple | None = None                                # (center, r0, width, chi)
 
     @property
     def ncell(self):
@@ -47,10 +48,13 @@ class Case:
 
 def to_oracle(c: Case):
     P = oracle.Problem(c.lattice, c.n, c.tau)
-    for face, (kind, u, prof) in c.faces.items():
-        P.set_boundary(face, kind, u, prof)
+    for face, spec in c.faces.items():
+        kind, u, prof = spec[:3]
+        P.set_boundary(face, kind, u, prof, rho=spec[3] if len(spec) > 3 else 1.0)
     for face, (w, chi) in c.sponges.items():
         P.set_sponge(face, w, chi, c.rho_ref, c.u_ref)
+    if c.radial is not None:
+        P.set_radial_sponge(c.radial[0], c.radial[1], c.radial[2], c.radial[3], c.rho_ref, c.u_ref)
     P.rho_ref, P.u_ref = c.rho_ref, list(c.u_ref)
     P.noise_seed, P.noise_amp = c.noise
     if c.solid is not None:
@@ -65,10 +69,16 @@ def to_oracle(c: Case):
 def to_gpu(c: Case, precision, block=None):
     from paper_1710_02065_gb300 import lbm
     s = lbm.Solver(c.lattice, c.n, c.tau, precision)
-    for face, (kind, u, prof) in c.faces.items():
-        lbm.lbm_set_boundary(s.h, face, kind, u, prof)
+    for face, spec in c.faces.items():
+        kind, u, prof = spec[:3]
+        if kind == PRESSURE:
+            lbm.lbm_set_pressure(s.h, face, spec[3] if len(spec) > 3 else 1.0)
+        else:
+            lbm.lbm_set_boundary(s.h, face, kind, u, prof)
     for face, (w, chi) in c.sponges.items():
         lbm.lbm_set_sponge(s.h, face, w, chi, c.rho_ref, c.u_ref)
+    if c.radial is not None:
+        lbm.lbm_set_radial_sponge(s.h, c.radial[0], c.radial[1], c.radial[2], c.radial[3], c.rho_ref, c.u_ref)
     if c.noise[1] > 0:
         lbm.lbm_set_inlet_noise(s.h, c.noise[0], c.noise[1])
     if c.solid is not None:

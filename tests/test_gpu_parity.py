@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
-from cases import (Case, D2Q9, D3Q19, OUTFLOW, PERIODIC, VELOCITY, acoustic_pulse, cylinder,
+from cases import (Case, D2Q9, D3Q19, FREESLIP, OUTFLOW, PERIODIC, PRESSURE, VELOCITY, acoustic_pulse, cylinder,
                    round_jet, taylor_green_3d, to_gpu, to_oracle, with_random_state)
 from paper_1710_02065_gb300 import inputs
 
@@ -41,6 +41,23 @@ def _pop_tol(prec, f_ref, w, steps):
         return 1e-5 * np.abs(f_ref).max()
     bits = 10 if prec == "fp16" else 7
     return (steps + 1) * 2.0 ** -bits * g + 1e-7
+
+
+# Update kernels: the row-staged kernel (bulk copies into shared memory; FP32,
+# FP16, BF16) and the register kernels, one or V cells per thread.
+KERNELS = {"fp64": ["cell", "vec2"], "fp32": ["rows", "cell", "vec2", "vec4"],
+           "fp16": ["rows", "cell", "vec2", "vec4"], "bf16": ["rows", "cell", "vec2", "vec4"]}
+
+
+def use_kernel(s, kind, block=64):
+    """Select one update kernel on solver s; 'rows' must then be active."""
+    from paper_1710_02065_gb300 import lbm
+    if kind == "rows":
+        lbm.lbm_set_staging(s.h, 1, 0, 0)
+        assert lbm.lbm_get_staging(s.h)[0] == 1, "row-staged kernel not eligible"
+    else:
+        lbm.lbm_set_staging(s.h, 0, 0, 0)
+        lbm.lbm_set_launch(s.h, block, 1 if kind == "cell" else int(kind[3:]))
 
 
 def _normwise(a, b):
@@ -346,6 +363,7 @@ def test_launch_shapes_match_oracle(lattice, prec):
         for vec in vecs:
             for block in (32, 128, 256):
                 s = to_gpu(c, PRECS[prec])
+                lbm.lbm_set_staging(s.h, 0, 0, 0)
                 lbm.lbm_set_launch(s.h, block, vec)
                 assert lbm.lbm_get_launch(s.h) == (block, vec)
                 s.step(3)
@@ -358,6 +376,7 @@ def test_launch_shapes_match_oracle(lattice, prec):
         ref = P.run(f, 2)
         for vec in vecs:
             s = to_gpu(cp, PRECS[prec])
+            lbm.lbm_set_staging(s.h, 0, 0, 0)
             lbm.lbm_set_launch(s.h, 64, vec)
             s.step(2)
             assert np.abs(s.populations() - ref).max() <= _pop_tol(prec, ref, w, 2)
@@ -376,8 +395,8 @@ def test_graph_replay_matches_direct_launches():
     def pair(c, setup=None):
         a = to_gpu(c, PRECS["fp32"])                     # legacy stream: direct launches
         b = lbm.Solver(c.lattice, c.n, c.tau, PRECS["fp32"], stream=stream.cuda_stream)
-        for face, (kind, u, prof) in c.faces.items():
-            lbm.lbm_set_boundary(b.h, face, kind, u, prof)
+        for face, spec in c.faces.items():
+            lbm.lbm_set_boundary(b.h, face, spec[0], spec[1], spec[2])
         for face, (w, chi) in c.sponges.items():
             lbm.lbm_set_sponge(b.h, face, w, chi, c.rho_ref, c.u_ref)
         if c.solid is not None:
@@ -427,3 +446,123 @@ def test_graph_replay_matches_direct_launches():
     lbm.lbm_get_populations_level(a.h, 1, fa)
     lbm.lbm_get_populations_level(b.h, 1, fb)
     assert np.array_equal(fa, fb)
+
+
+def _slip_box(lattice, n, seed):
+    """Velocity inflow, constant-pressure outlet, free-slip lateral walls,
+    a sponge; random off-equilibrium state."""
+    c = Case("slip", lattice, n, 0.57)
+    c.faces = {0: (VELOCITY, (0.05, 0.0, 0.0), None), 1: (PRESSURE, None, None, 1.003),
+               2: (FREESLIP, None, None), 3: (FREESLIP, None, None)}
+    if lattice == D3Q19:
+        c.faces[4] = (FREESLIP, None, None)
+        c.faces[5] = (PRESSURE, None, None, 0.998)
+    c.sponges = {1: (4, 0.4)}
+    c.rho_ref, c.u_ref = 1.0, (0.05, 0.0, 0.0)
+    return with_random_state(c, seed=seed, spread=0.08)
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
+def test_free_slip_and_pressure_faces_match_oracle(lattice, prec):
+    from paper_1710_02065_gb300 import lbm
+    _, _, _, w, _ = oracle.lattice(lattice)
+    n = (40, 14, 1) if lattice == D2Q9 else (24, 12, 10)
+    c = _slip_box(lattice, n, seed=8)
+    P, f = to_oracle(c)
+    ref = P.run(f, 3)
+    for kind in KERNELS[prec]:
+        s = to_gpu(c, PRECS[prec])
+        use_kernel(s, kind)
+        s.step(3)
+        err = np.abs(s.populations() - ref).max()
+        assert err <= _pop_tol(prec, ref, w, 3), (kind, err)
+        s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
+def test_radial_sponge_matches_oracle(lattice, prec):
+    """Circular / spherical sponge combined with a planar one, open faces."""
+    from paper_1710_02065_gb300 import lbm
+    _, _, _, w, _ = oracle.lattice(lattice)
+    n = (48, 40, 1) if lattice == D2Q9 else (32, 24, 20)
+    c = Case("radial", lattice, n, 0.6)
+    c.faces = {0: (VELOCITY, (0.04, 0.0, 0.0), None), 1: (OUTFLOW, None, None)}
+    c.sponges = {1: (5, 0.3)}
+    center = (n[0] / 2, n[1] / 2, n[2] / 2 if lattice == D3Q19 else 0)
+    c.radial = (center, 6.0, 8.0, 0.7)
+    c.rho_ref, c.u_ref = 1.0, (0.04, 0.0, 0.0)
+    c = with_random_state(c, seed=12, spread=0.06)
+    P, f = to_oracle(c)
+    ref = P.run(f, 3)
+    for kind in KERNELS[prec]:
+        s = to_gpu(c, PRECS[prec])
+        use_kernel(s, kind)
+        s.step(3)
+        assert np.abs(s.populations() - ref).max() <= _pop_tol(prec, ref, w, 3), kind
+        s.close()
+
+
+def _staged_cases(lattice):
+    """Shapes for the row-staged kernel: whole-plane tiles, several rows per
+    tile with a ragged last tile in y, one row per tile; open y/z (boundary
+    rows stream from their inward neighbour) and periodic y/z (wrapped
+    source rows split a tile's copies into runs)."""
+    if lattice == D2Q9:
+        return [(40, 12, 1), (512, 7, 1), (64, 9, 1)]
+    return [(24, 10, 6), (192, 10, 5), (96, 7, 9)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
+def test_staged_kernel_matches_oracle(lattice, prec):
+    """Row-staged kernel against the oracle: tile shapes, stage counts,
+    threads per CTA below and above a tile's cell count, open and periodic
+    axes with inflow profile + noise, outflow and sponges."""
+    from paper_1710_02065_gb300 import lbm
+    _, _, _, w, _ = oracle.lattice(lattice)
+    for n in _staged_cases(lattice):
+        for periodic in (False, True):
+            c = _open_box(lattice, n, seed=n[0] + n[1])
+            if periodic:
+                for f in range(2, 6 if lattice == D3Q19 else 4):
+                    c.faces.pop(f, None)
+                c.sponges = {1: (5, 0.8)}
+            P, f = to_oracle(c)
+            ref = P.run(f, 3)
+            tol = _pop_tol(prec, ref, w, 3)
+            for stages, block in ((0, 0), (3, 32), (5, 384), (2, 96)):
+                s = to_gpu(c, PRECS[prec])
+                lbm.lbm_set_staging(s.h, 1, stages, block)
+                active, ns, b, R, grid = lbm.lbm_get_staging(s.h)
+                assert active == 1 and ns == max(stages, 2) and R >= 1 and grid >= 1
+                assert b == block or block == 0
+                s.step(3)
+                err = np.abs(s.populations() - ref).max()
+                assert err <= tol, (n, periodic, stages, block, R, err)
+                s.sync()
+                s.close()
+
+
+def test_staged_kernel_eligibility_and_fallback():
+    """Rows that are not a multiple of 16 bytes, a cell-type mask, or FP64
+    storage leave the row-staged kernel inactive and lbm_step falls back to
+    the register kernels with the same results."""
+    from paper_1710_02065_gb300 import lbm
+    _, _, _, w, _ = oracle.lattice(D3Q19)
+    for n, prec, masked in (((22, 9, 5), "fp32", False), ((36, 8, 5), "fp16", False),
+                            ((32, 8, 5), "fp32", True), ((32, 8, 5), "fp64", False)):
+        c = _open_box(D3Q19, n, seed=4)
+        if masked:
+            solid = np.zeros(n[::-1], np.uint8)
+            solid[2:4, 3:5, 10:14] = 1
+            c.solid = solid.reshape(-1)
+        P, f = to_oracle(c)
+        ref = P.run(f, 2)
+        s = to_gpu(c, PRECS[prec])
+        lbm.lbm_set_staging(s.h, 1, 0, 0)
+        assert lbm.lbm_get_staging(s.h)[0] == 0, (n, prec, masked)
+        s.step(2)
+        assert np.abs(s.populations() - ref).max() <= _pop_tol(prec, ref, w, 2)
+        s.close()

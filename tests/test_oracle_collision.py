@@ -268,3 +268,17 @@ def test_splitmix64_published_vectors(repo_root):
     assert [int(v) for v in got_np] == want
     c = 123456789
     assert oracle.u01(c) == float(inputs.u01_np(np.array([c], dtype=np.uint64))[0])
+
+
+def test_circular_sponge_profile_covers_corners():
+    """Radial layer (Sec. III cylinder setup): zero inside r0, the polynomial
+    profile up to its maximum at r0 + 0.8 W, chi_max beyond (domain corners)."""
+    P = oracle.Problem(D2Q9, (101, 101), 0.7)
+    P.set_radial_sponge((50, 50), 30.0, 15.0, 0.6)
+    assert P.chi(50, 50) == 0.0
+    assert P.chi(50 + 30, 50) == 0.0
+    assert abs(P.chi(50 + 42, 50) - 0.6) < 1e-12          # d = 12 = 0.8 W
+    assert abs(P.chi(50 + 36, 50) - 0.6 * oracle.sigma(6.0, 15.0)) < 1e-15
+    assert P.chi(0, 0) == 0.6 and P.chi(100, 100) == 0.6  # corners
+    # radially symmetric
+    assert abs(P.chi(50, 50 + 36) - P.chi(50 + 36, 50)) < 1e-15
