@@ -341,52 +341,101 @@ __device__ __forceinline__ Mom<C> moments_pairs(const C *g)
     return m;
 }
 
-// Even (E) and odd (O) parts of the rebuilt population of direction i (1 <= i <= HALF)
+// ---------------------------------------------------------------------------
+// Reconstruction g_i = w_i [a0 + 3 xi.a1 + 4.5 H2_i:A2 + T3_i(A3)] for the
+// opposite pair (i, i + HALF): the even part E (a0 and second order) is
+// shared, the odd part O (first and third order) changes sign, so
+// g_i = w_i E + w_i O and g_opp = w_i E - w_i O, with w_i folded into the
+// constants.  The second order uses the trace form
+//   H2_i:A2 = sum_a xi_a^2 A_aa - tr(A2) / 3 + 2 sum_{a<b} xi_a xi_b A_ab
+// (c_s^2 = 1/3), so a face direction needs A_aa - tr/3 and the two edge
+// directions of a plane share A_aa + A_bb - tr/3.
+// ---------------------------------------------------------------------------
+template <class C>
+struct RebuildPre {
+    C tr3;             // tr(A2) / 3
+    C wa1, wa2;        // w a0 for the directions with one / two non-zero components
+    C bxy, bxz, byz;   // A_aa + A_bb - tr / 3 of the three coordinate planes
+    C s1, d1, s2, d2, s3, d3;  // third-order pair sums / differences (D3Q19)
+};
+
 template <class L, class C>
-__device__ __forceinline__ void rebuild_pair(const Coef<C> &k, int i, C &even, C &odd)
+__device__ __forceinline__ RebuildPre<C> rebuild_prep(const Coef<C> &k)
+{
+    // the two weight classes: |xi|^2 = 1 (direction 1 on both lattices) and
+    // |xi|^2 = 2 (w = 1/36 on both lattices)
+    RebuildPre<C> r;
+    C tr = k.xx + k.yy;
+    if (L::D == 3) tr += k.zz;
+    r.tr3 = tr * C(1.0 / 3.0);
+    r.wa1 = C(weight<L>(1)) * k.a0;
+    r.wa2 = C(1.0 / 36.0) * k.a0;
+    r.bxy = (k.xx + k.yy) - r.tr3;
+    if (L::D == 3) {
+        r.bxz = (k.xx + k.zz) - r.tr3;
+        r.byz = (k.yy + k.zz) - r.tr3;
+        r.s1 = k.xxy + k.yzz; r.d1 = k.xxy - k.yzz;
+        r.s2 = k.xzz + k.xyy; r.d2 = k.xzz - k.xyy;
+        r.s3 = k.yyz + k.xxz; r.d3 = k.yyz - k.xxz;
+    } else {
+        r.bxz = r.byz = r.s1 = r.d1 = r.s2 = r.d2 = r.s3 = r.d3 = C(0);
+    }
+    return r;
+}
+
+// g_i (plus) and g_opp(i) (minus) of the pair of direction i (1 <= i <= HALF)
+template <class L, class C>
+__device__ __forceinline__ void rebuild_pair(const Coef<C> &k, const RebuildPre<C> &r, int i, C &plus, C &minus)
 {
     constexpr double cs2 = 1.0 / 3.0;
     const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
-    C f2 = C(y * y - cs2) * k.yy;
-    f2 = fmac(C(x * x - cs2), k.xx, f2);
-    if (L::D == 3) f2 = fmac(C(z * z - cs2), k.zz, f2);
-    if (x * y) f2 = fmac(C(2 * x * y), k.xy, f2);
-    if (L::D == 3 && x * z) f2 = fmac(C(2 * x * z), k.xz, f2);
-    if (L::D == 3 && y * z) f2 = fmac(C(2 * y * z), k.yz, f2);
-    even = fmac(C(4.5), f2, k.a0);
-    // xi . a1 over the non-zero components only
+    const double w = weight<L>(i);
+    const int nnz = (x != 0) + (y != 0) + (z != 0);
+    // second order
+    C f2;
+    if (nnz == 1) {
+        f2 = (x ? k.xx : (y ? k.yy : k.zz)) - r.tr3;
+    } else {
+        const C base = (x && y) ? r.bxy : ((x && z) ? r.bxz : r.byz);
+        const C off = (x && y) ? k.xy : ((x && z) ? k.xz : k.yz);
+        f2 = fmac(C(2 * x * y + 2 * x * z + 2 * y * z), off, base);
+    }
+    const C E = fmac(C(4.5 * w), f2, nnz == 1 ? r.wa1 : r.wa2);
+    // first order over the non-zero components
     C f1;
     if (x) f1 = x > 0 ? k.a1x : -k.a1x;
     if (y) f1 = x ? (y > 0 ? f1 + k.a1y : f1 - k.a1y) : (y > 0 ? k.a1y : -k.a1y);
     if (z) f1 = (x || y) ? (z > 0 ? f1 + k.a1z : f1 - k.a1z) : (z > 0 ? k.a1z : -k.a1z);
-    C o = C(3) * f1;
+    C o = C(3.0 * w) * f1;
+    // third order, H_aab = xi_a^2 xi_b - c_s^2 xi_b
     const double hxxy = (x * x - cs2) * y, hxyy = (y * y - cs2) * x;
     if (L::D == 2) {
-        if (hxxy != 0.0) o = fmac(C(13.5 * hxxy), k.xxy, o);
-        if (hxyy != 0.0) o = fmac(C(13.5 * hxyy), k.xyy, o);
+        // 1 / (2 c_s^6) = 13.5
+        if (hxxy != 0.0) o = fmac(C(13.5 * w * hxxy), k.xxy, o);
+        if (hxyy != 0.0) o = fmac(C(13.5 * w * hxyy), k.xyy, o);
     } else {
+        // pairs (xxy, yzz), (xzz, xyy), (yyz, xxz); 1/(2 c_s^6) = 13.5, 1/(6 c_s^6) = 4.5
         const double hyzz = (z * z - cs2) * y, hxzz = (z * z - cs2) * x;
         const double hyyz = (y * y - cs2) * z, hxxz = (x * x - cs2) * z;
         const double p1 = hxxy + hyzz, m1 = hxxy - hyzz;
         const double p2 = hxzz + hxyy, m2 = hxzz - hxyy;
         const double p3 = hyyz + hxxz, m3 = hyyz - hxxz;
-        if (p1 != 0.0) o = fmac(C(13.5 * p1), k.xxy + k.yzz, o);
-        if (m1 != 0.0) o = fmac(C(4.5 * m1), k.xxy - k.yzz, o);
-        if (p2 != 0.0) o = fmac(C(13.5 * p2), k.xzz + k.xyy, o);
-        if (m2 != 0.0) o = fmac(C(4.5 * m2), k.xzz - k.xyy, o);
-        if (p3 != 0.0) o = fmac(C(13.5 * p3), k.yyz + k.xxz, o);
-        if (m3 != 0.0) o = fmac(C(4.5 * m3), k.yyz - k.xxz, o);
+        if (p1 != 0.0) o = fmac(C(13.5 * w * p1), r.s1, o);
+        if (m1 != 0.0) o = fmac(C(4.5 * w * m1), r.d1, o);
+        if (p2 != 0.0) o = fmac(C(13.5 * w * p2), r.s2, o);
+        if (m2 != 0.0) o = fmac(C(4.5 * w * m2), r.d2, o);
+        if (p3 != 0.0) o = fmac(C(13.5 * w * p3), r.s3, o);
+        if (m3 != 0.0) o = fmac(C(4.5 * w * m3), r.d3, o);
     }
-    odd = o;
+    plus = E + o;
+    minus = E - o;
 }
 
-// Rest population: w_0 (a0 - c_s^2 trace(A2) / (2 c_s^4))
+// Rest population: w_0 (a0 - c_s^2 tr(A2) / (2 c_s^4)) = w_0 a0 - 4.5 w_0 tr / 3
 template <class L, class C>
-__device__ __forceinline__ C rebuild_rest(const Coef<C> &k)
+__device__ __forceinline__ C rebuild_rest(const Coef<C> &k, const RebuildPre<C> &r)
 {
-    C tr = k.xx + k.yy;
-    if (L::D == 3) tr += k.zz;
-    return C(weight<L>(0)) * fmac(C(-1.5), tr, k.a0);
+    return fmac(C(-4.5 * weight<L>(0)), r.tr3, C(weight<L>(0)) * k.a0);
 }
 
 // Reciprocal used for 1 / rho: the fast single-precision division intrinsic

@@ -294,13 +294,14 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     const Coef<C> k = cell_coefficients<L, C>(p, m, chi, x, y, z, inlet);
 
     // ---- rebuild, relax and store (even/odd parts of each opposite pair)
-    Store<S>::st((S *)out[0] + cell, rebuild_rest<L, C>(k));
+    const RebuildPre<C> r = rebuild_prep<L, C>(k);
+    Store<S>::st((S *)out[0] + cell, rebuild_rest<L, C>(k, r));
 #pragma unroll
     for (int i = 1; i <= L::HALF; ++i) {
-        C e, o;
-        rebuild_pair<L, C>(k, i, e, o);
-        Store<S>::st((S *)out[i] + cell, C(weight<L>(i)) * (e + o));
-        Store<S>::st((S *)out[i + L::HALF] + cell, C(weight<L>(i)) * (e - o));
+        C gp, gm;
+        rebuild_pair<L, C>(k, r, i, gp, gm);
+        Store<S>::st((S *)out[i] + cell, gp);
+        Store<S>::st((S *)out[i + L::HALF] + cell, gm);
     }
 }
 

@@ -245,13 +245,14 @@ __device__ __forceinline__ void update_cell_staged(const StepParams &p, const S 
     const Coef<C> k = cell_coefficients<L, C>(p, m, chi, x, y, z, inlet);
 
     const unsigned cell = (unsigned)x + (unsigned)nx * ((unsigned)y + (unsigned)p.n[1] * (unsigned)z);
-    Store<S>::st((S *)p.out[0] + cell, rebuild_rest<L, C>(k));
+    const RebuildPre<C> r = rebuild_prep<L, C>(k);
+    Store<S>::st((S *)p.out[0] + cell, rebuild_rest<L, C>(k, r));
 #pragma unroll
     for (int i = 1; i <= L::HALF; ++i) {
-        C e, o;
-        rebuild_pair<L, C>(k, i, e, o);
-        Store<S>::st((S *)p.out[i] + cell, C(weight<L>(i)) * (e + o));
-        Store<S>::st((S *)p.out[i + L::HALF] + cell, C(weight<L>(i)) * (e - o));
+        C gp, gm;
+        rebuild_pair<L, C>(k, r, i, gp, gm);
+        Store<S>::st((S *)p.out[i] + cell, gp);
+        Store<S>::st((S *)p.out[i + L::HALF] + cell, gm);
     }
 }
 

@@ -224,22 +224,20 @@ __device__ __forceinline__ void update_vec(const StepParams &p, const char *cons
 
     // ---- rebuild and store, one direction pair at a time
     const unsigned base = (unsigned)nx * y + nxy * z + x0;
+    RebuildPre<C> rp[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) rp[k] = rebuild_prep<L, C>(cf[k]);
     {
         C o[V];
 #pragma unroll
-        for (int k = 0; k < V; ++k) o[k] = rebuild_rest<L, C>(cf[k]);
+        for (int k = 0; k < V; ++k) o[k] = rebuild_rest<L, C>(cf[k], rp[k]);
         VecIO<S, V>::st((S *)out[0] + base, o);
     }
 #pragma unroll
     for (int i = 1; i <= L::HALF; ++i) {
         C op[V], om[V];
 #pragma unroll
-        for (int k = 0; k < V; ++k) {
-            C e, o;
-            rebuild_pair<L, C>(cf[k], i, e, o);
-            op[k] = C(weight<L>(i)) * (e + o);
-            om[k] = C(weight<L>(i)) * (e - o);
-        }
+        for (int k = 0; k < V; ++k) rebuild_pair<L, C>(cf[k], rp[k], i, op[k], om[k]);
         VecIO<S, V>::st((S *)out[i] + base, op);
         VecIO<S, V>::st((S *)out[i + L::HALF] + base, om);
     }
