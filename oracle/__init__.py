@@ -72,6 +72,11 @@ class _Patch(C.Structure):
     _fields_ = [("X0", C.c_int), ("Y0", C.c_int), ("Wc", C.c_int), ("Hc", C.c_int)]
 
 
+class _Patch3(C.Structure):
+    _fields_ = [("X0", C.c_int), ("Y0", C.c_int), ("Z0", C.c_int), ("Wc", C.c_int), ("Hc", C.c_int),
+                ("Dc", C.c_int)]
+
+
 def lib():
     global _lib
     with _lock:
@@ -102,6 +107,11 @@ def lib():
             G = C.POINTER(_Patch)
             _lib.orc_refined_init_moments.argtypes = [P, G, dp, dp]
             _lib.orc_refined_step.argtypes = [P, P, G, dp, dp, dp, dp, dp, dp, C.c_int64]
+            G3 = C.POINTER(_Patch3)
+            _lib.orc_refined3_init_moments.argtypes = [P, G3, dp, dp]
+            _lib.orc_refined3_step.argtypes = [P, P, G3, dp, dp, dp, dp, dp, dp, C.c_int64]
+            _lib.orc_refine3_interp.argtypes = [P, G3, dp, dp, C.c_double, C.c_int, C.c_int, C.c_int, dp]
+            _lib.orc_refine3_filter.argtypes = [dp, dp]
         return _lib
 
 
@@ -350,3 +360,76 @@ class TwoLevel:
             lib().orc_refined_step(C.byref(sc), C.byref(sf), C.byref(g), _dp(self.fc), _dp(wc),
                                    _dp(self.ff), _dp(wf), _dp(self.M0), _dp(self.M1), self.step_index)
             self.step_index += 1
+
+
+class TwoLevel3:
+    """Two-level 2:1 D3Q19 grid (Sec. II.B): a coarse Problem plus a fine patch
+    over coarse nodes X0..X0+Wc, Y0..Y0+Hc, Z0..Z0+Dc, tau_f = 2 tau_c - 1/2.
+
+    The fine problem is periodic with its boundary shell fixed (rebuilt from
+    coarse data every half step); the covered coarse interior is fixed, its
+    first shell rebuilt from fine data every coarse step.  The patch must keep
+    2 coarse nodes from every coarse face.
+    """
+
+    def __init__(self, coarse: Problem, X0: int, Y0: int, Z0: int, Wc: int, Hc: int, Dc: int):
+        assert coarse.lattice == D3Q19
+        nxc, nyc, nzc = coarse.n
+        assert min(X0, Y0, Z0) >= 2 and min(Wc, Hc, Dc) >= 4
+        assert X0 + Wc <= nxc - 3 and Y0 + Hc <= nyc - 3 and Z0 + Dc <= nzc - 3
+        self.Pc = coarse
+        self.patch = (X0, Y0, Z0, Wc, Hc, Dc)
+        nf = (2 * Wc + 1, 2 * Hc + 1, 2 * Dc + 1)
+        self.Pf = Problem(D3Q19, nf, 2 * coarse.tau - 0.5)
+        shape_c = (nzc, nyc, nxc)
+        cmask = np.zeros(shape_c, np.uint8) if coarse.solid is None else coarse.solid.reshape(shape_c).copy()
+        cmask[Z0 + 1:Z0 + Dc, Y0 + 1:Y0 + Hc, X0 + 1:X0 + Wc] = FIXED
+        self.Pc.solid = cmask.reshape(-1)
+        fmask = np.zeros(nf[::-1], np.uint8)
+        fmask[0, :, :] = fmask[-1, :, :] = FIXED
+        fmask[:, 0, :] = fmask[:, -1, :] = FIXED
+        fmask[:, :, 0] = fmask[:, :, -1] = FIXED
+        self.Pf.solid = fmask.reshape(-1)
+        self.step_index = 0
+
+    def set_fine_solid(self, solid_fine: np.ndarray):
+        m = self.Pf.solid.copy()
+        s = np.asarray(solid_fine, np.uint8).reshape(-1)
+        m[(s == SOLID) & (m != FIXED)] = SOLID
+        self.Pf.solid = m
+
+    def init(self, rho_c, u_c, rho_f, u_f):
+        self.fc = self.Pc.equilibrium(rho_c, u_c)
+        self.ff = self.Pf.equilibrium(rho_f, u_f)
+        self.M0 = np.zeros(10 * self.Pc.ncell)
+        self.M1 = np.zeros(10 * self.Pc.ncell)
+        sc, g = self.Pc._struct(), _Patch3(*self.patch)
+        lib().orc_refined3_init_moments(C.byref(sc), C.byref(g), _dp(self.fc), _dp(self.M0))
+        self.step_index = 0
+
+    def run(self, nsteps: int):
+        sc, sf, g = self.Pc._struct(), self.Pf._struct(), _Patch3(*self.patch)
+        wc = np.empty_like(self.fc)
+        wf = np.empty_like(self.ff)
+        for _ in range(int(nsteps)):
+            lib().orc_refined3_step(C.byref(sc), C.byref(sf), C.byref(g), _dp(self.fc), _dp(wc),
+                                    _dp(self.ff), _dp(wf), _dp(self.M0), _dp(self.M1), self.step_index)
+            self.step_index += 1
+
+    def interp(self, M0: np.ndarray, M1: np.ndarray, a: float, i: int, j: int, k: int) -> np.ndarray:
+        """Coarse -> fine interface moments at fine shell node (i, j, k) from
+        per-coarse-cell moment arrays (10 per cell), time weight a."""
+        m = np.zeros(10)
+        sc, g = self.Pc._struct(), _Patch3(*self.patch)
+        lib().orc_refine3_interp(C.byref(sc), C.byref(g), _dp(np.ascontiguousarray(M0, dtype=np.float64)),
+                                 _dp(np.ascontiguousarray(M1, dtype=np.float64)), float(a), int(i), int(j), int(k),
+                                 _dp(m))
+        return m
+
+    @staticmethod
+    def filter(m27: np.ndarray) -> np.ndarray:
+        """Fine -> coarse moments from the 27 neighbours' moments, shape
+        (3, 3, 3, 10) indexed [dz, dy, dx] with offsets -1, 0, +1."""
+        mc = np.zeros(10)
+        lib().orc_refine3_filter(_dp(np.ascontiguousarray(m27, dtype=np.float64).reshape(-1)), _dp(mc))
+        return mc

@@ -821,3 +821,228 @@ int orc_refined_step(const orc_problem *Pc, const orc_problem *Pf, const orc_pat
     (void)Nf;
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Two-level 2:1 grid refinement (Sec. II.B), 3D (D3Q19)                    */
+/* ------------------------------------------------------------------------ */
+/*
+ * The 2D layout extended by one axis (readings R10-R12):
+ *   - the fine patch covers the coarse nodes X0..X0+Wc, Y0..Y0+Hc,
+ *     Z0..Z0+Dc; fine node (i, j, k) sits at (X0 + i/2, Y0 + j/2, Z0 + k/2);
+ *   - the fine boundary shell (a coordinate on a face of the fine box) is
+ *     rebuilt from coarse data after every fine substep; the first shell of
+ *     covered coarse nodes is rebuilt from fine data after every coarse step;
+ *     deeper covered coarse nodes are never read;
+ *   - coarse -> fine in space: along every axis on which the fine node is
+ *     odd, the 4-point centred cubic (-1, 9, 9, -1)/16; the tensor product of
+ *     these on the interface planes (a node odd in both in-plane axes takes
+ *     16 coarse nodes); linear in time as in 2D;
+ *   - fine -> coarse: rho, u of the coincident fine node, Pi^neq filtered
+ *     with the 3 x 3 x 3 full-weighting kernel (1,2,1)^3 / 64.
+ * Interface moments m = (rho, ux, uy, uz, Pxx, Pxy, Pxz, Pyy, Pyz, Pzz) are
+ * kept per coarse cell (10 doubles) on the six face planes of the patch
+ * box, extended by one node past every edge.
+ */
+typedef struct {
+    int X0, Y0, Z0, Wc, Hc, Dc;
+} orc_patch3;
+
+static void streamed_moments3(const orc_problem *P, const double *fin, int x, int y, int z, double m[10])
+{
+    const lattice_t *L = lattice(P->lattice);
+    const int64_t N = ncell(P);
+    const int64_t nx = P->n[0], ny = P->n[1], nz = P->n[2];
+    const int64_t cell = x + nx * (y + ny * (int64_t)z);
+    double f[19], rho, j[3], Pi[3][3], u[3], Pn[3][3];
+    for (int i = 0; i < L->q; ++i) {
+        int64_t sx = ((x - L->xi[i][0]) % nx + nx) % nx;
+        int64_t sy = ((y - L->xi[i][1]) % ny + ny) % ny;
+        int64_t sz = ((z - L->xi[i][2]) % nz + nz) % nz;
+        int64_t scl = sx + nx * (sy + ny * sz);
+        if (P->solid && P->solid[scl] == 1)
+            f[i] = fin[(int64_t)L->opp[i] * N + cell];
+        else
+            f[i] = fin[(int64_t)i * N + scl];
+    }
+    moments(L, f, &rho, j, Pi);
+    for (int a = 0; a < 3; ++a) u[a] = j[a] / rho;
+    pi_neq(3, rho, u, Pi, Pn);
+    m[0] = rho; m[1] = u[0]; m[2] = u[1]; m[3] = u[2];
+    m[4] = Pn[0][0]; m[5] = Pn[0][1]; m[6] = Pn[0][2]; m[7] = Pn[1][1]; m[8] = Pn[1][2]; m[9] = Pn[2][2];
+}
+
+static void rebuild_post3(const lattice_t *L, const double m[10], double alpha, double tau, double *out)
+{
+    double u[3] = {m[1], m[2], m[3]};
+    double Pn[3][3] = {{alpha * m[4], alpha * m[5], alpha * m[6]},
+                       {alpha * m[5], alpha * m[7], alpha * m[8]},
+                       {alpha * m[6], alpha * m[8], alpha * m[9]}};
+    double feq[19], fneq[19];
+    feqH(L, m[0], u, feq);
+    fneqH(L, u, Pn, fneq);
+    for (int i = 0; i < L->q; ++i) out[i] = feq[i] + (1.0 - 1.0 / tau) * fneq[i];
+}
+
+/* Coarse node (x, y, z) lies on a face plane of the patch box, within the
+ * box extended by one node along the in-plane axes. */
+static int on_interface_plane3(const orc_patch3 *G, int x, int y, int z)
+{
+    const int ix = x - G->X0, iy = y - G->Y0, iz = z - G->Z0;
+    if (ix < -1 || ix > G->Wc + 1 || iy < -1 || iy > G->Hc + 1 || iz < -1 || iz > G->Dc + 1) return 0;
+    return ix == 0 || ix == G->Wc || iy == 0 || iy == G->Hc || iz == 0 || iz == G->Dc;
+}
+
+static void coarse_plane_moments3(const orc_problem *Pc, const orc_patch3 *G, const double *fc, double *M)
+{
+    const int64_t nx = Pc->n[0], ny = Pc->n[1];
+    for (int z = G->Z0 - 1; z <= G->Z0 + G->Dc + 1; ++z)
+        for (int y = G->Y0 - 1; y <= G->Y0 + G->Hc + 1; ++y)
+            for (int x = G->X0 - 1; x <= G->X0 + G->Wc + 1; ++x)
+                if (on_interface_plane3(G, x, y, z))
+                    streamed_moments3(Pc, fc, x, y, z, M + 10 * (x + nx * (y + ny * (int64_t)z)));
+}
+
+/* 1D stencil of fine coordinate c along an axis: a coincident node (one
+ * point, weight 1) or the centred cubic between coarse nodes (c-1)/2 and
+ * (c+1)/2 (four points). */
+static int stencil1(int c, int origin, int idx[4], double w[4])
+{
+    if (c % 2 == 0) {
+        idx[0] = origin + c / 2;
+        w[0] = 1.0;
+        return 1;
+    }
+    const int a = origin + (c - 1) / 2;
+    idx[0] = a - 1; idx[1] = a; idx[2] = a + 1; idx[3] = a + 2;
+    w[0] = -1.0 / 16.0; w[1] = 9.0 / 16.0; w[2] = 9.0 / 16.0; w[3] = -1.0 / 16.0;
+    return 4;
+}
+
+/* Interface moments at fine shell node (i, j, k): the time mix (1 - a) M0 +
+ * a M1 of the coarse plane moments, interpolated by the tensor product of
+ * the 1D stencils (exported for the pins as orc_refine3_interp). */
+void orc_refine3_interp(const orc_problem *Pc, const orc_patch3 *G, const double *M0, const double *M1,
+                        double a, int i, int j, int k, double m[10])
+{
+    const int64_t nxc = Pc->n[0], nyc = Pc->n[1];
+    int ix[4], iy[4], iz[4];
+    double wx[4], wy[4], wz[4];
+    const int sx = stencil1(i, G->X0, ix, wx);
+    const int sy = stencil1(j, G->Y0, iy, wy);
+    const int sz = stencil1(k, G->Z0, iz, wz);
+    for (int e = 0; e < 10; ++e) m[e] = 0.0;
+    for (int c = 0; c < sz; ++c)
+        for (int b = 0; b < sy; ++b)
+            for (int q = 0; q < sx; ++q) {
+                const int64_t cell = ix[q] + nxc * (iy[b] + nyc * (int64_t)iz[c]);
+                const double wt = wx[q] * wy[b] * wz[c];
+                for (int e = 0; e < 10; ++e)
+                    m[e] += wt * ((1.0 - a) * M0[10 * cell + e] + a * M1[10 * cell + e]);
+            }
+}
+
+static void fill_fine_shell3(const orc_problem *Pc, const orc_problem *Pf, const orc_patch3 *G,
+                             const double *M0, const double *M1, double a, double *ff)
+{
+    const lattice_t *L = lattice(Pf->lattice);
+    const int64_t Nf = ncell(Pf);
+    const double alpha = Pf->tau / (2.0 * Pc->tau);
+    const int nfx = 2 * G->Wc + 1, nfy = 2 * G->Hc + 1, nfz = 2 * G->Dc + 1;
+    for (int k = 0; k < nfz; ++k)
+        for (int j = 0; j < nfy; ++j)
+            for (int i = 0; i < nfx; ++i) {
+                if (!(i == 0 || j == 0 || k == 0 || i == nfx - 1 || j == nfy - 1 || k == nfz - 1)) continue;
+                double m[10], out[19];
+                orc_refine3_interp(Pc, G, M0, M1, a, i, j, k, m);
+                rebuild_post3(L, m, alpha, Pf->tau, out);
+                const int64_t cell = i + (int64_t)nfx * (j + (int64_t)nfy * k);
+                for (int q = 0; q < L->q; ++q) ff[(int64_t)q * Nf + cell] = out[q];
+            }
+}
+
+/* Fine -> coarse moments from the 27 fine neighbours of the coincident node
+ * (m27[10 * (a + 3 b + 9 c)], offsets a, b, c = 0, 1, 2 for -1, 0, +1):
+ * rho, u of the centre, Pi^neq full-weighted by (1,2,1)^3 / 64 (exported
+ * for the pins as orc_refine3_filter). */
+void orc_refine3_filter(const double *m27, double mc[10])
+{
+    static const double w3[3] = {1.0, 2.0, 1.0};
+    for (int e = 0; e < 10; ++e) mc[e] = 0.0;
+    for (int c = 0; c < 3; ++c)
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a) {
+                const double *m = m27 + 10 * (a + 3 * b + 9 * c);
+                const double wt = w3[a] * w3[b] * w3[c] / 64.0;
+                for (int e = 4; e < 10; ++e) mc[e] += wt * m[e];
+                if (a == 1 && b == 1 && c == 1)
+                    for (int e = 0; e < 4; ++e) mc[e] = m[e];
+            }
+}
+
+static void restrict_to_coarse3(const orc_problem *Pc, const orc_problem *Pf, const orc_patch3 *G,
+                                const double *ff_prev, double *fc)
+{
+    const lattice_t *L = lattice(Pc->lattice);
+    const int64_t Nc = ncell(Pc);
+    const double alpha = 2.0 * Pc->tau / Pf->tau;
+    for (int z = G->Z0 + 1; z <= G->Z0 + G->Dc - 1; ++z)
+        for (int y = G->Y0 + 1; y <= G->Y0 + G->Hc - 1; ++y)
+            for (int x = G->X0 + 1; x <= G->X0 + G->Wc - 1; ++x) {
+                const int shell = x == G->X0 + 1 || x == G->X0 + G->Wc - 1 || y == G->Y0 + 1 ||
+                                  y == G->Y0 + G->Hc - 1 || z == G->Z0 + 1 || z == G->Z0 + G->Dc - 1;
+                if (!shell) continue;
+                const int i = 2 * (x - G->X0), j = 2 * (y - G->Y0), k = 2 * (z - G->Z0);
+                double m27[270], mc[10], out[19];
+                for (int c = 0; c < 3; ++c)
+                    for (int b = 0; b < 3; ++b)
+                        for (int a = 0; a < 3; ++a)
+                            streamed_moments3(Pf, ff_prev, i + a - 1, j + b - 1, k + c - 1,
+                                              m27 + 10 * (a + 3 * b + 9 * c));
+                orc_refine3_filter(m27, mc);
+                rebuild_post3(L, mc, alpha, Pc->tau, out);
+                const int64_t cell = x + (int64_t)Pc->n[0] * (y + (int64_t)Pc->n[1] * z);
+                for (int q = 0; q < L->q; ++q) fc[(int64_t)q * Nc + cell] = out[q];
+            }
+}
+
+/* Interface moments at t = 0: local moments of the stored coarse populations. */
+void orc_refined3_init_moments(const orc_problem *Pc, const orc_patch3 *G, const double *fc, double *M)
+{
+    const lattice_t *L = lattice(Pc->lattice);
+    const int64_t N = ncell(Pc);
+    const int64_t nx = Pc->n[0], ny = Pc->n[1];
+    for (int z = G->Z0 - 1; z <= G->Z0 + G->Dc + 1; ++z)
+        for (int y = G->Y0 - 1; y <= G->Y0 + G->Hc + 1; ++y)
+            for (int x = G->X0 - 1; x <= G->X0 + G->Wc + 1; ++x) {
+                if (!on_interface_plane3(G, x, y, z)) continue;
+                const int64_t cell = x + nx * (y + ny * (int64_t)z);
+                double f[19], rho, j[3], Pi[3][3], u[3], Pn[3][3];
+                for (int i = 0; i < L->q; ++i) f[i] = fc[(int64_t)i * N + cell];
+                moments(L, f, &rho, j, Pi);
+                for (int a = 0; a < 3; ++a) u[a] = j[a] / rho;
+                pi_neq(3, rho, u, Pi, Pn);
+                double *m = M + 10 * cell;
+                m[0] = rho; m[1] = u[0]; m[2] = u[1]; m[3] = u[2];
+                m[4] = Pn[0][0]; m[5] = Pn[0][1]; m[6] = Pn[0][2];
+                m[7] = Pn[1][1]; m[8] = Pn[1][2]; m[9] = Pn[2][2];
+            }
+}
+
+/* One coarse step of the 3D two-level grid, in the order of the 2D one. */
+int orc_refined3_step(const orc_problem *Pc, const orc_problem *Pf, const orc_patch3 *G,
+                      double *fc, double *fc_work, double *ff, double *ff_work, double *M0,
+                      double *M1, int64_t step)
+{
+    const lattice_t *L = lattice(Pc->lattice);
+    const int64_t Nc = ncell(Pc);
+    coarse_plane_moments3(Pc, G, fc, M1);
+    orc_step(Pc, fc, fc_work, step);
+    orc_step(Pf, ff, ff_work, 2 * step);
+    fill_fine_shell3(Pc, Pf, G, M0, M1, 0.5, ff_work);
+    orc_step(Pf, ff_work, ff, 2 * step + 1);
+    fill_fine_shell3(Pc, Pf, G, M0, M1, 1.0, ff);
+    restrict_to_coarse3(Pc, Pf, G, ff_work, fc_work);
+    memcpy(fc, fc_work, sizeof(double) * (size_t)Nc * (size_t)L->q);
+    memcpy(M0, M1, sizeof(double) * 10 * (size_t)Nc);
+    return 0;
+}
