@@ -33,6 +33,7 @@ _lib = None
 
 D2Q9, D3Q19 = 0, 1
 PERIODIC, VELOCITY, OUTFLOW, FREESLIP, PRESSURE = 0, 1, 2, 3, 4
+RR, BGK = 0, 1  # collision models
 CS2 = 1.0 / 3.0
 
 
@@ -65,6 +66,7 @@ class _Problem(C.Structure):
         ("radial", C.c_double * 6),
         ("solid", C.POINTER(C.c_uint8)),
         ("g", C.c_double * 3),
+        ("collision", C.c_int),
     ]
 
 
@@ -198,6 +200,7 @@ class Problem:
         self.solid = None
         self.g = [0.0, 0.0, 0.0]
         self.radial = [0.0] * 6
+        self.collision = RR  # RR: rrBGK (Eq. optimizedLB); BGK: plain BGK (Eq. standardLB)
 
     @property
     def ncell(self) -> int:
@@ -231,6 +234,7 @@ class Problem:
             s.u_ref[a] = self.u_ref[a]
             s.g[a] = self.g[a]
         s.tau = self.tau
+        s.collision = self.collision
         for f in range(6):
             s.face_kind[f] = self.face_kind[f]
             s.rho_face[f] = self.rho_face[f]

@@ -278,6 +278,78 @@ static void collide(const lattice_t *L, const double *f, double tau, double chi,
         }
 }
 
+/* Eq. truncatedEq: the quadratic equilibrium of the plain LBM-BGK,
+ * w_i rho (1 + xi.u / c_s^2 + (xi.u)^2 / (2 c_s^4) - |u|^2 / (2 c_s^2)). */
+static void feq_quadratic(const lattice_t *L, double rho, const double u[3], double *out)
+{
+    double uu = 0.0;
+    for (int a = 0; a < L->d; ++a) uu += u[a] * u[a];
+    for (int i = 0; i < L->q; ++i) {
+        double xu = 0.0;
+        for (int a = 0; a < L->d; ++a) xu += L->xi[i][a] * u[a];
+        out[i] = L->w[i] * rho * (1.0 + xu / CS2 + xu * xu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
+    }
+}
+
+/* Second-order Hermite part of f^neq, w_i H2_i : Pi^neq / (2 c_s^4): the
+ * off-equilibrium part a boundary node is rebuilt with under plain BGK. */
+static void fneq_second(const lattice_t *L, double Pn[3][3], double *out)
+{
+    for (int i = 0; i < L->q; ++i) {
+        double h2 = 0.0;
+        for (int a = 0; a < L->d; ++a)
+            for (int b = 0; b < L->d; ++b) h2 += H2(L, i, a, b) * Pn[a][b];
+        out[i] = L->w[i] * h2 / (2.0 * CS2 * CS2);
+    }
+}
+
+/* Plain BGK collision (Eq. standardLB): f* = f - (f - f^eq) / tau with the
+ * quadratic f^eq; in a sponge cell f^eq is taken at rho*, u* (reading R4) and
+ * the damping term chi (f^eq(rho_ref, u_ref) - f^eq(rho*, u*)) is added. */
+static void collide_bgk(const lattice_t *L, const double *f, double tau, double chi, double rho_ref,
+                        const double u_ref[3], const double g[3], double *out)
+{
+    double rho, j[3], Pi[3][3], u[3], feq[19];
+    moments(L, f, &rho, j, Pi);
+    double rs = rho;
+    if (chi > 0.0) {
+        rs = (rho + 0.5 * chi * rho_ref) / (1.0 + 0.5 * chi);
+        for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * chi * rho_ref * u_ref[a]) / (1.0 + 0.5 * chi) / rs;
+    } else {
+        for (int a = 0; a < 3; ++a) u[a] = j[a] / rho;
+    }
+    feq_quadratic(L, rs, u, feq);
+    for (int i = 0; i < L->q; ++i) out[i] = f[i] - (f[i] - feq[i]) / tau;
+    if (chi > 0.0) {
+        double fref[19];
+        feq_quadratic(L, rho_ref, u_ref, fref);
+        for (int i = 0; i < L->q; ++i) out[i] += chi * (fref[i] - feq[i]);
+    }
+    if (g && (g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0))
+        for (int i = 0; i < L->q; ++i) {
+            double xg = 0.0;
+            for (int a = 0; a < 3; ++a) xg += L->xi[i][a] * g[a];
+            out[i] += L->w[i] * rho * xg / CS2;
+        }
+}
+
+/* Rebuilt boundary node: feqH(rho, u) + (1 - 1/tau) fneqH(u, Pi^neq) under
+ * rrBGK; under plain BGK the node is rebuilt to second order, f^eq + f^neq_2,
+ * and the BGK collision of that is f^eq + (1 - 1/tau) f^neq_2. */
+static void rebuilt_node(int collision, double tau, const lattice_t *L, double rho, const double u[3],
+                         double Pn[3][3], double *out)
+{
+    double feq[19], fneq[19];
+    if (collision == 1) {
+        feq_quadratic(L, rho, u, feq);
+        fneq_second(L, Pn, fneq);
+    } else {
+        feqH(L, rho, u, feq);
+        fneqH(L, u, Pn, fneq);
+    }
+    for (int i = 0; i < L->q; ++i) out[i] = feq[i] + (1.0 - 1.0 / tau) * fneq[i];
+}
+
 /* ------------------------------------------------------------------------ */
 /* Counter-based uniform numbers (reading R9)                                 */
 /* ------------------------------------------------------------------------ */
@@ -318,6 +390,7 @@ typedef struct {
     double radial[6];        /* circular (spherical) layer: cx, cy, cz, r0, W, chi_max; W = 0: none */
     const uint8_t *solid;    /* optional per cell: 1 = solid wall, 2 = fixed */
     double g[3];             /* oracle-only body force */
+    int collision;           /* 0 = rrBGK (Eq. optimizedLB), 1 = BGK (Eq. standardLB) */
 } orc_problem;
 
 static int64_t ncell(const orc_problem *P) { return (int64_t)P->n[0] * P->n[1] * P->n[2]; }
@@ -419,7 +492,7 @@ void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int6
 
     if (inlet >= 0 && P->face_kind[inlet] != BC_VELOCITY) {
         /* Free-slip (R16) or constant-pressure (R17) node. */
-        double rho, j[3], Pi[3][3], us[3], Pn[3][3], feq[19], fneq[19];
+        double rho, j[3], Pi[3][3], us[3], Pn[3][3];
         moments(L, f, &rho, j, Pi);
         for (int a = 0; a < 3; ++a) us[a] = j[a] / rho;
         pi_neq(L->d, rho, us, Pi, Pn);
@@ -431,15 +504,13 @@ void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int6
         } else {
             rho = P->rho_face[inlet];
         }
-        feqH(L, rho, us, feq);
-        fneqH(L, us, Pn, fneq);
-        for (int i = 0; i < L->q; ++i) out[i] = feq[i] + (1.0 - 1.0 / P->tau) * fneq[i];
+        rebuilt_node(P->collision, P->tau, L, rho, us, Pn, out);
         return;
     }
 
     if (inlet >= 0) {
         /* Velocity node (R6). */
-        double rho, j[3], Pi[3][3], us[3], ub[3], Pn[3][3], feq[19], fneq[19];
+        double rho, j[3], Pi[3][3], us[3], ub[3], Pn[3][3];
         moments(L, f, &rho, j, Pi);
         for (int a = 0; a < 3; ++a) us[a] = j[a] / rho;
         pi_neq(L->d, rho, us, Pi, Pn);
@@ -455,13 +526,14 @@ void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int6
                     ub[a] += P->noise_amp * mag * (2.0 * orc_u01(base + (uint64_t)a) - 1.0);
             }
         }
-        feqH(L, rho, ub, feq);
-        fneqH(L, ub, Pn, fneq);
-        for (int i = 0; i < L->q; ++i) out[i] = feq[i] + (1.0 - 1.0 / P->tau) * fneq[i];
+        rebuilt_node(P->collision, P->tau, L, rho, ub, Pn, out);
         return;
     }
 
-    collide(L, f, P->tau, sponge_chi(P, c), P->rho_ref, P->u_ref, P->g, out);
+    if (P->collision == 1)
+        collide_bgk(L, f, P->tau, sponge_chi(P, c), P->rho_ref, P->u_ref, P->g, out);
+    else
+        collide(L, f, P->tau, sponge_chi(P, c), P->rho_ref, P->u_ref, P->g, out);
 }
 
 /* Post-collision populations of a list of cells (out: n x q, cell-major). */
