@@ -336,6 +336,37 @@ def pprime_errors(lbm, torch, stream):
     return res
 
 
+def stability_ab(lbm, stream, n=128, U=0.1, taus=(0.5001, 0.5002, 0.5005, 0.501, 0.502, 0.505)):
+    """A/B of the collision models on the periodic double shear layer (D2Q9
+    n^2, U = 0.1, kappa = 80, delta = 0.05, FP64 storage): for each tau the
+    step at which the populations stop being finite (checked every n/U/8
+    steps up to 2 n / U, two convective times), or None when the run stays
+    finite.  Sec. I of the paper motivates rrBGK by the instability of the
+    plain BGK at low viscosity."""
+    from paper_1710_02065_gb300 import inputs as _inp
+    rho0, u0 = _inp.double_shear_layer(n, U)
+    horizon = int(round(2 * n / U))
+    chunk = max(1, horizon // 16)
+    out = {"workload": f"D2Q9 double shear layer {n}^2, U {U}, kappa 80, delta 0.05, FP64, {horizon} steps",
+           "rrBGK": {}, "BGK": {}}
+    for name, model in (("rrBGK", lbm.LBM_COLLISION_RR), ("BGK", lbm.LBM_COLLISION_BGK)):
+        for tau in taus:
+            s = lbm.Solver(lbm.LBM_D2Q9, (n, n, 1), tau, lbm.LBM_FP64, stream=stream.cuda_stream)
+            lbm.lbm_set_collision(s.h, model)
+            s.set_state(rho0, u0)
+            t, failed = 0, None
+            while t < horizon:
+                lbm.lbm_step(s.h, chunk)
+                t += chunk
+                _, _, rc = s.reduce()
+                if rc != 0:
+                    failed = t
+                    break
+            out[name][str(tau)] = failed
+            s.close()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # cylinder workloads (single level and 2:1 two-level) and serving
 # ---------------------------------------------------------------------------
@@ -445,6 +476,47 @@ def run_cylinder_two_level(lbm, torch, args):
             "mlups_incl_sampling": cells * total / wall / 1e6, "stable": rc == 0, "tau_c": tau_c, "tau_f": tau_f}
 
 
+def run_jet_two_level(lbm, torch, args):
+    """2:1 two-level D3Q19 round jet: the 384x256x256 jet lattice (FP32,
+    Re_D 1e4, sponges, inlet noise) with a fine patch over the near-nozzle
+    region, coarse [2, 66] x [96, 160] x [96, 160] (129^3 fine nodes, the
+    inlet disc of diameter 24 in the middle of its cross-section).  Cell
+    updates per coarse step: coarse cells + 2 x fine cells; time by CUDA
+    events over args.steps coarse steps after args.warmup."""
+    spec = jet_spec()
+    stream = torch.cuda.Stream()
+    s = configure_gpu(lbm, spec, lbm.PRECISIONS[args.precision], stream.cuda_stream)
+    n = s.ncell
+    X0, Y0, Z0, W = 2, 96, 96, 64
+    lbm.lbm_add_refinement_patch(s.h, (X0, Y0, Z0), (W, W, W))
+    ext, tau_f = lbm.lbm_level_info(s.h, 1)
+    nf = int(np.prod(ext))
+    lbm.lbm_set_state_level(s.h, 1, np.ones(nf), np.zeros((nf, 3)))
+    s.set_state(np.ones(n), np.zeros((n, 3)))
+    lbm.lbm_step(s.h, args.warmup)
+    s.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    info0 = s.info()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        lbm.lbm_step(s.h, args.steps)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = s.info()["launches"] - info0["launches"]
+    _, _, rc = s.reduce()
+    rf = np.zeros(nf)
+    lbm.lbm_moments_level(s.h, 1, rf, None, None)
+    s.close()
+    cells = n + 2 * nf
+    return {"workload": f"D3Q19 round jet 384x256x256 + 2:1 patch {ext[0]}x{ext[1]}x{ext[2]} over the nozzle, "
+                        f"{args.precision}", "metric": "cell updates per second (coarse + 2 x fine per coarse step)",
+            "mlups": cells * args.steps / (ms / 1e3) / 1e6, "ms_per_coarse_step": ms / args.steps,
+            "coarse_steps": args.steps, "launches_per_coarse_step": launches / args.steps,
+            "tau_c": spec["tau"], "tau_f": tau_f, "stable": rc == 0 and bool(np.isfinite(rf).all())}
+
+
 def run_serving(lbm, torch, args):
     from paper_1710_02065_gb300 import inputs, serving
     reqs = inputs.serving_requests(args.requests, seed=5, rate_per_s=args.rate, steps_scale=args.steps_scale)
@@ -495,7 +567,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape (no autotuning)")
-    ap.add_argument("--workload", default="jet", choices=["jet", "cylinder", "cylinder2level", "serving"],
+    ap.add_argument("--workload", default="jet", choices=["jet", "cylinder", "cylinder2level", "jet2level",
+                                                          "serving"],
                     help="jet: the headline benchmark line; the others print their own JSON line")
     ap.add_argument("--cyl-steps", type=int, default=40000, help="fine-resolution steps of the cylinder runs")
     ap.add_argument("--requests", type=int, default=512)
@@ -524,7 +597,8 @@ def main():
     from paper_1710_02065_gb300 import lbm
 
     if args.workload != "jet":
-        fn = {"cylinder": run_cylinder, "cylinder2level": run_cylinder_two_level, "serving": run_serving}
+        fn = {"cylinder": run_cylinder, "cylinder2level": run_cylinder_two_level, "jet2level": run_jet_two_level,
+              "serving": run_serving}
         out = fn[args.workload](lbm, torch, args)
         if rank == 0:
             print(json.dumps(out), flush=True)
@@ -576,6 +650,7 @@ def main():
 
     if not args.no_extra:
         extra["pprime_error_vs_fp64"] = pprime_errors(lbm, torch, stream)
+        extra["stability_ab"] = stability_ab(lbm, stream)
         from paper_1710_02065_gb300 import inputs as _inp, serving as _srv
         reqs = _inp.serving_requests(96, seed=5, rate_per_s=40.0, steps_scale=0.1)
         sv = _srv.serve(reqs, hbm_budget_bytes=8 << 30, max_slots=256, steps_per_round=50)

@@ -273,6 +273,24 @@ int lbm_set_launch(lbm_handle h, int block, int cells_per_thread);
 int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread);
 
 /*
+ * lbm_set_collision -- collision model of the single-level update (Sec. II.A).
+ *   LBM_COLLISION_RR  (default) recursive Hermite-regularized rrBGK, order 3
+ *                     (Eq. optimizedLB with Eq. eqH, Eq. neqH, Eq. recursive2).
+ *   LBM_COLLISION_BGK plain LBM-BGK, f* = f - (f - f^eq)/tau with the
+ *                     quadratic equilibrium of Eq. truncatedEq (Eq. standardLB):
+ *                     the A/B baseline the paper improves on.  Sponge cells
+ *                     take f^eq at rho*, u* and add chi (f^eq(rho_ref, u_ref) -
+ *                     f^eq(rho*, u*)); velocity, free-slip and pressure nodes
+ *                     are rebuilt to second order, f^eq + (1 - 1/tau) f^neq_2.
+ *                     Runs on the general one-cell-per-thread kernel; not
+ *                     available with a refinement patch (LBM_EINVAL either way
+ *                     round) nor in the solve server.
+ */
+#define LBM_COLLISION_RR 0
+#define LBM_COLLISION_BGK 1
+int lbm_set_collision(lbm_handle h, int model);
+
+/*
  * lbm_set_staging -- the row-staged update kernel (a tuning knob; same update
  * as the other kernels, results equal up to FP round-off order).  A
  * persistent grid of CTAs walks over tiles of whole x rows; bulk asynchronous
@@ -324,23 +342,25 @@ int lbm_info(lbm_handle h, int64_t *step, int64_t *launches, double *bytes_per_c
              double *tau);
 
 /*
- * Two-level grid (Sec. II.B, multi-domain 2:1 refinement; D2Q9).
+ * Two-level grid (Sec. II.B, multi-domain 2:1 refinement; D2Q9 and D3Q19).
  *
  * lbm_add_refinement_patch -- add a fine level over the coarse nodes
- * origin[0]..origin[0]+extent[0], origin[1]..origin[1]+extent[1] (extent >= 4,
- * at least 2 coarse cells from every face).  The fine level has
- * (2 extent[0] + 1) x (2 extent[1] + 1) nodes, dx_f = dx_c / 2, two fine
- * steps per coarse step (Eq. convective), tau_f = 2 tau_c - 1/2 (same
- * physical viscosity), starts at rest.  Coupling per coarse step: the fine
- * boundary ring is rebuilt from coarse rho, u, Pi^neq interpolated in space
- * (copy at coincident nodes, 4-point cubic at mid nodes) and linearly in time
- * (t + 1/2, t + 1), Eq. couplingFC; the first ring of covered coarse nodes is
- * rebuilt from the coincident fine node's rho, u and its 3 x 3 full-weighted
- * (1,2,1)x(1,2,1)/16 Pi^neq, Eq. couplingCF.  f^neq is rescaled by
- * tau_f / (2 tau_c) coarse -> fine and 2 tau_c / tau_f fine -> coarse (the
- * leading-order Chapman-Enskog scaling of Sec. II.B).  Deeper covered coarse
- * cells are frozen.  Solids of level 1 must stay 2 fine cells inside the ring.
- * At most one patch per handle.
+ * origin[a]..origin[a]+extent[a] on every axis a of the lattice (x, y; and z
+ * for D3Q19; extent >= 4, at least 2 coarse cells from every face).  The fine
+ * level has 2 extent[a] + 1 nodes per axis, dx_f = dx_c / 2, two fine steps
+ * per coarse step (Eq. convective), tau_f = 2 tau_c - 1/2 (same physical
+ * viscosity), starts at rest.  Coupling per coarse step: the fine boundary
+ * ring (2D) / shell (3D) is rebuilt from coarse rho, u, Pi^neq interpolated
+ * in space (copy at coincident nodes; the 4-point cubic (-1, 9, 9, -1)/16
+ * along every axis on which the fine node falls between coarse nodes, their
+ * tensor product on the 3D interface planes) and linearly in time (t + 1/2,
+ * t + 1), Eq. couplingFC; the first ring / shell of covered coarse nodes is
+ * rebuilt from the coincident fine node's rho, u and its full-weighted
+ * Pi^neq ((1,2,1)^2 / 16 in 2D, (1,2,1)^3 / 64 in 3D), Eq. couplingCF.
+ * f^neq is rescaled by tau_f / (2 tau_c) coarse -> fine and 2 tau_c / tau_f
+ * fine -> coarse (the leading-order Chapman-Enskog scaling of Sec. II.B).
+ * Deeper covered coarse cells are frozen.  Solids of level 1 must stay 2 fine
+ * cells inside the ring / shell.  At most one patch per handle.
  *
  * Level-indexed variants (level 0 = coarse, the plain functions; level 1 =
  * fine): extents and tau of a level; geometry (fine cell types, the ring is

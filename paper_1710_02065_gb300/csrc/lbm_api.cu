@@ -58,6 +58,7 @@ struct lbm_ctx {
     int stages = 0;       // its shared-memory stages (0: 2)
     int rows_block = 0;   // its threads per CTA (0: automatic)
     unsigned *err_d = nullptr;  // device error word of the row-staged kernel (bounded waits)
+    int collision = LBM_COLLISION_RR;
     double *red_d = nullptr;  // reduction partials + result
     int red_blocks = 0;
     std::vector<uint8_t> user_mask;  // caller's cell types (host copy); empty: none
@@ -378,9 +379,13 @@ static int upload_coarse_mask(lbm_ctx *h)
     std::vector<uint8_t> m(h->user_mask);
     if (m.empty()) m.assign((size_t)h->ncell, (uint8_t)LBM_CELL_FLUID);
     if (patch) {
+        // covered coarse nodes (strictly inside the patch on every axis of it)
         const RefineGeom &g = h->fine->geom;
-        for (int y = g.Y0 + 1; y < g.Y0 + g.Hc; ++y)
-            for (int x = g.X0 + 1; x < g.X0 + g.Wc; ++x) m[(size_t)x + (size_t)h->n[0] * y] = LBM_CELL_FIXED;
+        const int z0 = h->d == 3 ? g.Z0 + 1 : 0, z1 = h->d == 3 ? g.Z0 + g.Dc : 1;
+        for (int z = z0; z < z1; ++z)
+            for (int y = g.Y0 + 1; y < g.Y0 + g.Hc; ++y)
+                for (int x = g.X0 + 1; x < g.X0 + g.Wc; ++x)
+                    m[(size_t)x + (size_t)h->n[0] * ((size_t)y + (size_t)h->n[1] * z)] = LBM_CELL_FIXED;
     }
     if (!h->solid_d) CUDA_TRY(h, cudaMalloc(&h->solid_d, (size_t)h->ncell));
     CUDA_TRY(h, cudaMemcpyAsync(h->solid_d, m.data(), (size_t)h->ncell, cudaMemcpyHostToDevice, h->stream));
@@ -393,10 +398,14 @@ static int upload_fine_mask(lbm_ctx *h)
     FineLevel *F = h->fine;
     std::vector<uint8_t> m(F->user_mask);
     if (m.empty()) m.assign((size_t)F->ncell, (uint8_t)LBM_CELL_FLUID);
-    for (int j = 0; j < F->n[1]; ++j)
-        for (int i = 0; i < F->n[0]; ++i)
-            if (i == 0 || j == 0 || i == F->n[0] - 1 || j == F->n[1] - 1)
-                m[(size_t)i + (size_t)F->n[0] * j] = LBM_CELL_FIXED;
+    // the boundary ring (2D) / shell (3D) of the fine box is rebuilt from coarse data
+    const bool three = h->d == 3;
+    for (int k = 0; k < F->n[2]; ++k)
+        for (int j = 0; j < F->n[1]; ++j)
+            for (int i = 0; i < F->n[0]; ++i)
+                if (i == 0 || j == 0 || i == F->n[0] - 1 || j == F->n[1] - 1 ||
+                    (three && (k == 0 || k == F->n[2] - 1)))
+                    m[(size_t)i + (size_t)F->n[0] * ((size_t)j + (size_t)F->n[1] * k)] = LBM_CELL_FIXED;
     if (!F->mask_d) CUDA_TRY(h, cudaMalloc(&F->mask_d, (size_t)F->ncell));
     CUDA_TRY(h, cudaMemcpyAsync(F->mask_d, m.data(), (size_t)F->ncell, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -683,6 +692,7 @@ static int build_params(lbm_ctx *h, StepParams &p)
     p.noise_amp = h->noise_amp;
     p.omega = 1.0 - 1.0 / h->tau;
     p.solid = h->solid_d;
+    p.bgk = h->collision == LBM_COLLISION_BGK ? 1 : 0;
     set_bulk_box(p);
     return LBM_OK;
 }
@@ -701,6 +711,13 @@ static bool staging_wanted(const lbm_ctx *h)
 // length allows it; else the general kernel.
 static cudaError_t launch_update(lbm_ctx *h, const StepParams &p, const void *fin, void *fout)
 {
+    if (p.bgk) {
+        // plain BGK: the general kernel only
+        h->launches += 1;
+        const int block = h->block > 0 ? h->block : block_default(1);
+        return h->lattice == LBM_D2Q9 ? step_d2q9(h->prec, p, fin, fout, block, h->stream)
+                                      : step_d3q19(h->prec, p, fin, fout, block, h->stream);
+    }
     if (staging_wanted(h)) {
         const cudaError_t e = h->lattice == LBM_D2Q9
                                   ? rows_d2q9(h->prec, p, fin, fout, h->rows_block, h->stages, h->err_d, h->stream)
@@ -738,9 +755,43 @@ static void fine_params(lbm_ctx *h, StepParams &p)
     set_bulk_box(p);
 }
 
+// D3Q19 patch: plane moments, fine shell, covered coarse shell
+template <class S>
+static cudaError_t refine_kernels3(lbm_ctx *h, int stage, int a_half)
+{
+    FineLevel *F = h->fine;
+    const RefineGeom &g = F->geom;
+    cudaStream_t st = h->stream;
+    switch (stage) {
+    case 0:  // coarse plane moments at t + 1 from the pre-step coarse field
+    case 3: {  // plane moments at t = 0: local moments of the stored coarse field
+        const int n = plane3_count(g);
+        double *M = stage == 0 ? F->M[1 - F->mcur] : F->M[F->mcur];
+        k_plane_moments3<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)h->f[h->cur], h->solid_d, stage == 0 ? 1 : 0,
+                                                           M);
+        break;
+    }
+    case 1: {  // fine shell at t + 1/2 (a_half = 1) or t + 1 (a_half = 0)
+        const int n = shell3_count(g.nfx, g.nfy, g.nfz);
+        k_fill_shell3<S><<<grid1(n, 128), 128, 0, st>>>(g, F->M[F->mcur], F->M[1 - F->mcur], a_half ? 0.5 : 1.0,
+                                                         F->tau / (2.0 * h->tau), F->tau, (S *)F->f[F->cur]);
+        break;
+    }
+    case 2: {  // covered coarse shell from the fine field; fine moments pulled from f(t + 1/2)
+        const int n = shell3_count(g.Wc - 1, g.Hc - 1, g.Dc - 1);
+        k_restrict3<S><<<grid1(n, 64), 64, 0, st>>>(g, (const S *)F->f[1 - F->cur], F->mask_d, 2.0 * h->tau / F->tau,
+                                                     h->tau, (S *)h->f[h->cur]);
+        break;
+    }
+    }
+    h->launches += 1;
+    return cudaGetLastError();
+}
+
 template <class S>
 static cudaError_t refine_kernels(lbm_ctx *h, int stage, int a_half)
 {
+    if (h->d == 3) return refine_kernels3<S>(h, stage, a_half);
     FineLevel *F = h->fine;
     const RefineGeom &g = F->geom;
     cudaStream_t st = h->stream;
@@ -909,21 +960,29 @@ extern "C" int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const
     CHECK_HANDLE(h);
     h->cfg_version++;
     if (h->fine) return fail(h, LBM_EINVAL, "the handle already has a refinement patch");
-    if (h->lattice != LBM_D2Q9) return fail(h, LBM_EINVAL, "refinement patches are implemented for D2Q9");
+    if (h->collision != LBM_COLLISION_RR)
+        return fail(h, LBM_EINVAL, "refinement patches couple rrBGK levels; select LBM_COLLISION_RR first");
     if (!origin || !extent) return fail(h, LBM_EINVAL, "origin and extent are required");
+    const bool three = h->d == 3;
     const int X0 = origin[0], Y0 = origin[1], Wc = extent[0], Hc = extent[1];
-    if (Wc < 4 || Hc < 4) return fail(h, LBM_EINVAL, "patch extent must be >= 4 coarse cells per axis");
-    if (X0 < 2 || Y0 < 2 || X0 + Wc > h->n[0] - 3 || Y0 + Hc > h->n[1] - 3)
+    const int Z0 = three ? origin[2] : 0, Dc = three ? extent[2] : 0;
+    if (Wc < 4 || Hc < 4 || (three && Dc < 4))
+        return fail(h, LBM_EINVAL, "patch extent must be >= 4 coarse cells per axis");
+    if (X0 < 2 || Y0 < 2 || X0 + Wc > h->n[0] - 3 || Y0 + Hc > h->n[1] - 3 ||
+        (three && (Z0 < 2 || Z0 + Dc > h->n[2] - 3)))
         return fail(h, LBM_EINVAL, "patch must keep 2 coarse cells from every face");
+    if ((int64_t)(2 * Wc + 1) * (2 * Hc + 1) * (three ? 2 * Dc + 1 : 1) > 2147483647LL)
+        return fail(h, LBM_EINVAL, "the fine level would hold more than 2^31 - 1 cells");
     FineLevel *F = new FineLevel();
     F->n[0] = 2 * Wc + 1;
     F->n[1] = 2 * Hc + 1;
-    F->n[2] = 1;
-    F->ncell = (int64_t)F->n[0] * F->n[1];
+    F->n[2] = three ? 2 * Dc + 1 : 1;
+    F->ncell = (int64_t)F->n[0] * F->n[1] * F->n[2];
     F->tau = 2.0 * h->tau - 0.5;
-    F->geom = RefineGeom{X0, Y0, Wc, Hc, h->n[0], h->n[1], F->n[0], F->n[1]};
+    F->geom = RefineGeom{X0, Y0, Wc, Hc, h->n[0], h->n[1], F->n[0], F->n[1], Z0, Dc, h->n[2], F->n[2]};
     const size_t bytes = (size_t)h->q * (size_t)F->ncell * h->elem;
-    const size_t mbytes = sizeof(double) * 6 * (size_t)line_count(F->geom);
+    const size_t mbytes = three ? sizeof(double) * 10 * (size_t)box3_entries(F->geom)
+                                : sizeof(double) * 6 * (size_t)line_count(F->geom);
     bool ok = true;
     for (int k = 0; k < 2 && ok; ++k)
         ok = cudaMalloc(&F->f[k], bytes) == cudaSuccess && cudaMalloc(&F->M[k], mbytes) == cudaSuccess &&
@@ -1074,6 +1133,18 @@ extern "C" int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread)
     if (h->solid_d || vec == 1 || !vec_supported(h->prec, vec) || h->n[0] % vec != 0) vec = 1;
     if (block) *block = h->block > 0 ? h->block : block_default(vec);  // level 0
     if (cells_per_thread) *cells_per_thread = vec;
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_collision(lbm_handle h, int model)
+{
+    CHECK_HANDLE(h);
+    h->cfg_version++;
+    if (model != LBM_COLLISION_RR && model != LBM_COLLISION_BGK)
+        return fail(h, LBM_EINVAL, "collision model %d is not LBM_COLLISION_RR or LBM_COLLISION_BGK", model);
+    if (model == LBM_COLLISION_BGK && h->fine)
+        return fail(h, LBM_EINVAL, "plain BGK is not available with a refinement patch");
+    h->collision = model;
     return LBM_OK;
 }
 

@@ -1,5 +1,5 @@
 // refine.cuh -- two-level 2:1 grid coupling kernels (Sec. II.B, Eq. couplingCF,
-// Eq. couplingFC), D2Q9.
+// Eq. couplingFC), D2Q9 and D3Q19 (the 3D kernels are at the end of the file).
 //
 // Layout (vertex based, dx_f = dx_c / 2, dt_f = dt_c / 2): the fine patch
 // covers the coarse nodes X0..X0+Wc, Y0..Y0+Hc; fine node (i, j) sits at
@@ -30,6 +30,8 @@ namespace rr {
 struct RefineGeom {
     int X0, Y0, Wc, Hc;
     int nxc, nyc, nfx, nfy;
+    // third axis of a D3Q19 patch (zero / one for D2Q9)
+    int Z0, Dc, nzc, nfz;
 };
 
 // number of line entries: two horizontal lines of Wc + 3, two vertical of Hc + 3
@@ -115,13 +117,14 @@ __device__ void store_rebuilt_2d(S *__restrict__ f, int64_t N, int64_t cell, con
     p.xx = C(alpha) * m[3]; p.xy = C(alpha) * m[4]; p.yy = C(alpha) * m[5];
     p.zz = p.xz = p.yz = C(0);
     add_neq<C, 2>(k, C(1.0 - 1.0 / tau), m[1], m[2], C(0), p);
-    Store<S>::st(f + cell, rebuild_rest<D2Q9, C>(k));
+    const RebuildPre<C> r = rebuild_prep<D2Q9, C>(k);
+    Store<S>::st(f + cell, rebuild_rest<D2Q9, C>(k, r));
 #pragma unroll
     for (int i = 1; i <= D2Q9::HALF; ++i) {
-        C e, o;
-        rebuild_pair<D2Q9, C>(k, i, e, o);
-        Store<S>::st(f + (int64_t)i * N + cell, C(weight<D2Q9>(i)) * (e + o));
-        Store<S>::st(f + (int64_t)(i + D2Q9::HALF) * N + cell, C(weight<D2Q9>(i)) * (e - o));
+        C gp, gm;
+        rebuild_pair<D2Q9, C>(k, r, i, gp, gm);
+        Store<S>::st(f + (int64_t)i * N + cell, gp);
+        Store<S>::st(f + (int64_t)(i + D2Q9::HALF) * N + cell, gm);
     }
 }
 
@@ -227,6 +230,238 @@ __global__ void k_restrict(RefineGeom g, const S *__restrict__ ff_prev, const ui
             if (k == 0 && l == 0) { mc[0] = m[0]; mc[1] = m[1]; mc[2] = m[2]; }
         }
     store_rebuilt_2d<S>(fc, (int64_t)g.nxc * g.nyc, x + (int64_t)g.nxc * y, mc, alpha, tau_c);
+}
+
+// ===========================================================================
+// D3Q19 patches.  The fine patch covers the coarse nodes X0..X0+Wc,
+// Y0..Y0+Hc, Z0..Z0+Dc; fine node (i, j, k) sits at (X0 + i/2, Y0 + j/2,
+// Z0 + k/2).  The fine boundary shell is rebuilt from coarse data, the first
+// shell of covered coarse nodes from fine data.  Interface moments m = (rho -
+// 1, ux, uy, uz, Pxx, Pxy, Pxz, Pyy, Pyz, Pzz) of the coarse nodes on the six
+// face planes of the patch box (extended by one node past every edge) are
+// kept in a dense box array over [X0-1, X0+Wc+1] x [Y0-1, Y0+Hc+1] x
+// [Z0-1, Z0+Dc+1] (10 doubles per node; off-plane entries unused).
+//   k_plane_moments3 : coarse moments on the six planes
+//   k_fill_shell3    : fine shell from plane moments mixed in time and
+//                      interpolated along every axis on which the fine node is
+//                      odd by (-1, 9, 9, -1)/16 (tensor product on the planes)
+//   k_restrict3      : covered coarse shell from the coincident fine node's
+//                      rho, u and its (1,2,1)^3 / 64 full-weighted Pi^neq
+// ===========================================================================
+__host__ __device__ inline int64_t box3_entries(const RefineGeom &g)
+{
+    return (int64_t)(g.Wc + 3) * (g.Hc + 3) * (g.Dc + 3);
+}
+__device__ inline int64_t box3_index(const RefineGeom &g, int x, int y, int z)
+{
+    return (x - g.X0 + 1) + (int64_t)(g.Wc + 3) * ((y - g.Y0 + 1) + (int64_t)(g.Hc + 3) * (z - g.Z0 + 1));
+}
+// number of plane entries (edge nodes shared by two planes are listed twice)
+__host__ __device__ inline int plane3_count(const RefineGeom &g)
+{
+    return 2 * (g.Hc + 3) * (g.Dc + 3) + 2 * (g.Wc + 3) * (g.Dc + 3) + 2 * (g.Wc + 3) * (g.Hc + 3);
+}
+__device__ inline void plane3_coord(const RefineGeom &g, int t, int &x, int &y, int &z)
+{
+    const int A = (g.Hc + 3) * (g.Dc + 3), B = (g.Wc + 3) * (g.Dc + 3);
+    if (t < 2 * A) {
+        const int side = t / A, r = t - side * A;
+        x = g.X0 + side * g.Wc; y = g.Y0 - 1 + r % (g.Hc + 3); z = g.Z0 - 1 + r / (g.Hc + 3);
+    } else if (t < 2 * A + 2 * B) {
+        t -= 2 * A;
+        const int side = t / B, r = t - side * B;
+        y = g.Y0 + side * g.Hc; x = g.X0 - 1 + r % (g.Wc + 3); z = g.Z0 - 1 + r / (g.Wc + 3);
+    } else {
+        t -= 2 * A + 2 * B;
+        const int Cn = (g.Wc + 3) * (g.Hc + 3);
+        const int side = t / Cn, r = t - side * Cn;
+        z = g.Z0 + side * g.Dc; x = g.X0 - 1 + r % (g.Wc + 3); y = g.Y0 - 1 + r / (g.Wc + 3);
+    }
+}
+
+template <class C>
+__device__ inline void pack_moments3(const Mom<C> &mo, C m[10])
+{
+    const C rho = C(1) + mo.dr;
+    const C ux = mo.jx / rho, uy = mo.jy / rho, uz = mo.jz / rho;
+    const Sym2<C> p = pi_neq<C>(mo, mo.dr, rho, ux, uy, uz, 3);
+    m[0] = mo.dr; m[1] = ux; m[2] = uy; m[3] = uz;
+    m[4] = p.xx; m[5] = p.xy; m[6] = p.xz; m[7] = p.yy; m[8] = p.yz; m[9] = p.zz;
+}
+
+// Pre-collision moments at (x, y, z) of a 3D lattice: pull with periodic
+// wrap and halfway bounce-back on mask == 1.
+template <class S>
+__device__ void streamed_moments_3d(const S *__restrict__ f, const uint8_t *__restrict__ mask, int nx, int ny,
+                                    int nz, int x, int y, int z, CT<S> m[10])
+{
+    using C = CT<S>;
+    const int64_t N = (int64_t)nx * ny * nz;
+    const int64_t cell = x + (int64_t)nx * (y + (int64_t)ny * z);
+    C g[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        int sx = x - D3Q19::cx(i), sy = y - D3Q19::cy(i), sz = z - D3Q19::cz(i);
+        sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+        sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
+        const int64_t src = sx + (int64_t)nx * (sy + (int64_t)ny * sz);
+        if (mask && i != 0 && mask[src] == 1)
+            g[i] = Store<S>::ld(f + (int64_t)opp<D3Q19>(i) * N + cell);
+        else
+            g[i] = Store<S>::ld(f + (int64_t)i * N + src);
+    }
+    pack_moments3<C>(moments_pairs<D3Q19, C>(g), m);
+}
+
+template <class S>
+__device__ void local_moments_3d(const S *__restrict__ f, int64_t N, int64_t cell, CT<S> m[10])
+{
+    using C = CT<S>;
+    C g[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell);
+    pack_moments3<C>(moments_pairs<D3Q19, C>(g), m);
+}
+
+// Store feqH(rho, u) + (1 - 1/tau) fneqH(u, alpha Pi^neq) at a cell
+template <class S>
+__device__ void store_rebuilt_3d(S *__restrict__ f, int64_t N, int64_t cell, const CT<S> m[10], double alpha,
+                                 double tau)
+{
+    using C = CT<S>;
+    Coef<C> k{};
+    const C rho = C(1) + m[0];
+    add_eq<C, 3>(k, C(1), m[0], rho, m[1], m[2], m[3]);
+    Sym2<C> p;
+    p.xx = C(alpha) * m[4]; p.xy = C(alpha) * m[5]; p.xz = C(alpha) * m[6];
+    p.yy = C(alpha) * m[7]; p.yz = C(alpha) * m[8]; p.zz = C(alpha) * m[9];
+    add_neq<C, 3>(k, C(1.0 - 1.0 / tau), m[1], m[2], m[3], p);
+    const RebuildPre<C> r = rebuild_prep<D3Q19, C>(k);
+    Store<S>::st(f + cell, rebuild_rest<D3Q19, C>(k, r));
+#pragma unroll
+    for (int i = 1; i <= D3Q19::HALF; ++i) {
+        C gp, gm;
+        rebuild_pair<D3Q19, C>(k, r, i, gp, gm);
+        Store<S>::st(f + (int64_t)i * N + cell, gp);
+        Store<S>::st(f + (int64_t)(i + D3Q19::HALF) * N + cell, gm);
+    }
+}
+
+template <class S>
+__global__ void k_plane_moments3(RefineGeom g, const S *__restrict__ fc, const uint8_t *__restrict__ mask,
+                                 int streamed, double *__restrict__ M)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= plane3_count(g)) return;
+    int x, y, z;
+    plane3_coord(g, t, x, y, z);
+    CT<S> m[10];
+    if (streamed)
+        streamed_moments_3d<S>(fc, mask, g.nxc, g.nyc, g.nzc, x, y, z, m);
+    else
+        local_moments_3d<S>(fc, (int64_t)g.nxc * g.nyc * g.nzc, x + (int64_t)g.nxc * (y + (int64_t)g.nyc * z), m);
+    const int64_t b = box3_index(g, x, y, z);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) M[10 * b + k] = (double)m[k];
+}
+
+// 1D stencil of fine coordinate c on an axis with coarse origin o: the
+// coincident node, or the centred cubic between o + (c-1)/2 and o + (c+1)/2
+template <class C>
+__device__ inline int stencil1(int c, int o, int idx[4], C w[4])
+{
+    if ((c & 1) == 0) {
+        idx[0] = o + c / 2;
+        w[0] = C(1);
+        return 1;
+    }
+    const int a = o + (c - 1) / 2;
+    idx[0] = a - 1; idx[1] = a; idx[2] = a + 1; idx[3] = a + 2;
+    w[0] = C(-0.0625); w[1] = C(0.5625); w[2] = C(0.5625); w[3] = C(-0.0625);
+    return 4;
+}
+
+__host__ __device__ inline int shell3_count(int nx, int ny, int nz)
+{
+    return nx * ny * nz - (nx - 2) * (ny - 2) * (nz - 2);
+}
+// node t of the boundary shell of an nx x ny x nz box
+__device__ inline void shell3_coord(int nx, int ny, int nz, int t, int &i, int &j, int &k)
+{
+    const int A = nx * ny, B = nx * (nz - 2);
+    if (t < 2 * A) {
+        const int side = t / A, r = t - side * A;
+        k = side ? nz - 1 : 0; i = r % nx; j = r / nx;
+    } else if (t < 2 * A + 2 * B) {
+        t -= 2 * A;
+        const int side = t / B, r = t - side * B;
+        j = side ? ny - 1 : 0; i = r % nx; k = 1 + r / nx;
+    } else {
+        t -= 2 * A + 2 * B;
+        const int Cn = (ny - 2) * (nz - 2);
+        const int side = t / Cn, r = t - side * Cn;
+        i = side ? nx - 1 : 0; j = 1 + r % (ny - 2); k = 1 + r / (ny - 2);
+    }
+}
+
+template <class S>
+__global__ void k_fill_shell3(RefineGeom g, const double *__restrict__ M0, const double *__restrict__ M1, double a,
+                              double alpha, double tau_f, S *__restrict__ ff)
+{
+    using C = CT<S>;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= shell3_count(g.nfx, g.nfy, g.nfz)) return;
+    int i, j, k;
+    shell3_coord(g.nfx, g.nfy, g.nfz, t, i, j, k);
+    int ix[4], iy[4], iz[4];
+    C wx[4], wy[4], wz[4];
+    const int sx = stencil1<C>(i, g.X0, ix, wx);
+    const int sy = stencil1<C>(j, g.Y0, iy, wy);
+    const int sz = stencil1<C>(k, g.Z0, iz, wz);
+    const C am = C(a), bm = C(1) - C(a);
+    C m[10];
+#pragma unroll
+    for (int e = 0; e < 10; ++e) m[e] = C(0);
+    for (int c = 0; c < sz; ++c)
+        for (int b = 0; b < sy; ++b)
+            for (int q = 0; q < sx; ++q) {
+                const int64_t e0 = 10 * box3_index(g, ix[q], iy[b], iz[c]);
+                const C wt = wx[q] * wy[b] * wz[c];
+#pragma unroll
+                for (int e = 0; e < 10; ++e) m[e] = fmac(wt, bm * C(M0[e0 + e]) + am * C(M1[e0 + e]), m[e]);
+            }
+    store_rebuilt_3d<S>(ff, (int64_t)g.nfx * g.nfy * g.nfz, i + (int64_t)g.nfx * (j + (int64_t)g.nfy * k), m,
+                        alpha, tau_f);
+}
+
+template <class S>
+__global__ void k_restrict3(RefineGeom g, const S *__restrict__ ff_prev, const uint8_t *__restrict__ fmask,
+                            double alpha, double tau_c, S *__restrict__ fc)
+{
+    using C = CT<S>;
+    const int w = g.Wc - 1, h = g.Hc - 1, d = g.Dc - 1;  // shell of [X0+1, X0+Wc-1] x ...
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= shell3_count(w, h, d)) return;
+    int a, b, c;
+    shell3_coord(w, h, d, t, a, b, c);
+    const int x = g.X0 + 1 + a, y = g.Y0 + 1 + b, z = g.Z0 + 1 + c;
+    const int i = 2 * (x - g.X0), j = 2 * (y - g.Y0), k = 2 * (z - g.Z0);
+    const C w3[3] = {C(1), C(2), C(1)};
+    C mc[10], m[10];
+#pragma unroll
+    for (int e = 0; e < 10; ++e) mc[e] = C(0);
+    for (int l = -1; l <= 1; ++l)
+        for (int q = -1; q <= 1; ++q)
+            for (int p = -1; p <= 1; ++p) {
+                streamed_moments_3d<S>(ff_prev, fmask, g.nfx, g.nfy, g.nfz, i + p, j + q, k + l, m);
+                const C wt = w3[p + 1] * w3[q + 1] * w3[l + 1] * C(1.0 / 64.0);
+#pragma unroll
+                for (int e = 4; e < 10; ++e) mc[e] = fmac(wt, m[e], mc[e]);
+                if (p == 0 && q == 0 && l == 0) { mc[0] = m[0]; mc[1] = m[1]; mc[2] = m[2]; mc[3] = m[3]; }
+            }
+    store_rebuilt_3d<S>(fc, (int64_t)g.nxc * g.nyc * g.nzc, x + (int64_t)g.nxc * (y + (int64_t)g.nyc * z), mc, alpha,
+                        tau_c);
 }
 
 }  // namespace rr

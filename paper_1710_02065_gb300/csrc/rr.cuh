@@ -198,8 +198,9 @@ struct Sym2 {
 
 // Equilibrium coefficients of (rho, u), scaled by s: a0 += s (rho - 1),
 // a1 += s rho u, A2 += s rho u u, A3 += s rho u u u.  dr = rho - 1 is passed
-// separately so that it keeps its own precision.
-template <class C, int D = 3>
+// separately so that it keeps its own precision.  O3 = false stops at second
+// order: the quadratic equilibrium of the plain LBM-BGK (Eq. truncatedEq).
+template <class C, int D = 3, bool O3 = true>
 __device__ __forceinline__ void add_eq(Coef<C> &k, C s, C dr, C rho, C ux, C uy, C uz)
 {
     const C r = s * rho;
@@ -211,14 +212,17 @@ __device__ __forceinline__ void add_eq(Coef<C> &k, C s, C dr, C rho, C ux, C uy,
     k.yy = fmac(ry, uy, k.yy);
     k.xy = fmac(rx, uy, k.xy);
     const C rxx = rx * ux, ryy = ry * uy;
-    k.xxy = fmac(rxx, uy, k.xxy);
-    k.xyy = fmac(ryy, ux, k.xyy);
+    if (O3) {
+        k.xxy = fmac(rxx, uy, k.xxy);
+        k.xyy = fmac(ryy, ux, k.xyy);
+    }
     if (D == 3) {
         const C rz = r * uz;
         k.a1z += rz;
         k.zz = fmac(rz, uz, k.zz);
         k.xz = fmac(rx, uz, k.xz);
         k.yz = fmac(ry, uz, k.yz);
+        if (!O3) return;
         const C rzz = rz * uz;
         k.xxz = fmac(rxx, uz, k.xxz);
         k.xzz = fmac(rzz, ux, k.xzz);
@@ -228,13 +232,22 @@ __device__ __forceinline__ void add_eq(Coef<C> &k, C s, C dr, C rho, C ux, C uy,
 }
 
 // Off-equilibrium coefficients scaled by s: A2 += s Pi^neq and
-// A3 += s a3_neq, a3_neq,abc = u_a P_bc + u_b P_ac + u_c P_ab (Eq. recursive2, n = 3)
-template <class C, int D = 3>
+// A3 += s a3_neq, a3_neq,abc = u_a P_bc + u_b P_ac + u_c P_ab (Eq. recursive2, n = 3);
+// O3 = false: A2 only.
+template <class C, int D = 3, bool O3 = true>
 __device__ __forceinline__ void add_neq(Coef<C> &k, C s, C ux, C uy, C uz, const Sym2<C> &p)
 {
     k.xx = fmac(s, p.xx, k.xx);
     k.yy = fmac(s, p.yy, k.yy);
     k.xy = fmac(s, p.xy, k.xy);
+    if (!O3) {
+        if (D == 3) {
+            k.zz = fmac(s, p.zz, k.zz);
+            k.xz = fmac(s, p.xz, k.xz);
+            k.yz = fmac(s, p.yz, k.yz);
+        }
+        return;
+    }
     const C ux2 = ux + ux, uy2 = uy + uy;
     k.xxy = fmac(s, fmac(ux2, p.xy, uy * p.xx), k.xxy);
     k.xyy = fmac(s, fmac(uy2, p.xy, ux * p.yy), k.xyy);

@@ -57,6 +57,9 @@ struct StepParams {
     // bulk box: cells with blo[a] <= c[a] < bhi[a] on every axis have no
     // boundary role and no sponge (filled by the host from faces and layers)
     int blo[3], bhi[3];
+    // collision model: 0 rrBGK (Eq. optimizedLB), 1 plain BGK (Eq. standardLB;
+    // general kernel only)
+    int bgk;
     // per-direction base addresses of the lattice read (in) and written (out):
     // in[i] = f_in + i * ncell elements; filled by the launchers
     const char *in[19];
@@ -156,11 +159,16 @@ __device__ __forceinline__ C chi_cell(const StepParams &p, C row, int x, int y, 
 
 // ---------------------------------------------------------------------------
 // Collision coefficients of one cell: velocity node, sponge cell or bulk.
+// BGK = true: the plain LBM-BGK (Eq. standardLB) -- boundary nodes rebuilt to
+// second order, f^eq + (1 - 1/tau) f^neq_2; other cells get the quadratic
+// equilibrium part (1 - 1/tau) f^eq (with the sponge's damping) and the
+// caller adds (1 - 1/tau) g_i of the streamed populations.
 // ---------------------------------------------------------------------------
-template <class L, class C>
+template <class L, class C, bool BGK = false>
 __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const Mom<C> &m, C chi, int cx,
                                                      int cy, int cz, int inlet)
 {
+    constexpr bool O3 = !BGK;
     const C om = C(p.omega);
     Coef<C> k{};
     if (inlet >= 0 && p.kind[inlet] != BC_VELOCITY) {
@@ -170,15 +178,15 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
         C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
         Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
         if (p.kind[inlet] == BC_PRESSURE) {
-            add_eq<C, L::D>(k, C(1), C(p.rho_face_m1[inlet]), C(p.rho_face[inlet]), ux, uy, uz);
+            add_eq<C, L::D, O3>(k, C(1), C(p.rho_face_m1[inlet]), C(p.rho_face[inlet]), ux, uy, uz);
         } else {
             const int a = inlet >> 1;
             if (a == 0) { ux = C(0); pn.xy = C(0); pn.xz = C(0); }
             if (a == 1) { uy = C(0); pn.xy = C(0); pn.yz = C(0); }
             if (a == 2) { uz = C(0); pn.xz = C(0); pn.yz = C(0); }
-            add_eq<C, L::D>(k, C(1), m.dr, rho, ux, uy, uz);
+            add_eq<C, L::D, O3>(k, C(1), m.dr, rho, ux, uy, uz);
         }
-        add_neq<C, L::D>(k, om, ux, uy, uz, pn);
+        add_neq<C, L::D, O3>(k, om, ux, uy, uz, pn);
         return k;
     }
     if (inlet >= 0) {
@@ -204,8 +212,8 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
             }
         }
         const C ux = C(ub[0]), uy = C(ub[1]), uz = L::D == 3 ? C(ub[2]) : C(0);
-        add_eq<C, L::D>(k, C(1), m.dr, rho, ux, uy, uz);
-        add_neq<C, L::D>(k, om, ux, uy, uz, pn);
+        add_eq<C, L::D, O3>(k, C(1), m.dr, rho, ux, uy, uz);
+        add_neq<C, L::D, O3>(k, om, ux, uy, uz, pn);
         return k;
     }
     if (chi > C(0)) {
@@ -219,18 +227,30 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
         const C ux = (m.jx + C(0.5) * chi * rr * C(p.u_ref[0])) * h * inv;
         const C uy = (m.jy + C(0.5) * chi * rr * C(p.u_ref[1])) * h * inv;
         const C uz = L::D == 3 ? (m.jz + C(0.5) * chi * rr * C(p.u_ref[2])) * h * inv : C(0);
+        if (BGK) {
+            // (1 - 1/tau - chi) f^eq(rho*, u*) + chi f^eq(ref); the caller adds (1 - 1/tau) g
+            add_eq<C, L::D, O3>(k, C(1) - om - chi, drs, rs, ux, uy, uz);
+            add_eq<C, L::D, O3>(k, chi, C(p.rho_ref_m1), rr, C(p.u_ref[0]), C(p.u_ref[1]),
+                                L::D == 3 ? C(p.u_ref[2]) : C(0));
+            return k;
+        }
         const Sym2<C> pn = pi_neq<C>(m, drs, rs, ux, uy, uz, L::D);
-        add_eq<C, L::D>(k, C(1) - chi, drs, rs, ux, uy, uz);
-        add_eq<C, L::D>(k, chi, C(p.rho_ref_m1), rr, C(p.u_ref[0]), C(p.u_ref[1]), L::D == 3 ? C(p.u_ref[2]) : C(0));
-        add_neq<C, L::D>(k, om, ux, uy, uz, pn);
+        add_eq<C, L::D, O3>(k, C(1) - chi, drs, rs, ux, uy, uz);
+        add_eq<C, L::D, O3>(k, chi, C(p.rho_ref_m1), rr, C(p.u_ref[0]), C(p.u_ref[1]), L::D == 3 ? C(p.u_ref[2]) : C(0));
+        add_neq<C, L::D, O3>(k, om, ux, uy, uz, pn);
         return k;
     }
     const C rho = C(1) + m.dr;
     const C inv = recip(rho);
     const C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
+    if (BGK) {
+        // (1 - 1/tau) f^eq; the caller adds (1 - 1/tau) g
+        add_eq<C, L::D, O3>(k, C(1) - om, m.dr, rho, ux, uy, uz);
+        return k;
+    }
     const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
-    add_eq<C, L::D>(k, C(1), m.dr, rho, ux, uy, uz);
-    add_neq<C, L::D>(k, om, ux, uy, uz, pn);
+    add_eq<C, L::D, O3>(k, C(1), m.dr, rho, ux, uy, uz);
+    add_neq<C, L::D, O3>(k, om, ux, uy, uz, pn);
     return k;
 }
 
@@ -239,7 +259,7 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
 // role from coordinates, collision, store.  Shared by the single-lattice
 // kernel below and the batched multi-domain kernel.
 // ---------------------------------------------------------------------------
-template <class L, class S, class C>
+template <class L, class S, class C, bool BGK = false>
 __device__ __forceinline__ void update_cell(const StepParams &p, const char *const *in, char *const *out,
                                             int x, int y, int z)
 {
@@ -291,30 +311,41 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
 
     const Mom<C> m = moments_pairs<L, C>(g);
     const C chi = (bulk || inlet >= 0) ? C(0) : chi_cell<L, C>(p, chi_row<L, C>(p, y, z), x, y, z);
-    const Coef<C> k = cell_coefficients<L, C>(p, m, chi, x, y, z, inlet);
+    const Coef<C> k = cell_coefficients<L, C, BGK>(p, m, chi, x, y, z, inlet);
 
-    // ---- rebuild, relax and store (even/odd parts of each opposite pair)
+    // ---- rebuild, relax and store (even/odd parts of each opposite pair);
+    // plain BGK adds (1 - 1/tau) g of the streamed populations except at
+    // rebuilt boundary nodes
+    const C keep = (BGK && inlet < 0) ? C(p.omega) : C(0);
     const RebuildPre<C> r = rebuild_prep<L, C>(k);
-    Store<S>::st((S *)out[0] + cell, rebuild_rest<L, C>(k, r));
+    C g0 = rebuild_rest<L, C>(k, r);
+    if (BGK) g0 = fmac(keep, g[0], g0);
+    Store<S>::st((S *)out[0] + cell, g0);
 #pragma unroll
     for (int i = 1; i <= L::HALF; ++i) {
         C gp, gm;
         rebuild_pair<L, C>(k, r, i, gp, gm);
+        if (BGK) {
+            gp = fmac(keep, g[i], gp);
+            gm = fmac(keep, g[i + L::HALF], gm);
+        }
         Store<S>::st((S *)out[i] + cell, gp);
         Store<S>::st((S *)out[i + L::HALF] + cell, gm);
     }
 }
 
-// General kernel: one thread per cell, optional cell-type mask.
-template <class L, class S, class C>
+// General kernel: one thread per cell, optional cell-type mask; BGK = true
+// is the plain LBM-BGK collision (Eq. standardLB).
+template <class L, class S, class C, bool BGK>
 __global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ StepParams p)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.n[0]) return;
-    update_cell<L, S, C>(p, p.in, p.out, x, blockIdx.y, blockIdx.z);
+    update_cell<L, S, C, BGK>(p, p.in, p.out, x, blockIdx.y, blockIdx.z);
 }
 
-// Launch wrapper: one thread per cell, blocks along x.
+// Launch wrapper: one thread per cell, blocks along x; p.bgk selects the
+// collision model.
 template <class L, class S, class C>
 cudaError_t launch_stream_collide(const StepParams &p, const void *fin, void *fout, int block,
                                   cudaStream_t st)
@@ -323,7 +354,10 @@ cudaError_t launch_stream_collide(const StepParams &p, const void *fin, void *fo
     set_bases<L, S>(q, fin, fout);
     dim3 b(block, 1, 1);
     dim3 g((p.n[0] + block - 1) / block, p.n[1], p.n[2]);
-    k_stream_collide<L, S, C><<<g, b, 0, st>>>(q);
+    if (p.bgk)
+        k_stream_collide<L, S, C, true><<<g, b, 0, st>>>(q);
+    else
+        k_stream_collide<L, S, C, false><<<g, b, 0, st>>>(q);
     return cudaGetLastError();
 }
 

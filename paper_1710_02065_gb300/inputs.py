@@ -72,6 +72,20 @@ def taylor_green_2d(n: int, u0: float = 0.01):
     return rho, u
 
 
+def double_shear_layer(n: int, U: float = 0.1, kappa: float = 80.0, delta: float = 0.05):
+    """Periodic double shear layer on an n x n box (the classic stability test
+    of lattice Boltzmann collision models): u_x = U tanh(kappa (y/n - 1/4))
+    for y <= n/2 and U tanh(kappa (3/4 - y/n)) above, u_y = delta U
+    sin(2 pi (x/n + 1/4)), rho = 1."""
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    yy = y / n
+    ux = np.where(yy <= 0.5, U * np.tanh(kappa * (yy - 0.25)), U * np.tanh(kappa * (0.75 - yy)))
+    u = np.zeros((n * n, 3))
+    u[:, 0] = ux.reshape(-1)
+    u[:, 1] = (delta * U * np.sin(2 * math.pi * (x / n + 0.25))).reshape(-1)
+    return np.ones(n * n), u
+
+
 def taylor_green_3d(n: int, u0: float = 0.01):
     """u = U0 (sin kx cos ky cos kz, -cos kx sin ky cos kz, 0), k = 2 pi / n."""
     k = 2 * math.pi / n

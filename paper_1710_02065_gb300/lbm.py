@@ -67,6 +67,7 @@ _sig("lbm_sync", [_h])
 _sig("lbm_set_launch", [_h, C.c_int, C.c_int])
 _sig("lbm_get_launch", [_h, _ip, _ip])
 _sig("lbm_set_staging", [_h, C.c_int, C.c_int, C.c_int])
+_sig("lbm_set_collision", [_h, C.c_int])
 _sig("lbm_get_staging", [_h, _ip, _ip, _ip, _ip, _ip])
 _sig("lbm_info", [_h, _i64p, _i64p, _dp, _dp])
 _sig("lbm_add_refinement_patch", [_h, _ip, _ip])
@@ -99,7 +100,7 @@ EXPORTED = [
     "lbm_set_boundary", "lbm_set_pressure", "lbm_set_inlet_noise", "lbm_set_sponge", "lbm_set_radial_sponge", "lbm_set_state",
     "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_moments", "lbm_reduce",
     "lbm_probe", "lbm_sync", "lbm_info", "lbm_save", "lbm_load", "lbm_set_launch", "lbm_get_launch",
-    "lbm_set_staging", "lbm_get_staging",
+    "lbm_set_staging", "lbm_get_staging", "lbm_set_collision",
     "lbm_add_refinement_patch", "lbm_level_info", "lbm_force", "lbm_set_geometry_level", "lbm_set_state_level",
     "lbm_set_populations_level", "lbm_get_populations_level", "lbm_moments_level",
     "lbm_reduce_noalloc", "lbm_server_create", "lbm_server_destroy", "lbm_server_last_error",
@@ -242,6 +243,13 @@ def lbm_get_launch(h):
     b, v = C.c_int(), C.c_int()
     _check(_lib.lbm_get_launch(h, C.byref(b), C.byref(v)), h)
     return b.value, v.value
+
+
+LBM_COLLISION_RR, LBM_COLLISION_BGK = 0, 1
+
+
+def lbm_set_collision(h, model: int):
+    return _check(_lib.lbm_set_collision(h, int(model)), h)
 
 
 def lbm_set_staging(h, mode: int = -1, stages: int = 0, block: int = 0):

@@ -566,3 +566,43 @@ def test_staged_kernel_eligibility_and_fallback():
         s.step(2)
         assert np.abs(s.populations() - ref).max() <= _pop_tol(prec, ref, w, 2)
         s.close()
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
+def test_plain_bgk_matches_oracle(lattice, prec):
+    """Plain LBM-BGK (Eq. standardLB, quadratic equilibrium): every boundary
+    rule (inflow profile + noise, outflow, sponges, bounce-back solid) and the
+    free-slip / constant-pressure faces, against the oracle's BGK."""
+    from paper_1710_02065_gb300 import lbm
+    _, _, _, w, _ = oracle.lattice(lattice)
+    n = (40, 14, 1) if lattice == D2Q9 else (24, 12, 10)
+    for c in (_boxed_case(lattice, seed=6), _slip_box(lattice, n, seed=9)):
+        P, f = to_oracle(c)
+        P.collision = oracle.BGK
+        ref = P.run(f, 3)
+        s = to_gpu(c, PRECS[prec])
+        lbm.lbm_set_collision(s.h, lbm.LBM_COLLISION_BGK)
+        s.step(3)
+        err = np.abs(s.populations() - ref).max()
+        assert err <= _pop_tol(prec, ref, w, 3), (c.name, err)
+        # the two collision models differ on this state by far more than the
+        # FP64 / FP32 tolerances (and more than the 16-bit ones)
+        P.collision = oracle.RR
+        assert np.abs(P.run(f, 3) - ref).max() > 5 * _pop_tol(prec, ref, w, 3)
+        s.close()
+
+
+def test_collision_model_and_refinement_exclude_each_other():
+    from paper_1710_02065_gb300 import lbm
+    s = lbm.Solver(D2Q9, (40, 30, 1), 0.6, PRECS["fp32"])
+    lbm.lbm_set_collision(s.h, lbm.LBM_COLLISION_BGK)
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_add_refinement_patch(s.h, (10, 8, 0), (16, 12, 1))
+    lbm.lbm_set_collision(s.h, lbm.LBM_COLLISION_RR)
+    lbm.lbm_add_refinement_patch(s.h, (10, 8, 0), (16, 12, 1))
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_set_collision(s.h, lbm.LBM_COLLISION_BGK)
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_set_collision(s.h, 7)
+    s.close()

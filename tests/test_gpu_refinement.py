@@ -116,3 +116,97 @@ def test_two_level_full_size_few_steps():
     fluid_f = solid_f == 0
     assert _normwise(grc, rc) <= 1e-5 and _normwise(guc, uc) <= 1e-5
     assert _normwise(grf[fluid_f], rf[fluid_f]) <= 1e-5 and _normwise(guf[fluid_f], uf[fluid_f]) <= 1e-5
+
+
+def _case_3d():
+    """D3Q19 box 24x20x18: inflow on -x, outflow behind a sponge on +x, y/z
+    periodic; smooth density pulse and shear on a uniform stream; a fine
+    patch over coarse [6, 16] x [5, 13] x [5, 12] holding a small solid
+    sphere on the fine level."""
+    from cases import Case
+    n = (24, 20, 18)
+    c = Case("two_level_3d", oracle.D3Q19, n, 0.6)
+    U = 0.04
+    c.faces = {0: (VELOCITY, (U, 0, 0), None), 1: (oracle.OUTFLOW, (0, 0, 0), None)}
+    c.sponges = {1: (4, 0.3)}
+    c.rho_ref, c.u_ref = 1.0, (U, 0.0, 0.0)
+
+    def fields(X, Y, Z):
+        r2 = (X - 11.0) ** 2 + (Y - 9.0) ** 2 + (Z - 8.5) ** 2
+        rho = 1.0 + 2e-3 * np.exp(-r2 / 8.0)
+        u = np.zeros(X.shape + (3,))
+        u[..., 0] = U
+        u[..., 1] = 0.01 * np.sin(2 * np.pi * Z / n[2])
+        u[..., 2] = 0.008 * np.cos(2 * np.pi * Y / n[1])
+        return rho.reshape(-1), u.reshape(-1, 3)
+
+    z, y, x = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    c.rho0, c.u0 = fields(x.astype(float), y.astype(float), z.astype(float))
+    patch = (6, 5, 5, 10, 8, 7)
+    X0, Y0, Z0, Wc, Hc, Dc = patch
+    nf = (2 * Wc + 1, 2 * Hc + 1, 2 * Dc + 1)
+    k, j, i = np.meshgrid(np.arange(nf[2]), np.arange(nf[1]), np.arange(nf[0]), indexing="ij")
+    rho_f, u_f = fields(X0 + i / 2, Y0 + j / 2, Z0 + k / 2)
+    solid_f = (((i - 9) ** 2 + (j - 8) ** 2 + (k - 7) ** 2) <= 6).astype(np.uint8).reshape(-1)
+    return c, patch, rho_f, u_f, solid_f
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+def test_two_level_3d_parity(prec, tol):
+    """D3Q19 patch (fine shell from the coarse planes, covered coarse shell
+    from the fine level) against the oracle's TwoLevel3 on both levels."""
+    from cases import to_gpu
+    from paper_1710_02065_gb300 import lbm
+    c, patch, rho_f, u_f, solid_f = _case_3d()
+    P, _ = to_oracle(c)
+    T = oracle.TwoLevel3(P, *patch)
+    T.set_fine_solid(solid_f)
+    T.init(c.rho0, c.u0, rho_f, u_f)
+    s = to_gpu(c, prec)
+    X0, Y0, Z0, Wc, Hc, Dc = patch
+    lbm.lbm_add_refinement_patch(s.h, (X0, Y0, Z0), (Wc, Hc, Dc))
+    lbm.lbm_set_geometry_level(s.h, 1, solid_f)
+    lbm.lbm_set_state_level(s.h, 1, rho_f, u_f)
+    lbm.lbm_set_state(s.h, c.rho0, c.u0)
+    ext, tau_f = lbm.lbm_level_info(s.h, 1)
+    assert ext == tuple(T.Pf.n) and abs(tau_f - T.Pf.tau) < 1e-15
+    steps = 10
+    T.run(steps)
+    s.step(steps)
+    rc, uc, _ = T.Pc.moments(T.fc)
+    rf, uf, _ = T.Pf.moments(T.ff)
+    grc = np.zeros(T.Pc.ncell); guc = np.zeros((T.Pc.ncell, 3))
+    grf = np.zeros(T.Pf.ncell); guf = np.zeros((T.Pf.ncell, 3))
+    lbm.lbm_moments_level(s.h, 0, grc, guc, None)
+    lbm.lbm_moments_level(s.h, 1, grf, guf, None)
+    nxc, nyc, nzc = T.Pc.n
+    live = np.ones((nzc, nyc, nxc), bool)
+    live[Z0 + 2:Z0 + Dc - 1, Y0 + 2:Y0 + Hc - 1, X0 + 2:X0 + Wc - 1] = False  # frozen covered coarse cells
+    live = live.reshape(-1)
+    fluid_f = solid_f == 0
+    assert _normwise(grc[live], rc[live]) <= tol
+    assert _normwise(guc[live], uc[live]) <= tol
+    assert _normwise(grf[fluid_f], rf[fluid_f]) <= tol
+    assert _normwise(guf[fluid_f], uf[fluid_f]) <= tol
+    F = lbm.lbm_force(s.h, 1)
+    F_ref = T.Pf.wall_force(T.ff)
+    assert np.abs(F - F_ref).max() <= tol * np.abs(F_ref).max() * 10
+    s.close()
+
+
+def test_two_level_3d_uniform_stream_exact():
+    from paper_1710_02065_gb300 import lbm
+    s = lbm.Solver(oracle.D3Q19, (20, 18, 16), 0.6, 0)
+    lbm.lbm_add_refinement_patch(s.h, (5, 4, 4), (8, 8, 6))
+    U = (0.04, -0.02, 0.01)
+    ext, _ = lbm.lbm_level_info(s.h, 1)
+    nf = int(np.prod(ext))
+    lbm.lbm_set_state_level(s.h, 1, np.ones(nf), np.tile(U, (nf, 1)))
+    s.set_state(np.ones(s.ncell), np.tile(U, (s.ncell, 1)))
+    f0 = s.populations()
+    s.step(4)
+    assert np.abs(s.populations() - f0).max() < 1e-15
+    rf = np.zeros(nf); uf = np.zeros((nf, 3))
+    lbm.lbm_moments_level(s.h, 1, rf, uf, None)
+    assert np.abs(uf - np.array(U)).max() < 1e-15 and np.abs(rf - 1).max() < 1e-15
+    s.close()
