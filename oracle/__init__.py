@@ -67,6 +67,7 @@ class _Problem(C.Structure):
         ("solid", C.POINTER(C.c_uint8)),
         ("g", C.c_double * 3),
         ("collision", C.c_int),
+        ("jet_ref", C.c_double * 7),
     ]
 
 
@@ -114,6 +115,7 @@ def lib():
             _lib.orc_refined3_step.argtypes = [P, P, G3, dp, dp, dp, dp, dp, dp, C.c_int64]
             _lib.orc_refine3_interp.argtypes = [P, G3, dp, dp, C.c_double, C.c_int, C.c_int, C.c_int, dp]
             _lib.orc_refine3_filter.argtypes = [dp, dp]
+            _lib.orc_sponge_reference.argtypes = [P, C.c_int, C.c_int, C.c_int, dp]
         return _lib
 
 
@@ -201,6 +203,7 @@ class Problem:
         self.g = [0.0, 0.0, 0.0]
         self.radial = [0.0] * 6
         self.collision = RR  # RR: rrBGK (Eq. optimizedLB); BGK: plain BGK (Eq. standardLB)
+        self.jet_ref = [0.0] * 7  # yc, zc, U_J, D, x0, B, S of the +x sponge's jet reference; D = 0: none
 
     @property
     def ncell(self) -> int:
@@ -220,6 +223,17 @@ class Problem:
         self.rho_ref = float(rho_ref)
         self.u_ref = [float(v) for v in u_ref]
 
+    def set_jet_reference(self, yc: float, zc: float, U_jet: float, D: float, x0: float, B: float = 5.8,
+                          S: float = 0.094):
+        """Round-jet similarity reference for the cells of the +x sponge layer."""
+        self.jet_ref = [float(yc), float(zc), float(U_jet), float(D), float(x0), float(B), float(S)]
+
+    def sponge_reference(self, x: int, y: int, z: int) -> np.ndarray:
+        u = np.zeros(3)
+        s = self._struct()
+        lib().orc_sponge_reference(C.byref(s), int(x), int(y), int(z), _dp(u))
+        return u
+
     def set_sponge(self, face: int, width: int, chi_max: float, rho_ref=1.0, u_ref=(0.0, 0.0, 0.0)):
         self.sponge_width[face] = int(width)
         self.sponge_chi[face] = float(chi_max)
@@ -235,6 +249,8 @@ class Problem:
             s.g[a] = self.g[a]
         s.tau = self.tau
         s.collision = self.collision
+        for k in range(7):
+            s.jet_ref[k] = self.jet_ref[k]
         for f in range(6):
             s.face_kind[f] = self.face_kind[f]
             s.rho_face[f] = self.rho_face[f]

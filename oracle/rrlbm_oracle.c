@@ -60,6 +60,10 @@
  *       chi_max sigma(r - r0) for r - r0 < 0.8 W, chi_max beyond.
  *   R15 Forces on walls (lift, drag; not printed as a formula in the paper):
  *       momentum exchange over the bounce-back links.
+ *   R21 Jet outflow sponge reference (Sec. IV: the jet similarity solution of
+ *       Pope 2000 as reference field of the outflow region): inside the +x
+ *       layer the reference velocity is the self-similar round-jet mean
+ *       axial profile (sponge_reference below); elsewhere the uniform u_ref.
  */
 #include <math.h>
 #include <stdint.h>
@@ -391,6 +395,8 @@ typedef struct {
     const uint8_t *solid;    /* optional per cell: 1 = solid wall, 2 = fixed */
     double g[3];             /* oracle-only body force */
     int collision;           /* 0 = rrBGK (Eq. optimizedLB), 1 = BGK (Eq. standardLB) */
+    double jet_ref[7];       /* round-jet similarity reference of the +x sponge (reading R21):
+                                yc, zc, U_J, D, x0, B, S; D = 0: none */
 } orc_problem;
 
 static int64_t ncell(const orc_problem *P) { return (int64_t)P->n[0] * P->n[1] * P->n[2]; }
@@ -438,6 +444,33 @@ static double sponge_chi(const orc_problem *P, const int c[3])
         if (s > chi) chi = s;
     }
     return chi;
+}
+
+/* Sponge reference velocity of a cell (reading R21): the uniform u_ref, or,
+ * inside the +x layer when a jet reference is set, the mean axial velocity of
+ * the self-similar round jet (Sec. IV cites Pope 2000 for it): centreline
+ * U_0 = min(U_J, B D U_J / (x - x0)), profile f(eta) = (1 + a eta^2)^-2 with
+ * eta = r / (x - x0) and a = (sqrt 2 - 1) / S^2, so that u = U_0 / 2 at the
+ * half-width r = S (x - x0); radial velocity not imposed. */
+static void sponge_reference(const orc_problem *P, const int c[3], double u[3])
+{
+    for (int a = 0; a < 3; ++a) u[a] = P->u_ref[a];
+    const double *J = P->jet_ref;
+    if (!(J[3] > 0.0) || P->sponge_width[1] <= 0 || c[0] < P->n[0] - P->sponge_width[1]) return;
+    const double xi = c[0] - J[4];
+    const double Uc = xi > 0.0 && J[5] * J[3] / xi < 1.0 ? J[5] * J[3] * J[2] / xi : J[2];
+    const double r = sqrt((c[1] - J[0]) * (c[1] - J[0]) + (c[2] - J[1]) * (c[2] - J[1]));
+    const double eta = xi > 0.0 ? r / xi : 0.0;
+    const double a = (sqrt(2.0) - 1.0) / (J[6] * J[6]);
+    const double q = 1.0 + a * eta * eta;
+    u[0] = Uc / (q * q);
+    u[1] = u[2] = 0.0;
+}
+
+void orc_sponge_reference(const orc_problem *P, int x, int y, int z, double u[3])
+{
+    const int c[3] = {x, y, z};
+    sponge_reference(P, c, u);
 }
 
 /* Post-collision populations of one cell at step `step` (the step that turns
@@ -530,10 +563,12 @@ void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int6
         return;
     }
 
+    double uref[3];
+    sponge_reference(P, c, uref);
     if (P->collision == 1)
-        collide_bgk(L, f, P->tau, sponge_chi(P, c), P->rho_ref, P->u_ref, P->g, out);
+        collide_bgk(L, f, P->tau, sponge_chi(P, c), P->rho_ref, uref, P->g, out);
     else
-        collide(L, f, P->tau, sponge_chi(P, c), P->rho_ref, P->u_ref, P->g, out);
+        collide(L, f, P->tau, sponge_chi(P, c), P->rho_ref, uref, P->g, out);
 }
 
 /* Post-collision populations of a list of cells (out: n x q, cell-major). */
