@@ -116,6 +116,12 @@ def lib():
             _lib.orc_refine3_interp.argtypes = [P, G3, dp, dp, C.c_double, C.c_int, C.c_int, C.c_int, dp]
             _lib.orc_refine3_filter.argtypes = [dp, dp]
             _lib.orc_sponge_reference.argtypes = [P, C.c_int, C.c_int, C.c_int, dp]
+            _lib.orc_refine2_line_moments.argtypes = [P, G, dp, dp]
+            _lib.orc_refine2_fill.argtypes = [P, P, G, dp, dp, C.c_double, dp]
+            _lib.orc_refine2_restrict.argtypes = [P, P, G, dp, dp]
+            _lib.orc_refine3_plane_moments.argtypes = [P, G3, dp, dp]
+            _lib.orc_refine3_fill.argtypes = [P, P, G3, dp, dp, C.c_double, dp]
+            _lib.orc_refine3_restrict.argtypes = [P, P, G3, dp, dp]
         return _lib
 
 
@@ -453,3 +459,104 @@ class TwoLevel3:
         mc = np.zeros(10)
         lib().orc_refine3_filter(_dp(np.ascontiguousarray(m27, dtype=np.float64).reshape(-1)), _dp(mc))
         return mc
+
+
+class MultiLevel:
+    """Nested 2:1 patches (Sec. II.B applied recursively, as the paper's
+    cylinder (4 levels) and jet (5 levels) use it): level 0 is the coarse
+    Problem; level k + 1 covers the level-k nodes origin..origin + extent
+    (per axis of the lattice), with tau_{k+1} = 2 tau_k - 1/2.  Every level
+    above 0 is a periodic box with its boundary ring / shell fixed and rebuilt
+    from its parent; every level with a child has the child's covered
+    interior fixed and its first ring / shell rebuilt from the child.
+
+    One step of level k: parent-side interface moments at t + 1 (when k has
+    a child), the level's own update, then two steps of the child with its
+    ring refilled at t + 1/2 and t + 1 from the interface moments, and the
+    covered ring of level k restricted from the child at t + 1/2 -- the order
+    of orc_refined_step, applied at every level.
+    """
+
+    def __init__(self, coarse: Problem, patches):
+        self.three = coarse.lattice == D3Q19
+        self.P = [coarse]
+        self.G = []
+        for origin, extent in patches:
+            parent = self.P[-1]
+            d = 3 if self.three else 2
+            o, e = [int(v) for v in origin[:d]], [int(v) for v in extent[:d]]
+            for a in range(d):
+                assert o[a] >= 2 and e[a] >= 4 and o[a] + e[a] <= parent.n[a] - 3
+            nf = tuple(2 * v + 1 for v in e)
+            fine = Problem(coarse.lattice, nf, 2 * parent.tau - 0.5)
+            shape = tuple(reversed(nf))
+            fm = np.zeros(shape, np.uint8)
+            if self.three:
+                fm[0], fm[-1] = FIXED, FIXED
+                fm[:, 0], fm[:, -1] = FIXED, FIXED
+                fm[:, :, 0], fm[:, :, -1] = FIXED, FIXED
+            else:
+                fm[0], fm[-1] = FIXED, FIXED
+                fm[:, 0], fm[:, -1] = FIXED, FIXED
+            fine.solid = fm.reshape(-1)
+            pshape = tuple(reversed(parent.n[:d]))
+            pm = np.zeros(pshape, np.uint8) if parent.solid is None else parent.solid.reshape(pshape).copy()
+            if self.three:
+                pm[o[2] + 1:o[2] + e[2], o[1] + 1:o[1] + e[1], o[0] + 1:o[0] + e[0]] = FIXED
+                self.G.append(_Patch3(o[0], o[1], o[2], e[0], e[1], e[2]))
+            else:
+                pm[o[1] + 1:o[1] + e[1], o[0] + 1:o[0] + e[0]] = FIXED
+                self.G.append(_Patch(o[0], o[1], e[0], e[1]))
+            parent.solid = pm.reshape(-1)
+            self.P.append(fine)
+
+    @property
+    def levels(self) -> int:
+        return len(self.P)
+
+    def set_solid(self, level: int, solid: np.ndarray):
+        m = self.P[level].solid.copy()
+        s = np.asarray(solid, np.uint8).reshape(-1)
+        m[(s == SOLID) & (m != FIXED)] = SOLID
+        self.P[level].solid = m
+
+    def init(self, states):
+        """states: one (rho, u) per level."""
+        self.f = [P.equilibrium(r, u) for P, (r, u) in zip(self.P, states)]
+        nm = 10 if self.three else 6
+        self.M0 = [np.zeros(nm * self.P[k].ncell) for k in range(len(self.G))]
+        self.M1 = [np.zeros(nm * self.P[k].ncell) for k in range(len(self.G))]
+        for k, g in enumerate(self.G):
+            sc = self.P[k]._struct()
+            init = lib().orc_refined3_init_moments if self.three else lib().orc_refined_init_moments
+            init(C.byref(sc), C.byref(g), _dp(self.f[k]), _dp(self.M0[k]))
+        self.step_index = 0
+
+    def _advance(self, k: int, step: int):
+        L = lib()
+        P = self.P[k]
+        child = k < len(self.G)
+        if child:
+            g, sc = self.G[k], P._struct()
+            (L.orc_refine3_plane_moments if self.three else L.orc_refine2_line_moments)(
+                C.byref(sc), C.byref(g), _dp(self.f[k]), _dp(self.M1[k]))
+        new = np.empty_like(self.f[k])
+        s = P._struct()
+        L.orc_step(C.byref(s), _dp(self.f[k]), _dp(new), int(step))
+        if child:
+            sf = self.P[k + 1]._struct()
+            fill = L.orc_refine3_fill if self.three else L.orc_refine2_fill
+            restrict = L.orc_refine3_restrict if self.three else L.orc_refine2_restrict
+            self._advance(k + 1, 2 * step)
+            fill(C.byref(sc), C.byref(sf), C.byref(g), _dp(self.M0[k]), _dp(self.M1[k]), 0.5, _dp(self.f[k + 1]))
+            half = self.f[k + 1].copy()
+            self._advance(k + 1, 2 * step + 1)
+            fill(C.byref(sc), C.byref(sf), C.byref(g), _dp(self.M0[k]), _dp(self.M1[k]), 1.0, _dp(self.f[k + 1]))
+            restrict(C.byref(sc), C.byref(sf), C.byref(g), _dp(half), _dp(new))
+            self.M0[k][:] = self.M1[k]
+        self.f[k] = new
+
+    def run(self, nsteps: int):
+        for _ in range(int(nsteps)):
+            self._advance(0, self.step_index)
+            self.step_index += 1

@@ -909,6 +909,26 @@ void orc_refined_init_moments(const orc_problem *Pc, const orc_patch *G, const d
  *   5. fine ring <- coarse moments at t + 1
  *   6. first covered coarse ring <- fine moments at t + 1
  * M0 holds the line moments at t on entry and at t + 1 on return. */
+/* The three coupling operations of one parent / child pair, exported so that
+ * a chain of nested patches can be stepped level by level (each level does
+ * two steps per step of its parent, in the order of orc_refined_step). */
+void orc_refine2_line_moments(const orc_problem *Pc, const orc_patch *G, const double *fc, double *M)
+{
+    coarse_line_moments(Pc, G, fc, M);
+}
+
+void orc_refine2_fill(const orc_problem *Pc, const orc_problem *Pf, const orc_patch *G, const double *M0,
+                      const double *M1, double a, double *ff)
+{
+    fill_fine_ring(Pc, Pf, G, M0, M1, a, ff);
+}
+
+void orc_refine2_restrict(const orc_problem *Pc, const orc_problem *Pf, const orc_patch *G, const double *ff_half,
+                          double *fc)
+{
+    restrict_to_coarse(Pc, Pf, G, ff_half, fc);
+}
+
 int orc_refined_step(const orc_problem *Pc, const orc_problem *Pf, const orc_patch *G,
                      double *fc, double *fc_work, double *ff, double *ff_work, double *M0,
                      double *M1, int64_t step)
@@ -1133,6 +1153,23 @@ void orc_refined3_init_moments(const orc_problem *Pc, const orc_patch3 *G, const
                 m[4] = Pn[0][0]; m[5] = Pn[0][1]; m[6] = Pn[0][2];
                 m[7] = Pn[1][1]; m[8] = Pn[1][2]; m[9] = Pn[2][2];
             }
+}
+
+void orc_refine3_plane_moments(const orc_problem *Pc, const orc_patch3 *G, const double *fc, double *M)
+{
+    coarse_plane_moments3(Pc, G, fc, M);
+}
+
+void orc_refine3_fill(const orc_problem *Pc, const orc_problem *Pf, const orc_patch3 *G, const double *M0,
+                      const double *M1, double a, double *ff)
+{
+    fill_fine_shell3(Pc, Pf, G, M0, M1, a, ff);
+}
+
+void orc_refine3_restrict(const orc_problem *Pc, const orc_problem *Pf, const orc_patch3 *G, const double *ff_half,
+                          double *fc)
+{
+    restrict_to_coarse3(Pc, Pf, G, ff_half, fc);
 }
 
 /* One coarse step of the 3D two-level grid, in the order of the 2D one. */

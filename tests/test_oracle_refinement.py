@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle import D2Q9, VELOCITY, Problem, TwoLevel
+from oracle import D2Q9, FIXED, VELOCITY, Problem, TwoLevel
 
 
 def test_printed_level_scales_follow_convective_scaling(repo_root):
@@ -223,3 +223,94 @@ def test_3d_restriction_filter_is_full_weighting():
                 m27b[c, b, a] = lin[:, 0] + lin[:, 1] * (a - 1) + lin[:, 2] * (b - 1) + lin[:, 3] * (c - 1) \
                     + 0.3 * (-1) ** (a + b + c)
     assert np.abs(TwoLevel3.filter(m27b)[4:] - lin[4:, 0]).max() < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# More than two levels: nested patches stepped recursively
+# ---------------------------------------------------------------------------
+from oracle import MultiLevel  # noqa: E402
+
+
+def _smooth_state(P, origin=(0.0, 0.0, 0.0), scale=1.0):
+    """rho, u of a smooth field at the nodes of P placed at coarse coordinates
+    origin + index * scale."""
+    d = 3 if P.lattice == D3Q19 else 2
+    n = P.n
+    idx = np.stack(np.meshgrid(*[np.arange(v) for v in reversed(n[:d])], indexing="ij"), -1).reshape(-1, d)[:, ::-1]
+    X = origin[0] + idx[:, 0] * scale
+    Y = origin[1] + idx[:, 1] * scale
+    rho = 1.0 + 1e-3 * np.sin(0.3 * X) * np.cos(0.2 * Y)
+    u = np.zeros((P.ncell, 3))
+    u[:, 0] = 0.03 + 0.01 * np.cos(0.25 * Y)
+    u[:, 1] = 0.01 * np.sin(0.21 * X)
+    if d == 3:
+        Z = origin[2] + idx[:, 2] * scale
+        rho *= 1.0 + 5e-4 * np.cos(0.3 * Z)
+        u[:, 2] = 0.005 * np.sin(0.17 * Y + 0.1 * Z)
+    return rho, u
+
+
+def test_one_nested_patch_is_the_two_level_step():
+    """The recursive stepping with a single patch reproduces the two-level
+    step bit for bit, in 2D and 3D."""
+    for lat, n, patch in ((D2Q9, (30, 26), ((6, 5), (12, 10))), (D3Q19, (18, 16, 14), ((4, 4, 3), (8, 6, 6)))):
+        P1, P2 = Problem(lat, n, 0.62), Problem(lat, n, 0.62)
+        (o, e) = patch
+        T = TwoLevel3(P1, *o, *e) if lat == D3Q19 else TwoLevel(P1, *o, *e)
+        M = MultiLevel(P2, [patch])
+        sc = _smooth_state(P1)
+        sf = _smooth_state(T.Pf, origin=o + (0,) * (3 - len(o)), scale=0.5)
+        T.init(*sc, *sf)
+        M.init([sc, sf])
+        T.run(5)
+        M.run(5)
+        assert np.array_equal(T.fc, M.f[0]) and np.array_equal(T.ff, M.f[1])
+
+
+def test_three_levels_keep_viscosity_and_a_uniform_stream():
+    P = Problem(D2Q9, (40, 34), 0.56)
+    M = MultiLevel(P, [((8, 7), (22, 18)), ((9, 8), (20, 16))])
+    assert M.levels == 3
+    for k in range(1, 3):
+        tau_p, tau = M.P[k - 1].tau, M.P[k].tau
+        # nu dt / dx^2 scales with dt/dx^2 = 2: (tau - 1/2) doubles per level
+        assert abs((tau - 0.5) - 2 * (tau_p - 0.5)) < 1e-15
+    U = (0.04, -0.015, 0.0)
+    M.init([(np.ones(p.ncell), np.tile(U, (p.ncell, 1))) for p in M.P])
+    f0 = [f.copy() for f in M.f]
+    M.run(3)
+    for a, b in zip(M.f, f0):
+        assert np.abs(a - b).max() < 1e-15
+
+
+def test_three_level_couette_flow_stays_linear():
+    """Steady Couette flow through two nested 2D patches stays linear (the
+    rescaling of f^neq is exact for the Navier-Stokes stress on every pair of
+    levels)."""
+    nx, ny, U = 32, 30, 0.04
+    P = Problem(D2Q9, (nx, ny), 0.7)
+    P.set_boundary(2, VELOCITY, (0, 0, 0))
+    P.set_boundary(3, VELOCITY, (U, 0, 0))
+    patches = [((6, 7), (18, 14)), ((8, 7), (18, 14))]
+    M = MultiLevel(P, patches)
+    states, origin, scale = [], np.zeros(2), 1.0
+    for k, p in enumerate(M.P):
+        y = origin[1] + (np.arange(p.ncell) // p.n[0]) * scale
+        u = np.zeros((p.ncell, 3))
+        u[:, 0] = U * y / (ny - 1)
+        states.append((np.ones(p.ncell), u))
+        if k < len(patches):
+            origin = origin + np.array(patches[k][0]) * scale
+            scale /= 2
+    M.init(states)
+    M.run(3000)
+    origin, scale = np.zeros(2), 1.0
+    for k, p in enumerate(M.P):
+        _, uu, _ = p.moments(M.f[k])
+        y = origin[1] + (np.arange(p.ncell) // p.n[0]) * scale
+        live = p.solid != FIXED if p.solid is not None else np.ones(p.ncell, bool)
+        err = np.abs(uu[:, 0] - U * y / (ny - 1))[live].max()
+        assert err < 1e-7, (k, err)
+        if k < len(patches):
+            origin = origin + np.array(patches[k][0]) * scale
+            scale /= 2
