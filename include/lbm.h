@@ -273,6 +273,40 @@ int lbm_set_launch(lbm_handle h, int block, int cells_per_thread);
 int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread);
 
 /*
+ * lbm_pressure_mean / lbm_pressure_fluctuation -- the fluctuating pressure
+ * Delta p~ = Delta p - Delta p_mean of Sec. III (Inoue and Hatakeyama), with
+ * Delta p = c_s^2 (rho - 1) and Delta p_mean its temporal mean, for every cell
+ * of the single level / coarse level.
+ *   lbm_pressure_mean(h, LBM_MEAN_RESET)       forget the samples
+ *   lbm_pressure_mean(h, LBM_MEAN_ACCUMULATE)  add rho of the stored field to
+ *       a device FP64 running sum (allocated on first use: 8 bytes per cell,
+ *       freed with the handle); the caller chooses the sampling steps
+ *   lbm_pressure_fluctuation(h, dp_tilde, dp_mean): host arrays of ncell
+ *       doubles (either may be NULL): c_s^2 (rho - mean rho) of the stored
+ *       field and c_s^2 (mean rho - 1).  LBM_EINVAL before any sample.
+ */
+#define LBM_MEAN_RESET 0
+#define LBM_MEAN_ACCUMULATE 1
+int lbm_pressure_mean(lbm_handle h, int op);
+int lbm_pressure_fluctuation(lbm_handle h, double *dp_tilde, double *dp_mean);
+
+/*
+ * lbm_set_sponge_jet_reference -- reference field of the outflow sponge for a
+ * round jet along +x (Sec. IV: the jet similarity solution of Pope 2000 as
+ * the sponge's reference in the outflow region; D3Q19).  In the cells of the
+ * +x face's sponge layer (lbm_set_sponge on face 1; x >= nx - width) the
+ * reference velocity becomes the self-similar mean axial profile
+ *   u_x = U_0(x) / (1 + a eta^2)^2,  U_0 = min(U_jet, B D U_jet / (x - x0)),
+ *   eta = r / (x - x0),  r = |(y, z) - (yc, zc)|,  a = (sqrt 2 - 1) / S^2
+ * (u_x = U_0 / 2 at the half-width r = S (x - x0)), u_y = u_z = 0; other
+ * sponge cells keep the uniform u_ref.  Lattice units; B 5.8 and S 0.094
+ * are the usual round-jet constants.  D = 0 removes it.  LBM_EINVAL for
+ * D2Q9, D, B or S <= 0, U_jet < 0, or non-finite values.
+ */
+int lbm_set_sponge_jet_reference(lbm_handle h, double yc, double zc, double U_jet, double D, double x0,
+                                 double B, double S);
+
+/*
  * lbm_set_collision -- collision model of the single-level update (Sec. II.A).
  *   LBM_COLLISION_RR  (default) recursive Hermite-regularized rrBGK, order 3
  *                     (Eq. optimizedLB with Eq. eqH, Eq. neqH, Eq. recursive2).

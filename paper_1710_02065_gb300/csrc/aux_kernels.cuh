@@ -7,6 +7,8 @@
 //   k_reduce      : FP64 per-block totals of rho - 1, rho u, fluid count and
 //                   non-finite count (warp shuffles, then a fixed-order pass)
 //   k_probe       : rho at listed cells
+//   k_rho_accumulate : running FP64 sum of rho per cell (temporal mean of p)
+//   k_pressure_fluct : Delta p~ = c_s^2 (rho - mean rho) per cell
 #pragma once
 
 #include "rr.cuh"
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(int64_t N, const S *__rest
     double acc[RED_FIELDS] = {0, 0, 0, 0, 0, 0};
     for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < N;
          cell += (int64_t)gridDim.x * blockDim.x) {
-        if (solid && solid[cell]) continue;  // fluid cells only
+        if (solid && (solid[cell] & MASK_TYPE)) continue;  // fluid cells only
         double g[L::Q];
         load_cell_fp64<L, S>(f, N, cell, g);
         bool finite = true;
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_force(int nx, int ny, int nz, int
     double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < N;
          cell += (int64_t)gridDim.x * blockDim.x) {
-        if (mask[cell]) continue;
+        if ((mask[cell] & MASK_TYPE) || !(mask[cell] & MASK_NEAR_SOLID)) continue;
         const int x = (int)(cell % nx), y = (int)((cell / nx) % ny), z = (int)(cell / ((int64_t)nx * ny));
 #pragma unroll
         for (int i = 1; i < L::Q; ++i) {
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_force(int nx, int ny, int nz, int
             if (py) Y = Y < 0 ? Y + ny : (Y >= ny ? Y - ny : Y);
             if (pz) Z = Z < 0 ? Z + nz : (Z >= nz ? Z - nz : Z);
             if (X < 0 || X >= nx || Y < 0 || Y >= ny || Z < 0 || Z >= nz) continue;
-            if (mask[X + (int64_t)nx * (Y + (int64_t)ny * Z)] != 1) continue;
+            if ((mask[X + (int64_t)nx * (Y + (int64_t)ny * Z)] & MASK_TYPE) != MASK_SOLID) continue;
             const double fi = (double)Store<S>::ld(f + (int64_t)i * N + cell) + weight<L>(i);
             acc[0] += 2.0 * L::cx(i) * fi;
             acc[1] += 2.0 * L::cy(i) * fi;
@@ -211,6 +213,35 @@ __global__ void k_probe(int n, const int64_t *__restrict__ cells, int64_t N, con
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) dr += g[i];
     rho[t] = 1.0 + dr;
+}
+
+// Running sum of rho per cell of the stored field (FP64), for the temporal
+// mean of the pressure (Sec. III: Delta p~ = Delta p - Delta p_mean)
+template <class L, class S>
+__global__ void k_rho_accumulate(int64_t N, const S *__restrict__ f, double *__restrict__ acc)
+{
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= N) return;
+    double dr = 0.0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) dr += (double)Store<S>::ld(f + (int64_t)i * N + cell);
+    acc[cell] += 1.0 + dr;
+}
+
+// Delta p~ = c_s^2 (rho - acc / count) of the stored field, and optionally the
+// mean Delta p = c_s^2 (acc / count - 1) (ambient rho = 1)
+template <class L, class S>
+__global__ void k_pressure_fluct(int64_t N, const S *__restrict__ f, const double *__restrict__ acc, double count,
+                                 double *__restrict__ dp, double *__restrict__ dp_mean)
+{
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (cell >= N) return;
+    double dr = 0.0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) dr += (double)Store<S>::ld(f + (int64_t)i * N + cell);
+    const double mean = acc[cell] / count;
+    dp[cell] = (1.0 + dr - mean) * (1.0 / 3.0);
+    if (dp_mean) dp_mean[cell] = (mean - 1.0) * (1.0 / 3.0);
 }
 
 }  // namespace rr

@@ -1,6 +1,7 @@
 // lbm_api.cu -- host runtime behind include/lbm.h: handle, validation,
 // device memory, launches.  Every numerical step runs in the kernels of
 // step.cuh / aux_kernels.cuh; this file only moves arguments.
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -59,6 +60,9 @@ struct lbm_ctx {
     int rows_block = 0;   // its threads per CTA (0: automatic)
     unsigned *err_d = nullptr;  // device error word of the row-staged kernel (bounded waits)
     int collision = LBM_COLLISION_RR;
+    double jet_ref[7] = {0, 0, 0, 0, 0, 0, 0};  // yc, zc, U_J, D, x0, B, S; D = 0: none
+    double *rho_acc = nullptr;  // running sum of rho per cell (temporal mean of p), or null
+    int64_t rho_count = 0;
     double *red_d = nullptr;  // reduction partials + result
     int red_blocks = 0;
     std::vector<uint8_t> user_mask;  // caller's cell types (host copy); empty: none
@@ -216,6 +220,24 @@ struct Probe {
     }
 };
 
+template <class L, class S>
+struct RhoAccumulate {
+    static cudaError_t run(cudaStream_t st, int64_t N, const void *f, double *acc)
+    {
+        k_rho_accumulate<L, S><<<grid1(N, 256), 256, 0, st>>>(N, (const S *)f, acc);
+        return cudaGetLastError();
+    }
+};
+template <class L, class S>
+struct PressureFluct {
+    static cudaError_t run(cudaStream_t st, int64_t N, const void *f, const double *acc, double count, double *dp,
+                           double *dp_mean)
+    {
+        k_pressure_fluct<L, S><<<grid1(N, 256), 256, 0, st>>>(N, (const S *)f, acc, count, dp, dp_mean);
+        return cudaGetLastError();
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Lattice table (host)
 // ---------------------------------------------------------------------------
@@ -269,6 +291,7 @@ static void release(lbm_ctx *h)
         if (h->prof_d[k]) cudaFree(h->prof_d[k]);
     if (h->red_d) cudaFree(h->red_d);
     if (h->err_d) cudaFree(h->err_d);
+    if (h->rho_acc) cudaFree(h->rho_acc);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->fine) {
         for (int k = 0; k < 2; ++k) {
@@ -366,6 +389,36 @@ extern "C" const char *lbm_last_error(lbm_handle h)
 // ---------------------------------------------------------------------------
 // Configuration
 // ---------------------------------------------------------------------------
+// Device cell-type byte: bits 0-1 the type (fluid 0, solid 1, fixed 2); bit 2
+// (MASK_NEAR_SOLID) set when some lattice neighbour x - xi_i (with wrap-around
+// on every axis, as the kernels pull) is solid, so that cells away from walls
+// skip the per-direction bounce-back tests.
+template <class L>
+static void add_near_solid_bits(std::vector<uint8_t> &m, const int n[3])
+{
+    // a cell c has the solid neighbour s = c - xi_i exactly when c = s + xi_i:
+    // mark the neighbours of every solid cell
+    const int64_t nx = n[0], ny = n[1], nz = n[2];
+    std::vector<int64_t> solids;
+    for (size_t c = 0; c < m.size(); ++c)
+        if ((m[c] & 3) == LBM_CELL_SOLID) solids.push_back((int64_t)c);
+    for (const int64_t c : solids) {
+        const int64_t x = c % nx, y = (c / nx) % ny, z = c / (nx * ny);
+        for (int i = 1; i < L::Q; ++i) {
+            const int64_t X = (x + L::cx(i) + nx) % nx, Y = (y + L::cy(i) + ny) % ny, Z = (z + L::cz(i) + nz) % nz;
+            m[X + nx * (Y + ny * Z)] |= MASK_NEAR_SOLID;
+        }
+    }
+}
+
+static void add_near_solid(lbm_ctx *h, std::vector<uint8_t> &m, const int n[3])
+{
+    if (h->lattice == LBM_D2Q9)
+        add_near_solid_bits<D2Q9>(m, n);
+    else
+        add_near_solid_bits<D3Q19>(m, n);
+}
+
 // Upload the coarse mask: the caller's cell types, plus the covered patch
 // interior as fixed cells when a fine level exists.
 static int upload_coarse_mask(lbm_ctx *h)
@@ -387,6 +440,7 @@ static int upload_coarse_mask(lbm_ctx *h)
                 for (int x = g.X0 + 1; x < g.X0 + g.Wc; ++x)
                     m[(size_t)x + (size_t)h->n[0] * ((size_t)y + (size_t)h->n[1] * z)] = LBM_CELL_FIXED;
     }
+    add_near_solid(h, m, h->n);
     if (!h->solid_d) CUDA_TRY(h, cudaMalloc(&h->solid_d, (size_t)h->ncell));
     CUDA_TRY(h, cudaMemcpyAsync(h->solid_d, m.data(), (size_t)h->ncell, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -406,6 +460,7 @@ static int upload_fine_mask(lbm_ctx *h)
                 if (i == 0 || j == 0 || i == F->n[0] - 1 || j == F->n[1] - 1 ||
                     (three && (k == 0 || k == F->n[2] - 1)))
                     m[(size_t)i + (size_t)F->n[0] * ((size_t)j + (size_t)F->n[1] * k)] = LBM_CELL_FIXED;
+    add_near_solid(h, m, F->n);
     if (!F->mask_d) CUDA_TRY(h, cudaMalloc(&F->mask_d, (size_t)F->ncell));
     CUDA_TRY(h, cudaMemcpyAsync(F->mask_d, m.data(), (size_t)F->ncell, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -693,6 +748,16 @@ static int build_params(lbm_ctx *h, StepParams &p)
     p.omega = 1.0 - 1.0 / h->tau;
     p.solid = h->solid_d;
     p.bgk = h->collision == LBM_COLLISION_BGK ? 1 : 0;
+    p.jet_x_layer = INT_MAX;
+    if (h->jet_ref[3] > 0.0 && h->sponge_w[1] > 0 && h->sponge_chi[1] > 0.0) {
+        p.jet_x_layer = h->n[0] - h->sponge_w[1];
+        p.jet_ref[0] = h->jet_ref[0];
+        p.jet_ref[1] = h->jet_ref[1];
+        p.jet_ref[2] = h->jet_ref[2];
+        p.jet_ref[3] = h->jet_ref[5] * h->jet_ref[3];  // B D
+        p.jet_ref[4] = h->jet_ref[4];
+        p.jet_ref[5] = (std::sqrt(2.0) - 1.0) / (h->jet_ref[6] * h->jet_ref[6]);
+    }
     set_bulk_box(p);
     return LBM_OK;
 }
@@ -751,6 +816,7 @@ static void fine_params(lbm_ctx *h, StepParams &p)
     for (int f = 0; f < 6; ++f) p.face_cells[f] = 1;
     p.rho_ref = 1.0;
     p.omega = 1.0 - 1.0 / F->tau;
+    p.jet_x_layer = INT_MAX;
     p.solid = F->mask_d;
     set_bulk_box(p);
 }
@@ -1145,6 +1211,74 @@ extern "C" int lbm_set_collision(lbm_handle h, int model)
     if (model == LBM_COLLISION_BGK && h->fine)
         return fail(h, LBM_EINVAL, "plain BGK is not available with a refinement patch");
     h->collision = model;
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_sponge_jet_reference(lbm_handle h, double yc, double zc, double U_jet, double D, double x0,
+                                            double B, double S)
+{
+    CHECK_HANDLE(h);
+    h->cfg_version++;
+    if (h->lattice != LBM_D3Q19) return fail(h, LBM_EINVAL, "the round-jet reference needs D3Q19");
+    if (D == 0.0) {
+        for (double &v : h->jet_ref) v = 0.0;
+        return LBM_OK;
+    }
+    if (!(D > 0.0) || !(U_jet >= 0.0) || !(B > 0.0) || !(S > 0.0) || !std::isfinite(x0) || !std::isfinite(yc) ||
+        !std::isfinite(zc) || !std::isfinite(U_jet * B * D / S))
+        return fail(h, LBM_EINVAL, "jet reference needs D > 0, U_jet >= 0, B > 0, S > 0, finite values");
+    const double v[7] = {yc, zc, U_jet, D, x0, B, S};
+    for (int k = 0; k < 7; ++k) h->jet_ref[k] = v[k];
+    return LBM_OK;
+}
+
+extern "C" int lbm_pressure_mean(lbm_handle h, int op)
+{
+    CHECK_HANDLE(h);
+    if (op != LBM_MEAN_RESET && op != LBM_MEAN_ACCUMULATE)
+        return fail(h, LBM_EINVAL, "op = %d is not LBM_MEAN_RESET or LBM_MEAN_ACCUMULATE", op);
+    const size_t bytes = sizeof(double) * (size_t)h->ncell;
+    if (op == LBM_MEAN_RESET) {
+        if (h->rho_acc) CUDA_TRY(h, cudaMemsetAsync(h->rho_acc, 0, bytes, h->stream));
+        h->rho_count = 0;
+        return LBM_OK;
+    }
+    if (!h->rho_acc) {
+        if (cudaMalloc(&h->rho_acc, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            h->rho_acc = nullptr;
+            return fail(h, LBM_ENOMEM, "cudaMalloc of the mean-pressure accumulator (%zu bytes) failed", bytes);
+        }
+        CUDA_TRY(h, cudaMemsetAsync(h->rho_acc, 0, bytes, h->stream));
+        h->rho_count = 0;
+    }
+    CUDA_TRY(h, dispatch<RhoAccumulate>(h->lattice, h->prec, h->stream, h->ncell, (const void *)h->f[h->cur],
+                                        h->rho_acc));
+    h->launches += 1;
+    h->rho_count += 1;
+    return LBM_OK;
+}
+
+extern "C" int lbm_pressure_fluctuation(lbm_handle h, double *dp_tilde, double *dp_mean)
+{
+    CHECK_HANDLE(h);
+    if (!dp_tilde && !dp_mean) return LBM_OK;
+    if (!h->rho_acc || h->rho_count == 0)
+        return fail(h, LBM_EINVAL, "no accumulated samples: call lbm_pressure_mean(h, LBM_MEAN_ACCUMULATE) first");
+    const int64_t N = h->ncell;
+    double *buf = nullptr;
+    CUDA_TRY(h, cudaMalloc(&buf, sizeof(double) * 2 * (size_t)N));
+    cudaError_t e = dispatch<PressureFluct>(h->lattice, h->prec, h->stream, N, (const void *)h->f[h->cur],
+                                            (const double *)h->rho_acc, (double)h->rho_count, buf,
+                                            dp_mean ? buf + N : (double *)nullptr);
+    if (e == cudaSuccess && dp_tilde)
+        e = cudaMemcpyAsync(dp_tilde, buf, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && dp_mean)
+        e = cudaMemcpyAsync(dp_mean, buf + N, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(buf);
+    h->launches += 1;
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "lbm_pressure_fluctuation: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
 

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <climits>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -295,6 +296,7 @@ static int admit(lbm_server *s)
         for (int f = 0; f < 6; ++f) d.p.face_cells[f] = 1;
         d.p.rho_ref = 1.0;
         d.p.omega = 1.0 - 1.0 / r->tau;
+        d.p.jet_x_layer = INT_MAX;
         set_bulk_box(d.p);
         d.f[0] = r->f[0];
         d.f[1] = r->f[1];

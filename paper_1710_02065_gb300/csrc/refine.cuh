@@ -75,7 +75,7 @@ __device__ void streamed_moments_2d(const S *__restrict__ f, const uint8_t *__re
         sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
         sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
         const int64_t src = sx + (int64_t)nx * sy;
-        if (mask && i != 0 && mask[src] == 1)
+        if (mask && i != 0 && (mask[src] & MASK_TYPE) == MASK_SOLID)
             g[i] = Store<S>::ld(f + (int64_t)opp<D2Q9>(i) * N + cell);
         else
             g[i] = Store<S>::ld(f + (int64_t)i * N + src);
@@ -306,7 +306,7 @@ __device__ void streamed_moments_3d(const S *__restrict__ f, const uint8_t *__re
         sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
         sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
         const int64_t src = sx + (int64_t)nx * (sy + (int64_t)ny * sz);
-        if (mask && i != 0 && mask[src] == 1)
+        if (mask && i != 0 && (mask[src] & MASK_TYPE) == MASK_SOLID)
             g[i] = Store<S>::ld(f + (int64_t)opp<D3Q19>(i) * N + cell);
         else
             g[i] = Store<S>::ld(f + (int64_t)i * N + src);

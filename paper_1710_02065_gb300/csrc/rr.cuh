@@ -138,6 +138,10 @@ struct Store<__nv_bfloat16> {
 __device__ __forceinline__ float fmac(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmac(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// Device cell-type byte: bits 0-1 the cell type (0 fluid, 1 solid wall,
+// 2 fixed), bit 2 set when a lattice neighbour is a solid wall.
+constexpr uint8_t MASK_TYPE = 3, MASK_SOLID = 1, MASK_NEAR_SOLID = 4;
+
 // compute type a storage format is written from
 template <class S>
 struct StoreC {

@@ -60,6 +60,11 @@ struct StepParams {
     // collision model: 0 rrBGK (Eq. optimizedLB), 1 plain BGK (Eq. standardLB;
     // general kernel only)
     int bgk;
+    // round-jet similarity reference of the +x sponge layer (cells with
+    // x >= jet_x_layer): yc, zc, U_J, B D, x0, a = (sqrt 2 - 1) / S^2;
+    // jet_x_layer = INT_MAX when none
+    int jet_x_layer;
+    double jet_ref[6];
     // per-direction base addresses of the lattice read (in) and written (out):
     // in[i] = f_in + i * ncell elements; filled by the launchers
     const char *in[19];
@@ -221,22 +226,33 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
         // f* = (1 - chi) feqH(rho*, u*) + chi feqH(rho_ref, u_ref) + (1 - 1/tau) fneqH
         const C h = C(1) / (C(1) + C(0.5) * chi);
         const C rr = C(p.rho_ref);
+        C urx = C(p.u_ref[0]), ury = C(p.u_ref[1]), urz = C(p.u_ref[2]);
+        if (L::D == 3 && cx >= p.jet_x_layer) {
+            // outflow layer: self-similar round jet, centreline min(U_J, B D U_J / xi),
+            // profile (1 + a eta^2)^-2, eta = r / xi, xi = x - x0
+            const C xi = C(cx) - C(p.jet_ref[4]);
+            const C Uc = (xi > C(0) && C(p.jet_ref[3]) < xi) ? C(p.jet_ref[3]) * C(p.jet_ref[2]) / xi : C(p.jet_ref[2]);
+            const C dy = C(cy) - C(p.jet_ref[0]), dz = C(cz) - C(p.jet_ref[1]);
+            const C e2 = xi > C(0) ? (dy * dy + dz * dz) / (xi * xi) : C(0);
+            const C q = C(1) + C(p.jet_ref[5]) * e2;
+            urx = Uc / (q * q);
+            ury = urz = C(0);
+        }
         const C drs = (m.dr + C(0.5) * chi * C(p.rho_ref_m1)) * h;  // rho* - 1
         const C rs = C(1) + drs;
         const C inv = recip(rs);
-        const C ux = (m.jx + C(0.5) * chi * rr * C(p.u_ref[0])) * h * inv;
-        const C uy = (m.jy + C(0.5) * chi * rr * C(p.u_ref[1])) * h * inv;
-        const C uz = L::D == 3 ? (m.jz + C(0.5) * chi * rr * C(p.u_ref[2])) * h * inv : C(0);
+        const C ux = (m.jx + C(0.5) * chi * rr * urx) * h * inv;
+        const C uy = (m.jy + C(0.5) * chi * rr * ury) * h * inv;
+        const C uz = L::D == 3 ? (m.jz + C(0.5) * chi * rr * urz) * h * inv : C(0);
         if (BGK) {
             // (1 - 1/tau - chi) f^eq(rho*, u*) + chi f^eq(ref); the caller adds (1 - 1/tau) g
             add_eq<C, L::D, O3>(k, C(1) - om - chi, drs, rs, ux, uy, uz);
-            add_eq<C, L::D, O3>(k, chi, C(p.rho_ref_m1), rr, C(p.u_ref[0]), C(p.u_ref[1]),
-                                L::D == 3 ? C(p.u_ref[2]) : C(0));
+            add_eq<C, L::D, O3>(k, chi, C(p.rho_ref_m1), rr, urx, ury, L::D == 3 ? urz : C(0));
             return k;
         }
         const Sym2<C> pn = pi_neq<C>(m, drs, rs, ux, uy, uz, L::D);
         add_eq<C, L::D, O3>(k, C(1) - chi, drs, rs, ux, uy, uz);
-        add_eq<C, L::D, O3>(k, chi, C(p.rho_ref_m1), rr, C(p.u_ref[0]), C(p.u_ref[1]), L::D == 3 ? C(p.u_ref[2]) : C(0));
+        add_eq<C, L::D, O3>(k, chi, C(p.rho_ref_m1), rr, urx, ury, L::D == 3 ? urz : C(0));
         add_neq<C, L::D, O3>(k, om, ux, uy, uz, pn);
         return k;
     }
@@ -268,7 +284,7 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     const unsigned nxy = nx * ny;
     const unsigned cell = x + nx * y + nxy * z;
     const uint8_t *__restrict__ solid = p.solid;
-    if (solid && solid[cell]) return;  // solid (1) and fixed (2) cells keep their populations
+    if (solid && (solid[cell] & MASK_TYPE)) return;  // solid (1) and fixed (2) cells keep their populations
 
     // ---- boundary role and the node whose streamed populations are used
     unsigned sx = x, sy = y, sz = z;
@@ -295,7 +311,9 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     const unsigned zm = sz == 0 ? nz - 1 : sz - 1, zp = sz == nz - 1 ? 0 : sz + 1;
     const unsigned scell = sx + nx * sy + nxy * sz;
 
-    // ---- streaming (pull) with halfway bounce-back
+    // ---- streaming (pull) with halfway bounce-back; only a node with a solid
+    // neighbour tests its links
+    const bool near = solid && (solid[scell] & MASK_NEAR_SOLID);
     C g[L::Q];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
@@ -303,7 +321,7 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
         const unsigned Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
         const unsigned Z = L::D == 2 ? 0u : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
         const unsigned src = X + nx * Y + nxy * Z;
-        if (solid && i != 0 && solid[src] == 1)
+        if (near && i != 0 && (solid[src] & MASK_TYPE) == MASK_SOLID)
             g[i] = Store<S>::ld((const S *)in[opp<L>(i)] + scell);
         else
             g[i] = Store<S>::ld((const S *)in[i] + src);

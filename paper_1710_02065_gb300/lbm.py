@@ -68,6 +68,9 @@ _sig("lbm_set_launch", [_h, C.c_int, C.c_int])
 _sig("lbm_get_launch", [_h, _ip, _ip])
 _sig("lbm_set_staging", [_h, C.c_int, C.c_int, C.c_int])
 _sig("lbm_set_collision", [_h, C.c_int])
+_sig("lbm_pressure_mean", [_h, C.c_int])
+_sig("lbm_pressure_fluctuation", [_h, _dp, _dp])
+_sig("lbm_set_sponge_jet_reference", [_h] + [C.c_double] * 7)
 _sig("lbm_get_staging", [_h, _ip, _ip, _ip, _ip, _ip])
 _sig("lbm_info", [_h, _i64p, _i64p, _dp, _dp])
 _sig("lbm_add_refinement_patch", [_h, _ip, _ip])
@@ -100,7 +103,8 @@ EXPORTED = [
     "lbm_set_boundary", "lbm_set_pressure", "lbm_set_inlet_noise", "lbm_set_sponge", "lbm_set_radial_sponge", "lbm_set_state",
     "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_moments", "lbm_reduce",
     "lbm_probe", "lbm_sync", "lbm_info", "lbm_save", "lbm_load", "lbm_set_launch", "lbm_get_launch",
-    "lbm_set_staging", "lbm_get_staging", "lbm_set_collision",
+    "lbm_set_staging", "lbm_get_staging", "lbm_set_collision", "lbm_set_sponge_jet_reference",
+    "lbm_pressure_mean", "lbm_pressure_fluctuation",
     "lbm_add_refinement_patch", "lbm_level_info", "lbm_force", "lbm_set_geometry_level", "lbm_set_state_level",
     "lbm_set_populations_level", "lbm_get_populations_level", "lbm_moments_level",
     "lbm_reduce_noalloc", "lbm_server_create", "lbm_server_destroy", "lbm_server_last_error",
@@ -246,6 +250,26 @@ def lbm_get_launch(h):
 
 
 LBM_COLLISION_RR, LBM_COLLISION_BGK = 0, 1
+
+
+def lbm_set_sponge_jet_reference(h, yc: float, zc: float, U_jet: float, D: float, x0: float, B: float = 5.8,
+                                 S: float = 0.094):
+    return _check(_lib.lbm_set_sponge_jet_reference(h, float(yc), float(zc), float(U_jet), float(D), float(x0),
+                                                    float(B), float(S)), h)
+
+
+LBM_MEAN_RESET, LBM_MEAN_ACCUMULATE = 0, 1
+
+
+def lbm_pressure_mean(h, op: int):
+    return _check(_lib.lbm_pressure_mean(h, int(op)), h)
+
+
+def lbm_pressure_fluctuation(h, dp_tilde=None, dp_mean=None):
+    """Fill host float64 arrays (ncell) with Delta p~ and the mean Delta p."""
+    for a in (dp_tilde, dp_mean):
+        assert a is None or (a.dtype == np.float64 and a.flags.c_contiguous)
+    return _check(_lib.lbm_pressure_fluctuation(h, _d(dp_tilde), _d(dp_mean)), h)
 
 
 def lbm_set_collision(h, model: int):

@@ -606,3 +606,63 @@ def test_collision_model_and_refinement_exclude_each_other():
     with pytest.raises(lbm.LBMError):
         lbm.lbm_set_collision(s.h, 7)
     s.close()
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+def test_jet_similarity_sponge_reference_matches_oracle(prec):
+    """Outflow sponge with the round-jet similarity reference (Sec. IV), a
+    jet inflow profile, outflow and lateral sponges; every kernel."""
+    from paper_1710_02065_gb300 import lbm
+    _, _, _, w, _ = oracle.lattice(D3Q19)
+    n = (48, 24, 24)
+    c = Case("jetref", D3Q19, n, 0.56)
+    prof = inputs.top_hat_profile(n[1], n[2], n[1] / 2, n[2] / 2, 4.0, 0.08, 1.0)
+    c.faces = {0: (VELOCITY, (0, 0, 0), prof), 1: (OUTFLOW, (0, 0, 0), None)}
+    c.sponges = {1: (16, 0.6), 3: (4, 0.3)}
+    c.rho_ref, c.u_ref = 1.0, (0.0, 0.0, 0.0)
+    c = with_random_state(c, seed=21, spread=0.05)
+    jet = (n[1] / 2 - 0.5, n[2] / 2 - 0.5, 0.08, 3.0, 18.0, 5.8, 0.094)  # capped for x < 35.4, decaying beyond
+    P, f = to_oracle(c)
+    P.set_jet_reference(*jet)
+    ref = P.run(f, 3)
+    P0, _ = to_oracle(c)
+    assert np.abs(P0.run(f, 3) - ref).max() > 1e-6  # the reference changes the result
+    for kind in KERNELS[prec]:
+        s = to_gpu(c, PRECS[prec])
+        lbm.lbm_set_sponge_jet_reference(s.h, *jet)
+        use_kernel(s, kind)
+        s.step(3)
+        err = np.abs(s.populations() - ref).max()
+        assert err <= _pop_tol(prec, ref, w, 3), (kind, err)
+        s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 5e-7)])
+def test_pressure_fluctuation_matches_oracle(prec, tol):
+    """Delta p~ = c_s^2 (rho - temporal mean rho) (Sec. III) over 12 sampled
+    steps of the D2Q9 acoustic pulse, and the mean Delta p, against the same
+    averages of the oracle's fields (absolute tolerances: FP64 round-off; FP32
+    storage keeps rho - 1 to about 1e-7)."""
+    from paper_1710_02065_gb300 import lbm
+    c = acoustic_pulse(64)
+    P, f = to_oracle(c)
+    s = to_gpu(c, PRECS[prec])
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_pressure_fluctuation(s.h, np.zeros(s.ncell), None)
+    rhos = []
+    for t in range(12):
+        f = P.run(f, 1, step0=t)
+        rhos.append(P.moments(f)[0])
+        s.step(1)
+        lbm.lbm_pressure_mean(s.h, lbm.LBM_MEAN_ACCUMULATE)
+    mean = np.mean(rhos, axis=0)
+    dp, dpm = np.zeros(s.ncell), np.zeros(s.ncell)
+    lbm.lbm_pressure_fluctuation(s.h, dp, dpm)
+    assert np.abs(dp - (rhos[-1] - mean) / 3).max() <= tol
+    assert np.abs(dpm - (mean - 1) / 3).max() <= tol
+    # reset: a single new sample makes Delta p~ vanish
+    lbm.lbm_pressure_mean(s.h, lbm.LBM_MEAN_RESET)
+    lbm.lbm_pressure_mean(s.h, lbm.LBM_MEAN_ACCUMULATE)
+    lbm.lbm_pressure_fluctuation(s.h, dp, None)
+    assert np.abs(dp).max() <= tol
+    s.close()
