@@ -476,6 +476,65 @@ def run_cylinder_two_level(lbm, torch, args):
             "mlups_incl_sampling": cells * total / wall / 1e6, "stable": rc == 0, "tau_c": tau_c, "tau_f": tau_f}
 
 
+def run_cylinder_three_level(lbm, torch, args):
+    """Three nested levels (the paper's cylinder uses four): coarse 400x200
+    (D = 10), level 1 over coarse [40, 240] x [50, 150] (401 x 201, D = 20),
+    level 2 over level-1 [60, 260] x [40, 160] (401 x 241, D = 40 around the
+    cylinder and 7 D of its wake); the cylinder at coarse (100, 100), same
+    Ma, Re, inflow, sponge (25 coarse cells) and seeds as the single-level
+    run.  Lift/drag on the finest level; cell updates per coarse step:
+    coarse + 2 x level 1 + 4 x level 2."""
+    from paper_1710_02065_gb300 import inputs
+    U = 0.2 * CS
+    D2 = 40.0
+    tau = [0.0, 0.0, 3 * U * D2 / 150.0 + 0.5]
+    tau[1] = (tau[2] + 0.5) / 2
+    tau[0] = (tau[1] + 0.5) / 2
+    nxc, nyc = 400, 200
+    stream = torch.cuda.Stream()
+    s = lbm.Solver(lbm.LBM_D2Q9, (nxc, nyc, 1), tau[0], lbm.PRECISIONS[args.precision], Ma_ref=0.2,
+                   stream=stream.cuda_stream)
+    lbm.lbm_set_boundary(s.h, 0, 1, (U, 0, 0))
+    lbm.lbm_set_boundary(s.h, 1, 2)
+    lbm.lbm_set_sponge(s.h, 1, 25, 0.5, 1.0, (U, 0, 0))
+    rho, u = inputs.uniform_flow_perturbed(nxc, nyc, U, 2)
+    s.set_state(rho, u)
+    patches = [((40, 50, 0), (200, 100, 1)), ((60, 40, 0), (200, 120, 1))]
+    for o, e in patches:
+        lbm.lbm_add_refinement_patch(s.h, o, e)
+    ext1, _ = lbm.lbm_level_info(s.h, 1)
+    ext2, _ = lbm.lbm_level_info(s.h, 2)
+    # cylinder centre in level-2 nodes: coarse (100, 100) -> level 1 (120, 100) -> level 2 (120, 120)
+    solid = inputs.cylinder_mask(ext2[0], ext2[1], 120.0, 120.0, D2)
+    lbm.lbm_set_geometry_level(s.h, 2, solid)
+    r1, u1 = inputs.uniform_flow_perturbed(ext1[0], ext1[1], U, 3)
+    r2, u2 = inputs.uniform_flow_perturbed(ext2[0], ext2[1], U, 4)
+    u2[solid == 1] = 0.0
+    lbm.lbm_set_state_level(s.h, 2, r2, u2)
+    lbm.lbm_set_state_level(s.h, 1, r1, u1)
+    lbm.lbm_set_state(s.h, rho, u)
+    total = args.cyl_steps // 4  # coarse steps covering the same physical time as the single-level run
+    every = 5
+    lift, drag = [], []
+    t0 = time.perf_counter()
+    for t in range(0, total, every):
+        lbm.lbm_step(s.h, every)
+        F = lbm.lbm_force(s.h, 2)
+        drag.append(F[0]); lift.append(F[1])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    _, _, rc = s.reduce()
+    s.close()
+    half = len(lift) // 2
+    q = 0.5 * U * U * D2
+    cells = nxc * nyc + 2 * ext1[0] * ext1[1] + 4 * ext2[0] * ext2[1]
+    return {"workload": f"D2Q9 cylinder, three nested levels: coarse 400x200 + {ext1[0]}x{ext1[1]} + "
+                        f"{ext2[0]}x{ext2[1]}", "coarse_steps": total,
+            "St": strouhal(lift[half:], 4 * every, D2, U), "Cd_mean": float(np.mean(drag[half:]) / q),
+            "Cl_amplitude": float((np.max(lift[half:]) - np.min(lift[half:])) / 2 / q),
+            "mlups_incl_sampling": cells * total / wall / 1e6, "stable": rc == 0, "tau": tau}
+
+
 def run_jet_two_level(lbm, torch, args):
     """2:1 two-level D3Q19 round jet: the 384x256x256 jet lattice (FP32,
     Re_D 1e4, sponges, inlet noise) with a fine patch over the near-nozzle
@@ -567,8 +626,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape (no autotuning)")
-    ap.add_argument("--workload", default="jet", choices=["jet", "cylinder", "cylinder2level", "jet2level",
-                                                          "serving"],
+    ap.add_argument("--workload", default="jet", choices=["jet", "cylinder", "cylinder2level", "cylinder3level",
+                                                          "jet2level", "serving"],
                     help="jet: the headline benchmark line; the others print their own JSON line")
     ap.add_argument("--cyl-steps", type=int, default=40000, help="fine-resolution steps of the cylinder runs")
     ap.add_argument("--requests", type=int, default=512)
@@ -597,8 +656,8 @@ def main():
     from paper_1710_02065_gb300 import lbm
 
     if args.workload != "jet":
-        fn = {"cylinder": run_cylinder, "cylinder2level": run_cylinder_two_level, "jet2level": run_jet_two_level,
-              "serving": run_serving}
+        fn = {"cylinder": run_cylinder, "cylinder2level": run_cylinder_two_level,
+              "cylinder3level": run_cylinder_three_level, "jet2level": run_jet_two_level, "serving": run_serving}
         out = fn[args.workload](lbm, torch, args)
         if rank == 0:
             print(json.dumps(out), flush=True)

@@ -376,32 +376,37 @@ int lbm_info(lbm_handle h, int64_t *step, int64_t *launches, double *bytes_per_c
              double *tau);
 
 /*
- * Two-level grid (Sec. II.B, multi-domain 2:1 refinement; D2Q9 and D3Q19).
+ * Refined levels (Sec. II.B, multi-domain 2:1 refinement; D2Q9 and D3Q19).
  *
- * lbm_add_refinement_patch -- add a fine level over the coarse nodes
- * origin[a]..origin[a]+extent[a] on every axis a of the lattice (x, y; and z
- * for D3Q19; extent >= 4, at least 2 coarse cells from every face).  The fine
- * level has 2 extent[a] + 1 nodes per axis, dx_f = dx_c / 2, two fine steps
- * per coarse step (Eq. convective), tau_f = 2 tau_c - 1/2 (same physical
- * viscosity), starts at rest.  Coupling per coarse step: the fine boundary
- * ring (2D) / shell (3D) is rebuilt from coarse rho, u, Pi^neq interpolated
- * in space (copy at coincident nodes; the 4-point cubic (-1, 9, 9, -1)/16
- * along every axis on which the fine node falls between coarse nodes, their
- * tensor product on the 3D interface planes) and linearly in time (t + 1/2,
- * t + 1), Eq. couplingFC; the first ring / shell of covered coarse nodes is
- * rebuilt from the coincident fine node's rho, u and its full-weighted
- * Pi^neq ((1,2,1)^2 / 16 in 2D, (1,2,1)^3 / 64 in 3D), Eq. couplingCF.
- * f^neq is rescaled by tau_f / (2 tau_c) coarse -> fine and 2 tau_c / tau_f
- * fine -> coarse (the leading-order Chapman-Enskog scaling of Sec. II.B).
- * Deeper covered coarse cells are frozen.  Solids of level 1 must stay 2 fine
- * cells inside the ring / shell.  At most one patch per handle.
+ * lbm_add_refinement_patch -- add a level inside the finest existing level
+ * (the first call refines level 0, the next one nests inside it, ...; at
+ * most LBM_MAX_LEVELS levels in all).  The new level covers the parent-level
+ * nodes origin[a]..origin[a]+extent[a] on every axis a of the lattice (x, y;
+ * and z for D3Q19; extent >= 4, at least 2 cells from every face of the
+ * parent).  It has 2 extent[a] + 1 nodes per axis, half the parent's spacing,
+ * two steps per parent step (Eq. convective), tau = 2 tau_parent - 1/2 (same
+ * physical viscosity), and starts at rest.  Coupling per parent step: the new
+ * level's boundary ring (2D) / shell (3D) is rebuilt from the parent's rho,
+ * u, Pi^neq interpolated in space (copy at coincident nodes; the 4-point
+ * cubic (-1, 9, 9, -1)/16 along every axis on which the node falls between
+ * parent nodes, their tensor product on the 3D interface planes) and linearly
+ * in time (t + 1/2, t + 1), Eq. couplingFC; the parent's first ring / shell of
+ * covered nodes is rebuilt from the coincident node's rho, u and its
+ * full-weighted Pi^neq ((1,2,1)^2 / 16 in 2D, (1,2,1)^3 / 64 in 3D),
+ * Eq. couplingCF.  f^neq is rescaled by tau_child / (2 tau_parent) parent ->
+ * child and 2 tau_parent / tau_child child -> parent (the leading-order
+ * Chapman-Enskog scaling of Sec. II.B).  Deeper covered parent cells are
+ * frozen.  Solids of a refined level must stay 2 of its cells inside its
+ * ring / shell and outside its child's box.
  *
- * Level-indexed variants (level 0 = coarse, the plain functions; level 1 =
- * fine): extents and tau of a level; geometry (fine cell types, the ring is
- * managed by the library); initial state and populations (set_*_level does
- * not touch the other level; setting level 0 also refreshes the interface
- * moments); populations and moments of the stored field.
+ * Level-indexed variants (level 0 = coarse, the plain functions; level k =
+ * the k-th refined level): extents and tau of a level; geometry (cell types
+ * of a refined level; its ring and its child's covered box are managed by the
+ * library); initial state and populations (set_*_level touches only that
+ * level and refreshes the interface moments of the level it is the parent
+ * of); populations and moments of the stored field.
  */
+#define LBM_MAX_LEVELS 8
 int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const int extent[3]);
 int lbm_level_info(lbm_handle h, int level, int extents[3], double *tau);
 int lbm_set_geometry_level(lbm_handle h, int level, const uint8_t *cell_type);

@@ -17,7 +17,8 @@
 
 using namespace rr;
 
-// The fine level of a two-level grid (Sec. II.B)
+// A refined level (Sec. II.B): level k + 1 covers a box of level k's nodes
+// at half the spacing; levels nest, each inside the previous one.
 struct FineLevel {
     int n[3] = {1, 1, 1};
     int64_t ncell = 0;
@@ -26,8 +27,8 @@ struct FineLevel {
     int cur = 0;
     uint8_t *mask_d = nullptr;           // ring fixed + user solids
     std::vector<uint8_t> user_mask;      // user solids (host copy)
-    RefineGeom geom{};
-    double *M[2] = {nullptr, nullptr};   // coarse line moments at t and t + 1
+    RefineGeom geom{};                   // position in the parent level's nodes
+    double *M[2] = {nullptr, nullptr};   // parent-side interface moments at t and t + 1
     int mcur = 0;
 };
 
@@ -66,13 +67,13 @@ struct lbm_ctx {
     double *red_d = nullptr;  // reduction partials + result
     int red_blocks = 0;
     std::vector<uint8_t> user_mask;  // caller's cell types (host copy); empty: none
-    FineLevel *fine = nullptr;       // two-level grid, or null
+    std::vector<FineLevel *> levels;  // refined levels 1, 2, ... (each inside the previous one)
     // graph of two steps (the parity period) replayed by lbm_step; valid for
     // one configuration version and parity
     int64_t cfg_version = 0;
     cudaGraphExec_t graph = nullptr;
     int64_t graph_version = -1;
-    int graph_cur = -1, graph_mcur = -1;
+    uint64_t graph_sig = 0;  // lattice parities the graph was captured at
     int64_t graph_launches = 0;
     std::string err;
 };
@@ -90,11 +91,15 @@ static GridRef coarse_ref(lbm_ctx *h)
 {
     return GridRef{{h->n[0], h->n[1], h->n[2]}, h->ncell, h->f, &h->cur, h->solid_d};
 }
-static GridRef fine_ref(lbm_ctx *h)
+static int nlevels(const lbm_ctx *h) { return 1 + (int)h->levels.size(); }
+static FineLevel *fine_level(lbm_ctx *h, int k) { return h->levels[(size_t)k - 1]; }  // k >= 1
+static GridRef level_grid(lbm_ctx *h, int k)
 {
-    FineLevel *F = h->fine;
+    if (k == 0) return coarse_ref(h);
+    FineLevel *F = fine_level(h, k);
     return GridRef{{F->n[0], F->n[1], F->n[2]}, F->ncell, F->f, &F->cur, F->mask_d};
 }
+static double level_tau(lbm_ctx *h, int k) { return k == 0 ? h->tau : fine_level(h, k)->tau; }
 
 static thread_local std::string g_create_err;
 
@@ -293,13 +298,13 @@ static void release(lbm_ctx *h)
     if (h->err_d) cudaFree(h->err_d);
     if (h->rho_acc) cudaFree(h->rho_acc);
     if (h->graph) cudaGraphExecDestroy(h->graph);
-    if (h->fine) {
+    for (FineLevel *F : h->levels) {
         for (int k = 0; k < 2; ++k) {
-            if (h->fine->f[k]) cudaFree(h->fine->f[k]);
-            if (h->fine->M[k]) cudaFree(h->fine->M[k]);
+            if (F->f[k]) cudaFree(F->f[k]);
+            if (F->M[k]) cudaFree(F->M[k]);
         }
-        if (h->fine->mask_d) cudaFree(h->fine->mask_d);
-        delete h->fine;
+        if (F->mask_d) cudaFree(F->mask_d);
+        delete F;
     }
     delete h;
 }
@@ -419,50 +424,43 @@ static void add_near_solid(lbm_ctx *h, std::vector<uint8_t> &m, const int n[3])
         add_near_solid_bits<D3Q19>(m, n);
 }
 
-// Upload the coarse mask: the caller's cell types, plus the covered patch
-// interior as fixed cells when a fine level exists.
-static int upload_coarse_mask(lbm_ctx *h)
+// Upload the cell types of level k: the caller's types; on a refined level
+// its boundary ring (2D) / shell (3D), rebuilt from the parent, as fixed
+// cells; on a level with a child the child's covered interior (strictly
+// inside the child's box on every axis) as fixed cells; plus the near-solid
+// bits.  Level 0 without types and without a child has no mask.
+static int upload_level_mask(lbm_ctx *h, int k)
 {
-    const bool patch = h->fine != nullptr;
-    if (h->user_mask.empty() && !patch) {
+    const bool has_child = k < (int)h->levels.size();
+    GridRef g = level_grid(h, k);
+    const std::vector<uint8_t> &user = k == 0 ? h->user_mask : fine_level(h, k)->user_mask;
+    if (k == 0 && user.empty() && !has_child) {
         if (h->solid_d) cudaFree(h->solid_d);
         h->solid_d = nullptr;
         return LBM_OK;
     }
-    std::vector<uint8_t> m(h->user_mask);
-    if (m.empty()) m.assign((size_t)h->ncell, (uint8_t)LBM_CELL_FLUID);
-    if (patch) {
-        // covered coarse nodes (strictly inside the patch on every axis of it)
-        const RefineGeom &g = h->fine->geom;
-        const int z0 = h->d == 3 ? g.Z0 + 1 : 0, z1 = h->d == 3 ? g.Z0 + g.Dc : 1;
-        for (int z = z0; z < z1; ++z)
-            for (int y = g.Y0 + 1; y < g.Y0 + g.Hc; ++y)
-                for (int x = g.X0 + 1; x < g.X0 + g.Wc; ++x)
-                    m[(size_t)x + (size_t)h->n[0] * ((size_t)y + (size_t)h->n[1] * z)] = LBM_CELL_FIXED;
-    }
-    add_near_solid(h, m, h->n);
-    if (!h->solid_d) CUDA_TRY(h, cudaMalloc(&h->solid_d, (size_t)h->ncell));
-    CUDA_TRY(h, cudaMemcpyAsync(h->solid_d, m.data(), (size_t)h->ncell, cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    return LBM_OK;
-}
-
-static int upload_fine_mask(lbm_ctx *h)
-{
-    FineLevel *F = h->fine;
-    std::vector<uint8_t> m(F->user_mask);
-    if (m.empty()) m.assign((size_t)F->ncell, (uint8_t)LBM_CELL_FLUID);
-    // the boundary ring (2D) / shell (3D) of the fine box is rebuilt from coarse data
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    std::vector<uint8_t> m(user);
+    if (m.empty()) m.assign((size_t)g.ncell, (uint8_t)LBM_CELL_FLUID);
+    auto at = [&](int x, int y, int z) -> uint8_t & { return m[(size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z)]; };
     const bool three = h->d == 3;
-    for (int k = 0; k < F->n[2]; ++k)
-        for (int j = 0; j < F->n[1]; ++j)
-            for (int i = 0; i < F->n[0]; ++i)
-                if (i == 0 || j == 0 || i == F->n[0] - 1 || j == F->n[1] - 1 ||
-                    (three && (k == 0 || k == F->n[2] - 1)))
-                    m[(size_t)i + (size_t)F->n[0] * ((size_t)j + (size_t)F->n[1] * k)] = LBM_CELL_FIXED;
-    add_near_solid(h, m, F->n);
-    if (!F->mask_d) CUDA_TRY(h, cudaMalloc(&F->mask_d, (size_t)F->ncell));
-    CUDA_TRY(h, cudaMemcpyAsync(F->mask_d, m.data(), (size_t)F->ncell, cudaMemcpyHostToDevice, h->stream));
+    if (k >= 1)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x)
+                    if (x == 0 || y == 0 || x == nx - 1 || y == ny - 1 || (three && (z == 0 || z == nz - 1)))
+                        at(x, y, z) = LBM_CELL_FIXED;
+    if (has_child) {
+        const RefineGeom &c = fine_level(h, k + 1)->geom;
+        const int z0 = three ? c.Z0 + 1 : 0, z1 = three ? c.Z0 + c.Dc : 1;
+        for (int z = z0; z < z1; ++z)
+            for (int y = c.Y0 + 1; y < c.Y0 + c.Hc; ++y)
+                for (int x = c.X0 + 1; x < c.X0 + c.Wc; ++x) at(x, y, z) = LBM_CELL_FIXED;
+    }
+    add_near_solid(h, m, g.n);
+    uint8_t *&dst = k == 0 ? h->solid_d : fine_level(h, k)->mask_d;
+    if (!dst) CUDA_TRY(h, cudaMalloc(&dst, (size_t)g.ncell));
+    CUDA_TRY(h, cudaMemcpyAsync(dst, m.data(), (size_t)g.ncell, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
@@ -486,7 +484,7 @@ extern "C" int lbm_set_geometry(lbm_handle h, const uint8_t *cell_type)
     } else {
         h->user_mask.clear();
     }
-    return upload_coarse_mask(h);
+    return upload_level_mask(h, 0);
 }
 
 static int64_t face_cells(const lbm_ctx *h, int face)
@@ -684,7 +682,7 @@ static int get_pops_grid(lbm_ctx *h, const GridRef &g, double *f)
     return LBM_OK;
 }
 
-static int init_line_moments(lbm_ctx *h);
+static int refresh_after_set(lbm_ctx *h, int k);
 static int level_ref(lbm_ctx *h, int level, GridRef &g);
 static int moments_grid(lbm_ctx *h, const GridRef &g, double *rho, double *u, double *pi_neq);
 
@@ -694,7 +692,7 @@ extern "C" int lbm_set_state(lbm_handle h, const double *rho, const double *u)
     int rc = set_state_grid(h, coarse_ref(h), rho, u);
     if (rc != LBM_OK) return rc;
     h->step = 0;
-    return h->fine ? init_line_moments(h) : LBM_OK;
+    return refresh_after_set(h, 0);
 }
 
 extern "C" int lbm_set_populations(lbm_handle h, const double *f)
@@ -703,7 +701,7 @@ extern "C" int lbm_set_populations(lbm_handle h, const double *f)
     int rc = set_pops_grid(h, coarse_ref(h), f);
     if (rc != LBM_OK) return rc;
     h->step = 0;
-    return h->fine ? init_line_moments(h) : LBM_OK;
+    return refresh_after_set(h, 0);
 }
 
 extern "C" int lbm_get_populations(lbm_handle h, double *f)
@@ -803,10 +801,10 @@ static cudaError_t launch_update(lbm_ctx *h, const StepParams &p, const void *fi
                                   : stepvec_d3q19(h->prec, vec, p, fin, fout, block, h->stream);
 }
 
-// Step parameters of the fine level: periodic box, ring fixed, no sponge/inflow
-static void fine_params(lbm_ctx *h, StepParams &p)
+// Step parameters of refined level k >= 1: periodic box, ring fixed, no sponge/inflow
+static void fine_params(lbm_ctx *h, int k, StepParams &p)
 {
-    FineLevel *F = h->fine;
+    FineLevel *F = fine_level(h, k);
     std::memset(&p, 0, sizeof p);
     for (int a = 0; a < 3; ++a) {
         p.n[a] = F->n[a];
@@ -823,9 +821,11 @@ static void fine_params(lbm_ctx *h, StepParams &p)
 
 // D3Q19 patch: plane moments, fine shell, covered coarse shell
 template <class S>
-static cudaError_t refine_kernels3(lbm_ctx *h, int stage, int a_half)
+static cudaError_t refine_kernels3(lbm_ctx *h, int k, int stage, int a_half)
 {
-    FineLevel *F = h->fine;
+    FineLevel *F = fine_level(h, k);
+    const GridRef P = level_grid(h, k - 1);  // the parent level
+    const double tau_p = level_tau(h, k - 1);
     const RefineGeom &g = F->geom;
     cudaStream_t st = h->stream;
     switch (stage) {
@@ -833,20 +833,19 @@ static cudaError_t refine_kernels3(lbm_ctx *h, int stage, int a_half)
     case 3: {  // plane moments at t = 0: local moments of the stored coarse field
         const int n = plane3_count(g);
         double *M = stage == 0 ? F->M[1 - F->mcur] : F->M[F->mcur];
-        k_plane_moments3<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)h->f[h->cur], h->solid_d, stage == 0 ? 1 : 0,
-                                                           M);
+        k_plane_moments3<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], P.mask, stage == 0 ? 1 : 0, M);
         break;
     }
     case 1: {  // fine shell at t + 1/2 (a_half = 1) or t + 1 (a_half = 0)
         const int n = shell3_count(g.nfx, g.nfy, g.nfz);
         k_fill_shell3<S><<<grid1(n, 128), 128, 0, st>>>(g, F->M[F->mcur], F->M[1 - F->mcur], a_half ? 0.5 : 1.0,
-                                                         F->tau / (2.0 * h->tau), F->tau, (S *)F->f[F->cur]);
+                                                         F->tau / (2.0 * tau_p), F->tau, (S *)F->f[F->cur]);
         break;
     }
     case 2: {  // covered coarse shell from the fine field; fine moments pulled from f(t + 1/2)
         const int n = shell3_count(g.Wc - 1, g.Hc - 1, g.Dc - 1);
-        k_restrict3<S><<<grid1(n, 64), 64, 0, st>>>(g, (const S *)F->f[1 - F->cur], F->mask_d, 2.0 * h->tau / F->tau,
-                                                     h->tau, (S *)h->f[h->cur]);
+        k_restrict3<S><<<grid1(n, 64), 64, 0, st>>>(g, (const S *)F->f[1 - F->cur], F->mask_d, 2.0 * tau_p / F->tau,
+                                                     tau_p, (S *)P.f[*P.cur]);
         break;
     }
     }
@@ -854,34 +853,41 @@ static cudaError_t refine_kernels3(lbm_ctx *h, int stage, int a_half)
     return cudaGetLastError();
 }
 
+// Coupling of refined level k >= 1 with its parent k - 1:
+//   stage 0: parent-side interface moments at t + 1 from the pre-step parent field
+//   stage 1: level k's ring / shell at t + 1/2 (a_half = 1) or t + 1 (a_half = 0)
+//   stage 2: the parent's covered ring / shell from level k at t + 1/2
+//   stage 3: interface moments at t = 0 (local moments of the stored parent field)
 template <class S>
-static cudaError_t refine_kernels(lbm_ctx *h, int stage, int a_half)
+static cudaError_t refine_kernels(lbm_ctx *h, int k, int stage, int a_half)
 {
-    if (h->d == 3) return refine_kernels3<S>(h, stage, a_half);
-    FineLevel *F = h->fine;
+    if (h->d == 3) return refine_kernels3<S>(h, k, stage, a_half);
+    FineLevel *F = fine_level(h, k);
+    const GridRef P = level_grid(h, k - 1);
+    const double tau_p = level_tau(h, k - 1);
     const RefineGeom &g = F->geom;
     cudaStream_t st = h->stream;
     switch (stage) {
     case 0: {  // coarse line moments at t + 1 from the pre-step coarse field
         const int n = line_count(g);
-        k_line_moments<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)h->f[h->cur], h->solid_d, 1, F->M[1 - F->mcur]);
+        k_line_moments<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], P.mask, 1, F->M[1 - F->mcur]);
         break;
     }
     case 1: {  // fine ring at t + 1/2 (a_half = 1) or t + 1 (a_half = 0)
         const int n = 2 * g.nfx + 2 * (g.nfy - 2);
         k_fill_ring<S><<<grid1(n, 128), 128, 0, st>>>(g, F->M[F->mcur], F->M[1 - F->mcur], a_half ? 0.5 : 1.0,
-                                                       F->tau / (2.0 * h->tau), F->tau, (S *)F->f[F->cur]);
+                                                       F->tau / (2.0 * tau_p), F->tau, (S *)F->f[F->cur]);
         break;
     }
     case 2: {  // covered coarse ring from the fine field; pre-collision fine moments pulled from f(t + 1/2)
         const int n = 2 * (g.Wc - 1) + 2 * (g.Hc - 3);
-        k_restrict<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)F->f[1 - F->cur], F->mask_d, 2.0 * h->tau / F->tau,
-                                                     h->tau, (S *)h->f[h->cur]);
+        k_restrict<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)F->f[1 - F->cur], F->mask_d, 2.0 * tau_p / F->tau,
+                                                     tau_p, (S *)P.f[*P.cur]);
         break;
     }
     case 3: {  // line moments at t = 0: local moments of the stored coarse field
         const int n = line_count(g);
-        k_line_moments<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)h->f[h->cur], h->solid_d, 0, F->M[F->mcur]);
+        k_line_moments<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], P.mask, 0, F->M[F->mcur]);
         break;
     }
     }
@@ -889,89 +895,109 @@ static cudaError_t refine_kernels(lbm_ctx *h, int stage, int a_half)
     return cudaGetLastError();
 }
 
-static cudaError_t refine_stage(lbm_ctx *h, int stage, int a_half = 0)
+static cudaError_t refine_stage(lbm_ctx *h, int k, int stage, int a_half = 0)
 {
     switch (h->prec) {
-    case LBM_FP64: return refine_kernels<double>(h, stage, a_half);
-    case LBM_FP32: return refine_kernels<float>(h, stage, a_half);
-    case LBM_FP16_SHIFTED: return refine_kernels<__half>(h, stage, a_half);
-    case LBM_BF16_SHIFTED: return refine_kernels<__nv_bfloat16>(h, stage, a_half);
+    case LBM_FP64: return refine_kernels<double>(h, k, stage, a_half);
+    case LBM_FP32: return refine_kernels<float>(h, k, stage, a_half);
+    case LBM_FP16_SHIFTED: return refine_kernels<__half>(h, k, stage, a_half);
+    case LBM_BF16_SHIFTED: return refine_kernels<__nv_bfloat16>(h, k, stage, a_half);
     }
     return cudaErrorInvalidValue;
 }
 
-static int init_line_moments(lbm_ctx *h)
+// Interface moments at t = 0 of the pair (k - 1, k), k >= 1
+static int init_pair_moments(lbm_ctx *h, int k)
 {
-    cudaError_t e = refine_stage(h, 3);
+    cudaError_t e = refine_stage(h, k, 3);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "interface moments: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
 
-// Enqueue n steps (single level, or coarse steps of the two-level grid).
-static int enqueue_steps(lbm_ctx *h, StepParams &p, StepParams &pf, int64_t n)
+// After level k's state was set: refresh the interface moments it is the parent of
+static int refresh_after_set(lbm_ctx *h, int k)
+{
+    return k < (int)h->levels.size() ? init_pair_moments(h, k + 1) : LBM_OK;
+}
+
+// One step of level k (Sec. II.B applied level by level): the interface
+// moments of its child at t + 1 from the pre-step field, its own update, then
+// two steps of the child with the child's ring refilled at t + 1/2 and t + 1,
+// and the covered ring of level k rebuilt from the child at t + 1/2.
+static cudaError_t advance_level(lbm_ctx *h, std::vector<StepParams> &params, int k, int64_t step)
+{
+    const bool child = k < (int)h->levels.size();
+    cudaError_t e = cudaSuccess;
+    if (child) e = refine_stage(h, k + 1, 0);
+    GridRef g = level_grid(h, k);
+    params[k].step = step;
+    if (e == cudaSuccess) e = launch_update(h, params[k], g.f[*g.cur], g.f[1 - *g.cur]);
+    if (e != cudaSuccess) return e;
+    *g.cur = 1 - *g.cur;
+    if (!child) return cudaSuccess;
+    e = advance_level(h, params, k + 1, 2 * step);
+    if (e == cudaSuccess) e = refine_stage(h, k + 1, 1, 1);
+    if (e == cudaSuccess) e = advance_level(h, params, k + 1, 2 * step + 1);
+    if (e == cudaSuccess) e = refine_stage(h, k + 1, 1, 0);
+    if (e == cudaSuccess) e = refine_stage(h, k + 1, 2);
+    FineLevel *F = fine_level(h, k + 1);
+    F->mcur = 1 - F->mcur;
+    return e;
+}
+
+// Enqueue n steps of level 0 (each with all refined levels beneath it).
+static int enqueue_steps(lbm_ctx *h, std::vector<StepParams> &params, int64_t n)
 {
     for (int64_t t = 0; t < n; ++t) {
-        p.step = h->step;
-        cudaError_t e = cudaSuccess;
-        if (h->fine) {
-            // one coarse step of the two-level grid (Sec. II.B):
-            // coarse line moments, coarse step, fine step, ring at t + 1/2,
-            // fine step, ring at t + 1, covered coarse ring from the fine grid
-            FineLevel *F = h->fine;
-            e = refine_stage(h, 0);
-            if (e == cudaSuccess) e = launch_update(h, p, h->f[h->cur], h->f[1 - h->cur]);
-            if (e == cudaSuccess) {
-                h->cur = 1 - h->cur;
-                pf.step = 2 * h->step;
-                e = launch_update(h, pf, F->f[F->cur], F->f[1 - F->cur]);
-            }
-            if (e == cudaSuccess) {
-                F->cur = 1 - F->cur;
-                e = refine_stage(h, 1, 1);
-            }
-            if (e == cudaSuccess) {
-                pf.step = 2 * h->step + 1;
-                e = launch_update(h, pf, F->f[F->cur], F->f[1 - F->cur]);
-            }
-            if (e == cudaSuccess) {
-                F->cur = 1 - F->cur;
-                e = refine_stage(h, 1, 0);
-            }
-            if (e == cudaSuccess) e = refine_stage(h, 2);
-            F->mcur = 1 - F->mcur;
-        } else {
-            e = launch_update(h, p, h->f[h->cur], h->f[1 - h->cur]);
-            h->cur = 1 - h->cur;
-        }
+        const cudaError_t e = advance_level(h, params, 0, h->step);
         if (e != cudaSuccess) return fail(h, LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
         h->step += 1;
     }
     return LBM_OK;
 }
 
+// Lattice parities of all levels and interface-moment buffers (the state a
+// captured pair of steps depends on)
+static uint64_t parity_signature(const lbm_ctx *h)
+{
+    uint64_t sig = (uint64_t)h->cur;
+    int bit = 1;
+    for (const FineLevel *F : h->levels) {
+        sig |= (uint64_t)F->cur << bit++;
+        sig |= (uint64_t)F->mcur << bit++;
+    }
+    return sig;
+}
+
 // Capture two steps into a graph for the current configuration and parity.
 // The host-side counters advanced by the capture are restored: the captured
 // work runs only when the graph is launched.
-static int capture_pair(lbm_ctx *h, StepParams &p, StepParams &pf)
+static int capture_pair(lbm_ctx *h, std::vector<StepParams> &params)
 {
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
     }
-    const int cur = h->cur, fcur = h->fine ? h->fine->cur : 0, mcur = h->fine ? h->fine->mcur : 0;
+    const int cur = h->cur;
+    std::vector<int> fcur, mcur;
+    for (FineLevel *F : h->levels) {
+        fcur.push_back(F->cur);
+        mcur.push_back(F->mcur);
+    }
+    const uint64_t sig = parity_signature(h);
     const int64_t step = h->step, launches = h->launches;
     cudaGraph_t g = nullptr;
     CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_steps(h, p, pf, 2);
+    int rc = enqueue_steps(h, params, 2);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     const int64_t per_pair = h->launches - launches;
     h->cur = cur;
     h->step = step;
     h->launches = launches;
-    if (h->fine) {
-        h->fine->cur = fcur;
-        h->fine->mcur = mcur;
+    for (size_t k = 0; k < h->levels.size(); ++k) {
+        h->levels[k]->cur = fcur[k];
+        h->levels[k]->mcur = mcur[k];
     }
     if (rc != LBM_OK || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -982,8 +1008,7 @@ static int capture_pair(lbm_ctx *h, StepParams &p, StepParams &pf)
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "instantiating steps: %s", cudaGetErrorString(e));
     h->graph_version = h->cfg_version;
-    h->graph_cur = cur;
-    h->graph_mcur = mcur;
+    h->graph_sig = sig;
     h->graph_launches = per_pair;
     return LBM_OK;
 }
@@ -993,18 +1018,17 @@ extern "C" int lbm_step(lbm_handle h, int64_t n)
     CHECK_HANDLE(h);
     if (n < 0) return fail(h, LBM_EINVAL, "n = %lld < 0", (long long)n);
     if (n == 0) return LBM_OK;
-    StepParams p;
-    int rc = build_params(h, p);
+    std::vector<StepParams> params((size_t)nlevels(h));
+    int rc = build_params(h, params[0]);
     if (rc != LBM_OK) return rc;
-    StepParams pf;
-    if (h->fine) fine_params(h, pf);
+    for (int k = 1; k < nlevels(h); ++k) fine_params(h, k, params[(size_t)k]);
     // Without inlet noise every step of a pair has the same parameters, so
     // pairs of steps are replayed from a captured graph (needs a stream other
-    // than the legacy default one).
+    // than the legacy default one).  Every refined level returns to the same
+    // lattice parity after two coarse steps.
     if (h->stream && h->noise_amp == 0.0 && n >= 2) {
-        const int mcur = h->fine ? h->fine->mcur : 0;
-        if (!h->graph || h->graph_version != h->cfg_version || h->graph_cur != h->cur || h->graph_mcur != mcur) {
-            rc = capture_pair(h, p, pf);
+        if (!h->graph || h->graph_version != h->cfg_version || h->graph_sig != parity_signature(h)) {
+            rc = capture_pair(h, params);
             if (rc != LBM_OK) return rc;
         }
         for (int64_t k = 0; k < n / 2; ++k) {
@@ -1015,37 +1039,40 @@ extern "C" int lbm_step(lbm_handle h, int64_t n)
         h->launches += h->graph_launches * (n / 2);
         n -= 2 * (n / 2);
     }
-    return enqueue_steps(h, p, pf, n);
+    return enqueue_steps(h, params, n);
 }
 
 // ---------------------------------------------------------------------------
-// Two-level grid
+// Refined levels
 // ---------------------------------------------------------------------------
 extern "C" int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const int extent[3])
 {
     CHECK_HANDLE(h);
     h->cfg_version++;
-    if (h->fine) return fail(h, LBM_EINVAL, "the handle already has a refinement patch");
     if (h->collision != LBM_COLLISION_RR)
         return fail(h, LBM_EINVAL, "refinement patches couple rrBGK levels; select LBM_COLLISION_RR first");
     if (!origin || !extent) return fail(h, LBM_EINVAL, "origin and extent are required");
+    if (h->levels.size() >= LBM_MAX_LEVELS - 1)
+        return fail(h, LBM_EINVAL, "at most %d levels", LBM_MAX_LEVELS);
+    const int parent = nlevels(h) - 1;  // the new patch nests inside the finest level
+    const GridRef P = level_grid(h, parent);
     const bool three = h->d == 3;
     const int X0 = origin[0], Y0 = origin[1], Wc = extent[0], Hc = extent[1];
     const int Z0 = three ? origin[2] : 0, Dc = three ? extent[2] : 0;
     if (Wc < 4 || Hc < 4 || (three && Dc < 4))
-        return fail(h, LBM_EINVAL, "patch extent must be >= 4 coarse cells per axis");
-    if (X0 < 2 || Y0 < 2 || X0 + Wc > h->n[0] - 3 || Y0 + Hc > h->n[1] - 3 ||
-        (three && (Z0 < 2 || Z0 + Dc > h->n[2] - 3)))
-        return fail(h, LBM_EINVAL, "patch must keep 2 coarse cells from every face");
+        return fail(h, LBM_EINVAL, "patch extent must be >= 4 parent cells per axis");
+    if (X0 < 2 || Y0 < 2 || X0 + Wc > P.n[0] - 3 || Y0 + Hc > P.n[1] - 3 ||
+        (three && (Z0 < 2 || Z0 + Dc > P.n[2] - 3)))
+        return fail(h, LBM_EINVAL, "patch must keep 2 cells from every face of level %d", parent);
     if ((int64_t)(2 * Wc + 1) * (2 * Hc + 1) * (three ? 2 * Dc + 1 : 1) > 2147483647LL)
-        return fail(h, LBM_EINVAL, "the fine level would hold more than 2^31 - 1 cells");
+        return fail(h, LBM_EINVAL, "the new level would hold more than 2^31 - 1 cells");
     FineLevel *F = new FineLevel();
     F->n[0] = 2 * Wc + 1;
     F->n[1] = 2 * Hc + 1;
     F->n[2] = three ? 2 * Dc + 1 : 1;
     F->ncell = (int64_t)F->n[0] * F->n[1] * F->n[2];
-    F->tau = 2.0 * h->tau - 0.5;
-    F->geom = RefineGeom{X0, Y0, Wc, Hc, h->n[0], h->n[1], F->n[0], F->n[1], Z0, Dc, h->n[2], F->n[2]};
+    F->tau = 2.0 * level_tau(h, parent) - 0.5;
+    F->geom = RefineGeom{X0, Y0, Wc, Hc, P.n[0], P.n[1], F->n[0], F->n[1], Z0, Dc, P.n[2], F->n[2]};
     const size_t bytes = (size_t)h->q * (size_t)F->ncell * h->elem;
     const size_t mbytes = three ? sizeof(double) * 10 * (size_t)box3_entries(F->geom)
                                 : sizeof(double) * 6 * (size_t)line_count(F->geom);
@@ -1053,7 +1080,6 @@ extern "C" int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const
     for (int k = 0; k < 2 && ok; ++k)
         ok = cudaMalloc(&F->f[k], bytes) == cudaSuccess && cudaMalloc(&F->M[k], mbytes) == cudaSuccess &&
              cudaMemsetAsync(F->f[k], 0, bytes, h->stream) == cudaSuccess;
-    h->fine = F;
     if (!ok) {
         cudaGetLastError();
         for (int k = 0; k < 2; ++k) {
@@ -1061,26 +1087,21 @@ extern "C" int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const
             if (F->M[k]) cudaFree(F->M[k]);
         }
         delete F;
-        h->fine = nullptr;
-        return fail(h, LBM_ENOMEM, "allocating the fine level failed");
+        return fail(h, LBM_ENOMEM, "allocating level %d failed", parent + 1);
     }
-    int rc = upload_fine_mask(h);
-    if (rc == LBM_OK) rc = upload_coarse_mask(h);
-    if (rc == LBM_OK) rc = init_line_moments(h);
+    h->levels.push_back(F);
+    const int k = parent + 1;
+    int rc = upload_level_mask(h, k);
+    if (rc == LBM_OK) rc = upload_level_mask(h, parent);
+    if (rc == LBM_OK) rc = init_pair_moments(h, k);
     return rc;
 }
 
 static int level_ref(lbm_ctx *h, int level, GridRef &g)
 {
-    if (level == 0) {
-        g = coarse_ref(h);
-        return LBM_OK;
-    }
-    if (level == 1 && h->fine) {
-        g = fine_ref(h);
-        return LBM_OK;
-    }
-    return fail(h, LBM_EINVAL, "no level %d", level);
+    if (level < 0 || level >= nlevels(h)) return fail(h, LBM_EINVAL, "no level %d", level);
+    g = level_grid(h, level);
+    return LBM_OK;
 }
 
 extern "C" int lbm_force(lbm_handle h, int level, double F[3])
@@ -1116,7 +1137,7 @@ extern "C" int lbm_level_info(lbm_handle h, int level, int extents[3], double *t
     if (rc != LBM_OK) return rc;
     if (extents)
         for (int a = 0; a < 3; ++a) extents[a] = g.n[a];
-    if (tau) *tau = level == 0 ? h->tau : h->fine->tau;
+    if (tau) *tau = level_tau(h, level);
     return LBM_OK;
 }
 
@@ -1128,7 +1149,7 @@ extern "C" int lbm_set_geometry_level(lbm_handle h, int level, const uint8_t *ce
     GridRef g;
     int rc = level_ref(h, level, g);
     if (rc != LBM_OK) return rc;
-    FineLevel *F = h->fine;
+    FineLevel *F = fine_level(h, level);
     if (cell_type) {
         rc = check_cell_types(h, cell_type, F->ncell);
         if (rc != LBM_OK) return rc;
@@ -1136,7 +1157,7 @@ extern "C" int lbm_set_geometry_level(lbm_handle h, int level, const uint8_t *ce
     } else {
         F->user_mask.clear();
     }
-    return upload_fine_mask(h);
+    return upload_level_mask(h, level);
 }
 
 extern "C" int lbm_set_state_level(lbm_handle h, int level, const double *rho, const double *u)
@@ -1147,7 +1168,8 @@ extern "C" int lbm_set_state_level(lbm_handle h, int level, const double *rho, c
     int rc = level_ref(h, level, g);
     if (rc != LBM_OK) return rc;
     h->step = 0;
-    return set_state_grid(h, g, rho, u);
+    rc = set_state_grid(h, g, rho, u);
+    return rc == LBM_OK ? refresh_after_set(h, level) : rc;
 }
 
 extern "C" int lbm_set_populations_level(lbm_handle h, int level, const double *f)
@@ -1158,7 +1180,8 @@ extern "C" int lbm_set_populations_level(lbm_handle h, int level, const double *
     int rc = level_ref(h, level, g);
     if (rc != LBM_OK) return rc;
     h->step = 0;
-    return set_pops_grid(h, g, f);
+    rc = set_pops_grid(h, g, f);
+    return rc == LBM_OK ? refresh_after_set(h, level) : rc;
 }
 
 extern "C" int lbm_get_populations_level(lbm_handle h, int level, double *f)
@@ -1208,7 +1231,7 @@ extern "C" int lbm_set_collision(lbm_handle h, int model)
     h->cfg_version++;
     if (model != LBM_COLLISION_RR && model != LBM_COLLISION_BGK)
         return fail(h, LBM_EINVAL, "collision model %d is not LBM_COLLISION_RR or LBM_COLLISION_BGK", model);
-    if (model == LBM_COLLISION_BGK && h->fine)
+    if (model == LBM_COLLISION_BGK && !h->levels.empty())
         return fail(h, LBM_EINVAL, "plain BGK is not available with a refinement patch");
     h->collision = model;
     return LBM_OK;

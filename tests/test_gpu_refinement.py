@@ -210,3 +210,93 @@ def test_two_level_3d_uniform_stream_exact():
     lbm.lbm_moments_level(s.h, 1, rf, uf, None)
     assert np.abs(uf - np.array(U)).max() < 1e-15 and np.abs(rf - 1).max() < 1e-15
     s.close()
+
+
+def _nested_case(lattice):
+    """Three levels: coarse box with inflow / outflow / sponge, two nested
+    patches (each inside the previous one), a solid on the finest level;
+    smooth initial state on every level (positions in coarse units)."""
+    from cases import Case
+    if lattice == oracle.D2Q9:
+        n, patches = (48, 40, 1), [((8, 7), (26, 22)), ((10, 9), (24, 20))]
+    else:
+        n, patches = (28, 24, 22), [((5, 5, 4), (14, 12, 12)), ((6, 5, 5), (12, 10, 10))]
+    d = 2 if lattice == oracle.D2Q9 else 3
+    c = Case("nested", lattice, n, 0.58)
+    U = 0.04
+    c.faces = {0: (VELOCITY, (U, 0, 0), None), 1: (oracle.OUTFLOW, (0, 0, 0), None)}
+    c.sponges = {1: (5, 0.3)}
+    c.rho_ref, c.u_ref = 1.0, (U, 0.0, 0.0)
+
+    def fields(pos):
+        X, Y = pos[:, 0], pos[:, 1]
+        Z = pos[:, 2] if d == 3 else 0.0 * X
+        rho = 1.0 + 1e-3 * np.exp(-((X - 20) ** 2 + (Y - 18) ** 2 + (Z - 11) ** 2 * (d == 3)) / 30.0)
+        u = np.zeros((len(X), 3))
+        u[:, 0] = U + 0.01 * np.sin(0.3 * Y)
+        u[:, 1] = 0.008 * np.cos(0.25 * X)
+        if d == 3:
+            u[:, 2] = 0.005 * np.sin(0.2 * Y + 0.1 * X)
+        return rho, u
+
+    def positions(shape, origin, scale):
+        idx = np.stack(np.meshgrid(*[np.arange(v) for v in reversed(shape[:d])], indexing="ij"), -1)
+        idx = idx.reshape(-1, d)[:, ::-1].astype(float)
+        pos = np.zeros((len(idx), 3))
+        pos[:, :d] = np.asarray(origin[:d]) + idx * scale
+        return pos
+
+    c.rho0, c.u0 = fields(positions(n, (0, 0, 0), 1.0))
+    states, origin, scale, shape = [], np.zeros(3), 1.0, n
+    for o, e in patches:
+        origin = origin + np.array(list(o) + [0] * (3 - len(o)), float) * scale
+        scale /= 2
+        shape = tuple(2 * v + 1 for v in e)
+        states.append(fields(positions(shape, origin, scale)))
+    nf = shape
+    if d == 2:
+        j, i = np.meshgrid(np.arange(nf[1]), np.arange(nf[0]), indexing="ij")
+        solid = ((i - nf[0] // 2) ** 2 + (j - nf[1] // 2) ** 2 <= 9).astype(np.uint8).reshape(-1)
+    else:
+        k, j, i = np.meshgrid(np.arange(nf[2]), np.arange(nf[1]), np.arange(nf[0]), indexing="ij")
+        solid = ((i - nf[0] // 2) ** 2 + (j - nf[1] // 2) ** 2 + (k - nf[2] // 2) ** 2 <= 4).astype(np.uint8).reshape(-1)
+    return c, patches, states, solid
+
+
+@pytest.mark.parametrize("lattice", [oracle.D2Q9, oracle.D3Q19])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
+def test_three_nested_levels_parity(lattice, prec, tol):
+    """Three levels (two nested patches, a solid on the finest) against the
+    oracle's recursive MultiLevel, every level, wall force on the finest."""
+    from cases import to_gpu
+    from paper_1710_02065_gb300 import lbm
+    c, patches, states, solid = _nested_case(lattice)
+    P, _ = to_oracle(c)
+    M = oracle.MultiLevel(P, patches)
+    M.set_solid(2, solid)
+    M.init([(c.rho0, c.u0)] + states)
+    s = to_gpu(c, prec)
+    for o, e in patches:
+        lbm.lbm_add_refinement_patch(s.h, tuple(o) + (0,) * (3 - len(o)), tuple(e) + (1,) * (3 - len(e)))
+    lbm.lbm_set_geometry_level(s.h, 2, solid)
+    for k in (2, 1):
+        lbm.lbm_set_state_level(s.h, k, *states[k - 1])
+    lbm.lbm_set_state(s.h, c.rho0, c.u0)
+    for k in range(3):
+        ext, tau = lbm.lbm_level_info(s.h, k)
+        assert ext[:2] == tuple(M.P[k].n[:2]) and abs(tau - M.P[k].tau) < 1e-15
+    steps = 6
+    M.run(steps)
+    s.step(steps)
+    for k in range(3):
+        r_ref, u_ref, _ = M.P[k].moments(M.f[k])
+        n = M.P[k].ncell
+        r, u = np.zeros(n), np.zeros((n, 3))
+        lbm.lbm_moments_level(s.h, k, r, u, None)
+        live = M.P[k].solid == 0 if M.P[k].solid is not None else np.ones(n, bool)
+        assert _normwise(r[live], r_ref[live]) <= tol, k
+        assert _normwise(u[live], u_ref[live]) <= tol, k
+    F = lbm.lbm_force(s.h, 2)
+    F_ref = M.P[2].wall_force(M.f[2])
+    assert np.abs(F - F_ref).max() <= tol * np.abs(F_ref).max() * 10
+    s.close()
