@@ -31,7 +31,8 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-D2Q9, D3Q19 = 0, 1
+D2Q9, D3Q19, D3Q27 = 0, 1, 2
+_Q = {D2Q9: 9, D3Q19: 19, D3Q27: 27}
 PERIODIC, VELOCITY, OUTFLOW, FREESLIP, PRESSURE = 0, 1, 2, 3, 4
 RR, BGK = 0, 1  # collision models
 CS2 = 1.0 / 3.0
@@ -131,21 +132,21 @@ def _dp(a: np.ndarray):
 
 
 def lattice(which: int):
-    """(d, q, xi[q,3] int, w[q], opp[q]) of D2Q9 (0) or D3Q19 (1)."""
+    """(d, q, xi[q,3] int, w[q], opp[q]) of D2Q9 (0), D3Q19 (1) or D3Q27 (2)."""
     d, q = C.c_int(), C.c_int()
-    xi = np.zeros(19 * 3, dtype=np.int32)
-    w = np.zeros(19)
-    opp = np.zeros(19, dtype=np.int32)
+    xi = np.zeros(27 * 3, dtype=np.int32)
+    w = np.zeros(27)
+    opp = np.zeros(27, dtype=np.int32)
     rc = lib().orc_lattice(which, C.byref(d), C.byref(q), xi.ctypes.data_as(C.POINTER(C.c_int)),
                            _dp(w), opp.ctypes.data_as(C.POINTER(C.c_int)))
     assert rc == 0
     q = q.value
-    return d.value, q, xi.reshape(19, 3)[:q].copy(), w[:q].copy(), opp[:q].copy()
+    return d.value, q, xi.reshape(27, 3)[:q].copy(), w[:q].copy(), opp[:q].copy()
 
 
 def feqH(which: int, rho: float, u) -> np.ndarray:
     """Hermite-regularized equilibrium, Eq. eqH (order 3, lattice-supported terms)."""
-    q = 9 if which == D2Q9 else 19
+    q = _Q[which]
     out = np.zeros(q)
     lib().orc_feqH(which, float(rho), _dp(np.ascontiguousarray(u, dtype=np.float64)), _dp(out))
     return out
@@ -153,7 +154,7 @@ def feqH(which: int, rho: float, u) -> np.ndarray:
 
 def fneqH(which: int, u, pi_neq) -> np.ndarray:
     """Hermite-regularized off-equilibrium part, Eq. neqH with Eq. recursive2."""
-    q = 9 if which == D2Q9 else 19
+    q = _Q[which]
     out = np.zeros(q)
     pn = np.ascontiguousarray(np.asarray(pi_neq, dtype=np.float64).reshape(9))
     lib().orc_fneqH(which, _dp(np.ascontiguousarray(u, dtype=np.float64)), _dp(pn), _dp(out))
@@ -193,7 +194,7 @@ class Problem:
         if lattice == D2Q9:
             n[2] = 1
         self.n = tuple(int(v) for v in n)
-        self.q = 9 if lattice == D2Q9 else 19
+        self.q = _Q[lattice]
         self.tau = float(tau)
         self.face_kind = [PERIODIC] * 6
         self.u_face = [[0.0, 0.0, 0.0] for _ in range(6)]

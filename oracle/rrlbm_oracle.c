@@ -77,11 +77,13 @@
 /* paper only says they are specific to the lattice, Eq. truncatedEq).       */
 /* ------------------------------------------------------------------------ */
 
+#define QMAX 27 /* largest lattice: D3Q27 */
+
 typedef struct {
     int d, q;
-    int xi[19][3];
-    double w[19];
-    int opp[19];
+    int xi[QMAX][3];
+    double w[QMAX];
+    int opp[QMAX];
 } lattice_t;
 
 static void build_lattice(int which, lattice_t *L)
@@ -93,15 +95,23 @@ static void build_lattice(int which, lattice_t *L)
     static const int d3q19_half[9][3] = {
         {1, 0, 0}, {0, 1, 0}, {0, 0, 1},
         {1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1}};
+    /* D3Q27: the D3Q19 set plus the eight corners (tensor product of D1Q3) */
+    static const int d3q27_half[13][3] = {
+        {1, 0, 0}, {0, 1, 0}, {0, 0, 1},
+        {1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1}, {0, 1, 1}, {0, 1, -1},
+        {1, 1, 1}, {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
     const int (*half)[3];
     int h;
-    double w0, w1, w2;
+    double w0, w1, w2, w3 = 0.0;
     if (which == 0) {
         L->d = 2; L->q = 9; half = d2q9_half; h = 4;
         w0 = 4.0 / 9.0; w1 = 1.0 / 9.0; w2 = 1.0 / 36.0;
-    } else {
+    } else if (which == 1) {
         L->d = 3; L->q = 19; half = d3q19_half; h = 9;
         w0 = 1.0 / 3.0; w1 = 1.0 / 18.0; w2 = 1.0 / 36.0;
+    } else {
+        L->d = 3; L->q = 27; half = d3q27_half; h = 13;
+        w0 = 8.0 / 27.0; w1 = 2.0 / 27.0; w2 = 1.0 / 54.0; w3 = 1.0 / 216.0;
     }
     memset(L->xi, 0, sizeof L->xi);
     for (int i = 0; i < h; ++i)
@@ -112,7 +122,7 @@ static void build_lattice(int which, lattice_t *L)
     for (int i = 0; i < L->q; ++i) {
         int n2 = L->xi[i][0] * L->xi[i][0] + L->xi[i][1] * L->xi[i][1] +
                  L->xi[i][2] * L->xi[i][2];
-        L->w[i] = n2 == 0 ? w0 : (n2 == 1 ? w1 : w2);
+        L->w[i] = n2 == 0 ? w0 : (n2 == 1 ? w1 : (n2 == 2 ? w2 : w3));
         for (int k = 0; k < L->q; ++k)
             if (L->xi[k][0] == -L->xi[i][0] && L->xi[k][1] == -L->xi[i][1] &&
                 L->xi[k][2] == -L->xi[i][2])
@@ -122,8 +132,8 @@ static void build_lattice(int which, lattice_t *L)
 
 static const lattice_t *lattice(int which)
 {
-    static lattice_t lat[2];
-    static int ready[2];
+    static lattice_t lat[3];
+    static int ready[3];
     if (!ready[which]) {
         build_lattice(which, &lat[which]);
         ready[which] = 1;
@@ -161,6 +171,16 @@ static double T3(const lattice_t *L, int i, double a[3][3][3])
     if (L->d == 2) {
         return (H3(L, i, X, X, Y) * a[X][X][Y] + H3(L, i, X, Y, Y) * a[X][Y][Y]) /
                (2.0 * cs6);
+    }
+    if (L->q == 27) {
+        /* D3Q27 supports the full third order except H_aaa (xi^3 = xi on
+         * {-1, 0, 1}): the six H_aab with multiplicity 3 and H_xyz with
+         * multiplicity 6 in the contraction H3 : a3 / (3! c_s^6); all are
+         * orthogonal on this tensor-product lattice with the continuous norms */
+        static const int A[6][3] = {{X, X, Y}, {X, X, Z}, {Y, Y, X}, {Y, Y, Z}, {Z, Z, X}, {Z, Z, Y}};
+        double s = 0.0;
+        for (int k = 0; k < 6; ++k) s += H3(L, i, A[k][0], A[k][1], A[k][2]) * a[A[k][0]][A[k][1]][A[k][2]];
+        return s / (2.0 * cs6) + H3(L, i, X, Y, Z) * a[X][Y][Z] / cs6;
     }
     /* pairs (p, q): (xxy, yzz), (xzz, xyy), (yyz, xxz) */
     static const int P[3][2][3] = {
@@ -254,11 +274,11 @@ static void collide(const lattice_t *L, const double *f, double tau, double chi,
                     double rho_ref, const double u_ref[3], const double g[3], double *out)
 {
     double rho, j[3], Pi[3][3], u[3], Pn[3][3];
-    double feq[19], fneq[19];
+    double feq[QMAX], fneq[QMAX];
     moments(L, f, &rho, j, Pi);
     if (chi > 0.0) {
         double rs = (rho + 0.5 * chi * rho_ref) / (1.0 + 0.5 * chi);
-        double fref[19];
+        double fref[QMAX];
         for (int a = 0; a < 3; ++a)
             u[a] = (j[a] + 0.5 * chi * rho_ref * u_ref[a]) / (1.0 + 0.5 * chi) / rs;
         pi_neq(L->d, rs, u, Pi, Pn);
@@ -313,7 +333,7 @@ static void fneq_second(const lattice_t *L, double Pn[3][3], double *out)
 static void collide_bgk(const lattice_t *L, const double *f, double tau, double chi, double rho_ref,
                         const double u_ref[3], const double g[3], double *out)
 {
-    double rho, j[3], Pi[3][3], u[3], feq[19];
+    double rho, j[3], Pi[3][3], u[3], feq[QMAX];
     moments(L, f, &rho, j, Pi);
     double rs = rho;
     if (chi > 0.0) {
@@ -325,7 +345,7 @@ static void collide_bgk(const lattice_t *L, const double *f, double tau, double 
     feq_quadratic(L, rs, u, feq);
     for (int i = 0; i < L->q; ++i) out[i] = f[i] - (f[i] - feq[i]) / tau;
     if (chi > 0.0) {
-        double fref[19];
+        double fref[QMAX];
         feq_quadratic(L, rho_ref, u_ref, fref);
         for (int i = 0; i < L->q; ++i) out[i] += chi * (fref[i] - feq[i]);
     }
@@ -343,7 +363,7 @@ static void collide_bgk(const lattice_t *L, const double *f, double tau, double 
 static void rebuilt_node(int collision, double tau, const lattice_t *L, double rho, const double u[3],
                          double Pn[3][3], double *out)
 {
-    double feq[19], fneq[19];
+    double feq[QMAX], fneq[QMAX];
     if (collision == 1) {
         feq_quadratic(L, rho, u, feq);
         fneq_second(L, Pn, fneq);
@@ -378,7 +398,7 @@ double orc_u01(uint64_t counter)
 enum { BC_PERIODIC = 0, BC_VELOCITY = 1, BC_OUTFLOW = 2, BC_FREESLIP = 3, BC_PRESSURE = 4 };
 
 typedef struct {
-    int lattice;             /* 0 = D2Q9, 1 = D3Q19 */
+    int lattice;             /* 0 = D2Q9, 1 = D3Q19, 2 = D3Q27 */
     int n[3];                /* extents; n[2] = 1 for D2Q9 */
     double tau;
     int face_kind[6];        /* -x, +x, -y, +y, -z, +z */
@@ -509,7 +529,7 @@ void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int6
     int64_t scell = s[0] + (int64_t)P->n[0] * (s[1] + (int64_t)P->n[1] * s[2]);
 
     /* Streaming: pull f_i(s) = f*_i(s - xi_i), periodic wrap, bounce-back (R8). */
-    double f[19];
+    double f[QMAX];
     for (int i = 0; i < L->q; ++i) {
         int src[3];
         for (int a = 0; a < 3; ++a) {
@@ -584,7 +604,7 @@ int orc_step(const orc_problem *P, const double *fin, double *fout, int64_t step
 {
     const lattice_t *L = lattice(P->lattice);
     const int64_t N = ncell(P);
-    double out[19];
+    double out[QMAX];
     for (int64_t cell = 0; cell < N; ++cell) {
         orc_update_cell(P, fin, cell, step, out);
         for (int i = 0; i < L->q; ++i) fout[(int64_t)i * N + cell] = out[i];
@@ -613,7 +633,7 @@ int orc_run(const orc_problem *P, double *f, double *work, int64_t step0, int64_
 
 int orc_lattice(int which, int *d, int *q, int *xi /* q*3 */, double *w, int *opp)
 {
-    if (which != 0 && which != 1) return -1;
+    if (which < 0 || which > 2) return -1;
     const lattice_t *L = lattice(which);
     *d = L->d;
     *q = L->q;
@@ -652,7 +672,7 @@ void orc_field_moments(const orc_problem *P, const double *fin, double *rho, dou
     const lattice_t *L = lattice(P->lattice);
     const int64_t N = ncell(P);
     for (int64_t cell = 0; cell < N; ++cell) {
-        double f[19], r, j[3], Pi[3][3], v[3], Pn[3][3];
+        double f[QMAX], r, j[3], Pi[3][3], v[3], Pn[3][3];
         for (int i = 0; i < L->q; ++i) f[i] = fin[(int64_t)i * N + cell];
         moments(L, f, &r, j, Pi);
         for (int a = 0; a < 3; ++a) v[a] = j[a] / r;
@@ -677,7 +697,7 @@ void orc_init_equilibrium(const orc_problem *P, const double *rho, const double 
     const lattice_t *L = lattice(P->lattice);
     const int64_t N = ncell(P);
     for (int64_t cell = 0; cell < N; ++cell) {
-        double out[19];
+        double out[QMAX];
         feqH(L, rho[cell], u + 3 * cell, out);
         for (int i = 0; i < L->q; ++i) f[(int64_t)i * N + cell] = out[i];
     }
@@ -763,7 +783,7 @@ static void streamed_moments(const orc_problem *P, const double *fin, int x, int
     const lattice_t *L = lattice(P->lattice);
     const int64_t N = ncell(P);
     const int64_t cell = x + (int64_t)P->n[0] * y;
-    double f[19], rho, j[3], Pi[3][3], u[3], Pn[3][3];
+    double f[QMAX], rho, j[3], Pi[3][3], u[3], Pn[3][3];
     for (int i = 0; i < L->q; ++i) {
         int sx = x - L->xi[i][0], sy = y - L->xi[i][1];
         sx = ((sx % P->n[0]) + P->n[0]) % P->n[0];
@@ -786,7 +806,7 @@ static void rebuild_post(const lattice_t *L, const double m[6], double alpha, do
 {
     double u[3] = {m[1], m[2], 0.0};
     double Pn[3][3] = {{alpha * m[3], alpha * m[4], 0}, {alpha * m[4], alpha * m[5], 0}, {0, 0, 0}};
-    double feq[19], fneq[19];
+    double feq[QMAX], fneq[QMAX];
     feqH(L, m[0], u, feq);
     fneqH(L, u, Pn, fneq);
     for (int i = 0; i < L->q; ++i) out[i] = feq[i] + (1.0 - 1.0 / tau) * fneq[i];
@@ -845,7 +865,7 @@ static void fill_fine_ring(const orc_problem *Pc, const orc_problem *Pf, const o
                 mix(M0, M1, a, nxc, xc, ya + 2, t3);
                 for (int k = 0; k < 6; ++k) m[k] = (-t0[k] + 9.0 * t1[k] + 9.0 * t2[k] - t3[k]) / 16.0;
             }
-            double out[19];
+            double out[QMAX];
             rebuild_post(L, m, alpha, tau_f, out);
             int64_t cell = i + (int64_t)nfx * j;
             for (int q = 0; q < L->q; ++q) ff[(int64_t)q * Nf + cell] = out[q];
@@ -874,7 +894,7 @@ static void restrict_to_coarse(const orc_problem *Pc, const orc_problem *Pf, con
                     for (int c = 3; c < 6; ++c) mc[c] += wgt * m[c];
                     if (k == 0 && l == 0) { mc[0] = m[0]; mc[1] = m[1]; mc[2] = m[2]; }
                 }
-            double out[19];
+            double out[QMAX];
             rebuild_post(L, mc, alpha, Pc->tau, out);
             int64_t cell = x + (int64_t)Pc->n[0] * y;
             for (int q = 0; q < L->q; ++q) fc[(int64_t)q * Nc + cell] = out[q];
@@ -890,7 +910,7 @@ void orc_refined_init_moments(const orc_problem *Pc, const orc_patch *G, const d
     for (int y = G->Y0 - 1; y <= G->Y0 + G->Hc + 1; ++y)
         for (int x = G->X0 - 1; x <= G->X0 + G->Wc + 1; ++x) {
             int64_t cell = x + (int64_t)Pc->n[0] * y;
-            double f[19], rho, j[3], Pi[3][3], u[3], Pn[3][3];
+            double f[QMAX], rho, j[3], Pi[3][3], u[3], Pn[3][3];
             for (int i = 0; i < L->q; ++i) f[i] = fc[(int64_t)i * N + cell];
             moments(L, f, &rho, j, Pi);
             for (int a = 0; a < 3; ++a) u[a] = j[a] / rho;
@@ -980,7 +1000,7 @@ static void streamed_moments3(const orc_problem *P, const double *fin, int x, in
     const int64_t N = ncell(P);
     const int64_t nx = P->n[0], ny = P->n[1], nz = P->n[2];
     const int64_t cell = x + nx * (y + ny * (int64_t)z);
-    double f[19], rho, j[3], Pi[3][3], u[3], Pn[3][3];
+    double f[QMAX], rho, j[3], Pi[3][3], u[3], Pn[3][3];
     for (int i = 0; i < L->q; ++i) {
         int64_t sx = ((x - L->xi[i][0]) % nx + nx) % nx;
         int64_t sy = ((y - L->xi[i][1]) % ny + ny) % ny;
@@ -1004,7 +1024,7 @@ static void rebuild_post3(const lattice_t *L, const double m[10], double alpha, 
     double Pn[3][3] = {{alpha * m[4], alpha * m[5], alpha * m[6]},
                        {alpha * m[5], alpha * m[7], alpha * m[8]},
                        {alpha * m[6], alpha * m[8], alpha * m[9]}};
-    double feq[19], fneq[19];
+    double feq[QMAX], fneq[QMAX];
     feqH(L, m[0], u, feq);
     fneqH(L, u, Pn, fneq);
     for (int i = 0; i < L->q; ++i) out[i] = feq[i] + (1.0 - 1.0 / tau) * fneq[i];
@@ -1079,7 +1099,7 @@ static void fill_fine_shell3(const orc_problem *Pc, const orc_problem *Pf, const
         for (int j = 0; j < nfy; ++j)
             for (int i = 0; i < nfx; ++i) {
                 if (!(i == 0 || j == 0 || k == 0 || i == nfx - 1 || j == nfy - 1 || k == nfz - 1)) continue;
-                double m[10], out[19];
+                double m[10], out[QMAX];
                 orc_refine3_interp(Pc, G, M0, M1, a, i, j, k, m);
                 rebuild_post3(L, m, alpha, Pf->tau, out);
                 const int64_t cell = i + (int64_t)nfx * (j + (int64_t)nfy * k);
@@ -1119,7 +1139,7 @@ static void restrict_to_coarse3(const orc_problem *Pc, const orc_problem *Pf, co
                                   y == G->Y0 + G->Hc - 1 || z == G->Z0 + 1 || z == G->Z0 + G->Dc - 1;
                 if (!shell) continue;
                 const int i = 2 * (x - G->X0), j = 2 * (y - G->Y0), k = 2 * (z - G->Z0);
-                double m27[270], mc[10], out[19];
+                double m27[270], mc[10], out[QMAX];
                 for (int c = 0; c < 3; ++c)
                     for (int b = 0; b < 3; ++b)
                         for (int a = 0; a < 3; ++a)
@@ -1143,7 +1163,7 @@ void orc_refined3_init_moments(const orc_problem *Pc, const orc_patch3 *G, const
             for (int x = G->X0 - 1; x <= G->X0 + G->Wc + 1; ++x) {
                 if (!on_interface_plane3(G, x, y, z)) continue;
                 const int64_t cell = x + nx * (y + ny * (int64_t)z);
-                double f[19], rho, j[3], Pi[3][3], u[3], Pn[3][3];
+                double f[QMAX], rho, j[3], Pi[3][3], u[3], Pn[3][3];
                 for (int i = 0; i < L->q; ++i) f[i] = fc[(int64_t)i * N + cell];
                 moments(L, f, &rho, j, Pi);
                 for (int a = 0; a < 3; ++a) u[a] = j[a] / rho;

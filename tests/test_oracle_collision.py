@@ -15,9 +15,10 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle import D2Q9, D3Q19, CS2
+from oracle import D2Q9, D3Q19, D3Q27, CS2
 
-LATS = [D2Q9, D3Q19]
+LATS = [D2Q9, D3Q19, D3Q27]
+Q = {D2Q9: 9, D3Q19: 19, D3Q27: 27}
 
 
 def _lat(which):
@@ -29,7 +30,7 @@ def _lat(which):
 def test_lattice_quadrature_identities(which):
     """Sum w = 1, odd moments vanish, sum w xi xi = c_s^2 I, 4th-order isotropy."""
     d, q, xi, w, opp = _lat(which)
-    assert q == (9 if which == D2Q9 else 19)
+    assert q == Q[which]
     assert abs(w.sum() - 1.0) < 1e-15
     for a in range(3):
         assert abs((w * xi[:, a]).sum()) < 1e-15
@@ -41,6 +42,12 @@ def test_lattice_quadrature_identities(which):
     for a, b, c, e in itertools.product(range(d), repeat=4):
         want = CS2 ** 2 * (dl(a, b) * dl(c, e) + dl(a, c) * dl(b, e) + dl(a, e) * dl(b, c))
         assert abs((w * xi[:, a] * xi[:, b] * xi[:, c] * xi[:, e]).sum() - want) < 1e-15
+    if which == D3Q27:
+        # the tensor-product lattice: weights factor into D1Q3 weights (2/3, 1/6, 1/6)
+        w1 = {0: 2 / 3, 1: 1 / 6, -1: 1 / 6}
+        for i in range(q):
+            v = xi[i].astype(int)
+            assert abs(w[i] - w1[v[0]] * w1[v[1]] * w1[v[2]]) < 1e-16
 
 
 @pytest.mark.parametrize("which", LATS)
@@ -52,10 +59,10 @@ def test_lattice_opposites_and_order(which):
         assert np.all(xi[opp[i]] == -xi[i])
     for i in range(1, h + 1):
         assert opp[i] == i + h
-    # all velocities distinct, unit components only, no corner velocities
+    # all velocities distinct, unit components only; corner velocities only on D3Q27
     assert len({tuple(v) for v in xi.astype(int)}) == q
     assert np.abs(xi).max() == 1
-    assert (np.abs(xi).sum(axis=1) <= 2).all()
+    assert (np.abs(xi).sum(axis=1) <= (3 if which == D3Q27 else 2)).all()
     if which == D2Q9:
         assert np.all(xi[:, 2] == 0)
 
@@ -145,7 +152,8 @@ def test_equilibrium_third_moments_match_maxwell_boltzmann(which):
     """Third moments of feqH equal those of the continuous Maxwell-Boltzmann
     distribution, int f xi_a xi_b xi_c = rho (u_a u_b u_c + c_s^2 (u_a d_bc + u_b d_ac + u_c d_ab)),
     for every combination the lattice supports (D2Q9: xxy, xyy; D3Q19: the
-    sums and differences of the pairs (xxy, yzz), (xzz, xyy), (yyz, xxz))."""
+    sums and differences of the pairs (xxy, yzz), (xzz, xyy), (yyz, xxz);
+    D3Q27: each of the six a a b and x y z on its own)."""
     d, q, xi, w, opp = _lat(which)
     rng = np.random.default_rng(7)
     dl = np.eye(3)
@@ -164,6 +172,9 @@ def test_equilibrium_third_moments_match_maxwell_boltzmann(which):
         f = oracle.feqH(which, rho, u)
         if which == D2Q9:
             for (a, b, c) in [(0, 0, 1), (0, 1, 1)]:
+                assert abs(m3(f, a, b, c) - mb(rho, u, a, b, c)) < 1e-15
+        elif which == D3Q27:
+            for (a, b, c) in [(0, 0, 1), (0, 0, 2), (1, 1, 0), (1, 1, 2), (2, 2, 0), (2, 2, 1), (0, 1, 2)]:
                 assert abs(m3(f, a, b, c) - mb(rho, u, a, b, c)) < 1e-15
         else:
             for p, qq in [((0, 0, 1), (1, 2, 2)), ((0, 2, 2), (0, 1, 1)), ((1, 1, 2), (0, 0, 2))]:
@@ -282,3 +293,20 @@ def test_circular_sponge_profile_covers_corners():
     assert P.chi(0, 0) == 0.6 and P.chi(100, 100) == 0.6  # corners
     # radially symmetric
     assert abs(P.chi(50, 50 + 36) - P.chi(50 + 36, 50)) < 1e-15
+
+
+def test_recursive_neq_third_order_special_cases_d3q27():
+    """Eq. recursive2 at n = 3 on D3Q27, every supported component on its own.
+    With u = (U, V, W) and Pi^neq whose only entry is P_yz = P_zy = P,
+    a_abc = u_a P_bc + u_b P_ac + u_c P_ab gives a_xyz = U P, a_yyz = 2 V P,
+    a_zzy = 2 W P and zero for xxy, xxz, yyx, zzx."""
+    U, V, W, P = 0.07, -0.04, 0.03, 3e-3
+    pn = np.zeros((3, 3)); pn[1, 2] = pn[2, 1] = P
+    f = oracle.fneqH(D3Q27, [U, V, W], pn)
+    want = {(0, 1, 2): U * P, (1, 1, 2): 2 * V * P, (2, 2, 1): 2 * W * P,
+            (0, 0, 1): 0.0, (0, 0, 2): 0.0, (1, 1, 0): 0.0, (2, 2, 0): 0.0}
+    for idx, val in want.items():
+        assert abs(_h3_moment(D3Q27, f, idx) - val) < 1e-17, idx
+    # the D3Q19 lattice cannot carry x y z: its H_xyz vanishes on every velocity
+    _, _, xi19, _, _ = _lat(D3Q19)
+    assert np.all(xi19[:, 0] * xi19[:, 1] * xi19[:, 2] == 0)

@@ -64,6 +64,26 @@ def test_taylor_green_3d_viscosity():
     assert abs(nu_fit / nu - 1) < 0.02, (nu_fit, nu)
 
 
+def test_taylor_green_3d_viscosity_d3q27():
+    """The same decay on the D3Q27 lattice (full third order)."""
+    n, tau = 20, 0.7
+    P = oracle.Problem(oracle.D3Q27, (n, n, n), tau)
+    rho, u = inputs.taylor_green_3d(n, 0.005)
+    f = P.equilibrium(rho, u)
+    k = 2 * math.pi / n
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    basis = (np.sin(k * x) * np.cos(k * y) * np.cos(k * z)).reshape(-1)
+    ts, amps = [], []
+    for t in range(0, 81, 20):
+        if t:
+            f = P.run(f, 20, step0=t - 20)
+        _, uu, _ = P.moments(f)
+        ts.append(t)
+        amps.append((uu[:, 0] * basis).sum() / (basis * basis).sum())
+    rate = _fit_rate(np.array(ts[1:]), np.array(amps[1:]))
+    assert abs(rate / (3 * k * k) / (CS2 * (tau - 0.5)) - 1) < 0.02
+
+
 def test_poiseuille_between_bounce_back_walls():
     """Body-force channel: u(y) = g/(2 nu) (y - 1/2)(H + 1/2 - y), walls halfway."""
     H, tau, g = 24, 0.8, 2e-6
