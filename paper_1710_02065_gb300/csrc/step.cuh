@@ -275,7 +275,7 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
 // role from coordinates, collision, store.  Shared by the single-lattice
 // kernel below and the batched multi-domain kernel.
 // ---------------------------------------------------------------------------
-template <class L, class S, class C, bool BGK = false>
+template <class L, class S, class C, bool BGK = false, bool MASK = true>
 __device__ __forceinline__ void update_cell(const StepParams &p, const char *const *in, char *const *out,
                                             int x, int y, int z)
 {
@@ -283,7 +283,8 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     const unsigned nx = p.n[0], ny = p.n[1], nz = p.n[2];
     const unsigned nxy = nx * ny;
     const unsigned cell = x + nx * y + nxy * z;
-    const uint8_t *__restrict__ solid = p.solid;
+    // MASK = false: compiled without any cell-type test (the lattice has no mask)
+    const uint8_t *__restrict__ solid = MASK ? p.solid : nullptr;
     if (solid && (solid[cell] & MASK_TYPE)) return;  // solid (1) and fixed (2) cells keep their populations
 
     // ---- boundary role and the node whose streamed populations are used
@@ -352,14 +353,14 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     }
 }
 
-// General kernel: one thread per cell, optional cell-type mask; BGK = true
-// is the plain LBM-BGK collision (Eq. standardLB).
-template <class L, class S, class C, bool BGK>
+// General kernel: one thread per cell; MASK = true reads the cell-type mask;
+// BGK = true is the plain LBM-BGK collision (Eq. standardLB).
+template <class L, class S, class C, bool BGK, bool MASK>
 __global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ StepParams p)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.n[0]) return;
-    update_cell<L, S, C, BGK>(p, p.in, p.out, x, blockIdx.y, blockIdx.z);
+    update_cell<L, S, C, BGK, MASK>(p, p.in, p.out, x, blockIdx.y, blockIdx.z);
 }
 
 // Launch wrapper: one thread per cell, blocks along x; p.bgk selects the
@@ -372,10 +373,17 @@ cudaError_t launch_stream_collide(const StepParams &p, const void *fin, void *fo
     set_bases<L, S>(q, fin, fout);
     dim3 b(block, 1, 1);
     dim3 g((p.n[0] + block - 1) / block, p.n[1], p.n[2]);
-    if (p.bgk)
-        k_stream_collide<L, S, C, true><<<g, b, 0, st>>>(q);
-    else
-        k_stream_collide<L, S, C, false><<<g, b, 0, st>>>(q);
+    if (p.bgk) {
+        if (p.solid)
+            k_stream_collide<L, S, C, true, true><<<g, b, 0, st>>>(q);
+        else
+            k_stream_collide<L, S, C, true, false><<<g, b, 0, st>>>(q);
+    } else {
+        if (p.solid)
+            k_stream_collide<L, S, C, false, true><<<g, b, 0, st>>>(q);
+        else
+            k_stream_collide<L, S, C, false, false><<<g, b, 0, st>>>(q);
+    }
     return cudaGetLastError();
 }
 

@@ -65,12 +65,25 @@ struct VecIO<double, 2> {
     }
 };
 
-__device__ __forceinline__ float h2f(unsigned short b) { return __half2float(__ushort_as_half(b)); }
-__device__ __forceinline__ unsigned short f2h(float v) { return __half_as_ushort(__float2half_rn(v)); }
-__device__ __forceinline__ float b2f(unsigned short b) { return __uint_as_float((unsigned)b << 16); }
-__device__ __forceinline__ unsigned short f2b(float v)
+// 16-bit pairs move as one 32-bit word; the paired conversion intrinsics
+// unpack / pack (round to nearest) both halves of a word at once.
+__device__ __forceinline__ float2 unpack_h2(unsigned v)
 {
-    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    return __half22float2(*reinterpret_cast<const __half2 *>(&v));
+}
+__device__ __forceinline__ unsigned pack_h2(float a, float b)
+{
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const unsigned *>(&h);
+}
+__device__ __forceinline__ float2 unpack_b2(unsigned v)
+{
+    return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
+}
+__device__ __forceinline__ unsigned pack_b2(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const unsigned *>(&h);
 }
 
 template <>
@@ -78,39 +91,36 @@ struct VecIO<__half, 4> {
     __device__ static void ld(const __half *p, float (&o)[4])
     {
         const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
-        o[0] = h2f(v.x & 0xffffu); o[1] = h2f(v.x >> 16);
-        o[2] = h2f(v.y & 0xffffu); o[3] = h2f(v.y >> 16);
+        const float2 a = unpack_h2(v.x), b = unpack_h2(v.y);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
     }
     __device__ static void st(__half *p, const float (&o)[4])
     {
-        uint2 v;
-        v.x = (unsigned)f2h(o[0]) | ((unsigned)f2h(o[1]) << 16);
-        v.y = (unsigned)f2h(o[2]) | ((unsigned)f2h(o[3]) << 16);
-        *reinterpret_cast<uint2 *>(p) = v;
+        *reinterpret_cast<uint2 *>(p) = make_uint2(pack_h2(o[0], o[1]), pack_h2(o[2], o[3]));
     }
 };
 template <>
 struct VecIO<__half, 2> {
     __device__ static void ld(const __half *p, float (&o)[2])
     {
-        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
-        o[0] = h2f(v & 0xffffu); o[1] = h2f(v >> 16);
+        const float2 a = unpack_h2(__ldg(reinterpret_cast<const unsigned *>(p)));
+        o[0] = a.x; o[1] = a.y;
     }
     __device__ static void st(__half *p, const float (&o)[2])
     {
-        *reinterpret_cast<unsigned *>(p) = (unsigned)f2h(o[0]) | ((unsigned)f2h(o[1]) << 16);
+        *reinterpret_cast<unsigned *>(p) = pack_h2(o[0], o[1]);
     }
 };
 template <>
 struct VecIO<__nv_bfloat16, 2> {
     __device__ static void ld(const __nv_bfloat16 *p, float (&o)[2])
     {
-        const unsigned v = __ldg(reinterpret_cast<const unsigned *>(p));
-        o[0] = __uint_as_float(v << 16); o[1] = __uint_as_float(v & 0xffff0000u);
+        const float2 a = unpack_b2(__ldg(reinterpret_cast<const unsigned *>(p)));
+        o[0] = a.x; o[1] = a.y;
     }
     __device__ static void st(__nv_bfloat16 *p, const float (&o)[2])
     {
-        *reinterpret_cast<unsigned *>(p) = (unsigned)f2b(o[0]) | ((unsigned)f2b(o[1]) << 16);
+        *reinterpret_cast<unsigned *>(p) = pack_b2(o[0], o[1]);
     }
 };
 template <>
@@ -118,15 +128,12 @@ struct VecIO<__nv_bfloat16, 4> {
     __device__ static void ld(const __nv_bfloat16 *p, float (&o)[4])
     {
         const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
-        o[0] = __uint_as_float(v.x << 16); o[1] = __uint_as_float(v.x & 0xffff0000u);
-        o[2] = __uint_as_float(v.y << 16); o[3] = __uint_as_float(v.y & 0xffff0000u);
+        const float2 a = unpack_b2(v.x), b = unpack_b2(v.y);
+        o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
     }
     __device__ static void st(__nv_bfloat16 *p, const float (&o)[4])
     {
-        uint2 v;
-        v.x = (unsigned)f2b(o[0]) | ((unsigned)f2b(o[1]) << 16);
-        v.y = (unsigned)f2b(o[2]) | ((unsigned)f2b(o[3]) << 16);
-        *reinterpret_cast<uint2 *>(p) = v;
+        *reinterpret_cast<uint2 *>(p) = make_uint2(pack_b2(o[0], o[1]), pack_b2(o[2], o[3]));
     }
 };
 
