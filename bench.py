@@ -48,13 +48,13 @@ def jet_spec(nx=384, ny=256, nz=256, diameter=24.0, sponge=32, Ma=0.3, Re=1e4, c
     U = Ma * CS
     tau = 3 * U * diameter / Re + 0.5
     return dict(n=(nx, ny, nz), diameter=diameter, sponge=sponge, U=U, tau=tau, chi=chi, seed=seed,
-                noise=noise, theta=diameter / 40.0)
+                noise=noise, theta=diameter / 40.0, lattice=1)
 
 
 def configure_gpu(lbm, spec, precision, stream):
     from paper_1710_02065_gb300 import inputs
     nx, ny, nz = spec["n"]
-    s = lbm.Solver(lbm.LBM_D3Q19, spec["n"], spec["tau"], precision, Ma_ref=0.3, stream=stream)
+    s = lbm.Solver(spec.get("lattice", lbm.LBM_D3Q19), spec["n"], spec["tau"], precision, Ma_ref=0.3, stream=stream)
     prof = inputs.top_hat_profile(ny, nz, ny / 2, nz / 2, spec["diameter"] / 2, spec["U"], spec["theta"])
     lbm.lbm_set_boundary(s.h, lbm.LBM_FACE_XM, lbm.LBM_BC_VELOCITY, None, prof)
     for f in range(1, 6):
@@ -702,6 +702,15 @@ def main():
             extra[name] = {"launch": r["launch"], "mlups": r["ncell"] / (k_ms / 1e3) / 1e6,
                            "gbs": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9,
                            "frac_of_measured_hbm": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9 / peak}
+        # the same jet on D3Q27 (complete third order; 27 populations, 216 B per cell in FP32)
+        spec27 = dict(spec, lattice=lbm.LBM_D3Q27)
+        r = time_precision(lbm, torch, spec27, lbm.PRECISIONS[args.precision], max(20, args.steps // 4),
+                           args.warmup, pg, stream, tune=not args.no_tune)
+        k_ms = float(np.mean(r["per_ms"]))
+        extra["d3q27_" + args.precision] = {
+            "launch": r["launch"], "mlups": r["ncell"] / (k_ms / 1e3) / 1e6,
+            "gbs": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9,
+            "frac_of_measured_hbm": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9 / peak}
         if "fp16" in extra:
             extra["fp16_store_speedup"] = extra["fp16"]["mlups"] / (ncell / (kernel_ms / 1e3) / 1e6)
         if "bf16" in extra:

@@ -58,9 +58,13 @@ typedef struct lbm_ctx *lbm_handle;
 #define LBM_EUNSTABLE (-4) /* non-finite populations found by lbm_reduce        */
 #define LBM_EIO (-5)       /* file error in lbm_save / lbm_load                 */
 
-/* Lattices (Sec. II.A: D2Q9 in 2D, D3Q19 in 3D) */
+/* Lattices (Sec. II.A: D2Q9 in 2D, D3Q19 in 3D).  LBM_D3Q27, the tensor
+ * product of D1Q3, carries the complete third-order Hermite set (the six
+ * H_aab and H_xyz) that D3Q19 can only keep as pairs; single level, general
+ * and two-cell kernels (no refinement patches, not in the solve server). */
 #define LBM_D2Q9 0
 #define LBM_D3Q19 1
+#define LBM_D3Q27 2
 
 /* Storage precision of the populations.  FP64 computes in FP64; the others
  * compute in FP32.  The *_SHIFTED formats store f_i - w_i (rho_0 = 1). */

@@ -20,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lbm_api.cu", "step_d2q9.cu", "step_d3q19.cu", "stepvec_d2q9.cu", "stepvec_d3q19.cu",
+SOURCES = ["lbm_api.cu", "step_d2q9.cu", "step_d3q19.cu", "step_d3q27.cu", "stepvec_d2q9.cu", "stepvec_d3q19.cu",
+           "stepvec_d3q27.cu",
            "rows_d2q9.cu", "rows_d3q19.cu", "lbm_noalloc.cu", "lbm_serve.cu"]
 
 

@@ -33,7 +33,7 @@ __global__ void k_init_eq(int64_t N, const double *__restrict__ rho, const doubl
     const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (cell >= N) return;
     Coef<C> k{};
-    add_eq<C, L::D>(k, C(1), C(rho[cell] - 1.0), C(rho[cell]), C(u[3 * cell]), C(u[3 * cell + 1]),
+    add_eq<C, L::D, true, full_third_order<L>()>(k, C(1), C(rho[cell] - 1.0), C(rho[cell]), C(u[3 * cell]), C(u[3 * cell + 1]),
               L::D == 3 ? C(u[3 * cell + 2]) : C(0));
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {

@@ -12,6 +12,8 @@ cudaError_t step_d2q9(int precision, const StepParams &p, const void *fin, void 
                       cudaStream_t st);
 cudaError_t step_d3q19(int precision, const StepParams &p, const void *fin, void *fout, int block,
                        cudaStream_t st);
+cudaError_t step_d3q27(int precision, const StepParams &p, const void *fin, void *fout, int block,
+                       cudaStream_t st);
 
 }  // namespace rr
 
@@ -25,6 +27,9 @@ void rr_set_global_error(const char *msg);
 cudaError_t stepvec_d2q9(int precision, int vec, const StepParams &p, const void *fin, void *fout,
                          int block, cudaStream_t st);
 cudaError_t stepvec_d3q19(int precision, int vec, const StepParams &p, const void *fin, void *fout,
+                          int block, cudaStream_t st);
+// D3Q27: two cells per thread (four fall back to the general kernel)
+cudaError_t stepvec_d3q27(int precision, int vec, const StepParams &p, const void *fin, void *fout,
                           int block, cudaStream_t st);
 
 // Cells per thread the vectorised kernel supports for a precision (0: none)

@@ -144,6 +144,13 @@ static cudaError_t dispatch(int lattice, int prec, A... args)
         case LBM_FP16_SHIFTED: return Fn<D2Q9, __half>::run(args...);
         case LBM_BF16_SHIFTED: return Fn<D2Q9, __nv_bfloat16>::run(args...);
         }
+    } else if (lattice == LBM_D3Q27) {
+        switch (prec) {
+        case LBM_FP64: return Fn<D3Q27, double>::run(args...);
+        case LBM_FP32: return Fn<D3Q27, float>::run(args...);
+        case LBM_FP16_SHIFTED: return Fn<D3Q27, __half>::run(args...);
+        case LBM_BF16_SHIFTED: return Fn<D3Q27, __nv_bfloat16>::run(args...);
+        }
     } else {
         switch (prec) {
         case LBM_FP64: return Fn<D3Q19, double>::run(args...);
@@ -267,6 +274,8 @@ extern "C" int lbm_lattice_table(int lattice, int *q, int *d, int *xi, double *w
         table<D2Q9>(q, d, xi, w);
     else if (lattice == LBM_D3Q19)
         table<D3Q19>(q, d, xi, w);
+    else if (lattice == LBM_D3Q27)
+        table<D3Q27>(q, d, xi, w);
     else
         return fail(nullptr, LBM_EINVAL, "unknown lattice %d", lattice);
     return LBM_OK;
@@ -314,7 +323,7 @@ extern "C" int lbm_create(lbm_handle *out, int lattice, const int extents[3], do
 {
     if (!out) return fail(nullptr, LBM_EINVAL, "out is null");
     *out = nullptr;
-    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19)
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19 && lattice != LBM_D3Q27)
         return fail(nullptr, LBM_EINVAL, "unknown lattice %d", lattice);
     if (!prec_bytes(precision)) return fail(nullptr, LBM_EINVAL, "unknown precision %d", precision);
     if (!extents) return fail(nullptr, LBM_EINVAL, "extents is null");
@@ -334,7 +343,7 @@ extern "C" int lbm_create(lbm_handle *out, int lattice, const int extents[3], do
 
     lbm_ctx *h = new lbm_ctx();
     h->lattice = lattice;
-    h->q = lattice == LBM_D2Q9 ? 9 : 19;
+    h->q = lattice == LBM_D2Q9 ? 9 : (lattice == LBM_D3Q19 ? 19 : 27);
     h->d = lattice == LBM_D2Q9 ? 2 : 3;
     h->prec = precision;
     h->elem = prec_bytes(precision);
@@ -420,8 +429,10 @@ static void add_near_solid(lbm_ctx *h, std::vector<uint8_t> &m, const int n[3])
 {
     if (h->lattice == LBM_D2Q9)
         add_near_solid_bits<D2Q9>(m, n);
-    else
+    else if (h->lattice == LBM_D3Q19)
         add_near_solid_bits<D3Q19>(m, n);
+    else
+        add_near_solid_bits<D3Q27>(m, n);
 }
 
 // Upload the cell types of level k: the caller's types; on a refined level
@@ -772,16 +783,23 @@ static bool staging_wanted(const lbm_ctx *h)
 // Launch one update of a grid: the row-staged kernel where it is wanted and
 // eligible; else the vectorised kernel when there is no mask and the row
 // length allows it; else the general kernel.
+static cudaError_t step_general(lbm_ctx *h, const StepParams &p, const void *fin, void *fout, int block)
+{
+    switch (h->lattice) {
+    case LBM_D2Q9: return step_d2q9(h->prec, p, fin, fout, block, h->stream);
+    case LBM_D3Q19: return step_d3q19(h->prec, p, fin, fout, block, h->stream);
+    default: return step_d3q27(h->prec, p, fin, fout, block, h->stream);
+    }
+}
+
 static cudaError_t launch_update(lbm_ctx *h, const StepParams &p, const void *fin, void *fout)
 {
     if (p.bgk) {
         // plain BGK: the general kernel only
         h->launches += 1;
-        const int block = h->block > 0 ? h->block : block_default(1);
-        return h->lattice == LBM_D2Q9 ? step_d2q9(h->prec, p, fin, fout, block, h->stream)
-                                      : step_d3q19(h->prec, p, fin, fout, block, h->stream);
+        return step_general(h, p, fin, fout, h->block > 0 ? h->block : block_default(1));
     }
-    if (staging_wanted(h)) {
+    if (staging_wanted(h) && h->lattice != LBM_D3Q27) {
         const cudaError_t e = h->lattice == LBM_D2Q9
                                   ? rows_d2q9(h->prec, p, fin, fout, h->rows_block, h->stages, h->err_d, h->stream)
                                   : rows_d3q19(h->prec, p, fin, fout, h->rows_block, h->stages, h->err_d, h->stream);
@@ -794,11 +812,12 @@ static cudaError_t launch_update(lbm_ctx *h, const StepParams &p, const void *fi
     if (p.solid || vec == 1 || !vec_supported(h->prec, vec) || p.n[0] % vec != 0) vec = 1;
     const int block = h->block > 0 ? h->block : block_default(vec);
     h->launches += 1;
-    if (vec == 1)
-        return h->lattice == LBM_D2Q9 ? step_d2q9(h->prec, p, fin, fout, block, h->stream)
-                                      : step_d3q19(h->prec, p, fin, fout, block, h->stream);
-    return h->lattice == LBM_D2Q9 ? stepvec_d2q9(h->prec, vec, p, fin, fout, block, h->stream)
-                                  : stepvec_d3q19(h->prec, vec, p, fin, fout, block, h->stream);
+    if (vec == 1) return step_general(h, p, fin, fout, block);
+    switch (h->lattice) {
+    case LBM_D2Q9: return stepvec_d2q9(h->prec, vec, p, fin, fout, block, h->stream);
+    case LBM_D3Q19: return stepvec_d3q19(h->prec, vec, p, fin, fout, block, h->stream);
+    default: return stepvec_d3q27(h->prec, vec, p, fin, fout, block, h->stream);
+    }
 }
 
 // Step parameters of refined level k >= 1: periodic box, ring fixed, no sponge/inflow
@@ -1052,6 +1071,7 @@ extern "C" int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const
     if (h->collision != LBM_COLLISION_RR)
         return fail(h, LBM_EINVAL, "refinement patches couple rrBGK levels; select LBM_COLLISION_RR first");
     if (!origin || !extent) return fail(h, LBM_EINVAL, "origin and extent are required");
+    if (h->lattice == LBM_D3Q27) return fail(h, LBM_EINVAL, "refinement patches are implemented for D2Q9 and D3Q19");
     if (h->levels.size() >= LBM_MAX_LEVELS - 1)
         return fail(h, LBM_EINVAL, "at most %d levels", LBM_MAX_LEVELS);
     const int parent = nlevels(h) - 1;  // the new patch nests inside the finest level
@@ -1242,7 +1262,7 @@ extern "C" int lbm_set_sponge_jet_reference(lbm_handle h, double yc, double zc, 
 {
     CHECK_HANDLE(h);
     h->cfg_version++;
-    if (h->lattice != LBM_D3Q19) return fail(h, LBM_EINVAL, "the round-jet reference needs D3Q19");
+    if (h->d != 3) return fail(h, LBM_EINVAL, "the round-jet reference needs a 3D lattice");
     if (D == 0.0) {
         for (double &v : h->jet_ref) v = 0.0;
         return LBM_OK;
@@ -1325,7 +1345,7 @@ extern "C" int lbm_get_staging(lbm_handle h, int *active, int *stages, int *bloc
     CHECK_HANDLE(h);
     RowsPlan pl{};
     bool on = false;
-    if (staging_wanted(h)) {
+    if (staging_wanted(h) && h->lattice != LBM_D3Q27) {
         StepParams p;
         int rc = build_params(h, p);
         if (rc != LBM_OK) return rc;

@@ -26,7 +26,8 @@ namespace rr {
 
 // ---------------------------------------------------------------------------
 // Lattices.  Direction 0 is the rest velocity; i and i + Q/2 (1 <= i <= Q/2)
-// are opposite.  Weights: D2Q9 4/9, 1/9, 1/36; D3Q19 1/3, 1/18, 1/36 by |xi|^2.
+// are opposite.  Weights by |xi|^2: D2Q9 4/9, 1/9, 1/36; D3Q19 1/3, 1/18,
+// 1/36; D3Q27 8/27, 2/27, 1/54, 1/216.
 // ---------------------------------------------------------------------------
 struct D2Q9 {
     static constexpr int Q = 9, D = 2, HALF = 4;
@@ -62,6 +63,40 @@ struct D3Q19 {
     }
 };
 
+// The tensor product of D1Q3: the D3Q19 velocities plus the eight corners;
+// every third-order Hermite polynomial but H_aaa is supported (H_xyz too).
+struct D3Q27 {
+    static constexpr int Q = 27, D = 3, HALF = 13;
+    __host__ __device__ static constexpr int cx(int i)
+    {
+        constexpr int v[27] = {0, 1, 0, 0, 1, 1, 1, 1, 0, 0, 1, 1, 1, 1,
+                               -1, 0, 0, -1, -1, -1, -1, 0, 0, -1, -1, -1, -1};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int cy(int i)
+    {
+        constexpr int v[27] = {0, 0, 1, 0, 1, -1, 0, 0, 1, 1, 1, 1, -1, -1,
+                               0, -1, 0, -1, 1, 0, 0, -1, -1, -1, -1, 1, 1};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int cz(int i)
+    {
+        constexpr int v[27] = {0, 0, 0, 1, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1,
+                               0, 0, -1, 0, 0, -1, 1, -1, 1, -1, 1, -1, 1};
+        return v[i];
+    }
+};
+
+// largest number of directions of a supported lattice (D3Q27)
+constexpr int kMaxQ = 27;
+
+// whether the lattice carries the complete third order (a_xyz as well)
+template <class L>
+__host__ __device__ constexpr bool full_third_order()
+{
+    return L::Q == 27;
+}
+
 template <class L>
 __host__ __device__ constexpr int opp(int i)
 {
@@ -72,11 +107,19 @@ template <class L>
 __host__ __device__ constexpr double weight(int i)
 {
     // |xi|^2 decides the weight class
-    return (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i)) == 0
-               ? (L::D == 2 ? 4.0 / 9.0 : 1.0 / 3.0)
-               : ((L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i)) == 1
-                      ? (L::D == 2 ? 1.0 / 9.0 : 1.0 / 18.0)
-                      : 1.0 / 36.0);
+    return L::Q == 27
+               ? ((L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i)) == 0
+                      ? 8.0 / 27.0
+                      : ((L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i)) == 1
+                             ? 2.0 / 27.0
+                             : ((L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i)) == 2
+                                    ? 1.0 / 54.0
+                                    : 1.0 / 216.0)))
+               : ((L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i)) == 0
+                      ? (L::D == 2 ? 4.0 / 9.0 : 1.0 / 3.0)
+                      : ((L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i)) == 1
+                             ? (L::D == 2 ? 1.0 / 9.0 : 1.0 / 18.0)
+                             : 1.0 / 36.0));
 }
 
 // ---------------------------------------------------------------------------
@@ -192,6 +235,7 @@ struct Coef {
     C a0, a1x, a1y, a1z;
     C xx, yy, zz, xy, xz, yz;
     C xxy, xyy, xxz, xzz, yyz, yzz;
+    C xyz;  // D3Q27 only
 };
 
 // Second-order symmetric tensor (xx, yy, zz, xy, xz, yz)
@@ -204,7 +248,7 @@ struct Sym2 {
 // a1 += s rho u, A2 += s rho u u, A3 += s rho u u u.  dr = rho - 1 is passed
 // separately so that it keeps its own precision.  O3 = false stops at second
 // order: the quadratic equilibrium of the plain LBM-BGK (Eq. truncatedEq).
-template <class C, int D = 3, bool O3 = true>
+template <class C, int D = 3, bool O3 = true, bool XYZ = false>
 __device__ __forceinline__ void add_eq(Coef<C> &k, C s, C dr, C rho, C ux, C uy, C uz)
 {
     const C r = s * rho;
@@ -232,13 +276,14 @@ __device__ __forceinline__ void add_eq(Coef<C> &k, C s, C dr, C rho, C ux, C uy,
         k.xzz = fmac(rzz, ux, k.xzz);
         k.yyz = fmac(ryy, uz, k.yyz);
         k.yzz = fmac(rzz, uy, k.yzz);
+        if (XYZ) k.xyz = fmac(rx * uy, uz, k.xyz);
     }
 }
 
 // Off-equilibrium coefficients scaled by s: A2 += s Pi^neq and
 // A3 += s a3_neq, a3_neq,abc = u_a P_bc + u_b P_ac + u_c P_ab (Eq. recursive2, n = 3);
 // O3 = false: A2 only.
-template <class C, int D = 3, bool O3 = true>
+template <class C, int D = 3, bool O3 = true, bool XYZ = false>
 __device__ __forceinline__ void add_neq(Coef<C> &k, C s, C ux, C uy, C uz, const Sym2<C> &p)
 {
     k.xx = fmac(s, p.xx, k.xx);
@@ -264,6 +309,8 @@ __device__ __forceinline__ void add_neq(Coef<C> &k, C s, C ux, C uy, C uz, const
         k.xzz = fmac(s, fmac(uz2, p.xz, ux * p.zz), k.xzz);
         k.yyz = fmac(s, fmac(uy2, p.yz, uz * p.yy), k.yyz);
         k.yzz = fmac(s, fmac(uz2, p.yz, uy * p.zz), k.yzz);
+        // a3_neq,xyz = u_x P_yz + u_y P_xz + u_z P_xy
+        if (XYZ) k.xyz = fmac(s, fmac(ux, p.yz, fmac(uy, p.xz, uz * p.xy)), k.xyz);
     }
 }
 
@@ -293,6 +340,17 @@ __device__ __forceinline__ C rebuild(const Coef<C> &k, int i)
         // 1 / (2 c_s^6) = 13.5
         if (hxxy != 0.0) r += C(13.5 * hxxy) * k.xxy;
         if (hxyy != 0.0) r += C(13.5 * hxyy) * k.xyy;
+    } else if (full_third_order<L>()) {
+        // every H_aab with 1 / (2 c_s^6) = 13.5, H_xyz with 1 / c_s^6 = 27
+        const double hyzz = (z * z - cs2) * y, hxzz = (z * z - cs2) * x;
+        const double hyyz = (y * y - cs2) * z, hxxz = (x * x - cs2) * z;
+        if (hxxy != 0.0) r += C(13.5 * hxxy) * k.xxy;
+        if (hxyy != 0.0) r += C(13.5 * hxyy) * k.xyy;
+        if (hxxz != 0.0) r += C(13.5 * hxxz) * k.xxz;
+        if (hxzz != 0.0) r += C(13.5 * hxzz) * k.xzz;
+        if (hyyz != 0.0) r += C(13.5 * hyyz) * k.yyz;
+        if (hyzz != 0.0) r += C(13.5 * hyzz) * k.yzz;
+        if (x * y * z != 0) r += C(27.0 * x * y * z) * k.xyz;
     } else {
         const double hyzz = (z * z - cs2) * y, hxzz = (z * z - cs2) * x;
         const double hyyz = (y * y - cs2) * z, hxxz = (x * x - cs2) * z;
@@ -371,7 +429,7 @@ __device__ __forceinline__ Mom<C> moments_pairs(const C *g)
 template <class C>
 struct RebuildPre {
     C tr3;             // tr(A2) / 3
-    C wa1, wa2;        // w a0 for the directions with one / two non-zero components
+    C wa1, wa2, wa3;   // w a0 for the directions with one / two / three non-zero components
     C bxy, bxz, byz;   // A_aa + A_bb - tr / 3 of the three coordinate planes
     C s1, d1, s2, d2, s3, d3;  // third-order pair sums / differences (D3Q19)
 };
@@ -379,14 +437,15 @@ struct RebuildPre {
 template <class L, class C>
 __device__ __forceinline__ RebuildPre<C> rebuild_prep(const Coef<C> &k)
 {
-    // the two weight classes: |xi|^2 = 1 (direction 1 on both lattices) and
-    // |xi|^2 = 2 (w = 1/36 on both lattices)
+    // weight classes by |xi|^2 = 1 (direction 1 on every lattice), 2 and 3
+    // (D3Q27 corners)
     RebuildPre<C> r;
     C tr = k.xx + k.yy;
     if (L::D == 3) tr += k.zz;
     r.tr3 = tr * C(1.0 / 3.0);
     r.wa1 = C(weight<L>(1)) * k.a0;
-    r.wa2 = C(1.0 / 36.0) * k.a0;
+    r.wa2 = C(full_third_order<L>() ? 1.0 / 54.0 : 1.0 / 36.0) * k.a0;
+    r.wa3 = full_third_order<L>() ? C(1.0 / 216.0) * k.a0 : C(0);
     r.bxy = (k.xx + k.yy) - r.tr3;
     if (L::D == 3) {
         r.bxz = (k.xx + k.zz) - r.tr3;
@@ -412,12 +471,15 @@ __device__ __forceinline__ void rebuild_pair(const Coef<C> &k, const RebuildPre<
     C f2;
     if (nnz == 1) {
         f2 = (x ? k.xx : (y ? k.yy : k.zz)) - r.tr3;
-    } else {
+    } else if (nnz == 2) {
         const C base = (x && y) ? r.bxy : ((x && z) ? r.bxz : r.byz);
         const C off = (x && y) ? k.xy : ((x && z) ? k.xz : k.yz);
         f2 = fmac(C(2 * x * y + 2 * x * z + 2 * y * z), off, base);
+    } else {
+        // corner (D3Q27): tr - tr/3 + 2 (xy A_xy + xz A_xz + yz A_yz)
+        f2 = fmac(C(2 * x * y), k.xy, fmac(C(2 * x * z), k.xz, fmac(C(2 * y * z), k.yz, r.tr3 + r.tr3)));
     }
-    const C E = fmac(C(4.5 * w), f2, nnz == 1 ? r.wa1 : r.wa2);
+    const C E = fmac(C(4.5 * w), f2, nnz == 1 ? r.wa1 : (nnz == 2 ? r.wa2 : r.wa3));
     // first order over the non-zero components
     C f1;
     if (x) f1 = x > 0 ? k.a1x : -k.a1x;
@@ -430,6 +492,17 @@ __device__ __forceinline__ void rebuild_pair(const Coef<C> &k, const RebuildPre<
         // 1 / (2 c_s^6) = 13.5
         if (hxxy != 0.0) o = fmac(C(13.5 * w * hxxy), k.xxy, o);
         if (hxyy != 0.0) o = fmac(C(13.5 * w * hxyy), k.xyy, o);
+    } else if (full_third_order<L>()) {
+        // D3Q27: every H_aab with 1/(2 c_s^6) = 13.5, H_xyz with 1/c_s^6 = 27
+        const double hyzz = (z * z - cs2) * y, hxzz = (z * z - cs2) * x;
+        const double hyyz = (y * y - cs2) * z, hxxz = (x * x - cs2) * z;
+        if (hxxy != 0.0) o = fmac(C(13.5 * w * hxxy), k.xxy, o);
+        if (hxyy != 0.0) o = fmac(C(13.5 * w * hxyy), k.xyy, o);
+        if (hxxz != 0.0) o = fmac(C(13.5 * w * hxxz), k.xxz, o);
+        if (hxzz != 0.0) o = fmac(C(13.5 * w * hxzz), k.xzz, o);
+        if (hyyz != 0.0) o = fmac(C(13.5 * w * hyyz), k.yyz, o);
+        if (hyzz != 0.0) o = fmac(C(13.5 * w * hyzz), k.yzz, o);
+        if (x * y * z != 0) o = fmac(C(27.0 * w * x * y * z), k.xyz, o);
     } else {
         // pairs (xxy, yzz), (xzz, xyy), (yyz, xxz); 1/(2 c_s^6) = 13.5, 1/(6 c_s^6) = 4.5
         const double hyzz = (z * z - cs2) * y, hxzz = (z * z - cs2) * x;

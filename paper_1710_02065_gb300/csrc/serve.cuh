@@ -18,7 +18,7 @@ namespace rr {
 struct BatchDomain {
     StepParams p;
     void *f[2];
-    char *base[2][19];  // per-direction base addresses of the two lattices
+    char *base[2][kMaxQ];  // per-direction base addresses of the two lattices
     int cur;
     int active;
     int64_t remaining;

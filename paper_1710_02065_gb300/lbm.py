@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_EIO = 0, -1, -2, -3, -4, -5
-LBM_D2Q9, LBM_D3Q19 = 0, 1
+LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 0, 1, 2
 LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED, LBM_BF16_SHIFTED = 0, 1, 2, 3
 LBM_FACE_XM, LBM_FACE_XP, LBM_FACE_YM, LBM_FACE_YP, LBM_FACE_ZM, LBM_FACE_ZP = range(6)
 LBM_BC_PERIODIC, LBM_BC_VELOCITY, LBM_BC_OUTFLOW, LBM_BC_FREESLIP, LBM_BC_PRESSURE = 0, 1, 2, 3, 4
@@ -142,8 +142,8 @@ def _c64(a):
 # ---------------------------------------------------------------------------
 def lbm_lattice_table(lattice: int):
     q, d = C.c_int(), C.c_int()
-    xi = np.zeros(19 * 3, dtype=np.int32)
-    w = np.zeros(19)
+    xi = np.zeros(27 * 3, dtype=np.int32)
+    w = np.zeros(27)
     _check(_lib.lbm_lattice_table(lattice, C.byref(q), C.byref(d), xi.ctypes.data_as(_ip), _d(w)))
     return q.value, d.value, xi[: 3 * q.value].reshape(q.value, 3).copy(), w[: q.value].copy()
 
@@ -433,7 +433,7 @@ class Solver:
         ext = list(extents) + [1] * (3 - len(extents))
         self.n = tuple(int(v) for v in ext)
         self.ncell = self.n[0] * self.n[1] * self.n[2]
-        self.q = 9 if lattice == LBM_D2Q9 else 19
+        self.q = {LBM_D2Q9: 9, LBM_D3Q19: 19, LBM_D3Q27: 27}[lattice]
         self.h = lbm_create(lattice, self.n, tau, value_is_nu, Ma_ref, precision, stream)
 
     def close(self):

@@ -15,7 +15,7 @@ import numpy as np
 import oracle
 from paper_1710_02065_gb300 import inputs
 
-D2Q9, D3Q19 = 0, 1
+D2Q9, D3Q19, D3Q27 = 0, 1, 2
 PERIODIC, VELOCITY, OUTFLOW, FREESLIP, PRESSURE = 0, 1, 2, 3, 4
 CS = 1.0 / math.sqrt(3.0)
 
@@ -43,7 +43,7 @@ class Case:
 
     @property
     def q(self):
-        return 9 if self.lattice == D2Q9 else 19
+        return {D2Q9: 9, D3Q19: 19, D3Q27: 27}[self.lattice]
 
 
 def to_oracle(c: Case):
@@ -99,9 +99,9 @@ def acoustic_pulse(n=128, tau=0.6):
     return Case("acoustic_pulse", D2Q9, (n, n, 1), tau, rho0=rho, u0=u)
 
 
-def taylor_green_3d(n=24, tau=0.7, u0=0.02):
+def taylor_green_3d(n=24, tau=0.7, u0=0.02, lattice=D3Q19):
     rho, u = inputs.taylor_green_3d(n, u0)
-    return Case("tgv3d", D3Q19, (n, n, n), tau, rho0=rho, u0=u)
+    return Case("tgv3d", lattice, (n, n, n), tau, rho0=rho, u0=u)
 
 
 def cylinder(nx=1600, ny=800, diameter=40.0, xc=None, yc=None, Ma=0.2, Re=150.0, sponge=100,

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(lbm, repo_root):
     assert declared <= set(dir(lbm)), declared - set(dir(lbm))
 
 
-@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("which", [0, 1, 2])
 def test_lattice_table_matches_oracle(lbm, which):
     q, d, xi, w = lbm.lbm_lattice_table(which)
     od, oq, oxi, ow, oopp = oracle.lattice(which)
