@@ -1,5 +1,7 @@
-// refine.cuh -- two-level 2:1 grid coupling kernels (Sec. II.B, Eq. couplingCF,
+// refine.cuh -- 2:1 grid coupling kernels of a parent / child level pair (Sec. II.B, Eq. couplingCF,
 // Eq. couplingFC), D2Q9 and D3Q19 (the 3D kernels are at the end of the file).
+// Below, "coarse" is the parent level of a pair and "fine" its child; nested
+// levels apply these kernels pair by pair.
 //
 // Layout (vertex based, dx_f = dx_c / 2, dt_f = dt_c / 2): the fine patch
 // covers the coarse nodes X0..X0+Wc, Y0..Y0+Hc; fine node (i, j) sits at
