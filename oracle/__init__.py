@@ -69,6 +69,7 @@ class _Problem(C.Structure):
         ("g", C.c_double * 3),
         ("collision", C.c_int),
         ("jet_ref", C.c_double * 7),
+        ("order4", C.c_int),
     ]
 
 
@@ -92,7 +93,7 @@ def lib():
                                          C.POINTER(C.c_int), dp, C.POINTER(C.c_int)]
             _lib.orc_feqH.argtypes = [C.c_int, C.c_double, dp, dp]
             _lib.orc_fneqH.argtypes = [C.c_int, dp, dp, dp]
-            _lib.orc_collide.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double, dp, dp, dp]
+            _lib.orc_collide.argtypes = [C.c_int, dp, C.c_double, C.c_double, C.c_double, dp, dp, C.c_int, dp]
             _lib.orc_step.argtypes = [P, dp, dp, C.c_int64]
             _lib.orc_run.argtypes = [P, dp, dp, C.c_int64, C.c_int64]
             _lib.orc_update_cell.argtypes = [P, dp, C.c_int64, C.c_int64, dp]
@@ -162,13 +163,13 @@ def fneqH(which: int, u, pi_neq) -> np.ndarray:
 
 
 def collide(which: int, f, tau: float, chi: float = 0.0, rho_ref: float = 1.0,
-            u_ref=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0)) -> np.ndarray:
+            u_ref=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0), order4: bool = False) -> np.ndarray:
     """One cell's rrBGK collision, Eq. optimizedLB (Eq. spongeLB when chi > 0)."""
     f = np.ascontiguousarray(f, dtype=np.float64)
     out = np.zeros_like(f)
     lib().orc_collide(which, _dp(f), float(tau), float(chi), float(rho_ref),
                       _dp(np.ascontiguousarray(u_ref, dtype=np.float64)),
-                      _dp(np.ascontiguousarray(g, dtype=np.float64)), _dp(out))
+                      _dp(np.ascontiguousarray(g, dtype=np.float64)), int(bool(order4)), _dp(out))
     return out
 
 
@@ -211,6 +212,7 @@ class Problem:
         self.radial = [0.0] * 6
         self.collision = RR  # RR: rrBGK (Eq. optimizedLB); BGK: plain BGK (Eq. standardLB)
         self.jet_ref = [0.0] * 7  # yc, zc, U_J, D, x0, B, S of the +x sponge's jet reference; D = 0: none
+        self.order4 = 0  # D2Q9: 1 adds the fourth-order H_xxyy term
 
     @property
     def ncell(self) -> int:
@@ -258,6 +260,7 @@ class Problem:
         s.collision = self.collision
         for k in range(7):
             s.jet_ref[k] = self.jet_ref[k]
+        s.order4 = int(self.order4)
         for f in range(6):
             s.face_kind[f] = self.face_kind[f]
             s.rho_face[f] = self.rho_face[f]

@@ -60,6 +60,10 @@
  *       chi_max sigma(r - r0) for r - r0 < 0.8 W, chi_max beyond.
  *   R15 Forces on walls (lift, drag; not printed as a formula in the paper):
  *       momentum exchange over the bounce-back links.
+ *   R23 D2Q9 fourth order (optional; Sec. II.A: D2Q9 supports an expansion
+ *       beyond n = 3): the H_xxyy term with a4_eq = rho u_x^2 u_y^2 and
+ *       Eq. recursive2 at n = 4 read as the symmetric sum over index pairs,
+ *       a4_neq = u_x^2 P_yy + u_y^2 P_xx + 4 u_x u_y P_xy.
  *   R21 Jet outflow sponge reference (Sec. IV: the jet similarity solution of
  *       Pope 2000 as reference field of the outflow region): inside the +x
  *       layer the reference velocity is the self-similar round-jet mean
@@ -258,6 +262,30 @@ static void fneqH(const lattice_t *L, const double u[3], double Pn[3][3], double
     }
 }
 
+/* Optional fourth order on D2Q9 (reading R23): H_xxyy = (xi_x^2 - c_s^2)
+ * (xi_y^2 - c_s^2), supported by D2Q9 with the continuous norm 4 c_s^8; it
+ * enters H4 : a4 / (4! c_s^8) with multiplicity 6, i.e. with 1 / (4 c_s^8).
+ * Equilibrium a4_xxyy = rho u_x^2 u_y^2 (Eq. recursive1); off-equilibrium
+ * from Eq. recursive2 at n = 4 read as the symmetric sum over the six index
+ * pairs, a4_xxyy = u_x^2 P_yy + u_y^2 P_xx + 4 u_x u_y P_xy. */
+static double H4xxyy(const lattice_t *L, int i)
+{
+    return ((double)L->xi[i][0] * L->xi[i][0] - CS2) * ((double)L->xi[i][1] * L->xi[i][1] - CS2);
+}
+
+static void add_fourth_eq(const lattice_t *L, double rho, const double u[3], double *f)
+{
+    const double a4 = rho * u[0] * u[0] * u[1] * u[1], c = 1.0 / (4.0 * CS2 * CS2 * CS2 * CS2);
+    for (int i = 0; i < L->q; ++i) f[i] += L->w[i] * H4xxyy(L, i) * a4 * c;
+}
+
+static void add_fourth_neq(const lattice_t *L, const double u[3], double Pn[3][3], double *f)
+{
+    const double a4 = u[0] * u[0] * Pn[1][1] + u[1] * u[1] * Pn[0][0] + 4.0 * u[0] * u[1] * Pn[0][1];
+    const double c = 1.0 / (4.0 * CS2 * CS2 * CS2 * CS2);
+    for (int i = 0; i < L->q; ++i) f[i] += L->w[i] * H4xxyy(L, i) * a4 * c;
+}
+
 /* Pi^neq = Pi - rho c_s^2 I - rho u u (reading R1); components outside the
  * lattice's d dimensions are zero. */
 static void pi_neq(int d, double rho, const double u[3], double Pi[3][3], double Pn[3][3])
@@ -271,8 +299,9 @@ static void pi_neq(int d, double rho, const double u[3], double Pi[3][3], double
  * Eq. dampingLBM when chi > 0 (reading R4).  g is a body force used only by
  * the oracle's own Poiseuille check (momentum source w_i rho xi_i.g / c_s^2). */
 static void collide(const lattice_t *L, const double *f, double tau, double chi,
-                    double rho_ref, const double u_ref[3], const double g[3], double *out)
+                    double rho_ref, const double u_ref[3], const double g[3], int o4, double *out)
 {
+    o4 = o4 && L->d == 2;
     double rho, j[3], Pi[3][3], u[3], Pn[3][3];
     double feq[QMAX], fneq[QMAX];
     moments(L, f, &rho, j, Pi);
@@ -285,6 +314,11 @@ static void collide(const lattice_t *L, const double *f, double tau, double chi,
         feqH(L, rs, u, feq);
         fneqH(L, u, Pn, fneq);
         feqH(L, rho_ref, u_ref, fref);
+        if (o4) {
+            add_fourth_eq(L, rs, u, feq);
+            add_fourth_neq(L, u, Pn, fneq);
+            add_fourth_eq(L, rho_ref, u_ref, fref);
+        }
         for (int i = 0; i < L->q; ++i)
             out[i] = feq[i] + (1.0 - 1.0 / tau) * fneq[i] + chi * (fref[i] - feq[i]);
     } else {
@@ -292,6 +326,10 @@ static void collide(const lattice_t *L, const double *f, double tau, double chi,
         pi_neq(L->d, rho, u, Pi, Pn);
         feqH(L, rho, u, feq);
         fneqH(L, u, Pn, fneq);
+        if (o4) {
+            add_fourth_eq(L, rho, u, feq);
+            add_fourth_neq(L, u, Pn, fneq);
+        }
         for (int i = 0; i < L->q; ++i) out[i] = feq[i] + (1.0 - 1.0 / tau) * fneq[i];
     }
     if (g && (g[0] != 0.0 || g[1] != 0.0 || g[2] != 0.0))
@@ -361,7 +399,7 @@ static void collide_bgk(const lattice_t *L, const double *f, double tau, double 
  * rrBGK; under plain BGK the node is rebuilt to second order, f^eq + f^neq_2,
  * and the BGK collision of that is f^eq + (1 - 1/tau) f^neq_2. */
 static void rebuilt_node(int collision, double tau, const lattice_t *L, double rho, const double u[3],
-                         double Pn[3][3], double *out)
+                         double Pn[3][3], int o4, double *out)
 {
     double feq[QMAX], fneq[QMAX];
     if (collision == 1) {
@@ -370,6 +408,10 @@ static void rebuilt_node(int collision, double tau, const lattice_t *L, double r
     } else {
         feqH(L, rho, u, feq);
         fneqH(L, u, Pn, fneq);
+        if (o4 && L->d == 2) {
+            add_fourth_eq(L, rho, u, feq);
+            add_fourth_neq(L, u, Pn, fneq);
+        }
     }
     for (int i = 0; i < L->q; ++i) out[i] = feq[i] + (1.0 - 1.0 / tau) * fneq[i];
 }
@@ -417,6 +459,7 @@ typedef struct {
     int collision;           /* 0 = rrBGK (Eq. optimizedLB), 1 = BGK (Eq. standardLB) */
     double jet_ref[7];       /* round-jet similarity reference of the +x sponge (reading R21):
                                 yc, zc, U_J, D, x0, B, S; D = 0: none */
+    int order4;              /* D2Q9: add the fourth-order H_xxyy term (reading R23) */
 } orc_problem;
 
 static int64_t ncell(const orc_problem *P) { return (int64_t)P->n[0] * P->n[1] * P->n[2]; }
@@ -557,7 +600,7 @@ void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int6
         } else {
             rho = P->rho_face[inlet];
         }
-        rebuilt_node(P->collision, P->tau, L, rho, us, Pn, out);
+        rebuilt_node(P->collision, P->tau, L, rho, us, Pn, P->order4, out);
         return;
     }
 
@@ -579,7 +622,7 @@ void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int6
                     ub[a] += P->noise_amp * mag * (2.0 * orc_u01(base + (uint64_t)a) - 1.0);
             }
         }
-        rebuilt_node(P->collision, P->tau, L, rho, ub, Pn, out);
+        rebuilt_node(P->collision, P->tau, L, rho, ub, Pn, P->order4, out);
         return;
     }
 
@@ -588,7 +631,7 @@ void orc_update_cell(const orc_problem *P, const double *fin, int64_t cell, int6
     if (P->collision == 1)
         collide_bgk(L, f, P->tau, sponge_chi(P, c), P->rho_ref, uref, P->g, out);
     else
-        collide(L, f, P->tau, sponge_chi(P, c), P->rho_ref, uref, P->g, out);
+        collide(L, f, P->tau, sponge_chi(P, c), P->rho_ref, uref, P->g, P->order4, out);
 }
 
 /* Post-collision populations of a list of cells (out: n x q, cell-major). */
@@ -659,9 +702,9 @@ void orc_fneqH(int which, const double *u, const double *Pn9, double *out)
 }
 
 void orc_collide(int which, const double *f, double tau, double chi, double rho_ref,
-                 const double *u_ref, const double *g, double *out)
+                 const double *u_ref, const double *g, int order4, double *out)
 {
-    collide(lattice(which), f, tau, chi, rho_ref, u_ref, g, out);
+    collide(lattice(which), f, tau, chi, rho_ref, u_ref, g, order4, out);
 }
 
 /* Moments of a stored field: rho (N), u (3N, per cell xyz), Pi^neq (6N, per
@@ -699,6 +742,7 @@ void orc_init_equilibrium(const orc_problem *P, const double *rho, const double 
     for (int64_t cell = 0; cell < N; ++cell) {
         double out[QMAX];
         feqH(L, rho[cell], u + 3 * cell, out);
+        if (P->order4 && L->d == 2) add_fourth_eq(L, rho[cell], u + 3 * cell, out);
         for (int i = 0; i < L->q; ++i) f[(int64_t)i * N + cell] = out[i];
     }
 }
