@@ -98,6 +98,31 @@ def time_oracle(max_seconds=15.0, max_steps=40, min_steps=2):
     return mlups, steps, dt, P.ncell
 
 
+def _oracle_replica(steps):
+    """One independent oracle solve of the 96 x 64 x 64 sample (a pool worker)."""
+    spec = jet_spec(**SAMPLE_SPEC)
+    P, f = configure_oracle(spec)
+    f = P.run(f, 1)
+    t0 = time.perf_counter()
+    f = P.run(f, steps, step0=1)
+    return P.ncell, steps, t0, time.perf_counter()
+
+
+def time_oracle_all_cores(cores=None, steps=6):
+    """Aggregate MLUPS of `cores` independent single-threaded oracle solves
+    running at once (one per host core; spawned processes, so it is safe after
+    CUDA initialisation).  The oracle itself is unchanged: this is replica
+    throughput, the way the host would run many independent problems."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_replica, [steps] * cores)
+    t0 = min(r[2] for r in res)
+    t1 = max(r[3] for r in res)
+    cells = sum(r[0] * r[1] for r in res)
+    return cells / (t1 - t0) / 1e6, cores, steps, t1 - t0
+
+
 # ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
@@ -738,6 +763,13 @@ def main():
         mlups_cpu, st, dt, nc = time_oracle()
         cpu = {"value": mlups_cpu, "unit": "MLUPS", "cores": 1, "kind": "oracle",
                "sample": f"D3Q19 round jet scaled to 96x64x64 ({nc} cells), {st} FP64 steps in {dt:.1f} s, 1 thread"}
+        try:
+            agg, nproc, rst, rdt = time_oracle_all_cores()
+            cpu["all_cores"] = {"value": agg, "unit": "MLUPS", "cores": nproc,
+                                "sample": f"{nproc} independent 96x64x64 oracle solves at once, "
+                                          f"{rst} FP64 steps each, {rdt:.1f} s wall"}
+        except Exception as e:  # a host without process spawning still reports the 1-thread figure
+            cpu["all_cores"] = {"unavailable": repr(e)}
 
     if rank == 0:
         line = {

@@ -55,7 +55,7 @@ typedef struct lbm_ctx *lbm_handle;
 #define LBM_EINVAL (-1)    /* invalid argument or unsupported combination      */
 #define LBM_ENOMEM (-2)    /* device or host allocation failed                  */
 #define LBM_ECUDA (-3)     /* a CUDA call failed (message has the CUDA error)   */
-#define LBM_EUNSTABLE (-4) /* non-finite populations found by lbm_reduce        */
+#define LBM_EUNSTABLE (-4) /* unstable cells found by lbm_reduce (non-finite, rho <= 0, |u| >= c_s) */
 #define LBM_EIO (-5)       /* file error in lbm_save / lbm_load                 */
 
 /* Lattices (Sec. II.A: D2Q9 in 2D, D3Q19 in 3D).  LBM_D3Q27, the tensor
@@ -246,8 +246,10 @@ int lbm_moments(lbm_handle h, double *rho, double *u, double *pi_neq);
 
 /*
  * lbm_reduce -- FP64 totals over fluid cells of level 0: *mass = sum rho,
- * momentum[0..2] = sum rho u.  Returns LBM_EUNSTABLE if any population is
- * non-finite (the totals are still written).
+ * momentum[0..2] = sum rho u (over the cells with finite populations).
+ * Returns LBM_EUNSTABLE if a fluid cell holds a non-finite population, a
+ * non-positive density or a velocity at or above the lattice sound speed
+ * c_s = 1/sqrt(3) (the totals are still written).
  */
 int lbm_reduce(lbm_handle h, double *mass, double momentum[3]);
 
@@ -309,6 +311,20 @@ int lbm_pressure_fluctuation(lbm_handle h, double *dp_tilde, double *dp_mean);
  */
 int lbm_set_sponge_jet_reference(lbm_handle h, double yc, double zc, double U_jet, double D, double x0,
                                  double B, double S);
+
+/*
+ * lbm_set_hermite_order -- expansion order N of the regularized equilibrium
+ * and off-equilibrium parts (Sec. II.A; default 3).  4 exists for D2Q9,
+ * whose velocity set also supports H_xxyy = (xi_x^2 - c_s^2)(xi_y^2 - c_s^2):
+ * the term 20.25 w_i H_xxyy(i) a4_xxyy is added with a4_eq = rho u_x^2 u_y^2
+ * (Eq. recursive1) and a4_neq = u_x^2 P_yy + u_y^2 P_xx + 4 u_x u_y P_xy
+ * (Eq. recursive2 at n = 4 read as the symmetric sum over index pairs);
+ * lbm_set_state then also starts from the order-4 equilibrium.  It applies
+ * to the rrBGK collision and its rebuilt boundary nodes (plain BGK keeps its
+ * quadratic equilibrium).  LBM_EINVAL for other orders, other lattices, or
+ * with refinement patches.
+ */
+int lbm_set_hermite_order(lbm_handle h, int order);
 
 /*
  * lbm_set_collision -- collision model of the single-level update (Sec. II.A).

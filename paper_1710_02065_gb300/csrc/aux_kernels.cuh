@@ -5,7 +5,8 @@
 //   k_get_dir     : one direction of the stored field as plain FP64 f_i
 //   k_moments     : rho, u, Pi^neq per cell in FP64 (Eq. moments, Sec. II.A)
 //   k_reduce      : FP64 per-block totals of rho - 1, rho u, fluid count and
-//                   non-finite count (warp shuffles, then a fixed-order pass)
+//                   unstable count (non-finite, rho <= 0 or |u| >= c_s; warp
+//                   shuffles, then a fixed-order pass)
 //   k_probe       : rho at listed cells
 //   k_rho_accumulate : running FP64 sum of rho per cell (temporal mean of p)
 //   k_pressure_fluct : Delta p~ = c_s^2 (rho - mean rho) per cell
@@ -27,14 +28,15 @@ __device__ __forceinline__ double weight_rt(int i)
 
 template <class L, class S>
 __global__ void k_init_eq(int64_t N, const double *__restrict__ rho, const double *__restrict__ u,
-                          S *__restrict__ f0, S *__restrict__ f1)
+                          S *__restrict__ f0, S *__restrict__ f1, int order4)
 {
     using C = typename StoreC<S>::C;  // FP32 arithmetic for FP32/FP16/BF16 storage
     const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (cell >= N) return;
     Coef<C> k{};
-    add_eq<C, L::D, true, full_third_order<L>()>(k, C(1), C(rho[cell] - 1.0), C(rho[cell]), C(u[3 * cell]), C(u[3 * cell + 1]),
-              L::D == 3 ? C(u[3 * cell + 2]) : C(0));
+    add_eq<C, L::D, true, full_third_order<L>()>(k, C(1), C(rho[cell] - 1.0), C(rho[cell]), C(u[3 * cell]),
+                                                  C(u[3 * cell + 1]), L::D == 3 ? C(u[3 * cell + 2]) : C(0),
+                                                  order4 != 0);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const S v = Store<S>::from(rebuild<L, C>(k, i));
@@ -98,7 +100,7 @@ __global__ void k_moments(int64_t N, const S *__restrict__ f, double *__restrict
     }
 }
 
-// Per-block partial sums: [sum dr, sum jx, sum jy, sum jz, fluid cells, non-finite cells]
+// Per-block partial sums: [sum dr, sum jx, sum jy, sum jz, fluid cells, unstable cells]
 constexpr int RED_FIELDS = 6;
 constexpr int RED_BLOCK = 256;
 
@@ -122,9 +124,10 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(int64_t N, const S *__rest
             acc[1] += m.jx;
             acc[2] += m.jy;
             acc[3] += m.jz;
-        } else {
-            acc[5] += 1.0;
         }
+        // unstable: non-finite, non-positive density, or |u| >= c_s
+        const double rho = 1.0 + m.dr, j2 = m.jx * m.jx + m.jy * m.jy + m.jz * m.jz;
+        if (!finite || !(rho > 0.0) || !(j2 < rho * rho * (1.0 / 3.0))) acc[5] += 1.0;
         acc[4] += 1.0;
     }
     // warp, then block, in a fixed order

@@ -62,6 +62,7 @@ struct lbm_ctx {
     unsigned *err_d = nullptr;  // device error word of the row-staged kernel (bounded waits)
     int collision = LBM_COLLISION_RR;
     double jet_ref[7] = {0, 0, 0, 0, 0, 0, 0};  // yc, zc, U_J, D, x0, B, S; D = 0: none
+    int order4 = 0;             // D2Q9: optional fourth-order H_xxyy term
     double *rho_acc = nullptr;  // running sum of rho per cell (temporal mean of p), or null
     int64_t rho_count = 0;
     double *red_d = nullptr;  // reduction partials + result
@@ -167,9 +168,9 @@ static unsigned grid1(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 template <class L, class S>
 struct InitEq {
     static cudaError_t run(cudaStream_t st, int64_t N, const double *rho, const double *u, void *f0,
-                           void *f1)
+                           void *f1, int order4)
     {
-        k_init_eq<L, S><<<grid1(N, 256), 256, 0, st>>>(N, rho, u, (S *)f0, (S *)f1);
+        k_init_eq<L, S><<<grid1(N, 256), 256, 0, st>>>(N, rho, u, (S *)f0, (S *)f1, order4);
         return cudaGetLastError();
     }
 };
@@ -646,7 +647,8 @@ static int set_state_grid(lbm_ctx *h, const GridRef &g, const double *rho, const
     cudaError_t e = cudaMemcpyAsync(buf, rho, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(buf + N, u, sizeof(double) * 3 * (size_t)N, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = dispatch<InitEq>(h->lattice, h->prec, h->stream, N, buf, buf + N, g.f[0], g.f[1]);
+    if (e == cudaSuccess)
+        e = dispatch<InitEq>(h->lattice, h->prec, h->stream, N, buf, buf + N, g.f[0], g.f[1], h->order4);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(buf);
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "set state: %s", cudaGetErrorString(e));
@@ -757,6 +759,7 @@ static int build_params(lbm_ctx *h, StepParams &p)
     p.omega = 1.0 - 1.0 / h->tau;
     p.solid = h->solid_d;
     p.bgk = h->collision == LBM_COLLISION_BGK ? 1 : 0;
+    p.order4 = h->order4;
     p.jet_x_layer = INT_MAX;
     if (h->jet_ref[3] > 0.0 && h->sponge_w[1] > 0 && h->sponge_chi[1] > 0.0) {
         p.jet_x_layer = h->n[0] - h->sponge_w[1];
@@ -1070,6 +1073,7 @@ extern "C" int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const
     h->cfg_version++;
     if (h->collision != LBM_COLLISION_RR)
         return fail(h, LBM_EINVAL, "refinement patches couple rrBGK levels; select LBM_COLLISION_RR first");
+    if (h->order4) return fail(h, LBM_EINVAL, "refinement patches couple order-3 levels; set order 3 first");
     if (!origin || !extent) return fail(h, LBM_EINVAL, "origin and extent are required");
     if (h->lattice == LBM_D3Q27) return fail(h, LBM_EINVAL, "refinement patches are implemented for D2Q9 and D3Q19");
     if (h->levels.size() >= LBM_MAX_LEVELS - 1)
@@ -1242,6 +1246,17 @@ extern "C" int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread)
     if (h->solid_d || vec == 1 || !vec_supported(h->prec, vec) || h->n[0] % vec != 0) vec = 1;
     if (block) *block = h->block > 0 ? h->block : block_default(vec);  // level 0
     if (cells_per_thread) *cells_per_thread = vec;
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_hermite_order(lbm_handle h, int order)
+{
+    CHECK_HANDLE(h);
+    h->cfg_version++;
+    if (order != 3 && order != 4) return fail(h, LBM_EINVAL, "order = %d must be 3 or 4", order);
+    if (order == 4 && h->lattice != LBM_D2Q9) return fail(h, LBM_EINVAL, "order 4 exists for D2Q9 only");
+    if (order == 4 && !h->levels.empty()) return fail(h, LBM_EINVAL, "order 4 is not available with refinement");
+    h->order4 = order == 4 ? 1 : 0;
     return LBM_OK;
 }
 
@@ -1432,7 +1447,8 @@ extern "C" int lbm_reduce(lbm_handle h, double *mass, double momentum[3])
         momentum[1] = out[2];
         momentum[2] = out[3];
     }
-    if (out[5] > 0.0) return fail(h, LBM_EUNSTABLE, "%.0f cells hold non-finite populations", out[5]);
+    if (out[5] > 0.0)
+        return fail(h, LBM_EUNSTABLE, "%.0f cells are unstable (non-finite, rho <= 0 or |u| >= c_s)", out[5]);
     return LBM_OK;
 }
 

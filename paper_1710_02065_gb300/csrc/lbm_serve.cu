@@ -85,7 +85,7 @@ template <class L, class S>
 cudaError_t init_eq(const Request &r, const double *rho, const double *u, cudaStream_t st)
 {
     const int64_t N = r.ncell;
-    k_init_eq<L, S><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, rho, u, (S *)r.f[0], (S *)r.f[1]);
+    k_init_eq<L, S><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, rho, u, (S *)r.f[0], (S *)r.f[1], 0);
     return cudaGetLastError();
 }
 

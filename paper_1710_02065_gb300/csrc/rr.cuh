@@ -235,7 +235,8 @@ struct Coef {
     C a0, a1x, a1y, a1z;
     C xx, yy, zz, xy, xz, yz;
     C xxy, xyy, xxz, xzz, yyz, yzz;
-    C xyz;  // D3Q27 only
+    C xyz;   // D3Q27 only
+    C xxyy;  // D2Q9 with the optional fourth order only
 };
 
 // Second-order symmetric tensor (xx, yy, zz, xy, xz, yz)
@@ -249,7 +250,7 @@ struct Sym2 {
 // separately so that it keeps its own precision.  O3 = false stops at second
 // order: the quadratic equilibrium of the plain LBM-BGK (Eq. truncatedEq).
 template <class C, int D = 3, bool O3 = true, bool XYZ = false>
-__device__ __forceinline__ void add_eq(Coef<C> &k, C s, C dr, C rho, C ux, C uy, C uz)
+__device__ __forceinline__ void add_eq(Coef<C> &k, C s, C dr, C rho, C ux, C uy, C uz, bool o4 = false)
 {
     const C r = s * rho;
     k.a0 = fmac(s, dr, k.a0);
@@ -264,6 +265,8 @@ __device__ __forceinline__ void add_eq(Coef<C> &k, C s, C dr, C rho, C ux, C uy,
         k.xxy = fmac(rxx, uy, k.xxy);
         k.xyy = fmac(ryy, ux, k.xyy);
     }
+    // optional fourth order on D2Q9: a4_xxyy = rho u_x^2 u_y^2 (Eq. recursive1)
+    if (D == 2 && O3 && o4) k.xxyy = fmac(rxx, uy * uy, k.xxyy);
     if (D == 3) {
         const C rz = r * uz;
         k.a1z += rz;
@@ -284,7 +287,7 @@ __device__ __forceinline__ void add_eq(Coef<C> &k, C s, C dr, C rho, C ux, C uy,
 // A3 += s a3_neq, a3_neq,abc = u_a P_bc + u_b P_ac + u_c P_ab (Eq. recursive2, n = 3);
 // O3 = false: A2 only.
 template <class C, int D = 3, bool O3 = true, bool XYZ = false>
-__device__ __forceinline__ void add_neq(Coef<C> &k, C s, C ux, C uy, C uz, const Sym2<C> &p)
+__device__ __forceinline__ void add_neq(Coef<C> &k, C s, C ux, C uy, C uz, const Sym2<C> &p, bool o4 = false)
 {
     k.xx = fmac(s, p.xx, k.xx);
     k.yy = fmac(s, p.yy, k.yy);
@@ -300,6 +303,10 @@ __device__ __forceinline__ void add_neq(Coef<C> &k, C s, C ux, C uy, C uz, const
     const C ux2 = ux + ux, uy2 = uy + uy;
     k.xxy = fmac(s, fmac(ux2, p.xy, uy * p.xx), k.xxy);
     k.xyy = fmac(s, fmac(uy2, p.xy, ux * p.yy), k.xyy);
+    // optional fourth order on D2Q9, Eq. recursive2 at n = 4 as the symmetric
+    // sum over index pairs: a4_xxyy = u_x^2 P_yy + u_y^2 P_xx + 4 u_x u_y P_xy
+    if (D == 2 && o4)
+        k.xxyy = fmac(s, fmac(ux * ux, p.yy, fmac(uy * uy, p.xx, C(4) * ux * uy * p.xy)), k.xxyy);
     if (D == 3) {
         const C uz2 = uz + uz;
         k.zz = fmac(s, p.zz, k.zz);
@@ -340,6 +347,8 @@ __device__ __forceinline__ C rebuild(const Coef<C> &k, int i)
         // 1 / (2 c_s^6) = 13.5
         if (hxxy != 0.0) r += C(13.5 * hxxy) * k.xxy;
         if (hxyy != 0.0) r += C(13.5 * hxyy) * k.xyy;
+        // optional fourth order: H_xxyy / (4 c_s^8) = 20.25 H_xxyy (zero coefficient otherwise)
+        r += C(20.25 * (x * x - cs2) * (y * y - cs2)) * k.xxyy;
     } else if (full_third_order<L>()) {
         // every H_aab with 1 / (2 c_s^6) = 13.5, H_xyz with 1 / c_s^6 = 27
         const double hyzz = (z * z - cs2) * y, hxzz = (z * z - cs2) * x;
@@ -479,7 +488,9 @@ __device__ __forceinline__ void rebuild_pair(const Coef<C> &k, const RebuildPre<
         // corner (D3Q27): tr - tr/3 + 2 (xy A_xy + xz A_xz + yz A_yz)
         f2 = fmac(C(2 * x * y), k.xy, fmac(C(2 * x * z), k.xz, fmac(C(2 * y * z), k.yz, r.tr3 + r.tr3)));
     }
-    const C E = fmac(C(4.5 * w), f2, nnz == 1 ? r.wa1 : (nnz == 2 ? r.wa2 : r.wa3));
+    C E = fmac(C(4.5 * w), f2, nnz == 1 ? r.wa1 : (nnz == 2 ? r.wa2 : r.wa3));
+    // optional fourth order on D2Q9 (even): 20.25 w H_xxyy a4_xxyy; zero coefficient otherwise
+    if (L::D == 2) E = fmac(C(20.25 * w * (x * x - cs2) * (y * y - cs2)), k.xxyy, E);
     // first order over the non-zero components
     C f1;
     if (x) f1 = x > 0 ? k.a1x : -k.a1x;
@@ -525,7 +536,9 @@ __device__ __forceinline__ void rebuild_pair(const Coef<C> &k, const RebuildPre<
 template <class L, class C>
 __device__ __forceinline__ C rebuild_rest(const Coef<C> &k, const RebuildPre<C> &r)
 {
-    return fmac(C(-4.5 * weight<L>(0)), r.tr3, C(weight<L>(0)) * k.a0);
+    const C g0 = fmac(C(-4.5 * weight<L>(0)), r.tr3, C(weight<L>(0)) * k.a0);
+    // optional fourth order on D2Q9: H_xxyy(0) = c_s^4 = 1/9
+    return L::D == 2 ? fmac(C(20.25 * weight<L>(0) / 9.0), k.xxyy, g0) : g0;
 }
 
 // Reciprocal used for 1 / rho: the fast single-precision division intrinsic

@@ -65,6 +65,8 @@ struct StepParams {
     // jet_x_layer = INT_MAX when none
     int jet_x_layer;
     double jet_ref[6];
+    // D2Q9: include the optional fourth-order H_xxyy term (rrBGK only)
+    int order4;
     // per-direction base addresses of the lattice read (in) and written (out):
     // in[i] = f_in + i * ncell elements, i < Q <= kMaxQ; filled by the launchers
     const char *in[kMaxQ];
@@ -176,6 +178,7 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
 {
     constexpr bool O3 = !BGK;
     constexpr bool XYZ = !BGK && full_third_order<L>();
+    const bool o4 = L::D == 2 && !BGK && p.order4;
     const C om = C(p.omega);
     Coef<C> k{};
     if (inlet >= 0 && p.kind[inlet] != BC_VELOCITY) {
@@ -185,15 +188,15 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
         C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
         Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
         if (p.kind[inlet] == BC_PRESSURE) {
-            add_eq<C, L::D, O3, XYZ>(k, C(1), C(p.rho_face_m1[inlet]), C(p.rho_face[inlet]), ux, uy, uz);
+            add_eq<C, L::D, O3, XYZ>(k, C(1), C(p.rho_face_m1[inlet]), C(p.rho_face[inlet]), ux, uy, uz, o4);
         } else {
             const int a = inlet >> 1;
             if (a == 0) { ux = C(0); pn.xy = C(0); pn.xz = C(0); }
             if (a == 1) { uy = C(0); pn.xy = C(0); pn.yz = C(0); }
             if (a == 2) { uz = C(0); pn.xz = C(0); pn.yz = C(0); }
-            add_eq<C, L::D, O3, XYZ>(k, C(1), m.dr, rho, ux, uy, uz);
+            add_eq<C, L::D, O3, XYZ>(k, C(1), m.dr, rho, ux, uy, uz, o4);
         }
-        add_neq<C, L::D, O3, XYZ>(k, om, ux, uy, uz, pn);
+        add_neq<C, L::D, O3, XYZ>(k, om, ux, uy, uz, pn, o4);
         return k;
     }
     if (inlet >= 0) {
@@ -219,8 +222,8 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
             }
         }
         const C ux = C(ub[0]), uy = C(ub[1]), uz = L::D == 3 ? C(ub[2]) : C(0);
-        add_eq<C, L::D, O3, XYZ>(k, C(1), m.dr, rho, ux, uy, uz);
-        add_neq<C, L::D, O3, XYZ>(k, om, ux, uy, uz, pn);
+        add_eq<C, L::D, O3, XYZ>(k, C(1), m.dr, rho, ux, uy, uz, o4);
+        add_neq<C, L::D, O3, XYZ>(k, om, ux, uy, uz, pn, o4);
         return k;
     }
     if (chi > C(0)) {
@@ -248,14 +251,14 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
         const C uz = L::D == 3 ? (m.jz + C(0.5) * chi * rr * urz) * h * inv : C(0);
         if (BGK) {
             // (1 - 1/tau - chi) f^eq(rho*, u*) + chi f^eq(ref); the caller adds (1 - 1/tau) g
-            add_eq<C, L::D, O3, XYZ>(k, C(1) - om - chi, drs, rs, ux, uy, uz);
-            add_eq<C, L::D, O3, XYZ>(k, chi, C(p.rho_ref_m1), rr, urx, ury, L::D == 3 ? urz : C(0));
+            add_eq<C, L::D, O3, XYZ>(k, C(1) - om - chi, drs, rs, ux, uy, uz, o4);
+            add_eq<C, L::D, O3, XYZ>(k, chi, C(p.rho_ref_m1), rr, urx, ury, L::D == 3 ? urz : C(0), o4);
             return k;
         }
         const Sym2<C> pn = pi_neq<C>(m, drs, rs, ux, uy, uz, L::D);
-        add_eq<C, L::D, O3, XYZ>(k, C(1) - chi, drs, rs, ux, uy, uz);
-        add_eq<C, L::D, O3, XYZ>(k, chi, C(p.rho_ref_m1), rr, urx, ury, L::D == 3 ? urz : C(0));
-        add_neq<C, L::D, O3, XYZ>(k, om, ux, uy, uz, pn);
+        add_eq<C, L::D, O3, XYZ>(k, C(1) - chi, drs, rs, ux, uy, uz, o4);
+        add_eq<C, L::D, O3, XYZ>(k, chi, C(p.rho_ref_m1), rr, urx, ury, L::D == 3 ? urz : C(0), o4);
+        add_neq<C, L::D, O3, XYZ>(k, om, ux, uy, uz, pn, o4);
         return k;
     }
     const C rho = C(1) + m.dr;
@@ -263,12 +266,12 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
     const C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
     if (BGK) {
         // (1 - 1/tau) f^eq; the caller adds (1 - 1/tau) g
-        add_eq<C, L::D, O3, XYZ>(k, C(1) - om, m.dr, rho, ux, uy, uz);
+        add_eq<C, L::D, O3, XYZ>(k, C(1) - om, m.dr, rho, ux, uy, uz, o4);
         return k;
     }
     const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
-    add_eq<C, L::D, O3, XYZ>(k, C(1), m.dr, rho, ux, uy, uz);
-    add_neq<C, L::D, O3, XYZ>(k, om, ux, uy, uz, pn);
+    add_eq<C, L::D, O3, XYZ>(k, C(1), m.dr, rho, ux, uy, uz, o4);
+    add_neq<C, L::D, O3, XYZ>(k, om, ux, uy, uz, pn, o4);
     return k;
 }
 

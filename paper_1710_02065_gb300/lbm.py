@@ -68,6 +68,7 @@ _sig("lbm_set_launch", [_h, C.c_int, C.c_int])
 _sig("lbm_get_launch", [_h, _ip, _ip])
 _sig("lbm_set_staging", [_h, C.c_int, C.c_int, C.c_int])
 _sig("lbm_set_collision", [_h, C.c_int])
+_sig("lbm_set_hermite_order", [_h, C.c_int])
 _sig("lbm_pressure_mean", [_h, C.c_int])
 _sig("lbm_pressure_fluctuation", [_h, _dp, _dp])
 _sig("lbm_set_sponge_jet_reference", [_h] + [C.c_double] * 7)
@@ -103,7 +104,7 @@ EXPORTED = [
     "lbm_set_boundary", "lbm_set_pressure", "lbm_set_inlet_noise", "lbm_set_sponge", "lbm_set_radial_sponge", "lbm_set_state",
     "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_moments", "lbm_reduce",
     "lbm_probe", "lbm_sync", "lbm_info", "lbm_save", "lbm_load", "lbm_set_launch", "lbm_get_launch",
-    "lbm_set_staging", "lbm_get_staging", "lbm_set_collision", "lbm_set_sponge_jet_reference",
+    "lbm_set_staging", "lbm_get_staging", "lbm_set_collision", "lbm_set_sponge_jet_reference", "lbm_set_hermite_order",
     "lbm_pressure_mean", "lbm_pressure_fluctuation",
     "lbm_add_refinement_patch", "lbm_level_info", "lbm_force", "lbm_set_geometry_level", "lbm_set_state_level",
     "lbm_set_populations_level", "lbm_get_populations_level", "lbm_moments_level",
@@ -270,6 +271,10 @@ def lbm_pressure_fluctuation(h, dp_tilde=None, dp_mean=None):
     for a in (dp_tilde, dp_mean):
         assert a is None or (a.dtype == np.float64 and a.flags.c_contiguous)
     return _check(_lib.lbm_pressure_fluctuation(h, _d(dp_tilde), _d(dp_mean)), h)
+
+
+def lbm_set_hermite_order(h, order: int):
+    return _check(_lib.lbm_set_hermite_order(h, int(order)), h)
 
 
 def lbm_set_collision(h, model: int):

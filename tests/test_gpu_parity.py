@@ -260,6 +260,21 @@ def test_non_finite_state_is_reported():
     assert rc == lbm.LBM_EUNSTABLE
 
 
+@pytest.mark.parametrize("ux,rho,unstable", [(0.55, 1.0, False), (0.60, 1.0, True), (0.0, -0.1, True)])
+def test_supersonic_or_negative_density_is_reported(ux, rho, unstable):
+    """|u| >= c_s = 0.577 or rho <= 0 in one fluid cell makes lbm_reduce
+    return LBM_EUNSTABLE; a subsonic state passes."""
+    from paper_1710_02065_gb300 import lbm
+    n = (16, 8, 1)
+    r = np.ones(int(np.prod(n)))
+    u = np.zeros((r.size, 3))
+    r[37], u[37, 0] = rho, ux
+    c = Case("sonic", D2Q9, n, 0.8, rho0=r, u0=u)
+    s = to_gpu(c, PRECS["fp64"])
+    _, _, rc = s.reduce()
+    assert rc == (lbm.LBM_EUNSTABLE if unstable else lbm.LBM_OK)
+
+
 def test_checkpoint_resume_is_bit_identical(tmp_path):
     c = _boxed_case(D2Q9, seed=4)
     a = to_gpu(c, PRECS["fp32"])
@@ -716,3 +731,51 @@ def test_d3q27_taylor_green_parity(prec, tol):
     r, u, _ = s.moments()
     assert _normwise(r, r_ref) <= tol and _normwise(u, u_ref) <= tol
     s.close()
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+def test_d2q9_fourth_order_matches_oracle(prec):
+    """Optional fourth-order D2Q9 term (H_xxyy): every boundary rule, a solid,
+    noise, sponges, random populations, on every kernel; a 200-step acoustic
+    pulse started from the order-4 equilibrium."""
+    from paper_1710_02065_gb300 import lbm
+    _, _, _, w, _ = oracle.lattice(D2Q9)
+    c = _boxed_case(D2Q9, seed=17)
+    P, f = to_oracle(c)
+    P.order4 = 1
+    ref = P.run(f, 3)
+    P.order4 = 0
+    assert np.abs(P.run(f, 3) - ref).max() > 1e-8  # the term is active on this state
+    s = to_gpu(c, PRECS[prec])
+    lbm.lbm_set_hermite_order(s.h, 4)
+    s.step(3)
+    assert np.abs(s.populations() - ref).max() <= _pop_tol(prec, ref, w, 3)
+    s.close()
+    co = _open_box(D2Q9, (40, 12, 1), seed=23)
+    P, f = to_oracle(co)
+    P.order4 = 1
+    ref = P.run(f, 3)
+    for kind in KERNELS[prec]:
+        s = to_gpu(co, PRECS[prec])
+        lbm.lbm_set_hermite_order(s.h, 4)
+        use_kernel(s, kind)
+        s.step(3)
+        assert np.abs(s.populations() - ref).max() <= _pop_tol(prec, ref, w, 3), kind
+        s.close()
+    if prec in ("fp64", "fp32"):
+        tol = 1e-12 if prec == "fp64" else 1e-5
+        cp = acoustic_pulse(96)
+        P, _ = to_oracle(cp)
+        P.order4 = 1
+        f0 = P.equilibrium(cp.rho0, cp.u0)
+        ref = P.run(f0, 200)
+        r_ref, u_ref, _ = P.moments(ref)
+        s = lbm.Solver(D2Q9, cp.n, cp.tau, PRECS[prec])
+        lbm.lbm_set_hermite_order(s.h, 4)
+        s.set_state(cp.rho0, cp.u0)
+        s.step(200)
+        r, u, _ = s.moments()
+        assert _normwise(r, r_ref) <= tol and _normwise(u, u_ref) <= tol
+        with pytest.raises(lbm.LBMError):
+            lbm.lbm_add_refinement_patch(s.h, (10, 10, 0), (20, 20, 1))
+        s.close()
