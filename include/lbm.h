@@ -522,7 +522,7 @@ int lbm_server_stats(lbm_server_handle s, int *queued, int *running, size_t *byt
  *               fluid cells are counted
  *   out       : device pointer to 6 doubles, written in stream order:
  *               [sum rho, sum rho ux, sum rho uy, sum rho uz, fluid cells,
- *               non-finite cells]
+ *               unstable cells (non-finite, rho <= 0 or |u| >= c_s)]
  *   cuda_stream : stream to enqueue on (NULL: legacy default stream)
  * Asynchronous: synchronise the stream before reading out.  The first call on
  * a device looks up the scratch array's device address (once per device,

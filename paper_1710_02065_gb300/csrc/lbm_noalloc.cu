@@ -37,7 +37,7 @@ std::mutex g_mu;
 double *g_scratch_addr[MAX_DEVICES] = {};
 
 // Final pass: totals in the lbm_reduce convention,
-// out = [sum rho, sum rho ux, sum rho uy, sum rho uz, fluid cells, non-finite cells]
+// out = [sum rho, sum rho ux, sum rho uy, sum rho uz, fluid cells, unstable cells]
 __global__ void k_reduce_totals(int nblocks, const double *__restrict__ partial, double *__restrict__ out)
 {
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
