@@ -49,6 +49,8 @@ struct lbm_ctx {
     int sponge_w[6] = {0, 0, 0, 0, 0, 0};
     double sponge_chi[6] = {0, 0, 0, 0, 0, 0};
     double radial[6] = {0, 0, 0, 0, 0, 0};
+    float *chi_tab_f = nullptr;   // per-axis face-layer strength (nx + ny + nz), FP32
+    double *chi_tab_d = nullptr;  // the same in FP64
     bool ref_set = false;
     double rho_ref = 1.0, u_ref[3] = {0, 0, 0};
     uint64_t noise_seed = 0;
@@ -296,6 +298,51 @@ static size_t prec_bytes(int prec)
     return 0;
 }
 
+// Per-axis sponge strength of the face layers (Sec. II.C): for each
+// coordinate c of axis a, the max over the axis's two faces of
+// chi_max sigma(d), d = depth of c inside the layer (0 at its inner edge),
+// sigma(d) = 3125 (W - d) d^4 / (256 W^5).  Computed in FP64 on the host and
+// copied, in stream order, to the FP64 and FP32 device tables the kernels
+// read (so launches already queued keep their own values).
+static int upload_sponge_tables(lbm_ctx *h)
+{
+    const int total = h->n[0] + h->n[1] + h->n[2];
+    if (!h->chi_tab_d) {
+        if (cudaMalloc(&h->chi_tab_d, sizeof(double) * (size_t)total) != cudaSuccess ||
+            cudaMalloc(&h->chi_tab_f, sizeof(float) * (size_t)total) != cudaSuccess)
+            return LBM_ENOMEM;
+    }
+    std::vector<double> td((size_t)total, 0.0);
+    std::vector<float> tf((size_t)total, 0.0f);
+    int off = 0;
+    for (int a = 0; a < 3; ++a) {
+        for (int c = 0; c < h->n[a]; ++c) {
+            double v = 0.0;
+            for (int f = 2 * a; f <= 2 * a + 1; ++f) {
+                const int W = h->sponge_w[f];
+                if (W <= 0 || !(h->sponge_chi[f] > 0.0)) continue;
+                const int d = (f & 1) ? c - (h->n[a] - W) : W - 1 - c;
+                if (d < 0) continue;
+                const double dd = d, WW = W;
+                const double sig = 3125.0 * (WW - dd) * dd * dd * dd * dd / (256.0 * WW * WW * WW * WW * WW);
+                const double chi = h->sponge_chi[f] * sig;
+                if (chi > v) v = chi;
+            }
+            td[(size_t)(off + c)] = v;
+            tf[(size_t)(off + c)] = (float)v;
+        }
+        off += h->n[a];
+    }
+    if (cudaMemcpyAsync(h->chi_tab_d, td.data(), sizeof(double) * td.size(), cudaMemcpyHostToDevice, h->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(h->chi_tab_f, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice, h->stream) !=
+            cudaSuccess)
+        return LBM_ECUDA;
+    // pageable sources: the copies are staged before the calls return, but
+    // make the host buffers' lifetime independent of that
+    return cudaStreamSynchronize(h->stream) == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
 static void release(lbm_ctx *h)
 {
     if (!h) return;
@@ -306,6 +353,8 @@ static void release(lbm_ctx *h)
         if (h->prof_d[k]) cudaFree(h->prof_d[k]);
     if (h->red_d) cudaFree(h->red_d);
     if (h->err_d) cudaFree(h->err_d);
+    if (h->chi_tab_f) cudaFree(h->chi_tab_f);
+    if (h->chi_tab_d) cudaFree(h->chi_tab_d);
     if (h->rho_acc) cudaFree(h->rho_acc);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     for (FineLevel *F : h->levels) {
@@ -376,6 +425,11 @@ extern "C" int lbm_create(lbm_handle *out, int lattice, const int extents[3], do
         cudaGetLastError();
         release(h);
         return fail(nullptr, LBM_ENOMEM, "cudaMalloc of the error word failed");
+    }
+    if (upload_sponge_tables(h) != LBM_OK) {
+        cudaGetLastError();
+        release(h);
+        return fail(nullptr, LBM_ENOMEM, "allocating the sponge tables failed");
     }
     // rest state: rho = 1, u = 0 is g = f - w = 0 in every storage format
     for (int k = 0; k < 2; ++k)
@@ -573,7 +627,8 @@ extern "C" int lbm_set_sponge(lbm_handle h, int face, int width, double chi_max,
     if (width == 0) {
         h->sponge_w[face] = 0;
         h->sponge_chi[face] = 0.0;
-        return LBM_OK;
+        return upload_sponge_tables(h) == LBM_OK ? LBM_OK
+                                                 : fail(h, LBM_ECUDA, "uploading the sponge tables failed");
     }
     if (!(chi_max >= 0.0) || !(chi_max < 4.0 * h->tau))
         return fail(h, LBM_EINVAL, "chi_max = %g must be in [0, 4 tau = %g) for stability", chi_max, 4.0 * h->tau);
@@ -593,6 +648,7 @@ extern "C" int lbm_set_sponge(lbm_handle h, int face, int width, double chi_max,
     h->rho_ref = rho_ref;
     for (int a = 0; a < 3; ++a) h->u_ref[a] = ur[a];
     h->ref_set = true;
+    if (upload_sponge_tables(h) != LBM_OK) return fail(h, LBM_ECUDA, "uploading the sponge tables failed");
     return LBM_OK;
 }
 
@@ -751,6 +807,8 @@ static int build_params(lbm_ctx *h, StepParams &p)
         p.u_profile[f] = h->prof_d[f];
     }
     if (h->radial[4] > 0.0 && h->radial[5] > 0.0) p.any_sponge = 1;
+    p.chi_tab_f = h->chi_tab_f;
+    p.chi_tab_d = h->chi_tab_d;
     p.rho_ref = h->rho_ref;
     p.rho_ref_m1 = h->rho_ref - 1.0;
     for (int a = 0; a < 3; ++a) p.u_ref[a] = h->u_ref[a];

@@ -47,6 +47,11 @@ struct StepParams {
     double rho_face[6], rho_face_m1[6];  // density of a constant-pressure face (and minus 1)
     const double *u_profile[6];  // device, 3 doubles per face cell, or null
     double sponge_chi[6];
+    // sponge strength of the face layers per axis coordinate, max over the two
+    // faces of each axis: chi_x[0..nx), chi_y[nx..nx+ny), chi_z[nx+ny..);
+    // device tables filled by the host in FP64 (and rounded to FP32)
+    const float *chi_tab_f;
+    const double *chi_tab_d;
     double radial[6];  // circular / spherical layer: centre (3), r0, width W, chi_max; W = 0: none
     double rho_ref, rho_ref_m1, u_ref[3];  // rho_ref_m1 = rho_ref - 1
     uint64_t noise_seed;
@@ -109,32 +114,30 @@ inline void set_bases(StepParams &p, const void *fin, void *fout)
 
 // ---------------------------------------------------------------------------
 // Sponge strength chi = chi_max sigma(d), maximum over the layers (Sec. II.C).
-// The y/z layers are uniform along a row; only the x layers vary along it.
+// The face layers come from the per-axis tables (the y/z layers are uniform
+// along a row; only the x layers vary along it); the circular layer is
+// evaluated per cell.
 // ---------------------------------------------------------------------------
-template <class L, class C>
-__device__ __forceinline__ C chi_face(const StepParams &p, int f, int coord)
+template <class C>
+__device__ __forceinline__ C chi_tab(const StepParams &p, int k);
+template <>
+__device__ __forceinline__ float chi_tab<float>(const StepParams &p, int k)
 {
-    const int W = p.sponge_w[f];
-    if (W <= 0) return C(0);
-    const int a = f >> 1;
-    const int d = (f & 1) ? coord - (p.n[a] - W) : W - 1 - coord;
-    if (d < 0) return C(0);
-    return C(p.sponge_chi[f]) * sigma<C>(C(d), C(W));
+    return __ldg(p.chi_tab_f + k);
+}
+template <>
+__device__ __forceinline__ double chi_tab<double>(const StepParams &p, int k)
+{
+    return __ldg(p.chi_tab_d + k);
 }
 
 template <class L, class C>
 __device__ __forceinline__ C chi_row(const StepParams &p, int y, int z)
 {
-    C chi = C(0);
-    if (!p.any_sponge) return chi;
-    C v = chi_face<L, C>(p, 2, y);
-    chi = v > chi ? v : chi;
-    v = chi_face<L, C>(p, 3, y);
-    chi = v > chi ? v : chi;
+    if (!p.any_sponge) return C(0);
+    C chi = chi_tab<C>(p, p.n[0] + y);
     if (L::D == 3) {
-        v = chi_face<L, C>(p, 4, z);
-        chi = v > chi ? v : chi;
-        v = chi_face<L, C>(p, 5, z);
+        const C v = chi_tab<C>(p, p.n[0] + p.n[1] + z);
         chi = v > chi ? v : chi;
     }
     return chi;
@@ -144,9 +147,7 @@ template <class L, class C>
 __device__ __forceinline__ C chi_cell(const StepParams &p, C row, int x, int y, int z)
 {
     if (!p.any_sponge) return row;
-    C v = chi_face<L, C>(p, 0, x);
-    row = v > row ? v : row;
-    v = chi_face<L, C>(p, 1, x);
+    C v = chi_tab<C>(p, x);
     row = v > row ? v : row;
     if (p.radial[4] > 0.0) {
         // circular layer: the profile up to its maximum at r0 + 0.8 W, chi_max beyond

@@ -1,13 +1,15 @@
 // step_vec.cuh -- vectorised fused stream + collide kernel (same update as
 // step.cuh) for lattices without a cell-type mask.
 //
-// Each thread owns V consecutive cells of one x row and moves them with one
-// V-wide load per direction (128-bit for FP32 V = 4 and FP64 V = 2; 64-bit for
-// FP16/BF16 V = 4).  Populations streamed along x (xi_x = +-1) are the same
-// aligned vector shifted by one cell: the missing end element comes from the
-// neighbouring lane by a warp shuffle, or, at a warp's first / last lane, from
-// one scalar load.  Stores are aligned V-wide vectors of the thread's own
-// cells.  Boundary roles are the ones of step.cuh: a node on a non-periodic
+// Each thread owns V consecutive cells of one x row.  Populations with
+// xi_x = 0 move as one aligned V-wide load per direction (128-bit for FP32
+// V = 4 and FP64 V = 2; 32-bit for FP16/BF16 V = 2).  Populations streamed
+// along x (xi_x = +-1) sit one cell off that alignment: they are read as V
+// scalar loads of the shifted cells (the sectors are the ones the warp's
+// aligned loads touch, so DRAM traffic is unchanged; measured on GB300 this
+// beats completing the aligned vector by a warp shuffle plus a scalar load
+// at the warp's edge lanes).  Stores are aligned V-wide vectors of the
+// thread's own cells.  Boundary roles are the ones of step.cuh: a node on a non-periodic
 // y/z face streams the row of its inward neighbour (uniform for a thread); a
 // node on a non-periodic x face takes the streamed populations of its x
 // neighbour, which lives in the same thread.
@@ -142,17 +144,15 @@ struct VecIO<__nv_bfloat16, 4> {
 // Requires: no cell-type mask, nx % V == 0.
 // ---------------------------------------------------------------------------
 // One thread's V cells of a row (x0raw = first cell, a multiple of V); the
-// 32 lanes of a warp hold consecutive V-cell groups of the same row.  Lanes
-// past the row end load wrapped data for their neighbours' shuffles and
-// store nothing.
+// lanes of a warp hold consecutive V-cell groups of the same row.  Lanes past
+// the row end do nothing.
 template <class L, class S, class C, int V>
 __device__ __forceinline__ void update_vec(const StepParams &p, const char *const *in, char *const *out, int x0raw,
                                            int y, int z)
 {
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
-    const int lane = threadIdx.x & 31;
-    const bool active = x0raw < nx;
-    const int x0 = x0raw % nx;  // idle lanes load a wrapped, valid vector
+    if (x0raw >= nx) return;  // lanes past the row end
+    const int x0 = x0raw;
     const unsigned nxy = (unsigned)nx * ny;
 
     // rows streamed from (uniform per thread): inward neighbour on non-periodic y/z faces
@@ -177,27 +177,23 @@ __device__ __forceinline__ void update_vec(const StepParams &p, const char *cons
         const int Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
         const int Z = L::D == 2 ? 0 : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
         const S *row = (const S *)in[i] + ((unsigned)nx * Y + nxy * Z);
-        C v[V];
-        VecIO<S, V>::ld(row + x0, v);
         if (L::cx(i) == 0) {
+            C v[V];
+            VecIO<S, V>::ld(row + x0, v);
 #pragma unroll
             for (int k = 0; k < V; ++k) g[i][k] = v[k];
         } else if (L::cx(i) > 0) {
-            // f_i(x) = f*_i(x - 1): shift right, first element from the left neighbour
-            C left = __shfl_up_sync(0xffffffffu, v[V - 1], 1);
-            if (lane == 0) left = Store<S>::ld(row + xl);
-            g[i][0] = left;
+            // f_i(x) = f*_i(x - 1): cells x0 - 1 (wrapped) .. x0 + V - 2
+            g[i][0] = Store<S>::ld(row + xl);
 #pragma unroll
-            for (int k = 1; k < V; ++k) g[i][k] = v[k - 1];
+            for (int k = 1; k < V; ++k) g[i][k] = Store<S>::ld(row + x0 + k - 1);
         } else {
-            C right = __shfl_down_sync(0xffffffffu, v[0], 1);
-            if (lane == 31) right = Store<S>::ld(row + xr);
+            // f_i(x) = f*_i(x + 1): cells x0 + 1 .. x0 + V (wrapped)
 #pragma unroll
-            for (int k = 0; k < V - 1; ++k) g[i][k] = v[k + 1];
-            g[i][V - 1] = right;
+            for (int k = 0; k < V - 1; ++k) g[i][k] = Store<S>::ld(row + x0 + k + 1);
+            g[i][V - 1] = Store<S>::ld(row + xr);
         }
     }
-    if (!active) return;
 
     // non-periodic x: boundary nodes take their x neighbour's streamed populations
     const bool xlo = !p.periodic[0] && x0 == 0, xhi = !p.periodic[0] && x0 + V == nx;
