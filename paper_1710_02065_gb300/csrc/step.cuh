@@ -230,7 +230,7 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
     if (chi > C(0)) {
         // sponge: damped moments rho*, rho* u* (n = m = 1/2), then
         // f* = (1 - chi) feqH(rho*, u*) + chi feqH(rho_ref, u_ref) + (1 - 1/tau) fneqH
-        const C h = C(1) / (C(1) + C(0.5) * chi);
+        const C h = recip(C(1) + C(0.5) * chi);
         const C rr = C(p.rho_ref);
         C urx = C(p.u_ref[0]), ury = C(p.u_ref[1]), urz = C(p.u_ref[2]);
         if (L::D == 3 && cx >= p.jet_x_layer) {
