@@ -218,7 +218,10 @@ int lbm_set_radial_sponge(lbm_handle h, const double center[3], double r0, doubl
 /*
  * lbm_set_state -- initialise every cell to feqH(rho, u) (Eq. eqH).
  *   rho : ncell doubles; u : 3*ncell doubles, per cell (ux, uy, uz) (host).
- * Resets the step counter to 0.
+ * Resets the step counter to 0.  The values are checked on the device while
+ * the field is written: LBM_EINVAL names the first cell whose rho is not
+ * finite and > 0 (or, 2D, whose u_z is not 0), and the field is then
+ * unspecified until it is set again.
  */
 int lbm_set_state(lbm_handle h, const double *rho, const double *u);
 
@@ -343,6 +346,17 @@ int lbm_set_hermite_order(lbm_handle h, int order);
 #define LBM_COLLISION_RR 0
 #define LBM_COLLISION_BGK 1
 int lbm_set_collision(lbm_handle h, int model);
+
+/*
+ * lbm_set_transfer_staging -- bound on the device memory that host transfers
+ * use.  lbm_set_state, lbm_set_populations, lbm_get_populations and
+ * lbm_moments (and their per-level forms) move fields through one device
+ * staging buffer per handle, in chunks of whole cells; it is allocated on
+ * first use, holds min(max_bytes, what one field needs) bytes and is freed
+ * with the handle.  Default 256 MiB; max_bytes must be >= 1024.  Transfers
+ * synchronise the stream once, at the end of the call.
+ */
+int lbm_set_transfer_staging(lbm_handle h, size_t max_bytes);
 
 /*
  * lbm_set_staging -- the row-staged update kernel (a tuning knob; same update

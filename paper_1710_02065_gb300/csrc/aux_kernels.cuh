@@ -3,7 +3,7 @@
 //   k_init_eq     : f = feqH(rho, u)  (Eq. eqH) into both lattices
 //   k_set_dir     : one direction of a caller field, f_i - w_i, into both lattices
 //   k_get_dir     : one direction of the stored field as plain FP64 f_i
-//   k_moments     : rho, u, Pi^neq per cell in FP64 (Eq. moments, Sec. II.A)
+//   k_moments     : rho, u, Pi^neq per cell, FP64 outputs (Eq. moments, Sec. II.A)
 //   k_reduce      : FP64 per-block totals of rho - 1, rho u, fluid count and
 //                   unstable count (non-finite, rho <= 0 or |u| >= c_s; warp
 //                   shuffles, then a fixed-order pass)
@@ -26,17 +26,28 @@ __device__ __forceinline__ double weight_rt(int i)
     return w;
 }
 
+// The host-transfer kernels work on cells c0 .. c0 + n - 1 of an N-cell
+// field (direction-major, stride N), with their host-side arrays staged for
+// just those cells (index t = cell - c0), so that transfers go through a
+// bounded staging buffer in chunks.
+
+// bad (nullable): lowest index of a cell whose rho is not finite and > 0, or
+// (2D) whose u_z is not 0; such cells are still written
 template <class L, class S>
-__global__ void k_init_eq(int64_t N, const double *__restrict__ rho, const double *__restrict__ u,
-                          S *__restrict__ f0, S *__restrict__ f1, int order4)
+__global__ void k_init_eq(int64_t N, int64_t c0, int64_t n, const double *__restrict__ rho,
+                          const double *__restrict__ u, S *__restrict__ f0, S *__restrict__ f1, int order4,
+                          unsigned long long *__restrict__ bad)
 {
     using C = typename StoreC<S>::C;  // FP32 arithmetic for FP32/FP16/BF16 storage
-    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (cell >= N) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t cell = c0 + t;
+    const double r = rho[t];
+    if (bad && (!(r > 0.0) || !isfinite(r) || (L::D == 2 && u[3 * t + 2] != 0.0)))
+        atomicMin(bad, (unsigned long long)cell);
     Coef<C> k{};
-    add_eq<C, L::D, true, full_third_order<L>()>(k, C(1), C(rho[cell] - 1.0), C(rho[cell]), C(u[3 * cell]),
-                                                  C(u[3 * cell + 1]), L::D == 3 ? C(u[3 * cell + 2]) : C(0),
-                                                  order4 != 0);
+    add_eq<C, L::D, true, full_third_order<L>()>(k, C(1), C(r - 1.0), C(r), C(u[3 * t]), C(u[3 * t + 1]),
+                                                  L::D == 3 ? C(u[3 * t + 2]) : C(0), order4 != 0);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const S v = Store<S>::from(rebuild<L, C>(k, i));
@@ -46,22 +57,23 @@ __global__ void k_init_eq(int64_t N, const double *__restrict__ rho, const doubl
 }
 
 template <class L, class S>
-__global__ void k_set_dir(int64_t N, int i, const double *__restrict__ src, S *__restrict__ f0,
-                          S *__restrict__ f1)
+__global__ void k_set_dir(int64_t N, int64_t c0, int64_t n, int i, const double *__restrict__ src,
+                          S *__restrict__ f0, S *__restrict__ f1)
 {
-    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (cell >= N) return;
-    const S v = Store<S>::from(src[cell] - weight_rt<L>(i));
-    f0[(int64_t)i * N + cell] = v;
-    f1[(int64_t)i * N + cell] = v;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const S v = Store<S>::from(src[t] - weight_rt<L>(i));
+    f0[(int64_t)i * N + c0 + t] = v;
+    f1[(int64_t)i * N + c0 + t] = v;
 }
 
 template <class L, class S>
-__global__ void k_get_dir(int64_t N, int i, const S *__restrict__ f, double *__restrict__ dst)
+__global__ void k_get_dir(int64_t N, int64_t c0, int64_t n, int i, const S *__restrict__ f,
+                          double *__restrict__ dst)
 {
-    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (cell >= N) return;
-    dst[cell] = (double)Store<S>::ld(f + (int64_t)i * N + cell) + weight_rt<L>(i);
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    dst[t] = (double)Store<S>::ld(f + (int64_t)i * N + c0 + t) + weight_rt<L>(i);
 }
 
 template <class L, class S>
@@ -72,31 +84,37 @@ __device__ __forceinline__ void load_cell_fp64(const S *__restrict__ f, int64_t 
     for (int i = 0; i < L::Q; ++i) g[i] = (double)Store<S>::ld(f + (int64_t)i * N + cell);
 }
 
+// Moments in the kernel's compute type (FP32 for FP32/FP16/BF16 storage,
+// whose values carry FP32 precision at most; FP64 for FP64 storage), stored
+// as FP64: rho = 1 + dr keeps dr's relative precision.
 template <class L, class S>
-__global__ void k_moments(int64_t N, const S *__restrict__ f, double *__restrict__ rho,
+__global__ void k_moments(int64_t N, int64_t c0, int64_t n, const S *__restrict__ f, double *__restrict__ rho,
                           double *__restrict__ u, double *__restrict__ pn)
 {
-    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (cell >= N) return;
-    double g[L::Q];
-    load_cell_fp64<L, S>(f, N, cell, g);
-    const Mom<double> m = moments<L, double>(g);
-    const double r = 1.0 + m.dr;
-    const double ux = m.jx / r, uy = m.jy / r, uz = L::D == 3 ? m.jz / r : 0.0;
-    if (rho) rho[cell] = r;
+    using C = typename StoreC<S>::C;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int64_t cell = c0 + t;
+    C g[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell);
+    const Mom<C> m = moments<L, C>(g);
+    const C r = C(1) + m.dr;
+    const C ux = m.jx / r, uy = m.jy / r, uz = L::D == 3 ? m.jz / r : C(0);
+    if (rho) rho[t] = 1.0 + (double)m.dr;
     if (u) {
-        u[3 * cell] = ux;
-        u[3 * cell + 1] = uy;
-        u[3 * cell + 2] = uz;
+        u[3 * t] = ux;
+        u[3 * t + 1] = uy;
+        u[3 * t + 2] = uz;
     }
     if (pn) {
-        const Sym2<double> p = pi_neq<double>(m, m.dr, r, ux, uy, uz, L::D);
-        pn[6 * cell + 0] = p.xx;
-        pn[6 * cell + 1] = p.xy;
-        pn[6 * cell + 2] = p.xz;
-        pn[6 * cell + 3] = p.yy;
-        pn[6 * cell + 4] = p.yz;
-        pn[6 * cell + 5] = p.zz;
+        const Sym2<C> p = pi_neq<C>(m, m.dr, r, ux, uy, uz, L::D);
+        pn[6 * t + 0] = p.xx;
+        pn[6 * t + 1] = p.xy;
+        pn[6 * t + 2] = p.xz;
+        pn[6 * t + 3] = p.yy;
+        pn[6 * t + 4] = p.yz;
+        pn[6 * t + 5] = p.zz;
     }
 }
 
@@ -109,27 +127,36 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(int64_t N, const S *__rest
                                                       const uint8_t *__restrict__ solid,
                                                       double *__restrict__ partial)
 {
+    // Per-cell moments in the compute type (FP32 for FP32/FP16/BF16 storage,
+    // whose values carry FP32 precision at most; FP64 for FP64 storage), the
+    // running totals in FP64: GB300's FP64 rate is a small fraction of its
+    // FP32 rate, and FP64 per-cell sums made this pass ALU-bound.
+    using C = typename StoreC<S>::C;
     double acc[RED_FIELDS] = {0, 0, 0, 0, 0, 0};
+    int fluid = 0, unstable = 0;
     for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < N;
          cell += (int64_t)gridDim.x * blockDim.x) {
         if (solid && (solid[cell] & MASK_TYPE)) continue;  // fluid cells only
-        double g[L::Q];
-        load_cell_fp64<L, S>(f, N, cell, g);
+        C g[L::Q];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell);
         bool finite = true;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) finite = finite && isfinite(g[i]);
-        const Mom<double> m = moments<L, double>(g);
+        const Mom<C> m = moments<L, C>(g);
         if (finite) {
-            acc[0] += m.dr;
-            acc[1] += m.jx;
-            acc[2] += m.jy;
-            acc[3] += m.jz;
+            acc[0] += (double)m.dr;
+            acc[1] += (double)m.jx;
+            acc[2] += (double)m.jy;
+            acc[3] += (double)m.jz;
         }
         // unstable: non-finite, non-positive density, or |u| >= c_s
-        const double rho = 1.0 + m.dr, j2 = m.jx * m.jx + m.jy * m.jy + m.jz * m.jz;
-        if (!finite || !(rho > 0.0) || !(j2 < rho * rho * (1.0 / 3.0))) acc[5] += 1.0;
-        acc[4] += 1.0;
+        const C rho = C(1) + m.dr, j2 = m.jx * m.jx + m.jy * m.jy + m.jz * m.jz;
+        if (!finite || !(rho > C(0)) || !(j2 < rho * rho * C(1.0 / 3.0))) ++unstable;
+        ++fluid;
     }
+    acc[4] = fluid;
+    acc[5] = unstable;
     // warp, then block, in a fixed order
     __shared__ double sh[RED_BLOCK / 32][RED_FIELDS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

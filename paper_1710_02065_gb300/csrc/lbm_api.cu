@@ -1,6 +1,7 @@
 // lbm_api.cu -- host runtime behind include/lbm.h: handle, validation,
 // device memory, launches.  Every numerical step runs in the kernels of
 // step.cuh / aux_kernels.cuh; this file only moves arguments.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -68,6 +69,13 @@ struct lbm_ctx {
     double *rho_acc = nullptr;  // running sum of rho per cell (temporal mean of p), or null
     int64_t rho_count = 0;
     double *red_d = nullptr;  // reduction partials + result
+    // bounded device staging of host transfers (set/get state, populations,
+    // moments), allocated on first use, at most kStageBytes; bad_d: lowest
+    // index of an invalid cell found by the state upload
+    double *stage_d = nullptr;
+    size_t stage_bytes = 0;
+    size_t stage_max = size_t(256) << 20;
+    unsigned long long *bad_d = nullptr;
     int red_blocks = 0;
     std::vector<uint8_t> user_mask;  // caller's cell types (host copy); empty: none
     std::vector<FineLevel *> levels;  // refined levels 1, 2, ... (each inside the previous one)
@@ -169,34 +177,36 @@ static unsigned grid1(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 template <class L, class S>
 struct InitEq {
-    static cudaError_t run(cudaStream_t st, int64_t N, const double *rho, const double *u, void *f0,
-                           void *f1, int order4)
+    static cudaError_t run(cudaStream_t st, int64_t N, int64_t c0, int64_t n, const double *rho, const double *u,
+                           void *f0, void *f1, int order4, unsigned long long *bad)
     {
-        k_init_eq<L, S><<<grid1(N, 256), 256, 0, st>>>(N, rho, u, (S *)f0, (S *)f1, order4);
+        k_init_eq<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, rho, u, (S *)f0, (S *)f1, order4, bad);
         return cudaGetLastError();
     }
 };
 template <class L, class S>
 struct SetDir {
-    static cudaError_t run(cudaStream_t st, int64_t N, int i, const double *src, void *f0, void *f1)
+    static cudaError_t run(cudaStream_t st, int64_t N, int64_t c0, int64_t n, int i, const double *src, void *f0,
+                           void *f1)
     {
-        k_set_dir<L, S><<<grid1(N, 256), 256, 0, st>>>(N, i, src, (S *)f0, (S *)f1);
+        k_set_dir<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, i, src, (S *)f0, (S *)f1);
         return cudaGetLastError();
     }
 };
 template <class L, class S>
 struct GetDir {
-    static cudaError_t run(cudaStream_t st, int64_t N, int i, const void *f, double *dst)
+    static cudaError_t run(cudaStream_t st, int64_t N, int64_t c0, int64_t n, int i, const void *f, double *dst)
     {
-        k_get_dir<L, S><<<grid1(N, 256), 256, 0, st>>>(N, i, (const S *)f, dst);
+        k_get_dir<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, i, (const S *)f, dst);
         return cudaGetLastError();
     }
 };
 template <class L, class S>
 struct Moments {
-    static cudaError_t run(cudaStream_t st, int64_t N, const void *f, double *rho, double *u, double *pn)
+    static cudaError_t run(cudaStream_t st, int64_t N, int64_t c0, int64_t n, const void *f, double *rho,
+                           double *u, double *pn)
     {
-        k_moments<L, S><<<grid1(N, 256), 256, 0, st>>>(N, (const S *)f, rho, u, pn);
+        k_moments<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, (const S *)f, rho, u, pn);
         return cudaGetLastError();
     }
 };
@@ -354,6 +364,8 @@ static void release(lbm_ctx *h)
     if (h->red_d) cudaFree(h->red_d);
     if (h->err_d) cudaFree(h->err_d);
     if (h->chi_tab_f) cudaFree(h->chi_tab_f);
+    if (h->stage_d) cudaFree(h->stage_d);
+    if (h->bad_d) cudaFree(h->bad_d);
     if (h->chi_tab_d) cudaFree(h->chi_tab_d);
     if (h->rho_acc) cudaFree(h->rho_acc);
     if (h->graph) cudaGraphExecDestroy(h->graph);
@@ -689,27 +701,76 @@ extern "C" int lbm_set_radial_sponge(lbm_handle h, const double center[3], doubl
 // ---------------------------------------------------------------------------
 // State
 // ---------------------------------------------------------------------------
+// Host transfers go through one device staging buffer per handle, in chunks
+// of whole cells, so that moving a field in or out never allocates more than
+// h->stage_max (nor the size of the field) on the device.  Chunks reuse the
+// buffer in stream order; the call synchronises once at the end.
+static int stage(lbm_ctx *h, int64_t N, size_t bytes_per_cell, int64_t &chunk)
+{
+    const size_t want = std::min(h->stage_max, (size_t)N * bytes_per_cell);
+    if (h->stage_bytes < want || h->stage_bytes > h->stage_max) {
+        if (h->stage_d) {
+            CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+            cudaFree(h->stage_d);
+            h->stage_d = nullptr;
+            h->stage_bytes = 0;
+        }
+        const cudaError_t e = cudaMalloc(&h->stage_d, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->stage_d = nullptr;
+            return fail(h, LBM_ENOMEM, "cudaMalloc of %zu bytes of transfer staging: %s", want, cudaGetErrorString(e));
+        }
+        h->stage_bytes = want;
+    }
+    chunk = (int64_t)(h->stage_bytes / bytes_per_cell);
+    if (chunk > N) chunk = N;
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_transfer_staging(lbm_handle h, size_t max_bytes)
+{
+    CHECK_HANDLE(h);
+    if (max_bytes < 1024) return fail(h, LBM_EINVAL, "max_bytes = %zu must be >= 1024", max_bytes);
+    h->stage_max = max_bytes;
+    return LBM_OK;
+}
+
 static int set_state_grid(lbm_ctx *h, const GridRef &g, const double *rho, const double *u)
 {
     if (!rho || !u) return fail(h, LBM_EINVAL, "rho and u are required");
     const int64_t N = g.ncell;
-    for (int64_t c = 0; c < N; ++c) {
-        if (!(rho[c] > 0.0) || !std::isfinite(rho[c]))
-            return fail(h, LBM_EINVAL, "rho[%lld] = %g must be finite and > 0", (long long)c, rho[c]);
-        if (h->d == 2 && u[3 * c + 2] != 0.0) return fail(h, LBM_EINVAL, "2D lattice: u_z must be 0");
+    int64_t chunk = 0;
+    int rc = stage(h, N, 4 * sizeof(double), chunk);
+    if (rc != LBM_OK) return rc;
+    if (!h->bad_d) CUDA_TRY(h, cudaMalloc(&h->bad_d, sizeof(unsigned long long)));
+    // the values are checked on the device while the field is written
+    cudaError_t e = cudaMemsetAsync(h->bad_d, 0xff, sizeof(unsigned long long), h->stream);
+    double *rd = h->stage_d, *ud = h->stage_d + chunk;
+    for (int64_t c0 = 0; c0 < N && e == cudaSuccess; c0 += chunk) {
+        const int64_t n = std::min(chunk, N - c0);
+        e = cudaMemcpyAsync(rd, rho + c0, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ud, u + 3 * c0, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = dispatch<InitEq>(h->lattice, h->prec, h->stream, N, c0, n, (const double *)rd, (const double *)ud,
+                                 g.f[0], g.f[1], h->order4, h->bad_d);
+        h->launches += 1;
     }
-    double *buf = nullptr;
-    CUDA_TRY(h, cudaMalloc(&buf, sizeof(double) * 4 * (size_t)N));
-    cudaError_t e = cudaMemcpyAsync(buf, rho, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, h->stream);
+    unsigned long long bad = ~0ull;
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(buf + N, u, sizeof(double) * 3 * (size_t)N, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess)
-        e = dispatch<InitEq>(h->lattice, h->prec, h->stream, N, buf, buf + N, g.f[0], g.f[1], h->order4);
+        e = cudaMemcpyAsync(&bad, h->bad_d, sizeof bad, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(buf);
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "set state: %s", cudaGetErrorString(e));
-    h->launches += 1;
     *g.cur = 0;
+    if (bad != ~0ull) {
+        const int64_t c = (int64_t)bad;
+        if (!(rho[c] > 0.0) || !std::isfinite(rho[c]))
+            return fail(h, LBM_EINVAL, "rho[%lld] = %g must be finite and > 0 (the field is unspecified until set again)",
+                        (long long)c, rho[c]);
+        return fail(h, LBM_EINVAL, "2D lattice: u_z must be 0 (cell %lld; the field is unspecified until set again)",
+                    (long long)c);
+    }
     return LBM_OK;
 }
 
@@ -717,16 +778,22 @@ static int set_pops_grid(lbm_ctx *h, const GridRef &g, const double *f)
 {
     if (!f) return fail(h, LBM_EINVAL, "f is null");
     const int64_t N = g.ncell;
-    double *buf = nullptr;
-    CUDA_TRY(h, cudaMalloc(&buf, sizeof(double) * (size_t)N));
+    int64_t chunk = 0;
+    int rc = stage(h, N, sizeof(double), chunk);
+    if (rc != LBM_OK) return rc;
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < h->q && e == cudaSuccess; ++i) {
-        e = cudaMemcpyAsync(buf, f + (size_t)i * N, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = dispatch<SetDir>(h->lattice, h->prec, h->stream, N, i, (const double *)buf, g.f[0], g.f[1]);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        h->launches += 1;
+        for (int64_t c0 = 0; c0 < N && e == cudaSuccess; c0 += chunk) {
+            const int64_t n = std::min(chunk, N - c0);
+            e = cudaMemcpyAsync(h->stage_d, f + (size_t)i * N + c0, sizeof(double) * (size_t)n,
+                                cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess)
+                e = dispatch<SetDir>(h->lattice, h->prec, h->stream, N, c0, n, i, (const double *)h->stage_d,
+                                     g.f[0], g.f[1]);
+            h->launches += 1;
+        }
     }
-    cudaFree(buf);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "set populations: %s", cudaGetErrorString(e));
     *g.cur = 0;
     return LBM_OK;
@@ -736,17 +803,21 @@ static int get_pops_grid(lbm_ctx *h, const GridRef &g, double *f)
 {
     if (!f) return fail(h, LBM_EINVAL, "f is null");
     const int64_t N = g.ncell;
-    double *buf = nullptr;
-    CUDA_TRY(h, cudaMalloc(&buf, sizeof(double) * (size_t)N));
+    int64_t chunk = 0;
+    int rc = stage(h, N, sizeof(double), chunk);
+    if (rc != LBM_OK) return rc;
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < h->q && e == cudaSuccess; ++i) {
-        e = dispatch<GetDir>(h->lattice, h->prec, h->stream, N, i, (const void *)g.f[*g.cur], buf);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(f + (size_t)i * N, buf, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        h->launches += 1;
+        for (int64_t c0 = 0; c0 < N && e == cudaSuccess; c0 += chunk) {
+            const int64_t n = std::min(chunk, N - c0);
+            e = dispatch<GetDir>(h->lattice, h->prec, h->stream, N, c0, n, i, (const void *)g.f[*g.cur], h->stage_d);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(f + (size_t)i * N + c0, h->stage_d, sizeof(double) * (size_t)n,
+                                    cudaMemcpyDeviceToHost, h->stream);
+            h->launches += 1;
+        }
     }
-    cudaFree(buf);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "get populations: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
@@ -1462,20 +1533,27 @@ static int moments_grid(lbm_ctx *h, const GridRef &g, double *rho, double *u, do
 {
     if (!rho && !u && !pi_neq) return LBM_OK;
     const int64_t N = g.ncell;
-    double *buf = nullptr;
-    CUDA_TRY(h, cudaMalloc(&buf, sizeof(double) * 10 * (size_t)N));
-    double *rd = buf, *ud = buf + N, *pd = buf + 4 * N;
-    cudaError_t e = dispatch<Moments>(h->lattice, h->prec, h->stream, N, (const void *)g.f[*g.cur],
-                                      rho ? rd : nullptr, u ? ud : nullptr, pi_neq ? pd : nullptr);
-    if (e == cudaSuccess && rho)
-        e = cudaMemcpyAsync(rho, rd, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess && u)
-        e = cudaMemcpyAsync(u, ud, sizeof(double) * 3 * (size_t)N, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess && pi_neq)
-        e = cudaMemcpyAsync(pi_neq, pd, sizeof(double) * 6 * (size_t)N, cudaMemcpyDeviceToHost, h->stream);
+    const size_t per = sizeof(double) * ((rho ? 1 : 0) + (u ? 3 : 0) + (pi_neq ? 6 : 0));
+    int64_t chunk = 0;
+    int rc = stage(h, N, per, chunk);
+    if (rc != LBM_OK) return rc;
+    double *rd = rho ? h->stage_d : nullptr;
+    double *ud = u ? h->stage_d + (rho ? chunk : 0) : nullptr;
+    double *pd = pi_neq ? h->stage_d + (rho ? chunk : 0) + (u ? 3 * chunk : 0) : nullptr;
+    cudaError_t e = cudaSuccess;
+    for (int64_t c0 = 0; c0 < N && e == cudaSuccess; c0 += chunk) {
+        const int64_t n = std::min(chunk, N - c0);
+        e = dispatch<Moments>(h->lattice, h->prec, h->stream, N, c0, n, (const void *)g.f[*g.cur], rd, ud, pd);
+        if (e == cudaSuccess && rho)
+            e = cudaMemcpyAsync(rho + c0, rd, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && u)
+            e = cudaMemcpyAsync(u + 3 * c0, ud, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess && pi_neq)
+            e = cudaMemcpyAsync(pi_neq + 6 * c0, pd, sizeof(double) * 6 * (size_t)n, cudaMemcpyDeviceToHost,
+                                h->stream);
+        h->launches += 1;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(buf);
-    h->launches += 1;
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "moments: %s", cudaGetErrorString(e));
     return LBM_OK;
 }

@@ -85,7 +85,8 @@ template <class L, class S>
 cudaError_t init_eq(const Request &r, const double *rho, const double *u, cudaStream_t st)
 {
     const int64_t N = r.ncell;
-    k_init_eq<L, S><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, rho, u, (S *)r.f[0], (S *)r.f[1], 0);
+    k_init_eq<L, S><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, 0, N, rho, u, (S *)r.f[0], (S *)r.f[1], 0,
+                                                                 nullptr);
     return cudaGetLastError();
 }
 
@@ -93,7 +94,7 @@ template <class L, class S>
 cudaError_t moments(const Request &r, int cur, double *rho, double *u, cudaStream_t st)
 {
     const int64_t N = r.ncell;
-    k_moments<L, S><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, (const S *)r.f[cur], rho, u, nullptr);
+    k_moments<L, S><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, 0, N, (const S *)r.f[cur], rho, u, nullptr);
     return cudaGetLastError();
 }
 

@@ -67,6 +67,7 @@ _sig("lbm_sync", [_h])
 _sig("lbm_set_launch", [_h, C.c_int, C.c_int])
 _sig("lbm_get_launch", [_h, _ip, _ip])
 _sig("lbm_set_staging", [_h, C.c_int, C.c_int, C.c_int])
+_sig("lbm_set_transfer_staging", [_h, C.c_size_t])
 _sig("lbm_set_collision", [_h, C.c_int])
 _sig("lbm_set_hermite_order", [_h, C.c_int])
 _sig("lbm_pressure_mean", [_h, C.c_int])
@@ -104,7 +105,7 @@ EXPORTED = [
     "lbm_set_boundary", "lbm_set_pressure", "lbm_set_inlet_noise", "lbm_set_sponge", "lbm_set_radial_sponge", "lbm_set_state",
     "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_moments", "lbm_reduce",
     "lbm_probe", "lbm_sync", "lbm_info", "lbm_save", "lbm_load", "lbm_set_launch", "lbm_get_launch",
-    "lbm_set_staging", "lbm_get_staging", "lbm_set_collision", "lbm_set_sponge_jet_reference", "lbm_set_hermite_order",
+    "lbm_set_staging", "lbm_get_staging", "lbm_set_transfer_staging", "lbm_set_collision", "lbm_set_sponge_jet_reference", "lbm_set_hermite_order",
     "lbm_pressure_mean", "lbm_pressure_fluctuation",
     "lbm_add_refinement_patch", "lbm_level_info", "lbm_force", "lbm_set_geometry_level", "lbm_set_state_level",
     "lbm_set_populations_level", "lbm_get_populations_level", "lbm_moments_level",
@@ -283,6 +284,11 @@ def lbm_set_collision(h, model: int):
 
 def lbm_set_staging(h, mode: int = -1, stages: int = 0, block: int = 0):
     return _check(_lib.lbm_set_staging(h, int(mode), int(stages), int(block)), h)
+
+
+def lbm_set_transfer_staging(h, max_bytes: int):
+    """Bound (bytes) on the device staging buffer of host transfers."""
+    return _check(_lib.lbm_set_transfer_staging(h, int(max_bytes)), h)
 
 
 def lbm_get_staging(h):
