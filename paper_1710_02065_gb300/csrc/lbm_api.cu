@@ -27,6 +27,7 @@ struct FineLevel {
     void *f[2] = {nullptr, nullptr};
     int cur = 0;
     uint8_t *mask_d = nullptr;           // ring fixed + user solids
+    bool has_solid = false;              // the mask holds solid cells
     std::vector<uint8_t> user_mask;      // user solids (host copy)
     RefineGeom geom{};                   // position in the parent level's nodes
     double *M[2] = {nullptr, nullptr};   // parent-side interface moments at t and t + 1
@@ -43,6 +44,7 @@ struct lbm_ctx {
     void *f[2] = {nullptr, nullptr};
     int cur = 0;
     uint8_t *solid_d = nullptr;
+    bool has_solid = false;  // level 0's mask holds solid cells (else only fixed ones)
     double *prof_d[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int kind[6] = {0, 0, 0, 0, 0, 0};
     double u_face[6][3] = {};
@@ -111,6 +113,12 @@ static GridRef level_grid(lbm_ctx *h, int k)
     return GridRef{{F->n[0], F->n[1], F->n[2]}, F->ncell, F->f, &F->cur, F->mask_d};
 }
 static double level_tau(lbm_ctx *h, int k) { return k == 0 ? h->tau : fine_level(h, k)->tau; }
+// The mask the interface kernels test for bounce-back links: null when the
+// level holds no solid cells (its fixed cells need no test there)
+static const uint8_t *links_mask(lbm_ctx *h, int k)
+{
+    return (k == 0 ? h->has_solid : fine_level(h, k)->has_solid) ? level_grid(h, k).mask : nullptr;
+}
 
 static thread_local std::string g_create_err;
 
@@ -515,6 +523,7 @@ static int upload_level_mask(lbm_ctx *h, int k)
     if (k == 0 && user.empty() && !has_child) {
         if (h->solid_d) cudaFree(h->solid_d);
         h->solid_d = nullptr;
+        h->has_solid = false;
         return LBM_OK;
     }
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -536,6 +545,9 @@ static int upload_level_mask(lbm_ctx *h, int k)
                 for (int x = c.X0 + 1; x < c.X0 + c.Wc; ++x) at(x, y, z) = LBM_CELL_FIXED;
     }
     add_near_solid(h, m, g.n);
+    bool any = false;
+    for (const uint8_t v : m) any = any || (v & MASK_TYPE) == MASK_SOLID;
+    (k == 0 ? h->has_solid : fine_level(h, k)->has_solid) = any;
     uint8_t *&dst = k == 0 ? h->solid_d : fine_level(h, k)->mask_d;
     if (!dst) CUDA_TRY(h, cudaMalloc(&dst, (size_t)g.ncell));
     CUDA_TRY(h, cudaMemcpyAsync(dst, m.data(), (size_t)g.ncell, cudaMemcpyHostToDevice, h->stream));
@@ -887,6 +899,7 @@ static int build_params(lbm_ctx *h, StepParams &p)
     p.noise_amp = h->noise_amp;
     p.omega = 1.0 - 1.0 / h->tau;
     p.solid = h->solid_d;
+    p.any_solid = h->has_solid ? 1 : 0;
     p.bgk = h->collision == LBM_COLLISION_BGK ? 1 : 0;
     p.order4 = h->order4;
     p.jet_x_layer = INT_MAX;
@@ -967,6 +980,7 @@ static void fine_params(lbm_ctx *h, int k, StepParams &p)
     p.omega = 1.0 - 1.0 / F->tau;
     p.jet_x_layer = INT_MAX;
     p.solid = F->mask_d;
+    p.any_solid = F->has_solid ? 1 : 0;
     set_bulk_box(p);
 }
 
@@ -984,19 +998,23 @@ static cudaError_t refine_kernels3(lbm_ctx *h, int k, int stage, int a_half)
     case 3: {  // plane moments at t = 0: local moments of the stored coarse field
         const int n = plane3_count(g);
         double *M = stage == 0 ? F->M[1 - F->mcur] : F->M[F->mcur];
-        k_plane_moments3<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], P.mask, stage == 0 ? 1 : 0, M);
+        k_plane_moments3<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], links_mask(h, k - 1),
+                                                            stage == 0 ? 1 : 0, M);
         break;
     }
     case 1: {  // fine shell at t + 1/2 (a_half = 1) or t + 1 (a_half = 0)
         const int n = shell3_count(g.nfx, g.nfy, g.nfz);
-        k_fill_shell3<S><<<grid1(n, 128), 128, 0, st>>>(g, F->M[F->mcur], F->M[1 - F->mcur], a_half ? 0.5 : 1.0,
-                                                         F->tau / (2.0 * tau_p), F->tau, (S *)F->f[F->cur]);
+        // 4 threads per shell node
+        k_fill_shell3<S><<<grid1(4 * (int64_t)n, 256), 256, 0, st>>>(
+            g, F->M[F->mcur], F->M[1 - F->mcur], a_half ? 0.5 : 1.0, F->tau / (2.0 * tau_p), F->tau,
+            (S *)F->f[F->cur]);
         break;
     }
     case 2: {  // covered coarse shell from the fine field; fine moments pulled from f(t + 1/2)
         const int n = shell3_count(g.Wc - 1, g.Hc - 1, g.Dc - 1);
-        k_restrict3<S><<<grid1(n, 64), 64, 0, st>>>(g, (const S *)F->f[1 - F->cur], F->mask_d, 2.0 * tau_p / F->tau,
-                                                     tau_p, (S *)P.f[*P.cur]);
+        // one warp per covered coarse node (one lane per filter point)
+        k_restrict3<S><<<grid1(32 * (int64_t)n, 256), 256, 0, st>>>(
+            g, (const S *)F->f[1 - F->cur], links_mask(h, k), 2.0 * tau_p / F->tau, tau_p, (S *)P.f[*P.cur]);
         break;
     }
     }
@@ -1021,7 +1039,8 @@ static cudaError_t refine_kernels(lbm_ctx *h, int k, int stage, int a_half)
     switch (stage) {
     case 0: {  // coarse line moments at t + 1 from the pre-step coarse field
         const int n = line_count(g);
-        k_line_moments<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], P.mask, 1, F->M[1 - F->mcur]);
+        k_line_moments<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], links_mask(h, k - 1), 1,
+                                                          F->M[1 - F->mcur]);
         break;
     }
     case 1: {  // fine ring at t + 1/2 (a_half = 1) or t + 1 (a_half = 0)
@@ -1032,13 +1051,15 @@ static cudaError_t refine_kernels(lbm_ctx *h, int k, int stage, int a_half)
     }
     case 2: {  // covered coarse ring from the fine field; pre-collision fine moments pulled from f(t + 1/2)
         const int n = 2 * (g.Wc - 1) + 2 * (g.Hc - 3);
-        k_restrict<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)F->f[1 - F->cur], F->mask_d, 2.0 * tau_p / F->tau,
+        k_restrict<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)F->f[1 - F->cur], links_mask(h, k),
+                                                      2.0 * tau_p / F->tau,
                                                      tau_p, (S *)P.f[*P.cur]);
         break;
     }
     case 3: {  // line moments at t = 0: local moments of the stored coarse field
         const int n = line_count(g);
-        k_line_moments<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], P.mask, 0, F->M[F->mcur]);
+        k_line_moments<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], links_mask(h, k - 1), 0,
+                                                          F->M[F->mcur]);
         break;
     }
     }

@@ -368,20 +368,21 @@ __global__ void k_plane_moments3(RefineGeom g, const S *__restrict__ fc, const u
     for (int k = 0; k < 10; ++k) M[10 * b + k] = (double)m[k];
 }
 
-// 1D stencil of fine coordinate c on an axis with coarse origin o: the
-// coincident node, or the centred cubic between o + (c-1)/2 and o + (c+1)/2
+// Point q of the 1D stencil of fine coordinate c on an axis with coarse
+// origin o: the coincident node (even c, q = 0), or the centred cubic
+// (-1, 9, 9, -1) / 16 between o + (c-1)/2 and o + (c+1)/2 (odd c, q = 0..3).
+// No index arrays: a runtime index into a per-thread array would go through
+// local memory.
 template <class C>
-__device__ inline int stencil1(int c, int o, int idx[4], C w[4])
+__device__ inline void stencil_point(int c, int o, int q, int &idx, C &w)
 {
     if ((c & 1) == 0) {
-        idx[0] = o + c / 2;
-        w[0] = C(1);
-        return 1;
+        idx = o + c / 2;
+        w = C(1);
+    } else {
+        idx = o + (c - 1) / 2 - 1 + q;
+        w = (q == 0 || q == 3) ? C(-0.0625) : C(0.5625);
     }
-    const int a = o + (c - 1) / 2;
-    idx[0] = a - 1; idx[1] = a; idx[2] = a + 1; idx[3] = a + 2;
-    w[0] = C(-0.0625); w[1] = C(0.5625); w[2] = C(0.5625); w[3] = C(-0.0625);
-    return 4;
 }
 
 __host__ __device__ inline int shell3_count(int nx, int ny, int nz)
@@ -407,63 +408,101 @@ __device__ inline void shell3_coord(int nx, int ny, int nz, int t, int &i, int &
     }
 }
 
+// Fine shell node values at t + a (Sec. II.B, coarse to fine): the coarse
+// plane moments interpolated linearly in time and by the tensor cubic in
+// space, f^neq rescaled by alpha, rebuilt.  A shell node's stencil has 1, 4
+// or 16 coarse points.  Four lanes take one node (lane r its points r, r + 4,
+// r + 8, r + 12), the weighted moments are summed over the four by shuffles,
+// and the node's first lane rebuilds and stores it: the loads are spread
+// over more threads than one per node, while the rebuild is still shared by
+// eight nodes per warp.
 template <class S>
-__global__ void k_fill_shell3(RefineGeom g, const double *__restrict__ M0, const double *__restrict__ M1, double a,
-                              double alpha, double tau_f, S *__restrict__ ff)
+__global__ void __launch_bounds__(256) k_fill_shell3(RefineGeom g, const double *__restrict__ M0,
+                                                     const double *__restrict__ M1, double a, double alpha,
+                                                     double tau_f, S *__restrict__ ff)
 {
     using C = CT<S>;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= shell3_count(g.nfx, g.nfy, g.nfz)) return;
-    int i, j, k;
-    shell3_coord(g.nfx, g.nfy, g.nfz, t, i, j, k);
-    int ix[4], iy[4], iz[4];
-    C wx[4], wy[4], wz[4];
-    const int sx = stencil1<C>(i, g.X0, ix, wx);
-    const int sy = stencil1<C>(j, g.Y0, iy, wy);
-    const int sz = stencil1<C>(k, g.Z0, iz, wz);
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int t = (int)(gt >> 2), r = (int)(gt & 3);
+    const int count = shell3_count(g.nfx, g.nfy, g.nfz);
+    const bool node = t < count;  // lanes past the last node still join the shuffles
+    int i = 0, j = 0, k = 0;
+    if (node) shell3_coord(g.nfx, g.nfy, g.nfz, t, i, j, k);
+    // per axis: 1 point (even fine coordinate) or 4 (odd); lx = log2 of the count
+    const int lx = (i & 1) << 1, ly = (j & 1) << 1, lz = (k & 1) << 1;
+    const int npts = node ? 1 << (lx + ly + lz) : 0;
     const C am = C(a), bm = C(1) - C(a);
     C m[10];
 #pragma unroll
     for (int e = 0; e < 10; ++e) m[e] = C(0);
-    for (int c = 0; c < sz; ++c)
-        for (int b = 0; b < sy; ++b)
-            for (int q = 0; q < sx; ++q) {
-                const int64_t e0 = 10 * box3_index(g, ix[q], iy[b], iz[c]);
-                const C wt = wx[q] * wy[b] * wz[c];
 #pragma unroll
-                for (int e = 0; e < 10; ++e) m[e] = fmac(wt, bm * C(M0[e0 + e]) + am * C(M1[e0 + e]), m[e]);
-            }
-    store_rebuilt_3d<S>(ff, (int64_t)g.nfx * g.nfy * g.nfz, i + (int64_t)g.nfx * (j + (int64_t)g.nfy * k), m,
-                        alpha, tau_f);
+    for (int s4 = 0; s4 < 4; ++s4) {
+        const int q = r + 4 * s4;  // stencil point (qx, qy, qz) of the node's stencil
+        if (q < npts) {
+            const int qx = q & ((1 << lx) - 1), qy = (q >> lx) & ((1 << ly) - 1), qz = q >> (lx + ly);
+            int cx, cy, cz;
+            C wx, wy, wz;
+            stencil_point<C>(i, g.X0, qx, cx, wx);
+            stencil_point<C>(j, g.Y0, qy, cy, wy);
+            stencil_point<C>(k, g.Z0, qz, cz, wz);
+            const int64_t e0 = 10 * box3_index(g, cx, cy, cz);
+            const C wt = wx * wy * wz;
+#pragma unroll
+            for (int e = 0; e < 10; ++e) m[e] = fmac(wt, bm * C(M0[e0 + e]) + am * C(M1[e0 + e]), m[e]);
+        }
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int e = 0; e < 10; ++e) m[e] += __shfl_xor_sync(0xffffffffu, m[e], o);
+    }
+    if (node && r == 0)
+        store_rebuilt_3d<S>(ff, (int64_t)g.nfx * g.nfy * g.nfz, i + (int64_t)g.nfx * (j + (int64_t)g.nfy * k), m,
+                            alpha, tau_f);
 }
 
+// Covered coarse shell (Sec. II.B, fine to coarse): rho, u of the coincident
+// fine node and the (1,2,1)^3 / 64 filtered Pi^neq of its 27 neighbours,
+// rescaled by alpha, rebuilt.  One warp per coarse node: lane l < 27 pulls
+// the streamed moments of stencil point l, the filtered sum is taken by
+// shuffles, and the centre lane (13) supplies rho and u.
 template <class S>
-__global__ void k_restrict3(RefineGeom g, const S *__restrict__ ff_prev, const uint8_t *__restrict__ fmask,
-                            double alpha, double tau_c, S *__restrict__ fc)
+__global__ void __launch_bounds__(256) k_restrict3(RefineGeom g, const S *__restrict__ ff_prev,
+                                                   const uint8_t *__restrict__ fmask, double alpha, double tau_c,
+                                                   S *__restrict__ fc)
 {
     using C = CT<S>;
     const int w = g.Wc - 1, h = g.Hc - 1, d = g.Dc - 1;  // shell of [X0+1, X0+Wc-1] x ...
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= shell3_count(w, h, d)) return;
-    int a, b, c;
-    shell3_coord(w, h, d, t, a, b, c);
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int t = (int)(gt >> 5), l = (int)(gt & 31);
+    const bool node = t < shell3_count(w, h, d);  // lanes past the last node still join the shuffles
+    int a = 0, b = 0, c = 0;
+    if (node) shell3_coord(w, h, d, t, a, b, c);
     const int x = g.X0 + 1 + a, y = g.Y0 + 1 + b, z = g.Z0 + 1 + c;
     const int i = 2 * (x - g.X0), j = 2 * (y - g.Y0), k = 2 * (z - g.Z0);
-    const C w3[3] = {C(1), C(2), C(1)};
-    C mc[10], m[10];
+    C m[10];
 #pragma unroll
-    for (int e = 0; e < 10; ++e) mc[e] = C(0);
-    for (int l = -1; l <= 1; ++l)
-        for (int q = -1; q <= 1; ++q)
-            for (int p = -1; p <= 1; ++p) {
-                streamed_moments_3d<S>(ff_prev, fmask, g.nfx, g.nfy, g.nfz, i + p, j + q, k + l, m);
-                const C wt = w3[p + 1] * w3[q + 1] * w3[l + 1] * C(1.0 / 64.0);
+    for (int e = 0; e < 10; ++e) m[e] = C(0);
+    if (node && l < 27) {
+        const int p = l % 3 - 1, q = (l / 3) % 3 - 1, r = l / 9 - 1;
+        streamed_moments_3d<S>(ff_prev, fmask, g.nfx, g.nfy, g.nfz, i + p, j + q, k + r, m);
+        const C wt = C((p ? 1 : 2) * (q ? 1 : 2) * (r ? 1 : 2)) * C(1.0 / 64.0);
 #pragma unroll
-                for (int e = 4; e < 10; ++e) mc[e] = fmac(wt, m[e], mc[e]);
-                if (p == 0 && q == 0 && l == 0) { mc[0] = m[0]; mc[1] = m[1]; mc[2] = m[2]; mc[3] = m[3]; }
-            }
-    store_rebuilt_3d<S>(fc, (int64_t)g.nxc * g.nyc * g.nzc, x + (int64_t)g.nxc * (y + (int64_t)g.nyc * z), mc, alpha,
-                        tau_c);
+        for (int e = 4; e < 10; ++e) m[e] *= wt;
+    }
+    C mc[10];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) mc[e] = __shfl_sync(0xffffffffu, m[e], 13);
+#pragma unroll
+    for (int e = 4; e < 10; ++e) {
+        C v = m[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        mc[e] = v;
+    }
+    if (node && l == 0)
+        store_rebuilt_3d<S>(fc, (int64_t)g.nxc * g.nyc * g.nzc, x + (int64_t)g.nxc * (y + (int64_t)g.nyc * z), mc,
+                            alpha, tau_c);
 }
 
 }  // namespace rr

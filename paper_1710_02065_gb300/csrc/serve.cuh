@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(128) k_batched(const BatchDomain *__restrict__
         const int y = tl.row % ny, z = tl.row / ny;
         const int x0 = (tl.xseg * 32 + lane) * V;
         if constexpr (V == 1) {
-            if (x0 < d.p.n[0]) update_cell<L, S, C, false, false>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);
+            if (x0 < d.p.n[0]) update_cell<L, S, C, false, kMaskNone>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);
         } else {
             update_vec<L, S, C, V>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);
         }

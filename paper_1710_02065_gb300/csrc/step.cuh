@@ -58,6 +58,7 @@ struct StepParams {
     double noise_amp;
     double omega;  // 1 - 1/tau
     const uint8_t *solid;  // device, or null
+    int any_solid;         // the mask holds solid cells (else only fixed ones)
     int64_t step;
     // bulk box: cells with blo[a] <= c[a] < bhi[a] on every axis have no
     // boundary role and no sponge (filled by the host from faces and layers)
@@ -281,7 +282,12 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
 // role from coordinates, collision, store.  Shared by the single-lattice
 // kernel below and the batched multi-domain kernel.
 // ---------------------------------------------------------------------------
-template <class L, class S, class C, bool BGK = false, bool MASK = true>
+// Cell-type mask handling compiled into an update: none (no mask), skip
+// (fixed cells are not updated; no solid cells, so no link tests), links
+// (skip, plus halfway bounce-back at cells next to a solid).
+enum { kMaskNone = 0, kMaskSkip = 1, kMaskLinks = 2 };
+
+template <class L, class S, class C, bool BGK = false, int MASK = kMaskLinks>
 __device__ __forceinline__ void update_cell(const StepParams &p, const char *const *in, char *const *out,
                                             int x, int y, int z)
 {
@@ -289,8 +295,8 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     const unsigned nx = p.n[0], ny = p.n[1], nz = p.n[2];
     const unsigned nxy = nx * ny;
     const unsigned cell = x + nx * y + nxy * z;
-    // MASK = false: compiled without any cell-type test (the lattice has no mask)
-    const uint8_t *__restrict__ solid = MASK ? p.solid : nullptr;
+    // kMaskNone: compiled without any cell-type test (the lattice has no mask)
+    const uint8_t *__restrict__ solid = MASK != kMaskNone ? p.solid : nullptr;
     if (solid && (solid[cell] & MASK_TYPE)) return;  // solid (1) and fixed (2) cells keep their populations
 
     // ---- boundary role and the node whose streamed populations are used
@@ -320,7 +326,7 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
 
     // ---- streaming (pull) with halfway bounce-back; only a node with a solid
     // neighbour tests its links
-    const bool near = solid && (solid[scell] & MASK_NEAR_SOLID);
+    const bool near = MASK == kMaskLinks && solid && (solid[scell] & MASK_NEAR_SOLID);
     C g[L::Q];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
@@ -359,14 +365,27 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     }
 }
 
-// General kernel: one thread per cell; MASK = true reads the cell-type mask;
+// General kernel: one thread per cell; MASK: cell-type handling (above);
 // BGK = true is the plain LBM-BGK collision (Eq. standardLB).
-template <class L, class S, class C, bool BGK, bool MASK>
+template <class L, class S, class C, bool BGK, int MASK>
 __global__ void __launch_bounds__(256) k_stream_collide(const __grid_constant__ StepParams p)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= p.n[0]) return;
     update_cell<L, S, C, BGK, MASK>(p, p.in, p.out, x, blockIdx.y, blockIdx.z);
+}
+
+// The same update with one thread per cell of the whole lattice, for rows
+// whose length would leave many threads of their blocks idle (a 129-cell row
+// in 128-thread blocks idles half of them); rrBGK only.
+template <class L, class S, class C, int MASK>
+__global__ void __launch_bounds__(256) k_stream_collide_lin(const __grid_constant__ StepParams p)
+{
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (unsigned)p.ncell) return;
+    const unsigned nx = p.n[0], nxy = nx * (unsigned)p.n[1];
+    const unsigned z = t / nxy, r = t - z * nxy, y = r / nx;
+    update_cell<L, S, C, false, MASK>(p, p.in, p.out, (int)(r - y * nx), (int)y, (int)z);
 }
 
 // Launch wrapper: one thread per cell, blocks along x; p.bgk selects the
@@ -379,16 +398,32 @@ cudaError_t launch_stream_collide(const StepParams &p, const void *fin, void *fo
     set_bases<L, S>(q, fin, fout);
     dim3 b(block, 1, 1);
     dim3 g((p.n[0] + block - 1) / block, p.n[1], p.n[2]);
+    // rows that leave more than 1/8 of their threads idle: the whole-lattice
+    // mapping
+    const int64_t row_threads = (int64_t)g.x * block;
+    const int mode = !p.solid ? kMaskNone : (p.any_solid ? kMaskLinks : kMaskSkip);
+    if (!p.bgk && 8 * (row_threads - p.n[0]) > row_threads) {
+        const dim3 gl((unsigned)((p.ncell + block - 1) / block), 1, 1);
+        if (mode == kMaskLinks)
+            k_stream_collide_lin<L, S, C, kMaskLinks><<<gl, b, 0, st>>>(q);
+        else if (mode == kMaskSkip)
+            k_stream_collide_lin<L, S, C, kMaskSkip><<<gl, b, 0, st>>>(q);
+        else
+            k_stream_collide_lin<L, S, C, kMaskNone><<<gl, b, 0, st>>>(q);
+        return cudaGetLastError();
+    }
     if (p.bgk) {
         if (p.solid)
-            k_stream_collide<L, S, C, true, true><<<g, b, 0, st>>>(q);
+            k_stream_collide<L, S, C, true, kMaskLinks><<<g, b, 0, st>>>(q);
         else
-            k_stream_collide<L, S, C, true, false><<<g, b, 0, st>>>(q);
+            k_stream_collide<L, S, C, true, kMaskNone><<<g, b, 0, st>>>(q);
     } else {
-        if (p.solid)
-            k_stream_collide<L, S, C, false, true><<<g, b, 0, st>>>(q);
+        if (mode == kMaskLinks)
+            k_stream_collide<L, S, C, false, kMaskLinks><<<g, b, 0, st>>>(q);
+        else if (mode == kMaskSkip)
+            k_stream_collide<L, S, C, false, kMaskSkip><<<g, b, 0, st>>>(q);
         else
-            k_stream_collide<L, S, C, false, false><<<g, b, 0, st>>>(q);
+            k_stream_collide<L, S, C, false, kMaskNone><<<g, b, 0, st>>>(q);
     }
     return cudaGetLastError();
 }
