@@ -30,7 +30,7 @@ struct FineLevel {
     bool has_solid = false;              // the mask holds solid cells
     std::vector<uint8_t> user_mask;      // user solids (host copy)
     RefineGeom geom{};                   // position in the parent level's nodes
-    double *M[2] = {nullptr, nullptr};   // parent-side interface moments at t and t + 1
+    double *M[2] = {nullptr, nullptr};   // parent-side interface moments at t and t + 1 (compute type; sized for FP64)
     int mcur = 0;
 };
 
@@ -997,7 +997,8 @@ static cudaError_t refine_kernels3(lbm_ctx *h, int k, int stage, int a_half)
     case 0:  // coarse plane moments at t + 1 from the pre-step coarse field
     case 3: {  // plane moments at t = 0: local moments of the stored coarse field
         const int n = plane3_count(g);
-        double *M = stage == 0 ? F->M[1 - F->mcur] : F->M[F->mcur];
+        // the moment buffers (sized for FP64) hold the compute type
+        CT<S> *M = (CT<S> *)(stage == 0 ? F->M[1 - F->mcur] : F->M[F->mcur]);
         k_plane_moments3<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], links_mask(h, k - 1),
                                                             stage == 0 ? 1 : 0, M);
         break;
@@ -1006,15 +1007,16 @@ static cudaError_t refine_kernels3(lbm_ctx *h, int k, int stage, int a_half)
         const int n = shell3_count(g.nfx, g.nfy, g.nfz);
         // 4 threads per shell node
         k_fill_shell3<S><<<grid1(4 * (int64_t)n, 256), 256, 0, st>>>(
-            g, F->M[F->mcur], F->M[1 - F->mcur], a_half ? 0.5 : 1.0, F->tau / (2.0 * tau_p), F->tau,
-            (S *)F->f[F->cur]);
+            g, (const CT<S> *)F->M[F->mcur], (const CT<S> *)F->M[1 - F->mcur], CT<S>(a_half ? 0.5 : 1.0),
+            CT<S>(F->tau / (2.0 * tau_p)), CT<S>(1.0 - 1.0 / F->tau), (S *)F->f[F->cur]);
         break;
     }
     case 2: {  // covered coarse shell from the fine field; fine moments pulled from f(t + 1/2)
         const int n = shell3_count(g.Wc - 1, g.Hc - 1, g.Dc - 1);
         // one warp per covered coarse node (one lane per filter point)
         k_restrict3<S><<<grid1(32 * (int64_t)n, 256), 256, 0, st>>>(
-            g, (const S *)F->f[1 - F->cur], links_mask(h, k), 2.0 * tau_p / F->tau, tau_p, (S *)P.f[*P.cur]);
+            g, (const S *)F->f[1 - F->cur], links_mask(h, k), CT<S>(2.0 * tau_p / F->tau), CT<S>(1.0 - 1.0 / tau_p),
+            (S *)P.f[*P.cur]);
         break;
     }
     }
@@ -1040,26 +1042,27 @@ static cudaError_t refine_kernels(lbm_ctx *h, int k, int stage, int a_half)
     case 0: {  // coarse line moments at t + 1 from the pre-step coarse field
         const int n = line_count(g);
         k_line_moments<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], links_mask(h, k - 1), 1,
-                                                          F->M[1 - F->mcur]);
+                                                          (CT<S> *)F->M[1 - F->mcur]);
         break;
     }
     case 1: {  // fine ring at t + 1/2 (a_half = 1) or t + 1 (a_half = 0)
         const int n = 2 * g.nfx + 2 * (g.nfy - 2);
-        k_fill_ring<S><<<grid1(n, 128), 128, 0, st>>>(g, F->M[F->mcur], F->M[1 - F->mcur], a_half ? 0.5 : 1.0,
-                                                       F->tau / (2.0 * tau_p), F->tau, (S *)F->f[F->cur]);
+        k_fill_ring<S><<<grid1(n, 128), 128, 0, st>>>(
+            g, (const CT<S> *)F->M[F->mcur], (const CT<S> *)F->M[1 - F->mcur], CT<S>(a_half ? 0.5 : 1.0),
+            CT<S>(F->tau / (2.0 * tau_p)), CT<S>(1.0 - 1.0 / F->tau), (S *)F->f[F->cur]);
         break;
     }
     case 2: {  // covered coarse ring from the fine field; pre-collision fine moments pulled from f(t + 1/2)
         const int n = 2 * (g.Wc - 1) + 2 * (g.Hc - 3);
         k_restrict<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)F->f[1 - F->cur], links_mask(h, k),
-                                                      2.0 * tau_p / F->tau,
-                                                     tau_p, (S *)P.f[*P.cur]);
+                                                      CT<S>(2.0 * tau_p / F->tau), CT<S>(1.0 - 1.0 / tau_p),
+                                                      (S *)P.f[*P.cur]);
         break;
     }
     case 3: {  // line moments at t = 0: local moments of the stored coarse field
         const int n = line_count(g);
         k_line_moments<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], links_mask(h, k - 1), 0,
-                                                          F->M[F->mcur]);
+                                                          (CT<S> *)F->M[F->mcur]);
         break;
     }
     }

@@ -106,19 +106,20 @@ __device__ void local_moments_2d(const S *__restrict__ f, int nx, int ny, int x,
     m[0] = mo.dr; m[1] = ux; m[2] = uy; m[3] = p.xx; m[4] = p.xy; m[5] = p.yy;
 }
 
-// Store feqH(rho, u) + (1 - 1/tau) fneqH(u, alpha Pi^neq) at a cell
+// Store feqH(rho, u) + omega fneqH(u, alpha Pi^neq) at a cell, omega = 1 - 1/tau
+// (alpha and omega come from the host in the compute type)
 template <class S>
-__device__ void store_rebuilt_2d(S *__restrict__ f, int64_t N, int64_t cell, const CT<S> m[6], double alpha,
-                                 double tau)
+__device__ void store_rebuilt_2d(S *__restrict__ f, int64_t N, int64_t cell, const CT<S> m[6], CT<S> alpha,
+                                 CT<S> omega)
 {
     using C = CT<S>;
     Coef<C> k{};
     const C rho = C(1) + m[0];
     add_eq<C, 2>(k, C(1), m[0], rho, m[1], m[2], C(0));
     Sym2<C> p;
-    p.xx = C(alpha) * m[3]; p.xy = C(alpha) * m[4]; p.yy = C(alpha) * m[5];
+    p.xx = alpha * m[3]; p.xy = alpha * m[4]; p.yy = alpha * m[5];
     p.zz = p.xz = p.yz = C(0);
-    add_neq<C, 2>(k, C(1.0 - 1.0 / tau), m[1], m[2], C(0), p);
+    add_neq<C, 2>(k, omega, m[1], m[2], C(0), p);
     const RebuildPre<C> r = rebuild_prep<D2Q9, C>(k);
     Store<S>::st(f + cell, rebuild_rest<D2Q9, C>(k, r));
 #pragma unroll
@@ -132,7 +133,7 @@ __device__ void store_rebuilt_2d(S *__restrict__ f, int64_t N, int64_t cell, con
 
 template <class S>
 __global__ void k_line_moments(RefineGeom g, const S *__restrict__ fc, const uint8_t *__restrict__ mask,
-                               int streamed, double *__restrict__ M)
+                               int streamed, CT<S> *__restrict__ M)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= line_count(g)) return;
@@ -144,19 +145,19 @@ __global__ void k_line_moments(RefineGeom g, const S *__restrict__ fc, const uin
     else
         local_moments_2d<S>(fc, g.nxc, g.nyc, x, y, m);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) M[6 * e + k] = (double)m[k];
+    for (int k = 0; k < 6; ++k) M[6 * e + k] = m[k];
 }
 
 template <class C>
-__device__ inline void mix6(const double *__restrict__ M0, const double *__restrict__ M1, C a, int e, C out[6])
+__device__ inline void mix6(const C *__restrict__ M0, const C *__restrict__ M1, C a, int e, C out[6])
 {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) out[k] = (C(1) - a) * C(M0[6 * e + k]) + a * C(M1[6 * e + k]);
+    for (int k = 0; k < 6; ++k) out[k] = (C(1) - a) * M0[6 * e + k] + a * M1[6 * e + k];
 }
 
 template <class S>
-__global__ void k_fill_ring(RefineGeom g, const double *__restrict__ M0, const double *__restrict__ M1, double a,
-                            double alpha, double tau_f, S *__restrict__ ff)
+__global__ void k_fill_ring(RefineGeom g, const CT<S> *__restrict__ M0, const CT<S> *__restrict__ M1, CT<S> a,
+                            CT<S> alpha, CT<S> omega, S *__restrict__ ff)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int nfx = g.nfx, nfy = g.nfy;
@@ -169,7 +170,7 @@ __global__ void k_fill_ring(RefineGeom g, const double *__restrict__ M0, const d
     else { i = nfx - 1; j = 1 + t - 2 * nfx - (nfy - 2); }
     using C = CT<S>;
     const bool on_h = (j == 0 || j == nfy - 1);
-    const C am = C(a);
+    const C am = a;
     C m[6];
     if (on_h) {
         const int top = j == 0 ? 0 : 1;
@@ -200,12 +201,12 @@ __global__ void k_fill_ring(RefineGeom g, const double *__restrict__ M0, const d
             for (int k = 0; k < 6; ++k) m[k] = (-t0[k] + C(9) * t1[k] + C(9) * t2[k] - t3[k]) * C(0.0625);
         }
     }
-    store_rebuilt_2d<S>(ff, (int64_t)nfx * nfy, i + (int64_t)nfx * j, m, alpha, tau_f);
+    store_rebuilt_2d<S>(ff, (int64_t)nfx * nfy, i + (int64_t)nfx * j, m, alpha, omega);
 }
 
 template <class S>
 __global__ void k_restrict(RefineGeom g, const S *__restrict__ ff_prev, const uint8_t *__restrict__ fmask,
-                           double alpha, double tau_c, S *__restrict__ fc)
+                           CT<S> alpha, CT<S> omega, S *__restrict__ fc)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int w = g.Wc - 1, h = g.Hc - 1;  // ring of the rectangle [X0+1, X0+Wc-1] x [Y0+1, Y0+Hc-1]
@@ -231,7 +232,7 @@ __global__ void k_restrict(RefineGeom g, const S *__restrict__ ff_prev, const ui
             mc[5] += wt * m[5];
             if (k == 0 && l == 0) { mc[0] = m[0]; mc[1] = m[1]; mc[2] = m[2]; }
         }
-    store_rebuilt_2d<S>(fc, (int64_t)g.nxc * g.nyc, x + (int64_t)g.nxc * y, mc, alpha, tau_c);
+    store_rebuilt_2d<S>(fc, (int64_t)g.nxc * g.nyc, x + (int64_t)g.nxc * y, mc, alpha, omega);
 }
 
 // ===========================================================================
@@ -242,7 +243,8 @@ __global__ void k_restrict(RefineGeom g, const S *__restrict__ ff_prev, const ui
 // 1, ux, uy, uz, Pxx, Pxy, Pxz, Pyy, Pyz, Pzz) of the coarse nodes on the six
 // face planes of the patch box (extended by one node past every edge) are
 // kept in a dense box array over [X0-1, X0+Wc+1] x [Y0-1, Y0+Hc+1] x
-// [Z0-1, Z0+Dc+1] (10 doubles per node; off-plane entries unused).
+// [Z0-1, Z0+Dc+1] (10 values of the compute type per node; off-plane entries
+// unused).
 //   k_plane_moments3 : coarse moments on the six planes
 //   k_fill_shell3    : fine shell from plane moments mixed in time and
 //                      interpolated along every axis on which the fine node is
@@ -326,19 +328,21 @@ __device__ void local_moments_3d(const S *__restrict__ f, int64_t N, int64_t cel
     pack_moments3<C>(moments_pairs<D3Q19, C>(g), m);
 }
 
-// Store feqH(rho, u) + (1 - 1/tau) fneqH(u, alpha Pi^neq) at a cell
+// Store feqH(rho, u) + omega fneqH(u, alpha Pi^neq) at a cell, omega = 1 - 1/tau
+// (alpha and omega come from the host in the compute type: no FP64
+// arithmetic on the device)
 template <class S>
-__device__ void store_rebuilt_3d(S *__restrict__ f, int64_t N, int64_t cell, const CT<S> m[10], double alpha,
-                                 double tau)
+__device__ void store_rebuilt_3d(S *__restrict__ f, int64_t N, int64_t cell, const CT<S> m[10], CT<S> alpha,
+                                 CT<S> omega)
 {
     using C = CT<S>;
     Coef<C> k{};
     const C rho = C(1) + m[0];
     add_eq<C, 3>(k, C(1), m[0], rho, m[1], m[2], m[3]);
     Sym2<C> p;
-    p.xx = C(alpha) * m[4]; p.xy = C(alpha) * m[5]; p.xz = C(alpha) * m[6];
-    p.yy = C(alpha) * m[7]; p.yz = C(alpha) * m[8]; p.zz = C(alpha) * m[9];
-    add_neq<C, 3>(k, C(1.0 - 1.0 / tau), m[1], m[2], m[3], p);
+    p.xx = alpha * m[4]; p.xy = alpha * m[5]; p.xz = alpha * m[6];
+    p.yy = alpha * m[7]; p.yz = alpha * m[8]; p.zz = alpha * m[9];
+    add_neq<C, 3>(k, omega, m[1], m[2], m[3], p);
     const RebuildPre<C> r = rebuild_prep<D3Q19, C>(k);
     Store<S>::st(f + cell, rebuild_rest<D3Q19, C>(k, r));
 #pragma unroll
@@ -350,9 +354,11 @@ __device__ void store_rebuilt_3d(S *__restrict__ f, int64_t N, int64_t cell, con
     }
 }
 
+// Interface moments of the coarse plane nodes, stored in the compute type
+// (10 per node: rho - 1, u, Pi^neq)
 template <class S>
 __global__ void k_plane_moments3(RefineGeom g, const S *__restrict__ fc, const uint8_t *__restrict__ mask,
-                                 int streamed, double *__restrict__ M)
+                                 int streamed, CT<S> *__restrict__ M)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= plane3_count(g)) return;
@@ -365,7 +371,7 @@ __global__ void k_plane_moments3(RefineGeom g, const S *__restrict__ fc, const u
         local_moments_3d<S>(fc, (int64_t)g.nxc * g.nyc * g.nzc, x + (int64_t)g.nxc * (y + (int64_t)g.nyc * z), m);
     const int64_t b = box3_index(g, x, y, z);
 #pragma unroll
-    for (int k = 0; k < 10; ++k) M[10 * b + k] = (double)m[k];
+    for (int k = 0; k < 10; ++k) M[10 * b + k] = m[k];
 }
 
 // Point q of the 1D stencil of fine coordinate c on an axis with coarse
@@ -417,9 +423,9 @@ __device__ inline void shell3_coord(int nx, int ny, int nz, int t, int &i, int &
 // over more threads than one per node, while the rebuild is still shared by
 // eight nodes per warp.
 template <class S>
-__global__ void __launch_bounds__(256) k_fill_shell3(RefineGeom g, const double *__restrict__ M0,
-                                                     const double *__restrict__ M1, double a, double alpha,
-                                                     double tau_f, S *__restrict__ ff)
+__global__ void __launch_bounds__(256) k_fill_shell3(RefineGeom g, const CT<S> *__restrict__ M0,
+                                                     const CT<S> *__restrict__ M1, CT<S> a, CT<S> alpha,
+                                                     CT<S> omega, S *__restrict__ ff)
 {
     using C = CT<S>;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -431,7 +437,7 @@ __global__ void __launch_bounds__(256) k_fill_shell3(RefineGeom g, const double 
     // per axis: 1 point (even fine coordinate) or 4 (odd); lx = log2 of the count
     const int lx = (i & 1) << 1, ly = (j & 1) << 1, lz = (k & 1) << 1;
     const int npts = node ? 1 << (lx + ly + lz) : 0;
-    const C am = C(a), bm = C(1) - C(a);
+    const C am = a, bm = C(1) - a;
     C m[10];
 #pragma unroll
     for (int e = 0; e < 10; ++e) m[e] = C(0);
@@ -448,7 +454,7 @@ __global__ void __launch_bounds__(256) k_fill_shell3(RefineGeom g, const double 
             const int64_t e0 = 10 * box3_index(g, cx, cy, cz);
             const C wt = wx * wy * wz;
 #pragma unroll
-            for (int e = 0; e < 10; ++e) m[e] = fmac(wt, bm * C(M0[e0 + e]) + am * C(M1[e0 + e]), m[e]);
+            for (int e = 0; e < 10; ++e) m[e] = fmac(wt, bm * M0[e0 + e] + am * M1[e0 + e], m[e]);
         }
     }
 #pragma unroll
@@ -458,7 +464,7 @@ __global__ void __launch_bounds__(256) k_fill_shell3(RefineGeom g, const double 
     }
     if (node && r == 0)
         store_rebuilt_3d<S>(ff, (int64_t)g.nfx * g.nfy * g.nfz, i + (int64_t)g.nfx * (j + (int64_t)g.nfy * k), m,
-                            alpha, tau_f);
+                            alpha, omega);
 }
 
 // Covered coarse shell (Sec. II.B, fine to coarse): rho, u of the coincident
@@ -468,7 +474,7 @@ __global__ void __launch_bounds__(256) k_fill_shell3(RefineGeom g, const double 
 // shuffles, and the centre lane (13) supplies rho and u.
 template <class S>
 __global__ void __launch_bounds__(256) k_restrict3(RefineGeom g, const S *__restrict__ ff_prev,
-                                                   const uint8_t *__restrict__ fmask, double alpha, double tau_c,
+                                                   const uint8_t *__restrict__ fmask, CT<S> alpha, CT<S> omega,
                                                    S *__restrict__ fc)
 {
     using C = CT<S>;
@@ -502,7 +508,7 @@ __global__ void __launch_bounds__(256) k_restrict3(RefineGeom g, const S *__rest
     }
     if (node && l == 0)
         store_rebuilt_3d<S>(fc, (int64_t)g.nxc * g.nyc * g.nzc, x + (int64_t)g.nxc * (y + (int64_t)g.nyc * z), mc,
-                            alpha, tau_c);
+                            alpha, omega);
 }
 
 }  // namespace rr
