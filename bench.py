@@ -608,8 +608,9 @@ def run_serving(lbm, torch, args):
                         steps_per_round=args.round_steps)
     out["workload"] = (f"{args.requests} requests, Poisson arrivals {args.rate}/s, D2Q9 pulses 64^2-1024^2 and "
                        f"D3Q19 Taylor-Green 32^3-192^3, steps x{args.steps_scale}, FP32/FP16")
-    out["arrival_rate_note"] = ("default rate 5.4/s = 0.8 x the saturated service rate of this stream "
-                                "(6.8 requests/s: 1.48e12 cell updates at 19.6 G cell updates/s)")
+    out["arrival_rate_note"] = ("default rate 9.7/s = 0.8 x the saturated service rate of this stream "
+                                "(12.1 requests/s: 1.48e12 cell updates at 35.0 G cell updates/s, measured "
+                                "with arrivals at 40/s)")
     return out
 
 
@@ -658,9 +659,9 @@ def main():
                     help="jet: the headline benchmark line; the others print their own JSON line")
     ap.add_argument("--cyl-steps", type=int, default=40000, help="fine-resolution steps of the cylinder runs")
     ap.add_argument("--requests", type=int, default=512)
-    ap.add_argument("--rate", type=float, default=5.4,
-                    help="serving arrival rate (requests/s); the default is 0.8 x the 6.8 requests/s this "
-                         "stream is served at when saturated (1.48e12 cell updates at 19.6 G/s)")
+    ap.add_argument("--rate", type=float, default=9.7,
+                    help="serving arrival rate (requests/s); the default is 0.8 x the 12.1 requests/s this "
+                         "stream is served at when saturated (1.48e12 cell updates at 35.0 G/s)")
     ap.add_argument("--steps-scale", type=float, default=1.0, help="serving: scale of per-request steps")
     ap.add_argument("--budget-gb", type=float, default=8.0, help="serving: HBM budget for populations")
     ap.add_argument("--round-steps", type=int, default=100, help="serving: steps per batched round")

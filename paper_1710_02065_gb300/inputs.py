@@ -89,10 +89,11 @@ def double_shear_layer(n: int, U: float = 0.1, kappa: float = 80.0, delta: float
 def taylor_green_3d(n: int, u0: float = 0.01):
     """u = U0 (sin kx cos ky cos kz, -cos kx sin ky cos kz, 0), k = 2 pi / n."""
     k = 2 * math.pi / n
-    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    c = np.arange(n)
+    s1, c1 = np.sin(k * c), np.cos(k * c)  # separable: same products, evaluated left to right
     u = np.zeros((n ** 3, 3))
-    u[:, 0] = (u0 * np.sin(k * x) * np.cos(k * y) * np.cos(k * z)).reshape(-1)
-    u[:, 1] = (-u0 * np.cos(k * x) * np.sin(k * y) * np.cos(k * z)).reshape(-1)
+    u[:, 0] = ((u0 * s1)[None, None, :] * c1[None, :, None] * c1[:, None, None]).reshape(-1)
+    u[:, 1] = ((-u0 * c1)[None, None, :] * s1[None, :, None] * c1[:, None, None]).reshape(-1)
     rho = np.ones(n ** 3)
     return rho, u
 

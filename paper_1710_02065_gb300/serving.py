@@ -4,9 +4,17 @@ Requests arrive in real time (their `arrival` offsets, seconds); every round
 submits what has arrived, lets the server admit by HBM budget and advance all
 admitted requests together, and collects what finished.  Reports aggregate
 MLUPS and time-to-solution percentiles (arrival to result on the host).
+
+The request payloads (initial rho, u) are the clients' data: a client thread
+synthesises each one ahead of its arrival (at most `lookahead_s` early and
+`max_ready` payloads held), the way a client holds its data before it
+submits, so that payload synthesis on the host does not stall the server
+loop.  A payload that is not ready at its arrival time is submitted when it
+is, and the wait counts in that request's time to solution.
 """
 from __future__ import annotations
 
+import threading
 import time
 
 import numpy as np
@@ -49,37 +57,84 @@ class Server:
         return lbm.lbm_server_stats(self.s)
 
 
+class _Client(threading.Thread):
+    """Synthesises request payloads in arrival order, ahead of arrival."""
+
+    def __init__(self, pending, t0: float, lookahead_s: float, max_ready: int):
+        super().__init__(daemon=True)
+        self.pending, self.t0, self.lookahead, self.max_ready = pending, t0, lookahead_s, max_ready
+        self.ready = {}  # index -> (rho, u)
+        self.cv = threading.Condition()
+        self.stop = False
+
+    def run(self):
+        for k, req in enumerate(self.pending):
+            with self.cv:
+                while not self.stop and len(self.ready) >= self.max_ready:
+                    self.cv.wait(0.05)
+                if self.stop:
+                    return
+            wait = req["arrival"] - self.lookahead - (time.perf_counter() - self.t0)
+            if wait > 0:
+                with self.cv:
+                    if self.cv.wait_for(lambda: self.stop, timeout=wait):
+                        return
+            payload = inputs.request_initial_state(req)
+            with self.cv:
+                self.ready[k] = payload
+                self.cv.notify_all()
+
+    def take(self, k: int):
+        with self.cv:
+            p = self.ready.pop(k, None)
+            if p is not None:
+                self.cv.notify_all()
+            return p
+
+
 def serve(requests, hbm_budget_bytes: int = 8 << 30, max_slots: int = 256, steps_per_round: int = 100,
-          keep_results: bool = False):
+          keep_results: bool = False, lookahead_s: float = 2.0, max_ready: int = 16):
     """Run a request stream to completion; returns a summary dict (and results)."""
     srv = Server(hbm_budget_bytes, max_slots)
     pending = sorted(requests, key=lambda r: r["arrival"])
     inflight = {}  # id -> (request, arrival wall time)
     tts, results, failed = [], {}, 0
     t0 = time.perf_counter()
+    client = _Client(pending, t0, lookahead_s, max_ready)
+    client.start()
     i = 0
-    while i < len(pending) or inflight:
-        now = time.perf_counter() - t0
-        while i < len(pending) and pending[i]["arrival"] <= now:
-            req = pending[i]
-            rho, u = inputs.request_initial_state(req)
-            rid = srv.submit(req, rho, u)
-            inflight[rid] = (req, t0 + req["arrival"], i)
-            i += 1
-        if not inflight:
-            time.sleep(max(0.0, pending[i]["arrival"] - (time.perf_counter() - t0)))
-            continue
-        srv.run(steps_per_round)
-        for rid in list(inflight):
-            state, _ = srv.poll(rid)
-            if state in (lbm.LBM_REQ_DONE, lbm.LBM_REQ_FAILED):
-                req, t_arr, k = inflight.pop(rid)
-                ncell = int(np.prod(req["extents"]))
-                rho, u, rc = srv.result(rid, ncell)
-                tts.append(time.perf_counter() - t_arr)
-                failed += rc != lbm.LBM_OK
-                if keep_results:
-                    results[k] = (rho, u)
+    try:
+        while i < len(pending) or inflight:
+            now = time.perf_counter() - t0
+            while i < len(pending) and pending[i]["arrival"] <= now:
+                payload = client.take(i)
+                if payload is None:
+                    break  # not synthesised yet: submitted in a later round
+                req = pending[i]
+                rid = srv.submit(req, *payload)
+                inflight[rid] = (req, t0 + req["arrival"], i)
+                i += 1
+            if not inflight:
+                dt = pending[i]["arrival"] - (time.perf_counter() - t0)
+                with client.cv:
+                    client.cv.wait(0.05 if dt <= 0 else min(0.05, dt))
+                continue
+            srv.run(steps_per_round)
+            for rid in list(inflight):
+                state, _ = srv.poll(rid)
+                if state in (lbm.LBM_REQ_DONE, lbm.LBM_REQ_FAILED):
+                    req, t_arr, k = inflight.pop(rid)
+                    ncell = int(np.prod(req["extents"]))
+                    rho, u, rc = srv.result(rid, ncell)
+                    tts.append(time.perf_counter() - t_arr)
+                    failed += rc != lbm.LBM_OK
+                    if keep_results:
+                        results[k] = (rho, u)
+    finally:
+        with client.cv:
+            client.stop = True
+            client.cv.notify_all()
+        client.join()
     wall = time.perf_counter() - t0
     cells = srv.stats()["cell_updates"]
     srv.close()
