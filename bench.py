@@ -409,6 +409,28 @@ def strouhal(signal, dt_steps, D, U):
     return f * D / U
 
 
+def record_series(lbm, torch, s, total, every, level, probes=None):
+    """Advance `total` steps and record lift/drag of `level` (and p' at the
+    probe cells) every `every` steps into device memory, read back once at the
+    end: the samples are taken in stream order without host round trips.
+    Returns (wall seconds, forces [n, 3], p' [n, len(probes)] or None)."""
+    n = (total + every - 1) // every
+    F = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    P = torch.zeros((n, len(probes)), dtype=torch.float64, device="cuda") if probes else None
+    cells = torch.tensor(probes, dtype=torch.int64, device="cuda") if probes else None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(n):
+        lbm.lbm_step(s.h, min(every, total - k * every))
+        lbm.lbm_force_async(s.h, level, F[k].data_ptr())
+        if probes:
+            lbm.lbm_probe_async(s.h, len(probes), cells.data_ptr(), P[k].data_ptr())
+    s.sync()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return wall, F.cpu().numpy(), (P.cpu().numpy() if probes else None)
+
+
 def run_cylinder(lbm, torch, args):
     """Single-level D2Q9 cylinder: 1600x800, D = 40 at (400, 400), Ma 0.2,
     Re 150, inflow on -x, 100-cell sponge + zero-gradient outflow on +x, y
@@ -430,17 +452,9 @@ def run_cylinder(lbm, torch, args):
     s.set_state(rho, u)
     total = args.cyl_steps
     every = 10
-    lift, drag = [], []
     probes = [400 + nx * 700, 1200 + nx * 400]
-    pp = []
-    t0 = time.perf_counter()
-    for t in range(0, total, every):
-        lbm.lbm_step(s.h, every)
-        F = lbm.lbm_force(s.h, 0)
-        drag.append(F[0]); lift.append(F[1])
-        pp.append(lbm.lbm_probe(s.h, probes))
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
+    wall, Fs, pp = record_series(lbm, torch, s, total, every, 0, probes)
+    drag, lift = list(Fs[:, 0]), list(Fs[:, 1])
     _, _, rc = s.reduce()
     s.close()
     half = len(lift) // 2
@@ -482,14 +496,8 @@ def run_cylinder_two_level(lbm, torch, args):
     lbm.lbm_set_state(s.h, rho, u)
     total = args.cyl_steps // 2  # coarse steps covering the same physical time
     every = 5
-    lift, drag = [], []
-    t0 = time.perf_counter()
-    for t in range(0, total, every):
-        lbm.lbm_step(s.h, every)
-        F = lbm.lbm_force(s.h, 1)
-        drag.append(F[0]); lift.append(F[1])
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
+    wall, Fs, _ = record_series(lbm, torch, s, total, every, 1)
+    drag, lift = list(Fs[:, 0]), list(Fs[:, 1])
     _, _, rc = s.reduce()
     s.close()
     half = len(lift) // 2
@@ -540,14 +548,8 @@ def run_cylinder_three_level(lbm, torch, args):
     lbm.lbm_set_state(s.h, rho, u)
     total = args.cyl_steps // 4  # coarse steps covering the same physical time as the single-level run
     every = 5
-    lift, drag = [], []
-    t0 = time.perf_counter()
-    for t in range(0, total, every):
-        lbm.lbm_step(s.h, every)
-        F = lbm.lbm_force(s.h, 2)
-        drag.append(F[0]); lift.append(F[1])
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
+    wall, Fs, _ = record_series(lbm, torch, s, total, every, 2)
+    drag, lift = list(Fs[:, 0]), list(Fs[:, 1])
     _, _, rc = s.reduce()
     s.close()
     half = len(lift) // 2

@@ -394,6 +394,24 @@ int lbm_get_staging(lbm_handle h, int *active, int *stages, int *block, int *row
  */
 int lbm_force(lbm_handle h, int level, double F[3]);
 
+/*
+ * lbm_force_async / lbm_probe_async -- lbm_force and lbm_probe written to
+ * caller-owned DEVICE memory in stream order, without synchronising the
+ * stream: a time series of lift, drag and probe pressures can be recorded
+ * every few steps and read back once, so that sampling does not stall the
+ * stepping.
+ *   lbm_force_async : F_dev = 3 doubles (device) of level `level`
+ *   lbm_probe_async : cells_dev = n cell indices (device, int64), p_dev = n
+ *                     doubles (device); p' = c_s^2 (rho - rho_ref) as in
+ *                     lbm_probe.  Indices are not checked on the host (they
+ *                     are device data): an index outside [0, ncell) is
+ *                     skipped and its output set to NaN.
+ * Both return launch errors at once and execution errors at the next
+ * synchronising call.
+ */
+int lbm_force_async(lbm_handle h, int level, double *F_dev);
+int lbm_probe_async(lbm_handle h, int n, const int64_t *cells_dev, double *p_dev);
+
 /* lbm_sync -- wait for all work of h; returns any pending execution error,
  * including a bulk copy of the row-staged kernel that timed out. */
 int lbm_sync(lbm_handle h);

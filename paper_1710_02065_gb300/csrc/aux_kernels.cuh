@@ -231,18 +231,26 @@ __global__ void __launch_bounds__(RED_BLOCK) k_force(int nx, int ny, int nz, int
     }
 }
 
+// rho at the listed cells; pressure = 1: p' = c_s^2 (rho - rho_ref) instead.
+// A cell index outside [0, N) gives NaN (device-side lists are not checked
+// on the host).
 template <class L, class S>
 __global__ void k_probe(int n, const int64_t *__restrict__ cells, int64_t N, const S *__restrict__ f,
-                        double *__restrict__ rho)
+                        double *__restrict__ rho, int pressure, double rho_ref)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
+    const int64_t c = cells[t];
+    if (c < 0 || c >= N) {
+        rho[t] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
     double g[L::Q];
-    load_cell_fp64<L, S>(f, N, cells[t], g);
+    load_cell_fp64<L, S>(f, N, c, g);
     double dr = 0.0;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) dr += g[i];
-    rho[t] = 1.0 + dr;
+    rho[t] = pressure ? (1.0 + dr - rho_ref) / 3.0 : 1.0 + dr;
 }
 
 // Running sum of rho per cell of the stored field (FP64), for the temporal

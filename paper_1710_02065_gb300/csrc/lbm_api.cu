@@ -246,9 +246,9 @@ struct Force {
 template <class L, class S>
 struct Probe {
     static cudaError_t run(cudaStream_t st, int n, const int64_t *cells, int64_t N, const void *f,
-                           double *rho)
+                           double *rho, int pressure, double rho_ref)
     {
-        k_probe<L, S><<<grid1(n, 128), 128, 0, st>>>(n, cells, N, (const S *)f, rho);
+        k_probe<L, S><<<grid1(n, 128), 128, 0, st>>>(n, cells, N, (const S *)f, rho, pressure, rho_ref);
         return cudaGetLastError();
     }
 };
@@ -1306,6 +1306,31 @@ extern "C" int lbm_force(lbm_handle h, int level, double F[3])
     return LBM_OK;
 }
 
+extern "C" int lbm_force_async(lbm_handle h, int level, double *F_dev)
+{
+    CHECK_HANDLE(h);
+    if (!F_dev) return fail(h, LBM_EINVAL, "F_dev is null");
+    GridRef g;
+    int rc = level_ref(h, level, g);
+    if (rc != LBM_OK) return rc;
+    cudaError_t e;
+    if (!g.mask) {
+        e = cudaMemsetAsync(F_dev, 0, 3 * sizeof(double), h->stream);
+    } else {
+        int per[3] = {1, 1, 1};
+        if (level == 0)
+            for (int a = 0; a < 3; ++a) per[a] = h->kind[2 * a] == LBM_BC_PERIODIC ? 1 : 0;
+        e = dispatch<Force>(h->lattice, h->prec, h->stream, (const int *)g.n, (const int *)per,
+                            (const void *)g.f[*g.cur], g.mask, h->red_d, h->red_blocks);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(F_dev, h->red_d + (size_t)h->red_blocks * RED_FIELDS, 3 * sizeof(double),
+                                cudaMemcpyDeviceToDevice, h->stream);
+        h->launches += 2;
+    }
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "lbm_force_async: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
 extern "C" int lbm_level_info(lbm_handle h, int level, int extents[3], double *tau)
 {
     CHECK_HANDLE(h);
@@ -1627,7 +1652,7 @@ extern "C" int lbm_probe(lbm_handle h, int n, const int64_t *cells, double *p_pr
     cudaError_t e = cudaMemcpyAsync(cd, cells, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = dispatch<Probe>(h->lattice, h->prec, h->stream, n, (const int64_t *)cd, h->ncell,
-                            (const void *)h->f[h->cur], rd);
+                            (const void *)h->f[h->cur], rd, 0, 0.0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p_prime, rd, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1635,6 +1660,19 @@ extern "C" int lbm_probe(lbm_handle h, int n, const int64_t *cells, double *p_pr
     h->launches += 1;
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "lbm_probe: %s", cudaGetErrorString(e));
     for (int k = 0; k < n; ++k) p_prime[k] = (p_prime[k] - h->rho_ref) / 3.0;
+    return LBM_OK;
+}
+
+extern "C" int lbm_probe_async(lbm_handle h, int n, const int64_t *cells_dev, double *p_dev)
+{
+    CHECK_HANDLE(h);
+    if (n < 0) return fail(h, LBM_EINVAL, "n < 0");
+    if (n == 0) return LBM_OK;
+    if (!cells_dev || !p_dev) return fail(h, LBM_EINVAL, "cells_dev and p_dev are required");
+    const cudaError_t e = dispatch<Probe>(h->lattice, h->prec, h->stream, n, cells_dev, h->ncell,
+                                          (const void *)h->f[h->cur], p_dev, 1, h->rho_ref);
+    h->launches += 1;
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "lbm_probe_async: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
 

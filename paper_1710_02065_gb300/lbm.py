@@ -77,6 +77,8 @@ _sig("lbm_get_staging", [_h, _ip, _ip, _ip, _ip, _ip])
 _sig("lbm_info", [_h, _i64p, _i64p, _dp, _dp])
 _sig("lbm_add_refinement_patch", [_h, _ip, _ip])
 _sig("lbm_force", [_h, C.c_int, _dp])
+_sig("lbm_force_async", [_h, C.c_int, C.c_void_p])
+_sig("lbm_probe_async", [_h, C.c_int, C.c_void_p, C.c_void_p])
 _sig("lbm_level_info", [_h, C.c_int, _ip, _dp])
 _sig("lbm_set_geometry_level", [_h, C.c_int, C.POINTER(C.c_uint8)])
 _sig("lbm_set_state_level", [_h, C.c_int, _dp, _dp])
@@ -107,7 +109,7 @@ EXPORTED = [
     "lbm_probe", "lbm_sync", "lbm_info", "lbm_save", "lbm_load", "lbm_set_launch", "lbm_get_launch",
     "lbm_set_staging", "lbm_get_staging", "lbm_set_transfer_staging", "lbm_set_collision", "lbm_set_sponge_jet_reference", "lbm_set_hermite_order",
     "lbm_pressure_mean", "lbm_pressure_fluctuation",
-    "lbm_add_refinement_patch", "lbm_level_info", "lbm_force", "lbm_set_geometry_level", "lbm_set_state_level",
+    "lbm_add_refinement_patch", "lbm_level_info", "lbm_force", "lbm_force_async", "lbm_probe_async", "lbm_set_geometry_level", "lbm_set_state_level",
     "lbm_set_populations_level", "lbm_get_populations_level", "lbm_moments_level",
     "lbm_reduce_noalloc", "lbm_server_create", "lbm_server_destroy", "lbm_server_last_error",
     "lbm_server_submit", "lbm_server_run", "lbm_server_poll", "lbm_server_result", "lbm_server_stats",
@@ -327,6 +329,16 @@ def lbm_force(h, level: int = 0) -> np.ndarray:
     F = np.zeros(3)
     _check(_lib.lbm_force(h, level, _d(F)), h)
     return F
+
+
+def lbm_force_async(h, level: int, F_dev: int):
+    """Force of a level into 3 doubles of device memory (address F_dev), no sync."""
+    return _check(_lib.lbm_force_async(h, level, C.c_void_p(F_dev)), h)
+
+
+def lbm_probe_async(h, n: int, cells_dev: int, p_dev: int):
+    """p' at n cells (device int64 list at cells_dev) into device doubles at p_dev, no sync."""
+    return _check(_lib.lbm_probe_async(h, int(n), C.c_void_p(cells_dev), C.c_void_p(p_dev)), h)
 
 
 def lbm_level_info(h, level: int):

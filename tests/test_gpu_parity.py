@@ -333,6 +333,44 @@ def test_invalid_state_is_rejected_with_its_cell():
     s.close()
 
 
+def test_async_force_and_probe_match_synchronous_calls():
+    """lbm_force_async / lbm_probe_async record into device memory without a
+    sync; their values equal lbm_force / lbm_probe (an out-of-range index
+    gives NaN)."""
+    torch = pytest.importorskip("torch")
+    from paper_1710_02065_gb300 import lbm, inputs
+    nx, ny = 96, 64
+    s = lbm.Solver(D2Q9, (nx, ny, 1), 0.6, PRECS["fp64"])
+    lbm.lbm_set_boundary(s.h, 0, lbm.LBM_BC_VELOCITY, (0.05, 0, 0))
+    lbm.lbm_set_boundary(s.h, 1, lbm.LBM_BC_OUTFLOW)
+    lbm.lbm_set_sponge(s.h, 1, 16, 0.5, 1.0, (0.05, 0, 0))
+    solid = inputs.cylinder_mask(nx, ny, 30, 32, 10.0)
+    lbm.lbm_set_geometry(s.h, solid)
+    rho, u = np.ones(nx * ny), np.zeros((nx * ny, 3))
+    u[:, 0] = 0.05
+    u[solid == 1] = 0
+    s.set_state(rho, u)
+    cells = np.array([5 + nx * 7, 60 + nx * 40, nx * ny - 1], dtype=np.int64)
+    cd = torch.tensor(list(cells) + [nx * ny], dtype=torch.int64, device="cuda")
+    Fd = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
+    pd = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
+    F_ref, p_ref = [], []
+    for k in range(4):
+        s.step(5)
+        F_ref.append(lbm.lbm_force(s.h, 0))
+        p_ref.append(lbm.lbm_probe(s.h, cells))
+        lbm.lbm_force_async(s.h, 0, Fd[k].data_ptr())
+        lbm.lbm_probe_async(s.h, 4, cd.data_ptr(), pd[k].data_ptr())
+    s.sync()
+    torch.cuda.synchronize()
+    assert np.abs(Fd.cpu().numpy() - np.array(F_ref)).max() == 0.0
+    assert np.abs(F_ref[-1]).max() > 0
+    p = pd.cpu().numpy()
+    assert np.abs(p[:, :3] - np.array(p_ref)).max() <= 1e-17
+    assert np.isnan(p[:, 3]).all()
+    s.close()
+
+
 def test_checkpoint_resume_is_bit_identical(tmp_path):
     c = _boxed_case(D2Q9, seed=4)
     a = to_gpu(c, PRECS["fp32"])
