@@ -209,6 +209,24 @@ def recorded_traffic(kernel_key: str):
     return None
 
 
+def recorded_fp64_inst(kernel_key: str):
+    """(FP64 thread instructions, FP64 flops) per cell from the committed ncu
+    counts, if they were taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_fp64_inst.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel_key and parts[1] == src:
+            return float(parts[2]), float(parts[3])
+    return None
+
+
+# GB300 FP64: 1.25 TFLOP/s nominal = 625 G FMA instructions/s (no measured FP64 peak is available)
+FP64_INST_PEAK_G = 625.0
+
+
 def dist_setup():
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -243,12 +261,18 @@ def barrier(pg):
 # ---------------------------------------------------------------------------
 # timing of one precision
 # ---------------------------------------------------------------------------
-def time_precision(lbm, torch, spec, precision, steps, warmup, pg, stream, tune=True):
+def time_precision(lbm, torch, spec, precision, steps, warmup, pg, stream, tune=True, launch=None):
+    """launch: a fixed (kind, knob) candidate instead of tuning, e.g. ("cell", 64)."""
     from paper_1710_02065_gb300 import autotune
     s = configure_gpu(lbm, spec, precision, stream.cuda_stream)
     n = s.ncell
     s.set_state(np.ones(n), np.zeros((n, 3)))
-    tuned = autotune.autotune(s.h, precision, stream, steps=5, torch=torch)[1] if tune else {}
+    tuned = {}
+    if launch is not None:
+        if not autotune.apply(s.h, launch):
+            raise SystemExit(f"--launch {launch[0]}:{launch[1]} does not apply to this lattice / size")
+    elif tune:
+        tuned = autotune.autotune(s.h, precision, stream, steps=5, torch=torch)[1]
     launch = autotune.describe(s.h)
     lbm.lbm_step(s.h, warmup)
     s.sync()
@@ -656,6 +680,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape (no autotuning)")
+    ap.add_argument("--launch", default=None,
+                    help="fixed kernel and launch shape for the main precision instead of tuning: "
+                         "cell:BLOCK, vec2:BLOCK, vec4:BLOCK or rows:STAGES")
     ap.add_argument("--workload", default="jet", choices=["jet", "cylinder", "cylinder2level", "cylinder3level",
                                                           "jet2level", "serving"],
                     help="jet: the headline benchmark line; the others print their own JSON line")
@@ -704,7 +731,12 @@ def main():
     stream = torch.cuda.Stream()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    main_run = time_precision(lbm, torch, spec, prec, args.steps, args.warmup, pg, stream, tune=not args.no_tune)
+    fixed = None
+    if args.launch:
+        kind, knob = args.launch.split(":")
+        fixed = (kind, int(knob))
+    main_run = time_precision(lbm, torch, spec, prec, args.steps, args.warmup, pg, stream, tune=not args.no_tune,
+                              launch=fixed)
     clk = clocks.stop()
     total_s = max_over_ranks(main_run["total_ms"] / 1e3, pg, world)
     ncell = main_run["ncell"]
@@ -734,6 +766,16 @@ def main():
             extra[name] = {"launch": r["launch"], "mlups": r["ncell"] / (k_ms / 1e3) / 1e6,
                            "gbs": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9,
                            "frac_of_measured_hbm": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9 / peak}
+            if name == "fp64":
+                kk = "k_stream_collide_vec" if r["launch"]["kernel"].startswith("vec") else "k_stream_collide"
+                ins = recorded_fp64_inst(f"{kk}_d3q19_fp64_jet")
+                if ins is not None and r["launch"]["kernel"] in ("cell", "vec2"):
+                    rate = extra[name]["mlups"] / 1e3  # G cells/s
+                    extra[name]["roofline"] = {
+                        "bound": "alu", "achieved": rate * ins[0], "peak": FP64_INST_PEAK_G,
+                        "unit": "G FP64 instr/s", "frac": rate * ins[0] / FP64_INST_PEAK_G,
+                        "fp64_inst_per_cell": ins[0], "fp64_tflops": rate * ins[1] / 1e3,
+                        "peak_source": "nominal 1.25 TFLOP/s FP64 (625 G FMA/s); counts from profiles/ncu_fp64_inst.txt"}
         # the same jet on D3Q27 (complete third order; 27 populations, 216 B per cell in FP32)
         spec27 = dict(spec, lattice=lbm.LBM_D3Q27)
         r = time_precision(lbm, torch, spec27, lbm.PRECISIONS[args.precision], max(20, args.steps // 4),
