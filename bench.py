@@ -756,7 +756,12 @@ def main():
     traffic = recorded_traffic(key)
 
     extra = {}
-    if not args.no_extra:
+    # the other precisions, lattices and studies are properties of one GPU: the
+    # single-GPU run reports them, replica runs (N > 1) time the main line only
+    run_extra = not args.no_extra and world == 1
+    if not args.no_extra and world > 1:
+        extra["note"] = "per-GPU extras (other precisions, D3Q27, p' errors, A/B, serving) are in the N = 1 run"
+    if run_extra:
         for name in ("fp16", "bf16", "fp64"):
             if name == args.precision:
                 continue
@@ -790,7 +795,7 @@ def main():
         if "bf16" in extra:
             extra["bf16_store_speedup"] = extra["bf16"]["mlups"] / (ncell / (kernel_ms / 1e3) / 1e6)
 
-    if not args.no_extra:
+    if run_extra:
         extra["pprime_error_vs_fp64"] = pprime_errors(lbm, torch, stream)
         extra["stability_ab"] = stability_ab(lbm, stream)
         from paper_1710_02065_gb300 import inputs as _inp, serving as _srv
