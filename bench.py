@@ -51,6 +51,12 @@ def jet_spec(nx=384, ny=256, nz=256, diameter=24.0, sponge=32, Ma=0.3, Re=1e4, c
                 noise=noise, theta=diameter / 40.0, lattice=1)
 
 
+def jet_workload_name(nx, ny, nz):
+    """The workload both benchmark arms name in their config."""
+    return (f"D3Q19 round jet {nx}x{ny}x{nz}, Re_D 1e4, Ma 0.3, two-lattice pull, fused inflow/outflow/sponge "
+            "(storage precision in config.storage)")
+
+
 def configure_gpu(lbm, spec, precision, stream):
     from paper_1710_02065_gb300 import inputs
     nx, ny, nz = spec["n"]
@@ -661,7 +667,9 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "D3Q19 round jet 384x256x256 (bounded sample 64x48x48 on host cores)",
+        "config": {"workload": jet_workload_name(384, 256, 256), "cells": 384 * 256 * 256,
+                   "storage": "fp64 (the oracle)", "sample": "64x48x48 copy of the jet per step",
+                   "inlet": "top hat, tanh shear layer theta = D/40, Ma 0.3, 1% seeded noise",
                    "parallelism": "none (host, 1 thread)"},
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -828,8 +836,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic",
-            "config": {"workload": f"D3Q19 round jet {nx}x{ny}x{nz}, {args.precision} population storage, "
-                                   "two-lattice pull, fused inflow/outflow/sponge",
+            "config": {"workload": jet_workload_name(nx, ny, nz),
                        "cells": ncell, "tau": spec["tau"], "storage": args.precision,
                        "inlet": "top hat, tanh shear layer theta = D/40, Ma 0.3, 1% seeded noise",
                        "launch": main_run["launch"], "autotune_ms_per_step": main_run["tuning"],
