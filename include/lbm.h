@@ -271,7 +271,9 @@ int lbm_probe(lbm_handle h, int n, const int64_t *cells, double *p_prime);
  *   cells_per_thread : 1 = one cell per thread (the general kernel); 2 or 4 =
  *                      vectorised kernel with that many consecutive x cells per
  *                      thread (FP64: 2; FP32, FP16, BF16: 2 or 4); 0 = default
- *                      (FP32 1; FP16, BF16, FP64 2).  The vectorised kernel is used only when
+ *                      (measured fastest on GB300: 2 for FP16 / BF16 on D3Q19
+ *                      and D3Q27 and for FP32 on D3Q27, else 1).  The
+ *                      vectorised kernel is used only when
  *                      there is no cell-type mask and nx is a multiple of it;
  *                      otherwise the general kernel runs.  These kernels
  *                      run when the row-staged kernel (lbm_set_staging) is off

@@ -43,9 +43,16 @@ inline bool vec_supported(int precision, int vec)
     }
     return false;
 }
-// Defaults measured on GB300 for the D3Q19 jet (384 x 256 x 256): FP32 is
-// fastest one cell per thread; FP16/BF16 two cells (32-bit loads); FP64 two.
-inline int vec_default(int precision) { return precision == PREC_FP32 ? 1 : 2; }
+// Default cells per thread, measured on GB300 (round jet 384 x 256 x 256,
+// G cell updates/s, one cell per thread vs two): D3Q19 FP16 52.9 vs 63.2,
+// FP64 2.05 vs 2.00, FP32 at the copy bandwidth either way; D3Q27 FP32 31.4
+// vs 32.4, FP16 38.0 vs 44.5; D2Q9 (1600 x 800) FP32 89 vs 81, FP16 96 vs 83.
+inline int vec_default(int lattice, int precision)
+{
+    if (lattice == 0 /* D2Q9 */ || precision == PREC_FP64) return 1;
+    if (precision == PREC_FP32) return lattice == 2 /* D3Q27 */ ? 2 : 1;
+    return 2;
+}
 inline int block_default(int vec) { return vec == 1 ? 128 : 64; }
 
 // Row-staged kernel (bulk copies of whole rows into shared memory; FP32,

@@ -953,7 +953,7 @@ static cudaError_t launch_update(lbm_ctx *h, const StepParams &p, const void *fi
             return e;
         }
     }
-    int vec = h->vec == 0 ? vec_default(h->prec) : h->vec;
+    int vec = h->vec == 0 ? vec_default(h->lattice, h->prec) : h->vec;
     if (p.solid || vec == 1 || !vec_supported(h->prec, vec) || p.n[0] % vec != 0) vec = 1;
     const int block = h->block > 0 ? h->block : block_default(vec);
     h->launches += 1;
@@ -1420,7 +1420,7 @@ extern "C" int lbm_set_launch(lbm_handle h, int block, int cells_per_thread)
 extern "C" int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread)
 {
     CHECK_HANDLE(h);
-    int vec = h->vec == 0 ? vec_default(h->prec) : h->vec;
+    int vec = h->vec == 0 ? vec_default(h->lattice, h->prec) : h->vec;
     if (h->solid_d || vec == 1 || !vec_supported(h->prec, vec) || h->n[0] % vec != 0) vec = 1;
     if (block) *block = h->block > 0 ? h->block : block_default(vec);  // level 0
     if (cells_per_thread) *cells_per_thread = vec;
