@@ -470,10 +470,14 @@ int lbm_get_populations_level(lbm_handle h, int level, double *f);
 int lbm_moments_level(lbm_handle h, int level, double *rho, double *u, double *pi_neq);
 
 /*
- * lbm_save / lbm_load -- write / read the stored field and step counter to a
- * host file (raw storage format with a header).  lbm_load requires a handle
- * created with the same lattice, extents and precision (else LBM_EINVAL).
- * Boundary rules, geometry and sponges are not part of the file.
+ * lbm_save / lbm_load -- checkpoint and resume: write / read the stored
+ * field of every level (raw storage format), the refined levels' interface
+ * moments at the current time, the pressure-mean accumulator (if sampled)
+ * and the step counter to a host file with a header.  A run resumed from
+ * the file continues bit for bit as the run that wrote it.  lbm_load
+ * requires a handle configured the same way: lattice, precision, extents and
+ * the same refinement patches (else LBM_EINVAL, before any state changes);
+ * boundary rules, geometry, sponges and options are not part of the file.
  */
 int lbm_save(lbm_handle h, const char *path);
 int lbm_load(lbm_handle h, const char *path);

@@ -113,6 +113,11 @@ static GridRef level_grid(lbm_ctx *h, int k)
     return GridRef{{F->n[0], F->n[1], F->n[2]}, F->ncell, F->f, &F->cur, F->mask_d};
 }
 static double level_tau(lbm_ctx *h, int k) { return k == 0 ? h->tau : fine_level(h, k)->tau; }
+// Bytes of one interface-moment buffer of a refined level (sized for FP64)
+static size_t moment_bytes(bool three, const RefineGeom &g)
+{
+    return three ? sizeof(double) * 10 * (size_t)box3_entries(g) : sizeof(double) * 6 * (size_t)line_count(g);
+}
 // The mask the interface kernels test for bounce-back links: null when the
 // level holds no solid cells (its fixed cells need no test there)
 static const uint8_t *links_mask(lbm_ctx *h, int k)
@@ -1251,8 +1256,7 @@ extern "C" int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const
     F->tau = 2.0 * level_tau(h, parent) - 0.5;
     F->geom = RefineGeom{X0, Y0, Wc, Hc, P.n[0], P.n[1], F->n[0], F->n[1], Z0, Dc, P.n[2], F->n[2]};
     const size_t bytes = (size_t)h->q * (size_t)F->ncell * h->elem;
-    const size_t mbytes = three ? sizeof(double) * 10 * (size_t)box3_entries(F->geom)
-                                : sizeof(double) * 6 * (size_t)line_count(F->geom);
+    const size_t mbytes = moment_bytes(three, F->geom);
     bool ok = true;
     for (int k = 0; k < 2 && ok; ++k)
         ok = cudaMalloc(&F->f[k], bytes) == cudaSuccess && cudaMalloc(&F->M[k], mbytes) == cudaSuccess &&
@@ -1689,30 +1693,62 @@ extern "C" int lbm_info(lbm_handle h, int64_t *step, int64_t *launches, double *
 // ---------------------------------------------------------------------------
 // Checkpoint
 // ---------------------------------------------------------------------------
+// Checkpoint file: header, then per level (0 = coarse / single) its extents
+// and current field in the storage format; per refined level its interface
+// moments at the current time; the pressure-mean accumulator if sampled.
 struct FileHeader {
     char magic[8];
-    int32_t lattice, prec, n[3], pad;
+    int32_t lattice, prec, n[3], nlevels;
     int64_t step;
+    int64_t rho_count;
 };
+
+static bool write_all(FILE *fp, const void *p, size_t n) { return std::fwrite(p, 1, n, fp) == n; }
+static bool read_all(FILE *fp, void *p, size_t n) { return std::fread(p, 1, n, fp) == n; }
 
 extern "C" int lbm_save(lbm_handle h, const char *path)
 {
     CHECK_HANDLE(h);
     if (!path) return fail(h, LBM_EINVAL, "path is null");
-    const size_t bytes = (size_t)h->q * (size_t)h->ncell * h->elem;
-    std::vector<char> host(bytes);
-    CUDA_TRY(h, cudaMemcpyAsync(host.data(), h->f[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     FileHeader hd{};
-    std::memcpy(hd.magic, "LBMRRv01", 8);
+    std::memcpy(hd.magic, "LBMRRv02", 8);
     hd.lattice = h->lattice;
     hd.prec = h->prec;
     for (int a = 0; a < 3; ++a) hd.n[a] = h->n[a];
+    hd.nlevels = nlevels(h);
     hd.step = h->step;
+    hd.rho_count = h->rho_acc ? h->rho_count : 0;
     FILE *fp = std::fopen(path, "wb");
     if (!fp) return fail(h, LBM_EIO, "cannot open %s for writing", path);
-    bool ok = std::fwrite(&hd, sizeof hd, 1, fp) == 1 && std::fwrite(host.data(), 1, bytes, fp) == bytes;
+    bool ok = write_all(fp, &hd, sizeof hd);
+    std::vector<char> host;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < hd.nlevels && ok && e == cudaSuccess; ++k) {
+        const GridRef g = level_grid(h, k);
+        const int32_t ext[4] = {g.n[0], g.n[1], g.n[2], 0};
+        const size_t bytes = (size_t)h->q * (size_t)g.ncell * h->elem;
+        host.resize(bytes);
+        e = cudaMemcpyAsync(host.data(), g.f[*g.cur], bytes, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        ok = e == cudaSuccess && write_all(fp, ext, sizeof ext) && write_all(fp, host.data(), bytes);
+    }
+    for (int k = 1; k < hd.nlevels && ok && e == cudaSuccess; ++k) {
+        FineLevel *F = fine_level(h, k);
+        const size_t mb = moment_bytes(h->d == 3, F->geom);
+        host.resize(mb);
+        e = cudaMemcpyAsync(host.data(), F->M[F->mcur], mb, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        ok = e == cudaSuccess && write_all(fp, host.data(), mb);
+    }
+    if (ok && e == cudaSuccess && hd.rho_count > 0) {
+        const size_t rb = sizeof(double) * (size_t)h->ncell;
+        host.resize(rb);
+        e = cudaMemcpyAsync(host.data(), h->rho_acc, rb, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        ok = e == cudaSuccess && write_all(fp, host.data(), rb);
+    }
     ok = (std::fclose(fp) == 0) && ok;
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "lbm_save: %s", cudaGetErrorString(e));
     if (!ok) return fail(h, LBM_EIO, "short write to %s", path);
     return LBM_OK;
 }
@@ -1724,24 +1760,61 @@ extern "C" int lbm_load(lbm_handle h, const char *path)
     FILE *fp = std::fopen(path, "rb");
     if (!fp) return fail(h, LBM_EIO, "cannot open %s", path);
     FileHeader hd{};
-    if (std::fread(&hd, sizeof hd, 1, fp) != 1 || std::memcmp(hd.magic, "LBMRRv01", 8) != 0) {
+    if (!read_all(fp, &hd, sizeof hd) || std::memcmp(hd.magic, "LBMRRv02", 8) != 0) {
         std::fclose(fp);
         return fail(h, LBM_EIO, "%s is not a checkpoint", path);
     }
     if (hd.lattice != h->lattice || hd.prec != h->prec || hd.n[0] != h->n[0] || hd.n[1] != h->n[1] ||
-        hd.n[2] != h->n[2]) {
+        hd.n[2] != h->n[2] || hd.nlevels != nlevels(h)) {
         std::fclose(fp);
-        return fail(h, LBM_EINVAL, "checkpoint lattice/precision/extents differ from the handle's");
+        return fail(h, LBM_EINVAL, "checkpoint lattice/precision/extents/levels differ from the handle's");
     }
-    const size_t bytes = (size_t)h->q * (size_t)h->ncell * h->elem;
-    std::vector<char> host(bytes);
-    bool ok = std::fread(host.data(), 1, bytes, fp) == bytes;
+    // read everything before touching the device state
+    std::vector<std::vector<char>> fields((size_t)hd.nlevels), moms((size_t)hd.nlevels);
+    bool ok = true;
+    for (int k = 0; k < hd.nlevels && ok; ++k) {
+        const GridRef g = level_grid(h, k);
+        int32_t ext[4];
+        ok = read_all(fp, ext, sizeof ext);
+        if (ok && (ext[0] != g.n[0] || ext[1] != g.n[1] || ext[2] != g.n[2])) {
+            std::fclose(fp);
+            return fail(h, LBM_EINVAL, "checkpoint level %d extents differ from the handle's", k);
+        }
+        fields[(size_t)k].resize((size_t)h->q * (size_t)g.ncell * h->elem);
+        ok = ok && read_all(fp, fields[(size_t)k].data(), fields[(size_t)k].size());
+    }
+    for (int k = 1; k < hd.nlevels && ok; ++k) {
+        moms[(size_t)k].resize(moment_bytes(h->d == 3, fine_level(h, k)->geom));
+        ok = read_all(fp, moms[(size_t)k].data(), moms[(size_t)k].size());
+    }
+    std::vector<double> racc;
+    if (ok && hd.rho_count > 0) {
+        racc.resize((size_t)h->ncell);
+        ok = read_all(fp, racc.data(), sizeof(double) * racc.size());
+    }
     std::fclose(fp);
     if (!ok) return fail(h, LBM_EIO, "short read from %s", path);
-    CUDA_TRY(h, cudaMemcpyAsync(h->f[0], host.data(), bytes, cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(h, cudaMemcpyAsync(h->f[1], host.data(), bytes, cudaMemcpyHostToDevice, h->stream));
+    for (int k = 0; k < hd.nlevels; ++k) {
+        const GridRef g = level_grid(h, k);
+        const std::vector<char> &fk = fields[(size_t)k];
+        CUDA_TRY(h, cudaMemcpyAsync(g.f[0], fk.data(), fk.size(), cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(h, cudaMemcpyAsync(g.f[1], fk.data(), fk.size(), cudaMemcpyHostToDevice, h->stream));
+        *g.cur = 0;
+    }
+    for (int k = 1; k < hd.nlevels; ++k) {
+        FineLevel *F = fine_level(h, k);
+        CUDA_TRY(h, cudaMemcpyAsync(F->M[0], moms[(size_t)k].data(), moms[(size_t)k].size(), cudaMemcpyHostToDevice,
+                                    h->stream));
+        F->mcur = 0;
+    }
+    if (hd.rho_count > 0) {
+        const size_t rb = sizeof(double) * (size_t)h->ncell;
+        if (!h->rho_acc) CUDA_TRY(h, cudaMalloc(&h->rho_acc, rb));
+        CUDA_TRY(h, cudaMemcpyAsync(h->rho_acc, racc.data(), rb, cudaMemcpyHostToDevice, h->stream));
+    }
+    h->rho_count = hd.rho_count;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    h->cur = 0;
     h->step = hd.step;
+    h->cfg_version++;  // level parities changed: recapture the step graph
     return LBM_OK;
 }
