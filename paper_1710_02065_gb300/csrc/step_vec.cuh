@@ -20,9 +20,41 @@
 // f_opp = w (E - O).
 #pragma once
 
+#include <type_traits>
+
 #include "step.cuh"
 
 namespace rr {
+
+// Two FP32 lanes computed by one packed instruction (add / mul / fma .f32x2
+// of sm_100+): the rebuild of a thread's two cells with the same code.
+// Measured on GB300 for the D3Q19 jet: BF16 storage 59.6 -> 64.2 G cell
+// updates/s, FP16 63.1 -> 61.5, FP32 46.2 -> 44.7; so only the BF16
+// two-cell kernel uses it.
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ F2(float2 a) : v(a) {}
+    __device__ __forceinline__ F2(double c) : v(make_float2((float)c, (float)c)) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y))); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 &operator+=(F2 &a, F2 b) { a = a + b; return a; }
+__device__ __forceinline__ F2 fmac(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ Coef<F2> pack_coef(const Coef<float> &a, const Coef<float> &b)
+{
+    Coef<F2> k;
+    k.a0 = F2(a.a0, b.a0); k.a1x = F2(a.a1x, b.a1x); k.a1y = F2(a.a1y, b.a1y); k.a1z = F2(a.a1z, b.a1z);
+    k.xx = F2(a.xx, b.xx); k.yy = F2(a.yy, b.yy); k.zz = F2(a.zz, b.zz);
+    k.xy = F2(a.xy, b.xy); k.xz = F2(a.xz, b.xz); k.yz = F2(a.yz, b.yz);
+    k.xxy = F2(a.xxy, b.xxy); k.xyy = F2(a.xyy, b.xyy); k.xxz = F2(a.xxz, b.xxz);
+    k.xzz = F2(a.xzz, b.xzz); k.yyz = F2(a.yyz, b.yyz); k.yzz = F2(a.yzz, b.yzz);
+    k.xyz = F2(a.xyz, b.xyz); k.xxyy = F2(a.xxyy, b.xxyy);
+    return k;
+}
 
 // ---------------------------------------------------------------------------
 // V-wide aligned loads / stores converting to / from the compute type C
@@ -227,6 +259,24 @@ __device__ __forceinline__ void update_vec(const StepParams &p, const char *cons
 
     // ---- rebuild and store, one direction pair at a time
     const unsigned base = (unsigned)nx * y + nxy * z + x0;
+    if constexpr (V == 2 && std::is_same<S, __nv_bfloat16>::value) {
+        const Coef<F2> c2 = pack_coef(cf[0], cf[1]);
+        const RebuildPre<F2> r2 = rebuild_prep<L, F2>(c2);
+        {
+            const F2 g0 = rebuild_rest<L, F2>(c2, r2);
+            C o[V] = {g0.v.x, g0.v.y};
+            VecIO<S, V>::st((S *)out[0] + base, o);
+        }
+#pragma unroll
+        for (int i = 1; i <= L::HALF; ++i) {
+            F2 p2, m2;
+            rebuild_pair<L, F2>(c2, r2, i, p2, m2);
+            C op[V] = {p2.v.x, p2.v.y}, om[V] = {m2.v.x, m2.v.y};
+            VecIO<S, V>::st((S *)out[i] + base, op);
+            VecIO<S, V>::st((S *)out[i + L::HALF] + base, om);
+        }
+        return;
+    }
     RebuildPre<C> rp[V];
 #pragma unroll
     for (int k = 0; k < V; ++k) rp[k] = rebuild_prep<L, C>(cf[k]);
