@@ -393,7 +393,7 @@ class TwoLevel:
 
 
 class TwoLevel3:
-    """Two-level 2:1 D3Q19 grid (Sec. II.B): a coarse Problem plus a fine patch
+    """Two-level 2:1 D3Q19 or D3Q27 grid (Sec. II.B): a coarse Problem plus a fine patch
     over coarse nodes X0..X0+Wc, Y0..Y0+Hc, Z0..Z0+Dc, tau_f = 2 tau_c - 1/2.
 
     The fine problem is periodic with its boundary shell fixed (rebuilt from
@@ -403,14 +403,14 @@ class TwoLevel3:
     """
 
     def __init__(self, coarse: Problem, X0: int, Y0: int, Z0: int, Wc: int, Hc: int, Dc: int):
-        assert coarse.lattice == D3Q19
+        assert coarse.lattice in (D3Q19, D3Q27)
         nxc, nyc, nzc = coarse.n
         assert min(X0, Y0, Z0) >= 2 and min(Wc, Hc, Dc) >= 4
         assert X0 + Wc <= nxc - 3 and Y0 + Hc <= nyc - 3 and Z0 + Dc <= nzc - 3
         self.Pc = coarse
         self.patch = (X0, Y0, Z0, Wc, Hc, Dc)
         nf = (2 * Wc + 1, 2 * Hc + 1, 2 * Dc + 1)
-        self.Pf = Problem(D3Q19, nf, 2 * coarse.tau - 0.5)
+        self.Pf = Problem(coarse.lattice, nf, 2 * coarse.tau - 0.5)
         shape_c = (nzc, nyc, nxc)
         cmask = np.zeros(shape_c, np.uint8) if coarse.solid is None else coarse.solid.reshape(shape_c).copy()
         cmask[Z0 + 1:Z0 + Dc, Y0 + 1:Y0 + Hc, X0 + 1:X0 + Wc] = FIXED
@@ -482,7 +482,7 @@ class MultiLevel:
     """
 
     def __init__(self, coarse: Problem, patches):
-        self.three = coarse.lattice == D3Q19
+        self.three = coarse.lattice in (D3Q19, D3Q27)
         self.P = [coarse]
         self.G = []
         for origin, extent in patches:

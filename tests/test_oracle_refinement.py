@@ -90,16 +90,16 @@ def test_couette_flow_stays_linear_across_interface():
 # ---------------------------------------------------------------------------
 # D3Q19 patches (the 2D layout extended by one axis)
 # ---------------------------------------------------------------------------
-from oracle import D3Q19, TwoLevel3  # noqa: E402
+from oracle import D3Q19, D3Q27, TwoLevel3  # noqa: E402
 
 
-def _couette3(U, nsteps, n=(12, 12, 12), patch=(3, 3, 3, 6, 6, 6), tau=0.7):
+def _couette3(U, nsteps, n=(12, 12, 12), patch=(3, 3, 3, 6, 6, 6), tau=0.7, lattice=D3Q19):
     """Couette flow u_x(y) between velocity walls on the y faces, x and z
     periodic, through a 3D patch; returns the largest deviation of the fine
     velocity from the linear profile."""
     nx, ny, nz = n
     X0, Y0, Z0, Wc, Hc, Dc = patch
-    P = Problem(D3Q19, n, tau)
+    P = Problem(lattice, n, tau)
     P.set_boundary(2, VELOCITY, (0, 0, 0))
     P.set_boundary(3, VELOCITY, (U, 0, 0))
     T = TwoLevel3(P, *patch)
@@ -116,8 +116,9 @@ def _couette3(U, nsteps, n=(12, 12, 12), patch=(3, 3, 3, 6, 6, 6), tau=0.7):
     return np.abs(uff - uf).max()
 
 
-def test_uniform_stream_crosses_3d_interface_unchanged():
-    P = Problem(D3Q19, (20, 18, 16), 0.6)
+@pytest.mark.parametrize("lattice", [D3Q19, D3Q27])
+def test_uniform_stream_crosses_3d_interface_unchanged(lattice):
+    P = Problem(lattice, (20, 18, 16), 0.6)
     T = TwoLevel3(P, 5, 4, 4, 8, 8, 6)
     U = (0.04, -0.02, 0.01)
     T.init(np.ones(P.ncell), np.tile(U, (P.ncell, 1)), np.ones(T.Pf.ncell), np.tile(U, (T.Pf.ncell, 1)))
@@ -140,6 +141,18 @@ def test_3d_couette_interface_error_is_second_order_in_shear():
     e2 = _couette3(0.02, 600)
     assert e1 < 2e-6
     assert 3.5 < e1 / e2 < 4.5, (e1, e2)
+
+
+def test_3d_couette_crosses_a_d3q27_interface_exactly():
+    """The same flow on D3Q27 patches, whose levels rebuild with the complete
+    third-order Hermite set: the O(G^2) deviation that D3Q19's paired third
+    order leaves (previous test) is absent, and what remains is the start-up
+    transient, which decays (1e-8 after 600 steps, round-off after 1800).  A
+    rescaling wrong at first order would leave a steady O(G) deviation."""
+    e600 = _couette3(0.04, 600, lattice=D3Q27)
+    e1800 = _couette3(0.04, 1800, lattice=D3Q27)
+    assert e600 < 1e-7
+    assert e1800 < 1e-10 and e1800 < 1e-2 * e600, (e600, e1800)
 
 
 def _poly_moments(P, deg):
