@@ -60,8 +60,8 @@ typedef struct lbm_ctx *lbm_handle;
 
 /* Lattices (Sec. II.A: D2Q9 in 2D, D3Q19 in 3D).  LBM_D3Q27, the tensor
  * product of D1Q3, carries the complete third-order Hermite set (the six
- * H_aab and H_xyz) that D3Q19 can only keep as pairs; single level, general
- * and two-cell kernels (no refinement patches, not in the solve server). */
+ * H_aab and H_xyz) that D3Q19 can only keep as pairs; general and two-cell
+ * kernels, refinement patches (not in the solve server). */
 #define LBM_D2Q9 0
 #define LBM_D3Q19 1
 #define LBM_D3Q27 2
@@ -430,13 +430,14 @@ int lbm_info(lbm_handle h, int64_t *step, int64_t *launches, double *bytes_per_c
              double *tau);
 
 /*
- * Refined levels (Sec. II.B, multi-domain 2:1 refinement; D2Q9 and D3Q19).
+ * Refined levels (Sec. II.B, multi-domain 2:1 refinement; D2Q9, D3Q19 and
+ * D3Q27).
  *
  * lbm_add_refinement_patch -- add a level inside the finest existing level
  * (the first call refines level 0, the next one nests inside it, ...; at
  * most LBM_MAX_LEVELS levels in all).  The new level covers the parent-level
  * nodes origin[a]..origin[a]+extent[a] on every axis a of the lattice (x, y;
- * and z for D3Q19; extent >= 4, at least 2 cells from every face of the
+ * and z in 3D; extent >= 4, at least 2 cells from every face of the
  * parent).  It has 2 extent[a] + 1 nodes per axis, half the parent's spacing,
  * two steps per parent step (Eq. convective), tau = 2 tau_parent - 1/2 (same
  * physical viscosity), and starts at rest.  Coupling per parent step: the new

@@ -989,8 +989,8 @@ static void fine_params(lbm_ctx *h, int k, StepParams &p)
     set_bulk_box(p);
 }
 
-// D3Q19 patch: plane moments, fine shell, covered coarse shell
-template <class S>
+// 3D patch (D3Q19 or D3Q27): plane moments, fine shell, covered coarse shell
+template <class L, class S>
 static cudaError_t refine_kernels3(lbm_ctx *h, int k, int stage, int a_half)
 {
     FineLevel *F = fine_level(h, k);
@@ -1004,14 +1004,14 @@ static cudaError_t refine_kernels3(lbm_ctx *h, int k, int stage, int a_half)
         const int n = plane3_count(g);
         // the moment buffers (sized for FP64) hold the compute type
         CT<S> *M = (CT<S> *)(stage == 0 ? F->M[1 - F->mcur] : F->M[F->mcur]);
-        k_plane_moments3<S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], links_mask(h, k - 1),
+        k_plane_moments3<L, S><<<grid1(n, 128), 128, 0, st>>>(g, (const S *)P.f[*P.cur], links_mask(h, k - 1),
                                                             stage == 0 ? 1 : 0, M);
         break;
     }
     case 1: {  // fine shell at t + 1/2 (a_half = 1) or t + 1 (a_half = 0)
         const int n = shell3_count(g.nfx, g.nfy, g.nfz);
         // 4 threads per shell node
-        k_fill_shell3<S><<<grid1(4 * (int64_t)n, 256), 256, 0, st>>>(
+        k_fill_shell3<L, S><<<grid1(4 * (int64_t)n, 256), 256, 0, st>>>(
             g, (const CT<S> *)F->M[F->mcur], (const CT<S> *)F->M[1 - F->mcur], CT<S>(a_half ? 0.5 : 1.0),
             CT<S>(F->tau / (2.0 * tau_p)), CT<S>(1.0 - 1.0 / F->tau), (S *)F->f[F->cur]);
         break;
@@ -1019,7 +1019,7 @@ static cudaError_t refine_kernels3(lbm_ctx *h, int k, int stage, int a_half)
     case 2: {  // covered coarse shell from the fine field; fine moments pulled from f(t + 1/2)
         const int n = shell3_count(g.Wc - 1, g.Hc - 1, g.Dc - 1);
         // one warp per covered coarse node (one lane per filter point)
-        k_restrict3<S><<<grid1(32 * (int64_t)n, 256), 256, 0, st>>>(
+        k_restrict3<L, S><<<grid1(32 * (int64_t)n, 256), 256, 0, st>>>(
             g, (const S *)F->f[1 - F->cur], links_mask(h, k), CT<S>(2.0 * tau_p / F->tau), CT<S>(1.0 - 1.0 / tau_p),
             (S *)P.f[*P.cur]);
         break;
@@ -1037,7 +1037,8 @@ static cudaError_t refine_kernels3(lbm_ctx *h, int k, int stage, int a_half)
 template <class S>
 static cudaError_t refine_kernels(lbm_ctx *h, int k, int stage, int a_half)
 {
-    if (h->d == 3) return refine_kernels3<S>(h, k, stage, a_half);
+    if (h->lattice == LBM_D3Q27) return refine_kernels3<D3Q27, S>(h, k, stage, a_half);
+    if (h->d == 3) return refine_kernels3<D3Q19, S>(h, k, stage, a_half);
     FineLevel *F = fine_level(h, k);
     const GridRef P = level_grid(h, k - 1);
     const double tau_p = level_tau(h, k - 1);
@@ -1233,7 +1234,6 @@ extern "C" int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const
         return fail(h, LBM_EINVAL, "refinement patches couple rrBGK levels; select LBM_COLLISION_RR first");
     if (h->order4) return fail(h, LBM_EINVAL, "refinement patches couple order-3 levels; set order 3 first");
     if (!origin || !extent) return fail(h, LBM_EINVAL, "origin and extent are required");
-    if (h->lattice == LBM_D3Q27) return fail(h, LBM_EINVAL, "refinement patches are implemented for D2Q9 and D3Q19");
     if (h->levels.size() >= LBM_MAX_LEVELS - 1)
         return fail(h, LBM_EINVAL, "at most %d levels", LBM_MAX_LEVELS);
     const int parent = nlevels(h) - 1;  // the new patch nests inside the finest level

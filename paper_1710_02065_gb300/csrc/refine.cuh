@@ -1,5 +1,6 @@
 // refine.cuh -- 2:1 grid coupling kernels of a parent / child level pair (Sec. II.B, Eq. couplingCF,
-// Eq. couplingFC), D2Q9 and D3Q19 (the 3D kernels are at the end of the file).
+// Eq. couplingFC), D2Q9, and D3Q19 / D3Q27 (the 3D kernels, templated on the
+// lattice, are at the end of the file).
 // Below, "coarse" is the parent level of a pair and "fine" its child; nested
 // levels apply these kernels pair by pair.
 //
@@ -32,7 +33,7 @@ namespace rr {
 struct RefineGeom {
     int X0, Y0, Wc, Hc;
     int nxc, nyc, nfx, nfy;
-    // third axis of a D3Q19 patch (zero / one for D2Q9)
+    // third axis of a 3D patch (zero / one for D2Q9)
     int Z0, Dc, nzc, nfz;
 };
 
@@ -236,7 +237,7 @@ __global__ void k_restrict(RefineGeom g, const S *__restrict__ ff_prev, const ui
 }
 
 // ===========================================================================
-// D3Q19 patches.  The fine patch covers the coarse nodes X0..X0+Wc,
+// D3Q19 and D3Q27 patches.  The fine patch covers the coarse nodes X0..X0+Wc,
 // Y0..Y0+Hc, Z0..Z0+Dc; fine node (i, j, k) sits at (X0 + i/2, Y0 + j/2,
 // Z0 + k/2).  The fine boundary shell is rebuilt from coarse data, the first
 // shell of covered coarse nodes from fine data.  Interface moments m = (rho -
@@ -295,68 +296,68 @@ __device__ inline void pack_moments3(const Mom<C> &mo, C m[10])
 
 // Pre-collision moments at (x, y, z) of a 3D lattice: pull with periodic
 // wrap and halfway bounce-back on mask == 1.
-template <class S>
+template <class L, class S>
 __device__ void streamed_moments_3d(const S *__restrict__ f, const uint8_t *__restrict__ mask, int nx, int ny,
                                     int nz, int x, int y, int z, CT<S> m[10])
 {
     using C = CT<S>;
     const int64_t N = (int64_t)nx * ny * nz;
     const int64_t cell = x + (int64_t)nx * (y + (int64_t)ny * z);
-    C g[19];
+    C g[L::Q];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        int sx = x - D3Q19::cx(i), sy = y - D3Q19::cy(i), sz = z - D3Q19::cz(i);
+    for (int i = 0; i < L::Q; ++i) {
+        int sx = x - L::cx(i), sy = y - L::cy(i), sz = z - L::cz(i);
         sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
         sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
         sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
         const int64_t src = sx + (int64_t)nx * (sy + (int64_t)ny * sz);
         if (mask && i != 0 && (mask[src] & MASK_TYPE) == MASK_SOLID)
-            g[i] = Store<S>::ld(f + (int64_t)opp<D3Q19>(i) * N + cell);
+            g[i] = Store<S>::ld(f + (int64_t)opp<L>(i) * N + cell);
         else
             g[i] = Store<S>::ld(f + (int64_t)i * N + src);
     }
-    pack_moments3<C>(moments_pairs<D3Q19, C>(g), m);
+    pack_moments3<C>(moments_pairs<L, C>(g), m);
 }
 
-template <class S>
+template <class L, class S>
 __device__ void local_moments_3d(const S *__restrict__ f, int64_t N, int64_t cell, CT<S> m[10])
 {
     using C = CT<S>;
-    C g[19];
+    C g[L::Q];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell);
-    pack_moments3<C>(moments_pairs<D3Q19, C>(g), m);
+    for (int i = 0; i < L::Q; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell);
+    pack_moments3<C>(moments_pairs<L, C>(g), m);
 }
 
 // Store feqH(rho, u) + omega fneqH(u, alpha Pi^neq) at a cell, omega = 1 - 1/tau
 // (alpha and omega come from the host in the compute type: no FP64
 // arithmetic on the device)
-template <class S>
+template <class L, class S>
 __device__ void store_rebuilt_3d(S *__restrict__ f, int64_t N, int64_t cell, const CT<S> m[10], CT<S> alpha,
                                  CT<S> omega)
 {
     using C = CT<S>;
     Coef<C> k{};
     const C rho = C(1) + m[0];
-    add_eq<C, 3>(k, C(1), m[0], rho, m[1], m[2], m[3]);
+    add_eq<C, 3, true, full_third_order<L>()>(k, C(1), m[0], rho, m[1], m[2], m[3]);
     Sym2<C> p;
     p.xx = alpha * m[4]; p.xy = alpha * m[5]; p.xz = alpha * m[6];
     p.yy = alpha * m[7]; p.yz = alpha * m[8]; p.zz = alpha * m[9];
-    add_neq<C, 3>(k, omega, m[1], m[2], m[3], p);
-    const RebuildPre<C> r = rebuild_prep<D3Q19, C>(k);
-    Store<S>::st(f + cell, rebuild_rest<D3Q19, C>(k, r));
+    add_neq<C, 3, true, full_third_order<L>()>(k, omega, m[1], m[2], m[3], p);
+    const RebuildPre<C> r = rebuild_prep<L, C>(k);
+    Store<S>::st(f + cell, rebuild_rest<L, C>(k, r));
 #pragma unroll
-    for (int i = 1; i <= D3Q19::HALF; ++i) {
+    for (int i = 1; i <= L::HALF; ++i) {
         C gp, gm;
-        rebuild_pair<D3Q19, C>(k, r, i, gp, gm);
+        rebuild_pair<L, C>(k, r, i, gp, gm);
         Store<S>::st(f + (int64_t)i * N + cell, gp);
-        Store<S>::st(f + (int64_t)(i + D3Q19::HALF) * N + cell, gm);
+        Store<S>::st(f + (int64_t)(i + L::HALF) * N + cell, gm);
     }
 }
 
 // Interface moments of the coarse plane nodes, stored in the compute type
 // (10 per node: rho - 1, u, Pi^neq)
-template <class S>
+template <class L, class S>
 __global__ void k_plane_moments3(RefineGeom g, const S *__restrict__ fc, const uint8_t *__restrict__ mask,
                                  int streamed, CT<S> *__restrict__ M)
 {
@@ -366,9 +367,9 @@ __global__ void k_plane_moments3(RefineGeom g, const S *__restrict__ fc, const u
     plane3_coord(g, t, x, y, z);
     CT<S> m[10];
     if (streamed)
-        streamed_moments_3d<S>(fc, mask, g.nxc, g.nyc, g.nzc, x, y, z, m);
+        streamed_moments_3d<L, S>(fc, mask, g.nxc, g.nyc, g.nzc, x, y, z, m);
     else
-        local_moments_3d<S>(fc, (int64_t)g.nxc * g.nyc * g.nzc, x + (int64_t)g.nxc * (y + (int64_t)g.nyc * z), m);
+        local_moments_3d<L, S>(fc, (int64_t)g.nxc * g.nyc * g.nzc, x + (int64_t)g.nxc * (y + (int64_t)g.nyc * z), m);
     const int64_t b = box3_index(g, x, y, z);
 #pragma unroll
     for (int k = 0; k < 10; ++k) M[10 * b + k] = m[k];
@@ -422,7 +423,7 @@ __device__ inline void shell3_coord(int nx, int ny, int nz, int t, int &i, int &
 // and the node's first lane rebuilds and stores it: the loads are spread
 // over more threads than one per node, while the rebuild is still shared by
 // eight nodes per warp.
-template <class S>
+template <class L, class S>
 __global__ void __launch_bounds__(256) k_fill_shell3(RefineGeom g, const CT<S> *__restrict__ M0,
                                                      const CT<S> *__restrict__ M1, CT<S> a, CT<S> alpha,
                                                      CT<S> omega, S *__restrict__ ff)
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(256) k_fill_shell3(RefineGeom g, const CT<S> *
         for (int e = 0; e < 10; ++e) m[e] += __shfl_xor_sync(0xffffffffu, m[e], o);
     }
     if (node && r == 0)
-        store_rebuilt_3d<S>(ff, (int64_t)g.nfx * g.nfy * g.nfz, i + (int64_t)g.nfx * (j + (int64_t)g.nfy * k), m,
+        store_rebuilt_3d<L, S>(ff, (int64_t)g.nfx * g.nfy * g.nfz, i + (int64_t)g.nfx * (j + (int64_t)g.nfy * k), m,
                             alpha, omega);
 }
 
@@ -472,7 +473,7 @@ __global__ void __launch_bounds__(256) k_fill_shell3(RefineGeom g, const CT<S> *
 // rescaled by alpha, rebuilt.  One warp per coarse node: lane l < 27 pulls
 // the streamed moments of stencil point l, the filtered sum is taken by
 // shuffles, and the centre lane (13) supplies rho and u.
-template <class S>
+template <class L, class S>
 __global__ void __launch_bounds__(256) k_restrict3(RefineGeom g, const S *__restrict__ ff_prev,
                                                    const uint8_t *__restrict__ fmask, CT<S> alpha, CT<S> omega,
                                                    S *__restrict__ fc)
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(256) k_restrict3(RefineGeom g, const S *__rest
     for (int e = 0; e < 10; ++e) m[e] = C(0);
     if (node && l < 27) {
         const int p = l % 3 - 1, q = (l / 3) % 3 - 1, r = l / 9 - 1;
-        streamed_moments_3d<S>(ff_prev, fmask, g.nfx, g.nfy, g.nfz, i + p, j + q, k + r, m);
+        streamed_moments_3d<L, S>(ff_prev, fmask, g.nfx, g.nfy, g.nfz, i + p, j + q, k + r, m);
         const C wt = C((p ? 1 : 2) * (q ? 1 : 2) * (r ? 1 : 2)) * C(1.0 / 64.0);
 #pragma unroll
         for (int e = 4; e < 10; ++e) m[e] *= wt;
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(256) k_restrict3(RefineGeom g, const S *__rest
         mc[e] = v;
     }
     if (node && l == 0)
-        store_rebuilt_3d<S>(fc, (int64_t)g.nxc * g.nyc * g.nzc, x + (int64_t)g.nxc * (y + (int64_t)g.nyc * z), mc,
+        store_rebuilt_3d<L, S>(fc, (int64_t)g.nxc * g.nyc * g.nzc, x + (int64_t)g.nxc * (y + (int64_t)g.nyc * z), mc,
                             alpha, omega);
 }
 

@@ -118,14 +118,14 @@ def test_two_level_full_size_few_steps():
     assert _normwise(grf[fluid_f], rf[fluid_f]) <= 1e-5 and _normwise(guf[fluid_f], uf[fluid_f]) <= 1e-5
 
 
-def _case_3d():
-    """D3Q19 box 24x20x18: inflow on -x, outflow behind a sponge on +x, y/z
-    periodic; smooth density pulse and shear on a uniform stream; a fine
-    patch over coarse [6, 16] x [5, 13] x [5, 12] holding a small solid
+def _case_3d(lattice=oracle.D3Q19):
+    """D3Q19 (or D3Q27) box 24x20x18: inflow on -x, outflow behind a sponge on
+    +x, y/z periodic; smooth density pulse and shear on a uniform stream; a
+    fine patch over coarse [6, 16] x [5, 13] x [5, 12] holding a small solid
     sphere on the fine level."""
     from cases import Case
     n = (24, 20, 18)
-    c = Case("two_level_3d", oracle.D3Q19, n, 0.6)
+    c = Case("two_level_3d", lattice, n, 0.6)
     U = 0.04
     c.faces = {0: (VELOCITY, (U, 0, 0), None), 1: (oracle.OUTFLOW, (0, 0, 0), None)}
     c.sponges = {1: (4, 0.3)}
@@ -152,12 +152,13 @@ def _case_3d():
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-5)])
-def test_two_level_3d_parity(prec, tol):
-    """D3Q19 patch (fine shell from the coarse planes, covered coarse shell
-    from the fine level) against the oracle's TwoLevel3 on both levels."""
+@pytest.mark.parametrize("lattice", [oracle.D3Q19, oracle.D3Q27])
+def test_two_level_3d_parity(prec, tol, lattice):
+    """D3Q19 / D3Q27 patch (fine shell from the coarse planes, covered coarse
+    shell from the fine level) against the oracle's TwoLevel3 on both levels."""
     from cases import to_gpu
     from paper_1710_02065_gb300 import lbm
-    c, patch, rho_f, u_f, solid_f = _case_3d()
+    c, patch, rho_f, u_f, solid_f = _case_3d(lattice)
     P, _ = to_oracle(c)
     T = oracle.TwoLevel3(P, *patch)
     T.set_fine_solid(solid_f)
@@ -194,9 +195,10 @@ def test_two_level_3d_parity(prec, tol):
     s.close()
 
 
-def test_two_level_3d_uniform_stream_exact():
+@pytest.mark.parametrize("lattice", [oracle.D3Q19, oracle.D3Q27])
+def test_two_level_3d_uniform_stream_exact(lattice):
     from paper_1710_02065_gb300 import lbm
-    s = lbm.Solver(oracle.D3Q19, (20, 18, 16), 0.6, 0)
+    s = lbm.Solver(lattice, (20, 18, 16), 0.6, 0)
     lbm.lbm_add_refinement_patch(s.h, (5, 4, 4), (8, 8, 6))
     U = (0.04, -0.02, 0.01)
     ext, _ = lbm.lbm_level_info(s.h, 1)
