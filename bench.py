@@ -593,13 +593,14 @@ def run_cylinder_three_level(lbm, torch, args):
 
 
 def run_jet_two_level(lbm, torch, args):
-    """2:1 two-level D3Q19 round jet: the 384x256x256 jet lattice (FP32,
+    """2:1 two-level round jet (D3Q19, or D3Q27 with --lattice): the 384x256x256 jet lattice (FP32,
     Re_D 1e4, sponges, inlet noise) with a fine patch over the near-nozzle
     region, coarse [2, 66] x [96, 160] x [96, 160] (129^3 fine nodes, the
     inlet disc of diameter 24 in the middle of its cross-section).  Cell
     updates per coarse step: coarse cells + 2 x fine cells; time by CUDA
     events over args.steps coarse steps after args.warmup."""
     spec = jet_spec()
+    spec["lattice"] = {"d3q19": lbm.LBM_D3Q19, "d3q27": lbm.LBM_D3Q27}[args.lattice]
     stream = torch.cuda.Stream()
     s = configure_gpu(lbm, spec, lbm.PRECISIONS[args.precision], stream.cuda_stream)
     n = s.ncell
@@ -626,7 +627,7 @@ def run_jet_two_level(lbm, torch, args):
     lbm.lbm_moments_level(s.h, 1, rf, None, None)
     s.close()
     cells = n + 2 * nf
-    return {"workload": f"D3Q19 round jet 384x256x256 + 2:1 patch {ext[0]}x{ext[1]}x{ext[2]} over the nozzle, "
+    return {"workload": f"{args.lattice.upper()} round jet 384x256x256 + 2:1 patch {ext[0]}x{ext[1]}x{ext[2]} over the nozzle, "
                         f"{args.precision}", "metric": "cell updates per second (coarse + 2 x fine per coarse step)",
             "mlups": cells * args.steps / (ms / 1e3) / 1e6, "ms_per_coarse_step": ms / args.steps,
             "coarse_steps": args.steps, "launches_per_coarse_step": launches / args.steps,
@@ -702,6 +703,8 @@ def main():
     ap.add_argument("--steps-scale", type=float, default=1.0, help="serving: scale of per-request steps")
     ap.add_argument("--budget-gb", type=float, default=8.0, help="serving: HBM budget for populations")
     ap.add_argument("--round-steps", type=int, default=100, help="serving: steps per batched round")
+    ap.add_argument("--lattice", default="d3q19", choices=["d3q19", "d3q27"],
+                    help="lattice of the two-level jet workload (the jet benchmark line is D3Q19)")
     ap.add_argument("--grid", default="384x256x256",
                     help="jet extents NXxNYxNZ; inlet diameter and sponges scale with NX/384")
     args = ap.parse_args()
