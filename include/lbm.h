@@ -61,7 +61,7 @@ typedef struct lbm_ctx *lbm_handle;
 /* Lattices (Sec. II.A: D2Q9 in 2D, D3Q19 in 3D).  LBM_D3Q27, the tensor
  * product of D1Q3, carries the complete third-order Hermite set (the six
  * H_aab and H_xyz) that D3Q19 can only keep as pairs; general and two-cell
- * kernels, refinement patches (not in the solve server). */
+ * kernels, refinement patches and the solve server. */
 #define LBM_D2Q9 0
 #define LBM_D3Q19 1
 #define LBM_D3Q27 2

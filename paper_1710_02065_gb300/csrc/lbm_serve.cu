@@ -43,8 +43,8 @@ struct Request {
     void *f[2] = {nullptr, nullptr};
 };
 
-// groups: lattice (2) x precision (4) x cells per lane (1, 2)
-constexpr int NGROUPS = 16;
+// groups: lattice (3) x precision (4) x cells per lane (1, 2)
+constexpr int NGROUPS = 24;
 // Cells per lane: two except for FP32 (in the batched kernel a warp item is
 // 32 x V cells of a row, and larger items amortise the per-item work; one
 // cell per lane for every D2Q9 request measured slower on the serving stream:
@@ -85,6 +85,10 @@ cudaError_t launch_group(int g, const BatchDomain *doms, const BatchTile *tiles,
     case 5: return launch_v<D3Q19, float>(v, doms, tiles, ntiles, grid, st);
     case 6: return launch_v<D3Q19, __half>(v, doms, tiles, ntiles, grid, st);
     case 7: return launch_v<D3Q19, __nv_bfloat16>(v, doms, tiles, ntiles, grid, st);
+    case 8: return launch_v<D3Q27, double>(v, doms, tiles, ntiles, grid, st);
+    case 9: return launch_v<D3Q27, float>(v, doms, tiles, ntiles, grid, st);
+    case 10: return launch_v<D3Q27, __half>(v, doms, tiles, ntiles, grid, st);
+    case 11: return launch_v<D3Q27, __nv_bfloat16>(v, doms, tiles, ntiles, grid, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -106,16 +110,15 @@ cudaError_t moments(const Request &r, int cur, double *rho, double *u, cudaStrea
     return cudaGetLastError();
 }
 
+#define TYPED_L(fn, L, prec, ...)                                                                   \
+    ((prec) == LBM_FP64 ? fn<L, double>(__VA_ARGS__)                                                \
+                        : (prec) == LBM_FP32 ? fn<L, float>(__VA_ARGS__)                            \
+                                             : (prec) == LBM_FP16_SHIFTED ? fn<L, __half>(__VA_ARGS__) \
+                                                                          : fn<L, __nv_bfloat16>(__VA_ARGS__))
 #define TYPED(fn, lat, prec, ...)                                                                   \
-    ((lat) == LBM_D2Q9                                                                              \
-         ? ((prec) == LBM_FP64 ? fn<D2Q9, double>(__VA_ARGS__)                                      \
-                               : (prec) == LBM_FP32 ? fn<D2Q9, float>(__VA_ARGS__)                  \
-                                                    : (prec) == LBM_FP16_SHIFTED ? fn<D2Q9, __half>(__VA_ARGS__) \
-                                                                                 : fn<D2Q9, __nv_bfloat16>(__VA_ARGS__)) \
-         : ((prec) == LBM_FP64 ? fn<D3Q19, double>(__VA_ARGS__)                                     \
-                               : (prec) == LBM_FP32 ? fn<D3Q19, float>(__VA_ARGS__)                 \
-                                                    : (prec) == LBM_FP16_SHIFTED ? fn<D3Q19, __half>(__VA_ARGS__) \
-                                                                                 : fn<D3Q19, __nv_bfloat16>(__VA_ARGS__)))
+    ((lat) == LBM_D2Q9 ? TYPED_L(fn, D2Q9, prec, __VA_ARGS__)                                       \
+                       : (lat) == LBM_D3Q19 ? TYPED_L(fn, D3Q19, prec, __VA_ARGS__)                 \
+                                            : TYPED_L(fn, D3Q27, prec, __VA_ARGS__))
 
 }  // namespace
 
@@ -224,7 +227,8 @@ extern "C" int lbm_server_submit(lbm_server_handle s, const lbm_request *req, in
 {
     if (!s) return sfail(nullptr, LBM_EINVAL, "null server");
     if (!req || !id) return sfail(s, LBM_EINVAL, "req and id are required");
-    if (req->lattice != LBM_D2Q9 && req->lattice != LBM_D3Q19) return sfail(s, LBM_EINVAL, "unknown lattice");
+    if (req->lattice != LBM_D2Q9 && req->lattice != LBM_D3Q19 && req->lattice != LBM_D3Q27)
+        return sfail(s, LBM_EINVAL, "unknown lattice");
     if (req->precision < LBM_FP64 || req->precision > LBM_BF16_SHIFTED) return sfail(s, LBM_EINVAL, "unknown precision");
     if (!(req->tau > 0.5) || !std::isfinite(req->tau)) return sfail(s, LBM_EINVAL, "tau must be > 1/2");
     if (req->steps < 0) return sfail(s, LBM_EINVAL, "steps must be >= 0");
@@ -236,7 +240,7 @@ extern "C" int lbm_server_submit(lbm_server_handle s, const lbm_request *req, in
     Request *r = new Request();
     r->lattice = req->lattice;
     r->prec = req->precision;
-    r->q = req->lattice == LBM_D2Q9 ? 9 : 19;
+    r->q = req->lattice == LBM_D2Q9 ? 9 : (req->lattice == LBM_D3Q19 ? 19 : 27);
     for (int a = 0; a < 3; ++a) r->n[a] = req->extents[a];
     r->ncell = (int64_t)r->n[0] * r->n[1] * r->n[2];
     r->tau = req->tau;

@@ -59,7 +59,7 @@ def test_result_is_the_same_alone_and_in_a_mix(serving):
     a = _req(0, 64, 0.61, 150, 1)
     alone = _run(serving, [a])[0]
     mix = [_req(1, 24, 0.7, 90, 2), a, _req(0, 40, 0.55, 33, 0), _req(1, 16, 0.9, 200, 1),
-           _req(0, 128, 0.8, 10, 2)]
+           _req(0, 128, 0.8, 10, 2), _req(2, 20, 0.7, 50, 1), _req(2, 14, 0.6, 30, 3)]
     batched = _run(serving, mix)
     for k in range(len(mix)):
         assert batched[k][2] == 0
@@ -68,7 +68,8 @@ def test_result_is_the_same_alone_and_in_a_mix(serving):
 
 
 @pytest.mark.parametrize("lattice,N,prec,tol,floor", [(0, 32, 0, 1e-12, 1e-13), (0, 48, 1, 1e-5, 1e-8),
-                                                      (1, 12, 0, 1e-12, 1e-13), (1, 16, 1, 1e-5, 1e-8)])
+                                                      (1, 12, 0, 1e-12, 1e-13), (1, 16, 1, 1e-5, 1e-8),
+                                                      (2, 12, 0, 1e-12, 1e-13), (2, 16, 1, 1e-5, 1e-8)])
 def test_served_results_match_oracle(serving, lattice, N, prec, tol, floor):
     r = _req(lattice, N, 0.66, 40, prec)
     rho_g, u_g, rc = _run(serving, [r])[0]
