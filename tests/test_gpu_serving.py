@@ -141,3 +141,40 @@ def test_largest_2d_request_matches_oracle(serving):
     assert np.linalg.norm(rho_g - rho) / np.linalg.norm(rho) <= 1e-5
     du = u_g - u
     assert np.linalg.norm(du) / np.linalg.norm(u) <= 1e-5 or np.abs(du).max() <= 1e-8
+
+
+def test_unstable_request_fails_alone(serving):
+    """Failure isolation: a request that blows up (random supersonic start at
+    tau just above 1/2) is retired as failed with LBM_EUNSTABLE and its memory
+    and slot returned, while the requests batched with it finish with the
+    same result as when run alone."""
+    from paper_1710_02065_gb300 import lbm
+    good = _req(1, 16, 0.7, 60, 1)
+    alone = _run(serving, [good])[0]
+    bad = _req(1, 16, 0.5001, 400, 1)
+    srv = serving.Server(1 << 30, 8)
+    n = 16 ** 3
+    rng = np.random.default_rng(13)
+    u_bad = rng.uniform(-0.45, 0.45, (n, 3))  # uncorrelated, |u| up to 0.78 > c_s = 0.577
+    rho_bad = rng.uniform(0.5, 1.5, n)
+    ids = [srv.submit(bad, rho_bad, u_bad)]
+    rho0, u0 = inputs.request_initial_state(good)
+    ids.append(srv.submit(good, rho0, u0))
+    states = {}
+    for _ in range(200):
+        srv.run(20)
+        for rid in ids:
+            st, _ = srv.poll(rid)
+            if st in (lbm.LBM_REQ_DONE, lbm.LBM_REQ_FAILED):
+                states[rid] = st
+        if len(states) == 2:
+            break
+    assert states[ids[0]] == lbm.LBM_REQ_FAILED
+    assert states[ids[1]] == lbm.LBM_REQ_DONE
+    _, _, rc_bad = srv.result(ids[0], n)
+    rho_g, u_g, rc_good = srv.result(ids[1], n)
+    assert rc_bad == lbm.LBM_EUNSTABLE and rc_good == 0
+    assert np.array_equal(rho_g, alone[0]) and np.array_equal(u_g, alone[1])
+    st = srv.stats()
+    assert st["running"] == 0 and st["bytes_in_use"] == 0  # slot and memory returned
+    srv.close()
