@@ -415,7 +415,10 @@ int lbm_force_async(lbm_handle h, int level, double *F_dev);
 int lbm_probe_async(lbm_handle h, int n, const int64_t *cells_dev, double *p_dev);
 
 /* lbm_sync -- wait for all work of h; returns any pending execution error,
- * including a bulk copy of the row-staged kernel that timed out. */
+ * including a bulk copy of the row-staged kernel that timed out and, in the
+ * checked build of the library (built with LBM_BOUNDS_CHECK, every index of
+ * the update kernels tested before use), an index outside the lattice
+ * (LBM_ECUDA; the condition is cleared). */
 int lbm_sync(lbm_handle h);
 
 /*

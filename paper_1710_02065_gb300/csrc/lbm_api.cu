@@ -905,6 +905,7 @@ static int build_params(lbm_ctx *h, StepParams &p)
     p.omega = 1.0 - 1.0 / h->tau;
     p.solid = h->solid_d;
     p.any_solid = h->has_solid ? 1 : 0;
+    p.err = h->err_d;
     p.bgk = h->collision == LBM_COLLISION_BGK ? 1 : 0;
     p.order4 = h->order4;
     p.jet_x_layer = INT_MAX;
@@ -986,6 +987,7 @@ static void fine_params(lbm_ctx *h, int k, StepParams &p)
     p.jet_x_layer = INT_MAX;
     p.solid = F->mask_d;
     p.any_solid = F->has_solid ? 1 : 0;
+    p.err = h->err_d;
     set_bulk_box(p);
 }
 
@@ -1574,6 +1576,9 @@ extern "C" int lbm_sync(lbm_handle h)
     CUDA_TRY(h, cudaMemcpy(&err, h->err_d, sizeof err, cudaMemcpyDeviceToHost));
     if (err) {
         CUDA_TRY(h, cudaMemset(h->err_d, 0, sizeof err));
+        if (err & kErrBounds)
+            return fail(h, LBM_ECUDA, "checked build: an update computed an index outside its lattice (error word %u)",
+                        err);
         return fail(h, LBM_ECUDA, "row-staged kernel: a bulk copy did not arrive within 2 s (error word %u)", err);
     }
     return LBM_OK;

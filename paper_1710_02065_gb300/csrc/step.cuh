@@ -73,6 +73,9 @@ struct StepParams {
     double jet_ref[6];
     // D2Q9: include the optional fourth-order H_xxyy term (rrBGK only)
     int order4;
+    // device error word of the handle (or null): bit 0 a bounded wait of the
+    // row-staged kernel gave up, bit 1 an index check of a checked build
+    unsigned *err;
     // per-direction base addresses of the lattice read (in) and written (out):
     // in[i] = f_in + i * ncell elements, i < Q <= kMaxQ; filled by the launchers
     const char *in[kMaxQ];
@@ -287,6 +290,25 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
 // (skip, plus halfway bounce-back at cells next to a solid).
 enum { kMaskNone = 0, kMaskSkip = 1, kMaskLinks = 2 };
 
+// Checked builds (-DLBM_BOUNDS_CHECK, `build(checked=True)`): every index an
+// update reads or writes is tested against the lattice before any access; a
+// cell whose indices fall outside is not updated and bit 1 of the handle's
+// error word is set (reported by lbm_sync).  The substitute for a memory
+// sanitizer on a pool where compute-sanitizer is closed; release builds
+// compile the checks away.
+constexpr unsigned kErrBounds = 2u;
+__device__ __forceinline__ bool index_fault(const StepParams &p, bool bad)
+{
+#ifdef LBM_BOUNDS_CHECK
+    if (bad && p.err) atomicOr(p.err, kErrBounds);
+    return bad;
+#else
+    (void)p;
+    (void)bad;
+    return false;
+#endif
+}
+
 template <class L, class S, class C, bool BGK = false, int MASK = kMaskLinks>
 __device__ __forceinline__ void update_cell(const StepParams &p, const char *const *in, char *const *out,
                                             int x, int y, int z)
@@ -295,6 +317,7 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     const unsigned nx = p.n[0], ny = p.n[1], nz = p.n[2];
     const unsigned nxy = nx * ny;
     const unsigned cell = x + nx * y + nxy * z;
+    if (index_fault(p, x < 0 || y < 0 || z < 0 || cell >= (unsigned)p.ncell)) return;
     // kMaskNone: compiled without any cell-type test (the lattice has no mask)
     const uint8_t *__restrict__ solid = MASK != kMaskNone ? p.solid : nullptr;
     if (solid && (solid[cell] & MASK_TYPE)) return;  // solid (1) and fixed (2) cells keep their populations
@@ -323,6 +346,18 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     const unsigned ym = sy == 0 ? ny - 1 : sy - 1, yp = sy == ny - 1 ? 0 : sy + 1;
     const unsigned zm = sz == 0 ? nz - 1 : sz - 1, zp = sz == nz - 1 ? 0 : sz + 1;
     const unsigned scell = sx + nx * sy + nxy * sz;
+#ifdef LBM_BOUNDS_CHECK
+    {
+        bool bad = scell >= (unsigned)p.ncell;
+        for (int i = 0; i < L::Q; ++i) {
+            const unsigned X = L::cx(i) > 0 ? xm : (L::cx(i) < 0 ? xp : sx);
+            const unsigned Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
+            const unsigned Z = L::D == 2 ? 0u : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
+            bad = bad || X >= nx || Y >= ny || Z >= nz || X + nx * Y + nxy * Z >= (unsigned)p.ncell;
+        }
+        if (index_fault(p, bad)) return;
+    }
+#endif
 
     // ---- streaming (pull) with halfway bounce-back; only a node with a solid
     // neighbour tests its links

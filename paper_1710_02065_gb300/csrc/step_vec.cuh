@@ -202,6 +202,21 @@ __device__ __forceinline__ void update_vec(const StepParams &p, const char *cons
     const int xl = x0 == 0 ? nx - 1 : x0 - 1;        // cell left of the vector (wrapped)
     const int xr = x0 + V == nx ? 0 : x0 + V;        // cell right of the vector (wrapped)
 
+#ifdef LBM_BOUNDS_CHECK
+    {
+        // every row this thread reads (x0 - 1 .. x0 + V, wrapped) and writes
+        bool bad = x0 < 0 || x0 + V > nx || xl >= nx || xr >= nx || sy >= ny || sz >= nz ||
+                   (unsigned)nx * y + nxy * z + x0 + V > (unsigned)p.ncell;
+        for (int i = 0; i < L::Q; ++i) {
+            const int Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
+            const int Z = L::D == 2 ? 0 : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
+            bad = bad || Y < 0 || Y >= ny || Z < 0 || Z >= nz ||
+                  (unsigned)nx * Y + nxy * Z + (unsigned)nx > (unsigned)p.ncell;
+        }
+        if (index_fault(p, bad)) return;
+    }
+#endif
+
     // ---- gather
     C g[L::Q][V];
 #pragma unroll

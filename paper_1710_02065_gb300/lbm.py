@@ -16,7 +16,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
+# LBM_CHECKED=1 loads the checked build (every update index tested before use;
+# built by build.build(checked=True)) instead of the release library
+LIB_PATH = os.path.join(_HERE, "_build", "liblbm_checked.so" if os.environ.get("LBM_CHECKED") == "1" else "liblbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_EIO = 0, -1, -2, -3, -4, -5
 LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 0, 1, 2
