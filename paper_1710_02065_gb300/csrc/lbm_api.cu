@@ -88,6 +88,7 @@ struct lbm_ctx {
     int64_t graph_version = -1;
     uint64_t graph_sig = 0;  // lattice parities the graph was captured at
     int64_t graph_launches = 0;
+    int graph_pairs = 0;  // step pairs the graph holds
     std::string err;
 };
 
@@ -1156,7 +1157,7 @@ static uint64_t parity_signature(const lbm_ctx *h)
 // Capture two steps into a graph for the current configuration and parity.
 // The host-side counters advanced by the capture are restored: the captured
 // work runs only when the graph is launched.
-static int capture_pair(lbm_ctx *h, std::vector<StepParams> &params)
+static int capture_pairs(lbm_ctx *h, std::vector<StepParams> &params, int npairs)
 {
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
@@ -1172,9 +1173,9 @@ static int capture_pair(lbm_ctx *h, std::vector<StepParams> &params)
     const int64_t step = h->step, launches = h->launches;
     cudaGraph_t g = nullptr;
     CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_steps(h, params, 2);
+    int rc = enqueue_steps(h, params, 2 * (int64_t)npairs);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
-    const int64_t per_pair = h->launches - launches;
+    const int64_t per_graph = h->launches - launches;
     h->cur = cur;
     h->step = step;
     h->launches = launches;
@@ -1192,7 +1193,8 @@ static int capture_pair(lbm_ctx *h, std::vector<StepParams> &params)
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "instantiating steps: %s", cudaGetErrorString(e));
     h->graph_version = h->cfg_version;
     h->graph_sig = sig;
-    h->graph_launches = per_pair;
+    h->graph_launches = per_graph;
+    h->graph_pairs = npairs;
     return LBM_OK;
 }
 
@@ -1208,19 +1210,26 @@ extern "C" int lbm_step(lbm_handle h, int64_t n)
     // Without inlet noise every step of a pair has the same parameters, so
     // pairs of steps are replayed from a captured graph (needs a stream other
     // than the legacy default one).  Every refined level returns to the same
-    // lattice parity after two coarse steps.
+    // lattice parity after two coarse steps.  The graph holds up to
+    // kGraphPairs pairs (as many as one call asks for), so that a call of n
+    // steps costs few graph launches; it is recaptured when the pair count a
+    // call asks for changes.  Steps left over run as direct launches.
+    constexpr int64_t kGraphPairs = 16;
     if (h->stream && h->noise_amp == 0.0 && n >= 2) {
-        if (!h->graph || h->graph_version != h->cfg_version || h->graph_sig != parity_signature(h)) {
-            rc = capture_pair(h, params);
+        const int pairs = (int)std::min<int64_t>(n / 2, kGraphPairs);
+        if (!h->graph || h->graph_version != h->cfg_version || h->graph_sig != parity_signature(h) ||
+            h->graph_pairs != pairs) {
+            rc = capture_pairs(h, params, pairs);
             if (rc != LBM_OK) return rc;
         }
-        for (int64_t k = 0; k < n / 2; ++k) {
+        const int64_t reps = n / (2 * (int64_t)pairs);
+        for (int64_t k = 0; k < reps; ++k) {
             cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
             if (e != cudaSuccess) return fail(h, LBM_ECUDA, "graph launch: %s", cudaGetErrorString(e));
         }
-        h->step += 2 * (n / 2);
-        h->launches += h->graph_launches * (n / 2);
-        n -= 2 * (n / 2);
+        h->step += 2 * pairs * reps;
+        h->launches += h->graph_launches * reps;
+        n -= 2 * pairs * reps;
     }
     return enqueue_steps(h, params, n);
 }

@@ -533,6 +533,13 @@ def test_graph_replay_matches_direct_launches():
     a.step(6)
     b.step(6)
     assert np.array_equal(a.populations(), b.populations())
+    # a long call: one graph of 16 step pairs replayed, the rest direct
+    a.step(41)
+    b.step(41)
+    b.step(41)
+    a.step(41)
+    assert np.array_equal(a.populations(), b.populations())
+    assert a.info()["step"] == b.info()["step"] == 11 + 6 + 82
 
     cj = round_jet(32, 24, 24, diameter=6.0, sponge=6, Re=1000.0, noise=0.0)
     a, b = pair(cj)
