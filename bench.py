@@ -231,6 +231,23 @@ def recorded_fp64_inst(kernel_key: str):
 
 # GB300 FP64: 1.25 TFLOP/s nominal = 625 G FMA instructions/s (no measured FP64 peak is available)
 FP64_INST_PEAK_G = 625.0
+# Warp-instruction issue limit: 152 SMs x 4 schedulers x 1 warp instruction per cycle at the 2070 MHz
+# maximum SM clock
+ISSUE_PEAK_G = 152 * 4 * 2.070
+
+
+def recorded_issue(kernel_key: str):
+    """Warp instructions per cell from the committed ncu counts, if taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_issue.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel_key and parts[1] == src:
+            return float(parts[2])
+    return None
 
 
 def dist_setup():
@@ -782,6 +799,15 @@ def main():
             extra[name] = {"launch": r["launch"], "mlups": r["ncell"] / (k_ms / 1e3) / 1e6,
                            "gbs": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9,
                            "frac_of_measured_hbm": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9 / peak}
+            if name in ("fp16", "bf16") and r["launch"]["kernel"] == "vec2":
+                ins = recorded_issue(f"k_stream_collide_vec_d3q19_{name}_jet")
+                if ins is not None:
+                    rate = extra[name]["mlups"] / 1e3  # G cells/s
+                    extra[name]["roofline"] = {
+                        "bound": "alu", "achieved": rate * ins, "peak": ISSUE_PEAK_G, "unit": "G warp instr/s",
+                        "frac": rate * ins / ISSUE_PEAK_G, "warp_inst_per_cell": ins,
+                        "peak_source": "152 SMs x 4 schedulers x 2.07 GHz (one warp instruction per scheduler "
+                                       "per cycle); counts from profiles/ncu_issue.txt"}
             if name == "fp64":
                 kk = "k_stream_collide_vec" if r["launch"]["kernel"].startswith("vec") else "k_stream_collide"
                 ins = recorded_fp64_inst(f"{kk}_d3q19_fp64_jet")
