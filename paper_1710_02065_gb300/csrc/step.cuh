@@ -366,16 +366,30 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     // neighbour tests its links
     const bool near = MASK == kMaskLinks && solid && (solid[scell] & MASK_NEAR_SOLID);
     C g[L::Q];
+    // two gather loops, the link tests only in the one for cells next to a
+    // solid: with the test inside a single loop the masked D2Q9 FP16 / BF16
+    // update ran 30% slower on GB300 (1600 x 800 cylinder: 64 -> 92 G cell
+    // updates/s with the split; FP32 83 -> 84)
+    if (near) {
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        const unsigned X = L::cx(i) > 0 ? xm : (L::cx(i) < 0 ? xp : sx);
-        const unsigned Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
-        const unsigned Z = L::D == 2 ? 0u : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
-        const unsigned src = X + nx * Y + nxy * Z;
-        if (near && i != 0 && (solid[src] & MASK_TYPE) == MASK_SOLID)
-            g[i] = Store<S>::ld((const S *)in[opp<L>(i)] + scell);
-        else
-            g[i] = Store<S>::ld((const S *)in[i] + src);
+        for (int i = 0; i < L::Q; ++i) {
+            const unsigned X = L::cx(i) > 0 ? xm : (L::cx(i) < 0 ? xp : sx);
+            const unsigned Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
+            const unsigned Z = L::D == 2 ? 0u : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
+            const unsigned src = X + nx * Y + nxy * Z;
+            if (i != 0 && (solid[src] & MASK_TYPE) == MASK_SOLID)
+                g[i] = Store<S>::ld((const S *)in[opp<L>(i)] + scell);
+            else
+                g[i] = Store<S>::ld((const S *)in[i] + src);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const unsigned X = L::cx(i) > 0 ? xm : (L::cx(i) < 0 ? xp : sx);
+            const unsigned Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
+            const unsigned Z = L::D == 2 ? 0u : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
+            g[i] = Store<S>::ld((const S *)in[i] + (X + nx * Y + nxy * Z));
+        }
     }
 
     const Mom<C> m = moments_pairs<L, C>(g);
