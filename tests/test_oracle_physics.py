@@ -301,6 +301,54 @@ def test_free_slip_and_pressure_faces_keep_a_uniform_stream(which):
     assert np.abs(outlet - 1.002).max() < 1e-14
 
 
+@pytest.mark.parametrize("which", [D2Q9, D3Q19])
+def test_pressure_outlet_carries_the_shear_of_a_channel_flow(which):
+    """Pressure-driven channel (Sec. IV outlet, reading R17): a parabolic
+    velocity inlet, a constant-pressure outlet at rho = 1 and halfway
+    bounce-back walls at y = 1/2 and H + 1/2.  The outlet node takes u and
+    Pi^neq of its inward neighbour with the imposed density, so after any
+    number of steps its stored moments equal the neighbour's (density aside)
+    to round-off, and in the developed flow they are the Poiseuille ones: the
+    profile is the parabola and the stored shear stress is
+    Pi^neq_xy = rho c_s^2 (1 - tau) du/dy (the relaxed viscous stress
+    (1 - 1/tau) (-rho c_s^2 tau du/dy)).  Dropping Pi^neq at the outlet, or
+    taking it from the outlet node's own streamed populations, breaks both."""
+    from oracle import PRESSURE
+    H, nx, tau, U = 16, 48, 0.8, 0.04
+    ny, nz = H + 2, (1 if which == D2Q9 else 3)
+    P = oracle.Problem(which, (nx, ny) if which == D2Q9 else (nx, ny, nz), tau)
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    solid[:, 0, :] = solid[:, -1, :] = 1
+    P.solid = solid.reshape(-1)
+    fluid = slice(1, ny - 1)
+    y = np.arange(ny) - 0.5  # distance from the lower wall
+    prof_y = np.zeros(ny)
+    prof_y[fluid] = 4 * U * y[fluid] * (H - y[fluid]) / H ** 2
+    prof = np.zeros((ny * nz, 3))
+    prof[:, 0] = np.tile(prof_y, nz)
+    P.set_boundary(0, VELOCITY, profile=prof)
+    P.set_boundary(1, PRESSURE, rho=1.0)
+    u = np.zeros((P.ncell, 3))
+    u[:, 0] = np.broadcast_to(prof_y[None, :, None], (nz, ny, nx)).reshape(-1)
+    f = P.run(P.equilibrium(np.ones(P.ncell), u), 2000)
+    rho, uu, pn = P.moments(f)
+    r = rho.reshape(nz, ny, nx)[:, fluid]
+    ux = uu[:, 0].reshape(nz, ny, nx)[:, fluid]
+    uy = uu[:, 1].reshape(nz, ny, nx)[:, fluid]
+    pxy = pn[:, 1].reshape(nz, ny, nx)[:, fluid]
+    # the rule itself, through a whole update: imposed density, neighbour's u and Pi^neq
+    assert np.abs(r[:, :, -1] - 1.0).max() < 1e-14
+    assert np.abs(ux[:, :, -1] - ux[:, :, -2]).max() < 1e-15
+    assert np.abs(uy[:, :, -1] - uy[:, :, -2]).max() < 1e-15
+    assert np.abs(pxy[:, :, -1] - pxy[:, :, -2]).max() < 1e-12 * np.abs(pxy[:, :, -2]).max()
+    # the developed channel flow at the outlet
+    shape = ux[0, :, -1] / ux[0, :, -1].sum() - prof_y[fluid] / prof_y[fluid].sum()
+    assert np.abs(shape).max() < 2e-3 * (prof_y[fluid] / prof_y[fluid].sum()).max()
+    dudy = 4 * U * (H - 2 * y[fluid]) / H ** 2
+    stress = r[0, :, -1] * CS2 * (1 - tau) * dudy
+    assert np.abs(pxy[0, :, -1] - stress).max() < 0.03 * np.abs(stress).max()
+
+
 def test_sponge_absorbs_a_plane_pulse():
     """Plane acoustic pulse (amplitude 1e-3 split into two waves of 5e-4)
     leaving a D2Q9 channel through zero-gradient outflow faces, with and
