@@ -69,6 +69,7 @@
  *       layer the reference velocity is the self-similar round-jet mean
  *       axial profile (sponge_reference below); elsewhere the uniform u_ref.
  */
+#include <pthread.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -664,6 +665,57 @@ int orc_run(const orc_problem *P, double *f, double *work, int64_t step0, int64_
     double *a = f, *b = work;
     for (int64_t t = 0; t < nsteps; ++t) {
         orc_step(P, a, b, step0 + t);
+        double *tmp = a; a = b; b = tmp;
+    }
+    if (a != f) memcpy(f, a, sizeof(double) * (size_t)N * (size_t)L->q);
+    return 0;
+}
+
+/* The same nsteps steps with the cells of each step split over nthreads host
+ * threads (contiguous ranges, joined before the next step).  Every cell is
+ * computed by orc_update_cell exactly as in orc_step, so the result is bitwise
+ * that of orc_run; the threads only shorten long reference runs. */
+typedef struct {
+    const orc_problem *P;
+    const double *fin;
+    double *fout;
+    int64_t c0, c1, step;
+} orc_slice;
+
+static void *orc_slice_run(void *arg)
+{
+    const orc_slice *s = (const orc_slice *)arg;
+    const lattice_t *L = lattice(s->P->lattice);
+    const int64_t N = ncell(s->P);
+    double out[QMAX];
+    for (int64_t cell = s->c0; cell < s->c1; ++cell) {
+        orc_update_cell(s->P, s->fin, cell, s->step, out);
+        for (int i = 0; i < L->q; ++i) s->fout[(int64_t)i * N + cell] = out[i];
+    }
+    return NULL;
+}
+
+int orc_run_threads(const orc_problem *P, double *f, double *work, int64_t step0, int64_t nsteps, int nthreads)
+{
+    enum { MAXT = 256 };
+    if (nthreads <= 1) return orc_run(P, f, work, step0, nsteps);
+    if (nthreads > MAXT) nthreads = MAXT;
+    const lattice_t *L = lattice(P->lattice);
+    const int64_t N = ncell(P);
+    double *a = f, *b = work;
+    pthread_t th[MAXT];
+    orc_slice sl[MAXT];
+    for (int64_t t = 0; t < nsteps; ++t) {
+        for (int k = 0; k < nthreads; ++k) {
+            sl[k].P = P;
+            sl[k].fin = a;
+            sl[k].fout = b;
+            sl[k].c0 = N * k / nthreads;
+            sl[k].c1 = N * (k + 1) / nthreads;
+            sl[k].step = step0 + t;
+            if (pthread_create(&th[k], NULL, orc_slice_run, &sl[k]) != 0) return -1;
+        }
+        for (int k = 0; k < nthreads; ++k) pthread_join(th[k], NULL);
         double *tmp = a; a = b; b = tmp;
     }
     if (a != f) memcpy(f, a, sizeof(double) * (size_t)N * (size_t)L->q);

@@ -375,3 +375,22 @@ def test_sponge_absorbs_a_plane_pulse():
     bare, sponge = reflected(0), reflected(30)
     assert bare > -20 and bare < -10, bare
     assert sponge < -50, sponge
+
+
+def test_threaded_run_is_bitwise_the_plain_run():
+    """Problem.run(threads=k) splits each step's cells over host threads; every
+    cell is the same orc_update_cell call, so the field is bitwise the one of
+    the single-threaded run (inflow with noise, outflow, sponges, a solid)."""
+    P = oracle.Problem(D3Q19, (20, 14, 12), 0.56)
+    P.set_boundary(0, VELOCITY, (0.04, 0.0, 0.0))
+    P.set_boundary(1, OUTFLOW)
+    P.set_sponge(1, 5, 0.6)
+    P.noise_seed, P.noise_amp = 4, 0.02
+    solid = np.zeros((12, 14, 20), np.uint8)
+    solid[5:7, 6:8, 8:10] = 1
+    P.solid = solid.reshape(-1)
+    _, _, _, w, _ = oracle.lattice(D3Q19)
+    f0 = inputs.random_populations(w, P.ncell, 3, 0.05)
+    a = P.run(f0, 7, step0=2)
+    for k in (2, 5, 16):
+        assert np.array_equal(P.run(f0, 7, step0=2, threads=k), a)
