@@ -108,7 +108,8 @@ int lbm_lattice_table(int lattice, int *q, int *d, int *xi, double *w);
  * lbm_create -- allocate a lattice of extents[0] x extents[1] x extents[2]
  * cells on the current CUDA device, fully periodic, every cell fluid and at
  * rest (rho = 1, u = 0).
- *   lattice     : LBM_D2Q9 (extents[2] must be 1) or LBM_D3Q19
+ *   lattice     : LBM_D2Q9 (extents[2] must be 1), LBM_D3Q19 or LBM_D3Q27
+ *                 (the tensor-product lattice with the complete third order)
  *   tau_or_nu   : relaxation time tau (> 1/2) or, if value_is_nu != 0, the
  *                 kinematic viscosity nu > 0, tau = nu / c_s^2 + 1/2
  *                 (Sec. II.A, below Eq. truncatedEq)
@@ -243,13 +244,18 @@ int lbm_step(lbm_handle h, int64_t n);
  *   u      : 3*ncell doubles, (sum_i f_i xi_i) / rho        (Eq. moments)
  *   pi_neq : 6*ncell doubles, Pi - rho c_s^2 I - rho u u, Pi = sum_i f_i xi_i xi_i,
  *            per cell (xx, xy, xz, yy, yz, zz); z components are 0 in 2D.
- * Computed in FP64 on the device from the stored populations.
+ * Computed on the device from the stored populations in the compute type of
+ * the storage: FP64 for LBM_FP64, FP32 for LBM_FP32 and the shifted 16-bit
+ * formats (rho = 1 + sum_i (f_i - w_i) keeps the precision of the small
+ * sum), and returned as FP64.
  */
 int lbm_moments(lbm_handle h, double *rho, double *u, double *pi_neq);
 
 /*
  * lbm_reduce -- FP64 totals over fluid cells of level 0: *mass = sum rho,
- * momentum[0..2] = sum rho u (over the cells with finite populations).
+ * momentum[0..2] = sum rho u (over the cells with finite populations); the
+ * per-cell moments are formed in the storage's compute type (as for
+ * lbm_moments) and summed in FP64 in a fixed order.
  * Returns LBM_EUNSTABLE if a fluid cell holds a non-finite population, a
  * non-positive density or a velocity at or above the lattice sound speed
  * c_s = 1/sqrt(3) (the totals are still written).
@@ -384,6 +390,45 @@ int lbm_set_transfer_staging(lbm_handle h, size_t max_bytes);
  */
 int lbm_set_staging(lbm_handle h, int mode, int stages, int block);
 int lbm_get_staging(lbm_handle h, int *active, int *stages, int *block, int *rows_per_tile, int *grid);
+
+/*
+ * lbm_set_streaming -- streaming pattern of the single level (the update of
+ * Eq. optimizedLB is the same with either; Sec. II.A streams post-collision
+ * populations along xi_i, and where they are stored between steps is free):
+ *   LBM_STREAM_PULL (default): two lattices; every step pulls the populations
+ *       streamed into a cell from one lattice and writes the other.
+ *   LBM_STREAM_AA: one lattice updated in place (half the device memory),
+ *       with two step types that alternate.  A gather-push step pulls as the
+ *       pull update does and pushes each collided population o_i into the
+ *       slot P_opp(i)[x + xi_i] the neighbour will read (or back to P_i[x]
+ *       at a solid or outside a non-periodic face); the next, local step
+ *       reads P_opp(i)[x], collides and writes P_i[x], which restores the
+ *       standard layout.  Every cell reads exactly the slots it writes; a
+ *       boundary node is updated by the thread of the inward neighbour whose
+ *       populations it takes.  Results equal the pull update's to round-off.
+ *       Calls that read or write the populations (moments, reduce, probes,
+ *       forces, checkpoints, transfers) first bring an odd-step lattice back
+ *       to the standard layout in place.  Not with refinement patches.
+ * The state is kept.  Switching to AA frees the second lattice; switching
+ * back allocates it (LBM_ENOMEM if that fails; the handle stays AA).
+ * lbm_get_streaming reports the pattern in use.
+ */
+#define LBM_STREAM_PULL 0
+#define LBM_STREAM_AA 1
+int lbm_set_streaming(lbm_handle h, int pattern);
+int lbm_get_streaming(lbm_handle h, int *pattern);
+
+/*
+ * lbm_set_staging_wait -- limit of each wait of the row-staged kernel for a
+ * tile's bulk copies, in nanoseconds of device global time (default 2e9).
+ * 0 makes each wait one non-blocking test: a tile whose copies are still in
+ * flight at that instant counts as late, so the failure path (error word set,
+ * the CTA awaits its remaining copies with the 2 s limit and returns,
+ * lbm_sync reports LBM_ECUDA) can be exercised without any copy actually
+ * failing.  The populations written by such a step are unspecified.  No paper
+ * counterpart: failure detection of the runtime.
+ */
+int lbm_set_staging_wait(lbm_handle h, uint64_t limit_ns);
 
 /*
  * lbm_force -- force on the solid cells of a level (0 coarse / single level, 1
@@ -547,14 +592,15 @@ int lbm_server_stats(lbm_server_handle s, int *queued, int *running, size_t *byt
  * counterpart: this is an integration entry point.)
  *
  * For callers that cannot allocate device memory where they need the totals:
- * code being recorded into a CUDA graph by stream capture (allocation is not
- * capturable), loops that must never enter an allocator, or hosts that keep
- * a fixed device-memory budget and lend the library only their own buffers.
+ * loops that must never enter an allocator (real-time or memory-accounted
+ * code), or hosts that keep a fixed device-memory budget and lend the
+ * library only their own buffers.
  * The per-block partial sums live in a static device array inside the
  * library, sized for at most LBM_NOALLOC_MAX_CELLS cells, which every GPU
  * that loads the library keeps until the process exits.  The call itself
  * allocates nothing and does not use a handle.
- *   lattice, precision : as for lbm_create
+ *   lattice   : LBM_D2Q9, LBM_D3Q19 or LBM_D3Q27
+ *   precision : LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED or LBM_BF16_SHIFTED
  *   f         : device pointer to the field in the library's storage layout:
  *               q * ncell values of the precision's type, direction-major
  *               (f[i * ncell + cell]), each holding f_i - w_i

@@ -22,7 +22,7 @@ LIB = os.path.join(BUILD, "liblbm.so")
 CHECKED_LIB = os.path.join(BUILD, "liblbm_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lbm_api.cu", "step_d2q9.cu", "step_d3q19.cu", "step_d3q27.cu", "stepvec_d2q9.cu", "stepvec_d3q19.cu",
-           "stepvec_d3q27.cu",
+           "stepvec_d3q27.cu", "aa_d2q9.cu", "aa_d3q19.cu", "aa_d3q27.cu",
            "rows_d2q9.cu", "rows_d3q19.cu", "lbm_noalloc.cu", "lbm_serve.cu"]
 
 

@@ -1,0 +1,30 @@
+// aa_d3q27.cu -- instantiations of the in-place AA stream + collide kernels
+// for D3Q27 (one translation unit per lattice so the library builds in parallel).
+#include "step.cuh"
+#include "dispatch.h"
+
+namespace rr {
+
+cudaError_t step_aa_d3q27(int precision, const StepParams &p, void *f, int block, bool loc, cudaStream_t st)
+{
+    switch (precision) {
+    case PREC_FP64: return launch_stream_collide_aa<D3Q27, double, double>(p, f, block, loc, st);
+    case PREC_FP32: return launch_stream_collide_aa<D3Q27, float, float>(p, f, block, loc, st);
+    case PREC_FP16: return launch_stream_collide_aa<D3Q27, __half, float>(p, f, block, loc, st);
+    case PREC_BF16: return launch_stream_collide_aa<D3Q27, __nv_bfloat16, float>(p, f, block, loc, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t aa_unswap_d3q27(int precision, const StepParams &p, void *f, cudaStream_t st)
+{
+    switch (precision) {
+    case PREC_FP64: return launch_aa_unswap<D3Q27, double>(p, f, st);
+    case PREC_FP32: return launch_aa_unswap<D3Q27, float>(p, f, st);
+    case PREC_FP16: return launch_aa_unswap<D3Q27, __half>(p, f, st);
+    case PREC_BF16: return launch_aa_unswap<D3Q27, __nv_bfloat16>(p, f, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rr

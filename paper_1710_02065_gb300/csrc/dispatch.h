@@ -1,6 +1,7 @@
 // dispatch.h -- entry points of the per-lattice kernel translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <cstdint>
 
 namespace rr {
 
@@ -15,6 +16,15 @@ cudaError_t step_d3q19(int precision, const StepParams &p, const void *fin, void
 cudaError_t step_d3q27(int precision, const StepParams &p, const void *fin, void *fout, int block,
                        cudaStream_t st);
 
+// In-place AA streaming on one lattice f: one step (loc: the local step, else
+// gather-push) and the conversion of the push layout to the standard one
+cudaError_t step_aa_d2q9(int precision, const StepParams &p, void *f, int block, bool loc, cudaStream_t st);
+cudaError_t step_aa_d3q19(int precision, const StepParams &p, void *f, int block, bool loc, cudaStream_t st);
+cudaError_t step_aa_d3q27(int precision, const StepParams &p, void *f, int block, bool loc, cudaStream_t st);
+cudaError_t aa_unswap_d2q9(int precision, const StepParams &p, void *f, cudaStream_t st);
+cudaError_t aa_unswap_d3q19(int precision, const StepParams &p, void *f, cudaStream_t st);
+cudaError_t aa_unswap_d3q27(int precision, const StepParams &p, void *f, cudaStream_t st);
+
 }  // namespace rr
 
 namespace rr {
@@ -23,14 +33,16 @@ namespace rr {
 void rr_set_global_error(const char *msg);
 
 // Vectorised kernel (no cell-type mask, nx % vec == 0).  Supported (precision,
-// vec): FP64 2; FP32 2, 4; FP16 2, 4; BF16 2, 4.
+// vec): FP64 2; FP32 2, 4; FP16 2, 4; BF16 2, 4.  sp: 0 the two-lattice pull
+// (fin read, fout written), 1 / 2 the AA gather-push / local step (in place,
+// fin == fout).
 cudaError_t stepvec_d2q9(int precision, int vec, const StepParams &p, const void *fin, void *fout,
-                         int block, cudaStream_t st);
+                         int block, cudaStream_t st, int sp = 0);
 cudaError_t stepvec_d3q19(int precision, int vec, const StepParams &p, const void *fin, void *fout,
-                          int block, cudaStream_t st);
+                          int block, cudaStream_t st, int sp = 0);
 // D3Q27: two cells per thread (four fall back to the general kernel)
 cudaError_t stepvec_d3q27(int precision, int vec, const StepParams &p, const void *fin, void *fout,
-                          int block, cudaStream_t st);
+                          int block, cudaStream_t st, int sp = 0);
 
 // Cells per thread the vectorised kernel supports for a precision (0: none)
 inline bool vec_supported(int precision, int vec)
@@ -67,10 +79,12 @@ struct RowsPlan {
     size_t smem;  // dynamic shared memory per CTA, bytes
 };
 // cudaErrorNotSupported (nothing launched, no CUDA error state): not eligible
+// wait_ns: limit of each wait for a tile's bulk copies (0: one non-blocking
+// test, for failure-path tests)
 cudaError_t rows_d2q9(int precision, const StepParams &p, const void *fin, void *fout, int block, int stages,
-                      unsigned *err, cudaStream_t st);
+                      unsigned *err, uint64_t wait_ns, cudaStream_t st);
 cudaError_t rows_d3q19(int precision, const StepParams &p, const void *fin, void *fout, int block, int stages,
-                       unsigned *err, cudaStream_t st);
+                       unsigned *err, uint64_t wait_ns, cudaStream_t st);
 cudaError_t rows_plan_d2q9(int precision, const StepParams &p, const void *fin, const void *fout, int block,
                            int stages, RowsPlan &pl);
 cudaError_t rows_plan_d3q19(int precision, const StepParams &p, const void *fin, const void *fout, int block,

@@ -65,7 +65,14 @@ struct lbm_ctx {
     int stages = 0;       // its shared-memory stages (0: 2)
     int rows_block = 0;   // its threads per CTA (0: automatic)
     unsigned *err_d = nullptr;  // device error word of the row-staged kernel (bounded waits)
+    uint64_t rows_wait_ns = 2000000000ull;  // limit of each of its waits for a tile's copies
     int collision = LBM_COLLISION_RR;
+    // streaming pattern of level 0: LBM_STREAM_PULL (two lattices) or
+    // LBM_STREAM_AA (one lattice in place, f[1] aliases f[0]); aa_odd: the
+    // lattice holds the push layout a gather-push step left (the next step is
+    // a local one), else the standard layout
+    int pattern = LBM_STREAM_PULL;
+    int aa_odd = 0;
     double jet_ref[7] = {0, 0, 0, 0, 0, 0, 0};  // yc, zc, U_J, D, x0, B, S; D = 0: none
     int order4 = 0;             // D2Q9: optional fourth-order H_xxyy term
     double *rho_acc = nullptr;  // running sum of rho per cell (temporal mean of p), or null
@@ -370,8 +377,8 @@ static int upload_sponge_tables(lbm_ctx *h)
 static void release(lbm_ctx *h)
 {
     if (!h) return;
-    for (int k = 0; k < 2; ++k)
-        if (h->f[k]) cudaFree(h->f[k]);
+    if (h->f[0]) cudaFree(h->f[0]);
+    if (h->f[1] && h->f[1] != h->f[0]) cudaFree(h->f[1]);
     if (h->solid_d) cudaFree(h->solid_d);
     for (int k = 0; k < 6; ++k)
         if (h->prof_d[k]) cudaFree(h->prof_d[k]);
@@ -754,6 +761,8 @@ extern "C" int lbm_set_transfer_staging(lbm_handle h, size_t max_bytes)
     return LBM_OK;
 }
 
+static int aa_normalize(lbm_ctx *h);
+
 static int set_state_grid(lbm_ctx *h, const GridRef &g, const double *rho, const double *u)
 {
     if (!rho || !u) return fail(h, LBM_EINVAL, "rho and u are required");
@@ -781,6 +790,7 @@ static int set_state_grid(lbm_ctx *h, const GridRef &g, const double *rho, const
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "set state: %s", cudaGetErrorString(e));
     *g.cur = 0;
+    if (g.f == h->f) h->aa_odd = 0;
     if (bad != ~0ull) {
         const int64_t c = (int64_t)bad;
         if (!(rho[c] > 0.0) || !std::isfinite(rho[c]))
@@ -814,11 +824,16 @@ static int set_pops_grid(lbm_ctx *h, const GridRef &g, const double *f)
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "set populations: %s", cudaGetErrorString(e));
     *g.cur = 0;
+    if (g.f == h->f) h->aa_odd = 0;
     return LBM_OK;
 }
 
 static int get_pops_grid(lbm_ctx *h, const GridRef &g, double *f)
 {
+    if (g.f == h->f) {
+        const int rc0 = aa_normalize(h);
+        if (rc0 != LBM_OK) return rc0;
+    }
     if (!f) return fail(h, LBM_EINVAL, "f is null");
     const int64_t N = g.ncell;
     int64_t chunk = 0;
@@ -919,6 +934,10 @@ static int build_params(lbm_ctx *h, StepParams &p)
         p.jet_ref[4] = h->jet_ref[4];
         p.jet_ref[5] = (std::sqrt(2.0) - 1.0) / (h->jet_ref[6] * h->jet_ref[6]);
     }
+    p.sponge_rest = (h->rho_ref == 1.0 && h->u_ref[0] == 0.0 && h->u_ref[1] == 0.0 && h->u_ref[2] == 0.0 &&
+                     p.jet_x_layer == INT_MAX)
+                        ? 1
+                        : 0;
     set_bulk_box(p);
     return LBM_OK;
 }
@@ -926,7 +945,7 @@ static int build_params(lbm_ctx *h, StepParams &p)
 // Whether the row-staged kernel is asked for (it still runs only where eligible)
 static bool staging_wanted(const lbm_ctx *h)
 {
-    if (h->staging == 0) return false;
+    if (h->staging == 0 || h->pattern == LBM_STREAM_AA) return false;
     // default: off -- measured on GB300 for the D3Q19 jet (384 x 256 x 256) the
     // register kernels are faster (FP32 43.3 vs 25.9 GLUPS, FP16 48.9 vs 34.9)
     return h->staging == 1;
@@ -953,8 +972,10 @@ static cudaError_t launch_update(lbm_ctx *h, const StepParams &p, const void *fi
     }
     if (staging_wanted(h) && h->lattice != LBM_D3Q27) {
         const cudaError_t e = h->lattice == LBM_D2Q9
-                                  ? rows_d2q9(h->prec, p, fin, fout, h->rows_block, h->stages, h->err_d, h->stream)
-                                  : rows_d3q19(h->prec, p, fin, fout, h->rows_block, h->stages, h->err_d, h->stream);
+                                  ? rows_d2q9(h->prec, p, fin, fout, h->rows_block, h->stages, h->err_d,
+                                              h->rows_wait_ns, h->stream)
+                                  : rows_d3q19(h->prec, p, fin, fout, h->rows_block, h->stages, h->err_d,
+                                               h->rows_wait_ns, h->stream);
         if (e != cudaErrorNotSupported) {
             h->launches += 1;
             return e;
@@ -1105,6 +1126,56 @@ static int refresh_after_set(lbm_ctx *h, int k)
     return k < (int)h->levels.size() ? init_pair_moments(h, k + 1) : LBM_OK;
 }
 
+// One in-place AA step of level 0: gather-push from the standard layout or
+// the local step from the push layout (which restores the standard one)
+static cudaError_t aa_step(lbm_ctx *h, const StepParams &p)
+{
+    const bool loc = h->aa_odd != 0;
+    int vec = h->vec == 0 ? vec_default(h->lattice, h->prec) : h->vec;
+    if (p.solid || p.bgk || vec == 1 || !vec_supported(h->prec, vec) || p.n[0] % vec != 0) vec = 1;
+    const int block = h->block > 0 ? h->block : block_default(vec);
+    h->launches += 1;
+    h->aa_odd ^= 1;
+    if (vec > 1) {
+        const int sp = loc ? 2 : 1;
+        switch (h->lattice) {
+        case LBM_D2Q9: return stepvec_d2q9(h->prec, vec, p, h->f[0], h->f[0], block, h->stream, sp);
+        case LBM_D3Q19: return stepvec_d3q19(h->prec, vec, p, h->f[0], h->f[0], block, h->stream, sp);
+        default: return stepvec_d3q27(h->prec, vec, p, h->f[0], h->f[0], block, h->stream, sp);
+        }
+    }
+    switch (h->lattice) {
+    case LBM_D2Q9: return step_aa_d2q9(h->prec, p, h->f[0], block, loc, h->stream);
+    case LBM_D3Q19: return step_aa_d3q19(h->prec, p, h->f[0], block, loc, h->stream);
+    default: return step_aa_d3q27(h->prec, p, h->f[0], block, loc, h->stream);
+    }
+}
+
+// Bring an AA lattice left in the push layout back to the standard layout
+// (in place, stream-ordered) before its populations are read as f*_i(x)
+static int aa_normalize(lbm_ctx *h)
+{
+    if (h->pattern != LBM_STREAM_AA || !h->aa_odd) return LBM_OK;
+    StepParams p;
+    std::memset(&p, 0, sizeof p);
+    for (int a = 0; a < 3; ++a) {
+        p.n[a] = h->n[a];
+        p.periodic[a] = h->kind[2 * a] == LBM_BC_PERIODIC ? 1 : 0;
+    }
+    p.ncell = h->ncell;
+    p.solid = h->solid_d;
+    cudaError_t e;
+    switch (h->lattice) {
+    case LBM_D2Q9: e = aa_unswap_d2q9(h->prec, p, h->f[0], h->stream); break;
+    case LBM_D3Q19: e = aa_unswap_d3q19(h->prec, p, h->f[0], h->stream); break;
+    default: e = aa_unswap_d3q27(h->prec, p, h->f[0], h->stream); break;
+    }
+    h->launches += 1;
+    if (e != cudaSuccess) return fail(h, LBM_ECUDA, "AA layout conversion: %s", cudaGetErrorString(e));
+    h->aa_odd = 0;
+    return LBM_OK;
+}
+
 // One step of level k (Sec. II.B applied level by level): the interface
 // moments of its child at t + 1 from the pre-step field, its own update, then
 // two steps of the child with the child's ring refilled at t + 1/2 and t + 1,
@@ -1116,9 +1187,10 @@ static cudaError_t advance_level(lbm_ctx *h, std::vector<StepParams> &params, in
     if (child) e = refine_stage(h, k + 1, 0);
     GridRef g = level_grid(h, k);
     params[k].step = step;
-    if (e == cudaSuccess) e = launch_update(h, params[k], g.f[*g.cur], g.f[1 - *g.cur]);
+    const bool aa = k == 0 && h->pattern == LBM_STREAM_AA;
+    if (e == cudaSuccess) e = aa ? aa_step(h, params[k]) : launch_update(h, params[k], g.f[*g.cur], g.f[1 - *g.cur]);
     if (e != cudaSuccess) return e;
-    *g.cur = 1 - *g.cur;
+    if (!aa) *g.cur = 1 - *g.cur;
     if (!child) return cudaSuccess;
     e = advance_level(h, params, k + 1, 2 * step);
     if (e == cudaSuccess) e = refine_stage(h, k + 1, 1, 1);
@@ -1145,7 +1217,7 @@ static int enqueue_steps(lbm_ctx *h, std::vector<StepParams> &params, int64_t n)
 // captured pair of steps depends on)
 static uint64_t parity_signature(const lbm_ctx *h)
 {
-    uint64_t sig = (uint64_t)h->cur;
+    uint64_t sig = (uint64_t)h->cur | ((uint64_t)h->aa_odd << 63);
     int bit = 1;
     for (const FineLevel *F : h->levels) {
         sig |= (uint64_t)F->cur << bit++;
@@ -1163,7 +1235,7 @@ static int capture_pairs(lbm_ctx *h, std::vector<StepParams> &params, int npairs
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
     }
-    const int cur = h->cur;
+    const int cur = h->cur, aa_odd = h->aa_odd;
     std::vector<int> fcur, mcur;
     for (FineLevel *F : h->levels) {
         fcur.push_back(F->cur);
@@ -1177,6 +1249,7 @@ static int capture_pairs(lbm_ctx *h, std::vector<StepParams> &params, int npairs
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     const int64_t per_graph = h->launches - launches;
     h->cur = cur;
+    h->aa_odd = aa_odd;
     h->step = step;
     h->launches = launches;
     for (size_t k = 0; k < h->levels.size(); ++k) {
@@ -1240,6 +1313,8 @@ extern "C" int lbm_step(lbm_handle h, int64_t n)
 extern "C" int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const int extent[3])
 {
     CHECK_HANDLE(h);
+    if (h->pattern == LBM_STREAM_AA)
+        return fail(h, LBM_EINVAL, "refinement patches need the two-lattice pull pattern (lbm_set_streaming)");
     h->cfg_version++;
     if (h->collision != LBM_COLLISION_RR)
         return fail(h, LBM_EINVAL, "refinement patches couple rrBGK levels; select LBM_COLLISION_RR first");
@@ -1299,6 +1374,10 @@ static int level_ref(lbm_ctx *h, int level, GridRef &g)
 extern "C" int lbm_force(lbm_handle h, int level, double F[3])
 {
     CHECK_HANDLE(h);
+    {
+        const int rc0 = aa_normalize(h);
+        if (rc0 != LBM_OK) return rc0;
+    }
     if (!F) return fail(h, LBM_EINVAL, "F is null");
     GridRef g;
     int rc = level_ref(h, level, g);
@@ -1324,6 +1403,10 @@ extern "C" int lbm_force(lbm_handle h, int level, double F[3])
 extern "C" int lbm_force_async(lbm_handle h, int level, double *F_dev)
 {
     CHECK_HANDLE(h);
+    {
+        const int rc0 = aa_normalize(h);
+        if (rc0 != LBM_OK) return rc0;
+    }
     if (!F_dev) return fail(h, LBM_EINVAL, "F_dev is null");
     GridRef g;
     int rc = level_ref(h, level, g);
@@ -1486,6 +1569,10 @@ extern "C" int lbm_set_sponge_jet_reference(lbm_handle h, double yc, double zc, 
 extern "C" int lbm_pressure_mean(lbm_handle h, int op)
 {
     CHECK_HANDLE(h);
+    {
+        const int rc0 = aa_normalize(h);
+        if (rc0 != LBM_OK) return rc0;
+    }
     if (op != LBM_MEAN_RESET && op != LBM_MEAN_ACCUMULATE)
         return fail(h, LBM_EINVAL, "op = %d is not LBM_MEAN_RESET or LBM_MEAN_ACCUMULATE", op);
     const size_t bytes = sizeof(double) * (size_t)h->ncell;
@@ -1513,6 +1600,10 @@ extern "C" int lbm_pressure_mean(lbm_handle h, int op)
 extern "C" int lbm_pressure_fluctuation(lbm_handle h, double *dp_tilde, double *dp_mean)
 {
     CHECK_HANDLE(h);
+    {
+        const int rc0 = aa_normalize(h);
+        if (rc0 != LBM_OK) return rc0;
+    }
     if (!dp_tilde && !dp_mean) return LBM_OK;
     if (!h->rho_acc || h->rho_count == 0)
         return fail(h, LBM_EINVAL, "no accumulated samples: call lbm_pressure_mean(h, LBM_MEAN_ACCUMULATE) first");
@@ -1544,6 +1635,62 @@ extern "C" int lbm_set_staging(lbm_handle h, int mode, int stages, int block)
     h->staging = mode;
     h->stages = stages;
     h->rows_block = block;
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_streaming(lbm_handle h, int pattern)
+{
+    CHECK_HANDLE(h);
+    if (pattern != LBM_STREAM_PULL && pattern != LBM_STREAM_AA)
+        return fail(h, LBM_EINVAL, "pattern = %d must be LBM_STREAM_PULL or LBM_STREAM_AA", pattern);
+    if (pattern == h->pattern) return LBM_OK;
+    const size_t bytes = (size_t)h->q * (size_t)h->ncell * h->elem;
+    if (pattern == LBM_STREAM_AA) {
+        if (!h->levels.empty())
+            return fail(h, LBM_EINVAL, "the AA pattern is not available with refinement patches");
+        // keep the current lattice, release the other one
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        if (h->cur == 1) std::swap(h->f[0], h->f[1]);
+        CUDA_TRY(h, cudaFree(h->f[1]));
+        h->f[1] = h->f[0];
+        h->cur = 0;
+        h->aa_odd = 0;
+    } else {
+        int rc = aa_normalize(h);
+        if (rc != LBM_OK) return rc;
+        void *f1 = nullptr;
+        cudaError_t e = cudaMalloc(&f1, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, LBM_ENOMEM, "second lattice of %zu bytes: %s", bytes, cudaGetErrorString(e));
+        }
+        // both lattices hold the state (solid cells are never rewritten by the pull update)
+        e = cudaMemcpyAsync(f1, h->f[0], bytes, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            cudaFree(f1);
+            return fail(h, LBM_ECUDA, "copying the lattice: %s", cudaGetErrorString(e));
+        }
+        h->f[1] = f1;
+        h->cur = 0;
+    }
+    h->pattern = pattern;
+    h->cfg_version++;
+    return LBM_OK;
+}
+
+extern "C" int lbm_get_streaming(lbm_handle h, int *pattern)
+{
+    CHECK_HANDLE(h);
+    if (pattern) *pattern = h->pattern;
+    return LBM_OK;
+}
+
+extern "C" int lbm_set_staging_wait(lbm_handle h, uint64_t limit_ns)
+{
+    CHECK_HANDLE(h);
+    h->cfg_version++;
+    h->rows_wait_ns = limit_ns;
     return LBM_OK;
 }
 
@@ -1598,6 +1745,10 @@ extern "C" int lbm_sync(lbm_handle h)
 // ---------------------------------------------------------------------------
 static int moments_grid(lbm_ctx *h, const GridRef &g, double *rho, double *u, double *pi_neq)
 {
+    if (g.f == h->f) {
+        const int rc0 = aa_normalize(h);
+        if (rc0 != LBM_OK) return rc0;
+    }
     if (!rho && !u && !pi_neq) return LBM_OK;
     const int64_t N = g.ncell;
     const size_t per = sizeof(double) * ((rho ? 1 : 0) + (u ? 3 : 0) + (pi_neq ? 6 : 0));
@@ -1634,6 +1785,10 @@ extern "C" int lbm_moments(lbm_handle h, double *rho, double *u, double *pi_neq)
 extern "C" int lbm_reduce(lbm_handle h, double *mass, double momentum[3])
 {
     CHECK_HANDLE(h);
+    {
+        const int rc0 = aa_normalize(h);
+        if (rc0 != LBM_OK) return rc0;
+    }
     double out[RED_FIELDS];
     cudaError_t e = dispatch<Reduce>(h->lattice, h->prec, h->stream, h->ncell, (const void *)h->f[h->cur],
                                      (const uint8_t *)h->solid_d, h->red_d, h->red_blocks);
@@ -1658,6 +1813,10 @@ extern "C" int lbm_reduce(lbm_handle h, double *mass, double momentum[3])
 extern "C" int lbm_probe(lbm_handle h, int n, const int64_t *cells, double *p_prime)
 {
     CHECK_HANDLE(h);
+    {
+        const int rc0 = aa_normalize(h);
+        if (rc0 != LBM_OK) return rc0;
+    }
     if (n < 0) return fail(h, LBM_EINVAL, "n < 0");
     if (n == 0) return LBM_OK;
     if (!cells || !p_prime) return fail(h, LBM_EINVAL, "cells and p_prime are required");
@@ -1684,6 +1843,10 @@ extern "C" int lbm_probe(lbm_handle h, int n, const int64_t *cells, double *p_pr
 extern "C" int lbm_probe_async(lbm_handle h, int n, const int64_t *cells_dev, double *p_dev)
 {
     CHECK_HANDLE(h);
+    {
+        const int rc0 = aa_normalize(h);
+        if (rc0 != LBM_OK) return rc0;
+    }
     if (n < 0) return fail(h, LBM_EINVAL, "n < 0");
     if (n == 0) return LBM_OK;
     if (!cells_dev || !p_dev) return fail(h, LBM_EINVAL, "cells_dev and p_dev are required");
@@ -1723,6 +1886,10 @@ static bool read_all(FILE *fp, void *p, size_t n) { return std::fread(p, 1, n, f
 extern "C" int lbm_save(lbm_handle h, const char *path)
 {
     CHECK_HANDLE(h);
+    {
+        const int rc0 = aa_normalize(h);
+        if (rc0 != LBM_OK) return rc0;
+    }
     if (!path) return fail(h, LBM_EINVAL, "path is null");
     FileHeader hd{};
     std::memcpy(hd.magic, "LBMRRv02", 8);
@@ -1814,6 +1981,7 @@ extern "C" int lbm_load(lbm_handle h, const char *path)
         CUDA_TRY(h, cudaMemcpyAsync(g.f[0], fk.data(), fk.size(), cudaMemcpyHostToDevice, h->stream));
         CUDA_TRY(h, cudaMemcpyAsync(g.f[1], fk.data(), fk.size(), cudaMemcpyHostToDevice, h->stream));
         *g.cur = 0;
+        if (g.f == h->f) h->aa_odd = 0;
     }
     for (int k = 1; k < hd.nlevels; ++k) {
         FineLevel *F = fine_level(h, k);

@@ -2,13 +2,12 @@
 // caller-owned population field, computed without allocating any memory.
 //
 // Some callers cannot allocate device memory at the point where they need
-// the totals: code running under a CUDA stream capture (allocation calls are
-// not capturable), code that must not touch the allocator in a real-time or
-// memory-accounted loop, or a host that owns a fixed device-memory budget and
-// hands the library only its own buffers.  This entry point serves them: the
-// per-block partial sums live in one file-scope static device array, sized
-// for at most LBM_NOALLOC_MAX_CELLS cells, that every GPU which loads the
-// library holds until the process exits.  Nothing here calls cudaMalloc,
+// the totals: a loop that must never enter an allocator (real-time or
+// memory-accounted code), or a host that owns a fixed device-memory budget
+// and hands the library only its own buffers.  This entry point serves them:
+// the per-block partial sums live in one file-scope static device array,
+// sized for at most LBM_NOALLOC_MAX_CELLS cells, that every GPU which loads
+// the library holds until the process exits.  Nothing here calls cudaMalloc,
 // cudaFree or an allocating library routine.
 #include <cstdio>
 #include <mutex>
@@ -36,18 +35,6 @@ __device__ __align__(256) double g_reduce_scratch[NOALLOC_MAX_BLOCKS * RED_FIELD
 std::mutex g_mu;
 double *g_scratch_addr[MAX_DEVICES] = {};
 
-// Final pass: totals in the lbm_reduce convention,
-// out = [sum rho, sum rho ux, sum rho uy, sum rho uz, fluid cells, unstable cells]
-__global__ void k_reduce_totals(int nblocks, const double *__restrict__ partial, double *__restrict__ out)
-{
-    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (k >= RED_FIELDS) return;
-    double v = 0.0;
-    for (int b = lane; b < nblocks; b += 32) v += partial[(int64_t)b * RED_FIELDS + k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) out[k] = v;
-}
-
 // sum rho = fluid cells + sum (rho - 1), after the totals are written
 __global__ void k_reduce_mass(double *__restrict__ out) { out[0] += out[4]; }
 
@@ -58,7 +45,7 @@ cudaError_t launch(const void *f, int64_t ncell, const uint8_t *mask, double *sc
     k_reduce<L, S><<<nblocks, RED_BLOCK, 0, st>>>(ncell, (const S *)f, mask, scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_reduce_totals<<<1, 32 * RED_FIELDS, 0, st>>>(nblocks, scratch, out);
+    k_reduce_final<<<1, 32 * RED_FIELDS, 0, st>>>(nblocks, scratch, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_mass<<<1, 1, 0, st>>>(out);
@@ -76,7 +63,8 @@ int set_error(int code, const char *msg)
 extern "C" int lbm_reduce_noalloc(int lattice, int precision, const void *f, int64_t ncell,
                                   const uint8_t *cell_type, double *out, void *cuda_stream)
 {
-    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19) return set_error(LBM_EINVAL, "lbm_reduce_noalloc: unknown lattice");
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q19 && lattice != LBM_D3Q27)
+        return set_error(LBM_EINVAL, "lbm_reduce_noalloc: unknown lattice");
     if (precision < LBM_FP64 || precision > LBM_BF16_SHIFTED)
         return set_error(LBM_EINVAL, "lbm_reduce_noalloc: unknown precision");
     if (!f || !out) return set_error(LBM_EINVAL, "lbm_reduce_noalloc: f and out are required");
@@ -115,12 +103,19 @@ extern "C" int lbm_reduce_noalloc(int lattice, int precision, const void *f, int
         case LBM_FP16_SHIFTED: e = launch<D2Q9, __half>(f, ncell, cell_type, scratch, nblocks, out, st); break;
         default: e = launch<D2Q9, __nv_bfloat16>(f, ncell, cell_type, scratch, nblocks, out, st); break;
         }
-    } else {
+    } else if (lattice == LBM_D3Q19) {
         switch (precision) {
         case LBM_FP64: e = launch<D3Q19, double>(f, ncell, cell_type, scratch, nblocks, out, st); break;
         case LBM_FP32: e = launch<D3Q19, float>(f, ncell, cell_type, scratch, nblocks, out, st); break;
         case LBM_FP16_SHIFTED: e = launch<D3Q19, __half>(f, ncell, cell_type, scratch, nblocks, out, st); break;
         default: e = launch<D3Q19, __nv_bfloat16>(f, ncell, cell_type, scratch, nblocks, out, st); break;
+        }
+    } else {
+        switch (precision) {
+        case LBM_FP64: e = launch<D3Q27, double>(f, ncell, cell_type, scratch, nblocks, out, st); break;
+        case LBM_FP32: e = launch<D3Q27, float>(f, ncell, cell_type, scratch, nblocks, out, st); break;
+        case LBM_FP16_SHIFTED: e = launch<D3Q27, __half>(f, ncell, cell_type, scratch, nblocks, out, st); break;
+        default: e = launch<D3Q27, __nv_bfloat16>(f, ncell, cell_type, scratch, nblocks, out, st); break;
         }
     }
     if (e != cudaSuccess) return set_error(LBM_ECUDA, cudaGetErrorString(e));

@@ -110,6 +110,14 @@ cudaError_t moments(const Request &r, int cur, double *rho, double *u, cudaStrea
     return cudaGetLastError();
 }
 
+// Per-direction offsets of the vectorised interior path for a domain
+template <class L, class S>
+cudaError_t domain_offsets(StepParams &p)
+{
+    set_offsets<L, S>(p);
+    return cudaSuccess;
+}
+
 #define TYPED_L(fn, L, prec, ...)                                                                   \
     ((prec) == LBM_FP64 ? fn<L, double>(__VA_ARGS__)                                                \
                         : (prec) == LBM_FP32 ? fn<L, float>(__VA_ARGS__)                            \
@@ -311,6 +319,7 @@ static int admit(lbm_server *s)
         d.p.omega = 1.0 - 1.0 / r->tau;
         d.p.jet_x_layer = INT_MAX;
         set_bulk_box(d.p);
+        TYPED(domain_offsets, r->lattice, r->prec, d.p);
         d.f[0] = r->f[0];
         d.f[1] = r->f[1];
         for (int b = 0; b < 2; ++b)

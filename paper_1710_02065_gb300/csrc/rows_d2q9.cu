@@ -5,13 +5,13 @@
 namespace rr {
 
 cudaError_t rows_d2q9(int precision, const StepParams &p, const void *fin, void *fout, int block, int stages,
-                       unsigned *err, cudaStream_t st)
+                       unsigned *err, uint64_t wait_ns, cudaStream_t st)
 {
     switch (precision) {
-    case PREC_FP32: return launch_stream_collide_rows<D2Q9, float, float>(p, fin, fout, block, stages, err, st);
-    case PREC_FP16: return launch_stream_collide_rows<D2Q9, __half, float>(p, fin, fout, block, stages, err, st);
+    case PREC_FP32: return launch_stream_collide_rows<D2Q9, float, float>(p, fin, fout, block, stages, err, wait_ns, st);
+    case PREC_FP16: return launch_stream_collide_rows<D2Q9, __half, float>(p, fin, fout, block, stages, err, wait_ns, st);
     case PREC_BF16:
-        return launch_stream_collide_rows<D2Q9, __nv_bfloat16, float>(p, fin, fout, block, stages, err, st);
+        return launch_stream_collide_rows<D2Q9, __nv_bfloat16, float>(p, fin, fout, block, stages, err, wait_ns, st);
     default: return cudaErrorNotSupported;
     }
 }

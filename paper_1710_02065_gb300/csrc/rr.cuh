@@ -401,26 +401,66 @@ __device__ __forceinline__ Sym2<C> pi_neq(const Mom<C> &m, C dr, C rho, C ux, C 
 
 // ---------------------------------------------------------------------------
 // Moments from direction pairs: s = g_i + g_opp (even), d = g_i - g_opp (odd)
+// (Eq. moments).  D2Q9 and D3Q19 are written out so that partial sums shared
+// by several moments are formed once (the compiler may not reassociate
+// floating-point sums); D3Q27 uses the generic loop over the pairs.
 // ---------------------------------------------------------------------------
 template <class L, class C>
 __device__ __forceinline__ Mom<C> moments_pairs(const C *g)
 {
-    Mom<C> m{};
-    m.dr = g[0];
+    Mom<C> m;
+    if constexpr (L::Q == 19) {
+        // pairs 1 (1,0,0) 2 (0,1,0) 3 (0,0,1) 4 (1,1,0) 5 (1,-1,0)
+        //       6 (1,0,1) 7 (1,0,-1) 8 (0,1,1) 9 (0,1,-1)
+        C s[10], d[10];
 #pragma unroll
-    for (int i = 1; i <= L::HALF; ++i) {
-        const C s = g[i] + g[i + L::HALF], d = g[i] - g[i + L::HALF];
-        const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
-        m.dr += s;
-        if (x) m.jx = x > 0 ? m.jx + d : m.jx - d;
-        if (y) m.jy = y > 0 ? m.jy + d : m.jy - d;
-        if (z) m.jz = z > 0 ? m.jz + d : m.jz - d;
-        if (x) m.sxx += s;
-        if (y) m.syy += s;
-        if (z) m.szz += s;
-        if (x && y) m.sxy = x * y > 0 ? m.sxy + s : m.sxy - s;
-        if (x && z) m.sxz = x * z > 0 ? m.sxz + s : m.sxz - s;
-        if (y && z) m.syz = y * z > 0 ? m.syz + s : m.syz - s;
+        for (int i = 1; i <= 9; ++i) {
+            s[i] = g[i] + g[i + 9];
+            d[i] = g[i] - g[i + 9];
+        }
+        const C a = s[4] + s[5], b = s[6] + s[7], c = s[8] + s[9];
+        m.dr = ((g[0] + s[1]) + (s[2] + s[3])) + ((a + b) + c);
+        m.jx = (d[1] + (d[4] + d[5])) + (d[6] + d[7]);
+        m.jy = (d[2] + (d[4] - d[5])) + (d[8] + d[9]);
+        m.jz = (d[3] + (d[6] - d[7])) + (d[8] - d[9]);
+        m.sxx = (s[1] + a) + b;
+        m.syy = (s[2] + a) + c;
+        m.szz = (s[3] + b) + c;
+        m.sxy = s[4] - s[5];
+        m.sxz = s[6] - s[7];
+        m.syz = s[8] - s[9];
+    } else if constexpr (L::Q == 9) {
+        // pairs 1 (1,0) 2 (0,1) 3 (1,1) 4 (-1,1)
+        const C s1 = g[1] + g[5], s2 = g[2] + g[6], s3 = g[3] + g[7], s4 = g[4] + g[8];
+        const C d1 = g[1] - g[5], d2 = g[2] - g[6], d3 = g[3] - g[7], d4 = g[4] - g[8];
+        const C a = s3 + s4;
+        m.dr = (g[0] + s1) + (s2 + a);
+        m.jx = d1 + (d3 - d4);
+        m.jy = d2 + (d3 + d4);
+        m.jz = C(0);
+        m.sxx = s1 + a;
+        m.syy = s2 + a;
+        m.szz = C(0);
+        m.sxy = s3 - s4;
+        m.sxz = m.syz = C(0);
+    } else {
+        m = Mom<C>{};
+        m.dr = g[0];
+#pragma unroll
+        for (int i = 1; i <= L::HALF; ++i) {
+            const C s = g[i] + g[i + L::HALF], d = g[i] - g[i + L::HALF];
+            const int x = L::cx(i), y = L::cy(i), z = L::cz(i);
+            m.dr += s;
+            if (x) m.jx = x > 0 ? m.jx + d : m.jx - d;
+            if (y) m.jy = y > 0 ? m.jy + d : m.jy - d;
+            if (z) m.jz = z > 0 ? m.jz + d : m.jz - d;
+            if (x) m.sxx += s;
+            if (y) m.syy += s;
+            if (z) m.szz += s;
+            if (x && y) m.sxy = x * y > 0 ? m.sxy + s : m.sxy - s;
+            if (x && z) m.sxz = x * z > 0 ? m.sxz + s : m.sxz - s;
+            if (y && z) m.syz = y * z > 0 ? m.syz + s : m.syz - s;
+        }
     }
     return m;
 }
@@ -545,6 +585,203 @@ __device__ __forceinline__ C rebuild_rest(const Coef<C> &k, const RebuildPre<C> 
 // in FP32 (a few ulp; the FP32 path's tolerance is 1e-5), IEEE in FP64.
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// ---------------------------------------------------------------------------
+// All Q rebuilt populations of one cell, o[i] = w_i [a0 + 3 xi.a1 + 4.5 H2_i:A2
+// + T3_i(A3)] in the lattice's direction order.  D2Q9 and D3Q19 are written
+// out with the weights folded into the constants and the sums shared by an
+// opposite pair (even part E, odd part O: o_i = E + O, o_opp = E - O) or by
+// the two pairs of a coordinate plane formed once.  With the D3Q19 pairing
+// of the third order (sums / differences of (xxy, yzz), (xzz, xyy),
+// (yyz, xxz) over their lattice norms) the third-order part of a direction
+// reduces to
+//   face s e_a:            -9 w1 s T_a   (T_x = A_xyy + A_xzz,
+//                                         T_y = A_xxy + A_yzz, T_z = A_xxz + A_yyz),
+//   edge s_a e_a + s_b e_b:  9 w2 (s_b A_aab + s_a A_abb),
+// which is what the pair sums and differences of rebuild_pair evaluate to.
+// O4 = false drops the optional fourth-order D2Q9 term.  D3Q27 uses the
+// generic pair rebuild.
+// ---------------------------------------------------------------------------
+template <class L, class C, bool O4 = true>
+__device__ __forceinline__ void rebuild_all(const Coef<C> &k, C *o)
+{
+    if constexpr (L::Q == 19) {
+        // w0 = 1/3, w1 = 1/18, w2 = 1/36; 4.5 w1 = 1/4, 4.5 w2 = 1/8, 9 w2 = 1/4
+        const C tr = (k.xx + k.yy) + k.zz;
+        const C tr3 = tr * C(1.0 / 3.0), t23 = tr - tr3;
+        o[0] = fmac(C(-1.5), tr3, C(1.0 / 3.0) * k.a0);
+        const C wa1 = C(1.0 / 18.0) * k.a0, wa2 = C(1.0 / 36.0) * k.a0;
+        // faces: E = w1 a0 + (A_aa - tr/3) / 4, O = a1_a / 6 - T_a / 2
+        {
+            const C E = fmac(C(0.25), k.xx - tr3, wa1);
+            const C O = fmac(C(-0.5), k.xzz + k.xyy, C(1.0 / 6.0) * k.a1x);
+            o[1] = E + O;
+            o[10] = E - O;
+        }
+        {
+            const C E = fmac(C(0.25), k.yy - tr3, wa1);
+            const C O = fmac(C(-0.5), k.xxy + k.yzz, C(1.0 / 6.0) * k.a1y);
+            o[2] = E + O;
+            o[11] = E - O;
+        }
+        {
+            const C E = fmac(C(0.25), k.zz - tr3, wa1);
+            const C O = fmac(C(-0.5), k.yyz + k.xxz, C(1.0 / 6.0) * k.a1z);
+            o[3] = E + O;
+            o[12] = E - O;
+        }
+        // edges: a1 / 12 shared by the three planes
+        const C jx = C(1.0 / 12.0) * k.a1x, jy = C(1.0 / 12.0) * k.a1y, jz = C(1.0 / 12.0) * k.a1z;
+        {  // xy plane: 4 (1,1,0) / 13, 5 (1,-1,0) / 14
+            const C base = fmac(C(0.125), t23 - k.zz, wa2);
+            const C Ep = fmac(C(0.25), k.xy, base), Em = fmac(C(-0.25), k.xy, base);
+            const C Op = fmac(C(0.25), k.xxy + k.xyy, jx + jy);
+            const C Om = fmac(C(0.25), k.xyy - k.xxy, jx - jy);
+            o[4] = Ep + Op;
+            o[13] = Ep - Op;
+            o[5] = Em + Om;
+            o[14] = Em - Om;
+        }
+        {  // xz plane: 6 (1,0,1) / 15, 7 (1,0,-1) / 16
+            const C base = fmac(C(0.125), t23 - k.yy, wa2);
+            const C Ep = fmac(C(0.25), k.xz, base), Em = fmac(C(-0.25), k.xz, base);
+            const C Op = fmac(C(0.25), k.xzz + k.xxz, jx + jz);
+            const C Om = fmac(C(0.25), k.xzz - k.xxz, jx - jz);
+            o[6] = Ep + Op;
+            o[15] = Ep - Op;
+            o[7] = Em + Om;
+            o[16] = Em - Om;
+        }
+        {  // yz plane: 8 (0,1,1) / 17, 9 (0,1,-1) / 18
+            const C base = fmac(C(0.125), t23 - k.xx, wa2);
+            const C Ep = fmac(C(0.25), k.yz, base), Em = fmac(C(-0.25), k.yz, base);
+            const C Op = fmac(C(0.25), k.yzz + k.yyz, jy + jz);
+            const C Om = fmac(C(0.25), k.yzz - k.yyz, jy - jz);
+            o[8] = Ep + Op;
+            o[17] = Ep - Op;
+            o[9] = Em + Om;
+            o[18] = Em - Om;
+        }
+    } else if constexpr (L::Q == 9) {
+        // w0 = 4/9, w1 = 1/9, w2 = 1/36; H_xxyy / (4 c_s^8) weighted: rest 1,
+        // faces -1/2, diagonals 1/4 (zero coefficient unless fourth order)
+        const C tr = k.xx + k.yy;
+        const C tr3 = tr * C(1.0 / 3.0);
+        C g0 = fmac(C(-2.0), tr3, C(4.0 / 9.0) * k.a0);
+        if (O4) g0 = g0 + k.xxyy;
+        o[0] = g0;
+        const C wa1 = C(1.0 / 9.0) * k.a0, wa2 = C(1.0 / 36.0) * k.a0;
+        {  // 1 (1,0) / 5
+            C E = fmac(C(0.5), k.xx - tr3, wa1);
+            if (O4) E = fmac(C(-0.5), k.xxyy, E);
+            const C O = fmac(C(-0.5), k.xyy, C(1.0 / 3.0) * k.a1x);
+            o[1] = E + O;
+            o[5] = E - O;
+        }
+        {  // 2 (0,1) / 6
+            C E = fmac(C(0.5), k.yy - tr3, wa1);
+            if (O4) E = fmac(C(-0.5), k.xxyy, E);
+            const C O = fmac(C(-0.5), k.xxy, C(1.0 / 3.0) * k.a1y);
+            o[2] = E + O;
+            o[6] = E - O;
+        }
+        {  // 3 (1,1) / 7, 4 (-1,1) / 8
+            C base = fmac(C(0.125), tr - tr3, wa2);
+            if (O4) base = fmac(C(0.25), k.xxyy, base);
+            const C jx = C(1.0 / 12.0) * k.a1x, jy = C(1.0 / 12.0) * k.a1y;
+            const C Ep = fmac(C(0.25), k.xy, base), Em = fmac(C(-0.25), k.xy, base);
+            const C Op = fmac(C(0.25), k.xxy + k.xyy, jx + jy);
+            const C Om = fmac(C(0.25), k.xxy - k.xyy, jy - jx);
+            o[3] = Ep + Op;
+            o[7] = Ep - Op;
+            o[4] = Em + Om;
+            o[8] = Em - Om;
+        }
+    } else {
+        const RebuildPre<C> r = rebuild_prep<L, C>(k);
+        o[0] = rebuild_rest<L, C>(k, r);
+#pragma unroll
+        for (int i = 1; i <= L::HALF; ++i) rebuild_pair<L, C>(k, r, i, o[i], o[i + L::HALF]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Collision coefficients of an interior cell (no boundary role) of the
+// rrBGK update, Eq. optimizedLB: a0 = rho - 1, a1 = j, with
+//   P_ab = j_a u_b (= rho u_a u_b),  Pi^neq_ab = s_ab - (rho - 1) c_s^2 d_ab - P_ab,
+//   A2 = P + w Pi^neq (w = 1 - 1/tau),
+//   A3_aab = a3_eq + w a3_neq = P_aa u_b + w (2 u_a Pi^neq_ab + u_b Pi^neq_aa)
+//          = u_b A2_aa + 2 u_a (w Pi^neq_ab)                  (Eq. recursive1/2),
+// and the optional fourth-order D2Q9 term a4 = P_xx u_y^2 + w (u_x^2 Pi_yy +
+// u_y^2 Pi_xx + 4 u_x u_y Pi_xy).
+// Sponge cells whose reference state is the rest state rho_ref = 1, u_ref = 0
+// (Eq. spongeLB with Eq. dampingLBM, n = m = 1/2): the moments are damped,
+// rho* - 1 = (rho - 1) h, j* = j h, h = 1 / (1 + chi / 2), the equilibrium part
+// is scaled by 1 - chi and feqH(rho_ref, u_ref) is the rest state, zero in
+// shifted form.  chi = 0 gives the bulk coefficients.
+// ---------------------------------------------------------------------------
+template <class L, class C, bool SPONGE>
+__device__ __forceinline__ Coef<C> coef_interior(const Mom<C> &m, C om, C chi, bool o4 = false)
+{
+    Coef<C> k;
+    C dr = m.dr, jx = m.jx, jy = m.jy, jz = m.jz, sc = C(1);
+    if (SPONGE) {
+        const C h = recip(fmac(C(0.5), chi, C(1)));
+        dr = dr * h;
+        jx = jx * h;
+        jy = jy * h;
+        jz = jz * h;
+        sc = C(1) - chi;
+    }
+    const C inv = recip(C(1) + dr);
+    const C ux = jx * inv, uy = jy * inv;
+    const C c = dr * C(1.0 / 3.0);
+    const C Pxx = jx * ux, Pyy = jy * uy, Pxy = jx * uy;
+    const C nxx = (m.sxx - c) - Pxx, nyy = (m.syy - c) - Pyy;
+    const C qxy = om * (m.sxy - Pxy);
+    k.a0 = SPONGE ? sc * dr : dr;
+    k.a1x = SPONGE ? sc * jx : jx;
+    k.a1y = SPONGE ? sc * jy : jy;
+    k.xx = fmac(om, nxx, SPONGE ? sc * Pxx : Pxx);
+    k.yy = fmac(om, nyy, SPONGE ? sc * Pyy : Pyy);
+    k.xy = fmac(SPONGE ? sc : C(1), Pxy, qxy);
+    const C ux2 = ux + ux, uy2 = uy + uy;
+    k.xxy = fmac(uy, k.xx, ux2 * qxy);
+    k.xyy = fmac(ux, k.yy, uy2 * qxy);
+    if constexpr (L::D == 3) {
+        const C uz = jz * inv;
+        const C Pzz = jz * uz, Pxz = jx * uz, Pyz = jy * uz;
+        const C nzz = (m.szz - c) - Pzz;
+        const C qxz = om * (m.sxz - Pxz), qyz = om * (m.syz - Pyz);
+        k.a1z = SPONGE ? sc * jz : jz;
+        k.zz = fmac(om, nzz, SPONGE ? sc * Pzz : Pzz);
+        k.xz = fmac(SPONGE ? sc : C(1), Pxz, qxz);
+        k.yz = fmac(SPONGE ? sc : C(1), Pyz, qyz);
+        const C uz2 = uz + uz;
+        k.xxz = fmac(uz, k.xx, ux2 * qxz);
+        k.xzz = fmac(ux, k.zz, uz2 * qxz);
+        k.yyz = fmac(uz, k.yy, uy2 * qyz);
+        k.yzz = fmac(uy, k.zz, uz2 * qyz);
+        if constexpr (full_third_order<L>()) {
+            // A3_xyz = P_xy u_z (scaled) + w (u_x Pi_yz + u_y Pi_xz + u_z Pi_xy)
+            //        = u_z A2_xy + u_x q_yz + u_y q_xz
+            k.xyz = fmac(uz, k.xy, fmac(ux, qyz, uy * qxz));
+        } else {
+            k.xyz = C(0);
+        }
+        k.xxyy = C(0);
+    } else {
+        k.a1z = k.zz = k.xz = k.yz = C(0);
+        k.xxz = k.xzz = k.yyz = k.yzz = k.xyz = C(0);
+        k.xxyy = C(0);
+        if (o4) {
+            const C uxx = ux * ux, uyy = uy * uy;
+            const C a4n = fmac(uxx, nyy, fmac(uyy, nxx, C(4) * ux * uy * (m.sxy - Pxy)));
+            k.xxyy = fmac(om, a4n, (SPONGE ? sc * Pxx : Pxx) * uyy);
+        }
+    }
+    return k;
+}
 
 // splitmix64 (Steele, Lea and Flood 2014): counter-based uniform in [0, 1)
 __device__ __forceinline__ double u01(uint64_t x)

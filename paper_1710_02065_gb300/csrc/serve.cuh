@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(128) k_batched(const BatchDomain *__restrict__
         if constexpr (V == 1) {
             if (x0 < d.p.n[0]) update_cell<L, S, C, false, kMaskNone>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);
         } else {
-            update_vec<L, S, C, V>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);
+            update_vec<L, S, C, V, V>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);
         }
     }
 }

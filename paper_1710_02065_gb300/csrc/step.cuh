@@ -83,6 +83,18 @@ struct StepParams {
     // their parameter offsets and cost the BF16 two-cell kernel 4% and the
     // FP32 one 2% (measured on GB300).
     unsigned *err;
+    // every sponge layer relaxes to the rest state (rho_ref = 1, u_ref = 0,
+    // no jet reference): the closed-form sponge coefficients apply
+    int sponge_rest;
+    // interior path of the vectorised kernel: byte offsets, from a cell's own
+    // offset, of the cell its direction-i population is pulled from in the
+    // lattice read (ld_off: direction i's array, row y - c_y, z - c_z) and of
+    // direction i's array in the lattice written (st_off); valid when off32
+    // (all directions of a lattice span fewer than 2^31 bytes)
+    int off32;
+    int ld_off[kMaxQ];
+    int st_off[kMaxQ];
+    int radial_on;  // the circular / spherical sponge layer is set (radial[4] > 0)
 };
 
 // Bulk box of a lattice (host): on each axis the coordinates that are neither
@@ -106,6 +118,22 @@ inline void set_bulk_box(StepParams &p)
         p.blo[a] = lo;
         p.bhi[a] = hi > lo ? hi : lo;
     }
+    p.radial_on = (p.any_sponge && p.radial[4] > 0.0) ? 1 : 0;
+}
+
+// Per-direction byte offsets of the vectorised kernel's interior path (host)
+template <class L, class S>
+inline void set_offsets(StepParams &p)
+{
+    const int64_t span = (int64_t)L::Q * p.ncell * (int64_t)sizeof(S);
+    p.off32 = span < ((int64_t)1 << 31) ? 1 : 0;
+    const int64_t nx = p.n[0], nxy = (int64_t)p.n[0] * p.n[1];
+    for (int i = 0; i < kMaxQ; ++i) {
+        p.ld_off[i] = p.st_off[i] = 0;
+        if (!p.off32 || i >= L::Q) continue;
+        p.st_off[i] = (int)(i * p.ncell * (int64_t)sizeof(S));
+        p.ld_off[i] = (int)((i * p.ncell - L::cy(i) * nx - L::cz(i) * nxy) * (int64_t)sizeof(S));
+    }
 }
 
 // Fill the per-direction base addresses for one launch (host)
@@ -117,6 +145,7 @@ inline void set_bases(StepParams &p, const void *fin, void *fout)
         p.in[i] = (const char *)fin + (size_t)i * (size_t)p.ncell * sizeof(S);
         p.out[i] = (char *)fout + (size_t)i * (size_t)p.ncell * sizeof(S);
     }
+    set_offsets<L, S>(p);
 }
 
 // ---------------------------------------------------------------------------
@@ -156,7 +185,7 @@ __device__ __forceinline__ C chi_cell(const StepParams &p, C row, int x, int y, 
     if (!p.any_sponge) return row;
     C v = chi_tab<C>(p, x);
     row = v > row ? v : row;
-    if (p.radial[4] > 0.0) {
+    if (p.radial_on) {
         // circular layer: the profile up to its maximum at r0 + 0.8 W, chi_max beyond
         const C dx = C(x) - C(p.radial[0]), dy = C(y) - C(p.radial[1]);
         C r2 = dx * dx + dy * dy;
@@ -234,6 +263,7 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
         add_neq<C, L::D, O3, XYZ>(k, om, ux, uy, uz, pn, o4);
         return k;
     }
+    if (!BGK && chi > C(0) && p.sponge_rest) return coef_interior<L, C, true>(m, om, chi, o4);
     if (chi > C(0)) {
         // sponge: damped moments rho*, rho* u* (n = m = 1/2), then
         // f* = (1 - chi) feqH(rho*, u*) + chi feqH(rho_ref, u_ref) + (1 - 1/tau) fneqH
@@ -269,17 +299,12 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
         add_neq<C, L::D, O3, XYZ>(k, om, ux, uy, uz, pn, o4);
         return k;
     }
+    if (!BGK) return coef_interior<L, C, false>(m, om, C(0), o4);
     const C rho = C(1) + m.dr;
     const C inv = recip(rho);
     const C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
-    if (BGK) {
-        // (1 - 1/tau) f^eq; the caller adds (1 - 1/tau) g
-        add_eq<C, L::D, O3, XYZ>(k, C(1) - om, m.dr, rho, ux, uy, uz, o4);
-        return k;
-    }
-    const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
-    add_eq<C, L::D, O3, XYZ>(k, C(1), m.dr, rho, ux, uy, uz, o4);
-    add_neq<C, L::D, O3, XYZ>(k, om, ux, uy, uz, pn, o4);
+    // (1 - 1/tau) f^eq; the caller adds (1 - 1/tau) g
+    add_eq<C, L::D, O3, XYZ>(k, C(1) - om, m.dr, rho, ux, uy, uz, o4);
     return k;
 }
 
@@ -400,21 +425,239 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     // plain BGK adds (1 - 1/tau) g of the streamed populations except at
     // rebuilt boundary nodes
     const C keep = (BGK && inlet < 0) ? C(p.omega) : C(0);
-    const RebuildPre<C> r = rebuild_prep<L, C>(k);
-    C g0 = rebuild_rest<L, C>(k, r);
-    if (BGK) g0 = fmac(keep, g[0], g0);
-    Store<S>::st((S *)out[0] + cell, g0);
+    C o[L::Q];
+    if (L::D == 2 && p.order4)
+        rebuild_all<L, C, true>(k, o);
+    else
+        rebuild_all<L, C, false>(k, o);
 #pragma unroll
-    for (int i = 1; i <= L::HALF; ++i) {
-        C gp, gm;
-        rebuild_pair<L, C>(k, r, i, gp, gm);
-        if (BGK) {
-            gp = fmac(keep, g[i], gp);
-            gm = fmac(keep, g[i + L::HALF], gm);
-        }
-        Store<S>::st((S *)out[i] + cell, gp);
-        Store<S>::st((S *)out[i + L::HALF] + cell, gm);
+    for (int i = 0; i < L::Q; ++i) {
+        if (BGK) o[i] = fmac(keep, g[i], o[i]);
+        Store<S>::st((S *)out[i] + cell, o[i]);
     }
+}
+
+// ---------------------------------------------------------------------------
+// In-place AA streaming: one lattice, two step types that alternate.
+//   gather-push (LOC = false), from the standard layout P_i[x] = f*_i(x):
+//     pull g_i = P_i[x - xi_i] (halfway bounce-back: P_opp(i)[x]), collide,
+//     push o_i to P_opp(i)[x + xi_i] -- or back to P_i[x] when x + xi_i is a
+//     solid cell or lies outside a non-periodic face;
+//   local (LOC = true): g_i = P_opp(i)[x], which is where the push left the
+//     population streamed into x (a bounce-back included), collide, o_i ->
+//     P_i[x]: the standard layout again.
+// Each cell writes exactly the slots it reads, so the lattice is updated in
+// place without races.  A boundary node collides the populations streamed
+// into its inward neighbour (the same rules as the pull update); to keep the
+// reads and writes of those slots in one thread it is updated by the thread
+// of that neighbour, and the threads of face nodes do nothing.  The
+// arithmetic is the pull update's; only where the populations are read and
+// written differs.
+// ---------------------------------------------------------------------------
+template <class L, class S, class C, bool BGK, int MASK, bool LOC>
+__device__ __forceinline__ void update_cell_aa(const StepParams &p, char *const *f, int x, int y, int z)
+{
+    const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+    if (!p.periodic[0] && (x == 0 || x == nx - 1)) return;
+    if (!p.periodic[1] && (y == 0 || y == ny - 1)) return;
+    if (L::D == 3 && !p.periodic[2] && (z == 0 || z == nz - 1)) return;
+    const unsigned unx = nx, uny = ny, unz = nz, nxy = unx * uny;
+    const unsigned cell = x + unx * y + nxy * z;
+    if (index_fault(p, x < 0 || y < 0 || z < 0 || cell >= (unsigned)p.ncell)) return;
+    const uint8_t *__restrict__ solid = MASK != kMaskNone ? p.solid : nullptr;
+    // neighbours of the cell (it is not on a non-periodic face, so only
+    // periodic axes wrap)
+    const unsigned xm = x == 0 ? unx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const unsigned ym = y == 0 ? uny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const unsigned zm = z == 0 ? unz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+
+    C g[L::Q];
+    if (LOC) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) g[i] = Store<S>::ld((const S *)f[opp<L>(i)] + cell);
+    } else {
+        const bool near = MASK == kMaskLinks && solid && (solid[cell] & MASK_NEAR_SOLID);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const unsigned X = L::cx(i) > 0 ? xm : (L::cx(i) < 0 ? xp : (unsigned)x);
+            const unsigned Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : (unsigned)y);
+            const unsigned Z = L::D == 2 ? 0u : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : (unsigned)z));
+            const unsigned src = X + unx * Y + nxy * Z;
+            if (near && i != 0 && (solid[src] & MASK_TYPE) == MASK_SOLID)
+                g[i] = Store<S>::ld((const S *)f[opp<L>(i)] + cell);
+            else
+                g[i] = Store<S>::ld((const S *)f[i] + src);
+        }
+    }
+    const Mom<C> m = moments_pairs<L, C>(g);
+
+    // this cell and the boundary nodes that take its populations
+    int tx[3], ty[3], tz[3], ntx = 1, nty = 1, ntz = 1;
+    tx[0] = x;
+    ty[0] = y;
+    tz[0] = z;
+    if (!p.periodic[0]) {
+        if (x == 1) tx[ntx++] = 0;
+        if (x == nx - 2) tx[ntx++] = nx - 1;
+    }
+    if (!p.periodic[1]) {
+        if (y == 1) ty[nty++] = 0;
+        if (y == ny - 2) ty[nty++] = ny - 1;
+    }
+    if (L::D == 3 && !p.periodic[2]) {
+        if (z == 1) tz[ntz++] = 0;
+        if (z == nz - 2) tz[ntz++] = nz - 1;
+    }
+#pragma unroll 1
+    for (int c = 0; c < ntz; ++c)
+#pragma unroll 1
+        for (int b = 0; b < nty; ++b)
+#pragma unroll 1
+            for (int a = 0; a < ntx; ++a) {
+                const int X = tx[a], Y = ty[b], Z = tz[c];
+                const unsigned t = X + unx * Y + nxy * Z;
+                if (solid && (solid[t] & MASK_TYPE)) continue;  // solid and fixed cells keep their populations
+                // boundary role of the target, as in update_cell
+                int inlet = -1;
+                if (!p.periodic[0]) {
+                    if (X == 0 && p.kind[0] != BC_OUTFLOW) inlet = 0;
+                    if (X == nx - 1 && p.kind[1] != BC_OUTFLOW && inlet < 0) inlet = 1;
+                }
+                if (!p.periodic[1]) {
+                    if (Y == 0 && p.kind[2] != BC_OUTFLOW && inlet < 0) inlet = 2;
+                    if (Y == ny - 1 && p.kind[3] != BC_OUTFLOW && inlet < 0) inlet = 3;
+                }
+                if (L::D == 3 && !p.periodic[2]) {
+                    if (Z == 0 && p.kind[4] != BC_OUTFLOW && inlet < 0) inlet = 4;
+                    if (Z == nz - 1 && p.kind[5] != BC_OUTFLOW && inlet < 0) inlet = 5;
+                }
+                const bool bulk = X >= p.blo[0] && X < p.bhi[0] && Y >= p.blo[1] && Y < p.bhi[1] &&
+                                  Z >= p.blo[2] && Z < p.bhi[2];
+                const C chi = (bulk || inlet >= 0) ? C(0) : chi_cell<L, C>(p, chi_row<L, C>(p, Y, Z), X, Y, Z);
+                const Coef<C> k = cell_coefficients<L, C, BGK>(p, m, chi, X, Y, Z, inlet);
+                const C keep = (BGK && inlet < 0) ? C(p.omega) : C(0);
+                C o[L::Q];
+                if (L::D == 2 && p.order4)
+                    rebuild_all<L, C, true>(k, o);
+                else
+                    rebuild_all<L, C, false>(k, o);
+                if (BGK) {
+#pragma unroll
+                    for (int i = 0; i < L::Q; ++i) o[i] = fmac(keep, g[i], o[i]);
+                }
+                if (LOC) {
+#pragma unroll
+                    for (int i = 0; i < L::Q; ++i) Store<S>::st((S *)f[i] + t, o[i]);
+                } else {
+                    const bool tnear = MASK == kMaskLinks && solid && (solid[t] & MASK_NEAR_SOLID);
+#pragma unroll
+                    for (int i = 0; i < L::Q; ++i) {
+                        int DX = X + L::cx(i), DY = Y + L::cy(i), DZ = Z + L::cz(i);
+                        bool out = false;
+                        if (DX < 0 || DX >= nx) {
+                            if (p.periodic[0]) DX = DX < 0 ? nx - 1 : 0;
+                            else out = true;
+                        }
+                        if (DY < 0 || DY >= ny) {
+                            if (p.periodic[1]) DY = DY < 0 ? ny - 1 : 0;
+                            else out = true;
+                        }
+                        if (L::D == 3 && (DZ < 0 || DZ >= nz)) {
+                            if (p.periodic[2]) DZ = DZ < 0 ? nz - 1 : 0;
+                            else out = true;
+                        }
+                        const unsigned dst = (unsigned)DX + unx * (unsigned)DY + nxy * (unsigned)(L::D == 2 ? 0 : DZ);
+                        if (!out && tnear && i != 0 && (solid[dst] & MASK_TYPE) == MASK_SOLID) out = true;
+                        if (out)
+                            Store<S>::st((S *)f[i] + t, o[i]);
+                        else
+                            Store<S>::st((S *)f[opp<L>(i)] + dst, o[i]);
+                    }
+                }
+            }
+}
+
+// The AA step kernels: one thread per cell, blocks along x (the face nodes'
+// threads return at once)
+template <class L, class S, class C, bool BGK, int MASK, bool LOC>
+__global__ void __launch_bounds__(256) k_stream_collide_aa(const __grid_constant__ StepParams p)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.n[0]) return;
+    update_cell_aa<L, S, C, BGK, MASK, LOC>(p, p.out, x, blockIdx.y, blockIdx.z);
+}
+
+// Launch one AA step (loc: the local step, else gather-push) of the lattice f
+template <class L, class S, class C>
+cudaError_t launch_stream_collide_aa(const StepParams &p, void *f, int block, bool loc, cudaStream_t st)
+{
+    StepParams q = p;
+    set_bases<L, S>(q, f, f);
+    dim3 b(block, 1, 1);
+    dim3 g((p.n[0] + block - 1) / block, p.n[1], p.n[2]);
+    const bool links = p.solid != nullptr;  // user masks hold solid cells (no fixed cells without refinement)
+    if (p.bgk) {
+        if (loc)
+            links ? k_stream_collide_aa<L, S, C, true, kMaskLinks, true><<<g, b, 0, st>>>(q)
+                  : k_stream_collide_aa<L, S, C, true, kMaskNone, true><<<g, b, 0, st>>>(q);
+        else
+            links ? k_stream_collide_aa<L, S, C, true, kMaskLinks, false><<<g, b, 0, st>>>(q)
+                  : k_stream_collide_aa<L, S, C, true, kMaskNone, false><<<g, b, 0, st>>>(q);
+    } else {
+        if (loc)
+            links ? k_stream_collide_aa<L, S, C, false, kMaskLinks, true><<<g, b, 0, st>>>(q)
+                  : k_stream_collide_aa<L, S, C, false, kMaskNone, true><<<g, b, 0, st>>>(q);
+        else
+            links ? k_stream_collide_aa<L, S, C, false, kMaskLinks, false><<<g, b, 0, st>>>(q)
+                  : k_stream_collide_aa<L, S, C, false, kMaskNone, false><<<g, b, 0, st>>>(q);
+    }
+    return cudaGetLastError();
+}
+
+// In-place conversion of the AA push layout (left by a gather-push step)
+// back to the standard layout: the pairs P_i[x] <-> P_opp(i)[x + xi_i]
+// (i = 1..Q/2, x + xi_i inside the lattice with wrap-around on periodic axes,
+// neither end solid) are swapped; each pair is visited once.
+template <class L, class S>
+__global__ void k_aa_unswap(StepParams p, S *f)
+{
+    const int64_t N = p.ncell;
+    const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+    for (int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cell < N;
+         cell += (int64_t)gridDim.x * blockDim.x) {
+        if (p.solid && (p.solid[cell] & MASK_TYPE) == MASK_SOLID) continue;
+        const int x = (int)(cell % nx), y = (int)((cell / nx) % ny), z = (int)(cell / ((int64_t)nx * ny));
+#pragma unroll
+        for (int i = 1; i <= L::HALF; ++i) {
+            int X = x + L::cx(i), Y = y + L::cy(i), Z = z + L::cz(i);
+            if (X < 0 || X >= nx) {
+                if (!p.periodic[0]) continue;
+                X = X < 0 ? nx - 1 : 0;
+            }
+            if (Y < 0 || Y >= ny) {
+                if (!p.periodic[1]) continue;
+                Y = Y < 0 ? ny - 1 : 0;
+            }
+            if (Z < 0 || Z >= nz) {
+                if (!p.periodic[2]) continue;
+                Z = Z < 0 ? nz - 1 : 0;
+            }
+            const int64_t dst = X + (int64_t)nx * (Y + (int64_t)ny * Z);
+            if (p.solid && (p.solid[dst] & MASK_TYPE) == MASK_SOLID) continue;
+            S *a = f + (int64_t)i * N + cell, *b = f + (int64_t)opp<L>(i) * N + dst;
+            const S t = *a;
+            *a = *b;
+            *b = t;
+        }
+    }
+}
+
+template <class L, class S>
+cudaError_t launch_aa_unswap(const StepParams &p, void *f, cudaStream_t st)
+{
+    const int64_t blocks = (p.ncell + 255) / 256;
+    k_aa_unswap<L, S><<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, st>>>(p, (S *)f);
+    return cudaGetLastError();
 }
 
 // General kernel: one thread per cell; MASK: cell-type handling (above);

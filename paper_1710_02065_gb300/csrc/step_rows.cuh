@@ -74,9 +74,26 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Wait for the phase of `parity` to complete; false after `limit_ns`.
+// Non-blocking test of the phase of `parity`
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `parity` to complete; false after `limit_ns`.  A limit
+// of 0 tests once without blocking (the failure path of the bounded wait,
+// exercised by tests: the copies of a tile just issued are still in flight).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, uint64_t limit_ns)
 {
+    if (limit_ns == 0) return mbar_test_wait(bar, parity);
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (;;) {
@@ -258,9 +275,12 @@ __device__ __forceinline__ void update_cell_staged(const StepParams &p, const S 
 
 // The kernel.  Dynamic shared memory: NS barriers (padded to 128 bytes), then
 // NS stages of Q directions x RS elements (RS = R nx rounded up to 16 bytes).
+// wait_ns bounds each wait for a tile's copies (kRowsWaitLimitNs unless a
+// test asks for less); the copies still in flight after a wait gave up are
+// always awaited with kRowsWaitLimitNs before the CTA exits.
 template <class L, class S, class C>
 __global__ void __launch_bounds__(384, 2) k_stream_collide_rows(const __grid_constant__ StepParams p, int R, int RS,
-                                                             int NS, unsigned *err)
+                                                             int NS, unsigned *err, uint64_t wait_ns)
 {
     extern __shared__ __align__(128) unsigned char rows_smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(rows_smem);
@@ -290,7 +310,7 @@ __global__ void __launch_bounds__(384, 2) k_stream_collide_rows(const __grid_con
     int bad = 0, s = 0, k = 0;
     unsigned phase = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++k) {
-        if (!mbar_wait_bounded(&bar[s], phase, kRowsWaitLimitNs)) bad = 1;
+        if (!mbar_wait_bounded(&bar[s], phase, wait_ns)) bad = 1;
         const RowsTile tl = rows_tile(p, t, R);
         const S *st = stages + s * stage_elems;
         int x = x_first, j = j_first, jc = -1;
@@ -379,14 +399,14 @@ cudaError_t rows_plan(const StepParams &p, const void *fin, const void *fout, in
 
 template <class L, class S, class C>
 cudaError_t launch_stream_collide_rows(const StepParams &p, const void *fin, void *fout, int block, int stages,
-                                       unsigned *err, cudaStream_t st)
+                                       unsigned *err, uint64_t wait_ns, cudaStream_t st)
 {
     RowsPlan pl;
     const cudaError_t e = rows_plan<L, S, C>(p, fin, fout, block, stages, pl);
     if (e != cudaSuccess) return e;
     StepParams q = p;
     set_bases<L, S>(q, fin, fout);
-    k_stream_collide_rows<L, S, C><<<pl.grid, pl.block, pl.smem, st>>>(q, pl.R, pl.RS, pl.stages, err);
+    k_stream_collide_rows<L, S, C><<<pl.grid, pl.block, pl.smem, st>>>(q, pl.R, pl.RS, pl.stages, err, wait_ns);
     return cudaGetLastError();
 }
 

@@ -172,163 +172,447 @@ struct VecIO<__nv_bfloat16, 4> {
 };
 
 // ---------------------------------------------------------------------------
-// The kernel.  Block = one warp-multiple of threads along one x row.
-// Requires: no cell-type mask, nx % V == 0.
+// Raw V-wide words of the storage format (one aligned load) and the
+// conversion of element k to the compute type.
 // ---------------------------------------------------------------------------
-// One thread's V cells of a row (x0raw = first cell, a multiple of V); the
-// lanes of a warp hold consecutive V-cell groups of the same row.  Lanes past
-// the row end do nothing.
-template <class L, class S, class C, int V>
-__device__ __forceinline__ void update_vec(const StepParams &p, const char *const *in, char *const *out, int x0raw,
-                                           int y, int z)
-{
-    const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
-    if (x0raw >= nx) return;  // lanes past the row end
-    const int x0 = x0raw;
-    const unsigned nxy = (unsigned)nx * ny;
-
-    // rows streamed from (uniform per thread): inward neighbour on non-periodic y/z faces
-    int sy = y, sz = z, inlet_row = -1;
-    if (!p.periodic[1]) {
-        if (y == 0) { sy = 1; if (p.kind[2] != BC_OUTFLOW) inlet_row = 2; }
-        if (y == ny - 1) { sy = ny - 2; if (p.kind[3] != BC_OUTFLOW && inlet_row < 0) inlet_row = 3; }
-    }
-    if (L::D == 3 && !p.periodic[2]) {
-        if (z == 0) { sz = 1; if (p.kind[4] != BC_OUTFLOW && inlet_row < 0) inlet_row = 4; }
-        if (z == nz - 1) { sz = nz - 2; if (p.kind[5] != BC_OUTFLOW && inlet_row < 0) inlet_row = 5; }
-    }
-    const int ym = sy == 0 ? ny - 1 : sy - 1, yp = sy == ny - 1 ? 0 : sy + 1;
-    const int zm = sz == 0 ? nz - 1 : sz - 1, zp = sz == nz - 1 ? 0 : sz + 1;
-    const int xl = x0 == 0 ? nx - 1 : x0 - 1;        // cell left of the vector (wrapped)
-    const int xr = x0 + V == nx ? 0 : x0 + V;        // cell right of the vector (wrapped)
-
-#ifdef LBM_BOUNDS_CHECK
+template <class S, int V>
+struct Raw;
+template <>
+struct Raw<double, 2> {
+    using T = double2;
+    __device__ static T ld(const double *p) { return __ldg(reinterpret_cast<const double2 *>(p)); }
+    __device__ static double get(const T &v, int k) { return k == 0 ? v.x : v.y; }
+};
+template <>
+struct Raw<float, 2> {
+    using T = float2;
+    __device__ static T ld(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+    __device__ static float get(const T &v, int k) { return k == 0 ? v.x : v.y; }
+};
+template <>
+struct Raw<float, 4> {
+    using T = float4;
+    __device__ static T ld(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+    __device__ static float get(const T &v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); }
+};
+__device__ __forceinline__ float half_lo(unsigned w) { return __low2float(*reinterpret_cast<const __half2 *>(&w)); }
+__device__ __forceinline__ float half_hi(unsigned w) { return __high2float(*reinterpret_cast<const __half2 *>(&w)); }
+template <>
+struct Raw<__half, 2> {
+    using T = unsigned;
+    __device__ static T ld(const __half *p) { return __ldg(reinterpret_cast<const unsigned *>(p)); }
+    __device__ static float get(const T &v, int k) { return k == 0 ? half_lo(v) : half_hi(v); }
+};
+template <>
+struct Raw<__half, 4> {
+    using T = uint2;
+    __device__ static T ld(const __half *p) { return __ldg(reinterpret_cast<const uint2 *>(p)); }
+    __device__ static float get(const T &v, int k)
     {
-        // every row this thread reads (x0 - 1 .. x0 + V, wrapped) and writes
-        bool bad = x0 < 0 || x0 + V > nx || xl >= nx || xr >= nx || sy >= ny || sz >= nz ||
-                   (unsigned)nx * y + nxy * z + x0 + V > (unsigned)p.ncell;
-        for (int i = 0; i < L::Q; ++i) {
-            const int Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
-            const int Z = L::D == 2 ? 0 : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
-            bad = bad || Y < 0 || Y >= ny || Z < 0 || Z >= nz ||
-                  (unsigned)nx * Y + nxy * Z + (unsigned)nx > (unsigned)p.ncell;
-        }
-        if (index_fault(p, bad)) return;
+        return k == 0 ? half_lo(v.x) : (k == 1 ? half_hi(v.x) : (k == 2 ? half_lo(v.y) : half_hi(v.y)));
     }
-#endif
+};
+__device__ __forceinline__ float bf_lo(unsigned w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(unsigned w) { return __uint_as_float(w & 0xffff0000u); }
+template <>
+struct Raw<__nv_bfloat16, 2> {
+    using T = unsigned;
+    __device__ static T ld(const __nv_bfloat16 *p) { return __ldg(reinterpret_cast<const unsigned *>(p)); }
+    __device__ static float get(const T &v, int k) { return k == 0 ? bf_lo(v) : bf_hi(v); }
+};
+template <>
+struct Raw<__nv_bfloat16, 4> {
+    using T = uint2;
+    __device__ static T ld(const __nv_bfloat16 *p) { return __ldg(reinterpret_cast<const uint2 *>(p)); }
+    __device__ static float get(const T &v, int k)
+    {
+        return k == 0 ? bf_lo(v.x) : (k == 1 ? bf_hi(v.x) : (k == 2 ? bf_lo(v.y) : bf_hi(v.y)));
+    }
+};
 
-    // ---- gather
-    C g[L::Q][V];
+// Store G consecutive values (aligned): one G-wide store, 16-bit pairs packed
+// with one rounding conversion each
+template <class S, int G>
+struct GroupSt;
+template <>
+struct GroupSt<double, 2> {
+    __device__ static void st(double *p, const double *o) { *reinterpret_cast<double2 *>(p) = make_double2(o[0], o[1]); }
+};
+template <>
+struct GroupSt<float, 2> {
+    __device__ static void st(float *p, const float *o) { *reinterpret_cast<float2 *>(p) = make_float2(o[0], o[1]); }
+};
+template <>
+struct GroupSt<float, 4> {
+    __device__ static void st(float *p, const float *o)
+    {
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+template <>
+struct GroupSt<__half, 2> {
+    __device__ static void st(__half *p, const float *o) { *reinterpret_cast<unsigned *>(p) = pack_h2(o[0], o[1]); }
+};
+template <>
+struct GroupSt<__half, 4> {
+    __device__ static void st(__half *p, const float *o)
+    {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(pack_h2(o[0], o[1]), pack_h2(o[2], o[3]));
+    }
+};
+template <>
+struct GroupSt<__nv_bfloat16, 2> {
+    __device__ static void st(__nv_bfloat16 *p, const float *o)
+    {
+        *reinterpret_cast<unsigned *>(p) = pack_b2(o[0], o[1]);
+    }
+};
+template <>
+struct GroupSt<__nv_bfloat16, 4> {
+    __device__ static void st(__nv_bfloat16 *p, const float *o)
+    {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(pack_b2(o[0], o[1]), pack_b2(o[2], o[3]));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Rows whose y / z neighbour rows do not wrap around and that are not on a
+// non-periodic y / z face (1 <= y <= ny - 2, 1 <= z <= nz - 2): every
+// population is pulled from a fixed offset of the thread's own cell -- the
+// row x - xi_i in direction i's array, i times the direction stride
+// (p.st_off[1] bytes) from the lattice: one V-wide aligned load per
+// direction plus, for xi_x = +-1, one scalar load of the cell just outside
+// the vector (x0 - 1 or x0 + V, wrapped around on a periodic x axis).  The V
+// cells' populations are then taken element by element; a node on a
+// non-periodic x face takes its x neighbour's streamed populations (same
+// thread) and its boundary role.  Cells are collided and stored G at a time.
+// An interior cell is bulk or a sponge cell: layers relaxing to the rest
+// state use the closed form of coef_interior (which gives the bulk
+// coefficients bit for bit at chi = 0), other references and velocity /
+// free-slip / pressure nodes the general coefficients.
+//
+// Streaming patterns (SP): kPull reads one lattice and writes the other;
+// the two in-place AA step types of update_cell_aa work on one lattice:
+// kAAPush pulls as kPull does and pushes each o_i to P_opp(i)[x + xi_i]
+// (back to P_i[x] outside a non-periodic x face), kAALocal reads the V-wide
+// word of P_opp(i) at the thread's own cells and writes P_i there.  The AA
+// vector path takes rows whose y / z neighbours are not face rows either
+// (a face node is updated with the node it takes populations from).
+// ---------------------------------------------------------------------------
+enum { kPull = 0, kAAPush = 1, kAALocal = 2 };
+
+template <class L, class S, class C, int V>
+struct VecIn {
+    typename Raw<S, V>::T v[L::Q];  // V-wide words, all directions
+    C e[L::Q];                      // edge values, xi_x = +-1 directions (pulls)
+};
+
+// Populations streamed into cell k of a thread's vector: element k of the
+// V-wide load for xi_x = 0 (every direction for the local AA step), the
+// neighbouring element (or the scalar edge value) for xi_x = +-1
+template <class L, class S, class C, int V, int SP>
+__device__ __forceinline__ void gather_vec(const VecIn<L, S, C, V> &r, int k, C *g)
+{
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        const int Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
-        const int Z = L::D == 2 ? 0 : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
-        const S *row = (const S *)in[i] + ((unsigned)nx * Y + nxy * Z);
-        if (L::cx(i) == 0) {
-            C v[V];
-            VecIO<S, V>::ld(row + x0, v);
+        if (SP == kAALocal || L::cx(i) == 0) g[i] = Raw<S, V>::get(r.v[i], k);
+        else if (L::cx(i) > 0) g[i] = k == 0 ? r.e[i] : Raw<S, V>::get(r.v[i], k - 1);
+        else g[i] = k == V - 1 ? r.e[i] : Raw<S, V>::get(r.v[i], k + 1);
+    }
+}
+
+// Address of the row direction i of a cell pulls from: the cell's row
+// shifted by -c_y(i), -c_z(i), in direction i's array (i times the direction
+// stride in bytes)
+template <class L, class S>
+__device__ __forceinline__ const S *vec_row_ptr(const char *bin, int i, int nx, unsigned nxy, unsigned dstride)
+{
+    const char *rb = bin - ((long long)L::cy(i) * nx + (long long)L::cz(i) * (long long)nxy) * (long long)sizeof(S);
+    return reinterpret_cast<const S *>(rb + (size_t)i * dstride);
+}
+
+// Loads of one thread's vector (x0, y, z) of such a row; false when a
+// checked build finds an index outside the lattice (nothing loaded).
+template <class L, class S, class C, int V, int SP>
+__device__ __forceinline__ bool vec_load(const StepParams &p, const char *in0, int x0, int y, int z,
+                                         VecIn<L, S, C, V> &r)
+{
+    using RW = Raw<S, V>;
+    const int nx = p.n[0];
+    const unsigned nxy = (unsigned)nx * (unsigned)p.n[1];
+    const unsigned cell = (unsigned)x0 + (unsigned)nx * y + nxy * z;
+    // cells just left / right of the vector, relative to x0, on a periodic x
+    // axis (wrapped around)
+    const int dl = x0 > 0 ? -1 : nx - 1;
+    const int dr = x0 + V < nx ? V : -x0;
+#ifdef LBM_BOUNDS_CHECK
+    {
+        // every value used lies in its direction's lattice; the unused edge
+        // reads of non-periodic x faces stay inside the allocation
+        const int64_t N = p.ncell;
+        bool bad = (int64_t)cell + V > N;
+        for (int i = 0; i < L::Q && SP != kAALocal; ++i) {
+            const int64_t src = (int64_t)cell - (int64_t)L::cy(i) * nx - (int64_t)L::cz(i) * nxy;
+            bad = bad || src < 0 || src + V > N;
+            if (p.periodic[0]) {
+                if (L::cx(i) > 0) bad = bad || src + dl < 0 || src + dl >= N;
+                if (L::cx(i) < 0) bad = bad || src + dr < 0 || src + dr >= N;
+            } else {
+                if (L::cx(i) > 0) bad = bad || i * N + src - 1 < 0 || (x0 > 0 && src - 1 < 0);
+                if (L::cx(i) < 0) bad = bad || i * N + src + V >= L::Q * N || (x0 + V < nx && src + V >= N);
+            }
+        }
+        if (index_fault(p, bad)) return false;
+    }
+#endif
+    const char *bin = in0 + (size_t)cell * sizeof(S);
+    const unsigned dstride = (unsigned)p.st_off[1];
+    if (SP == kAALocal) {
 #pragma unroll
-            for (int k = 0; k < V; ++k) g[i][k] = v[k];
-        } else if (L::cx(i) > 0) {
-            // f_i(x) = f*_i(x - 1): cells x0 - 1 (wrapped) .. x0 + V - 2
-            g[i][0] = Store<S>::ld(row + xl);
+        for (int i = 0; i < L::Q; ++i)
+            r.v[i] = RW::ld(reinterpret_cast<const S *>(bin + (size_t)opp<L>(i) * dstride));
+    } else if (!p.periodic[0]) {
+        // The edge values at x0 - 1 / x0 + V are read unconditionally: on the
+        // x faces (x0 = 0, x0 + V = nx) they are not used (the face node takes
+        // its neighbour's populations), and the addresses stay inside the
+        // lattice's allocation -- direction i >= 1 with xi_x > 0 reads at
+        // index i ncell + src - 1 >= 0, and the last direction with xi_x < 0
+        // (D2Q9 7, D3Q19 16, D3Q27 26) pulls from a row before the last one,
+        // so i ncell + src + V < Q ncell.  A uniform branch, so no warp
+        // diverges on it.
 #pragma unroll
-            for (int k = 1; k < V; ++k) g[i][k] = Store<S>::ld(row + x0 + k - 1);
-        } else {
-            // f_i(x) = f*_i(x + 1): cells x0 + 1 .. x0 + V (wrapped)
+        for (int i = 0; i < L::Q; ++i) {
+            const S *row = vec_row_ptr<L, S>(bin, i, nx, nxy, dstride);
+            r.v[i] = RW::ld(row);
+            if (L::cx(i) > 0) r.e[i] = Store<S>::ld(row - 1);
+            if (L::cx(i) < 0) r.e[i] = Store<S>::ld(row + V);
+        }
+    } else {
 #pragma unroll
-            for (int k = 0; k < V - 1; ++k) g[i][k] = Store<S>::ld(row + x0 + k + 1);
-            g[i][V - 1] = Store<S>::ld(row + xr);
+        for (int i = 0; i < L::Q; ++i) {
+            const S *row = vec_row_ptr<L, S>(bin, i, nx, nxy, dstride);
+            r.v[i] = RW::ld(row);
+            if (L::cx(i) > 0) r.e[i] = Store<S>::ld(row + dl);
+            if (L::cx(i) < 0) r.e[i] = Store<S>::ld(row + dr);
         }
     }
+    return true;
+}
 
-    // non-periodic x: boundary nodes take their x neighbour's streamed populations
-    const bool xlo = !p.periodic[0] && x0 == 0, xhi = !p.periodic[0] && x0 + V == nx;
-    if (xlo) {
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) g[i][0] = g[i][1];
-    }
-    if (xhi) {
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) g[i][V - 1] = g[i][V - 2];
-    }
+// General collision coefficients as a call (boundary nodes of the vector
+// path, sponge layers with a non-rest reference): kept out of line so that
+// the common path of the vector kernel carries none of its code
+template <class L, class C>
+__device__ __noinline__ Coef<C> coef_general(const StepParams &p, const Mom<C> &m, C chi, int x, int y, int z,
+                                             int inlet)
+{
+    return cell_coefficients<L, C>(p, m, chi, x, y, z, inlet);
+}
 
-    // ---- collision coefficients of the V cells
-    const bool bulk_row = y >= p.blo[1] && y < p.bhi[1] && z >= p.blo[2] && z < p.bhi[2];
-    const C chirow = bulk_row ? C(0) : chi_row<L, C>(p, y, z);
-    Coef<C> cf[V];
+// Store the rebuilt populations o[kk][i] of the group's cells k0 .. k0 + G - 1.
+// kPull / kAALocal: direction i's array at the cells themselves (G-wide).
+// kAAPush: o_i of cell x goes to P_opp(i)[x + xi_i]: a G-wide store in the
+// row y + c_y, z + c_z for xi_x = 0; single values for xi_x = +-1, back to
+// P_i[x] where x + xi_x leaves a non-periodic x axis and wrapped around a
+// periodic one.
+template <class L, class S, class C, int V, int G, int SP>
+__device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x0, int k0, const C (&o)[G][L::Q])
+{
+    const unsigned dstride = (unsigned)p.st_off[1];
+    if (SP != kAAPush) {
 #pragma unroll
-    for (int k = 0; k < V; ++k) {
-        C gk[L::Q];
+        for (int i = 0; i < L::Q; ++i) {
+            C w[G];
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) gk[i] = g[i][k];
-        const Mom<C> m = moments_pairs<L, C>(gk);
-        int inlet = -1;
-        if (k == 0 && xlo && p.kind[0] != BC_OUTFLOW) inlet = 0;
-        else if (k == V - 1 && xhi && p.kind[1] != BC_OUTFLOW) inlet = 1;
-        if (inlet < 0) inlet = inlet_row;
-        const bool bulk = bulk_row && x0 + k >= p.blo[0] && x0 + k < p.bhi[0];
-        const C chi = (bulk || inlet >= 0) ? C(0) : chi_cell<L, C>(p, chirow, x0 + k, y, z);
-        cf[k] = cell_coefficients<L, C>(p, m, chi, x0 + k, y, z, inlet);
-    }
-
-    // ---- rebuild and store, one direction pair at a time
-    const unsigned base = (unsigned)nx * y + nxy * z + x0;
-    if constexpr (V == 2 && std::is_same<S, __nv_bfloat16>::value) {
-        const Coef<F2> c2 = pack_coef(cf[0], cf[1]);
-        const RebuildPre<F2> r2 = rebuild_prep<L, F2>(c2);
-        {
-            const F2 g0 = rebuild_rest<L, F2>(c2, r2);
-            C o[V] = {g0.v.x, g0.v.y};
-            VecIO<S, V>::st((S *)out[0] + base, o);
-        }
-#pragma unroll
-        for (int i = 1; i <= L::HALF; ++i) {
-            F2 p2, m2;
-            rebuild_pair<L, F2>(c2, r2, i, p2, m2);
-            C op[V] = {p2.v.x, p2.v.y}, om[V] = {m2.v.x, m2.v.y};
-            VecIO<S, V>::st((S *)out[i] + base, op);
-            VecIO<S, V>::st((S *)out[i + L::HALF] + base, om);
+            for (int kk = 0; kk < G; ++kk) w[kk] = o[kk][i];
+            GroupSt<S, G>::st(reinterpret_cast<S *>(bout + (size_t)i * dstride) + k0, w);
         }
         return;
     }
-    RebuildPre<C> rp[V];
+    const int nx = p.n[0];
+    const long long nxy = (long long)nx * p.n[1];
 #pragma unroll
-    for (int k = 0; k < V; ++k) rp[k] = rebuild_prep<L, C>(cf[k]);
-    {
-        C o[V];
+    for (int i = 0; i < L::Q; ++i) {
+        const int j = opp<L>(i);
+        S *own = reinterpret_cast<S *>(bout + (size_t)i * dstride) + k0;
+        S *dst = reinterpret_cast<S *>(bout + (size_t)j * dstride +
+                                       ((long long)L::cy(i) * nx + (long long)L::cz(i) * nxy) * (long long)sizeof(S)) +
+                 k0;
+        if (L::cx(i) == 0) {
+            C w[G];
 #pragma unroll
-        for (int k = 0; k < V; ++k) o[k] = rebuild_rest<L, C>(cf[k], rp[k]);
-        VecIO<S, V>::st((S *)out[0] + base, o);
+            for (int kk = 0; kk < G; ++kk) w[kk] = o[kk][i];
+            GroupSt<S, G>::st(dst, w);
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < G; ++kk) {
+                const int x = x0 + k0 + kk, xd = x + L::cx(i);
+                if (xd >= 0 && xd < nx)
+                    Store<S>::st(dst + kk + L::cx(i), o[kk][i]);
+                else if (p.periodic[0])
+                    Store<S>::st(dst + kk + (xd < 0 ? nx - 1 - x : -x), o[kk][i]);
+                else
+                    Store<S>::st(own + kk, o[kk][i]);
+            }
+        }
     }
+}
+
+// Collide the V cells of a loaded vector and store them.  all_bulk: every cell
+// of the vector is bulk (no sponge, no boundary role), decided by the caller
+// for a whole warp so that the warp runs one code path.  Otherwise the
+// moments of a group's cells are taken first, so that an x-face node can use
+// its neighbour's; interior cells relaxing to a rest-state sponge reference
+// (chi from the per-axis tables, 0 in the bulk) use the closed form of
+// coef_interior, everything else the general coefficients (out of line).
+template <class L, class S, class C, int V, int G, int SP>
+__device__ __forceinline__ void vec_collide_store(const StepParams &p, char *out0, int x0, int y, int z,
+                                                  const VecIn<L, S, C, V> &r, bool all_bulk)
+{
+    const int nx = p.n[0];
+    const unsigned nxy = (unsigned)nx * (unsigned)p.n[1];
+    const unsigned cell = (unsigned)x0 + (unsigned)nx * y + nxy * z;
+    char *bout = out0 + (size_t)cell * sizeof(S);
+    const C om = C(p.omega);
+    const bool bulk_row = y >= p.blo[1] && y < p.bhi[1] && z >= p.blo[2] && z < p.bhi[2];
+    const C chirow = bulk_row ? C(0) : chi_row<L, C>(p, y, z);
+    const bool xlo = !p.periodic[0] && x0 == 0, xhi = !p.periodic[0] && x0 + V == nx;
+    // the closed sponge form covers the face layers of a rest-state reference
+    const bool lean = p.sponge_rest && !p.radial_on;
 #pragma unroll
-    for (int i = 1; i <= L::HALF; ++i) {
-        C op[V], om[V];
+    for (int k0 = 0; k0 < V; k0 += G) {
+        C o[G][L::Q];
+        if (all_bulk) {
 #pragma unroll
-        for (int k = 0; k < V; ++k) rebuild_pair<L, C>(cf[k], rp[k], i, op[k], om[k]);
-        VecIO<S, V>::st((S *)out[i] + base, op);
-        VecIO<S, V>::st((S *)out[i + L::HALF] + base, om);
+            for (int kk = 0; kk < G; ++kk) {
+                C g[L::Q];
+                gather_vec<L, S, C, V, SP>(r, k0 + kk, g);
+                rebuild_all<L, C, false>(coef_interior<L, C, false>(moments_pairs<L, C>(g), om, C(0)), o[kk]);
+            }
+        } else {
+            // moments of the group's cells, and of the x neighbour of a face
+            // cell at the group's edge when that neighbour is in another group
+            Mom<C> m[G];
+#pragma unroll
+            for (int kk = 0; kk < G; ++kk) {
+                C g[L::Q];
+                gather_vec<L, S, C, V, SP>(r, k0 + kk, g);
+                m[kk] = moments_pairs<L, C>(g);
+            }
+#pragma unroll
+            for (int kk = 0; kk < G; ++kk) {
+                const int k = k0 + kk, x = x0 + k;
+                const bool face = (k == 0 && xlo) || (k == V - 1 && xhi);
+                // an x-face node collides the populations streamed into its neighbour
+                Mom<C> mk = m[kk];
+                if (face) {
+                    const int kn = k == 0 ? 1 : V - 2;
+                    if (kn >= k0 && kn < k0 + G) {
+                        mk = m[kn - k0];
+                    } else {
+                        C g[L::Q];
+                        gather_vec<L, S, C, V, SP>(r, kn, g);
+                        mk = moments_pairs<L, C>(g);
+                    }
+                }
+                const int inlet = !face ? -1 : (k == 0 ? (p.kind[0] != BC_OUTFLOW ? 0 : -1)
+                                                        : (p.kind[1] != BC_OUTFLOW ? 1 : -1));
+                const bool xbulk = x >= p.blo[0] && x < p.bhi[0];
+                C chi = C(0);
+                if (inlet < 0) {
+                    chi = chirow;
+                    if (!xbulk && p.any_sponge) {
+                        const C v = chi_tab<C>(p, x);
+                        chi = v > chi ? v : chi;
+                    }
+                }
+                Coef<C> cf;
+                if (inlet < 0 && lean)
+                    cf = coef_interior<L, C, true>(mk, om, chi);
+                else
+                    cf = coef_general<L, C>(p, mk, inlet < 0 ? chi_cell<L, C>(p, chirow, x, y, z) : C(0), x, y, z,
+                                            inlet);
+                rebuild_all<L, C, false>(cf, o[kk]);
+            }
+        }
+        vec_store<L, S, C, V, G, SP>(p, bout, x0, k0, o);
+    }
+}
+
+// Whether the vector path applies to row (y, z): its y / z neighbour rows do
+// not wrap and it is not on a non-periodic y / z face; for the AA steps its
+// neighbours are not face rows either.
+template <class L, int SP>
+__device__ __forceinline__ bool vec_row(const StepParams &p, int y, int z)
+{
+    const int ny = p.n[1], nz = p.n[2];
+    bool ok = p.off32 && !p.order4 && y > 0 && y < ny - 1 && (L::D == 2 || (z > 0 && z < nz - 1));
+    if (SP != kPull) {
+        if (!p.periodic[1]) ok = ok && y > 1 && y < ny - 2;
+        if (L::D == 3 && !p.periodic[2]) ok = ok && z > 1 && z < nz - 2;
+    }
+    return ok;
+}
+
+// ---------------------------------------------------------------------------
+// One thread's V cells of a row (x0 = first cell, a multiple of V); lanes
+// past the row end do nothing.  Rows outside the vector path update their
+// cells one by one with the general update (the same arithmetic).  in / out:
+// per-direction bases of the lattices (one lattice for the AA steps).  Used
+// by the single-lattice kernel and by the batched serving kernel.
+// ---------------------------------------------------------------------------
+template <class L, class S, class C, int V, int G, int SP = kPull>
+__device__ __forceinline__ void update_vec(const StepParams &p, const char *const *in, char *const *out, int x0,
+                                           int y, int z)
+{
+    if (x0 >= p.n[0]) return;  // lanes past the row end
+    if (vec_row<L, SP>(p, y, z)) {
+        VecIn<L, S, C, V> r;
+        if (!vec_load<L, S, C, V, SP>(p, in[0], x0, y, z, r)) return;
+        const bool bulk = y >= p.blo[1] && y < p.bhi[1] && z >= p.blo[2] && z < p.bhi[2] && x0 >= p.blo[0] &&
+                          x0 + V <= p.bhi[0];
+        vec_collide_store<L, S, C, V, G, SP>(p, out[0], x0, y, z, r, bulk);
+        return;
+    }
+#pragma unroll 1
+    for (int k = 0; k < V; ++k) {
+        if (SP == kPull)
+            update_cell<L, S, C, false, kMaskNone>(p, in, out, x0 + k, y, z);
+        else
+            update_cell_aa<L, S, C, false, kMaskNone, SP == kAALocal>(p, out, x0 + k, y, z);
     }
 }
 
 // Minimum resident 256-thread blocks per SM asked of the compiler: 16-bit
-// storage with 2 cells per thread is issue-bound, and capping it at 64
-// registers (4 x 256 threads per SM, a few bytes of spill) measured 3%
-// faster on GB300; every other instantiation keeps its natural allocation.
+// storage with 2 cells per thread is issue-bound, and 64 registers (4 x 256
+// threads per SM) keep enough warps resident to hide the loads; the wider
+// types and 4 cells per thread take 128.
 template <class S, int V>
 struct VecMinBlocks {
-    static constexpr int value = (sizeof(S) == 2 && V == 2) ? 4 : 1;
+    static constexpr int value = (sizeof(S) == 2 && V == 2) ? 4 : 2;
 };
 
-template <class L, class S, class C, int V>
+// Cells collided and stored together (one G-wide store per direction)
+template <class S, int V>
+struct VecGroup {
+    static constexpr int value = 2;
+};
+
+// ---------------------------------------------------------------------------
+// The kernel: blocks along x rows (blockIdx.y = y, blockIdx.z = z), V cells
+// per thread.  Requires: no cell-type mask, nx % V == 0.
+// ---------------------------------------------------------------------------
+template <class L, class S, class C, int V, int SP>
 __global__ void __launch_bounds__(256, (VecMinBlocks<S, V>::value)) k_stream_collide_vec(const __grid_constant__ StepParams p)
 {
-    update_vec<L, S, C, V>(p, p.in, p.out, (blockIdx.x * blockDim.x + threadIdx.x) * V, blockIdx.y, blockIdx.z);
+    update_vec<L, S, C, V, VecGroup<S, V>::value, SP>(p, p.in, p.out, (blockIdx.x * blockDim.x + threadIdx.x) * V,
+                                                      blockIdx.y, blockIdx.z);
 }
 
+// sp: kPull (fin read, fout written) or an AA step type (fin == fout)
 template <class L, class S, class C, int V>
 cudaError_t launch_stream_collide_vec(const StepParams &p, const void *fin, void *fout, int block,
-                                      cudaStream_t st)
+                                      cudaStream_t st, int sp = kPull)
 {
     const int threads_per_row = (p.n[0] / V + 31) / 32 * 32;
     const int b = block < threads_per_row ? block : threads_per_row;
@@ -336,7 +620,12 @@ cudaError_t launch_stream_collide_vec(const StepParams &p, const void *fin, void
     dim3 g((p.n[0] / V + b - 1) / b, p.n[1], p.n[2]);
     StepParams q = p;
     set_bases<L, S>(q, fin, fout);
-    k_stream_collide_vec<L, S, C, V><<<g, bd, 0, st>>>(q);
+    if (sp == kAAPush)
+        k_stream_collide_vec<L, S, C, V, kAAPush><<<g, bd, 0, st>>>(q);
+    else if (sp == kAALocal)
+        k_stream_collide_vec<L, S, C, V, kAALocal><<<g, bd, 0, st>>>(q);
+    else
+        k_stream_collide_vec<L, S, C, V, kPull><<<g, bd, 0, st>>>(q);
     return cudaGetLastError();
 }
 

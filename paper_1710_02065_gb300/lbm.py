@@ -26,6 +26,7 @@ LBM_FP64, LBM_FP32, LBM_FP16_SHIFTED, LBM_BF16_SHIFTED = 0, 1, 2, 3
 LBM_FACE_XM, LBM_FACE_XP, LBM_FACE_YM, LBM_FACE_YP, LBM_FACE_ZM, LBM_FACE_ZP = range(6)
 LBM_BC_PERIODIC, LBM_BC_VELOCITY, LBM_BC_OUTFLOW, LBM_BC_FREESLIP, LBM_BC_PRESSURE = 0, 1, 2, 3, 4
 LBM_CELL_FLUID, LBM_CELL_SOLID = 0, 1
+LBM_STREAM_PULL, LBM_STREAM_AA = 0, 1
 
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16_SHIFTED, "bf16": LBM_BF16_SHIFTED}
 
@@ -76,6 +77,9 @@ _sig("lbm_pressure_mean", [_h, C.c_int])
 _sig("lbm_pressure_fluctuation", [_h, _dp, _dp])
 _sig("lbm_set_sponge_jet_reference", [_h] + [C.c_double] * 7)
 _sig("lbm_get_staging", [_h, _ip, _ip, _ip, _ip, _ip])
+_sig("lbm_set_staging_wait", [_h, C.c_uint64])
+_sig("lbm_set_streaming", [_h, C.c_int])
+_sig("lbm_get_streaming", [_h, _ip])
 _sig("lbm_info", [_h, _i64p, _i64p, _dp, _dp])
 _sig("lbm_add_refinement_patch", [_h, _ip, _ip])
 _sig("lbm_force", [_h, C.c_int, _dp])
@@ -288,6 +292,22 @@ def lbm_set_collision(h, model: int):
 
 def lbm_set_staging(h, mode: int = -1, stages: int = 0, block: int = 0):
     return _check(_lib.lbm_set_staging(h, int(mode), int(stages), int(block)), h)
+
+
+def lbm_set_streaming(h, pattern: int):
+    """LBM_STREAM_PULL (two lattices) or LBM_STREAM_AA (one lattice in place)."""
+    return _check(_lib.lbm_set_streaming(h, int(pattern)), h)
+
+
+def lbm_get_streaming(h) -> int:
+    v = C.c_int()
+    _check(_lib.lbm_get_streaming(h, C.byref(v)), h)
+    return v.value
+
+
+def lbm_set_staging_wait(h, limit_ns: int):
+    """Limit (ns) of each wait of the row-staged kernel for a tile's copies."""
+    return _check(_lib.lbm_set_staging_wait(h, int(limit_ns)), h)
 
 
 def lbm_set_transfer_staging(h, max_bytes: int):

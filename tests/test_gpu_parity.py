@@ -50,14 +50,15 @@ KERNELS = {"fp64": ["cell", "vec2"], "fp32": ["rows", "cell", "vec2", "vec4"],
 
 
 def use_kernel(s, kind, block=64):
-    """Select one update kernel on solver s; 'rows' must then be active."""
-    from paper_1710_02065_gb300 import lbm
+    """Select one update kernel (and streaming pattern, 'aa-' prefix) on
+    solver s; 'rows' must then be active."""
+    from paper_1710_02065_gb300 import autotune, lbm
     if kind == "rows":
+        lbm.lbm_set_streaming(s.h, lbm.LBM_STREAM_PULL)
         lbm.lbm_set_staging(s.h, 1, 0, 0)
         assert lbm.lbm_get_staging(s.h)[0] == 1, "row-staged kernel not eligible"
     else:
-        lbm.lbm_set_staging(s.h, 0, 0, 0)
-        lbm.lbm_set_launch(s.h, block, 1 if kind == "cell" else int(kind[3:]))
+        assert autotune.apply(s.h, (kind, block))
 
 
 def _normwise(a, b):
@@ -401,16 +402,19 @@ def test_full_size_cylinder_one_step():
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
 def test_full_size_round_jet_sampled_cells(prec):
-    """384 x 256 x 256 round jet at full size in the benchmark's launch
-    configuration: one step from a random state; 6000 sampled cells (random,
-    plus every face, edge, sponge and inlet class) checked cell by cell."""
+    """384 x 256 x 256 round jet at full size, in every launch configuration
+    the benchmark's autotuner may pick for the precision (one cell per thread,
+    the vectorised kernel with 2 and 4 cells per thread, the row-staged
+    kernel; two-lattice pull and in-place AA): one step from a random state
+    (for AA a gather-push step, read back through the layout conversion);
+    6000 sampled cells (random, plus every face, edge, sponge and inlet class)
+    checked cell by cell."""
+    from paper_1710_02065_gb300 import autotune
     c = round_jet()
     _, _, _, w, _ = oracle.lattice(D3Q19)
     c.f0 = inputs.random_populations(w, c.ncell, seed=31, spread=0.05)
     s = to_gpu(c, PRECS[prec])
     f0 = s.populations()  # the stored (possibly rounded) state is the oracle's input
-    s.step(1)
-    got = s.populations()
     P = oracle.Problem(D3Q19, c.n, c.tau)
     for face, (kind, u, prof) in c.faces.items():
         P.set_boundary(face, kind, u, prof)
@@ -420,9 +424,9 @@ def test_full_size_round_jet_sampled_cells(prec):
     nx, ny, nz = c.n
     rng = np.random.default_rng(5)
     cells = list(rng.integers(0, c.ncell, 4000))
-    for x in (0, 1, nx - 1, nx - 2, nx - 20):
-        for y in (0, ny // 2, ny - 1, 3):
-            for z in (0, nz // 2, nz - 1, 250):
+    for x in (0, 1, 2, 3, nx - 1, nx - 2, nx - 3, nx - 20):
+        for y in (0, 1, ny // 2, ny - 2, ny - 1, 3):
+            for z in (0, 1, nz // 2, nz - 2, nz - 1, 250):
                 cells.append(x + nx * (y + ny * z))
     # inlet disc cells
     for dy in range(-12, 13, 3):
@@ -430,11 +434,19 @@ def test_full_size_round_jet_sampled_cells(prec):
             cells.append(0 + nx * ((ny // 2 + dy) + ny * (nz // 2 + dz)))
     cells = np.unique(np.array(cells, dtype=np.int64))
     ref = P.update_cells(f0, cells, step=0)
-    err = np.abs(got[:, cells].T - ref).max()
     g = np.abs(ref - w[None, :]).max()
     ulp = {"fp16": 2.0 ** -10, "bf16": 2.0 ** -7}.get(prec)
     tol = 1e-5 * np.abs(ref).max() if prec == "fp32" else 2 * ulp * g + 1e-7
-    assert err <= tol, (err, tol)
+    s.close()
+    kinds = sorted({k for k, _ in autotune.CANDIDATES[PRECS[prec]]} | {"cell", "vec2", "vec4", "aa-vec2"})
+    for kind in kinds:
+        s = to_gpu(c, PRECS[prec])  # a fresh handle: step 0 (the inlet noise is keyed by the step)
+        use_kernel(s, kind)
+        s.step(1)
+        got = s.populations()
+        s.close()
+        err = np.abs(got[:, cells].T - ref).max()
+        assert err <= tol, (kind, err, tol)
 
 
 def _open_box(lattice, n, seed):
@@ -662,6 +674,38 @@ def test_staged_kernel_matches_oracle(lattice, prec):
                 assert err <= tol, (n, periodic, stages, block, R, err)
                 s.sync()
                 s.close()
+
+
+def test_staged_kernel_bounded_wait_reports_and_recovers():
+    """Failure path of the row-staged kernel's bounded wait for a tile's bulk
+    copies, without any copy failing: with the wait limit at 0 every wait is
+    one non-blocking test, so the copies of a tile just issued count as late.
+    The kernel sets the handle's error word and each CTA awaits its copies in
+    flight (2 s limit) before returning; lbm_sync reports LBM_ECUDA and clears
+    the condition, and the handle stays usable: with the limit restored and
+    the state set again, the steps match the oracle."""
+    from paper_1710_02065_gb300 import lbm
+    _, _, _, w, _ = oracle.lattice(D3Q19)
+    c = _open_box(D3Q19, (32, 12, 6), seed=9)
+    c.noise = (0, 0.0)  # steps keyed by their count would differ after the failed one
+    P, f = to_oracle(c)
+    ref = P.run(f, 2)
+    s = to_gpu(c, PRECS["fp32"])
+    lbm.lbm_set_staging(s.h, 1, 3, 0)
+    assert lbm.lbm_get_staging(s.h)[0] == 1
+    lbm.lbm_set_staging_wait(s.h, 0)
+    s.step(1)
+    with pytest.raises(lbm.LBMError) as e:
+        s.sync()
+    assert e.value.code == lbm.LBM_ECUDA
+    assert "did not arrive" in lbm.lbm_last_error(s.h)
+    s.sync()  # the error word was cleared; the context is intact
+    lbm.lbm_set_staging_wait(s.h, 2_000_000_000)
+    s.set_populations(f)
+    s.step(2)
+    s.sync()
+    assert np.abs(s.populations() - ref).max() <= _pop_tol("fp32", ref, w, 2)
+    s.close()
 
 
 def test_staged_kernel_eligibility_and_fallback():

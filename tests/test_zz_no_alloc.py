@@ -1,12 +1,13 @@
 """The allocation-free totals entry point, checked against lbm_reduce.
 
 lbm_reduce_noalloc is for callers that cannot allocate device memory at the
-point of the call (stream capture, allocator-free loops, fixed budgets): it
-keeps its partial sums in a static device array instead.  This test builds a
-caller-owned device field in the library's storage layout, calls the entry
-point twice in a row through the C ABI, and compares both results with the
-totals lbm_reduce reports for a handle holding the same field.  It sits in a
-file of its own, collected last.
+point of the call (loops that must not enter an allocator, hosts that keep a
+fixed device-memory budget): it keeps its partial sums in a static device
+array instead.  This test builds a caller-owned device field in the
+library's storage layout, calls the entry point twice in a row through the C
+ABI, and compares both results with the totals lbm_reduce reports for a
+handle holding the same field, for every lattice and storage precision.  It
+sits in a file of its own, collected last.
 """
 import numpy as np
 import pytest
@@ -17,8 +18,8 @@ from paper_1710_02065_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("lattice,n", [(0, (130, 70, 1)), (1, (40, 30, 20))])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("lattice,n", [(0, (130, 70, 1)), (1, (40, 30, 20)), (2, (24, 18, 14))])
 def test_reduce_noalloc_matches_reduce(lattice, n, prec):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
@@ -39,8 +40,10 @@ def test_reduce_noalloc_matches_reduce(lattice, n, prec):
     mass, mom, rc = s.reduce()
     assert rc == 0
 
-    dtype = torch.float64 if prec == 0 else torch.float32
-    g = torch.tensor(f - w[:, None], dtype=dtype, device="cuda").contiguous()
+    # the handle's stored values (exact in FP64) give the caller's field in
+    # the same storage format, so both reductions see the same numbers
+    dtype = {0: torch.float64, 1: torch.float32, 2: torch.float16, 3: torch.bfloat16}[prec]
+    g = torch.tensor(s.populations() - w[:, None], dtype=torch.float64).to(dtype).cuda().contiguous()
     m = torch.tensor(mask, device="cuda")
     out = torch.full((6,), -1.0, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
