@@ -233,20 +233,24 @@ def recorded_fp64_inst(kernel_key: str):
 FP64_INST_PEAK_G = 625.0
 # Warp-instruction issue limit: 152 SMs x 4 schedulers x 1 warp instruction per cycle at the 2070 MHz
 # maximum SM clock
-ISSUE_PEAK_G = 152 * 4 * 2.070
+def issue_peak_g(sm_mhz=None):
+    """Warp instructions per second the SMs can issue (G/s): 152 SMs x 4
+    schedulers x one warp instruction per cycle at the SM clock sampled during
+    the timed region (the 2070 MHz maximum when no sample exists)."""
+    return 152 * 4 * (sm_mhz or 2070.0) / 1e3
 
 
-def recorded_issue(kernel_key: str):
+def recorded_issue(kernel_key: str, grid: str):
     """Warp instructions per cell from the committed ncu counts, if taken on
-    the current kernel source (else None)."""
+    the current kernel source and on the same grid (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_issue.txt")
     if not os.path.exists(path):
         return None
     src = kernel_source_hash()
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 3 and parts[0] == kernel_key and parts[1] == src:
-            return float(parts[2])
+        if len(parts) >= 4 and parts[0] == kernel_key and parts[1] == src and parts[2] == grid:
+            return float(parts[3])
     return None
 
 
@@ -345,66 +349,100 @@ def e2e_run(lbm, torch, spec, precision, steps, stream):
     return dict(seconds=dt, h2d=(rho.nbytes + u.nbytes) / steps, d2h=(ro.nbytes + uo.nbytes) / steps)
 
 
-def _pprime_compare(runs, checkpoints):
+def _pprime_compare(runs, checkpoints, ref_name):
     out = {}
-    for name in ("fp32", "fp16", "bf16"):
+    for name in runs:
+        if name == ref_name:
+            continue
         out[name] = {}
         for c in checkpoints:
-            ref = runs["fp64"][c]
+            ref = runs[ref_name][c]
             d = runs[name][c] - ref
             scale = np.abs(ref).max()
             out[name][str(c)] = {"max_rel": float(np.abs(d).max() / scale),
                                  "rms_rel": float(np.sqrt(np.mean(d * d)) / scale)}
-    out["max_abs_p64"] = {str(c): float(np.abs(runs["fp64"][c]).max()) for c in checkpoints}
+    out["max_abs_p_ref"] = {str(c): float(np.abs(runs[ref_name][c]).max()) for c in checkpoints}
     return out
 
 
-def pprime_errors(lbm, torch, stream):
-    """Error of p' = c_s^2 (rho - 1) for each storage precision against the
-    FP64 path (whose parity with the FP64 oracle is 1e-12), at several steps:
+def _gpu_pprime(lbm, make, checkpoints):
+    s = make()
+    t, fields = 0, {}
+    for c in checkpoints:
+        lbm.lbm_step(s.h, c - t)
+        t = c
+        rho = np.zeros(s.ncell)
+        lbm.lbm_moments(s.h, rho, None, None)
+        fields[c] = (rho - 1.0) / 3.0
+    s.close()
+    return fields
+
+
+def _oracle_pprime(P, f, checkpoints, threads):
+    t, fields = 0, {}
+    for c in checkpoints:
+        f = P.run(f, c - t, step0=t, threads=threads)
+        t = c
+        rho, _, _ = P.moments(f)
+        fields[c] = (rho - 1.0) / 3.0
+    return fields
+
+
+def pprime_errors(lbm, torch, stream, threads=None):
+    """Error of p' = c_s^2 (rho - 1) for each storage precision against the FP64
+    oracle (the reference, run on `threads` host threads -- bitwise the
+    single-threaded oracle), with the GPU FP64 path as a second column:
       * the round jet scaled to 96x64x64 (D = 6, sponges 8, Ma 0.3) at Re_D
-        1250 with a D/20 shear layer: at Re_D 2500 (the full-size lattice
-        viscosity) this copy leaves the stable range before step 1000, at
-        1250 it runs 5000 steps; late times also measure the decorrelation of
-        an unsteady shear flow, not only storage rounding
-      * the D2Q9 128^2 acoustic pulse (laminar, tau 0.6), 200 steps"""
-    res = {}
+        1250 with a D/20 shear layer, at steps 100, 500, 1000 (at Re_D 2500,
+        the full-size lattice viscosity, this copy leaves the stable range
+        before step 1000); the ambient is at rest, so the default storage
+        shift is the rest state already
+      * the D2Q9 128^2 acoustic pulse (amplitude 1e-3, laminar, tau 0.6) on a
+        mean flow u0 = (0.05, 0), steps 50 and 200; 16-bit storage with the
+        default shift (f - w) and shifted by the mean-flow equilibrium
+        (f - feqH(1, u0), lbm_set_storage_shift)"""
+    threads = threads or os.cpu_count() or 1
+    res = {"oracle_threads": threads}
     spec = jet_spec(Re=1250.0, **SAMPLE_SPEC)
     spec["theta"] = spec["diameter"] / 20.0
-    cps = (100, 500, 1000, 2000, 5000)
+    cps = (100, 500, 1000)
     runs = {}
     for name in ("fp64", "fp32", "fp16", "bf16"):
-        s = configure_gpu(lbm, spec, lbm.PRECISIONS[name], stream.cuda_stream)
-        n = s.ncell
-        s.set_state(np.ones(n), np.zeros((n, 3)))
-        t, fields = 0, {}
-        for c in cps:
-            lbm.lbm_step(s.h, c - t)
-            t = c
-            rho = np.zeros(n)
-            lbm.lbm_moments(s.h, rho, None, None)
-            fields[c] = (rho - 1.0) / 3.0
-        runs[name] = fields
-        s.close()
-    res["jet_96x64x64_Re1250"] = _pprime_compare(runs, cps)
+        def make(name=name):
+            s = configure_gpu(lbm, spec, lbm.PRECISIONS[name], stream.cuda_stream)
+            s.set_state(np.ones(s.ncell), np.zeros((s.ncell, 3)))
+            return s
+        runs[name] = _gpu_pprime(lbm, make, cps)
+    t0 = time.perf_counter()
+    P, f = configure_oracle(spec)
+    runs["oracle"] = _oracle_pprime(P, f, cps, threads)
+    jet_s = time.perf_counter() - t0
+    res["jet_96x64x64_Re1250"] = {
+        "vs_oracle": _pprime_compare(runs, cps, "oracle"),
+        "vs_gpu_fp64": _pprime_compare({k: v for k, v in runs.items() if k != "oracle"}, cps, "fp64"),
+        "oracle_seconds": round(jet_s, 1)}
     from paper_1710_02065_gb300 import inputs
-    rho0, u0 = inputs.gaussian_pulse_2d(128, 1e-3, 6.0, (0.05, 0.0))
+    import oracle
+    u0 = (0.05, 0.0, 0.0)
+    rho0, uu0 = inputs.gaussian_pulse_2d(128, 1e-3, 6.0, u0[:2])
     cps2 = (50, 200)
     runs = {}
-    for name in ("fp64", "fp32", "fp16", "bf16"):
-        s = lbm.Solver(lbm.LBM_D2Q9, (128, 128, 1), 0.6, lbm.PRECISIONS[name], stream=stream.cuda_stream)
-        s.set_state(rho0, u0)
-        t, fields = 0, {}
-        for c in cps2:
-            lbm.lbm_step(s.h, c - t)
-            t = c
-            rho = np.zeros(s.ncell)
-            lbm.lbm_moments(s.h, rho, None, None)
-            fields[c] = (rho - 1.0) / 3.0
-        runs[name] = fields
-        s.close()
-    res["acoustic_pulse_d2q9_128"] = _pprime_compare(runs, cps2)
-    res["reference"] = "GPU FP64 path; errors relative to max |p'_64| at that step"
+    for name, shift in (("fp64", None), ("fp32", None), ("fp16", None), ("bf16", None),
+                        ("fp16_shift_u0", u0), ("bf16_shift_u0", u0)):
+        def make(name=name, shift=shift):
+            s = lbm.Solver(lbm.LBM_D2Q9, (128, 128, 1), 0.6, lbm.PRECISIONS[name[:4]], stream=stream.cuda_stream)
+            if shift is not None:
+                lbm.lbm_set_storage_shift(s.h, shift)
+            s.set_state(rho0, uu0)
+            return s
+        runs[name] = _gpu_pprime(lbm, make, cps2)
+    P = oracle.Problem(oracle.D2Q9, (128, 128), 0.6)
+    runs["oracle"] = _oracle_pprime(P, P.equilibrium(rho0, uu0), cps2, threads)
+    res["acoustic_pulse_d2q9_128_u0.05"] = {
+        "vs_oracle": _pprime_compare(runs, cps2, "oracle"),
+        "vs_gpu_fp64": _pprime_compare({k: v for k, v in runs.items() if k != "oracle"}, cps2, "fp64")}
+    res["reference"] = ("FP64 oracle (vs_oracle) and the GPU FP64 path (vs_gpu_fp64); errors relative to "
+                        "max |p'| of the reference at that step; *_shift_u0: stored as f - feqH(1, u0)")
     return res
 
 
@@ -799,15 +837,18 @@ def main():
             extra[name] = {"launch": r["launch"], "mlups": r["ncell"] / (k_ms / 1e3) / 1e6,
                            "gbs": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9,
                            "frac_of_measured_hbm": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9 / peak}
-            if name in ("fp16", "bf16") and r["launch"]["kernel"] == "vec2":
-                ins = recorded_issue(f"k_stream_collide_vec_d3q19_{name}_jet")
+            if name in ("fp16", "bf16") and r["launch"]["kernel"] == "vec2" and r["launch"]["streaming"] == "pull":
+                ins = recorded_issue(f"k_stream_collide_vec_d3q19_{name}_jet", args.grid.lower())
                 if ins is not None:
                     rate = extra[name]["mlups"] / 1e3  # G cells/s
+                    mhz = (clk or {}).get("sm_mhz")
+                    ipk = issue_peak_g(mhz)
                     extra[name]["roofline"] = {
-                        "bound": "alu", "achieved": rate * ins, "peak": ISSUE_PEAK_G, "unit": "G warp instr/s",
-                        "frac": rate * ins / ISSUE_PEAK_G, "warp_inst_per_cell": ins,
-                        "peak_source": "152 SMs x 4 schedulers x 2.07 GHz (one warp instruction per scheduler "
-                                       "per cycle); counts from profiles/ncu_issue.txt"}
+                        "bound": "alu", "achieved": rate * ins, "peak": ipk, "unit": "G warp instr/s",
+                        "frac": rate * ins / ipk, "warp_inst_per_cell": ins, "sm_mhz": mhz or 2070.0,
+                        "peak_source": "152 SMs x 4 schedulers x the median SM clock sampled during the main "
+                                       "timed region (one warp instruction per scheduler per cycle); counts "
+                                       "from profiles/ncu_issue.txt, taken on this grid"}
             if name == "fp64":
                 kk = "k_stream_collide_vec" if r["launch"]["kernel"].startswith("vec") else "k_stream_collide"
                 ins = recorded_fp64_inst(f"{kk}_d3q19_fp64_jet")
@@ -833,7 +874,7 @@ def main():
             extra["bf16_store_speedup"] = extra["bf16"]["mlups"] / (ncell / (kernel_ms / 1e3) / 1e6)
 
     if run_extra:
-        extra["pprime_error_vs_fp64"] = pprime_errors(lbm, torch, stream)
+        extra["pprime_error"] = pprime_errors(lbm, torch, stream)
         extra["stability_ab"] = stability_ab(lbm, stream)
         from paper_1710_02065_gb300 import inputs as _inp, serving as _srv
         reqs = _inp.serving_requests(96, seed=5, rate_per_s=40.0, steps_scale=0.1)

@@ -392,6 +392,24 @@ int lbm_set_staging(lbm_handle h, int mode, int stages, int block);
 int lbm_get_staging(lbm_handle h, int *active, int *stages, int *block, int *rows_per_tile, int *grid);
 
 /*
+ * lbm_set_storage_shift -- the constant subtracted from the stored
+ * populations.  By default a population is stored as f_i - w_i (the rest
+ * equilibrium at rho = 1); with u_s != 0 it is stored as f_i - feqH_i(1, u_s),
+ * the third-order Hermite equilibrium of Eq. eqH at rho = 1 and the mean flow
+ * u_s.  On a mean flow the stored values are then the acoustic and
+ * non-equilibrium parts only, so the 16-bit formats round p' (Sec. III: the
+ * acoustic pressure on a mean flow) far less; for FP32 / FP64 storage it only
+ * moves the rounding.  u_s = NULL or (0, 0, 0) restores the default.  The
+ * stored field (both lattices) is re-expressed in the new shift on the
+ * device.  The arithmetic is unchanged: a loaded value gets
+ * feqH_i(1, u_s) - w_i added, a stored one subtracted.  Runs on the general
+ * update kernel (the vectorised and row-staged kernels are not used); not with
+ * the AA pattern or refinement patches (LBM_EINVAL); |u_s| < c_s.
+ * Checkpoints record the shift and load only into a handle with the same one.
+ */
+int lbm_set_storage_shift(lbm_handle h, const double u_s[3]);
+
+/*
  * lbm_set_streaming -- streaming pattern of the single level (the update of
  * Eq. optimizedLB is the same with either; Sec. II.A streams post-collision
  * populations along xi_i, and where they are stored between steps is free):

@@ -33,10 +33,14 @@ __device__ __forceinline__ double weight_rt(int i)
 
 // bad (nullable): lowest index of a cell whose rho is not finite and > 0, or
 // (2D) whose u_z is not 0; such cells are still written
+// dsh (nullable, here and below): per-direction storage shift of a handle
+// storing f_i - feqH_i(1, u_s) instead of f_i - w_i, dsh[i] = feqH_i(1, u_s) - w_i;
+// stored value + dsh[i] is the population in the w_i-shifted convention the
+// arithmetic uses.
 template <class L, class S>
 __global__ void k_init_eq(int64_t N, int64_t c0, int64_t n, const double *__restrict__ rho,
                           const double *__restrict__ u, S *__restrict__ f0, S *__restrict__ f1, int order4,
-                          unsigned long long *__restrict__ bad)
+                          unsigned long long *__restrict__ bad, const double *__restrict__ dsh = nullptr)
 {
     using C = typename StoreC<S>::C;  // FP32 arithmetic for FP32/FP16/BF16 storage
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -50,30 +54,40 @@ __global__ void k_init_eq(int64_t N, int64_t c0, int64_t n, const double *__rest
                                                   L::D == 3 ? C(u[3 * t + 2]) : C(0), order4 != 0);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        const S v = Store<S>::from(rebuild<L, C>(k, i));
+        const S v = Store<S>::from(dsh ? rebuild<L, C>(k, i) - C(dsh[i]) : rebuild<L, C>(k, i));
         f0[(int64_t)i * N + cell] = v;
         f1[(int64_t)i * N + cell] = v;
     }
 }
 
-template <class L, class S>
-__global__ void k_set_dir(int64_t N, int64_t c0, int64_t n, int i, const double *__restrict__ src,
-                          S *__restrict__ f0, S *__restrict__ f1)
+// Change of the storage shift of one direction's values in place:
+// stored + delta, delta = dsh_old[i] - dsh_new[i] (rounded once to the storage format)
+template <class S>
+__global__ void k_shift_values(int64_t n, S *__restrict__ f, double delta)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
-    const S v = Store<S>::from(src[t] - weight_rt<L>(i));
+    f[t] = Store<S>::from((double)Store<S>::ld(f + t) + delta);
+}
+
+template <class L, class S>
+__global__ void k_set_dir(int64_t N, int64_t c0, int64_t n, int i, const double *__restrict__ src,
+                          S *__restrict__ f0, S *__restrict__ f1, const double *__restrict__ dsh = nullptr)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const S v = Store<S>::from(src[t] - weight_rt<L>(i) - (dsh ? dsh[i] : 0.0));
     f0[(int64_t)i * N + c0 + t] = v;
     f1[(int64_t)i * N + c0 + t] = v;
 }
 
 template <class L, class S>
 __global__ void k_get_dir(int64_t N, int64_t c0, int64_t n, int i, const S *__restrict__ f,
-                          double *__restrict__ dst)
+                          double *__restrict__ dst, const double *__restrict__ dsh = nullptr)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
-    dst[t] = (double)Store<S>::ld(f + (int64_t)i * N + c0 + t) + weight_rt<L>(i);
+    dst[t] = (double)Store<S>::ld(f + (int64_t)i * N + c0 + t) + (dsh ? dsh[i] : 0.0) + weight_rt<L>(i);
 }
 
 template <class L, class S>
@@ -89,7 +103,7 @@ __device__ __forceinline__ void load_cell_fp64(const S *__restrict__ f, int64_t 
 // as FP64: rho = 1 + dr keeps dr's relative precision.
 template <class L, class S>
 __global__ void k_moments(int64_t N, int64_t c0, int64_t n, const S *__restrict__ f, double *__restrict__ rho,
-                          double *__restrict__ u, double *__restrict__ pn)
+                          double *__restrict__ u, double *__restrict__ pn, const double *__restrict__ dsh = nullptr)
 {
     using C = typename StoreC<S>::C;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -97,7 +111,7 @@ __global__ void k_moments(int64_t N, int64_t c0, int64_t n, const S *__restrict_
     const int64_t cell = c0 + t;
     C g[L::Q];
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell);
+    for (int i = 0; i < L::Q; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell) + (dsh ? C(dsh[i]) : C(0));
     const Mom<C> m = moments<L, C>(g);
     const C r = C(1) + m.dr;
     const C ux = m.jx / r, uy = m.jy / r, uz = L::D == 3 ? m.jz / r : C(0);
@@ -125,7 +139,8 @@ constexpr int RED_BLOCK = 256;
 template <class L, class S>
 __global__ void __launch_bounds__(RED_BLOCK) k_reduce(int64_t N, const S *__restrict__ f,
                                                       const uint8_t *__restrict__ solid,
-                                                      double *__restrict__ partial)
+                                                      double *__restrict__ partial,
+                                                      const double *__restrict__ dsh = nullptr)
 {
     // Per-cell moments in the compute type (FP32 for FP32/FP16/BF16 storage,
     // whose values carry FP32 precision at most; FP64 for FP64 storage), the
@@ -139,7 +154,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(int64_t N, const S *__rest
         if (solid && (solid[cell] & MASK_TYPE)) continue;  // fluid cells only
         C g[L::Q];
 #pragma unroll
-        for (int i = 0; i < L::Q; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell);
+        for (int i = 0; i < L::Q; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell) + (dsh ? C(dsh[i]) : C(0));
         bool finite = true;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) finite = finite && isfinite(g[i]);
@@ -192,7 +207,8 @@ static __global__ void k_reduce_final(int nblocks, const double *__restrict__ pa
 template <class L, class S>
 __global__ void __launch_bounds__(RED_BLOCK) k_force(int nx, int ny, int nz, int px, int py, int pz,
                                                      const S *__restrict__ f, const uint8_t *__restrict__ mask,
-                                                     double *__restrict__ partial)
+                                                     double *__restrict__ partial,
+                                                     const double *__restrict__ dsh = nullptr)
 {
     const int64_t N = (int64_t)nx * ny * nz;
     double acc[3] = {0.0, 0.0, 0.0};
@@ -208,7 +224,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_force(int nx, int ny, int nz, int
             if (pz) Z = Z < 0 ? Z + nz : (Z >= nz ? Z - nz : Z);
             if (X < 0 || X >= nx || Y < 0 || Y >= ny || Z < 0 || Z >= nz) continue;
             if ((mask[X + (int64_t)nx * (Y + (int64_t)ny * Z)] & MASK_TYPE) != MASK_SOLID) continue;
-            const double fi = (double)Store<S>::ld(f + (int64_t)i * N + cell) + weight<L>(i);
+            const double fi = (double)Store<S>::ld(f + (int64_t)i * N + cell) + (dsh ? dsh[i] : 0.0) + weight<L>(i);
             acc[0] += 2.0 * L::cx(i) * fi;
             acc[1] += 2.0 * L::cy(i) * fi;
             acc[2] += 2.0 * L::cz(i) * fi;

@@ -73,6 +73,12 @@ struct lbm_ctx {
     // a local one), else the standard layout
     int pattern = LBM_STREAM_PULL;
     int aa_odd = 0;
+    // storage shift by the equilibrium at (1, shift_u): dsh[i] = feqH_i(1, u) - w_i
+    // (host in FP64, device table dsh_d of q doubles); shifted = false: w_i
+    bool shifted = false;
+    double shift_u[3] = {0, 0, 0};
+    double dsh[27] = {};
+    double *dsh_d = nullptr;
     double jet_ref[7] = {0, 0, 0, 0, 0, 0, 0};  // yc, zc, U_J, D, x0, B, S; D = 0: none
     int order4 = 0;             // D2Q9: optional fourth-order H_xxyy term
     double *rho_acc = nullptr;  // running sum of rho per cell (temporal mean of p), or null
@@ -99,6 +105,11 @@ struct lbm_ctx {
     std::string err;
 };
 
+// Device shift table of a level's storage (null: the w_i shift); only the
+// single level carries one (a shift is not combined with refinement patches)
+struct GridRef;
+static const double *shift_of(const lbm_ctx *h, const GridRef &g);
+
 // View of one level's storage, so state and diagnostics work on either level
 struct GridRef {
     int n[3];
@@ -107,6 +118,11 @@ struct GridRef {
     int *cur;
     const uint8_t *mask;
 };
+
+static const double *shift_of(const lbm_ctx *h, const GridRef &g)
+{
+    return (h->shifted && g.f == h->f) ? h->dsh_d : nullptr;
+}
 
 static GridRef coarse_ref(lbm_ctx *h)
 {
@@ -199,44 +215,45 @@ static unsigned grid1(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 template <class L, class S>
 struct InitEq {
     static cudaError_t run(cudaStream_t st, int64_t N, int64_t c0, int64_t n, const double *rho, const double *u,
-                           void *f0, void *f1, int order4, unsigned long long *bad)
+                           void *f0, void *f1, int order4, unsigned long long *bad, const double *dsh)
     {
-        k_init_eq<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, rho, u, (S *)f0, (S *)f1, order4, bad);
+        k_init_eq<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, rho, u, (S *)f0, (S *)f1, order4, bad, dsh);
         return cudaGetLastError();
     }
 };
 template <class L, class S>
 struct SetDir {
     static cudaError_t run(cudaStream_t st, int64_t N, int64_t c0, int64_t n, int i, const double *src, void *f0,
-                           void *f1)
+                           void *f1, const double *dsh)
     {
-        k_set_dir<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, i, src, (S *)f0, (S *)f1);
+        k_set_dir<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, i, src, (S *)f0, (S *)f1, dsh);
         return cudaGetLastError();
     }
 };
 template <class L, class S>
 struct GetDir {
-    static cudaError_t run(cudaStream_t st, int64_t N, int64_t c0, int64_t n, int i, const void *f, double *dst)
+    static cudaError_t run(cudaStream_t st, int64_t N, int64_t c0, int64_t n, int i, const void *f, double *dst,
+                           const double *dsh)
     {
-        k_get_dir<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, i, (const S *)f, dst);
+        k_get_dir<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, i, (const S *)f, dst, dsh);
         return cudaGetLastError();
     }
 };
 template <class L, class S>
 struct Moments {
     static cudaError_t run(cudaStream_t st, int64_t N, int64_t c0, int64_t n, const void *f, double *rho,
-                           double *u, double *pn)
+                           double *u, double *pn, const double *dsh)
     {
-        k_moments<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, (const S *)f, rho, u, pn);
+        k_moments<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, (const S *)f, rho, u, pn, dsh);
         return cudaGetLastError();
     }
 };
 template <class L, class S>
 struct Reduce {
     static cudaError_t run(cudaStream_t st, int64_t N, const void *f, const uint8_t *solid,
-                           double *partial, int nblocks)
+                           double *partial, int nblocks, const double *dsh)
     {
-        k_reduce<L, S><<<nblocks, RED_BLOCK, 0, st>>>(N, (const S *)f, solid, partial);
+        k_reduce<L, S><<<nblocks, RED_BLOCK, 0, st>>>(N, (const S *)f, solid, partial, dsh);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         k_reduce_final<<<1, 32 * RED_FIELDS, 0, st>>>(nblocks, partial, partial + (int64_t)nblocks * RED_FIELDS);
@@ -246,13 +263,30 @@ struct Reduce {
 template <class L, class S>
 struct Force {
     static cudaError_t run(cudaStream_t st, const int *n, const int *per, const void *f, const uint8_t *mask,
-                           double *partial, int nblocks)
+                           double *partial, int nblocks, const double *dsh)
     {
         k_force<L, S><<<nblocks, RED_BLOCK, 0, st>>>(n[0], n[1], n[2], per[0], per[1], per[2], (const S *)f, mask,
-                                                      partial);
+                                                      partial, dsh);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         k_reduce_final<<<1, 32 * RED_FIELDS, 0, st>>>(nblocks, partial, partial + (int64_t)nblocks * RED_FIELDS);
+        return cudaGetLastError();
+    }
+};
+template <class L, class S>
+struct ShiftValues {
+    static cudaError_t run(cudaStream_t st, int64_t N, int i, void *f, double delta)
+    {
+        k_shift_values<S><<<grid1(N, 256), 256, 0, st>>>(N, (S *)f + (int64_t)i * N, delta);
+        return cudaGetLastError();
+    }
+};
+template <class L, class S>
+struct ShiftTable {
+    // dsh[i] = feqH_i(1, u) - w_i: the w_i-shifted equilibrium of one cell at rho = 1, in FP64
+    static cudaError_t run(cudaStream_t st, const double *one_u, double *dsh)
+    {
+        k_init_eq<L, double><<<1, 1, 0, st>>>(1, 0, 1, one_u, one_u + 1, dsh, dsh, 0, nullptr);
         return cudaGetLastError();
     }
 };
@@ -379,6 +413,7 @@ static void release(lbm_ctx *h)
     if (!h) return;
     if (h->f[0]) cudaFree(h->f[0]);
     if (h->f[1] && h->f[1] != h->f[0]) cudaFree(h->f[1]);
+    if (h->dsh_d) cudaFree(h->dsh_d);
     if (h->solid_d) cudaFree(h->solid_d);
     for (int k = 0; k < 6; ++k)
         if (h->prof_d[k]) cudaFree(h->prof_d[k]);
@@ -781,7 +816,7 @@ static int set_state_grid(lbm_ctx *h, const GridRef &g, const double *rho, const
             e = cudaMemcpyAsync(ud, u + 3 * c0, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess)
             e = dispatch<InitEq>(h->lattice, h->prec, h->stream, N, c0, n, (const double *)rd, (const double *)ud,
-                                 g.f[0], g.f[1], h->order4, h->bad_d);
+                                 g.f[0], g.f[1], h->order4, h->bad_d, shift_of(h, g));
         h->launches += 1;
     }
     unsigned long long bad = ~0ull;
@@ -817,7 +852,7 @@ static int set_pops_grid(lbm_ctx *h, const GridRef &g, const double *f)
                                 cudaMemcpyHostToDevice, h->stream);
             if (e == cudaSuccess)
                 e = dispatch<SetDir>(h->lattice, h->prec, h->stream, N, c0, n, i, (const double *)h->stage_d,
-                                     g.f[0], g.f[1]);
+                                     g.f[0], g.f[1], shift_of(h, g));
             h->launches += 1;
         }
     }
@@ -843,7 +878,8 @@ static int get_pops_grid(lbm_ctx *h, const GridRef &g, double *f)
     for (int i = 0; i < h->q && e == cudaSuccess; ++i) {
         for (int64_t c0 = 0; c0 < N && e == cudaSuccess; c0 += chunk) {
             const int64_t n = std::min(chunk, N - c0);
-            e = dispatch<GetDir>(h->lattice, h->prec, h->stream, N, c0, n, i, (const void *)g.f[*g.cur], h->stage_d);
+            e = dispatch<GetDir>(h->lattice, h->prec, h->stream, N, c0, n, i, (const void *)g.f[*g.cur], h->stage_d,
+                                 shift_of(h, g));
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(f + (size_t)i * N + c0, h->stage_d, sizeof(double) * (size_t)n,
                                     cudaMemcpyDeviceToHost, h->stream);
@@ -934,6 +970,11 @@ static int build_params(lbm_ctx *h, StepParams &p)
         p.jet_ref[4] = h->jet_ref[4];
         p.jet_ref[5] = (std::sqrt(2.0) - 1.0) / (h->jet_ref[6] * h->jet_ref[6]);
     }
+    p.shifted = h->shifted ? 1 : 0;
+    for (int i = 0; i < h->q && h->shifted; ++i) {
+        p.dsh_d[i] = h->dsh[i];
+        p.dsh_f[i] = (float)h->dsh[i];
+    }
     p.sponge_rest = (h->rho_ref == 1.0 && h->u_ref[0] == 0.0 && h->u_ref[1] == 0.0 && h->u_ref[2] == 0.0 &&
                      p.jet_x_layer == INT_MAX)
                         ? 1
@@ -945,10 +986,18 @@ static int build_params(lbm_ctx *h, StepParams &p)
 // Whether the row-staged kernel is asked for (it still runs only where eligible)
 static bool staging_wanted(const lbm_ctx *h)
 {
-    if (h->staging == 0 || h->pattern == LBM_STREAM_AA) return false;
+    if (h->staging == 0 || h->pattern == LBM_STREAM_AA || h->shifted) return false;
     // default: off -- measured on GB300 for the D3Q19 jet (384 x 256 x 256) the
     // register kernels are faster (FP32 43.3 vs 25.9 GLUPS, FP16 48.9 vs 34.9)
     return h->staging == 1;
+}
+
+// Whether the vectorised kernel can update a grid: no cell-type mask, the
+// rrBGK collision, the default storage shift, and sponge layers (if any)
+// relaxing to the rest state through face layers only (its closed form)
+static bool vec_eligible(const StepParams &p)
+{
+    return !p.solid && !p.bgk && !p.shifted && (!p.any_sponge || (p.sponge_rest && !p.radial_on));
 }
 
 // Launch one update of a grid: the row-staged kernel where it is wanted and
@@ -982,7 +1031,7 @@ static cudaError_t launch_update(lbm_ctx *h, const StepParams &p, const void *fi
         }
     }
     int vec = h->vec == 0 ? vec_default(h->lattice, h->prec) : h->vec;
-    if (p.solid || vec == 1 || !vec_supported(h->prec, vec) || p.n[0] % vec != 0) vec = 1;
+    if (!vec_eligible(p) || vec == 1 || !vec_supported(h->prec, vec) || p.n[0] % vec != 0) vec = 1;
     const int block = h->block > 0 ? h->block : block_default(vec);
     h->launches += 1;
     if (vec == 1) return step_general(h, p, fin, fout, block);
@@ -1132,7 +1181,7 @@ static cudaError_t aa_step(lbm_ctx *h, const StepParams &p)
 {
     const bool loc = h->aa_odd != 0;
     int vec = h->vec == 0 ? vec_default(h->lattice, h->prec) : h->vec;
-    if (p.solid || p.bgk || vec == 1 || !vec_supported(h->prec, vec) || p.n[0] % vec != 0) vec = 1;
+    if (!vec_eligible(p) || vec == 1 || !vec_supported(h->prec, vec) || p.n[0] % vec != 0) vec = 1;
     const int block = h->block > 0 ? h->block : block_default(vec);
     h->launches += 1;
     h->aa_odd ^= 1;
@@ -1315,6 +1364,7 @@ extern "C" int lbm_add_refinement_patch(lbm_handle h, const int origin[3], const
     CHECK_HANDLE(h);
     if (h->pattern == LBM_STREAM_AA)
         return fail(h, LBM_EINVAL, "refinement patches need the two-lattice pull pattern (lbm_set_streaming)");
+    if (h->shifted) return fail(h, LBM_EINVAL, "refinement patches need the default storage shift");
     h->cfg_version++;
     if (h->collision != LBM_COLLISION_RR)
         return fail(h, LBM_EINVAL, "refinement patches couple rrBGK levels; select LBM_COLLISION_RR first");
@@ -1389,7 +1439,7 @@ extern "C" int lbm_force(lbm_handle h, int level, double F[3])
         for (int a = 0; a < 3; ++a) per[a] = h->kind[2 * a] == LBM_BC_PERIODIC ? 1 : 0;
     double out[RED_FIELDS];
     cudaError_t e = dispatch<Force>(h->lattice, h->prec, h->stream, (const int *)g.n, (const int *)per,
-                                    (const void *)g.f[*g.cur], g.mask, h->red_d, h->red_blocks);
+                                    (const void *)g.f[*g.cur], g.mask, h->red_d, h->red_blocks, shift_of(h, g));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, h->red_d + (size_t)h->red_blocks * RED_FIELDS, sizeof out, cudaMemcpyDeviceToHost,
                             h->stream);
@@ -1419,7 +1469,7 @@ extern "C" int lbm_force_async(lbm_handle h, int level, double *F_dev)
         if (level == 0)
             for (int a = 0; a < 3; ++a) per[a] = h->kind[2 * a] == LBM_BC_PERIODIC ? 1 : 0;
         e = dispatch<Force>(h->lattice, h->prec, h->stream, (const int *)g.n, (const int *)per,
-                            (const void *)g.f[*g.cur], g.mask, h->red_d, h->red_blocks);
+                            (const void *)g.f[*g.cur], g.mask, h->red_d, h->red_blocks, shift_of(h, g));
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(F_dev, h->red_d + (size_t)h->red_blocks * RED_FIELDS, 3 * sizeof(double),
                                 cudaMemcpyDeviceToDevice, h->stream);
@@ -1638,6 +1688,53 @@ extern "C" int lbm_set_staging(lbm_handle h, int mode, int stages, int block)
     return LBM_OK;
 }
 
+extern "C" int lbm_set_storage_shift(lbm_handle h, const double u_s[3])
+{
+    CHECK_HANDLE(h);
+    const double u[3] = {u_s ? u_s[0] : 0.0, u_s ? u_s[1] : 0.0, (u_s && h->d == 3) ? u_s[2] : 0.0};
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(u[a])) return fail(h, LBM_EINVAL, "u_s[%d] is not finite", a);
+    if (u_s && h->d == 2 && u_s[2] != 0.0) return fail(h, LBM_EINVAL, "2D lattice: u_s[2] must be 0");
+    if (u[0] * u[0] + u[1] * u[1] + u[2] * u[2] >= 1.0 / 3.0)
+        return fail(h, LBM_EINVAL, "|u_s| must be below the lattice sound speed");
+    const bool on = u[0] != 0.0 || u[1] != 0.0 || u[2] != 0.0;
+    if (on && h->pattern == LBM_STREAM_AA)
+        return fail(h, LBM_EINVAL, "a reference-equilibrium storage shift needs the pull pattern");
+    if (on && !h->levels.empty()) return fail(h, LBM_EINVAL, "a storage shift is not combined with refinement");
+    // the new table, from the device's own equilibrium (one cell, rho = 1, u_s)
+    double newd[27] = {};
+    if (on) {
+        if (!h->dsh_d) CUDA_TRY(h, cudaMalloc(&h->dsh_d, sizeof(double) * 27));
+        double *tmp = nullptr;
+        CUDA_TRY(h, cudaMalloc(&tmp, sizeof(double) * (4 + 27)));
+        const double one_u[4] = {1.0, u[0], u[1], u[2]};
+        cudaError_t e = cudaMemcpyAsync(tmp, one_u, sizeof one_u, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = dispatch<ShiftTable>(h->lattice, h->prec, h->stream, (const double *)tmp, tmp + 4);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(newd, tmp + 4, sizeof(double) * h->q, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(tmp);
+        if (e != cudaSuccess) return fail(h, LBM_ECUDA, "storage shift table: %s", cudaGetErrorString(e));
+    }
+    // re-express the stored field (both lattices) in the new shift
+    for (int i = 0; i < h->q; ++i) {
+        const double delta = h->dsh[i] - newd[i];
+        if (delta == 0.0) continue;
+        for (int b = 0; b < 2; ++b) {
+            if (b == 1 && h->f[1] == h->f[0]) break;
+            CUDA_TRY(h, dispatch<ShiftValues>(h->lattice, h->prec, h->stream, h->ncell, i, h->f[b], delta));
+            h->launches += 1;
+        }
+    }
+    for (int i = 0; i < 27; ++i) h->dsh[i] = newd[i];
+    for (int a = 0; a < 3; ++a) h->shift_u[a] = u[a];
+    h->shifted = on;
+    if (on) CUDA_TRY(h, cudaMemcpyAsync(h->dsh_d, h->dsh, sizeof(double) * 27, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->cfg_version++;
+    return LBM_OK;
+}
+
 extern "C" int lbm_set_streaming(lbm_handle h, int pattern)
 {
     CHECK_HANDLE(h);
@@ -1648,6 +1745,8 @@ extern "C" int lbm_set_streaming(lbm_handle h, int pattern)
     if (pattern == LBM_STREAM_AA) {
         if (!h->levels.empty())
             return fail(h, LBM_EINVAL, "the AA pattern is not available with refinement patches");
+        if (h->shifted)
+            return fail(h, LBM_EINVAL, "the AA pattern is not available with a reference-equilibrium storage shift");
         // keep the current lattice, release the other one
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         if (h->cur == 1) std::swap(h->f[0], h->f[1]);
@@ -1761,7 +1860,8 @@ static int moments_grid(lbm_ctx *h, const GridRef &g, double *rho, double *u, do
     cudaError_t e = cudaSuccess;
     for (int64_t c0 = 0; c0 < N && e == cudaSuccess; c0 += chunk) {
         const int64_t n = std::min(chunk, N - c0);
-        e = dispatch<Moments>(h->lattice, h->prec, h->stream, N, c0, n, (const void *)g.f[*g.cur], rd, ud, pd);
+        e = dispatch<Moments>(h->lattice, h->prec, h->stream, N, c0, n, (const void *)g.f[*g.cur], rd, ud, pd,
+                              shift_of(h, g));
         if (e == cudaSuccess && rho)
             e = cudaMemcpyAsync(rho + c0, rd, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess && u)
@@ -1791,7 +1891,7 @@ extern "C" int lbm_reduce(lbm_handle h, double *mass, double momentum[3])
     }
     double out[RED_FIELDS];
     cudaError_t e = dispatch<Reduce>(h->lattice, h->prec, h->stream, h->ncell, (const void *)h->f[h->cur],
-                                     (const uint8_t *)h->solid_d, h->red_d, h->red_blocks);
+                                     (const uint8_t *)h->solid_d, h->red_d, h->red_blocks, (const double *)h->dsh_d);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, h->red_d + (size_t)h->red_blocks * RED_FIELDS, sizeof out,
                             cudaMemcpyDeviceToHost, h->stream);
@@ -1878,6 +1978,7 @@ struct FileHeader {
     int32_t lattice, prec, n[3], nlevels;
     int64_t step;
     int64_t rho_count;
+    double shift_u[3];  // storage shift of the stored values (0: w_i); from version 3
 };
 
 static bool write_all(FILE *fp, const void *p, size_t n) { return std::fwrite(p, 1, n, fp) == n; }
@@ -1892,7 +1993,8 @@ extern "C" int lbm_save(lbm_handle h, const char *path)
     }
     if (!path) return fail(h, LBM_EINVAL, "path is null");
     FileHeader hd{};
-    std::memcpy(hd.magic, "LBMRRv02", 8);
+    std::memcpy(hd.magic, "LBMRRv03", 8);
+    for (int a = 0; a < 3; ++a) hd.shift_u[a] = h->shift_u[a];
     hd.lattice = h->lattice;
     hd.prec = h->prec;
     for (int a = 0; a < 3; ++a) hd.n[a] = h->n[a];
@@ -1941,9 +2043,15 @@ extern "C" int lbm_load(lbm_handle h, const char *path)
     FILE *fp = std::fopen(path, "rb");
     if (!fp) return fail(h, LBM_EIO, "cannot open %s", path);
     FileHeader hd{};
-    if (!read_all(fp, &hd, sizeof hd) || std::memcmp(hd.magic, "LBMRRv02", 8) != 0) {
+    if (!read_all(fp, &hd, sizeof hd) || std::memcmp(hd.magic, "LBMRRv03", 8) != 0) {
         std::fclose(fp);
         return fail(h, LBM_EIO, "%s is not a checkpoint", path);
+    }
+    if (hd.shift_u[0] != h->shift_u[0] || hd.shift_u[1] != h->shift_u[1] || hd.shift_u[2] != h->shift_u[2]) {
+        std::fclose(fp);
+        return fail(h, LBM_EINVAL, "checkpoint stored with storage shift (%g, %g, %g); set it (lbm_set_storage_shift) "
+                                   "before loading",
+                    hd.shift_u[0], hd.shift_u[1], hd.shift_u[2]);
     }
     if (hd.lattice != h->lattice || hd.prec != h->prec || hd.n[0] != h->n[0] || hd.n[1] != h->n[1] ||
         hd.n[2] != h->n[2] || hd.nlevels != nlevels(h)) {

@@ -95,7 +95,27 @@ struct StepParams {
     int ld_off[kMaxQ];
     int st_off[kMaxQ];
     int radial_on;  // the circular / spherical sponge layer is set (radial[4] > 0)
+    // storage shift by a reference equilibrium: stored values are
+    // f_i - feqH_i(1, u_s) instead of f_i - w_i; dsh[i] = feqH_i(1, u_s) - w_i is
+    // added to a loaded value and subtracted before a store (general update
+    // kernels only; 0 / unused when shifted = 0)
+    int shifted;
+    float dsh_f[kMaxQ];
+    double dsh_d[kMaxQ];
 };
+
+template <class C>
+__device__ __forceinline__ C dsh(const StepParams &p, int i);
+template <>
+__device__ __forceinline__ float dsh<float>(const StepParams &p, int i)
+{
+    return p.dsh_f[i];
+}
+template <>
+__device__ __forceinline__ double dsh<double>(const StepParams &p, int i)
+{
+    return p.dsh_d[i];
+}
 
 // Bulk box of a lattice (host): on each axis the coordinates that are neither
 // on a non-periodic face nor inside a sponge layer of that axis.
@@ -402,10 +422,10 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
             const unsigned Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
             const unsigned Z = L::D == 2 ? 0u : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
             const unsigned src = X + nx * Y + nxy * Z;
-            if (i != 0 && (solid[src] & MASK_TYPE) == MASK_SOLID)
-                g[i] = Store<S>::ld((const S *)in[opp<L>(i)] + scell);
-            else
-                g[i] = Store<S>::ld((const S *)in[i] + src);
+            // a bounced population is stored in the opposite direction's array (and shift)
+            const int k = (i != 0 && (solid[src] & MASK_TYPE) == MASK_SOLID) ? opp<L>(i) : i;
+            g[i] = Store<S>::ld((const S *)in[k] + (k == i ? src : scell));
+            if (p.shifted) g[i] += dsh<C>(p, k);
         }
     } else {
 #pragma unroll
@@ -414,6 +434,10 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
             const unsigned Y = L::cy(i) > 0 ? ym : (L::cy(i) < 0 ? yp : sy);
             const unsigned Z = L::D == 2 ? 0u : (L::cz(i) > 0 ? zm : (L::cz(i) < 0 ? zp : sz));
             g[i] = Store<S>::ld((const S *)in[i] + (X + nx * Y + nxy * Z));
+        }
+        if (p.shifted) {
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) g[i] += dsh<C>(p, i);
         }
     }
 
@@ -431,10 +455,14 @@ __device__ __forceinline__ void update_cell(const StepParams &p, const char *con
     else
         rebuild_all<L, C, false>(k, o);
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
+    for (int i = 0; i < L::Q; ++i)
         if (BGK) o[i] = fmac(keep, g[i], o[i]);
-        Store<S>::st((S *)out[i] + cell, o[i]);
+    if (p.shifted) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) o[i] -= dsh<C>(p, i);
     }
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) Store<S>::st((S *)out[i] + cell, o[i]);
 }
 
 // ---------------------------------------------------------------------------

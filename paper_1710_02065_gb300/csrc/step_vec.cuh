@@ -399,22 +399,11 @@ __device__ __forceinline__ bool vec_load(const StepParams &p, const char *in0, i
     return true;
 }
 
-// General collision coefficients as a call (boundary nodes of the vector
-// path, sponge layers with a non-rest reference): kept out of line so that
-// the common path of the vector kernel carries none of its code
-template <class L, class C>
-__device__ __noinline__ Coef<C> coef_general(const StepParams &p, const Mom<C> &m, C chi, int x, int y, int z,
-                                             int inlet)
-{
-    return cell_coefficients<L, C>(p, m, chi, x, y, z, inlet);
-}
-
 // Store the rebuilt populations o[kk][i] of the group's cells k0 .. k0 + G - 1.
 // kPull / kAALocal: direction i's array at the cells themselves (G-wide).
 // kAAPush: o_i of cell x goes to P_opp(i)[x + xi_i]: a G-wide store in the
-// row y + c_y, z + c_z for xi_x = 0; single values for xi_x = +-1, back to
-// P_i[x] where x + xi_x leaves a non-periodic x axis and wrapped around a
-// periodic one.
+// row y + c_y, z + c_z for xi_x = 0; single values for xi_x = +-1, wrapped
+// around a periodic x axis (the AA vector path has no x-face cells).
 template <class L, class S, class C, int V, int G, int SP>
 __device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x0, int k0, const C (&o)[G][L::Q])
 {
@@ -434,7 +423,6 @@ __device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const int j = opp<L>(i);
-        S *own = reinterpret_cast<S *>(bout + (size_t)i * dstride) + k0;
         S *dst = reinterpret_cast<S *>(bout + (size_t)j * dstride +
                                        ((long long)L::cy(i) * nx + (long long)L::cz(i) * nxy) * (long long)sizeof(S)) +
                  k0;
@@ -446,25 +434,21 @@ __device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x
         } else {
 #pragma unroll
             for (int kk = 0; kk < G; ++kk) {
-                const int x = x0 + k0 + kk, xd = x + L::cx(i);
-                if (xd >= 0 && xd < nx)
-                    Store<S>::st(dst + kk + L::cx(i), o[kk][i]);
-                else if (p.periodic[0])
-                    Store<S>::st(dst + kk + (xd < 0 ? nx - 1 - x : -x), o[kk][i]);
-                else
-                    Store<S>::st(own + kk, o[kk][i]);
+                const int xd = x0 + k0 + kk + L::cx(i);
+                const int wrap = xd < 0 ? nx : (xd >= nx ? -nx : 0);  // periodic x only
+                Store<S>::st(dst + kk + L::cx(i) + wrap, o[kk][i]);
             }
         }
     }
 }
 
-// Collide the V cells of a loaded vector and store them.  all_bulk: every cell
-// of the vector is bulk (no sponge, no boundary role), decided by the caller
-// for a whole warp so that the warp runs one code path.  Otherwise the
-// moments of a group's cells are taken first, so that an x-face node can use
-// its neighbour's; interior cells relaxing to a rest-state sponge reference
-// (chi from the per-axis tables, 0 in the bulk) use the closed form of
-// coef_interior, everything else the general coefficients (out of line).
+// Collide the V cells of a loaded vector and store them, one cell at a time
+// (gather, moments, coefficients, rebuild).  all_bulk: every cell of the
+// vector is bulk (no sponge, no boundary role), decided by the caller for a
+// whole warp so that the warp runs one code path; otherwise each cell takes
+// its sponge strength from the per-axis tables (0 in the bulk) and the
+// closed-form coefficients of a rest-state reference.  Cells on a
+// non-periodic x face come out wrong here and are recomputed by the caller.
 template <class L, class S, class C, int V, int G, int SP>
 __device__ __forceinline__ void vec_collide_store(const StepParams &p, char *out0, int x0, int y, int z,
                                                   const VecIn<L, S, C, V> &r, bool all_bulk)
@@ -476,64 +460,27 @@ __device__ __forceinline__ void vec_collide_store(const StepParams &p, char *out
     const C om = C(p.omega);
     const bool bulk_row = y >= p.blo[1] && y < p.bhi[1] && z >= p.blo[2] && z < p.bhi[2];
     const C chirow = bulk_row ? C(0) : chi_row<L, C>(p, y, z);
-    const bool xlo = !p.periodic[0] && x0 == 0, xhi = !p.periodic[0] && x0 + V == nx;
-    // the closed sponge form covers the face layers of a rest-state reference
-    const bool lean = p.sponge_rest && !p.radial_on;
 #pragma unroll
     for (int k0 = 0; k0 < V; k0 += G) {
         C o[G][L::Q];
-        if (all_bulk) {
 #pragma unroll
-            for (int kk = 0; kk < G; ++kk) {
-                C g[L::Q];
-                gather_vec<L, S, C, V, SP>(r, k0 + kk, g);
-                rebuild_all<L, C, false>(coef_interior<L, C, false>(moments_pairs<L, C>(g), om, C(0)), o[kk]);
-            }
-        } else {
-            // moments of the group's cells, and of the x neighbour of a face
-            // cell at the group's edge when that neighbour is in another group
-            Mom<C> m[G];
-#pragma unroll
-            for (int kk = 0; kk < G; ++kk) {
-                C g[L::Q];
-                gather_vec<L, S, C, V, SP>(r, k0 + kk, g);
-                m[kk] = moments_pairs<L, C>(g);
-            }
-#pragma unroll
-            for (int kk = 0; kk < G; ++kk) {
-                const int k = k0 + kk, x = x0 + k;
-                const bool face = (k == 0 && xlo) || (k == V - 1 && xhi);
-                // an x-face node collides the populations streamed into its neighbour
-                Mom<C> mk = m[kk];
-                if (face) {
-                    const int kn = k == 0 ? 1 : V - 2;
-                    if (kn >= k0 && kn < k0 + G) {
-                        mk = m[kn - k0];
-                    } else {
-                        C g[L::Q];
-                        gather_vec<L, S, C, V, SP>(r, kn, g);
-                        mk = moments_pairs<L, C>(g);
-                    }
+        for (int kk = 0; kk < G; ++kk) {
+            C g[L::Q];
+            gather_vec<L, S, C, V, SP>(r, k0 + kk, g);
+            const Mom<C> m = moments_pairs<L, C>(g);
+            Coef<C> cf;
+            if (all_bulk) {
+                cf = coef_interior<L, C, false>(m, om, C(0));
+            } else {
+                const int x = x0 + k0 + kk;
+                C chi = chirow;
+                if (!(x >= p.blo[0] && x < p.bhi[0]) && p.any_sponge) {
+                    const C v = chi_tab<C>(p, x);
+                    chi = v > chi ? v : chi;
                 }
-                const int inlet = !face ? -1 : (k == 0 ? (p.kind[0] != BC_OUTFLOW ? 0 : -1)
-                                                        : (p.kind[1] != BC_OUTFLOW ? 1 : -1));
-                const bool xbulk = x >= p.blo[0] && x < p.bhi[0];
-                C chi = C(0);
-                if (inlet < 0) {
-                    chi = chirow;
-                    if (!xbulk && p.any_sponge) {
-                        const C v = chi_tab<C>(p, x);
-                        chi = v > chi ? v : chi;
-                    }
-                }
-                Coef<C> cf;
-                if (inlet < 0 && lean)
-                    cf = coef_interior<L, C, true>(mk, om, chi);
-                else
-                    cf = coef_general<L, C>(p, mk, inlet < 0 ? chi_cell<L, C>(p, chirow, x, y, z) : C(0), x, y, z,
-                                            inlet);
-                rebuild_all<L, C, false>(cf, o[kk]);
+                cf = coef_interior<L, C, true>(m, om, chi);
             }
+            rebuild_all<L, C, false>(cf, o[kk]);
         }
         vec_store<L, S, C, V, G, SP>(p, bout, x0, k0, o);
     }
@@ -541,7 +488,8 @@ __device__ __forceinline__ void vec_collide_store(const StepParams &p, char *out
 
 // Whether the vector path applies to row (y, z): its y / z neighbour rows do
 // not wrap and it is not on a non-periodic y / z face; for the AA steps its
-// neighbours are not face rows either.
+// neighbours are not face rows either.  The handle's sponge layers relax to
+// the rest state (the vector path's closed form) -- launch_update checks it.
 template <class L, int SP>
 __device__ __forceinline__ bool vec_row(const StepParams &p, int y, int z)
 {
@@ -560,18 +508,31 @@ __device__ __forceinline__ bool vec_row(const StepParams &p, int y, int z)
 // cells one by one with the general update (the same arithmetic).  in / out:
 // per-direction bases of the lattices (one lattice for the AA steps).  Used
 // by the single-lattice kernel and by the batched serving kernel.
+//
+// Nodes on a non-periodic x face take their neighbour's populations and, on
+// a velocity / free-slip / pressure face, the general coefficients; keeping
+// that code out of the vector path keeps the path lean (measured on GB300,
+// D3Q19 FP16 jet: 411 instead of 462-490 instructions per cell).  In the pull
+// pattern the vector path computes a face cell like an interior one and the
+// thread recomputes it afterwards with the general update, which reads the
+// unchanged input lattice.  The in-place AA steps cannot recompute (the
+// inputs are overwritten), so their x-edge threads run the general AA update.
 // ---------------------------------------------------------------------------
 template <class L, class S, class C, int V, int G, int SP = kPull>
 __device__ __forceinline__ void update_vec(const StepParams &p, const char *const *in, char *const *out, int x0,
                                            int y, int z)
 {
-    if (x0 >= p.n[0]) return;  // lanes past the row end
-    if (vec_row<L, SP>(p, y, z)) {
+    const int nx = p.n[0];
+    if (x0 >= nx) return;  // lanes past the row end
+    const bool xedge = !p.periodic[0] && (x0 == 0 || x0 + V == nx);
+    if (vec_row<L, SP>(p, y, z) && (SP == kPull || !xedge)) {
         VecIn<L, S, C, V> r;
         if (!vec_load<L, S, C, V, SP>(p, in[0], x0, y, z, r)) return;
         const bool bulk = y >= p.blo[1] && y < p.bhi[1] && z >= p.blo[2] && z < p.bhi[2] && x0 >= p.blo[0] &&
                           x0 + V <= p.bhi[0];
         vec_collide_store<L, S, C, V, G, SP>(p, out[0], x0, y, z, r, bulk);
+        if (SP == kPull && xedge)
+            update_cell<L, S, C, false, kMaskNone>(p, in, out, x0 == 0 ? 0 : nx - 1, y, z);
         return;
     }
 #pragma unroll 1

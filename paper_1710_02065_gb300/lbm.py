@@ -79,6 +79,7 @@ _sig("lbm_set_sponge_jet_reference", [_h] + [C.c_double] * 7)
 _sig("lbm_get_staging", [_h, _ip, _ip, _ip, _ip, _ip])
 _sig("lbm_set_staging_wait", [_h, C.c_uint64])
 _sig("lbm_set_streaming", [_h, C.c_int])
+_sig("lbm_set_storage_shift", [_h, _dp])
 _sig("lbm_get_streaming", [_h, _ip])
 _sig("lbm_info", [_h, _i64p, _i64p, _dp, _dp])
 _sig("lbm_add_refinement_patch", [_h, _ip, _ip])
@@ -292,6 +293,14 @@ def lbm_set_collision(h, model: int):
 
 def lbm_set_staging(h, mode: int = -1, stages: int = 0, block: int = 0):
     return _check(_lib.lbm_set_staging(h, int(mode), int(stages), int(block)), h)
+
+
+def lbm_set_storage_shift(h, u_s=None):
+    """Store f_i - feqH_i(1, u_s) instead of f_i - w_i (None: the default)."""
+    if u_s is None:
+        return _check(_lib.lbm_set_storage_shift(h, None), h)
+    a = np.ascontiguousarray(u_s, dtype=np.float64)
+    return _check(_lib.lbm_set_storage_shift(h, a.ctypes.data_as(_dp)), h)
 
 
 def lbm_set_streaming(h, pattern: int):

@@ -64,7 +64,7 @@ def test_aa_open_box_and_periodic_axes_match_oracle(lattice, prec):
     _, _, _, w, _ = oracle.lattice(lattice)
     n = (40, 12, 1) if lattice == D2Q9 else (24, 10, 8)
     for periodic in (False, True):
-        c = _open_box(lattice, n, seed=7)
+        c = _open_box(lattice, n, seed=7, rest=True)
         if periodic:
             for face in range(2, 6 if lattice == D3Q19 else 4):
                 c.faces.pop(face, None)

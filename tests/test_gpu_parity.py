@@ -449,9 +449,11 @@ def test_full_size_round_jet_sampled_cells(prec):
         assert err <= tol, (kind, err, tol)
 
 
-def _open_box(lattice, n, seed):
+def _open_box(lattice, n, seed, rest=False):
     """Box without a mask: velocity inflow (profile + noise) on -x, outflow on
-    +x, open or periodic y/z, sponges; random off-equilibrium state."""
+    +x, open or periodic y/z, sponges; random off-equilibrium state.  rest:
+    the sponges relax to the rest state (the vectorised kernel's closed
+    form; a moving reference runs the general kernel)."""
     c = Case("open", lattice, n, 0.56)
     nf = n[1] * n[2]
     prof = np.zeros((nf, 3))
@@ -466,7 +468,7 @@ def _open_box(lattice, n, seed):
         c.faces[2] = (VELOCITY, (0.0, 0.01, 0.0), None)
         c.faces[3] = (OUTFLOW, (0, 0, 0), None)
     c.noise = (9, 0.05)
-    c.rho_ref, c.u_ref = 1.0, (0.01, 0.0, 0.0)
+    c.rho_ref, c.u_ref = 1.0, ((0.0, 0.0, 0.0) if rest else (0.01, 0.0, 0.0))
     return with_random_state(c, seed=seed, spread=0.08)
 
 
@@ -474,13 +476,15 @@ def _open_box(lattice, n, seed):
 @pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
 def test_launch_shapes_match_oracle(lattice, prec):
     """Scalar and vectorised kernels, several block sizes, partial warps
-    (nx/V not a multiple of 32), periodic and open x: all equal the oracle."""
+    (nx/V not a multiple of 32), periodic and open x, sponges relaxing to the
+    rest state (the vectorised kernel) and to a moving state (the general
+    kernel): all equal the oracle."""
     from paper_1710_02065_gb300 import lbm
     _, _, _, w, _ = oracle.lattice(lattice)
     vecs = {"fp64": [1, 2], "fp32": [1, 2, 4], "fp16": [1, 2, 4], "bf16": [1, 2, 4]}[prec]
     sizes = [(40, 12, 1), (136, 7, 1)] if lattice == D2Q9 else [(24, 10, 6), (136, 5, 4)]
-    for n in sizes:
-        c = _open_box(lattice, n, seed=n[0])
+    for n, rest in [(n, r) for n in sizes for r in (True, False)]:
+        c = _open_box(lattice, n, seed=n[0], rest=rest)
         P, f = to_oracle(c)
         ref = P.run(f, 3)
         tol = _pop_tol(prec, ref, w, 3)
@@ -850,15 +854,16 @@ def test_d3q27_all_boundary_rules_match_oracle(prec):
     s.step(3)
     assert np.abs(s.populations() - ref).max() <= tol
     s.close()
-    co = _open_box(D3Q27, (24, 10, 6), seed=31)
-    P, f = to_oracle(co)
-    ref = P.run(f, 3)
-    for kind in ("cell", "vec2"):
-        s = to_gpu(co, PRECS[prec])
-        use_kernel(s, kind)
-        s.step(3)
-        assert np.abs(s.populations() - ref).max() <= _pop_tol(prec, ref, w, 3), kind
-        s.close()
+    for rest in (True, False):
+        co = _open_box(D3Q27, (24, 10, 6), seed=31, rest=rest)
+        P, f = to_oracle(co)
+        ref = P.run(f, 3)
+        for kind in ("cell", "vec2"):
+            s = to_gpu(co, PRECS[prec])
+            use_kernel(s, kind)
+            s.step(3)
+            assert np.abs(s.populations() - ref).max() <= _pop_tol(prec, ref, w, 3), (kind, rest)
+            s.close()
     P.collision = oracle.BGK
     ref = P.run(f, 3)
     s = to_gpu(co, PRECS[prec])

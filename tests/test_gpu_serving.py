@@ -178,3 +178,57 @@ def test_unstable_request_fails_alone(serving):
     st = srv.stats()
     assert st["running"] == 0 and st["bytes_in_use"] == 0  # slot and memory returned
     srv.close()
+
+
+def test_late_arrival_is_bitwise_the_same_as_alone(serving):
+    """Continuous batching: a request submitted after the server has run
+    rounds and after another request has retired (so it is admitted into a
+    running mix, with rebuilt tile lists and a recaptured round) finishes
+    bitwise as when it runs alone."""
+    late = _req(1, 20, 0.64, 45, 2)
+    alone = _run(serving, [late])[0]
+    srv = serving.Server(1 << 30, 16)
+    early = [_req(0, 48, 0.7, 14, 1), _req(1, 16, 0.8, 200, 3), _req(2, 12, 0.6, 120, 1)]
+    ids = []
+    for r in early:
+        rho, u = inputs.request_initial_state(r)
+        ids.append(srv.submit(r, rho, u))
+    # run until the short request has retired while the others still run
+    for _ in range(100):
+        srv.run(7)
+        if srv.poll(ids[0])[0] == 2:
+            break
+    assert srv.poll(ids[0])[0] == 2 and srv.poll(ids[1])[0] == 1
+    srv.result(ids[0], 48 * 48)
+    rho, u = inputs.request_initial_state(late)
+    lid = srv.submit(late, rho, u)
+    got = None
+    for _ in range(1000):
+        srv.run(7)
+        if srv.poll(lid)[0] == 2:
+            got = srv.result(lid, 20 ** 3)
+            break
+    srv.close()
+    assert got is not None and got[2] == 0
+    assert np.array_equal(alone[0], got[0]) and np.array_equal(alone[1], got[1])
+
+
+@pytest.mark.parametrize("lattice,N,prec", [(0, 48, 2), (0, 48, 3), (1, 16, 2), (1, 16, 3)])
+def test_16bit_served_results_match_oracle(serving, lattice, N, prec):
+    """FP16 / BF16 storage in the server against the FP64 oracle: the density
+    error stays within the rounding of the stored shifted populations (one
+    half-ulp of max |f - w| per step and direction, summed over Q)."""
+    r = _req(lattice, N, 0.66, 30, prec)
+    rho_g, u_g, rc = _run(serving, [r])[0]
+    assert rc == 0
+    rho0, u0 = inputs.request_initial_state(r)
+    P = oracle.Problem(lattice, r["extents"], r["tau"])
+    f0 = P.equilibrium(rho0, u0)
+    f = P.run(f0, r["steps"])
+    rho, u, _ = P.moments(f)
+    _, q, _, w, _ = oracle.lattice(lattice)
+    ulp = 2.0 ** -11 if prec == 2 else 2.0 ** -8
+    g = max(np.abs(f - w[:, None]).max(), np.abs(f0 - w[:, None]).max())
+    bound = (r["steps"] + 1) * q * ulp * g
+    assert np.abs(rho_g - rho).max() <= bound
+    assert np.abs(u_g - u).max() <= 2 * bound
