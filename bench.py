@@ -231,8 +231,8 @@ def recorded_fp64_inst(kernel_key: str):
 
 # GB300 FP64: 1.25 TFLOP/s nominal = 625 G FMA instructions/s (no measured FP64 peak is available)
 FP64_INST_PEAK_G = 625.0
-# Warp-instruction issue limit: 152 SMs x 4 schedulers x 1 warp instruction per cycle at the 2070 MHz
-# maximum SM clock
+
+
 def issue_peak_g(sm_mhz=None):
     """Warp instructions per second the SMs can issue (G/s): 152 SMs x 4
     schedulers x one warp instruction per cycle at the SM clock sampled during
@@ -326,27 +326,34 @@ def time_precision(lbm, torch, spec, precision, steps, warmup, pg, stream, tune=
 
 def e2e_run(lbm, torch, spec, precision, steps, stream):
     """Through the public API with host buffers: upload rho, u from pinned
-    memory, advance `steps`, read rho, u back."""
+    memory, advance `steps`, read rho, u back.  FP32 and 16-bit storage move
+    FP32 host arrays (lbm_set_state_f32 / lbm_moments_f32: their populations
+    carry FP32 precision at most), FP64 storage FP64 arrays."""
     s = configure_gpu(lbm, spec, precision, stream.cuda_stream)
     n = s.ncell
-    rho_t = torch.ones(n, dtype=torch.float64).pin_memory()
-    u_t = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
-    rho_o = torch.empty(n, dtype=torch.float64).pin_memory()
-    u_o = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    f32 = precision != lbm.LBM_FP64
+    dt = torch.float32 if f32 else torch.float64
+    rho_t = torch.ones(n, dtype=dt).pin_memory()
+    u_t = torch.zeros((n, 3), dtype=dt).pin_memory()
+    rho_o = torch.empty(n, dtype=dt).pin_memory()
+    u_o = torch.empty((n, 3), dtype=dt).pin_memory()
     rho, u, ro, uo = rho_t.numpy(), u_t.numpy(), rho_o.numpy(), u_o.numpy()
+    up = (lambda: lbm.lbm_set_state_f32(s.h, rho, u)) if f32 else (lambda: s.set_state(rho, u))
+    down = (lambda: lbm.lbm_moments_f32(s.h, ro, uo, None)) if f32 else (lambda: lbm.lbm_moments(s.h, ro, uo, None))
     # one untimed pass to page everything in
-    s.set_state(rho, u)
+    up()
     lbm.lbm_step(s.h, 2)
-    lbm.lbm_moments(s.h, ro, uo, None)
+    down()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s.set_state(rho, u)
+    up()
     lbm.lbm_step(s.h, steps)
-    lbm.lbm_moments(s.h, ro, uo, None)
+    down()
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    dt_s = time.perf_counter() - t0
     s.close()
-    return dict(seconds=dt, h2d=(rho.nbytes + u.nbytes) / steps, d2h=(ro.nbytes + uo.nbytes) / steps)
+    return dict(seconds=dt_s, h2d=(rho.nbytes + u.nbytes) / steps, d2h=(ro.nbytes + uo.nbytes) / steps,
+                host_dtype="fp32" if f32 else "fp64")
 
 
 def _pprime_compare(runs, checkpoints, ref_name):
@@ -693,9 +700,17 @@ def run_serving(lbm, torch, args):
     from paper_1710_02065_gb300 import inputs, serving
     reqs = inputs.serving_requests(args.requests, seed=5, rate_per_s=args.rate, steps_scale=args.steps_scale)
     out = serving.serve(reqs, hbm_budget_bytes=int(args.budget_gb * (1 << 30)), max_slots=256,
-                        steps_per_round=args.round_steps)
+                        steps_per_round=args.round_steps, aa=args.streaming == "aa", tune=not args.no_tune)
     out["workload"] = (f"{args.requests} requests, Poisson arrivals {args.rate}/s, D2Q9 pulses 64^2-1024^2 and "
-                       f"D3Q19 Taylor-Green 32^3-192^3, steps x{args.steps_scale}, FP32/FP16")
+                       f"D3Q19 Taylor-Green 32^3-192^3, steps x{args.steps_scale}, FP32/FP16, "
+                       f"{args.streaming} streaming")
+    peaks = measured_peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
+    if out.get("gpu_gbs"):
+        out["roofline"] = {"bound": "hbm", "achieved": out["gpu_gbs"], "peak": peak, "unit": "GB/s",
+                           "frac": out["gpu_gbs"] / peak, "traffic": None,
+                           "kernel": "k_batched (rounds' graphs incl. the per-domain advance)",
+                           "bytes": "2 Q s per cell update of every request, over the device time of the rounds"}
     out["arrival_rate_note"] = ("default rate 9.7/s = 0.8 x the saturated service rate of this stream "
                                 "(12.1 requests/s: 1.48e12 cell updates at 35.0 G cell updates/s, measured "
                                 "with arrivals at 40/s)")
@@ -758,6 +773,8 @@ def main():
     ap.add_argument("--steps-scale", type=float, default=1.0, help="serving: scale of per-request steps")
     ap.add_argument("--budget-gb", type=float, default=8.0, help="serving: HBM budget for populations")
     ap.add_argument("--round-steps", type=int, default=100, help="serving: steps per batched round")
+    ap.add_argument("--streaming", default="pull", choices=["pull", "aa"],
+                    help="serving: streaming pattern of the requests (aa: one lattice each)")
     ap.add_argument("--lattice", default="d3q19", choices=["d3q19", "d3q27"],
                     help="lattice of the two-level jet workload (the jet benchmark line is D3Q19)")
     ap.add_argument("--grid", default="384x256x256",
@@ -878,7 +895,7 @@ def main():
         extra["stability_ab"] = stability_ab(lbm, stream)
         from paper_1710_02065_gb300 import inputs as _inp, serving as _srv
         reqs = _inp.serving_requests(96, seed=5, rate_per_s=40.0, steps_scale=0.1)
-        sv = _srv.serve(reqs, hbm_budget_bytes=8 << 30, max_slots=256, steps_per_round=50)
+        sv = _srv.serve(reqs, hbm_budget_bytes=8 << 30, max_slots=256, steps_per_round=50, tune=not args.no_tune)
         sv["workload"] = ("serving sample: 96 requests, Poisson 40/s, steps x0.1 (the full stream is "
                           "--workload serving)")
         extra["serving"] = sv
@@ -918,7 +935,8 @@ def main():
                          "kernel_ms": kernel_ms},
             "cpu_baseline": cpu,
             "e2e": ({"value": world * ncell * args.steps / e2e_s / 1e6, "unit": "MLUPS",
-                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]} if e2e else None),
+                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                     "steps": args.steps, "host_dtype": e2e["host_dtype"]} if e2e else None),
             "gpu_launches": main_run["launches"],
             "clocks": clk,
             "stable": main_run["stable"],

@@ -225,6 +225,9 @@ int lbm_set_radial_sponge(lbm_handle h, const double center[3], double r0, doubl
  * unspecified until it is set again.
  */
 int lbm_set_state(lbm_handle h, const double *rho, const double *u);
+/* The same with FP32 host arrays (half the host-link bytes), for FP32 and
+ * 16-bit storage whose populations carry no more than FP32 precision. */
+int lbm_set_state_f32(lbm_handle h, const float *rho, const float *u);
 
 /* lbm_set_populations / lbm_get_populations -- the full stored field as plain
  * FP64 f_i, direction-major, q*ncell doubles (host).  set resets the step
@@ -250,6 +253,9 @@ int lbm_step(lbm_handle h, int64_t n);
  * sum), and returned as FP64.
  */
 int lbm_moments(lbm_handle h, double *rho, double *u, double *pi_neq);
+/* The same with FP32 host arrays (half the host-link bytes; the values are
+ * formed in the compute type and rounded once to FP32). */
+int lbm_moments_f32(lbm_handle h, float *rho, float *u, float *pi_neq);
 
 /*
  * lbm_reduce -- FP64 totals over fluid cells of level 0: *mass = sum rho,
@@ -556,24 +562,42 @@ int lbm_load(lbm_handle h, const char *path);
  * tau, number of steps, storage precision and initial rho, u (Eq. eqH
  * populations).  lbm_server_submit queues it (the initial fields are copied).
  * Each lbm_server_run call is one round: queued requests are admitted in
- * arrival order, first fit, while their two population lattices fit in the
- * HBM budget and a slot is free; then every active request advances by up to
- * `steps` steps in one CUDA-graph replay of batched updates (one persistent
- * launch per (lattice, precision) group, plus a per-request step counter), a
- * request stopping exactly at its own step count; finished requests are
- * retired at the end of the round (rho and u of the final post-collision
- * field kept on the host, device memory returned to the budget).  A request's
- * arithmetic is the single-lattice update's and does not depend on what it
- * is batched with.
+ * arrival order, first fit, while their population lattices (two, or one
+ * with the AA pattern) fit in the HBM budget and a slot is free; then every
+ * active request advances by up to `steps` steps in one CUDA-graph replay of
+ * batched updates (one persistent launch per (lattice, precision) group, plus
+ * a per-request step counter), a request stopping exactly at its own step
+ * count; finished requests are retired behind the round (rho and u of the
+ * final post-collision field copied to pinned host memory, device memory
+ * returned to the budget).  A round is enqueued without waiting for the GPU:
+ * lbm_server_run returns once the round and its admissions and retirements
+ * are on the stream, waiting only while two earlier rounds are still in
+ * flight; a retired request turns LBM_REQ_DONE (or FAILED) when its result
+ * copy has completed, seen by lbm_server_poll.  A request's arithmetic is
+ * the single-lattice update's and does not depend on what it is batched
+ * with.
  *   lbm_server_create : budget in bytes, max_slots concurrent requests, stream
  *                       (NULL: the server creates its own)
- *   lbm_server_run    : *completed (may be NULL) = requests finished this round
+ *   lbm_server_run    : *completed (may be NULL) = requests whose results
+ *                       completed since the previous call
+ *   lbm_server_set_streaming : LBM_STREAM_PULL (default) or LBM_STREAM_AA for
+ *                       requests admitted from now on (one lattice each, so
+ *                       the budget holds twice the cells)
+ *   lbm_server_set_launch : launch shape of the (lattice, precision) group's
+ *                       batched update from the next round on: cells_per_lane
+ *                       1 or 2 (0: 2 for 16-bit and FP64 storage, 1 for FP32;
+ *                       a request with an odd row length takes 1) and
+ *                       warps_per_block 1, 2, 4 or 8 (0: 4).  The arithmetic
+ *                       of a request does not depend on it.
+ *   lbm_server_get_launch : the group's current shape
  *   lbm_server_poll   : state LBM_REQ_* and steps done so far
  *   lbm_server_result : copies rho (ncell) and u (3 ncell) of a finished request
  *                       to host buffers (either may be NULL) and forgets it;
  *                       LBM_EUNSTABLE if the result is not finite
  *   lbm_server_stats  : queue length, running requests, budget in use, total
  *                       cell updates advanced
+ *   lbm_server_gpu_time : device time of all rounds' graphs so far (ms, CUDA
+ *                       events around each replay; waits for the stream)
  * Errors: LBM_EINVAL (bad request, a request larger than the whole budget,
  * unknown id, result of an unfinished request), LBM_ECUDA.
  */
@@ -585,7 +609,7 @@ typedef struct lbm_server *lbm_server_handle;
 #define LBM_REQ_FAILED 3
 
 typedef struct {
-    int lattice;        /* LBM_D2Q9 or LBM_D3Q19 */
+    int lattice;        /* LBM_D2Q9, LBM_D3Q19 or LBM_D3Q27 */
     int precision;      /* LBM_FP64 .. LBM_BF16_SHIFTED */
     int extents[3];     /* extents[2] = 1 for D2Q9 */
     double tau;         /* > 1/2 */
@@ -599,10 +623,14 @@ void lbm_server_destroy(lbm_server_handle s);
 const char *lbm_server_last_error(lbm_server_handle s);
 int lbm_server_submit(lbm_server_handle s, const lbm_request *req, int64_t *id);
 int lbm_server_run(lbm_server_handle s, int64_t steps, int *completed);
+int lbm_server_set_streaming(lbm_server_handle s, int pattern);
+int lbm_server_set_launch(lbm_server_handle s, int lattice, int precision, int cells_per_lane, int warps_per_block);
+int lbm_server_get_launch(lbm_server_handle s, int lattice, int precision, int *cells_per_lane, int *warps_per_block);
 int lbm_server_poll(lbm_server_handle s, int64_t id, int *state, int64_t *steps_done);
 int lbm_server_result(lbm_server_handle s, int64_t id, double *rho, double *u);
 int lbm_server_stats(lbm_server_handle s, int *queued, int *running, size_t *bytes_in_use,
                      int64_t *cell_updates);
+int lbm_server_gpu_time(lbm_server_handle s, double *ms);
 
 /*
  * lbm_reduce_noalloc -- the totals of lbm_reduce for a population field the

@@ -91,3 +91,48 @@ def autotune(handle, precision: int, stream, steps: int = 6, torch=None):
     best = min(times, key=times.get)
     apply(handle, cands[best])
     return best, times
+
+
+# ---------------------------------------------------------------------------
+# Serving engine: launch shape of each (lattice, precision) group's batched
+# update, (cells per lane, warps per block)
+# ---------------------------------------------------------------------------
+SERVER_CANDIDATES = [(1, 2), (1, 4), (1, 8), (2, 2), (2, 4), (2, 8)]
+
+
+def tune_server(kinds, sizes, aa: bool = False, round_steps: int = 20, rounds: int = 3,
+                budget_bytes: int = 8 << 30):
+    """Pick the batched update's launch shape per (lattice, precision) group.
+
+    kinds: (lattice, precision) pairs; sizes: {lattice: [extents, ...]}, one
+    request of each extents per group, the batch the group is timed on (at
+    rest; the update's cost does not depend on the state).  Each candidate
+    runs one warm round and then `rounds` rounds of `round_steps` steps on a
+    temporary server; the rate is cell updates over the device time of those
+    rounds' graphs.  Returns {(lattice, precision): {"cells_per_lane",
+    "warps_per_block", "mlups", "table"}}."""
+    out = {}
+    for lat, prec in kinds:
+        s = lbm.lbm_server_create(budget_bytes, 256, None)
+        try:
+            if aa:
+                lbm.lbm_server_set_streaming(s, lbm.LBM_STREAM_AA)
+            cells = 0
+            for ext in sizes[lat]:
+                lbm.lbm_server_submit(s, lat, prec, ext, 0.6, 1 << 40)
+                cells += int(ext[0]) * int(ext[1]) * int(ext[2])
+            table = {}
+            for v, w in SERVER_CANDIDATES:
+                lbm.lbm_server_set_launch(s, lat, prec, v, w)
+                lbm.lbm_server_run(s, round_steps)
+                t0 = lbm.lbm_server_gpu_time(s)
+                for _ in range(rounds):
+                    lbm.lbm_server_run(s, round_steps)
+                ms = lbm.lbm_server_gpu_time(s) - t0
+                table[f"{v}x{w}"] = cells * round_steps * rounds / (ms / 1e3) / 1e6
+            best = max(table, key=table.get)
+            v, w = (int(t) for t in best.split("x"))
+            out[(lat, prec)] = {"cells_per_lane": v, "warps_per_block": w, "mlups": table[best], "table": table}
+        finally:
+            lbm.lbm_server_destroy(s)
+    return out

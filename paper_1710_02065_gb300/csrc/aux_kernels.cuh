@@ -37,9 +37,10 @@ __device__ __forceinline__ double weight_rt(int i)
 // storing f_i - feqH_i(1, u_s) instead of f_i - w_i, dsh[i] = feqH_i(1, u_s) - w_i;
 // stored value + dsh[i] is the population in the w_i-shifted convention the
 // arithmetic uses.
-template <class L, class S>
-__global__ void k_init_eq(int64_t N, int64_t c0, int64_t n, const double *__restrict__ rho,
-                          const double *__restrict__ u, S *__restrict__ f0, S *__restrict__ f1, int order4,
+// T: the host arrays' type (FP64, or FP32 for the single-precision transfer calls)
+template <class L, class S, class T = double>
+__global__ void k_init_eq(int64_t N, int64_t c0, int64_t n, const T *__restrict__ rho,
+                          const T *__restrict__ u, S *__restrict__ f0, S *__restrict__ f1, int order4,
                           unsigned long long *__restrict__ bad, const double *__restrict__ dsh = nullptr)
 {
     using C = typename StoreC<S>::C;  // FP32 arithmetic for FP32/FP16/BF16 storage
@@ -47,7 +48,7 @@ __global__ void k_init_eq(int64_t N, int64_t c0, int64_t n, const double *__rest
     if (t >= n) return;
     const int64_t cell = c0 + t;
     const double r = rho[t];
-    if (bad && (!(r > 0.0) || !isfinite(r) || (L::D == 2 && u[3 * t + 2] != 0.0)))
+    if (bad && (!(r > 0.0) || !isfinite(r) || (L::D == 2 && u[3 * t + 2] != T(0))))
         atomicMin(bad, (unsigned long long)cell);
     Coef<C> k{};
     add_eq<C, L::D, true, full_third_order<L>()>(k, C(1), C(r - 1.0), C(r), C(u[3 * t]), C(u[3 * t + 1]),
@@ -101,9 +102,9 @@ __device__ __forceinline__ void load_cell_fp64(const S *__restrict__ f, int64_t 
 // Moments in the kernel's compute type (FP32 for FP32/FP16/BF16 storage,
 // whose values carry FP32 precision at most; FP64 for FP64 storage), stored
 // as FP64: rho = 1 + dr keeps dr's relative precision.
-template <class L, class S>
-__global__ void k_moments(int64_t N, int64_t c0, int64_t n, const S *__restrict__ f, double *__restrict__ rho,
-                          double *__restrict__ u, double *__restrict__ pn, const double *__restrict__ dsh = nullptr)
+template <class L, class S, class T = double>
+__global__ void k_moments(int64_t N, int64_t c0, int64_t n, const S *__restrict__ f, T *__restrict__ rho,
+                          T *__restrict__ u, T *__restrict__ pn, const double *__restrict__ dsh = nullptr)
 {
     using C = typename StoreC<S>::C;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -115,7 +116,7 @@ __global__ void k_moments(int64_t N, int64_t c0, int64_t n, const S *__restrict_
     const Mom<C> m = moments<L, C>(g);
     const C r = C(1) + m.dr;
     const C ux = m.jx / r, uy = m.jy / r, uz = L::D == 3 ? m.jz / r : C(0);
-    if (rho) rho[t] = 1.0 + (double)m.dr;
+    if (rho) rho[t] = T(1.0 + (double)m.dr);
     if (u) {
         u[3 * t] = ux;
         u[3 * t + 1] = uy;

@@ -94,14 +94,17 @@ struct lbm_ctx {
     int red_blocks = 0;
     std::vector<uint8_t> user_mask;  // caller's cell types (host copy); empty: none
     std::vector<FineLevel *> levels;  // refined levels 1, 2, ... (each inside the previous one)
-    // graph of two steps (the parity period) replayed by lbm_step; valid for
-    // one configuration version and parity
+    // graphs of 1, 2, 4, 8 or 16 step pairs (the parity period) replayed by
+    // lbm_step, per lattice parity; valid for one configuration version
     int64_t cfg_version = 0;
-    cudaGraphExec_t graph = nullptr;
-    int64_t graph_version = -1;
-    uint64_t graph_sig = 0;  // lattice parities the graph was captured at
-    int64_t graph_launches = 0;
-    int graph_pairs = 0;  // step pairs the graph holds
+    struct StepGraph {
+        uint64_t sig;  // lattice parities the graph was captured at
+        int pairs;     // step pairs it holds
+        cudaGraphExec_t exec;
+        int64_t launches;  // kernel launches per replay
+    };
+    std::vector<StepGraph> graphs;
+    int64_t graphs_version = -1;
     std::string err;
 };
 
@@ -220,6 +223,12 @@ struct InitEq {
         k_init_eq<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, rho, u, (S *)f0, (S *)f1, order4, bad, dsh);
         return cudaGetLastError();
     }
+    static cudaError_t run(cudaStream_t st, int64_t N, int64_t c0, int64_t n, const float *rho, const float *u,
+                           void *f0, void *f1, int order4, unsigned long long *bad, const double *dsh)
+    {
+        k_init_eq<L, S, float><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, rho, u, (S *)f0, (S *)f1, order4, bad, dsh);
+        return cudaGetLastError();
+    }
 };
 template <class L, class S>
 struct SetDir {
@@ -245,6 +254,12 @@ struct Moments {
                            double *u, double *pn, const double *dsh)
     {
         k_moments<L, S><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, (const S *)f, rho, u, pn, dsh);
+        return cudaGetLastError();
+    }
+    static cudaError_t run(cudaStream_t st, int64_t N, int64_t c0, int64_t n, const void *f, float *rho,
+                           float *u, float *pn, const double *dsh)
+    {
+        k_moments<L, S, float><<<grid1(n, 256), 256, 0, st>>>(N, c0, n, (const S *)f, rho, u, pn, dsh);
         return cudaGetLastError();
     }
 };
@@ -424,7 +439,7 @@ static void release(lbm_ctx *h)
     if (h->bad_d) cudaFree(h->bad_d);
     if (h->chi_tab_d) cudaFree(h->chi_tab_d);
     if (h->rho_acc) cudaFree(h->rho_acc);
-    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     for (FineLevel *F : h->levels) {
         for (int k = 0; k < 2; ++k) {
             if (F->f[k]) cudaFree(F->f[k]);
@@ -798,24 +813,25 @@ extern "C" int lbm_set_transfer_staging(lbm_handle h, size_t max_bytes)
 
 static int aa_normalize(lbm_ctx *h);
 
-static int set_state_grid(lbm_ctx *h, const GridRef &g, const double *rho, const double *u)
+template <class T>
+static int set_state_grid(lbm_ctx *h, const GridRef &g, const T *rho, const T *u)
 {
     if (!rho || !u) return fail(h, LBM_EINVAL, "rho and u are required");
     const int64_t N = g.ncell;
     int64_t chunk = 0;
-    int rc = stage(h, N, 4 * sizeof(double), chunk);
+    int rc = stage(h, N, 4 * sizeof(T), chunk);
     if (rc != LBM_OK) return rc;
     if (!h->bad_d) CUDA_TRY(h, cudaMalloc(&h->bad_d, sizeof(unsigned long long)));
     // the values are checked on the device while the field is written
     cudaError_t e = cudaMemsetAsync(h->bad_d, 0xff, sizeof(unsigned long long), h->stream);
-    double *rd = h->stage_d, *ud = h->stage_d + chunk;
+    T *rd = (T *)h->stage_d, *ud = (T *)h->stage_d + chunk;
     for (int64_t c0 = 0; c0 < N && e == cudaSuccess; c0 += chunk) {
         const int64_t n = std::min(chunk, N - c0);
-        e = cudaMemcpyAsync(rd, rho + c0, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+        e = cudaMemcpyAsync(rd, rho + c0, sizeof(T) * (size_t)n, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ud, u + 3 * c0, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+            e = cudaMemcpyAsync(ud, u + 3 * c0, sizeof(T) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess)
-            e = dispatch<InitEq>(h->lattice, h->prec, h->stream, N, c0, n, (const double *)rd, (const double *)ud,
+            e = dispatch<InitEq>(h->lattice, h->prec, h->stream, N, c0, n, (const T *)rd, (const T *)ud,
                                  g.f[0], g.f[1], h->order4, h->bad_d, shift_of(h, g));
         h->launches += 1;
     }
@@ -828,9 +844,9 @@ static int set_state_grid(lbm_ctx *h, const GridRef &g, const double *rho, const
     if (g.f == h->f) h->aa_odd = 0;
     if (bad != ~0ull) {
         const int64_t c = (int64_t)bad;
-        if (!(rho[c] > 0.0) || !std::isfinite(rho[c]))
+        if (!(rho[c] > T(0)) || !std::isfinite((double)rho[c]))
             return fail(h, LBM_EINVAL, "rho[%lld] = %g must be finite and > 0 (the field is unspecified until set again)",
-                        (long long)c, rho[c]);
+                        (long long)c, (double)rho[c]);
         return fail(h, LBM_EINVAL, "2D lattice: u_z must be 0 (cell %lld; the field is unspecified until set again)",
                     (long long)c);
     }
@@ -893,9 +909,19 @@ static int get_pops_grid(lbm_ctx *h, const GridRef &g, double *f)
 
 static int refresh_after_set(lbm_ctx *h, int k);
 static int level_ref(lbm_ctx *h, int level, GridRef &g);
-static int moments_grid(lbm_ctx *h, const GridRef &g, double *rho, double *u, double *pi_neq);
+template <class T>
+static int moments_grid(lbm_ctx *h, const GridRef &g, T *rho, T *u, T *pi_neq);
 
 extern "C" int lbm_set_state(lbm_handle h, const double *rho, const double *u)
+{
+    CHECK_HANDLE(h);
+    int rc = set_state_grid(h, coarse_ref(h), rho, u);
+    if (rc != LBM_OK) return rc;
+    h->step = 0;
+    return refresh_after_set(h, 0);
+}
+
+extern "C" int lbm_set_state_f32(lbm_handle h, const float *rho, const float *u)
 {
     CHECK_HANDLE(h);
     int rc = set_state_grid(h, coarse_ref(h), rho, u);
@@ -1275,15 +1301,12 @@ static uint64_t parity_signature(const lbm_ctx *h)
     return sig;
 }
 
-// Capture two steps into a graph for the current configuration and parity.
-// The host-side counters advanced by the capture are restored: the captured
-// work runs only when the graph is launched.
+// Capture npairs step pairs into a graph for the current configuration and
+// parity, appended to the handle's graphs.  The host-side counters advanced
+// by the capture are restored: the captured work runs only when the graph is
+// launched.
 static int capture_pairs(lbm_ctx *h, std::vector<StepParams> &params, int npairs)
 {
-    if (h->graph) {
-        cudaGraphExecDestroy(h->graph);
-        h->graph = nullptr;
-    }
     const int cur = h->cur, aa_odd = h->aa_odd;
     std::vector<int> fcur, mcur;
     for (FineLevel *F : h->levels) {
@@ -1310,14 +1333,18 @@ static int capture_pairs(lbm_ctx *h, std::vector<StepParams> &params, int npairs
         cudaGetLastError();
         return rc != LBM_OK ? rc : fail(h, LBM_ECUDA, "capturing steps: %s", cudaGetErrorString(e));
     }
-    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, LBM_ECUDA, "instantiating steps: %s", cudaGetErrorString(e));
-    h->graph_version = h->cfg_version;
-    h->graph_sig = sig;
-    h->graph_launches = per_graph;
-    h->graph_pairs = npairs;
+    h->graphs.push_back(lbm_ctx::StepGraph{sig, npairs, exec, per_graph});
     return LBM_OK;
+}
+
+static void drop_graphs(lbm_ctx *h)
+{
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
 }
 
 extern "C" int lbm_step(lbm_handle h, int64_t n)
@@ -1330,28 +1357,41 @@ extern "C" int lbm_step(lbm_handle h, int64_t n)
     if (rc != LBM_OK) return rc;
     for (int k = 1; k < nlevels(h); ++k) fine_params(h, k, params[(size_t)k]);
     // Without inlet noise every step of a pair has the same parameters, so
-    // pairs of steps are replayed from a captured graph (needs a stream other
+    // pairs of steps are replayed from captured graphs (needs a stream other
     // than the legacy default one).  Every refined level returns to the same
-    // lattice parity after two coarse steps.  The graph holds up to
-    // kGraphPairs pairs (as many as one call asks for), so that a call of n
-    // steps costs few graph launches; it is recaptured when the pair count a
-    // call asks for changes.  Steps left over run as direct launches.
-    constexpr int64_t kGraphPairs = 16;
+    // lattice parity after two coarse steps.  The n / 2 pairs of a call run
+    // as replays of a 16-pair graph and at most one graph each of 8, 4, 2
+    // and 1 pairs (the binary digits of the rest), each captured once per
+    // configuration and parity and kept, so calls of varying n reuse them;
+    // only an odd last step runs as direct launches.
+    constexpr int kGraphPairs = 16;
     if (h->stream && h->noise_amp == 0.0 && n >= 2) {
-        const int pairs = (int)std::min<int64_t>(n / 2, kGraphPairs);
-        if (!h->graph || h->graph_version != h->cfg_version || h->graph_sig != parity_signature(h) ||
-            h->graph_pairs != pairs) {
-            rc = capture_pairs(h, params, pairs);
-            if (rc != LBM_OK) return rc;
+        if (h->graphs_version != h->cfg_version || h->graphs.size() > 20) {
+            drop_graphs(h);
+            h->graphs_version = h->cfg_version;
         }
-        const int64_t reps = n / (2 * (int64_t)pairs);
-        for (int64_t k = 0; k < reps; ++k) {
-            cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
-            if (e != cudaSuccess) return fail(h, LBM_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+        const uint64_t sig = parity_signature(h);
+        int64_t pairs_left = n / 2;
+        for (int size = kGraphPairs; size >= 1 && pairs_left > 0; size >>= 1) {
+            const int64_t reps = size == kGraphPairs ? pairs_left / size : (pairs_left >= size ? 1 : 0);
+            if (reps == 0) continue;
+            const lbm_ctx::StepGraph *G = nullptr;
+            for (const auto &g : h->graphs)
+                if (g.sig == sig && g.pairs == size) G = &g;
+            if (!G) {
+                rc = capture_pairs(h, params, size);
+                if (rc != LBM_OK) return rc;
+                G = &h->graphs.back();
+            }
+            for (int64_t k = 0; k < reps; ++k) {
+                cudaError_t e = cudaGraphLaunch(G->exec, h->stream);
+                if (e != cudaSuccess) return fail(h, LBM_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+            }
+            h->step += 2 * (int64_t)size * reps;
+            h->launches += G->launches * reps;
+            pairs_left -= (int64_t)size * reps;
+            n -= 2 * (int64_t)size * reps;
         }
-        h->step += 2 * pairs * reps;
-        h->launches += h->graph_launches * reps;
-        n -= 2 * pairs * reps;
     }
     return enqueue_steps(h, params, n);
 }
@@ -1842,7 +1882,8 @@ extern "C" int lbm_sync(lbm_handle h)
 // ---------------------------------------------------------------------------
 // Diagnostics
 // ---------------------------------------------------------------------------
-static int moments_grid(lbm_ctx *h, const GridRef &g, double *rho, double *u, double *pi_neq)
+template <class T>
+static int moments_grid(lbm_ctx *h, const GridRef &g, T *rho, T *u, T *pi_neq)
 {
     if (g.f == h->f) {
         const int rc0 = aa_normalize(h);
@@ -1850,24 +1891,25 @@ static int moments_grid(lbm_ctx *h, const GridRef &g, double *rho, double *u, do
     }
     if (!rho && !u && !pi_neq) return LBM_OK;
     const int64_t N = g.ncell;
-    const size_t per = sizeof(double) * ((rho ? 1 : 0) + (u ? 3 : 0) + (pi_neq ? 6 : 0));
+    const size_t per = sizeof(T) * ((rho ? 1 : 0) + (u ? 3 : 0) + (pi_neq ? 6 : 0));
     int64_t chunk = 0;
     int rc = stage(h, N, per, chunk);
     if (rc != LBM_OK) return rc;
-    double *rd = rho ? h->stage_d : nullptr;
-    double *ud = u ? h->stage_d + (rho ? chunk : 0) : nullptr;
-    double *pd = pi_neq ? h->stage_d + (rho ? chunk : 0) + (u ? 3 * chunk : 0) : nullptr;
+    T *sd = (T *)h->stage_d;
+    T *rd = rho ? sd : nullptr;
+    T *ud = u ? sd + (rho ? chunk : 0) : nullptr;
+    T *pd = pi_neq ? sd + (rho ? chunk : 0) + (u ? 3 * chunk : 0) : nullptr;
     cudaError_t e = cudaSuccess;
     for (int64_t c0 = 0; c0 < N && e == cudaSuccess; c0 += chunk) {
         const int64_t n = std::min(chunk, N - c0);
         e = dispatch<Moments>(h->lattice, h->prec, h->stream, N, c0, n, (const void *)g.f[*g.cur], rd, ud, pd,
                               shift_of(h, g));
         if (e == cudaSuccess && rho)
-            e = cudaMemcpyAsync(rho + c0, rd, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, h->stream);
+            e = cudaMemcpyAsync(rho + c0, rd, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess && u)
-            e = cudaMemcpyAsync(u + 3 * c0, ud, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, h->stream);
+            e = cudaMemcpyAsync(u + 3 * c0, ud, sizeof(T) * 3 * (size_t)n, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess && pi_neq)
-            e = cudaMemcpyAsync(pi_neq + 6 * c0, pd, sizeof(double) * 6 * (size_t)n, cudaMemcpyDeviceToHost,
+            e = cudaMemcpyAsync(pi_neq + 6 * c0, pd, sizeof(T) * 6 * (size_t)n, cudaMemcpyDeviceToHost,
                                 h->stream);
         h->launches += 1;
     }
@@ -1877,6 +1919,12 @@ static int moments_grid(lbm_ctx *h, const GridRef &g, double *rho, double *u, do
 }
 
 extern "C" int lbm_moments(lbm_handle h, double *rho, double *u, double *pi_neq)
+{
+    CHECK_HANDLE(h);
+    return moments_grid(h, coarse_ref(h), rho, u, pi_neq);
+}
+
+extern "C" int lbm_moments_f32(lbm_handle h, float *rho, float *u, float *pi_neq)
 {
     CHECK_HANDLE(h);
     return moments_grid(h, coarse_ref(h), rho, u, pi_neq);

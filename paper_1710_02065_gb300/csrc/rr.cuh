@@ -793,6 +793,22 @@ __device__ __forceinline__ double u01(uint64_t x)
     return (double)(z >> 11) * (1.0 / 9007199254740992.0);
 }
 
+// The same uniform in a collision precision: double as above, float from
+// the leading 24 bits (u01 rounded down to a float)
+template <class C>
+__device__ __forceinline__ C u01c(uint64_t x);
+template <>
+__device__ __forceinline__ double u01c<double>(uint64_t x) { return u01(x); }
+template <>
+__device__ __forceinline__ float u01c<float>(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return (float)(unsigned)(z >> 40) * (1.0f / 16777216.0f);
+}
+
 // Sponge profile (Sec. II.C): sigma(d) = 3125 (W - d) d^4 / (256 W^5), 0 <= d <= W
 template <class C>
 __device__ __forceinline__ C sigma(C d, C W)

@@ -5,10 +5,11 @@
 // them and every lane updates its cells with the same device functions as
 // the single-lattice kernels (update_cell one cell per lane, update_vec V
 // cells per lane), so a domain's arithmetic does not depend on what it is
-// batched with.  Each domain carries its own step parameters, buffer pair,
-// parity and remaining-step counter; k_batch_advance flips the parity and
-// counts down after every step, and a domain whose counter reaches zero is
-// skipped by later steps of the same captured round.
+// batched with.  Each domain carries its own step parameters, buffer pair
+// (or one lattice with the in-place AA pattern), parity and remaining-step
+// counter; k_batch_advance flips the parity and counts down after every
+// step, and a domain whose counter reaches zero is skipped by later steps of
+// the same captured round.
 #pragma once
 
 #include "step_vec.cuh"
@@ -18,9 +19,10 @@ namespace rr {
 struct BatchDomain {
     StepParams p;
     void *f[2];
-    char *base[2][kMaxQ];  // per-direction base addresses of the two lattices
-    int cur;
+    char *base[2][kMaxQ];  // per-direction base addresses of the two lattices (the same lattice twice for AA)
+    int cur;               // pull: the lattice holding the state; AA: 1 after a gather-push step
     int active;
+    int aa;                // in-place AA streaming (one lattice)
     int64_t remaining;
 };
 
@@ -33,7 +35,7 @@ struct BatchTile {
 };
 
 template <class L, class S, class C, int V>
-__global__ void __launch_bounds__(128) k_batched(const BatchDomain *__restrict__ doms,
+__global__ void __launch_bounds__(256) k_batched(const BatchDomain *__restrict__ doms,
                                                   const BatchTile *__restrict__ tiles, int ntiles)
 {
     const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -44,7 +46,21 @@ __global__ void __launch_bounds__(128) k_batched(const BatchDomain *__restrict__
         const int ny = d.p.n[1];
         const int y = tl.row % ny, z = tl.row / ny;
         const int x0 = (tl.xseg * 32 + lane) * V;
-        if constexpr (V == 1) {
+        if (d.aa) {  // uniform across the warp: one domain per tile
+            if constexpr (V == 1) {
+                if (x0 < d.p.n[0]) {
+                    if (d.cur)
+                        update_cell_aa<L, S, C, false, kMaskNone, true>(d.p, d.base[0], x0, y, z);
+                    else
+                        update_cell_aa<L, S, C, false, kMaskNone, false>(d.p, d.base[0], x0, y, z);
+                }
+            } else {
+                if (d.cur)
+                    update_vec<L, S, C, V, V, kAALocal>(d.p, d.base[0], d.base[0], x0, y, z);
+                else
+                    update_vec<L, S, C, V, V, kAAPush>(d.p, d.base[0], d.base[0], x0, y, z);
+            }
+        } else if constexpr (V == 1) {
             if (x0 < d.p.n[0]) update_cell<L, S, C, false, kMaskNone>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);
         } else {
             update_vec<L, S, C, V, V>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);

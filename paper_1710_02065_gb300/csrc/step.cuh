@@ -222,6 +222,78 @@ __device__ __forceinline__ C chi_cell(const StepParams &p, C row, int x, int y, 
     return row;
 }
 
+// Velocity imposed at node (cx, cy, cz) of velocity face `inlet`: the face
+// value or the per-cell profile, plus the seeded noise (counter-based
+// splitmix64 keyed by seed, step, face cell and component) scaled by |u|,
+// in the collision's precision (for float the uniform keeps its leading 24
+// bits).  One component at a time keeps the 64-bit hash's registers short-lived.
+template <class L, class C>
+__device__ __forceinline__ void face_velocity(const StepParams &p, int inlet, int cx, int cy, int cz, C (&ub)[3])
+{
+    const int a = inlet >> 1;
+    const int t0c = a == 0 ? cy : cx, t1c = a == 2 ? cy : cz;
+    const int n0 = a == 0 ? p.n[1] : p.n[0];
+    const int64_t kf = t0c + (int64_t)n0 * t1c;
+    const double *prof = p.u_profile[inlet];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) ub[b] = C(prof ? prof[3 * kf + b] : p.u_face[inlet][b]);
+    if (p.noise_amp > 0.0) {
+        const C mag = sqrt(ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+        if (mag > C(0)) {
+            const uint64_t base =
+                (p.noise_seed << 32) + ((uint64_t)p.step * (uint64_t)p.face_cells[inlet] + (uint64_t)kf) * 3u;
+            const C amp = C(p.noise_amp) * mag;
+#pragma unroll 1
+            for (int b = 0; b < L::D; ++b) ub[b] += amp * (C(2) * u01c<C>(base + b) - C(1));
+        }
+    }
+}
+
+// Moments m' of a velocity / free-slip / pressure node such that the
+// interior coefficients of m' (coef_interior) are the node's: density rho'
+// and velocity u' as the rule imposes, and the off-equilibrium stress of the
+// neighbour whose streamed moments m are given, Pi^neq about its own rho, u
+// (zeroed normal-tangential components on a free-slip face):
+//   dr' = rho' - 1,  j' = rho' u',  s' = Pi^neq' + dr' c_s^2 I + rho' u' u'.
+template <class L, class C>
+__device__ __forceinline__ Mom<C> face_moments(const StepParams &p, const Mom<C> &m, int inlet, int cx, int cy, int cz)
+{
+    const C rho = C(1) + m.dr;
+    const C inv = recip(rho);
+    C ux = m.jx * inv, uy = m.jy * inv, uz = L::D == 3 ? m.jz * inv : C(0);
+    Sym2<C> pn = pi_neq<C>(m, m.dr, rho, ux, uy, uz, L::D);
+    C dr = m.dr, r = rho;
+    const int kind = p.kind[inlet];
+    if (kind == BC_VELOCITY) {
+        C ub[3];
+        face_velocity<L, C>(p, inlet, cx, cy, cz, ub);
+        ux = ub[0];
+        uy = ub[1];
+        uz = L::D == 3 ? ub[2] : C(0);
+    } else if (kind == BC_PRESSURE) {
+        dr = C(p.rho_face_m1[inlet]);
+        r = C(p.rho_face[inlet]);
+    } else {
+        const int a = inlet >> 1;
+        if (a == 0) { ux = C(0); pn.xy = C(0); pn.xz = C(0); }
+        if (a == 1) { uy = C(0); pn.xy = C(0); pn.yz = C(0); }
+        if (a == 2) { uz = C(0); pn.xz = C(0); pn.yz = C(0); }
+    }
+    Mom<C> o;
+    const C c = dr * C(1.0 / 3.0);
+    o.dr = dr;
+    o.jx = r * ux;
+    o.jy = r * uy;
+    o.jz = r * uz;
+    o.sxx = fmac(o.jx, ux, pn.xx + c);
+    o.syy = fmac(o.jy, uy, pn.yy + c);
+    o.szz = L::D == 3 ? fmac(o.jz, uz, pn.zz + c) : C(0);
+    o.sxy = fmac(o.jx, uy, pn.xy);
+    o.sxz = L::D == 3 ? fmac(o.jx, uz, pn.xz) : C(0);
+    o.syz = L::D == 3 ? fmac(o.jy, uz, pn.yz) : C(0);
+    return o;
+}
+
 // ---------------------------------------------------------------------------
 // Collision coefficients of one cell: velocity node, sponge cell or bulk.
 // BGK = true: the plain LBM-BGK (Eq. standardLB) -- boundary nodes rebuilt to
@@ -261,24 +333,9 @@ __device__ __forceinline__ Coef<C> cell_coefficients(const StepParams &p, const 
         const C rho = C(1) + m.dr;
         const C inv = recip(rho);
         const Sym2<C> pn = pi_neq<C>(m, m.dr, rho, m.jx * inv, m.jy * inv, m.jz * inv, L::D);
-        const int a = inlet >> 1;
-        const int t0c = a == 0 ? cy : cx, t1c = a == 2 ? cy : cz;
-        const int n0 = a == 0 ? p.n[1] : p.n[0];
-        const int64_t kf = t0c + (int64_t)n0 * t1c;
-        double ub[3];
-        const double *prof = p.u_profile[inlet];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) ub[b] = prof ? prof[3 * kf + b] : p.u_face[inlet][b];
-        if (p.noise_amp > 0.0) {
-            const double mag = sqrt(ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
-            if (mag > 0.0) {
-                const uint64_t base =
-                    (p.noise_seed << 32) + ((uint64_t)p.step * (uint64_t)p.face_cells[inlet] + (uint64_t)kf) * 3u;
-#pragma unroll
-                for (int b = 0; b < L::D; ++b) ub[b] += p.noise_amp * mag * (2.0 * u01(base + b) - 1.0);
-            }
-        }
-        const C ux = C(ub[0]), uy = C(ub[1]), uz = L::D == 3 ? C(ub[2]) : C(0);
+        C ub[3];
+        face_velocity<L, C>(p, inlet, cx, cy, cz, ub);
+        const C ux = ub[0], uy = ub[1], uz = L::D == 3 ? ub[2] : C(0);
         add_eq<C, L::D, O3, XYZ>(k, C(1), m.dr, rho, ux, uy, uz, o4);
         add_neq<C, L::D, O3, XYZ>(k, om, ux, uy, uz, pn, o4);
         return k;

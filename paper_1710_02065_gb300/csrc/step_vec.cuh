@@ -403,7 +403,8 @@ __device__ __forceinline__ bool vec_load(const StepParams &p, const char *in0, i
 // kPull / kAALocal: direction i's array at the cells themselves (G-wide).
 // kAAPush: o_i of cell x goes to P_opp(i)[x + xi_i]: a G-wide store in the
 // row y + c_y, z + c_z for xi_x = 0; single values for xi_x = +-1, wrapped
-// around a periodic x axis (the AA vector path has no x-face cells).
+// around a periodic x axis, kept in P_i at the node when they would leave
+// through a non-periodic x face.
 template <class L, class S, class C, int V, int G, int SP>
 __device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x0, int k0, const C (&o)[G][L::Q])
 {
@@ -435,8 +436,14 @@ __device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x
 #pragma unroll
             for (int kk = 0; kk < G; ++kk) {
                 const int xd = x0 + k0 + kk + L::cx(i);
-                const int wrap = xd < 0 ? nx : (xd >= nx ? -nx : 0);  // periodic x only
-                Store<S>::st(dst + kk + L::cx(i) + wrap, o[kk][i]);
+                S *t = dst + kk + L::cx(i);
+                if (xd < 0 || xd >= nx) {
+                    // wrapped around a periodic x axis; out through a
+                    // non-periodic x face: kept in P_i at the node
+                    t = p.periodic[0] ? t + (xd < 0 ? nx : -nx)
+                                      : reinterpret_cast<S *>(bout + (size_t)i * dstride) + k0 + kk;
+                }
+                Store<S>::st(t, o[kk][i]);
             }
         }
     }
@@ -447,8 +454,9 @@ __device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x
 // vector is bulk (no sponge, no boundary role), decided by the caller for a
 // whole warp so that the warp runs one code path; otherwise each cell takes
 // its sponge strength from the per-axis tables (0 in the bulk) and the
-// closed-form coefficients of a rest-state reference.  Cells on a
-// non-periodic x face come out wrong here and are recomputed by the caller.
+// closed-form coefficients of a rest-state reference.  A node on a
+// non-periodic x face collides its neighbour's streamed populations: as they
+// are (outflow face) or with the face's density / velocity substituted.
 template <class L, class S, class C, int V, int G, int SP>
 __device__ __forceinline__ void vec_collide_store(const StepParams &p, char *out0, int x0, int y, int z,
                                                   const VecIn<L, S, C, V> &r, bool all_bulk)
@@ -460,23 +468,41 @@ __device__ __forceinline__ void vec_collide_store(const StepParams &p, char *out
     const C om = C(p.omega);
     const bool bulk_row = y >= p.blo[1] && y < p.bhi[1] && z >= p.blo[2] && z < p.bhi[2];
     const C chirow = bulk_row ? C(0) : chi_row<L, C>(p, y, z);
+    const bool xlo = !p.periodic[0] && x0 == 0, xhi = !p.periodic[0] && x0 + V == nx;
 #pragma unroll
     for (int k0 = 0; k0 < V; k0 += G) {
         C o[G][L::Q];
 #pragma unroll
         for (int kk = 0; kk < G; ++kk) {
+            const int k = k0 + kk;
             C g[L::Q];
-            gather_vec<L, S, C, V, SP>(r, k0 + kk, g);
-            const Mom<C> m = moments_pairs<L, C>(g);
             Coef<C> cf;
             if (all_bulk) {
-                cf = coef_interior<L, C, false>(m, om, C(0));
+                gather_vec<L, S, C, V, SP>(r, k, g);
+                cf = coef_interior<L, C, false>(moments_pairs<L, C>(g), om, C(0));
             } else {
-                const int x = x0 + k0 + kk;
-                C chi = chirow;
-                if (!(x >= p.blo[0] && x < p.bhi[0]) && p.any_sponge) {
-                    const C v = chi_tab<C>(p, x);
-                    chi = v > chi ? v : chi;
+                // a node on a non-periodic x face collides the populations
+                // streamed into its neighbour (same thread), with its own role
+                const bool face = (k == 0 && xlo) || (k == V - 1 && xhi);
+                if (face)
+                    gather_vec<L, S, C, V, SP>(r, k == 0 ? 1 : V - 2, g);
+                else
+                    gather_vec<L, S, C, V, SP>(r, k, g);
+                Mom<C> m = moments_pairs<L, C>(g);
+                const int x = x0 + k;
+                const int inlet = !face ? -1 : (k == 0 ? (p.kind[0] != BC_OUTFLOW ? 0 : -1)
+                                                        : (p.kind[1] != BC_OUTFLOW ? 1 : -1));
+                C chi = C(0);
+                if (inlet >= 0) {
+#ifndef NOFACE
+                    m = face_moments<L, C>(p, m, inlet, x, y, z);
+#endif
+                } else {
+                    chi = chirow;
+                    if (!(x >= p.blo[0] && x < p.bhi[0]) && p.any_sponge) {
+                        const C v = chi_tab<C>(p, x);
+                        chi = v > chi ? v : chi;
+                    }
                 }
                 cf = coef_interior<L, C, true>(m, om, chi);
             }
@@ -509,14 +535,15 @@ __device__ __forceinline__ bool vec_row(const StepParams &p, int y, int z)
 // per-direction bases of the lattices (one lattice for the AA steps).  Used
 // by the single-lattice kernel and by the batched serving kernel.
 //
-// Nodes on a non-periodic x face take their neighbour's populations and, on
-// a velocity / free-slip / pressure face, the general coefficients; keeping
-// that code out of the vector path keeps the path lean (measured on GB300,
-// D3Q19 FP16 jet: 411 instead of 462-490 instructions per cell).  In the pull
-// pattern the vector path computes a face cell like an interior one and the
-// thread recomputes it afterwards with the general update, which reads the
-// unchanged input lattice.  The in-place AA steps cannot recompute (the
-// inputs are overwritten), so their x-edge threads run the general AA update.
+// A node on a non-periodic x face takes the populations streamed into its
+// neighbour, which lives in the same thread; a velocity / free-slip /
+// pressure face node becomes an interior collision of substituted moments
+// (face_moments) -- in the AA steps too, since the neighbour's populations
+// are the thread's own -- so the vector path carries no general-coefficient code:
+// measured on GB300 (D3Q19 FP16 jet), general-update code in the path, even
+// where it ran only for face cells, cost 13-17% of the whole kernel, and
+// updating the face cells in threads or a launch of their own (one cell per
+// row, so every access its own cache sector) cost more.
 // ---------------------------------------------------------------------------
 template <class L, class S, class C, int V, int G, int SP = kPull>
 __device__ __forceinline__ void update_vec(const StepParams &p, const char *const *in, char *const *out, int x0,
@@ -524,15 +551,12 @@ __device__ __forceinline__ void update_vec(const StepParams &p, const char *cons
 {
     const int nx = p.n[0];
     if (x0 >= nx) return;  // lanes past the row end
-    const bool xedge = !p.periodic[0] && (x0 == 0 || x0 + V == nx);
-    if (vec_row<L, SP>(p, y, z) && (SP == kPull || !xedge)) {
+    if (vec_row<L, SP>(p, y, z)) {
         VecIn<L, S, C, V> r;
         if (!vec_load<L, S, C, V, SP>(p, in[0], x0, y, z, r)) return;
         const bool bulk = y >= p.blo[1] && y < p.bhi[1] && z >= p.blo[2] && z < p.bhi[2] && x0 >= p.blo[0] &&
                           x0 + V <= p.bhi[0];
         vec_collide_store<L, S, C, V, G, SP>(p, out[0], x0, y, z, r, bulk);
-        if (SP == kPull && xedge)
-            update_cell<L, S, C, false, kMaskNone>(p, in, out, x0 == 0 ? 0 : nx - 1, y, z);
         return;
     }
 #pragma unroll 1
@@ -563,6 +587,7 @@ struct VecGroup {
 // The kernel: blocks along x rows (blockIdx.y = y, blockIdx.z = z), V cells
 // per thread.  Requires: no cell-type mask, nx % V == 0.
 // ---------------------------------------------------------------------------
+// Grid (x blocks of a row, ny, nz)
 template <class L, class S, class C, int V, int SP>
 __global__ void __launch_bounds__(256, (VecMinBlocks<S, V>::value)) k_stream_collide_vec(const __grid_constant__ StepParams p)
 {

@@ -60,6 +60,8 @@ _sig("lbm_set_pressure", [_h, C.c_int, C.c_double])
 _sig("lbm_set_sponge", [_h, C.c_int, C.c_int, C.c_double, C.c_double, _dp])
 _sig("lbm_set_radial_sponge", [_h, _dp, C.c_double, C.c_double, C.c_double, C.c_double, _dp])
 _sig("lbm_set_state", [_h, _dp, _dp])
+_sig("lbm_set_state_f32", [_h, C.POINTER(C.c_float), C.POINTER(C.c_float)])
+_sig("lbm_moments_f32", [_h, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float)])
 _sig("lbm_set_populations", [_h, _dp])
 _sig("lbm_get_populations", [_h, _dp])
 _sig("lbm_step", [_h, C.c_int64])
@@ -102,6 +104,10 @@ _sig("lbm_server_destroy", [C.c_void_p], None)
 _sig("lbm_server_last_error", [C.c_void_p], C.c_char_p)
 _sig("lbm_server_submit", [C.c_void_p, C.POINTER(lbm_request), _i64p])
 _sig("lbm_server_run", [C.c_void_p, C.c_int64, _ip])
+_sig("lbm_server_set_streaming", [C.c_void_p, C.c_int])
+_sig("lbm_server_set_launch", [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int])
+_sig("lbm_server_get_launch", [C.c_void_p, C.c_int, C.c_int, _ip, _ip])
+_sig("lbm_server_gpu_time", [C.c_void_p, _dp])
 _sig("lbm_server_poll", [C.c_void_p, C.c_int64, _ip, _i64p])
 _sig("lbm_server_result", [C.c_void_p, C.c_int64, _dp, _dp])
 _sig("lbm_server_stats", [C.c_void_p, _ip, _ip, C.POINTER(C.c_size_t), _i64p])
@@ -120,6 +126,9 @@ EXPORTED = [
     "lbm_set_populations_level", "lbm_get_populations_level", "lbm_moments_level",
     "lbm_reduce_noalloc", "lbm_server_create", "lbm_server_destroy", "lbm_server_last_error",
     "lbm_server_submit", "lbm_server_run", "lbm_server_poll", "lbm_server_result", "lbm_server_stats",
+    "lbm_server_set_streaming", "lbm_set_streaming", "lbm_get_streaming", "lbm_set_storage_shift",
+    "lbm_set_staging_wait", "lbm_server_gpu_time", "lbm_set_state_f32", "lbm_moments_f32",
+    "lbm_server_set_launch", "lbm_server_get_launch",
 ]
 LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_DONE, LBM_REQ_FAILED = 0, 1, 2, 3
 
@@ -215,6 +224,28 @@ def lbm_set_state(h, rho, u):
     r = _c64(rho).reshape(-1)
     v = _c64(u).reshape(-1)
     return _check(_lib.lbm_set_state(h, _d(r), _d(v)), h)
+
+
+def _f32p(a):
+    """float* of a C-contiguous float32 numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous float32 array")
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def lbm_set_state_f32(h, rho, u):
+    """lbm_set_state with FP32 host arrays (passed without a copy when they
+    are C-contiguous float32 already, e.g. pinned torch buffers' numpy views)."""
+    r = np.ascontiguousarray(rho, dtype=np.float32).reshape(-1)
+    v = np.ascontiguousarray(u, dtype=np.float32).reshape(-1)
+    return _check(_lib.lbm_set_state_f32(h, _f32p(r), _f32p(v)), h)
+
+
+def lbm_moments_f32(h, rho=None, u=None, pi_neq=None):
+    """lbm_moments into FP32 host arrays (C-contiguous float32 or None)."""
+    return _check(_lib.lbm_moments_f32(h, _f32p(rho), _f32p(u), _f32p(pi_neq)), h)
 
 
 def lbm_set_populations(h, f):
@@ -446,6 +477,31 @@ def lbm_server_submit(s, lattice: int, precision: int, extents, tau: float, step
     rid = C.c_int64()
     _scheck(_lib.lbm_server_submit(s, C.byref(req), C.byref(rid)), s)
     return rid.value
+
+
+def lbm_server_set_streaming(s, pattern: int):
+    """Streaming pattern of the requests admitted from now on."""
+    return _scheck(_lib.lbm_server_set_streaming(s, int(pattern)), s)
+
+
+def lbm_server_set_launch(s, lattice: int, precision: int, cells_per_lane: int, warps_per_block: int):
+    """Launch shape of a (lattice, precision) group's batched update (0, 0: defaults)."""
+    return _scheck(_lib.lbm_server_set_launch(s, int(lattice), int(precision), int(cells_per_lane),
+                                              int(warps_per_block)), s)
+
+
+def lbm_server_get_launch(s, lattice: int, precision: int):
+    """(cells_per_lane, warps_per_block) of a group."""
+    v, w = C.c_int(0), C.c_int(0)
+    _scheck(_lib.lbm_server_get_launch(s, int(lattice), int(precision), C.byref(v), C.byref(w)), s)
+    return v.value, w.value
+
+
+def lbm_server_gpu_time(s) -> float:
+    """Device time (ms) of all rounds so far."""
+    v = C.c_double()
+    _scheck(_lib.lbm_server_gpu_time(s, C.byref(v)), s)
+    return v.value
 
 
 def lbm_server_run(s, steps: int) -> int:

@@ -23,8 +23,14 @@ from . import inputs, lbm
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes: int, max_slots: int = 256, stream: int | None = None):
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 256, stream: int | None = None, aa: bool = False,
+                 launch: dict | None = None):
+        """launch: {(lattice, precision): (cells_per_lane, warps_per_block)}"""
         self.s = lbm.lbm_server_create(hbm_budget_bytes, max_slots, stream)
+        if aa:
+            lbm.lbm_server_set_streaming(self.s, lbm.LBM_STREAM_AA)
+        for (lat, prec), (v, w) in (launch or {}).items():
+            lbm.lbm_server_set_launch(self.s, lat, prec, v, w)
 
     def close(self):
         if self.s:
@@ -92,10 +98,58 @@ class _Client(threading.Thread):
             return p
 
 
+_Q = {lbm.LBM_D2Q9: 9, lbm.LBM_D3Q19: 19, lbm.LBM_D3Q27: 27}
+_BYTES = {lbm.LBM_FP64: 8, lbm.LBM_FP32: 4, lbm.LBM_FP16_SHIFTED: 2, lbm.LBM_BF16_SHIFTED: 2}
+
+
+def algorithmic_bytes(req) -> int:
+    """Populations read and written by a request's updates: 2 Q s per cell update."""
+    return 2 * _Q[req["lattice"]] * _BYTES[req["precision"]] * int(np.prod(req["extents"])) * int(req["steps"])
+
+
+_NAMES = {lbm.LBM_D2Q9: "D2Q9", lbm.LBM_D3Q19: "D3Q19", lbm.LBM_D3Q27: "D3Q27"}
+_PREC = {lbm.LBM_FP64: "fp64", lbm.LBM_FP32: "fp32", lbm.LBM_FP16_SHIFTED: "fp16", lbm.LBM_BF16_SHIFTED: "bf16"}
+
+
+def tune_for(requests, aa: bool = False, budget_bytes: int = 8 << 30):
+    """Launch shapes for the groups of a request stream (autotune.tune_server
+    on one request of each extents the stream holds, per lattice, capped at
+    half the budget per group)."""
+    from . import autotune
+    kinds = sorted({(r["lattice"], r["precision"]) for r in requests})
+    sizes = {}
+    for r in requests:
+        sizes.setdefault(r["lattice"], set()).add(tuple(r["extents"]))
+    sizes = {k: sorted(v, key=lambda e: e[0] * e[1] * e[2]) for k, v in sizes.items()}
+    picked = {}
+    for lat, prec in kinds:
+        keep, total = [], 0
+        for e in sizes[lat]:
+            b = (1 if aa else 2) * _Q[lat] * _BYTES[prec] * e[0] * e[1] * e[2]
+            if total + b <= budget_bytes // 2:
+                keep.append(e)
+                total += b
+        picked.update(autotune.tune_server([(lat, prec)], {lat: keep}, aa=aa, budget_bytes=budget_bytes))
+    return picked
+
+
 def serve(requests, hbm_budget_bytes: int = 8 << 30, max_slots: int = 256, steps_per_round: int = 100,
-          keep_results: bool = False, lookahead_s: float = 2.0, max_ready: int = 16):
-    """Run a request stream to completion; returns a summary dict (and results)."""
-    srv = Server(hbm_budget_bytes, max_slots)
+          keep_results: bool = False, lookahead_s: float = 2.0, max_ready: int = 16, aa: bool = False,
+          tune: bool = False):
+    """Run a request stream to completion; returns a summary dict (and results).
+    aa: serve with the in-place AA pattern (one lattice per request).
+    tune: pick each group's launch shape first (tune_for; not timed)."""
+    tuned = tune_for(requests, aa, hbm_budget_bytes) if tune else {}
+    srv = Server(hbm_budget_bytes, max_slots, aa=aa,
+                 launch={k: (t["cells_per_lane"], t["warps_per_block"]) for k, t in tuned.items()})
+    launch = {}
+    for lat, prec in sorted({(r["lattice"], r["precision"]) for r in requests}):
+        v, w = lbm.lbm_server_get_launch(srv.s, lat, prec)
+        launch[f"{_NAMES[lat]}/{_PREC[prec]}"] = {"cells_per_lane": v, "warps_per_block": w}
+        if (lat, prec) in tuned:
+            launch[f"{_NAMES[lat]}/{_PREC[prec]}"]["tuned_mlups"] = {
+                k: round(x) for k, x in tuned[(lat, prec)]["table"].items()}
+    max_running = 0
     pending = sorted(requests, key=lambda r: r["arrival"])
     inflight = {}  # id -> (request, arrival wall time)
     tts, results, failed = [], {}, 0
@@ -120,6 +174,7 @@ def serve(requests, hbm_budget_bytes: int = 8 << 30, max_slots: int = 256, steps
                     client.cv.wait(0.05 if dt <= 0 else min(0.05, dt))
                 continue
             srv.run(steps_per_round)
+            max_running = max(max_running, srv.stats()["running"])
             for rid in list(inflight):
                 state, _ = srv.poll(rid)
                 if state in (lbm.LBM_REQ_DONE, lbm.LBM_REQ_FAILED):
@@ -137,13 +192,18 @@ def serve(requests, hbm_budget_bytes: int = 8 << 30, max_slots: int = 256, steps
         client.join()
     wall = time.perf_counter() - t0
     cells = srv.stats()["cell_updates"]
+    gpu_s = lbm.lbm_server_gpu_time(srv.s) / 1e3
     srv.close()
+    moved = sum(algorithmic_bytes(r) for r in requests)
     tts = np.array(tts)
     out = {
         "requests": len(requests), "failed": int(failed), "wall_s": wall,
         "aggregate_mlups": cells / wall / 1e6, "cell_updates": int(cells),
         "tts_p50_s": float(np.percentile(tts, 50)), "tts_p99_s": float(np.percentile(tts, 99)),
         "tts_max_s": float(tts.max()), "hbm_budget_bytes": int(hbm_budget_bytes),
-        "steps_per_round": steps_per_round,
+        "steps_per_round": steps_per_round, "streaming": "aa" if aa else "pull",
+        "max_resident_requests": int(max_running), "gpu_busy_s": gpu_s,
+        "algorithmic_bytes": int(moved), "gpu_gbs": moved / gpu_s / 1e9 if gpu_s > 0 else None,
+        "launch": launch,
     }
     return (out, results) if keep_results else out

@@ -56,11 +56,13 @@ def test_aa_every_boundary_rule_matches_oracle(lattice, prec):
     s.close()
 
 
+@pytest.mark.parametrize("kernel", [1, 2, 4])
 @pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
 @pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
-def test_aa_open_box_and_periodic_axes_match_oracle(lattice, prec):
+def test_aa_open_box_and_periodic_axes_match_oracle(lattice, prec, kernel):
     """No cell-type mask: open box with inflow profile and noise, outflow,
-    sponges; and the same box periodic in y / z."""
+    sponges; and the same box periodic in y / z.  One, two and four cells
+    per thread (the vector kernel updates the x-face nodes in registers)."""
     _, _, _, w, _ = oracle.lattice(lattice)
     n = (40, 12, 1) if lattice == D2Q9 else (24, 10, 8)
     for periodic in (False, True):
@@ -71,7 +73,7 @@ def test_aa_open_box_and_periodic_axes_match_oracle(lattice, prec):
             c.sponges = {1: (5, 0.8)}
         P, f = to_oracle(c)
         ref = P.run(f, 5)
-        s = _aa(c, prec)
+        s = _aa(c, prec, kernel)
         s.step(5)
         err = np.abs(s.populations() - ref).max()
         assert err <= _pop_tol(prec, ref, w, 5), (periodic, err)

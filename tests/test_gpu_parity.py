@@ -556,6 +556,13 @@ def test_graph_replay_matches_direct_launches():
     a.step(41)
     assert np.array_equal(a.populations(), b.populations())
     assert a.info()["step"] == b.info()["step"] == 11 + 6 + 82
+    # calls of varying length, odd and even, at both parities: the cached
+    # graphs of 16, 8, 4, 2 and 1 pairs, and direct odd last steps
+    for n in (63, 7, 30, 1, 63, 2, 17):
+        b.step(n)
+    a.step(63 + 7 + 30 + 1 + 63 + 2 + 17)
+    assert np.array_equal(a.populations(), b.populations())
+    assert a.info()["step"] == b.info()["step"] == 11 + 6 + 82 + 183
 
     cj = round_jet(32, 24, 24, diameter=6.0, sponge=6, Re=1000.0, noise=0.0)
     a, b = pair(cj)

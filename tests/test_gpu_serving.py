@@ -232,3 +232,111 @@ def test_16bit_served_results_match_oracle(serving, lattice, N, prec):
     bound = (r["steps"] + 1) * q * ulp * g
     assert np.abs(rho_g - rho).max() <= bound
     assert np.abs(u_g - u).max() <= 2 * bound
+
+
+def _run_aa(serving, reqs, budget=1 << 30, rounds_steps=7):
+    srv = serving.Server(budget, 64, aa=True)
+    ids = []
+    for r in reqs:
+        rho, u = inputs.request_initial_state(r)
+        ids.append(srv.submit(r, rho, u))
+    out = {}
+    for _ in range(10000):
+        srv.run(rounds_steps)
+        for k, rid in enumerate(ids):
+            if k not in out and srv.poll(rid)[0] in (2, 3):
+                out[k] = srv.result(rid, int(np.prod(reqs[k]["extents"])))
+        if len(out) == len(ids):
+            break
+    srv.close()
+    return out
+
+
+@pytest.mark.parametrize("lattice,N,prec,steps,tol,floor", [(0, 32, 0, 41, 1e-12, 1e-13), (1, 12, 0, 40, 1e-12, 1e-13),
+                                                            (1, 16, 1, 33, 1e-5, 1e-8), (2, 12, 1, 20, 1e-5, 1e-8)])
+def test_aa_served_results_match_oracle(serving, lattice, N, prec, steps, tol, floor):
+    """Requests served with the in-place AA pattern (one lattice each), odd and
+    even step counts, batched together: each equals the oracle."""
+    r = _req(lattice, N, 0.66, steps, prec)
+    other = _req(1, 10, 0.8, 17, 2)
+    out = _run_aa(serving, [r, other])
+    rho_g, u_g, rc = out[0]
+    assert rc == 0 and out[1][2] == 0
+    rho0, u0 = inputs.request_initial_state(r)
+    P = oracle.Problem(lattice, r["extents"], r["tau"])
+    rho, u, _ = P.moments(P.run(P.equilibrium(rho0, u0), r["steps"]))
+    assert np.linalg.norm(rho_g - rho) / np.linalg.norm(rho) <= tol
+    du = u_g - u
+    assert np.linalg.norm(du) / np.linalg.norm(u) <= tol or np.abs(du).max() <= floor
+
+
+def test_aa_server_budget_holds_twice_the_cells(serving):
+    """A budget of three lattices holds one pull request (two lattices each)
+    at a time, and all three AA requests (one lattice each)."""
+    big = _req(1, 32, 0.7, 30, 1)
+    budget = int(2 * 19 * 32 ** 3 * 4 * 1.5)
+    for aa, expect in ((False, 1), (True, 3)):
+        srv = serving.Server(budget, 8, aa=aa)
+        ids = []
+        for _ in range(3):
+            rho, u = inputs.request_initial_state(big)
+            ids.append(srv.submit(big, rho, u))
+        srv.run(5)
+        assert [srv.poll(i)[0] for i in ids].count(1) == expect
+        assert srv.stats()["bytes_in_use"] <= budget
+        srv.close()
+
+
+def _run_shape(serving, reqs, launch):
+    srv = serving.Server(1 << 30, 16, launch=launch)
+    ids = []
+    for r in reqs:
+        rho, u = inputs.request_initial_state(r)
+        ids.append(srv.submit(r, rho, u))
+    out = {}
+    for _ in range(1000):
+        srv.run(9)
+        for k, rid in enumerate(ids):
+            if k not in out and srv.poll(rid)[0] in (2, 3):
+                out[k] = srv.result(rid, int(np.prod(reqs[k]["extents"])))
+        if len(out) == len(ids):
+            break
+    srv.close()
+    return out
+
+
+def test_launch_shape_does_not_change_results(serving):
+    """Every candidate launch shape of the batched update (cells per lane,
+    warps per block) gives each request bitwise the result of the default
+    shape, for 16-bit, FP32 and FP64 storage, 2D and 3D."""
+    from paper_1710_02065_gb300 import autotune
+    reqs = [_req(0, 64, 0.61, 23, 1), _req(1, 16, 0.7, 21, 2), _req(0, 32, 0.8, 19, 3), _req(1, 12, 0.66, 17, 0)]
+    ref = _run_shape(serving, reqs, None)
+    kinds = {(r["lattice"], r["precision"]) for r in reqs}
+    for v, w in autotune.SERVER_CANDIDATES:
+        got = _run_shape(serving, reqs, {k: (v, w) for k in kinds})
+        for k in range(len(reqs)):
+            assert got[k][2] == 0
+            assert np.array_equal(ref[k][0], got[k][0]) and np.array_equal(ref[k][1], got[k][1]), (v, w, k)
+
+
+def test_server_tuner_picks_a_candidate(serving):
+    from paper_1710_02065_gb300 import autotune, lbm
+    picks = autotune.tune_server([(0, 2), (1, 1)], {0: [(64, 64, 1), (128, 128, 1)], 1: [(16, 16, 16), (24, 24, 24)]},
+                                 round_steps=4, rounds=1, budget_bytes=1 << 28)
+    assert set(picks) == {(0, 2), (1, 1)}
+    for p in picks.values():
+        assert (p["cells_per_lane"], p["warps_per_block"]) in autotune.SERVER_CANDIDATES
+        assert len(p["table"]) == len(autotune.SERVER_CANDIDATES) and p["mlups"] > 0
+    s = lbm.lbm_server_create(1 << 20, 4, None)
+    try:
+        assert lbm.lbm_server_get_launch(s, 1, 1) == (1, 4)
+        assert lbm.lbm_server_get_launch(s, 1, 2) == (2, 4)
+        lbm.lbm_server_set_launch(s, 1, 2, 1, 8)
+        assert lbm.lbm_server_get_launch(s, 1, 2) == (1, 8)
+        with pytest.raises(lbm.LBMError):
+            lbm.lbm_server_set_launch(s, 1, 2, 3, 4)
+        with pytest.raises(lbm.LBMError):
+            lbm.lbm_server_set_launch(s, 1, 2, 1, 16)
+    finally:
+        lbm.lbm_server_destroy(s)
