@@ -578,6 +578,7 @@ def run_cylinder_two_level(lbm, torch, args):
     rho, u = inputs.uniform_flow_perturbed(nxc, nyc, U, 2)
     s.set_state(rho, u)
     X0, Y0, Wc, Hc = 160, 120, 320, 160
+    lbm.lbm_set_level_streams(s.h, args.level_streams)
     lbm.lbm_add_refinement_patch(s.h, (X0, Y0, 0), (Wc, Hc, 1))
     nfx, nfy = 2 * Wc + 1, 2 * Hc + 1
     solid_f = inputs.cylinder_mask(nfx, nfy, 2 * (200 - X0), 2 * (200 - Y0), Df)
@@ -625,6 +626,7 @@ def run_cylinder_three_level(lbm, torch, args):
     rho, u = inputs.uniform_flow_perturbed(nxc, nyc, U, 2)
     s.set_state(rho, u)
     patches = [((40, 50, 0), (200, 100, 1)), ((60, 40, 0), (200, 120, 1))]
+    lbm.lbm_set_level_streams(s.h, args.level_streams)
     for o, e in patches:
         lbm.lbm_add_refinement_patch(s.h, o, e)
     ext1, _ = lbm.lbm_level_info(s.h, 1)
@@ -665,6 +667,7 @@ def run_jet_two_level(lbm, torch, args):
     spec["lattice"] = {"d3q19": lbm.LBM_D3Q19, "d3q27": lbm.LBM_D3Q27}[args.lattice]
     stream = torch.cuda.Stream()
     s = configure_gpu(lbm, spec, lbm.PRECISIONS[args.precision], stream.cuda_stream)
+    lbm.lbm_set_level_streams(s.h, args.level_streams)
     n = s.ncell
     X0, Y0, Z0, W = 2, 96, 96, 64
     lbm.lbm_add_refinement_patch(s.h, (X0, Y0, Z0), (W, W, W))
@@ -693,6 +696,7 @@ def run_jet_two_level(lbm, torch, args):
                         f"{args.precision}", "metric": "cell updates per second (coarse + 2 x fine per coarse step)",
             "mlups": cells * args.steps / (ms / 1e3) / 1e6, "ms_per_coarse_step": ms / args.steps,
             "coarse_steps": args.steps, "launches_per_coarse_step": launches / args.steps,
+            "level_streams": "concurrent" if args.level_streams else "in order",
             "tau_c": spec["tau"], "tau_f": tau_f, "stable": rc == 0 and bool(np.isfinite(rf).all())}
 
 
@@ -775,6 +779,9 @@ def main():
     ap.add_argument("--round-steps", type=int, default=100, help="serving: steps per batched round")
     ap.add_argument("--streaming", default="pull", choices=["pull", "aa"],
                     help="serving: streaming pattern of the requests (aa: one lattice each)")
+    ap.add_argument("--level-streams", type=int, default=1, choices=[0, 1],
+                    help="refined workloads: 1 runs the refined levels concurrently with the level-0 update "
+                         "(lbm_set_level_streams), 0 in order on one stream")
     ap.add_argument("--lattice", default="d3q19", choices=["d3q19", "d3q27"],
                     help="lattice of the two-level jet workload (the jet benchmark line is D3Q19)")
     ap.add_argument("--grid", default="384x256x256",

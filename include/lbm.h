@@ -543,6 +543,20 @@ int lbm_get_populations_level(lbm_handle h, int level, double *f);
 int lbm_moments_level(lbm_handle h, int level, double *rho, double *u, double *pi_neq);
 
 /*
+ * lbm_set_level_streams -- how the refined levels' part of a step is
+ * scheduled (Sec. II.B: within one coarse step the fine levels read the
+ * coarse interface moments, not the coarse update).
+ *   concurrent = 1 (default): the levels below level 0 (their updates, ring
+ *                fills and the restriction into level 0's covered ring) run
+ *                on a second stream of the highest priority, concurrently
+ *                with the level-0 update; the handle's stream waits for them
+ *                at the end of each step.
+ *   concurrent = 0: everything in order on the handle's stream.
+ * The results are bitwise the same.  Errors: LBM_EINVAL (other values).
+ */
+int lbm_set_level_streams(lbm_handle h, int concurrent);
+
+/*
  * lbm_save / lbm_load -- checkpoint and resume: write / read the stored
  * field of every level (raw storage format), the refined levels' interface
  * moments at the current time, the pressure-mean accumulator (if sampled)
@@ -659,9 +673,9 @@ int lbm_server_gpu_time(lbm_server_handle s, double *ms);
  *               unstable cells (non-finite, rho <= 0 or |u| >= c_s)]
  *   cuda_stream : stream to enqueue on (NULL: legacy default stream)
  * Asynchronous: synchronise the stream before reading out.  The first call on
- * a device looks up the scratch array's device address (once per device,
- * with that device current); make that first call before any stream capture
- * begins.  Every call reuses the same scratch, so calls that overlap on the
+ * a device looks up the scratch array's device address on the host (once per
+ * device, with that device current).  Every call reuses the same scratch, so
+ * calls that overlap on the
  * GPU (other streams, other host threads) race; each call overwrites all the
  * scratch it reads, so nothing needs clearing between calls.  Errors are
  * reported by lbm_last_error(NULL).

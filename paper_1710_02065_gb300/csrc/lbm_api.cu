@@ -41,6 +41,11 @@ struct lbm_ctx {
     size_t elem = 0;
     double tau = 0.0, Ma_ref = 0.0;
     cudaStream_t stream = nullptr;
+    // refined levels beneath level 0 run on a second stream of higher
+    // priority, concurrent with the level-0 update (fork / join events)
+    int level_overlap = 1;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     void *f[2] = {nullptr, nullptr};
     int cur = 0;
     uint8_t *solid_d = nullptr;
@@ -440,6 +445,12 @@ static void release(lbm_ctx *h)
     if (h->chi_tab_d) cudaFree(h->chi_tab_d);
     if (h->rho_acc) cudaFree(h->rho_acc);
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
     for (FineLevel *F : h->levels) {
         for (int k = 0; k < 2; ++k) {
             if (F->f[k]) cudaFree(F->f[k]);
@@ -1251,23 +1262,26 @@ static int aa_normalize(lbm_ctx *h)
     return LBM_OK;
 }
 
-// One step of level k (Sec. II.B applied level by level): the interface
-// moments of its child at t + 1 from the pre-step field, its own update, then
-// two steps of the child with the child's ring refilled at t + 1/2 and t + 1,
-// and the covered ring of level k rebuilt from the child at t + 1/2.
-static cudaError_t advance_level(lbm_ctx *h, std::vector<StepParams> &params, int k, int64_t step)
+// The second stream and the fork / join events of the level overlap
+static cudaError_t ensure_side_stream(lbm_ctx *h)
 {
-    const bool child = k < (int)h->levels.size();
-    cudaError_t e = cudaSuccess;
-    if (child) e = refine_stage(h, k + 1, 0);
-    GridRef g = level_grid(h, k);
-    params[k].step = step;
-    const bool aa = k == 0 && h->pattern == LBM_STREAM_AA;
-    if (e == cudaSuccess) e = aa ? aa_step(h, params[k]) : launch_update(h, params[k], g.f[*g.cur], g.f[1 - *g.cur]);
-    if (e != cudaSuccess) return e;
-    if (!aa) *g.cur = 1 - *g.cur;
-    if (!child) return cudaSuccess;
-    e = advance_level(h, params, k + 1, 2 * step);
+    if (h->side) return cudaSuccess;
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming);
+    return e;
+}
+
+static cudaError_t advance_level(lbm_ctx *h, std::vector<StepParams> &params, int k, int64_t step);
+
+// The child's part of a step of level k: two steps of level k + 1 with its
+// ring refilled at t + 1/2 and t + 1, and the covered ring of level k rebuilt
+// from the child at t + 1/2.
+static cudaError_t advance_child(lbm_ctx *h, std::vector<StepParams> &params, int k, int64_t step)
+{
+    cudaError_t e = advance_level(h, params, k + 1, 2 * step);
     if (e == cudaSuccess) e = refine_stage(h, k + 1, 1, 1);
     if (e == cudaSuccess) e = advance_level(h, params, k + 1, 2 * step + 1);
     if (e == cudaSuccess) e = refine_stage(h, k + 1, 1, 0);
@@ -1275,6 +1289,49 @@ static cudaError_t advance_level(lbm_ctx *h, std::vector<StepParams> &params, in
     FineLevel *F = fine_level(h, k + 1);
     F->mcur = 1 - F->mcur;
     return e;
+}
+
+// One step of level k (Sec. II.B applied level by level): the interface
+// moments of its child at t + 1 from the pre-step field, its own update, and
+// the child's part (advance_child).  The child's part reads the interface
+// moments, not level k's update: it touches level k only to write the
+// covered ring of level k's new field, whose cells level k's update skips
+// (fixed cells) and does not read (it pulls from the old field).  So below
+// level 0 it runs on a second stream of the highest priority, concurrently
+// with the level-0 update, which is HBM-bound while the child's interface
+// kernels are latency-bound; the level-0 stream waits for it before the next
+// step.  The result is bitwise that of running the two in order.
+static cudaError_t advance_level(lbm_ctx *h, std::vector<StepParams> &params, int k, int64_t step)
+{
+    const bool child = k < (int)h->levels.size();
+    cudaError_t e = cudaSuccess;
+    if (child) e = refine_stage(h, k + 1, 0);
+    GridRef g = level_grid(h, k);
+    params[k].step = step;
+    const bool aa = k == 0 && h->pattern == LBM_STREAM_AA;  // (never with refined levels)
+    if (e == cudaSuccess && child && k == 0 && h->level_overlap && !aa) {
+        const void *fin = g.f[*g.cur];
+        void *fout = g.f[1 - *g.cur];
+        *g.cur = 1 - *g.cur;  // the child's restriction writes the new field
+        e = ensure_side_stream(h);
+        if (e == cudaSuccess) e = cudaEventRecord(h->fork_ev, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->side, h->fork_ev, 0);
+        if (e == cudaSuccess) {
+            const cudaStream_t main = h->stream;
+            h->stream = h->side;
+            e = advance_child(h, params, k, step);
+            h->stream = main;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(h->join_ev, h->side);
+        if (e == cudaSuccess) e = launch_update(h, params[k], fin, fout);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->join_ev, 0);
+        return e;
+    }
+    if (e == cudaSuccess) e = aa ? aa_step(h, params[k]) : launch_update(h, params[k], g.f[*g.cur], g.f[1 - *g.cur]);
+    if (e != cudaSuccess) return e;
+    if (!aa) *g.cur = 1 - *g.cur;
+    if (!child) return cudaSuccess;
+    return advance_child(h, params, k, step);
 }
 
 // Enqueue n steps of level 0 (each with all refined levels beneath it).
@@ -1590,6 +1647,15 @@ extern "C" int lbm_moments_level(lbm_handle h, int level, double *rho, double *u
     int rc = level_ref(h, level, g);
     if (rc != LBM_OK) return rc;
     return moments_grid(h, g, rho, u, pi_neq);
+}
+
+extern "C" int lbm_set_level_streams(lbm_handle h, int concurrent)
+{
+    CHECK_HANDLE(h);
+    if (concurrent != 0 && concurrent != 1) return fail(h, LBM_EINVAL, "concurrent must be 0 or 1");
+    h->cfg_version++;
+    h->level_overlap = concurrent;
+    return LBM_OK;
 }
 
 extern "C" int lbm_set_launch(lbm_handle h, int block, int cells_per_thread)

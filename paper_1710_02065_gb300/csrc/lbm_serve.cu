@@ -406,13 +406,15 @@ static int admit(lbm_server *s)
     return LBM_OK;
 }
 
-// Cells per lane of a request: the chosen (or default) value, one for a row
-// of odd length
+// Cells per lane of a request: the chosen (or default) value; one for a row
+// of odd length or a lattice whose direction arrays span 2 GB or more (the
+// vector path addresses them with 32-bit offsets)
 static int lanes_of(const lbm_server *s, const Request *r)
 {
     const int k = kind_of(r->lattice, r->prec);
     const int v = s->lanes[k] ? s->lanes[k] : lanes_default(r->prec);
-    return (v == 2 && r->n[0] % 2 == 0) ? 2 : 1;
+    const bool off32 = (int64_t)r->q * r->ncell * (int64_t)elem_bytes(r->prec) < ((int64_t)1 << 31);
+    return (v == 2 && r->n[0] % 2 == 0 && off32) ? 2 : 1;
 }
 
 // Warp tile lists per group: 32 x V consecutive cells of a row each.

@@ -4,8 +4,9 @@
 // warp work items (domain, row, x segment); a persistent grid strides over
 // them and every lane updates its cells with the same device functions as
 // the single-lattice kernels (update_cell one cell per lane, update_vec V
-// cells per lane), so a domain's arithmetic does not depend on what it is
-// batched with.  Each domain carries its own step parameters, buffer pair
+// cells per lane, every row on its vector path since the domains are
+// periodic), so a domain's arithmetic does not depend on what it is batched
+// with.  Each domain carries its own step parameters, buffer pair
 // (or one lattice with the in-place AA pattern), parity and remaining-step
 // counter; k_batch_advance flips the parity and counts down after every
 // step, and a domain whose counter reaches zero is skipped by later steps of
@@ -56,14 +57,14 @@ __global__ void __launch_bounds__(256) k_batched(const BatchDomain *__restrict__
                 }
             } else {
                 if (d.cur)
-                    update_vec<L, S, C, V, V, kAALocal>(d.p, d.base[0], d.base[0], x0, y, z);
+                    update_vec<L, S, C, V, V, kAALocal, 1>(d.p, d.base[0], d.base[0], x0, y, z);
                 else
-                    update_vec<L, S, C, V, V, kAAPush>(d.p, d.base[0], d.base[0], x0, y, z);
+                    update_vec<L, S, C, V, V, kAAPush, 1>(d.p, d.base[0], d.base[0], x0, y, z);
             }
         } else if constexpr (V == 1) {
             if (x0 < d.p.n[0]) update_cell<L, S, C, false, kMaskNone>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);
         } else {
-            update_vec<L, S, C, V, V>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);
+            update_vec<L, S, C, V, V, kPull, 1>(d.p, d.base[d.cur], d.base[1 - d.cur], x0, y, z);
         }
     }
 }

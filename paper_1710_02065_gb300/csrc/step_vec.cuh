@@ -321,13 +321,49 @@ __device__ __forceinline__ void gather_vec(const VecIn<L, S, C, V> &r, int k, C 
     }
 }
 
-// Address of the row direction i of a cell pulls from: the cell's row
-// shifted by -c_y(i), -c_z(i), in direction i's array (i times the direction
-// stride in bytes)
-template <class L, class S>
-__device__ __forceinline__ const S *vec_row_ptr(const char *bin, int i, int nx, unsigned nxy, unsigned dstride)
+// Cell offsets from a row to the rows a pull reads: ym / yp for directions
+// with c_y > 0 / < 0 (the rows y - 1 / y + 1), zm / zp likewise in z.  WR = 0:
+// rows whose neighbours do not wrap (-nx, +nx, -nx ny, +nx ny); WR = 1: any
+// row of a lattice periodic in y and z, the neighbours of the first and last
+// rows wrapped around.  A push to the row y + c_y uses yp for c_y > 0 and ym
+// for c_y < 0.
+struct RowOff {
+    int ym, yp, zm, zp;
+};
+
+template <class L, int WR>
+__device__ __forceinline__ RowOff row_offsets(const StepParams &p, int y, int z)
 {
-    const char *rb = bin - ((long long)L::cy(i) * nx + (long long)L::cz(i) * (long long)nxy) * (long long)sizeof(S);
+    const int nx = p.n[0], ny = p.n[1], nz = p.n[2], nxy = nx * ny;
+    RowOff o;
+    if (WR) {
+        o.ym = y == 0 ? (ny - 1) * nx : -nx;
+        o.yp = y == ny - 1 ? -(ny - 1) * nx : nx;
+        o.zm = L::D == 2 ? 0 : (z == 0 ? (nz - 1) * nxy : -nxy);
+        o.zp = L::D == 2 ? 0 : (z == nz - 1 ? -(nz - 1) * nxy : nxy);
+    } else {
+        o.ym = -nx;
+        o.yp = nx;
+        o.zm = -nxy;
+        o.zp = nxy;
+    }
+    return o;
+}
+
+// Offset (cells) from a cell to the cell direction i pulls from, in its row
+// pattern: -c_y(i), -c_z(i) rows away
+template <class L>
+__device__ __forceinline__ int pull_off(const RowOff &o, int i)
+{
+    return (L::cy(i) > 0 ? o.ym : (L::cy(i) < 0 ? o.yp : 0)) + (L::cz(i) > 0 ? o.zm : (L::cz(i) < 0 ? o.zp : 0));
+}
+
+// Address of the row direction i of a cell pulls from, in direction i's
+// array (i times the direction stride in bytes)
+template <class L, class S>
+__device__ __forceinline__ const S *vec_row_ptr(const char *bin, int i, const RowOff &o, unsigned dstride)
+{
+    const char *rb = bin + (long long)pull_off<L>(o, i) * (long long)sizeof(S);
     return reinterpret_cast<const S *>(rb + (size_t)i * dstride);
 }
 
@@ -335,7 +371,7 @@ __device__ __forceinline__ const S *vec_row_ptr(const char *bin, int i, int nx, 
 // checked build finds an index outside the lattice (nothing loaded).
 template <class L, class S, class C, int V, int SP>
 __device__ __forceinline__ bool vec_load(const StepParams &p, const char *in0, int x0, int y, int z,
-                                         VecIn<L, S, C, V> &r)
+                                         const RowOff &ro, VecIn<L, S, C, V> &r)
 {
     using RW = Raw<S, V>;
     const int nx = p.n[0];
@@ -352,7 +388,7 @@ __device__ __forceinline__ bool vec_load(const StepParams &p, const char *in0, i
         const int64_t N = p.ncell;
         bool bad = (int64_t)cell + V > N;
         for (int i = 0; i < L::Q && SP != kAALocal; ++i) {
-            const int64_t src = (int64_t)cell - (int64_t)L::cy(i) * nx - (int64_t)L::cz(i) * nxy;
+            const int64_t src = (int64_t)cell + pull_off<L>(ro, i);
             bad = bad || src < 0 || src + V > N;
             if (p.periodic[0]) {
                 if (L::cx(i) > 0) bad = bad || src + dl < 0 || src + dl >= N;
@@ -382,7 +418,7 @@ __device__ __forceinline__ bool vec_load(const StepParams &p, const char *in0, i
         // diverges on it.
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-            const S *row = vec_row_ptr<L, S>(bin, i, nx, nxy, dstride);
+            const S *row = vec_row_ptr<L, S>(bin, i, ro, dstride);
             r.v[i] = RW::ld(row);
             if (L::cx(i) > 0) r.e[i] = Store<S>::ld(row - 1);
             if (L::cx(i) < 0) r.e[i] = Store<S>::ld(row + V);
@@ -390,7 +426,7 @@ __device__ __forceinline__ bool vec_load(const StepParams &p, const char *in0, i
     } else {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-            const S *row = vec_row_ptr<L, S>(bin, i, nx, nxy, dstride);
+            const S *row = vec_row_ptr<L, S>(bin, i, ro, dstride);
             r.v[i] = RW::ld(row);
             if (L::cx(i) > 0) r.e[i] = Store<S>::ld(row + dl);
             if (L::cx(i) < 0) r.e[i] = Store<S>::ld(row + dr);
@@ -406,7 +442,8 @@ __device__ __forceinline__ bool vec_load(const StepParams &p, const char *in0, i
 // around a periodic x axis, kept in P_i at the node when they would leave
 // through a non-periodic x face.
 template <class L, class S, class C, int V, int G, int SP>
-__device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x0, int k0, const C (&o)[G][L::Q])
+__device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x0, int k0, const RowOff &ro,
+                                          const C (&o)[G][L::Q])
 {
     const unsigned dstride = (unsigned)p.st_off[1];
     if (SP != kAAPush) {
@@ -420,12 +457,11 @@ __device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x
         return;
     }
     const int nx = p.n[0];
-    const long long nxy = (long long)nx * p.n[1];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const int j = opp<L>(i);
-        S *dst = reinterpret_cast<S *>(bout + (size_t)j * dstride +
-                                       ((long long)L::cy(i) * nx + (long long)L::cz(i) * nxy) * (long long)sizeof(S)) +
+        // the row y + c_y(i), z + c_z(i): the row direction j = opp(i) pulls from
+        S *dst = reinterpret_cast<S *>(bout + (size_t)j * dstride + (long long)pull_off<L>(ro, j) * (long long)sizeof(S)) +
                  k0;
         if (L::cx(i) == 0) {
             C w[G];
@@ -459,7 +495,7 @@ __device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x
 // are (outflow face) or with the face's density / velocity substituted.
 template <class L, class S, class C, int V, int G, int SP>
 __device__ __forceinline__ void vec_collide_store(const StepParams &p, char *out0, int x0, int y, int z,
-                                                  const VecIn<L, S, C, V> &r, bool all_bulk)
+                                                  const RowOff &ro, const VecIn<L, S, C, V> &r, bool all_bulk)
 {
     const int nx = p.n[0];
     const unsigned nxy = (unsigned)nx * (unsigned)p.n[1];
@@ -508,7 +544,7 @@ __device__ __forceinline__ void vec_collide_store(const StepParams &p, char *out
             }
             rebuild_all<L, C, false>(cf, o[kk]);
         }
-        vec_store<L, S, C, V, G, SP>(p, bout, x0, k0, o);
+        vec_store<L, S, C, V, G, SP>(p, bout, x0, k0, ro, o);
     }
 }
 
@@ -544,27 +580,35 @@ __device__ __forceinline__ bool vec_row(const StepParams &p, int y, int z)
 // where it ran only for face cells, cost 13-17% of the whole kernel, and
 // updating the face cells in threads or a launch of their own (one cell per
 // row, so every access its own cache sector) cost more.
+//
+// WR = 1: a lattice periodic on every axis whose direction arrays span less
+// than 2 GB (32-bit offsets), as the serving engine's domains are: every row
+// takes the vector path, the first and last rows' neighbours wrapped
+// (row_offsets), and no general update is compiled in.
 // ---------------------------------------------------------------------------
-template <class L, class S, class C, int V, int G, int SP = kPull>
+template <class L, class S, class C, int V, int G, int SP = kPull, int WR = 0>
 __device__ __forceinline__ void update_vec(const StepParams &p, const char *const *in, char *const *out, int x0,
                                            int y, int z)
 {
     const int nx = p.n[0];
     if (x0 >= nx) return;  // lanes past the row end
-    if (vec_row<L, SP>(p, y, z)) {
+    if (WR || vec_row<L, SP>(p, y, z)) {
+        const RowOff ro = row_offsets<L, WR>(p, y, z);
         VecIn<L, S, C, V> r;
-        if (!vec_load<L, S, C, V, SP>(p, in[0], x0, y, z, r)) return;
+        if (!vec_load<L, S, C, V, SP>(p, in[0], x0, y, z, ro, r)) return;
         const bool bulk = y >= p.blo[1] && y < p.bhi[1] && z >= p.blo[2] && z < p.bhi[2] && x0 >= p.blo[0] &&
                           x0 + V <= p.bhi[0];
-        vec_collide_store<L, S, C, V, G, SP>(p, out[0], x0, y, z, r, bulk);
+        vec_collide_store<L, S, C, V, G, SP>(p, out[0], x0, y, z, ro, r, bulk);
         return;
     }
+    if constexpr (!WR) {
 #pragma unroll 1
-    for (int k = 0; k < V; ++k) {
-        if (SP == kPull)
-            update_cell<L, S, C, false, kMaskNone>(p, in, out, x0 + k, y, z);
-        else
-            update_cell_aa<L, S, C, false, kMaskNone, SP == kAALocal>(p, out, x0 + k, y, z);
+        for (int k = 0; k < V; ++k) {
+            if (SP == kPull)
+                update_cell<L, S, C, false, kMaskNone>(p, in, out, x0 + k, y, z);
+            else
+                update_cell_aa<L, S, C, false, kMaskNone, SP == kAALocal>(p, out, x0 + k, y, z);
+        }
     }
 }
 
@@ -572,7 +616,7 @@ __device__ __forceinline__ void update_vec(const StepParams &p, const char *cons
 // storage with 2 cells per thread is issue-bound, and 64 registers (4 x 256
 // threads per SM) keep enough warps resident to hide the loads; the wider
 // types and 4 cells per thread take 128.
-template <class S, int V>
+template <class S, int V, int SP = kPull>
 struct VecMinBlocks {
     static constexpr int value = (sizeof(S) == 2 && V == 2) ? 4 : 2;
 };
@@ -589,7 +633,7 @@ struct VecGroup {
 // ---------------------------------------------------------------------------
 // Grid (x blocks of a row, ny, nz)
 template <class L, class S, class C, int V, int SP>
-__global__ void __launch_bounds__(256, (VecMinBlocks<S, V>::value)) k_stream_collide_vec(const __grid_constant__ StepParams p)
+__global__ void __launch_bounds__(256, (VecMinBlocks<S, V, SP>::value)) k_stream_collide_vec(const __grid_constant__ StepParams p)
 {
     update_vec<L, S, C, V, VecGroup<S, V>::value, SP>(p, p.in, p.out, (blockIdx.x * blockDim.x + threadIdx.x) * V,
                                                       blockIdx.y, blockIdx.z);

@@ -106,6 +106,7 @@ _sig("lbm_server_submit", [C.c_void_p, C.POINTER(lbm_request), _i64p])
 _sig("lbm_server_run", [C.c_void_p, C.c_int64, _ip])
 _sig("lbm_server_set_streaming", [C.c_void_p, C.c_int])
 _sig("lbm_server_set_launch", [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int])
+_sig("lbm_set_level_streams", [C.c_void_p, C.c_int])
 _sig("lbm_server_get_launch", [C.c_void_p, C.c_int, C.c_int, _ip, _ip])
 _sig("lbm_server_gpu_time", [C.c_void_p, _dp])
 _sig("lbm_server_poll", [C.c_void_p, C.c_int64, _ip, _i64p])
@@ -128,7 +129,7 @@ EXPORTED = [
     "lbm_server_submit", "lbm_server_run", "lbm_server_poll", "lbm_server_result", "lbm_server_stats",
     "lbm_server_set_streaming", "lbm_set_streaming", "lbm_get_streaming", "lbm_set_storage_shift",
     "lbm_set_staging_wait", "lbm_server_gpu_time", "lbm_set_state_f32", "lbm_moments_f32",
-    "lbm_server_set_launch", "lbm_server_get_launch",
+    "lbm_server_set_launch", "lbm_server_get_launch", "lbm_set_level_streams",
 ]
 LBM_REQ_QUEUED, LBM_REQ_RUNNING, LBM_REQ_DONE, LBM_REQ_FAILED = 0, 1, 2, 3
 
@@ -279,6 +280,10 @@ def lbm_probe(h, cells) -> np.ndarray:
     out = np.zeros(len(c))
     _check(_lib.lbm_probe(h, len(c), c.ctypes.data_as(_i64p), _d(out)), h)
     return out
+
+
+def lbm_set_level_streams(h, concurrent: int):
+    return _check(_lib.lbm_set_level_streams(h, int(concurrent)), h)
 
 
 def lbm_set_launch(h, block: int = 0, cells_per_thread: int = 0):

@@ -358,3 +358,68 @@ def test_refined_checkpoint_resumes_bit_identically(tmp_path, three):
     assert np.array_equal(ma, mb) and np.array_equal(da, db)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("case", ["2d", "3d", "nested3"])
+def test_level_streams_concurrent_equals_in_order(case):
+    """The refined levels' part of a step on a second stream, concurrent with
+    the level-0 update (the default), leaves every level bitwise as running
+    everything in order on one stream; also through captured step graphs
+    (a non-default stream)."""
+    import torch
+    from cases import to_gpu
+    from paper_1710_02065_gb300 import lbm
+    stream = torch.cuda.Stream()
+
+    def build(concurrent, on_stream):
+        if case == "2d":
+            c, patch, rho_f, u_f, solid_f = cylinder_two_level()
+            X0, Y0, Wc, Hc = patch
+            pl = [((X0, Y0, 0), (Wc, Hc, 1))]
+            states, solid, finest = [(rho_f, u_f)], solid_f, 1
+        elif case == "3d":
+            c, patch, rho_f, u_f, solid_f = _case_3d()
+            X0, Y0, Z0, Wc, Hc, Dc = patch
+            pl = [((X0, Y0, Z0), (Wc, Hc, Dc))]
+            states, solid, finest = [(rho_f, u_f)], solid_f, 1
+        else:
+            c, patches, states, solid = _nested_case(oracle.D3Q19)
+            pl = [(tuple(o) + (0,) * (3 - len(o)), tuple(e) + (1,) * (3 - len(e))) for o, e in patches]
+            finest = 2
+        s = to_gpu(c, 1) if not on_stream else None
+        if on_stream:
+            s = lbm.Solver(c.lattice, c.n, c.tau, 1, stream=stream.cuda_stream)
+            for face, spec in c.faces.items():
+                lbm.lbm_set_boundary(s.h, face, spec[0], spec[1], spec[2])
+            for face, (w, chi) in c.sponges.items():
+                lbm.lbm_set_sponge(s.h, face, w, chi, c.rho_ref, c.u_ref)
+            if c.solid is not None:
+                lbm.lbm_set_geometry(s.h, c.solid)
+        lbm.lbm_set_level_streams(s.h, concurrent)
+        for o, e in pl:
+            lbm.lbm_add_refinement_patch(s.h, o, e)
+        lbm.lbm_set_geometry_level(s.h, finest, solid)
+        for k in range(len(states), 0, -1):
+            lbm.lbm_set_state_level(s.h, k, *states[k - 1])
+        lbm.lbm_set_state(s.h, c.rho0, c.u0)
+        return s, len(pl) + 1
+
+    ref, nlev = build(0, False)
+    ref.step(9)
+    for concurrent, on_stream in ((1, False), (1, True), (0, True)):
+        s, _ = build(concurrent, on_stream)
+        s.step(4)
+        s.step(5)
+        torch.cuda.synchronize()
+        for k in range(nlev):
+            ext, _ = lbm.lbm_level_info(ref.h, k)
+            q = 9 if ext[2] == 1 else 19
+            n = ext[0] * ext[1] * ext[2]
+            fa, fb = np.zeros((q, n)), np.zeros((q, n))
+            lbm.lbm_get_populations_level(ref.h, k, fa)
+            lbm.lbm_get_populations_level(s.h, k, fb)
+            assert np.array_equal(fa, fb), (concurrent, on_stream, k)
+        s.close()
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_set_level_streams(ref.h, 2)
+    ref.close()
