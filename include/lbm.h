@@ -599,9 +599,9 @@ int lbm_load(lbm_handle h, const char *path);
  *                       the budget holds twice the cells)
  *   lbm_server_set_launch : launch shape of the (lattice, precision) group's
  *                       batched update from the next round on: cells_per_lane
- *                       1 or 2 (0: 2 for 16-bit and FP64 storage, 1 for FP32;
- *                       a request with an odd row length takes 1) and
- *                       warps_per_block 1, 2, 4 or 8 (0: 4).  The arithmetic
+ *                       1 or 2 (0: 2; a request with an odd row length, or
+ *                       whose direction arrays span 2 GB or more, takes 1) and
+ *                       warps_per_block 1, 2, 4 or 8 (0: 2).  The arithmetic
  *                       of a request does not depend on it.
  *   lbm_server_get_launch : the group's current shape
  *   lbm_server_poll   : state LBM_REQ_* and steps done so far

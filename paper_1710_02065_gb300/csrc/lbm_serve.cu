@@ -59,12 +59,17 @@ struct Request {
 // groups: lattice (3) x precision (4) x cells per lane (1, 2)
 constexpr int NGROUPS = 24;
 constexpr int NKINDS = 12;  // (lattice, precision) pairs
-// Default cells per lane: two except for FP32 (in the batched kernel a warp
-// item is 32 x V cells of a row, and larger items amortise the per-item work;
-// one cell per lane for every D2Q9 request measured slower on the serving
-// stream: 33.2 vs 35.0 G cell updates/s saturated).  A row of odd length
-// takes one cell per lane.
-inline int lanes_default(int prec) { return prec != LBM_FP32 ? 2 : 1; }
+// Default launch shape of every group: two cells per lane (the vector path,
+// every row of a periodic domain on it) and two warps per block, the shape
+// the serving stream's tuning picked for D2Q9 / D3Q19 at FP32 and FP16
+// (GB300: D2Q9 FP32 87 vs 38 G cell updates/s with one cell per lane, D3Q19
+// FP16 52 vs 32).  A row of odd length takes one cell per lane.
+inline int lanes_default(int prec)
+{
+    (void)prec;
+    return 2;
+}
+constexpr int kWarpsDefault = 2;
 inline int kind_of(int lattice, int prec) { return lattice * 4 + prec; }
 inline int group_of(int lattice, int prec, int v) { return kind_of(lattice, prec) * 2 + (v == 2 ? 1 : 0); }
 
@@ -167,7 +172,8 @@ struct lbm_server {
     // launch shape per (lattice, precision): cells per lane (0: the default
     // rule) and warps per block
     int lanes[NKINDS] = {};
-    int wpb[NKINDS] = {4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
+    int wpb[NKINDS] = {kWarpsDefault, kWarpsDefault, kWarpsDefault, kWarpsDefault, kWarpsDefault, kWarpsDefault,
+                       kWarpsDefault, kWarpsDefault, kWarpsDefault, kWarpsDefault, kWarpsDefault, kWarpsDefault};
     int64_t cell_updates = 0;
     int pattern = LBM_STREAM_PULL;       // streaming pattern of requests admitted from now on
     std::vector<int64_t> remaining;      // host copy of each slot's remaining steps
@@ -557,7 +563,7 @@ extern "C" int lbm_server_set_launch(lbm_server_handle s, int lattice, int preci
         return sfail(s, LBM_EINVAL, "warps_per_block must be 0, 1, 2, 4 or 8");
     const int k = kind_of(lattice, precision);
     s->lanes[k] = cells_per_lane;
-    s->wpb[k] = warps_per_block ? warps_per_block : 4;
+    s->wpb[k] = warps_per_block ? warps_per_block : kWarpsDefault;
     s->dirty = true;  // new tile lists and a new graph at the next round
     return LBM_OK;
 }

@@ -330,8 +330,8 @@ def test_server_tuner_picks_a_candidate(serving):
         assert len(p["table"]) == len(autotune.SERVER_CANDIDATES) and p["mlups"] > 0
     s = lbm.lbm_server_create(1 << 20, 4, None)
     try:
-        assert lbm.lbm_server_get_launch(s, 1, 1) == (1, 4)
-        assert lbm.lbm_server_get_launch(s, 1, 2) == (2, 4)
+        assert lbm.lbm_server_get_launch(s, 1, 1) == (2, 2)
+        assert lbm.lbm_server_get_launch(s, 1, 2) == (2, 2)
         lbm.lbm_server_set_launch(s, 1, 2, 1, 8)
         assert lbm.lbm_server_get_launch(s, 1, 2) == (1, 8)
         with pytest.raises(lbm.LBMError):
