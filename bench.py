@@ -346,14 +346,15 @@ def e2e_run(lbm, torch, spec, precision, steps, stream):
     down()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    up()
+    up()  # returns once the field is written (it checks the values)
+    t1 = time.perf_counter()
     lbm.lbm_step(s.h, steps)
     down()
     torch.cuda.synchronize()
-    dt_s = time.perf_counter() - t0
+    t2 = time.perf_counter()
     s.close()
-    return dict(seconds=dt_s, h2d=(rho.nbytes + u.nbytes) / steps, d2h=(ro.nbytes + uo.nbytes) / steps,
-                host_dtype="fp32" if f32 else "fp64")
+    return dict(seconds=t2 - t0, upload_s=t1 - t0, h2d=(rho.nbytes + u.nbytes) / steps,
+                d2h=(ro.nbytes + uo.nbytes) / steps, host_dtype="fp32" if f32 else "fp64")
 
 
 def _pprime_compare(runs, checkpoints, ref_name):
@@ -944,7 +945,8 @@ def main():
             "cpu_baseline": cpu,
             "e2e": ({"value": world * ncell * args.steps / e2e_s / 1e6, "unit": "MLUPS",
                      "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
-                     "steps": args.steps, "host_dtype": e2e["host_dtype"]} if e2e else None),
+                     "steps": args.steps, "host_dtype": e2e["host_dtype"],
+                     "upload_ms": 1e3 * e2e["upload_s"]} if e2e else None),
             "gpu_launches": main_run["launches"],
             "clocks": clk,
             "stable": main_run["stable"],

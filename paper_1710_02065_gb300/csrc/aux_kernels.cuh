@@ -53,11 +53,20 @@ __global__ void k_init_eq(int64_t N, int64_t c0, int64_t n, const T *__restrict_
     Coef<C> k{};
     add_eq<C, L::D, true, full_third_order<L>()>(k, C(1), C(r - 1.0), C(r), C(u[3 * t]), C(u[3 * t + 1]),
                                                   L::D == 3 ? C(u[3 * t + 2]) : C(0), order4 != 0);
+    if (dsh) {
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        const S v = Store<S>::from(dsh ? rebuild<L, C>(k, i) - C(dsh[i]) : rebuild<L, C>(k, i));
-        f0[(int64_t)i * N + cell] = v;
-        f1[(int64_t)i * N + cell] = v;
+        for (int i = 0; i < L::Q; ++i) {
+            const S v = Store<S>::from(rebuild<L, C>(k, i) - C(dsh[i]));
+            f0[(int64_t)i * N + cell] = v;
+            f1[(int64_t)i * N + cell] = v;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const S v = Store<S>::from(rebuild<L, C>(k, i));
+            f0[(int64_t)i * N + cell] = v;
+            f1[(int64_t)i * N + cell] = v;
+        }
     }
 }
 
@@ -99,6 +108,22 @@ __device__ __forceinline__ void load_cell_fp64(const S *__restrict__ f, int64_t 
     for (int i = 0; i < L::Q; ++i) g[i] = (double)Store<S>::ld(f + (int64_t)i * N + cell);
 }
 
+// The Q populations of a cell in the compute type, the storage shift added
+// when the handle has one (a uniform branch: the per-direction conversion of
+// dsh to the compute type is not executed for the default shift)
+template <class L, class S, class C>
+__device__ __forceinline__ void load_cell(const S *__restrict__ f, int64_t N, int64_t cell,
+                                          const double *__restrict__ dsh, C (&g)[L::Q])
+{
+    if (dsh) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell) + C(dsh[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell);
+    }
+}
+
 // Moments in the kernel's compute type (FP32 for FP32/FP16/BF16 storage,
 // whose values carry FP32 precision at most; FP64 for FP64 storage), stored
 // as FP64: rho = 1 + dr keeps dr's relative precision.
@@ -111,8 +136,7 @@ __global__ void k_moments(int64_t N, int64_t c0, int64_t n, const S *__restrict_
     if (t >= n) return;
     const int64_t cell = c0 + t;
     C g[L::Q];
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell) + (dsh ? C(dsh[i]) : C(0));
+    load_cell<L, S, C>(f, N, cell, dsh, g);
     const Mom<C> m = moments<L, C>(g);
     const C r = C(1) + m.dr;
     const C ux = m.jx / r, uy = m.jy / r, uz = L::D == 3 ? m.jz / r : C(0);
@@ -154,8 +178,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce(int64_t N, const S *__rest
          cell += (int64_t)gridDim.x * blockDim.x) {
         if (solid && (solid[cell] & MASK_TYPE)) continue;  // fluid cells only
         C g[L::Q];
-#pragma unroll
-        for (int i = 0; i < L::Q; ++i) g[i] = Store<S>::ld(f + (int64_t)i * N + cell) + (dsh ? C(dsh[i]) : C(0));
+        load_cell<L, S, C>(f, N, cell, dsh, g);
         bool finite = true;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) finite = finite && isfinite(g[i]);

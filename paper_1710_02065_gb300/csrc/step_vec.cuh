@@ -9,10 +9,13 @@
 // aligned loads touch, so DRAM traffic is unchanged; measured on GB300 this
 // beats completing the aligned vector by a warp shuffle plus a scalar load
 // at the warp's edge lanes).  Stores are aligned V-wide vectors of the
-// thread's own cells.  Boundary roles are the ones of step.cuh: a node on a non-periodic
-// y/z face streams the row of its inward neighbour (uniform for a thread); a
-// node on a non-periodic x face takes the streamed populations of its x
-// neighbour, which lives in the same thread.
+// thread's own cells (the AA gather-push step stores its xi_x = +-1
+// populations one cell at a time).  Boundary roles are the ones of step.cuh:
+// rows on (or, for the AA steps, next to) a non-periodic y / z face take the
+// general update; a node on a non-periodic x face takes the streamed
+// populations of its x neighbour, which lives in the same thread, and its
+// velocity / pressure / free-slip role is applied to their moments in
+// registers.
 //
 // Reconstruction uses the parity of the Hermite terms: for an opposite pair
 // (i, i + Q/2) the even part E = a0 + H2:A2 / (2 c_s^4) is shared and the
@@ -25,36 +28,6 @@
 #include "step.cuh"
 
 namespace rr {
-
-// Two FP32 lanes computed by one packed instruction (add / mul / fma .f32x2
-// of sm_100+): the rebuild of a thread's two cells with the same code.
-// Measured on GB300 for the D3Q19 jet: BF16 storage 59.6 -> 64.2 G cell
-// updates/s, FP16 63.1 -> 61.5, FP32 46.2 -> 44.7; so only the BF16
-// two-cell kernel uses it.
-struct F2 {
-    float2 v;
-    __device__ __forceinline__ F2() {}
-    __device__ __forceinline__ F2(float2 a) : v(a) {}
-    __device__ __forceinline__ F2(double c) : v(make_float2((float)c, (float)c)) {}
-    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
-};
-__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
-__device__ __forceinline__ F2 operator-(F2 a) { return F2(make_float2(-a.v.x, -a.v.y)); }
-__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y))); }
-__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
-__device__ __forceinline__ F2 &operator+=(F2 &a, F2 b) { a = a + b; return a; }
-__device__ __forceinline__ F2 fmac(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
-__device__ __forceinline__ Coef<F2> pack_coef(const Coef<float> &a, const Coef<float> &b)
-{
-    Coef<F2> k;
-    k.a0 = F2(a.a0, b.a0); k.a1x = F2(a.a1x, b.a1x); k.a1y = F2(a.a1y, b.a1y); k.a1z = F2(a.a1z, b.a1z);
-    k.xx = F2(a.xx, b.xx); k.yy = F2(a.yy, b.yy); k.zz = F2(a.zz, b.zz);
-    k.xy = F2(a.xy, b.xy); k.xz = F2(a.xz, b.xz); k.yz = F2(a.yz, b.yz);
-    k.xxy = F2(a.xxy, b.xxy); k.xyy = F2(a.xyy, b.xyy); k.xxz = F2(a.xxz, b.xxz);
-    k.xzz = F2(a.xzz, b.xzz); k.yyz = F2(a.yyz, b.yyz); k.yzz = F2(a.yzz, b.yzz);
-    k.xyz = F2(a.xyz, b.xyz); k.xxyy = F2(a.xxyy, b.xxyy);
-    return k;
-}
 
 // ---------------------------------------------------------------------------
 // V-wide aligned loads / stores converting to / from the compute type C
