@@ -723,6 +723,58 @@ def run_serving(lbm, torch, args):
     return out
 
 
+def run_batched(lbm, torch, args):
+    """The serving engine's batched update (k_batched) on a fixed batch: `--batch
+    KxN` periodic requests of N^3 (D3Q19 / D3Q27) or N^2 (D2Q9) cells at rest,
+    one (lattice, precision) group, `--round-steps` steps per round; after
+    `--warmup` warm rounds, `--steps` rounds are timed by the device time of
+    their graphs (k_batched per step plus the per-domain advance).  The
+    roofline is 2 Q s bytes per cell update over that time."""
+    k, n = (int(v) for v in args.batch.lower().split("x"))
+    lat = {"d2q9": lbm.LBM_D2Q9, "d3q19": lbm.LBM_D3Q19, "d3q27": lbm.LBM_D3Q27}[args.lattice]
+    prec = lbm.PRECISIONS[args.precision]
+    q = {lbm.LBM_D2Q9: 9, lbm.LBM_D3Q19: 19, lbm.LBM_D3Q27: 27}[lat]
+    s_bytes = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}[args.precision]
+    ext = (n, n, 1) if lat == lbm.LBM_D2Q9 else (n, n, n)
+    cells = k * ext[0] * ext[1] * ext[2]
+    srv = lbm.lbm_server_create(16 << 30, 256, None)
+    try:
+        if args.streaming == "aa":
+            lbm.lbm_server_set_streaming(srv, lbm.LBM_STREAM_AA)
+        if args.launch:
+            v, w = (int(t) for t in args.launch.split("x"))
+            lbm.lbm_server_set_launch(srv, lat, prec, v, w)
+        for _ in range(k):
+            lbm.lbm_server_submit(srv, lat, prec, ext, 0.6, 1 << 40)
+        for _ in range(args.warmup):
+            lbm.lbm_server_run(srv, args.round_steps)
+        torch.cuda.synchronize()
+        t0 = lbm.lbm_server_gpu_time(srv)
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            lbm.lbm_server_run(srv, args.round_steps)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        ms = lbm.lbm_server_gpu_time(srv) - t0
+        v, w = lbm.lbm_server_get_launch(srv, lat, prec)
+    finally:
+        lbm.lbm_server_destroy(srv)
+    updates = cells * args.round_steps * args.steps
+    peaks = measured_peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
+    gbs = 2 * q * s_bytes * updates / (ms / 1e3) / 1e9
+    return {"workload": f"batched update, {k} periodic {args.lattice.upper()} requests of "
+                        f"{'x'.join(str(e) for e in ext)} cells at rest, {args.precision} storage, "
+                        f"{args.streaming} streaming",
+            "metric": "MLUPS", "value": updates / (ms / 1e3) / 1e6, "unit": "MLUPS",
+            "rounds": args.steps, "steps_per_round": args.round_steps, "warmup_rounds": args.warmup,
+            "device_ms": ms, "wall_ms": 1e3 * wall, "cells": cells,
+            "launch": {"cells_per_lane": v, "warps_per_block": w},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "kernel": "k_batched (+ k_batch_advance per step)",
+                         "bytes_per_cell": 2 * q * s_bytes}}
+
+
 # ---------------------------------------------------------------------------
 # main
 # ---------------------------------------------------------------------------
@@ -767,9 +819,10 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape (no autotuning)")
     ap.add_argument("--launch", default=None,
                     help="fixed kernel and launch shape for the main precision instead of tuning: "
-                         "cell:BLOCK, vec2:BLOCK, vec4:BLOCK or rows:STAGES")
+                         "cell:BLOCK, vec2:BLOCK, vec4:BLOCK or rows:STAGES; batched workload: VxW, cells per "
+                         "lane x warps per block")
     ap.add_argument("--workload", default="jet", choices=["jet", "cylinder", "cylinder2level", "cylinder3level",
-                                                          "jet2level", "serving"],
+                                                          "jet2level", "serving", "batched"],
                     help="jet: the headline benchmark line; the others print their own JSON line")
     ap.add_argument("--cyl-steps", type=int, default=40000, help="fine-resolution steps of the cylinder runs")
     ap.add_argument("--requests", type=int, default=512)
@@ -784,8 +837,11 @@ def main():
     ap.add_argument("--level-streams", type=int, default=1, choices=[0, 1],
                     help="refined workloads: 1 runs the refined levels concurrently with the level-0 update "
                          "(lbm_set_level_streams), 0 in order on one stream")
-    ap.add_argument("--lattice", default="d3q19", choices=["d3q19", "d3q27"],
-                    help="lattice of the two-level jet workload (the jet benchmark line is D3Q19)")
+    ap.add_argument("--lattice", default="d3q19", choices=["d2q9", "d3q19", "d3q27"],
+                    help="lattice of the two-level jet (d3q19 / d3q27) and batched workloads (the jet benchmark "
+                         "line is D3Q19)")
+    ap.add_argument("--batch", default="8x128",
+                    help="batched workload: KxN, K periodic requests of N^3 (N^2 for D2Q9) cells")
     ap.add_argument("--grid", default="384x256x256",
                     help="jet extents NXxNYxNZ; inlet diameter and sponges scale with NX/384")
     args = ap.parse_args()
@@ -808,7 +864,8 @@ def main():
 
     if args.workload != "jet":
         fn = {"cylinder": run_cylinder, "cylinder2level": run_cylinder_two_level,
-              "cylinder3level": run_cylinder_three_level, "jet2level": run_jet_two_level, "serving": run_serving}
+              "cylinder3level": run_cylinder_three_level, "jet2level": run_jet_two_level, "serving": run_serving,
+              "batched": run_batched}
         out = fn[args.workload](lbm, torch, args)
         if rank == 0:
             print(json.dumps(out), flush=True)

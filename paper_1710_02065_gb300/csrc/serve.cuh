@@ -35,9 +35,18 @@ struct BatchTile {
     int pad;
 };
 
+// Resident 256-thread blocks per SM asked of the compiler: as the
+// single-lattice kernel, 16-bit storage with two cells per lane is latency-
+// bound and gets 64 registers (32 resident warps per SM) on D2Q9 / D3Q19;
+// the other groups keep the registers they need.
+template <class L, class S, int V>
+struct BatchMinBlocks {
+    static constexpr int value = (sizeof(S) == 2 && V == 2 && L::Q <= 19) ? 4 : 0;
+};
+
 template <class L, class S, class C, int V>
-__global__ void __launch_bounds__(256) k_batched(const BatchDomain *__restrict__ doms,
-                                                  const BatchTile *__restrict__ tiles, int ntiles)
+__global__ void __launch_bounds__(256, (BatchMinBlocks<L, S, V>::value))
+    k_batched(const BatchDomain *__restrict__ doms, const BatchTile *__restrict__ tiles, int ntiles)
 {
     const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int t = blockIdx.x * wpb + warp; t < ntiles; t += gridDim.x * wpb) {
