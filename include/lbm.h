@@ -223,6 +223,11 @@ int lbm_set_radial_sponge(lbm_handle h, const double center[3], double r0, doubl
  * the field is written: LBM_EINVAL names the first cell whose rho is not
  * finite and > 0 (or, 2D, whose u_z is not 0), and the field is then
  * unspecified until it is set again.
+ * Page-locked host arrays (cudaHostAlloc / cudaMallocHost, or registered with
+ * cudaHostRegister, e.g. pinned torch tensors) are read by the kernel
+ * directly over the host link in one pass; pageable arrays are copied through
+ * the handle's staging buffer (lbm_set_transfer_staging).  Same values either
+ * way.
  */
 int lbm_set_state(lbm_handle h, const double *rho, const double *u);
 /* The same with FP32 host arrays (half the host-link bytes), for FP32 and
@@ -250,7 +255,9 @@ int lbm_step(lbm_handle h, int64_t n);
  * Computed on the device from the stored populations in the compute type of
  * the storage: FP64 for LBM_FP64, FP32 for LBM_FP32 and the shifted 16-bit
  * formats (rho = 1 + sum_i (f_i - w_i) keeps the precision of the small
- * sum), and returned as FP64.
+ * sum), and returned as FP64.  When every non-NULL output is page-locked
+ * host memory (as for lbm_set_state), the kernel writes the outputs directly;
+ * otherwise they pass through the staging buffer.
  */
 int lbm_moments(lbm_handle h, double *rho, double *u, double *pi_neq);
 /* The same with FP32 host arrays (half the host-link bytes; the values are
@@ -365,7 +372,8 @@ int lbm_set_collision(lbm_handle h, int model);
  * lbm_set_transfer_staging -- bound on the device memory that host transfers
  * use.  lbm_set_state, lbm_set_populations, lbm_get_populations and
  * lbm_moments (and their per-level forms) move fields through one device
- * staging buffer per handle, in chunks of whole cells; it is allocated on
+ * staging buffer per handle, in chunks of whole cells (state and moments in
+ * page-locked host memory skip it: the kernels access them directly); it is allocated on
  * first use, holds min(max_bytes, what one field needs) bytes and is freed
  * with the handle.  Default 256 MiB; max_bytes must be >= 1024.  Transfers
  * synchronise the stream once, at the end of the call.

@@ -38,21 +38,51 @@ __device__ __forceinline__ double weight_rt(int i)
 // stored value + dsh[i] is the population in the w_i-shifted convention the
 // arithmetic uses.
 // T: the host arrays' type (FP64, or FP32 for the single-precision transfer calls)
+//
+// The per-cell vectors (u: 3 values, Pi^neq: 6) are interleaved by cell, so
+// a thread's own components lie 12-48 bytes apart from its neighbour's.  The
+// kernels move a block's slice of them through shared memory with
+// contiguous loads / stores (consecutive threads, consecutive elements): the
+// host arrays may be page-locked host memory accessed over the host link,
+// where three strided accesses per value cost three transfers of the same
+// lines.  Blocks of at most kXferBlock threads.
+constexpr int kXferBlock = 256;
+
+template <class T, int M>
+__device__ __forceinline__ void stage_in(const T *__restrict__ src, int count, T *sm)
+{
+    for (int k = threadIdx.x; k < M * count; k += blockDim.x) sm[k] = src[k];
+}
+template <class T, int M>
+__device__ __forceinline__ void stage_out(T *__restrict__ dst, int count, const T *sm)
+{
+    for (int k = threadIdx.x; k < M * count; k += blockDim.x) dst[k] = sm[k];
+}
+
 template <class L, class S, class T = double>
-__global__ void k_init_eq(int64_t N, int64_t c0, int64_t n, const T *__restrict__ rho,
-                          const T *__restrict__ u, S *__restrict__ f0, S *__restrict__ f1, int order4,
-                          unsigned long long *__restrict__ bad, const double *__restrict__ dsh = nullptr)
+__global__ void __launch_bounds__(kXferBlock) k_init_eq(int64_t N, int64_t c0, int64_t n,
+                                                          const T *__restrict__ rho, const T *__restrict__ u,
+                                                          S *__restrict__ f0, S *__restrict__ f1, int order4,
+                                                          unsigned long long *__restrict__ bad,
+                                                          const double *__restrict__ dsh = nullptr)
 {
     using C = typename StoreC<S>::C;  // FP32 arithmetic for FP32/FP16/BF16 storage
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
+    __shared__ T su[3 * kXferBlock];
+    const int64_t b0 = blockIdx.x * (int64_t)blockDim.x;
+    const int cnt = (int)(n - b0 < (int64_t)blockDim.x ? n - b0 : (int64_t)blockDim.x);
+    stage_in<T, 3>(u + 3 * b0, cnt, su);
+    __syncthreads();
+    const int tid = threadIdx.x;
+    if (tid >= cnt) return;
+    const int64_t t = b0 + tid;
     const int64_t cell = c0 + t;
     const double r = rho[t];
-    if (bad && (!(r > 0.0) || !isfinite(r) || (L::D == 2 && u[3 * t + 2] != T(0))))
+    const T ux = su[3 * tid], uy = su[3 * tid + 1], uz = su[3 * tid + 2];
+    if (bad && (!(r > 0.0) || !isfinite(r) || (L::D == 2 && uz != T(0))))
         atomicMin(bad, (unsigned long long)cell);
     Coef<C> k{};
-    add_eq<C, L::D, true, full_third_order<L>()>(k, C(1), C(r - 1.0), C(r), C(u[3 * t]), C(u[3 * t + 1]),
-                                                  L::D == 3 ? C(u[3 * t + 2]) : C(0), order4 != 0);
+    add_eq<C, L::D, true, full_third_order<L>()>(k, C(1), C(r - 1.0), C(r), C(ux), C(uy),
+                                                  L::D == 3 ? C(uz) : C(0), order4 != 0);
     if (dsh) {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
@@ -128,32 +158,51 @@ __device__ __forceinline__ void load_cell(const S *__restrict__ f, int64_t N, in
 // whose values carry FP32 precision at most; FP64 for FP64 storage), stored
 // as FP64: rho = 1 + dr keeps dr's relative precision.
 template <class L, class S, class T = double>
-__global__ void k_moments(int64_t N, int64_t c0, int64_t n, const S *__restrict__ f, T *__restrict__ rho,
-                          T *__restrict__ u, T *__restrict__ pn, const double *__restrict__ dsh = nullptr)
+__global__ void __launch_bounds__(kXferBlock) k_moments(int64_t N, int64_t c0, int64_t n, const S *__restrict__ f,
+                                                          T *__restrict__ rho, T *__restrict__ u,
+                                                          T *__restrict__ pn, const double *__restrict__ dsh = nullptr)
 {
     using C = typename StoreC<S>::C;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int64_t cell = c0 + t;
-    C g[L::Q];
-    load_cell<L, S, C>(f, N, cell, dsh, g);
-    const Mom<C> m = moments<L, C>(g);
-    const C r = C(1) + m.dr;
-    const C ux = m.jx / r, uy = m.jy / r, uz = L::D == 3 ? m.jz / r : C(0);
-    if (rho) rho[t] = T(1.0 + (double)m.dr);
-    if (u) {
-        u[3 * t] = ux;
-        u[3 * t + 1] = uy;
-        u[3 * t + 2] = uz;
+    __shared__ T sm[6 * kXferBlock];  // u (3 per cell), then Pi^neq (6 per cell)
+    const int64_t b0 = blockIdx.x * (int64_t)blockDim.x;
+    const int cnt = (int)(n - b0 < (int64_t)blockDim.x ? n - b0 : (int64_t)blockDim.x);
+    const int tid = threadIdx.x;
+    const bool live = tid < cnt;
+    const int64_t t = b0 + tid;
+    Mom<C> m{};
+    C r = C(1), ux = C(0), uy = C(0), uz = C(0);
+    if (live) {
+        C g[L::Q];
+        load_cell<L, S, C>(f, N, c0 + t, dsh, g);
+        m = moments<L, C>(g);
+        r = C(1) + m.dr;
+        ux = m.jx / r;
+        uy = m.jy / r;
+        uz = L::D == 3 ? m.jz / r : C(0);
+        if (rho) rho[t] = T(1.0 + (double)m.dr);
+    }
+    if (u) {  // uniform: a kernel argument
+        if (live) {
+            sm[3 * tid] = ux;
+            sm[3 * tid + 1] = uy;
+            sm[3 * tid + 2] = uz;
+        }
+        __syncthreads();
+        stage_out<T, 3>(u + 3 * b0, cnt, sm);
     }
     if (pn) {
-        const Sym2<C> p = pi_neq<C>(m, m.dr, r, ux, uy, uz, L::D);
-        pn[6 * t + 0] = p.xx;
-        pn[6 * t + 1] = p.xy;
-        pn[6 * t + 2] = p.xz;
-        pn[6 * t + 3] = p.yy;
-        pn[6 * t + 4] = p.yz;
-        pn[6 * t + 5] = p.zz;
+        __syncthreads();
+        if (live) {
+            const Sym2<C> p = pi_neq<C>(m, m.dr, r, ux, uy, uz, L::D);
+            sm[6 * tid + 0] = p.xx;
+            sm[6 * tid + 1] = p.xy;
+            sm[6 * tid + 2] = p.xz;
+            sm[6 * tid + 3] = p.yy;
+            sm[6 * tid + 4] = p.yz;
+            sm[6 * tid + 5] = p.zz;
+        }
+        __syncthreads();
+        stage_out<T, 6>(pn + 6 * b0, cnt, sm);
     }
 }
 

@@ -824,19 +824,46 @@ extern "C" int lbm_set_transfer_staging(lbm_handle h, size_t max_bytes)
 
 static int aa_normalize(lbm_ctx *h);
 
+// Device address of a page-locked host buffer the device can reach (allocated
+// by cudaHostAlloc / cudaMallocHost or registered by cudaHostRegister, which
+// unified addressing maps into the device's address space), or null for
+// pageable memory.  Transfers of such buffers skip the staging copies: the
+// kernels read or write them over the host link directly.
+template <class T>
+static T *mapped_host(T *p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, (const void *)p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? (T *)a.devicePointer : nullptr;
+}
+
 template <class T>
 static int set_state_grid(lbm_ctx *h, const GridRef &g, const T *rho, const T *u)
 {
     if (!rho || !u) return fail(h, LBM_EINVAL, "rho and u are required");
     const int64_t N = g.ncell;
-    int64_t chunk = 0;
-    int rc = stage(h, N, 4 * sizeof(T), chunk);
-    if (rc != LBM_OK) return rc;
+    const T *rho_m = mapped_host(rho), *u_m = mapped_host(u);
+    const bool direct = rho_m && u_m;
+    int64_t chunk = N;
+    if (!direct) {
+        const int rc = stage(h, N, 4 * sizeof(T), chunk);
+        if (rc != LBM_OK) return rc;
+    }
     if (!h->bad_d) CUDA_TRY(h, cudaMalloc(&h->bad_d, sizeof(unsigned long long)));
     // the values are checked on the device while the field is written
     cudaError_t e = cudaMemsetAsync(h->bad_d, 0xff, sizeof(unsigned long long), h->stream);
-    T *rd = (T *)h->stage_d, *ud = (T *)h->stage_d + chunk;
-    for (int64_t c0 = 0; c0 < N && e == cudaSuccess; c0 += chunk) {
+    if (direct && e == cudaSuccess) {
+        // one pass, the kernel reading the page-locked host arrays
+        e = dispatch<InitEq>(h->lattice, h->prec, h->stream, N, (int64_t)0, N, rho_m, u_m, g.f[0], g.f[1],
+                             h->order4, h->bad_d, shift_of(h, g));
+        h->launches += 1;
+    }
+    T *rd = direct ? nullptr : (T *)h->stage_d, *ud = direct ? nullptr : (T *)h->stage_d + chunk;
+    for (int64_t c0 = 0; !direct && c0 < N && e == cudaSuccess; c0 += chunk) {
         const int64_t n = std::min(chunk, N - c0);
         e = cudaMemcpyAsync(rd, rho + c0, sizeof(T) * (size_t)n, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess)
@@ -1957,6 +1984,18 @@ static int moments_grid(lbm_ctx *h, const GridRef &g, T *rho, T *u, T *pi_neq)
     }
     if (!rho && !u && !pi_neq) return LBM_OK;
     const int64_t N = g.ncell;
+    {
+        // page-locked outputs: one pass, the kernel writing them over the host link
+        T *rm = mapped_host(rho), *um = mapped_host(u), *pm = mapped_host(pi_neq);
+        if ((!rho || rm) && (!u || um) && (!pi_neq || pm)) {
+            cudaError_t e = dispatch<Moments>(h->lattice, h->prec, h->stream, N, (int64_t)0, N,
+                                              (const void *)g.f[*g.cur], rm, um, pm, shift_of(h, g));
+            h->launches += 1;
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return fail(h, LBM_ECUDA, "moments: %s", cudaGetErrorString(e));
+            return LBM_OK;
+        }
+    }
     const size_t per = sizeof(T) * ((rho ? 1 : 0) + (u ? 3 : 0) + (pi_neq ? 6 : 0));
     int64_t chunk = 0;
     int rc = stage(h, N, per, chunk);

@@ -80,6 +80,34 @@ def test_aa_open_box_and_periodic_axes_match_oracle(lattice, prec, kernel):
         s.close()
 
 
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
+def test_aa_whole_warp_rows_match_oracle(lattice, prec):
+    """Two cells per thread on rows of whole warps (nx = 128: two warps per
+    row), where the gather-push step trades the x-moving populations between
+    lanes and stores aligned pairs: an open x axis (inflow with profile and
+    noise, outflow, sponges) and a periodic one (the values crossing the
+    row's ends wrap around), after odd and even step counts."""
+    _, _, _, w, _ = oracle.lattice(lattice)
+    n = (128, 10, 1) if lattice == D2Q9 else (128, 8, 6)
+    for xper in (False, True):
+        c = _open_box(lattice, n, seed=31, rest=True)
+        if xper:
+            c.faces.pop(0)
+            c.faces.pop(1)
+            c.sponges = {2: (3, 0.6)}
+        P, f = to_oracle(c)
+        s = _aa(c, prec, 2)
+        done = 0
+        for k in (3, 2):  # step counts 3 and 5
+            f = P.run(f, k, step0=done)
+            s.step(k)
+            done += k
+            err = np.abs(s.populations() - f).max()
+            assert err <= _pop_tol(prec, f, w, done), (xper, done, err)
+        s.close()
+
+
 def test_aa_equals_pull_and_survives_switches_and_checkpoints(tmp_path):
     """FP32 jet box: AA and pull agree to round-off after 9 steps; switching the
     pattern in the middle of a run (at an odd step) and a checkpoint written in
