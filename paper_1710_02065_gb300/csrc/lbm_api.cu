@@ -46,6 +46,7 @@ struct lbm_ctx {
     int level_overlap = 1;
     cudaStream_t side = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    int sms = 0;  // SMs of the device (set with the second stream)
     void *f[2] = {nullptr, nullptr};
     int cur = 0;
     uint8_t *solid_d = nullptr;
@@ -1126,6 +1127,10 @@ static void fine_params(lbm_ctx *h, int k, StepParams &p)
     set_bulk_box(p);
 }
 
+// 256-thread blocks per SM of the 3D fill and restriction when they run
+// beside the level-0 update
+constexpr int kInterfaceBlocksPerSm = 2;
+
 // 3D patch (D3Q19 or D3Q27): plane moments, fine shell, covered coarse shell
 template <class L, class S>
 static cudaError_t refine_kernels3(lbm_ctx *h, int k, int stage, int a_half)
@@ -1135,6 +1140,13 @@ static cudaError_t refine_kernels3(lbm_ctx *h, int k, int stage, int a_half)
     const double tau_p = level_tau(h, k - 1);
     const RefineGeom &g = F->geom;
     cudaStream_t st = h->stream;
+    // Beside the level-0 update (second stream) the latency-bound fill and
+    // restriction run on a bounded grid: at full width their blocks, of the
+    // higher-priority stream, would take the SMs from the HBM-bound update.
+    auto side_cap = [&](unsigned grid) {
+        const unsigned cap = (unsigned)(h->sms * kInterfaceBlocksPerSm);
+        return h->side && st == h->side && cap > 0 && grid > cap ? cap : grid;
+    };
     switch (stage) {
     case 0:  // coarse plane moments at t + 1 from the pre-step coarse field
     case 3: {  // plane moments at t = 0: local moments of the stored coarse field
@@ -1148,7 +1160,7 @@ static cudaError_t refine_kernels3(lbm_ctx *h, int k, int stage, int a_half)
     case 1: {  // fine shell at t + 1/2 (a_half = 1) or t + 1 (a_half = 0)
         const int n = shell3_count(g.nfx, g.nfy, g.nfz);
         // 4 threads per shell node
-        k_fill_shell3<L, S><<<grid1(4 * (int64_t)n, 256), 256, 0, st>>>(
+        k_fill_shell3<L, S><<<side_cap(grid1(4 * (int64_t)n, 256)), 256, 0, st>>>(
             g, (const CT<S> *)F->M[F->mcur], (const CT<S> *)F->M[1 - F->mcur], CT<S>(a_half ? 0.5 : 1.0),
             CT<S>(F->tau / (2.0 * tau_p)), CT<S>(1.0 - 1.0 / F->tau), (S *)F->f[F->cur]);
         break;
@@ -1156,7 +1168,7 @@ static cudaError_t refine_kernels3(lbm_ctx *h, int k, int stage, int a_half)
     case 2: {  // covered coarse shell from the fine field; fine moments pulled from f(t + 1/2)
         const int n = shell3_count(g.Wc - 1, g.Hc - 1, g.Dc - 1);
         // one warp per covered coarse node (one lane per filter point)
-        k_restrict3<L, S><<<grid1(32 * (int64_t)n, 256), 256, 0, st>>>(
+        k_restrict3<L, S><<<side_cap(grid1(32 * (int64_t)n, 256)), 256, 0, st>>>(
             g, (const S *)F->f[1 - F->cur], links_mask(h, k), CT<S>(2.0 * tau_p / F->tau), CT<S>(1.0 - 1.0 / tau_p),
             (S *)P.f[*P.cur]);
         break;
@@ -1298,6 +1310,9 @@ static cudaError_t ensure_side_stream(lbm_ctx *h)
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming);
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
     return e;
 }
 

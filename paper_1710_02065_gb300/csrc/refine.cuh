@@ -429,43 +429,49 @@ __global__ void __launch_bounds__(256) k_fill_shell3(RefineGeom g, const CT<S> *
                                                      CT<S> omega, S *__restrict__ ff)
 {
     using C = CT<S>;
-    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int t = (int)(gt >> 2), r = (int)(gt & 3);
     const int count = shell3_count(g.nfx, g.nfy, g.nfz);
-    const bool node = t < count;  // lanes past the last node still join the shuffles
-    int i = 0, j = 0, k = 0;
-    if (node) shell3_coord(g.nfx, g.nfy, g.nfz, t, i, j, k);
-    // per axis: 1 point (even fine coordinate) or 4 (odd); lx = log2 of the count
-    const int lx = (i & 1) << 1, ly = (j & 1) << 1, lz = (k & 1) << 1;
-    const int npts = node ? 1 << (lx + ly + lz) : 0;
-    const C am = a, bm = C(1) - a;
-    C m[10];
+    // block-strided over the nodes (every thread of a block takes the same
+    // number of turns), so that a grid smaller than the work can leave room
+    // on the SMs for a kernel running beside it
+    for (int64_t b0 = blockIdx.x * (int64_t)blockDim.x; b0 < 4 * (int64_t)count;
+         b0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t gt = b0 + threadIdx.x;
+        const int t = (int)(gt >> 2), r = (int)(gt & 3);
+        const bool node = t < count;  // lanes past the last node still join the shuffles
+        int i = 0, j = 0, k = 0;
+        if (node) shell3_coord(g.nfx, g.nfy, g.nfz, t, i, j, k);
+        // per axis: 1 point (even fine coordinate) or 4 (odd); lx = log2 of the count
+        const int lx = (i & 1) << 1, ly = (j & 1) << 1, lz = (k & 1) << 1;
+        const int npts = node ? 1 << (lx + ly + lz) : 0;
+        const C am = a, bm = C(1) - a;
+        C m[10];
 #pragma unroll
-    for (int e = 0; e < 10; ++e) m[e] = C(0);
+        for (int e = 0; e < 10; ++e) m[e] = C(0);
 #pragma unroll
-    for (int s4 = 0; s4 < 4; ++s4) {
-        const int q = r + 4 * s4;  // stencil point (qx, qy, qz) of the node's stencil
-        if (q < npts) {
-            const int qx = q & ((1 << lx) - 1), qy = (q >> lx) & ((1 << ly) - 1), qz = q >> (lx + ly);
-            int cx, cy, cz;
-            C wx, wy, wz;
-            stencil_point<C>(i, g.X0, qx, cx, wx);
-            stencil_point<C>(j, g.Y0, qy, cy, wy);
-            stencil_point<C>(k, g.Z0, qz, cz, wz);
-            const int64_t e0 = 10 * box3_index(g, cx, cy, cz);
-            const C wt = wx * wy * wz;
+        for (int s4 = 0; s4 < 4; ++s4) {
+            const int q = r + 4 * s4;  // stencil point (qx, qy, qz) of the node's stencil
+            if (q < npts) {
+                const int qx = q & ((1 << lx) - 1), qy = (q >> lx) & ((1 << ly) - 1), qz = q >> (lx + ly);
+                int cx, cy, cz;
+                C wx, wy, wz;
+                stencil_point<C>(i, g.X0, qx, cx, wx);
+                stencil_point<C>(j, g.Y0, qy, cy, wy);
+                stencil_point<C>(k, g.Z0, qz, cz, wz);
+                const int64_t e0 = 10 * box3_index(g, cx, cy, cz);
+                const C wt = wx * wy * wz;
 #pragma unroll
-            for (int e = 0; e < 10; ++e) m[e] = fmac(wt, bm * M0[e0 + e] + am * M1[e0 + e], m[e]);
+                for (int e = 0; e < 10; ++e) m[e] = fmac(wt, bm * M0[e0 + e] + am * M1[e0 + e], m[e]);
+            }
         }
-    }
 #pragma unroll
-    for (int o = 2; o > 0; o >>= 1) {
+        for (int o = 2; o > 0; o >>= 1) {
 #pragma unroll
-        for (int e = 0; e < 10; ++e) m[e] += __shfl_xor_sync(0xffffffffu, m[e], o);
+            for (int e = 0; e < 10; ++e) m[e] += __shfl_xor_sync(0xffffffffu, m[e], o);
+        }
+        if (node && r == 0)
+            store_rebuilt_3d<L, S>(ff, (int64_t)g.nfx * g.nfy * g.nfz, i + (int64_t)g.nfx * (j + (int64_t)g.nfy * k), m,
+                                alpha, omega);
     }
-    if (node && r == 0)
-        store_rebuilt_3d<L, S>(ff, (int64_t)g.nfx * g.nfy * g.nfz, i + (int64_t)g.nfx * (j + (int64_t)g.nfy * k), m,
-                            alpha, omega);
 }
 
 // Covered coarse shell (Sec. II.B, fine to coarse): rho, u of the coincident
@@ -480,36 +486,41 @@ __global__ void __launch_bounds__(256) k_restrict3(RefineGeom g, const S *__rest
 {
     using C = CT<S>;
     const int w = g.Wc - 1, h = g.Hc - 1, d = g.Dc - 1;  // shell of [X0+1, X0+Wc-1] x ...
-    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int t = (int)(gt >> 5), l = (int)(gt & 31);
-    const bool node = t < shell3_count(w, h, d);  // lanes past the last node still join the shuffles
-    int a = 0, b = 0, c = 0;
-    if (node) shell3_coord(w, h, d, t, a, b, c);
-    const int x = g.X0 + 1 + a, y = g.Y0 + 1 + b, z = g.Z0 + 1 + c;
-    const int i = 2 * (x - g.X0), j = 2 * (y - g.Y0), k = 2 * (z - g.Z0);
-    C m[10];
+    const int count = shell3_count(w, h, d);
+    // block-strided over the nodes, as k_fill_shell3
+    for (int64_t b0 = blockIdx.x * (int64_t)blockDim.x; b0 < 32 * (int64_t)count;
+         b0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t gt = b0 + threadIdx.x;
+        const int t = (int)(gt >> 5), l = (int)(gt & 31);
+        const bool node = t < count;  // lanes past the last node still join the shuffles
+        int a = 0, b = 0, c = 0;
+        if (node) shell3_coord(w, h, d, t, a, b, c);
+        const int x = g.X0 + 1 + a, y = g.Y0 + 1 + b, z = g.Z0 + 1 + c;
+        const int i = 2 * (x - g.X0), j = 2 * (y - g.Y0), k = 2 * (z - g.Z0);
+        C m[10];
 #pragma unroll
-    for (int e = 0; e < 10; ++e) m[e] = C(0);
-    if (node && l < 27) {
-        const int p = l % 3 - 1, q = (l / 3) % 3 - 1, r = l / 9 - 1;
-        streamed_moments_3d<L, S>(ff_prev, fmask, g.nfx, g.nfy, g.nfz, i + p, j + q, k + r, m);
-        const C wt = C((p ? 1 : 2) * (q ? 1 : 2) * (r ? 1 : 2)) * C(1.0 / 64.0);
+        for (int e = 0; e < 10; ++e) m[e] = C(0);
+        if (node && l < 27) {
+            const int p = l % 3 - 1, q = (l / 3) % 3 - 1, r = l / 9 - 1;
+            streamed_moments_3d<L, S>(ff_prev, fmask, g.nfx, g.nfy, g.nfz, i + p, j + q, k + r, m);
+            const C wt = C((p ? 1 : 2) * (q ? 1 : 2) * (r ? 1 : 2)) * C(1.0 / 64.0);
 #pragma unroll
-        for (int e = 4; e < 10; ++e) m[e] *= wt;
+            for (int e = 4; e < 10; ++e) m[e] *= wt;
+        }
+        C mc[10];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) mc[e] = __shfl_sync(0xffffffffu, m[e], 13);
+#pragma unroll
+        for (int e = 4; e < 10; ++e) {
+            C v = m[e];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            mc[e] = v;
+        }
+        if (node && l == 0)
+            store_rebuilt_3d<L, S>(fc, (int64_t)g.nxc * g.nyc * g.nzc, x + (int64_t)g.nxc * (y + (int64_t)g.nyc * z), mc,
+                                alpha, omega);
     }
-    C mc[10];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) mc[e] = __shfl_sync(0xffffffffu, m[e], 13);
-#pragma unroll
-    for (int e = 4; e < 10; ++e) {
-        C v = m[e];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        mc[e] = v;
-    }
-    if (node && l == 0)
-        store_rebuilt_3d<L, S>(fc, (int64_t)g.nxc * g.nyc * g.nzc, x + (int64_t)g.nxc * (y + (int64_t)g.nyc * z), mc,
-                            alpha, omega);
 }
 
 }  // namespace rr

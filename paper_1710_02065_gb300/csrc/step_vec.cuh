@@ -430,6 +430,10 @@ __device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x
         return;
     }
     const int nx = p.n[0];
+    // A value leaves the row only from its ends (nx is a multiple of V): the
+    // first cell of the row's first thread moving -x, the last cell of its
+    // last thread moving +x.
+    const bool first = x0 == 0, last = x0 + V >= nx;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const int j = opp<L>(i);
@@ -444,12 +448,11 @@ __device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x
         } else {
 #pragma unroll
             for (int kk = 0; kk < G; ++kk) {
-                const int xd = x0 + k0 + kk + L::cx(i);
                 S *t = dst + kk + L::cx(i);
-                if (xd < 0 || xd >= nx) {
+                if (L::cx(i) > 0 ? (k0 + kk == V - 1 && last) : (k0 + kk == 0 && first)) {
                     // wrapped around a periodic x axis; out through a
                     // non-periodic x face: kept in P_i at the node
-                    t = p.periodic[0] ? t + (xd < 0 ? nx : -nx)
+                    t = p.periodic[0] ? t + (L::cx(i) < 0 ? nx : -nx)
                                       : reinterpret_cast<S *>(bout + (size_t)i * dstride) + k0 + kk;
                 }
                 Store<S>::st(t, o[kk][i]);
