@@ -459,8 +459,13 @@ __global__ void __launch_bounds__(256) k_fill_shell3(RefineGeom g, const CT<S> *
                 stencil_point<C>(k, g.Z0, qz, cz, wz);
                 const int64_t e0 = 10 * box3_index(g, cx, cy, cz);
                 const C wt = wx * wy * wz;
+                if (a == C(1)) {  // at t + 1 the moments at t do not enter (uniform: a kernel argument)
 #pragma unroll
-                for (int e = 0; e < 10; ++e) m[e] = fmac(wt, bm * M0[e0 + e] + am * M1[e0 + e], m[e]);
+                    for (int e = 0; e < 10; ++e) m[e] = fmac(wt, M1[e0 + e], m[e]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 10; ++e) m[e] = fmac(wt, bm * M0[e0 + e] + am * M1[e0 + e], m[e]);
+                }
             }
         }
 #pragma unroll
