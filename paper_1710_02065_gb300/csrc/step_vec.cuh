@@ -332,10 +332,17 @@ __device__ __forceinline__ int pull_off(const RowOff &o, int i)
 }
 
 // Address of the row direction i of a cell pulls from, in direction i's
-// array (i times the direction stride in bytes)
-template <class L, class S>
+// array (i times the direction stride in bytes).  The vector path runs on
+// lattices that span less than 2 GB, and the address lies inside the lattice
+// past the thread's cell, so the pull step forms the byte offset from the
+// cell in 32-bit arithmetic (one 64-bit add: measured 1-2 % faster at 16-bit
+// storage); the AA gather-push step keeps the 64-bit form, which measured
+// faster there.
+template <class L, class S, int SP>
 __device__ __forceinline__ const S *vec_row_ptr(const char *bin, int i, const RowOff &o, unsigned dstride)
 {
+    if (SP == kPull)
+        return reinterpret_cast<const S *>(bin + ((unsigned)i * dstride + (unsigned)(pull_off<L>(o, i) * (int)sizeof(S))));
     const char *rb = bin + (long long)pull_off<L>(o, i) * (long long)sizeof(S);
     return reinterpret_cast<const S *>(rb + (size_t)i * dstride);
 }
@@ -391,7 +398,7 @@ __device__ __forceinline__ bool vec_load(const StepParams &p, const char *in0, i
         // diverges on it.
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-            const S *row = vec_row_ptr<L, S>(bin, i, ro, dstride);
+            const S *row = vec_row_ptr<L, S, SP>(bin, i, ro, dstride);
             r.v[i] = RW::ld(row);
             if (L::cx(i) > 0) r.e[i] = Store<S>::ld(row - 1);
             if (L::cx(i) < 0) r.e[i] = Store<S>::ld(row + V);
@@ -399,7 +406,7 @@ __device__ __forceinline__ bool vec_load(const StepParams &p, const char *in0, i
     } else {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-            const S *row = vec_row_ptr<L, S>(bin, i, ro, dstride);
+            const S *row = vec_row_ptr<L, S, SP>(bin, i, ro, dstride);
             r.v[i] = RW::ld(row);
             if (L::cx(i) > 0) r.e[i] = Store<S>::ld(row + dl);
             if (L::cx(i) < 0) r.e[i] = Store<S>::ld(row + dr);
@@ -438,8 +445,8 @@ __device__ __forceinline__ void vec_store(const StepParams &p, char *bout, int x
     for (int i = 0; i < L::Q; ++i) {
         const int j = opp<L>(i);
         // the row y + c_y(i), z + c_z(i): the row direction j = opp(i) pulls from
-        S *dst = reinterpret_cast<S *>(bout + (size_t)j * dstride + (long long)pull_off<L>(ro, j) * (long long)sizeof(S)) +
-                 k0;
+        // (32-bit byte offset from the cell, as the pull step's loads)
+        S *dst = reinterpret_cast<S *>(bout + ((unsigned)j * dstride + (unsigned)(pull_off<L>(ro, j) * (int)sizeof(S)))) + k0;
         if (L::cx(i) == 0) {
             C w[G];
 #pragma unroll
