@@ -51,9 +51,9 @@ def jet_spec(nx=384, ny=256, nz=256, diameter=24.0, sponge=32, Ma=0.3, Re=1e4, c
                 noise=noise, theta=diameter / 40.0, lattice=1)
 
 
-def jet_workload_name(nx, ny, nz):
+def jet_workload_name(nx, ny, nz, lattice="D3Q19"):
     """The workload both benchmark arms name in their config."""
-    return (f"D3Q19 round jet {nx}x{ny}x{nz}, Re_D 1e4, Ma 0.3, two-lattice pull, fused inflow/outflow/sponge "
+    return (f"{lattice} round jet {nx}x{ny}x{nz}, Re_D 1e4, Ma 0.3, two-lattice pull, fused inflow/outflow/sponge "
             "(storage precision in config.storage)")
 
 
@@ -838,8 +838,8 @@ def main():
                     help="refined workloads: 1 runs the refined levels concurrently with the level-0 update "
                          "(lbm_set_level_streams), 0 in order on one stream")
     ap.add_argument("--lattice", default="d3q19", choices=["d2q9", "d3q19", "d3q27"],
-                    help="lattice of the two-level jet (d3q19 / d3q27) and batched workloads (the jet benchmark "
-                         "line is D3Q19)")
+                    help="lattice of the jet (d3q19, the benchmark line, or d3q27), two-level jet and batched "
+                         "workloads")
     ap.add_argument("--batch", default="8x128",
                     help="batched workload: KxN, K periodic requests of N^3 (N^2 for D2Q9) cells")
     ap.add_argument("--grid", default="384x256x256",
@@ -876,6 +876,10 @@ def main():
     nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
     scale = nx / 384.0
     spec = jet_spec(nx, ny, nz, diameter=24.0 * scale, sponge=max(2, int(round(32 * scale))))
+    if args.lattice == "d2q9":
+        raise SystemExit("the jet workload is 3D: --lattice d3q19 or d3q27")
+    lat = args.lattice
+    spec["lattice"] = {"d3q19": lbm.LBM_D3Q19, "d3q27": lbm.LBM_D3Q27}[lat]
     prec = lbm.PRECISIONS[args.precision]
     stream = torch.cuda.Stream()
     clocks = ClockSampler(torch.cuda.current_device())
@@ -901,7 +905,7 @@ def main():
         peak, peak_src = 6800.0, "fallback"
     kind = main_run["launch"]["kernel"]
     kname = {"rows": "k_stream_collide_rows", "cell": "k_stream_collide"}.get(kind, "k_stream_collide_vec")
-    key = f"{kname}_d3q19_{args.precision}_jet{nx}x{ny}x{nz}"
+    key = f"{kname}_{lat}_{args.precision}_jet{nx}x{ny}x{nz}"
     traffic = recorded_traffic(key)
 
     extra = {}
@@ -921,7 +925,7 @@ def main():
                            "gbs": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9,
                            "frac_of_measured_hbm": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9 / peak}
             if name in ("fp16", "bf16") and r["launch"]["kernel"] == "vec2" and r["launch"]["streaming"] == "pull":
-                ins = recorded_issue(f"k_stream_collide_vec_d3q19_{name}_jet", args.grid.lower())
+                ins = recorded_issue(f"k_stream_collide_vec_{lat}_{name}_jet", args.grid.lower())
                 if ins is not None:
                     rate = extra[name]["mlups"] / 1e3  # G cells/s
                     mhz = (clk or {}).get("sm_mhz")
@@ -934,7 +938,7 @@ def main():
                                        "from profiles/ncu_issue.txt, taken on this grid"}
             if name == "fp64":
                 kk = "k_stream_collide_vec" if r["launch"]["kernel"].startswith("vec") else "k_stream_collide"
-                ins = recorded_fp64_inst(f"{kk}_d3q19_fp64_jet")
+                ins = recorded_fp64_inst(f"{kk}_{lat}_fp64_jet")
                 if ins is not None and r["launch"]["kernel"] in ("cell", "vec2"):
                     rate = extra[name]["mlups"] / 1e3  # G cells/s
                     extra[name]["roofline"] = {
@@ -943,14 +947,15 @@ def main():
                         "fp64_inst_per_cell": ins[0], "fp64_tflops": rate * ins[1] / 1e3,
                         "peak_source": "nominal 1.25 TFLOP/s FP64 (625 G FMA/s); counts from profiles/ncu_fp64_inst.txt"}
         # the same jet on D3Q27 (complete third order; 27 populations, 216 B per cell in FP32)
-        spec27 = dict(spec, lattice=lbm.LBM_D3Q27)
-        r = time_precision(lbm, torch, spec27, lbm.PRECISIONS[args.precision], max(20, args.steps // 4),
-                           args.warmup, pg, stream, tune=not args.no_tune)
-        k_ms = float(np.mean(r["per_ms"]))
-        extra["d3q27_" + args.precision] = {
-            "launch": r["launch"], "mlups": r["ncell"] / (k_ms / 1e3) / 1e6,
-            "gbs": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9,
-            "frac_of_measured_hbm": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9 / peak}
+        if lat == "d3q19":
+            spec27 = dict(spec, lattice=lbm.LBM_D3Q27)
+            r = time_precision(lbm, torch, spec27, lbm.PRECISIONS[args.precision], max(20, args.steps // 4),
+                               args.warmup, pg, stream, tune=not args.no_tune)
+            k_ms = float(np.mean(r["per_ms"]))
+            extra["d3q27_" + args.precision] = {
+                "launch": r["launch"], "mlups": r["ncell"] / (k_ms / 1e3) / 1e6,
+                "gbs": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9,
+                "frac_of_measured_hbm": r["bytes_per_cell"] * r["ncell"] / (k_ms / 1e3) / 1e9 / peak}
         if "fp16" in extra:
             extra["fp16_store_speedup"] = extra["fp16"]["mlups"] / (ncell / (kernel_ms / 1e3) / 1e6)
         if "bf16" in extra:
@@ -989,7 +994,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic",
-            "config": {"workload": jet_workload_name(nx, ny, nz),
+            "config": {"workload": jet_workload_name(nx, ny, nz, lat.upper()),
                        "cells": ncell, "tau": spec["tau"], "storage": args.precision,
                        "inlet": "top hat, tanh shear layer theta = D/40, Ma 0.3, 1% seeded noise",
                        "launch": main_run["launch"], "autotune_ms_per_step": main_run["tuning"],
@@ -997,7 +1002,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                         "kernel": f"{kname}<D3Q19>", "bytes_per_cell": bpc,
+                         "kernel": f"{kname}<{lat.upper()}>", "bytes_per_cell": bpc,
                          "kernel_ms": kernel_ms},
             "cpu_baseline": cpu,
             "e2e": ({"value": world * ncell * args.steps / e2e_s / 1e6, "unit": "MLUPS",

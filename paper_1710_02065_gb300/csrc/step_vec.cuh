@@ -597,11 +597,13 @@ __device__ __forceinline__ void update_vec(const StepParams &p, const char *cons
 
 // Minimum resident 256-thread blocks per SM asked of the compiler: 16-bit
 // storage with 2 cells per thread is issue-bound, and 64 registers (4 x 256
-// threads per SM) keep enough warps resident to hide the loads; the wider
+// threads per SM) keep enough warps resident to hide the loads; on D3Q27
+// (27 populations) 64 registers spill, and 3 blocks (80 registers) measured
+// fastest (FP16 jet 45.5 -> 48.7 G cell updates/s; 2 blocks 48.0); the wider
 // types and 4 cells per thread take 128.
-template <class S, int V, int SP = kPull>
+template <class L, class S, int V, int SP = kPull>
 struct VecMinBlocks {
-    static constexpr int value = (sizeof(S) == 2 && V == 2) ? 4 : 2;
+    static constexpr int value = (sizeof(S) == 2 && V == 2) ? (L::Q > 19 ? 3 : 4) : 2;
 };
 
 // Cells collided and stored together (one G-wide store per direction)
@@ -616,7 +618,7 @@ struct VecGroup {
 // ---------------------------------------------------------------------------
 // Grid (x blocks of a row, ny, nz)
 template <class L, class S, class C, int V, int SP>
-__global__ void __launch_bounds__(256, (VecMinBlocks<S, V, SP>::value)) k_stream_collide_vec(const __grid_constant__ StepParams p)
+__global__ void __launch_bounds__(256, (VecMinBlocks<L, S, V, SP>::value)) k_stream_collide_vec(const __grid_constant__ StepParams p)
 {
     update_vec<L, S, C, V, VecGroup<S, V>::value, SP>(p, p.in, p.out, (blockIdx.x * blockDim.x + threadIdx.x) * V,
                                                       blockIdx.y, blockIdx.z);
