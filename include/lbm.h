@@ -293,8 +293,9 @@ int lbm_probe(lbm_handle h, int n, const int64_t *cells, double *p_prime);
  *                      (measured fastest on GB300: 2 for FP16 / BF16 on D3Q19
  *                      and D3Q27 and for FP32 on D3Q27, else 1).  The
  *                      vectorised kernel is used only when
- *                      there is no cell-type mask and nx is a multiple of it;
- *                      otherwise the general kernel runs.  These kernels
+ *                      there is no cell-type mask and nx is a multiple of it
+ *                      (on D3Q27 only with 2 cells per thread); otherwise the
+ *                      general kernel runs.  These kernels
  *                      run when the row-staged kernel (lbm_set_staging) is off
  *                      or not eligible.
  * lbm_get_launch reports the shape lbm_step will use now.

@@ -823,6 +823,13 @@ extern "C" int lbm_set_transfer_staging(lbm_handle h, size_t max_bytes)
     return LBM_OK;
 }
 
+// Cells per thread the vector kernels provide for the handle: D3Q27 has the
+// two-cell form only (other requests run the one-cell-per-thread kernels)
+static bool vec_available(const lbm_ctx *h, int vec)
+{
+    return vec_supported(h->prec, vec) && (h->lattice != LBM_D3Q27 || vec == 2);
+}
+
 static int aa_normalize(lbm_ctx *h);
 
 // Device address of a page-locked host buffer the device can reach (allocated
@@ -1096,7 +1103,7 @@ static cudaError_t launch_update(lbm_ctx *h, const StepParams &p, const void *fi
         }
     }
     int vec = h->vec == 0 ? vec_default(h->lattice, h->prec) : h->vec;
-    if (!vec_eligible(p) || vec == 1 || !vec_supported(h->prec, vec) || p.n[0] % vec != 0) vec = 1;
+    if (!vec_eligible(p) || vec == 1 || !vec_available(h, vec) || p.n[0] % vec != 0) vec = 1;
     const int block = h->block > 0 ? h->block : block_default(vec);
     h->launches += 1;
     if (vec == 1) return step_general(h, p, fin, fout, block);
@@ -1258,7 +1265,7 @@ static cudaError_t aa_step(lbm_ctx *h, const StepParams &p)
 {
     const bool loc = h->aa_odd != 0;
     int vec = h->vec == 0 ? vec_default(h->lattice, h->prec) : h->vec;
-    if (!vec_eligible(p) || vec == 1 || !vec_supported(h->prec, vec) || p.n[0] % vec != 0) vec = 1;
+    if (!vec_eligible(p) || vec == 1 || !vec_available(h, vec) || p.n[0] % vec != 0) vec = 1;
     const int block = h->block > 0 ? h->block : block_default(vec);
     h->launches += 1;
     h->aa_odd ^= 1;
@@ -1718,7 +1725,7 @@ extern "C" int lbm_get_launch(lbm_handle h, int *block, int *cells_per_thread)
 {
     CHECK_HANDLE(h);
     int vec = h->vec == 0 ? vec_default(h->lattice, h->prec) : h->vec;
-    if (h->solid_d || vec == 1 || !vec_supported(h->prec, vec) || h->n[0] % vec != 0) vec = 1;
+    if (h->solid_d || vec == 1 || !vec_available(h, vec) || h->n[0] % vec != 0) vec = 1;
     if (block) *block = h->block > 0 ? h->block : block_default(vec);  // level 0
     if (cells_per_thread) *cells_per_thread = vec;
     return LBM_OK;

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
-from cases import D2Q9, D3Q19, round_jet, to_gpu, to_oracle, acoustic_pulse
+from cases import D2Q9, D3Q19, D3Q27, round_jet, to_gpu, to_oracle, acoustic_pulse
 from test_gpu_parity import PRECS, _boxed_case, _open_box, _pop_tol
 
 pytestmark = pytest.mark.gpu
@@ -40,7 +40,7 @@ def _aa(c, prec, kernel=None):
 
 
 @pytest.mark.parametrize("prec", list(PRECS))
-@pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
+@pytest.mark.parametrize("lattice", [D2Q9, D3Q19, D3Q27])
 def test_aa_every_boundary_rule_matches_oracle(lattice, prec):
     c = _boxed_case(lattice)
     P, f = to_oracle(c)
@@ -58,17 +58,19 @@ def test_aa_every_boundary_rule_matches_oracle(lattice, prec):
 
 @pytest.mark.parametrize("kernel", [1, 2, 4])
 @pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
-@pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
+@pytest.mark.parametrize("lattice", [D2Q9, D3Q19, D3Q27])
 def test_aa_open_box_and_periodic_axes_match_oracle(lattice, prec, kernel):
     """No cell-type mask: open box with inflow profile and noise, outflow,
     sponges; and the same box periodic in y / z.  One, two and four cells
-    per thread (the vector kernel updates the x-face nodes in registers)."""
+    per thread (the vector kernel updates the x-face nodes in registers; on
+    D3Q27, which has the two-cell form only, a request for four runs the
+    general in-place kernel)."""
     _, _, _, w, _ = oracle.lattice(lattice)
     n = (40, 12, 1) if lattice == D2Q9 else (24, 10, 8)
     for periodic in (False, True):
         c = _open_box(lattice, n, seed=7, rest=True)
         if periodic:
-            for face in range(2, 6 if lattice == D3Q19 else 4):
+            for face in range(2, 4 if lattice == D2Q9 else 6):
                 c.faces.pop(face, None)
             c.sponges = {1: (5, 0.8)}
         P, f = to_oracle(c)
@@ -81,13 +83,14 @@ def test_aa_open_box_and_periodic_axes_match_oracle(lattice, prec, kernel):
 
 
 @pytest.mark.parametrize("prec", list(PRECS))
-@pytest.mark.parametrize("lattice", [D2Q9, D3Q19])
+@pytest.mark.parametrize("lattice", [D2Q9, D3Q19, D3Q27])
 def test_aa_whole_warp_rows_match_oracle(lattice, prec):
     """Two cells per thread on rows of whole warps (nx = 128: two warps per
-    row), where the gather-push step trades the x-moving populations between
-    lanes and stores aligned pairs: an open x axis (inflow with profile and
-    noise, outflow, sponges) and a periodic one (the values crossing the
-    row's ends wrap around), after odd and even step counts."""
+    row, and the x-moving populations cross from warp to warp; only the row's
+    first and last threads push values out of the row): an open x axis
+    (inflow with profile and noise, outflow, sponges; values leaving through
+    a face are kept at the node) and a periodic one (they wrap around), after
+    odd and even step counts."""
     _, _, _, w, _ = oracle.lattice(lattice)
     n = (128, 10, 1) if lattice == D2Q9 else (128, 8, 6)
     for xper in (False, True):

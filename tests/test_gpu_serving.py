@@ -213,13 +213,16 @@ def test_late_arrival_is_bitwise_the_same_as_alone(serving):
     assert np.array_equal(alone[0], got[0]) and np.array_equal(alone[1], got[1])
 
 
-@pytest.mark.parametrize("lattice,N,prec", [(0, 48, 2), (0, 48, 3), (1, 16, 2), (1, 16, 3)])
-def test_16bit_served_results_match_oracle(serving, lattice, N, prec):
-    """FP16 / BF16 storage in the server against the FP64 oracle: the density
-    error stays within the rounding of the stored shifted populations (one
-    half-ulp of max |f - w| per step and direction, summed over Q)."""
-    r = _req(lattice, N, 0.66, 30, prec)
-    rho_g, u_g, rc = _run(serving, [r])[0]
+@pytest.mark.parametrize("lattice,N,prec,aa", [(0, 48, 2, False), (0, 48, 3, False), (1, 16, 2, False),
+                                               (1, 16, 3, False), (2, 12, 2, False), (2, 12, 3, False),
+                                               (0, 48, 3, True), (1, 16, 2, True), (2, 12, 2, True)])
+def test_16bit_served_results_match_oracle(serving, lattice, N, prec, aa):
+    """FP16 / BF16 storage in the server against the FP64 oracle, D2Q9, D3Q19
+    and D3Q27, two-lattice pull and in-place AA: the density error stays
+    within the rounding of the stored shifted populations (one half-ulp of
+    max |f - w| per step and direction, summed over Q)."""
+    r = _req(lattice, N, 0.66, 31 if aa else 30, prec)  # AA: an odd count ends in the push layout
+    rho_g, u_g, rc = _run_aa(serving, [r])[0] if aa else _run(serving, [r])[0]
     assert rc == 0
     rho0, u0 = inputs.request_initial_state(r)
     P = oracle.Problem(lattice, r["extents"], r["tau"])
