@@ -513,9 +513,7 @@ __device__ __forceinline__ void vec_collide_store(const StepParams &p, char *out
                                                         : (p.kind[1] != BC_OUTFLOW ? 1 : -1));
                 C chi = C(0);
                 if (inlet >= 0) {
-#ifndef NOFACE
                     m = face_moments<L, C>(p, m, inlet, x, y, z);
-#endif
                 } else {
                     chi = chirow;
                     if (!(x >= p.blo[0] && x < p.bhi[0]) && p.any_sponge) {
